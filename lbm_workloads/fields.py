@@ -1,0 +1,93 @@
+"""Seeded synthetic workloads: grids, boundary layouts and initial fields.
+
+Input generation only: these functions draw random numbers and lay out
+arrays; they contain no step of the lattice Boltzmann method.  Both the CUDA
+library (through its Python binding) and the CPU oracle take their inputs
+from here.  Random draws use numpy's Philox counter-based generator keyed by
+the seed, so the same bits reach both sides.
+
+Every workload is a dict:
+  lattice      "D3Q27" or "D2Q9"
+  shape        (nx, ny, nz)
+  dx           lattice spacing (m)
+  T_max        temperature bound for the default reference speed (K)
+  substeps     reaction sub-steps l
+  faces        boundary kind per face (-x, +x, -y, +y, -z, +z)
+  P, T         [nz, ny, nx] initial pressure (Pa) and temperature (K)
+  u            [3, nz, ny, nx] initial velocity (m/s)
+  Y            [M, nz, ny, nx] initial mass fractions
+  steps        nominal number of steps of the workload
+and, where the faces need them, the inlet and wall data.
+"""
+import numpy as np
+
+from .mechanism import (P_STANDARD, air_mole_fractions, mole_to_mass_fractions,
+                        h2_air_synthetic)
+
+
+def philox(seed: int) -> np.random.Generator:
+    return np.random.Generator(np.random.Philox(key=int(seed)))
+
+
+def _uniform_fields(mech, shape, T, P, Y, u=(0.0, 0.0, 0.0)):
+    nx, ny, nz = shape
+    g = (nz, ny, nx)
+    return dict(
+        P=np.full(g, float(P)), T=np.full(g, float(T)),
+        u=np.stack([np.full(g, float(v)) for v in u]),
+        Y=np.stack([np.full(g, float(y)) for y in Y]))
+
+
+def reactor(seed=0, n=16, phi=0.5, T0=1200.0, P=P_STANDARD, dx=1.0e-3,
+            perturbation=1e-3, steps=200, mech=None):
+    """Homogeneous constant-volume reactor: n^3 periodic D3Q27 box, fresh
+    H2/air at equivalence ratio phi, zero velocity, T = T0 (1 + eps U(-1,1))
+    with a seeded uniform perturbation (the paper's perfectly stirred reactor,
+    Sec. 3.8, on a larger box)."""
+    mech = mech or h2_air_synthetic()
+    Y = mole_to_mass_fractions(mech, air_mole_fractions(mech, phi))
+    w = _uniform_fields(mech, (n, n, n), T0, P, Y)
+    if perturbation:
+        w["T"] = T0 * (1.0 + perturbation * philox(seed).uniform(-1.0, 1.0, size=w["T"].shape))
+    w.update(lattice="D3Q27", shape=(n, n, n), dx=dx, T_max=3000.0, substeps=2,
+             faces=("periodic",) * 6, steps=steps, name=f"reactor {n}^3 D3Q27 phi={phi}",
+             seed=seed)
+    return w
+
+
+def flame_1d(seed=0, nx=1024, ny=4, nz=4, phi=0.5, T_u=300.0, T_b=1500.0,
+             x_ign=256, width=4.0, dx=12.5e-6, steps=20000, mech=None):
+    """Quasi-1D premixed flame: nx x ny x nz D3Q27, periodic in y and z,
+    velocity inlet at x = 0 (fresh mixture at phi, T_u, speed u_in drawn from
+    the seed in [0.5, 2] m/s) and pressure outlet at x = nx-1; a tanh
+    temperature kernel T_u -> T_b centred at x_ign ignites the mixture."""
+    mech = mech or h2_air_synthetic()
+    rng = philox(seed)
+    u_in = float(rng.uniform(0.5, 2.0))
+    Y = mole_to_mass_fractions(mech, air_mole_fractions(mech, phi))
+    w = _uniform_fields(mech, (nx, ny, nz), T_u, P_STANDARD, Y, u=(u_in, 0.0, 0.0))
+    x = np.arange(nx, dtype=float)
+    Tx = T_u + (T_b - T_u) * 0.5 * (1.0 + np.tanh((x - x_ign) / width))
+    w["T"] = np.broadcast_to(Tx, (nz, ny, nx)).copy()
+    w.update(lattice="D3Q27", shape=(nx, ny, nz), dx=dx, T_max=3000.0, substeps=2,
+             faces=("inlet", "outlet", "periodic", "periodic", "periodic", "periodic"),
+             inlet=dict(u=np.array([u_in, 0.0, 0.0]), T=T_u, Y=Y, P=P_STANDARD),
+             outlet=dict(P=P_STANDARD), steps=steps, seed=seed,
+             name=f"flame {nx}x{ny}x{nz} D3Q27 phi={phi} u_in={u_in:.3f}")
+    return w
+
+
+def shear_wave(nx=32, ny=1, nz=1, amplitude=1e-3, background=0.0, T=300.0,
+               dx=1e-6, lattice="D3Q27", mech=None):
+    """Decaying transverse shear wave u_y(x) = amplitude sin(2 pi x/nx) in a
+    uniform single-fluid (binary, equal composition) state, periodic box."""
+    from .mechanism import binary_inert
+    mech = mech or binary_inert()
+    nzz = nz if lattice == "D3Q27" else 1
+    w = _uniform_fields(mech, (nx, ny, nzz), T, P_STANDARD, (0.5, 0.5))
+    x = np.arange(nx)
+    w["u"][1] = amplitude * np.sin(2.0 * np.pi * x / nx)[None, None, :]
+    w["u"][0] = background
+    w.update(lattice=lattice, shape=(nx, ny, nzz), dx=dx, T_max=T, substeps=1,
+             faces=("periodic",) * 6, steps=0, name="shear wave")
+    return w
