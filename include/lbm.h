@@ -1,0 +1,220 @@
+/*
+ * lbm.h - C ABI of the GB300 reactive-mixture lattice Boltzmann library.
+ *
+ * The library advances the lattice Boltzmann model for reactive mixtures of
+ * Sawant, Dorschner & Karlin (arXiv 2108.07605): M species lattices with
+ * Stefan-Maxwell diffusion and reaction sources (Sec. 2), a momentum lattice
+ * f with the extended equilibrium and an energy lattice g carrying the
+ * enthalpy of formation (Sec. 3), the M-th species slaved to f (Sec. 3.7,
+ * Eq. strongest), Arrhenius chemistry in l forward-Euler sub-steps at frozen
+ * energy (Sec. 2.4, Eq. R3) and the temperature recovered from energy by
+ * Newton iteration (Sec. 3.1, Eq. temperature).  Every step runs in CUDA
+ * kernels for sm_103a on the caller's stream; there is no CPU fallback.
+ *
+ * Conventions shared by all entry points
+ *  - Units at the boundary are SI: kg/m^3, m/s, K, Pa, J/kg.  Internally the
+ *    library uses lattice units dx = dt = 1 with acoustic scaling (Sec. 3.6):
+ *    velocities are divided by the reference speed c_ref, dt = dx / c_ref.
+ *  - Node index n = x + nx*(y + ny*z), x fastest; N = nx*ny*nz.
+ *  - Field arrays: scalar fields [N]; velocity [3][N] (component-major, all
+ *    three components even for D2Q9, where u_z is written as 0 and ignored
+ *    on input); mass fractions [M][N] (species-major).
+ *  - Populations: [lattice][i][N] with lattice 0..M-2 the stored species,
+ *    M-1 the momentum lattice f, M the energy lattice g; velocity index
+ *    i = (cz+1)*9 + (cy+1)*3 + (cx+1) (D3Q27) or (cy+1)*3 + (cx+1) (D2Q9),
+ *    so the opposite of i is Q-1-i.
+ *  - "on_device" = 1: pointers are device memory of the handle's GPU and the
+ *    call is asynchronous on the handle's stream; 0: host memory, the call
+ *    copies and synchronises the stream.
+ *  - The caller owns every array it passes.  The library owns its population
+ *    buffers, allocated through cfg->dev_alloc (or cudaMalloc when NULL) at
+ *    lbm_create and released at lbm_destroy.
+ *  - Errors: calls return lbm_status.  Invalid arguments return
+ *    LBM_ERR_INVALID without touching state.  Device-side failures (Newton
+ *    not converged, non-finite moments) are recorded in a sticky status word
+ *    and returned by the next synchronising call (lbm_moments,
+ *    lbm_synchronize, lbm_get_populations).  lbm_last_error() gives text.
+ */
+#ifndef LBM_H
+#define LBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LBM_MAX_SPECIES 9
+#define LBM_MAX_REACTIONS 32
+#define LBM_NCP 3
+
+typedef enum {
+  LBM_OK = 0,
+  LBM_ERR_INVALID = 1,   /* bad argument or configuration                   */
+  LBM_ERR_OOM = 2,       /* device allocation failed                        */
+  LBM_ERR_CUDA = 3,      /* a CUDA runtime call failed                      */
+  LBM_ERR_NEWTON = 4,    /* temperature Newton did not converge (Eq. temperature) */
+  LBM_ERR_NONFINITE = 5, /* a non-finite or non-positive density appeared   */
+  LBM_ERR_RANGE = 6,     /* size beyond a documented limit                  */
+  LBM_ERR_TIMEOUT = 7,   /* a bounded device wait gave up                   */
+  LBM_ERR_STATE = 8      /* call out of order (e.g. step before init)       */
+} lbm_status;
+
+typedef enum { LBM_D2Q9 = 0, LBM_D3Q27 = 1 } lbm_lattice;
+
+/* Storage precision of the populations.  LBM_FP64: every operation in FP64
+ * (the path checked against the oracle to 1e-10).  LBM_FP32_STORE:
+ * populations stored in FP32; chemistry, Newton and transport in FP64. */
+typedef enum { LBM_FP64 = 0, LBM_FP32_STORE = 1, LBM_FP16_OFFSET = 2 } lbm_precision;
+
+/* Face boundary kinds (Sec. 4): periodic; bounce-back wall (Eq. bb);
+ * Tamm-Mott-Smith isothermal wall (Sec. 4.2.2); flux inlet (Sec. 4.3);
+ * LODI outlet with convective mass fractions (Sec. 4.4). */
+typedef enum {
+  LBM_PERIODIC = 0, LBM_BOUNCE_BACK = 1, LBM_TMS_WALL = 2, LBM_INLET = 3,
+  LBM_OUTLET = 4
+} lbm_bc;
+
+/* Species, thermodynamics, reactions and transport (Sec. 3.6).  Plain data,
+ * copied by lbm_create.
+ *  Heat capacity  c_p/R_U = cp[a][0] + cp[a][1] T + cp[a][2] T^2.
+ *  Enthalpy       h_a = h_formation[a] + int_T0^T c_p dT'  (J/mol, T0 = 298.15 K).
+ *  Entropy        s_a = s_standard[a] + int_T0^T c_p/T' dT' (J/(mol K)).
+ *  Rate constant  k_f = A T^b exp(-Ea/(R_U T)), SI (m^3/mol)^(order-1)/s.
+ *  Reverse rate   k_f / K_c, K_c from the table's Gibbs energies.
+ *  Third body     [M] = sum_a efficiency[r][a] C_a multiplies the rate.
+ *  Transport      D_ab = D0[a][b] (T/T0)^D_T_exponent (P0/P);
+ *                 mu = mu0 (T/T0)^mu_T_exponent; lambda = mu c_p / prandtl. */
+typedef struct lbm_mechanism {
+  int n_species;                                   /* M, 2..LBM_MAX_SPECIES */
+  int n_reactions;                                 /* 0..LBM_MAX_REACTIONS  */
+  double molar_mass[LBM_MAX_SPECIES];              /* kg/mol                */
+  double cp[LBM_MAX_SPECIES][LBM_NCP];
+  double h_formation[LBM_MAX_SPECIES];             /* J/mol at T0           */
+  double s_standard[LBM_MAX_SPECIES];              /* J/(mol K) at T0, P0   */
+  int nu_f[LBM_MAX_REACTIONS][LBM_MAX_SPECIES];    /* reactant coefficients */
+  int nu_r[LBM_MAX_REACTIONS][LBM_MAX_SPECIES];    /* product coefficients  */
+  double arrhenius[LBM_MAX_REACTIONS][3];          /* A, b, Ea (J/mol)      */
+  int third_body[LBM_MAX_REACTIONS];
+  double efficiency[LBM_MAX_REACTIONS][LBM_MAX_SPECIES];
+  int reversible[LBM_MAX_REACTIONS];
+  double D0[LBM_MAX_SPECIES][LBM_MAX_SPECIES];     /* m^2/s at T0, P0       */
+  double D_T_exponent;
+  double mu0;                                      /* Pa s at T0            */
+  double mu_T_exponent;
+  double prandtl;
+} lbm_mechanism;
+
+typedef struct lbm_config {
+  lbm_lattice lattice;
+  int nx, ny, nz;             /* nz = 1 for D2Q9                              */
+  lbm_precision precision;
+  int substeps;               /* reaction sub-steps l (Eq. R3), >= 1          */
+  double dx;                  /* lattice spacing, m                           */
+  double c_ref;               /* reference speed, m/s; 0 selects
+                                 sqrt(max_a R_a * T_max / 0.9)               */
+  double T_max;               /* K, used only by the default c_ref            */
+  lbm_mechanism mech;
+  lbm_bc face_bc[6];          /* faces -x, +x, -y, +y, -z, +z                  */
+  double wall_T[6];           /* TMS wall temperature per face, K             */
+  const double* inlet_u;      /* host [3][face nodes] inlet velocity, m/s, or
+                                 NULL for the uniform inlet_u_uniform         */
+  double inlet_u_uniform[3];
+  double inlet_Y[LBM_MAX_SPECIES];
+  double inlet_T, inlet_P;
+  double outlet_P;            /* LODI target pressure, Pa                     */
+  double outlet_sigma;        /* LODI relaxation factor                       */
+  int newton_max_iter;        /* default 50                                   */
+  double newton_rtol;         /* default 1e-13                                */
+  void* (*dev_alloc)(size_t bytes, void* user);  /* NULL: cudaMalloc          */
+  void (*dev_free)(void* ptr, void* user);
+  void* alloc_user;
+  void* stream;               /* cudaStream_t; NULL = legacy default stream   */
+  int device;                 /* CUDA device ordinal                          */
+} lbm_config;
+
+/* Derived lattice-unit data of a handle. */
+typedef struct lbm_info {
+  int Q, D, L, M;             /* velocities, dimension, lattices, species     */
+  long long n_nodes;
+  double c_ref, dt, dx;       /* m/s, s, m                                    */
+  size_t bytes_per_population;
+  size_t device_bytes;        /* everything the handle allocated              */
+  long long steps_done;
+} lbm_info;
+
+typedef struct lbm_ctx* lbm_t;
+
+/* Fill *cfg with defaults (D3Q27, FP64, periodic, l = 2, Newton 50 / 1e-13,
+ * T_max = 3000 K, outlet_sigma = 0.25).  Mechanism left zeroed. */
+void lbm_config_defaults(lbm_config* cfg);
+
+/* Bytes of device memory lbm_create would allocate for cfg, or 0 if cfg is
+ * invalid.  Lets a caller admit work against a memory budget. */
+size_t lbm_bytes_required(const lbm_config* cfg);
+
+/* Validate cfg, copy it, allocate the handle's device buffers.  Populations
+ * are undefined until lbm_init_fields.  On failure *out is NULL. */
+lbm_status lbm_create(const lbm_config* cfg, lbm_t* out);
+
+/* Set every population to the equilibria of the given fields (Sec. 4.1,
+ * Eqs. faEqGeneral, fEqGeneral, gEqGeneral): species f_a^eq(rho Y_a, u, T)
+ * for a < M, the momentum equilibrium f^eq(rho, Y, u, T) (Eq. feq) and the
+ * energy equilibrium g^eq(rho, Y, u, T) (Eq. geq_i).  rho [N] kg/m^3,
+ * u [3][N] m/s, T [N] K, Y [M][N].  Also sets the temperature guess. */
+lbm_status lbm_init_fields(lbm_t h, const double* rho, const double* u,
+                           const double* T, const double* Y, int on_device);
+
+/* As lbm_init_fields with the density from the ideal-gas law
+ * rho = P / (R T), R = R_U sum_a Y_a/m_a (Sec. 2.1, Eq. eosIdealGas);
+ * P [N] in Pa. */
+lbm_status lbm_init_fields_pressure(lbm_t h, const double* P, const double* u,
+                                    const double* T, const double* Y,
+                                    int on_device);
+
+/* Advance nsteps time steps (each: pull streaming, boundary reconstruction,
+ * moments, temperature, relaxation, gradients, diffusion velocities,
+ * reaction sub-steps, collision of all lattices; Sec. 2.3, Sec. 3, Sec. 4).
+ * Asynchronous on the handle's stream. */
+lbm_status lbm_step(lbm_t h, int nsteps);
+
+/* As lbm_step, and adds each kernel's device time in milliseconds, measured
+ * with CUDA events recorded on the handle's stream around every launch:
+ * kernel_ms[0] += moments/temperature kernel, kernel_ms[1] += collision
+ * kernel (n_kernels >= 2).  Synchronises the stream before returning. */
+lbm_status lbm_step_timed(lbm_t h, int nsteps, double* kernel_ms, int n_kernels);
+
+/* Fields of the stored post-collision state in SI units, T from Newton on
+ * Eq. temperature.  Any pointer may be NULL to skip that field.
+ * rho [N], u [3][N], T [N], Y [M][N], E [N] total specific energy (J/kg).
+ * Host pointers (on_device = 0) synchronise and return sticky errors. */
+lbm_status lbm_moments(lbm_t h, double* rho, double* u, double* T, double* Y,
+                       double* E, int on_device);
+
+/* All stored populations converted to FP64, layout [lattice][i][N]
+ * (lattice-unit values: species and f in kg/m^3, g in kg/m^3 * J/kg / c_ref^2). */
+lbm_status lbm_get_populations(lbm_t h, double* out, int on_device);
+
+/* Wait for the handle's stream; returns and clears nothing else than the
+ * sticky device status. */
+lbm_status lbm_synchronize(lbm_t h);
+
+/* Checkpoint: raw populations (storage precision), temperature guess and
+ * boundary history.  lbm_get_state with buf == NULL stores the size. */
+lbm_status lbm_get_state(lbm_t h, void* buf, size_t* bytes);
+lbm_status lbm_set_state(lbm_t h, const void* buf, size_t bytes);
+
+lbm_status lbm_get_info(lbm_t h, lbm_info* info);
+
+/* Release the handle and its device memory.  Returns the sticky status. */
+lbm_status lbm_destroy(lbm_t h);
+
+/* Text of the last error on h (or of the last lbm_create failure if h is
+ * NULL).  Valid until the next call on h. */
+const char* lbm_last_error(lbm_t h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LBM_H */

@@ -1,0 +1,546 @@
+// Host side of the C ABI declared in include/lbm.h: configuration checks,
+// mechanism preprocessing, device buffers, launches and error reporting.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "lbm_internal.h"
+
+using namespace lbm;
+
+struct lbm_ctx {
+  lbm_config cfg;
+  int D, Q, M, L, NF;
+  Geom g;
+  Units un;
+  DevMech mech;
+  size_t elem;              // bytes per stored population
+  void* pops[2] = {nullptr, nullptr};
+  int cur = 0;
+  double* rec = nullptr;    // moment records (scratch)
+  double* Tf = nullptr;     // temperature guess
+  int* status = nullptr;    // sticky device status word
+  double* io = nullptr;     // staging for host <-> device field copies
+  size_t io_bytes = 0;
+  cudaStream_t stream = nullptr;
+  size_t bytes = 0;
+  long long steps = 0;
+  bool initialized = false;
+  std::string err;
+};
+
+static thread_local std::string g_create_error;
+
+namespace {
+
+lbm_status fail(lbm_ctx* h, lbm_status st, const std::string& msg) {
+  if (h) h->err = msg; else g_create_error = msg;
+  return st;
+}
+
+lbm_status cuda_fail(lbm_ctx* h, cudaError_t e, const char* where) {
+  return fail(h, LBM_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+void* dalloc(const lbm_config& c, size_t bytes) {
+  if (bytes == 0) return nullptr;
+  if (c.dev_alloc) return c.dev_alloc(bytes, c.alloc_user);
+  void* p = nullptr;
+  if (cudaMalloc(&p, bytes) != cudaSuccess) return nullptr;
+  return p;
+}
+
+void dfree(const lbm_config& c, void* p) {
+  if (!p) return;
+  if (c.dev_free) c.dev_free(p, c.alloc_user);
+  else cudaFree(p);
+}
+
+int lattice_dim(lbm_lattice l) { return l == LBM_D3Q27 ? 3 : 2; }
+
+double default_c_ref(const lbm_config& c) {
+  double rmax = 0.0;
+  for (int a = 0; a < c.mech.n_species; ++a) rmax = std::max(rmax, R_U / c.mech.molar_mass[a]);
+  return std::sqrt(rmax * c.T_max / 0.9);
+}
+
+// Returns an empty string when cfg is valid.
+std::string validate(const lbm_config* c) {
+  if (!c) return "config is NULL";
+  if (c->lattice != LBM_D3Q27 && c->lattice != LBM_D2Q9) return "unknown lattice";
+  if (c->nx < 1 || c->ny < 1 || c->nz < 1) return "grid extents must be >= 1";
+  if (c->lattice == LBM_D2Q9 && c->nz != 1) return "D2Q9 needs nz = 1";
+  if (c->precision != LBM_FP64 && c->precision != LBM_FP32_STORE)
+    return "precision not supported by this build (FP64, FP32_STORE)";
+  if (c->substeps < 1 || c->substeps > 64) return "substeps must be in 1..64";
+  if (!(c->dx > 0.0) || !std::isfinite(c->dx)) return "dx must be positive";
+  if (c->c_ref < 0.0 || !std::isfinite(c->c_ref)) return "c_ref must be >= 0";
+  if (c->c_ref == 0.0 && !(c->T_max > 0.0)) return "T_max must be positive when c_ref = 0";
+  const lbm_mechanism& m = c->mech;
+  if (m.n_species != 2 && m.n_species != 9)
+    return "n_species must be 2 or 9 in this build";
+  if (m.n_reactions < 0 || m.n_reactions > LBM_MAX_REACTIONS) return "n_reactions out of range";
+  for (int a = 0; a < m.n_species; ++a) {
+    if (!(m.molar_mass[a] > 0.0)) return "molar masses must be positive";
+    for (int b = 0; b < m.n_species; ++b)
+      if (a != b && !(m.D0[a][b] > 0.0)) return "D0 must be positive off the diagonal";
+  }
+  for (int r = 0; r < m.n_reactions; ++r) {
+    int nr = 0, np = 0;
+    for (int a = 0; a < m.n_species; ++a) {
+      if (m.nu_f[r][a] < 0 || m.nu_r[r][a] < 0) return "stoichiometric coefficients must be >= 0";
+      nr += m.nu_f[r][a];
+      np += m.nu_r[r][a];
+    }
+    if (nr < 1 || nr > 3 || np < 1 || np > 3) return "reactions need 1..3 molecules per side";
+    if (!(m.arrhenius[r][0] > 0.0)) return "Arrhenius A must be positive";
+  }
+  if (!(m.mu0 > 0.0) || !(m.prandtl > 0.0)) return "mu0 and prandtl must be positive";
+  for (int f = 0; f < 6; ++f)
+    if (c->face_bc[f] != LBM_PERIODIC)
+      return "non-periodic faces are not supported by this build";
+  if (c->newton_max_iter < 1 || !(c->newton_rtol >= 0.0)) return "bad Newton parameters";
+  if (c->device < 0) return "device must be >= 0";
+  return "";
+}
+
+void build_mech(const lbm_mechanism& m, DevMech& d) {
+  std::memset(&d, 0, sizeof(d));
+  d.M = m.n_species;
+  d.R = m.n_reactions;
+  const double T0 = T_REF;
+  for (int a = 0; a < m.n_species; ++a) {
+    const double mm = m.molar_mass[a];
+    const double a0 = m.cp[a][0], a1 = m.cp[a][1], a2 = m.cp[a][2];
+    d.mm[a] = mm;
+    d.inv_mm[a] = 1.0 / mm;
+    d.Ra[a] = R_U / mm;
+    const double poly0 = a0 * T0 + 0.5 * a1 * T0 * T0 + a2 / 3.0 * T0 * T0 * T0;
+    d.u0[a] = (m.h_formation[a] - R_U * poly0) / mm;
+    d.u1[a] = d.Ra[a] * (a0 - 1.0);
+    d.u2[a] = d.Ra[a] * 0.5 * a1;
+    d.u3[a] = d.Ra[a] * a2 / 3.0;
+    d.g_inv[a] = m.h_formation[a] / R_U - poly0;
+    d.g0[a] = a0 - m.s_standard[a] / R_U + a0 * std::log(T0) + a1 * T0 + 0.5 * a2 * T0 * T0;
+    d.g1[a] = -0.5 * a1;
+    d.g2[a] = -a2 / 6.0;
+    d.a0[a] = a0;
+    for (int b = 0; b < m.n_species; ++b)
+      d.K[a][b] = a == b ? 0.0 : 1.0 / (mm * m.molar_mass[b] * m.D0[a][b]);
+  }
+  d.ln_p0_over_ru = std::log(P_REF / R_U);
+  for (int r = 0; r < m.n_reactions; ++r) {
+    DevReaction& x = d.rx[r];
+    x.nr = x.np = 0;
+    x.dn = 0;
+    for (int a = 0; a < m.n_species; ++a) {
+      for (int k = 0; k < m.nu_f[r][a]; ++k) x.reac[x.nr++] = a;
+      for (int k = 0; k < m.nu_r[r][a]; ++k) x.prod[x.np++] = a;
+      x.dn += m.nu_r[r][a] - m.nu_f[r][a];
+      d.eff[r][a] = m.efficiency[r][a];
+    }
+    x.reversible = m.reversible[r] ? 1 : 0;
+    x.third_body = m.third_body[r] ? 1 : 0;
+    x.lnA = std::log(m.arrhenius[r][0]);
+    x.b = m.arrhenius[r][1];
+    x.EaR = m.arrhenius[r][2] / R_U;
+  }
+  d.D_T_exp = m.D_T_exponent;
+  d.mu0 = m.mu0;
+  d.mu_T_exp = m.mu_T_exponent;
+  d.inv_prandtl = 1.0 / m.prandtl;
+}
+
+size_t elem_size(lbm_precision p) { return p == LBM_FP64 ? 8 : 4; }
+
+struct Sizes {
+  size_t pops, rec, tf, status, io, total;
+};
+
+Sizes sizes_for(const lbm_config& c) {
+  const int D = lattice_dim(c.lattice);
+  const int Q = D == 3 ? 27 : 9;
+  const int M = c.mech.n_species;
+  const long long N = (long long)c.nx * c.ny * c.nz;
+  Sizes s;
+  s.pops = (size_t)(M + 1) * Q * N * elem_size(c.precision);
+  s.rec = (size_t)record_fields(D, M) * N * sizeof(double);
+  s.tf = (size_t)N * sizeof(double);
+  s.status = 256;
+  s.io = 0;
+  s.total = 2 * s.pops + s.rec + s.tf + s.status;
+  return s;
+}
+
+lbm_status check_status(lbm_ctx* h) {
+  int st = 0;
+  cudaError_t e = cudaMemcpyAsync(&st, h->status, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "status read");
+  if (st & ST_NEWTON) return fail(h, LBM_ERR_NEWTON, "temperature Newton did not converge");
+  if (st & ST_NONFINITE) return fail(h, LBM_ERR_NONFINITE, "non-finite or non-positive density or temperature");
+  if (st & ST_RANGE) return fail(h, LBM_ERR_RANGE, "value out of range");
+  return LBM_OK;
+}
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    cudaGetDevice(&prev);
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int now = -1;
+    cudaGetDevice(&now);
+    if (prev >= 0 && now != prev) cudaSetDevice(prev);
+  }
+};
+
+lbm_status ensure_io(lbm_ctx* h, size_t bytes) {
+  if (h->io_bytes >= bytes) return LBM_OK;
+  if (h->io) {
+    cudaStreamSynchronize(h->stream);
+    dfree(h->cfg, h->io);
+    h->bytes -= h->io_bytes;
+    h->io = nullptr;
+    h->io_bytes = 0;
+  }
+  h->io = static_cast<double*>(dalloc(h->cfg, bytes));
+  if (!h->io) return fail(h, LBM_ERR_OOM, "staging buffer allocation failed");
+  h->io_bytes = bytes;
+  h->bytes += bytes;
+  return LBM_OK;
+}
+
+lbm_status init_common(lbm_ctx* h, const double* rho_or_P, int is_pressure, const double* u,
+                       const double* T, const double* Y, int on_device) {
+  if (!h) return fail(nullptr, LBM_ERR_INVALID, "handle is NULL");
+  if (!rho_or_P || !u || !T || !Y) return fail(h, LBM_ERR_INVALID, "field pointer is NULL");
+  DeviceGuard dg(h->cfg.device);
+  const long long N = h->g.N;
+  const int M = h->M;
+  const double *drho = rho_or_P, *du = u, *dT = T, *dY = Y;
+  if (!on_device) {
+    const size_t need = (size_t)(1 + 3 + 1 + M) * N * sizeof(double);
+    lbm_status st = ensure_io(h, need);
+    if (st != LBM_OK) return st;
+    double* p = h->io;
+    const size_t nb = N * sizeof(double);
+    cudaError_t e = cudaMemcpyAsync(p, rho_or_P, nb, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(p + N, u, 3 * nb, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(p + 4 * N, T, nb, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(p + 5 * N, Y, M * nb, cudaMemcpyHostToDevice, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "field upload");
+    drho = p; du = p + N; dT = p + 4 * N; dY = p + 5 * N;
+  }
+  cudaError_t e = cudaMemsetAsync(h->status, 0, sizeof(int), h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "status reset");
+  e = launch_init(h->D, M, h->cfg.precision, h->mech, h->g, h->un, drho, is_pressure, du, dT,
+                  dY, h->pops[h->cur], h->Tf, h->status, h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "init kernel");
+  h->initialized = true;
+  h->steps = 0;
+  if (!on_device) return check_status(h);
+  return LBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void lbm_config_defaults(lbm_config* cfg) {
+  if (!cfg) return;
+  std::memset(cfg, 0, sizeof(*cfg));
+  cfg->lattice = LBM_D3Q27;
+  cfg->nx = cfg->ny = cfg->nz = 1;
+  cfg->precision = LBM_FP64;
+  cfg->substeps = 2;
+  cfg->dx = 1e-3;
+  cfg->c_ref = 0.0;
+  cfg->T_max = 3000.0;
+  for (int f = 0; f < 6; ++f) cfg->face_bc[f] = LBM_PERIODIC;
+  cfg->outlet_sigma = 0.25;
+  cfg->outlet_P = P_REF;
+  cfg->inlet_P = P_REF;
+  cfg->newton_max_iter = 50;
+  cfg->newton_rtol = 1e-13;
+}
+
+size_t lbm_bytes_required(const lbm_config* cfg) {
+  if (!validate(cfg).empty()) return 0;
+  return sizes_for(*cfg).total;
+}
+
+lbm_status lbm_create(const lbm_config* cfg, lbm_t* out) {
+  if (!out) return fail(nullptr, LBM_ERR_INVALID, "out is NULL");
+  *out = nullptr;
+  const std::string why = validate(cfg);
+  if (!why.empty()) return fail(nullptr, LBM_ERR_INVALID, why);
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || cfg->device >= ndev)
+    return fail(nullptr, LBM_ERR_CUDA, "no CUDA device with that ordinal");
+  DeviceGuard dg(cfg->device);
+  lbm_ctx* h = new lbm_ctx();
+  h->cfg = *cfg;
+  h->cfg.inlet_u = nullptr;   // not retained
+  h->D = lattice_dim(cfg->lattice);
+  h->Q = h->D == 3 ? 27 : 9;
+  h->M = cfg->mech.n_species;
+  h->L = h->M + 1;
+  h->NF = record_fields(h->D, h->M);
+  h->g.nx = cfg->nx; h->g.ny = cfg->ny; h->g.nz = cfg->nz;
+  h->g.N = (long long)cfg->nx * cfg->ny * cfg->nz;
+  const double c = cfg->c_ref > 0.0 ? cfg->c_ref : default_c_ref(*cfg);
+  h->un.c = c;
+  h->un.inv_c = 1.0 / c;
+  h->un.inv_c2 = 1.0 / (c * c);
+  h->un.dx = cfg->dx;
+  h->un.dt = cfg->dx / c;
+  h->un.s_pref = R_U * R_U * cfg->dx / (c * P_REF);
+  h->un.nu_pref = 1.0 / (c * cfg->dx);
+  h->un.substeps = cfg->substeps;
+  h->un.newton_max_iter = cfg->newton_max_iter;
+  h->un.newton_rtol = cfg->newton_rtol;
+  build_mech(cfg->mech, h->mech);
+  h->elem = elem_size(cfg->precision);
+  h->stream = static_cast<cudaStream_t>(cfg->stream);
+  const Sizes s = sizes_for(*cfg);
+  h->pops[0] = dalloc(h->cfg, s.pops);
+  h->pops[1] = dalloc(h->cfg, s.pops);
+  h->rec = static_cast<double*>(dalloc(h->cfg, s.rec));
+  h->Tf = static_cast<double*>(dalloc(h->cfg, s.tf));
+  h->status = static_cast<int*>(dalloc(h->cfg, s.status));
+  h->bytes = s.total;
+  if (!h->pops[0] || !h->pops[1] || !h->rec || !h->Tf || !h->status) {
+    lbm_destroy(h);
+    return fail(nullptr, LBM_ERR_OOM, "device allocation failed");
+  }
+  cudaError_t e = cudaMemsetAsync(h->status, 0, sizeof(int), h->stream);
+  if (e != cudaSuccess) {
+    lbm_destroy(h);
+    return fail(nullptr, LBM_ERR_CUDA, std::string("status reset: ") + cudaGetErrorString(e));
+  }
+  *out = h;
+  return LBM_OK;
+}
+
+lbm_status lbm_init_fields(lbm_t h, const double* rho, const double* u, const double* T,
+                           const double* Y, int on_device) {
+  return init_common(h, rho, 0, u, T, Y, on_device);
+}
+
+lbm_status lbm_init_fields_pressure(lbm_t h, const double* P, const double* u,
+                                    const double* T, const double* Y, int on_device) {
+  return init_common(h, P, 1, u, T, Y, on_device);
+}
+
+lbm_status lbm_step(lbm_t h, int nsteps) {
+  if (!h) return fail(nullptr, LBM_ERR_INVALID, "handle is NULL");
+  if (nsteps < 0) return fail(h, LBM_ERR_INVALID, "nsteps must be >= 0");
+  if (!h->initialized) return fail(h, LBM_ERR_STATE, "lbm_step before lbm_init_fields");
+  DeviceGuard dg(h->cfg.device);
+  StepArgs a;
+  a.rec = h->rec;
+  a.Tfield = h->Tf;
+  a.status = h->status;
+  a.g = h->g;
+  a.un = h->un;
+  for (int k = 0; k < nsteps; ++k) {
+    a.src = h->pops[h->cur];
+    a.dst = h->pops[1 - h->cur];
+    cudaError_t e = launch_step(h->D, h->M, h->cfg.precision, h->mech, a, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "step launch");
+    h->cur = 1 - h->cur;
+    ++h->steps;
+  }
+  return LBM_OK;
+}
+
+lbm_status lbm_step_timed(lbm_t h, int nsteps, double* kernel_ms, int n_kernels) {
+  if (!h) return fail(nullptr, LBM_ERR_INVALID, "handle is NULL");
+  if (nsteps < 0 || !kernel_ms || n_kernels < 2)
+    return fail(h, LBM_ERR_INVALID, "need nsteps >= 0 and kernel_ms[2]");
+  if (!h->initialized) return fail(h, LBM_ERR_STATE, "lbm_step before lbm_init_fields");
+  DeviceGuard dg(h->cfg.device);
+  const int nev = 3 * nsteps;
+  std::vector<cudaEvent_t> ev(nev, nullptr);
+  for (auto& e : ev) cudaEventCreate(&e);
+  StepArgs a;
+  a.rec = h->rec;
+  a.Tfield = h->Tf;
+  a.status = h->status;
+  a.g = h->g;
+  a.un = h->un;
+  cudaError_t err = cudaSuccess;
+  for (int k = 0; k < nsteps && err == cudaSuccess; ++k) {
+    a.src = h->pops[h->cur];
+    a.dst = h->pops[1 - h->cur];
+    cudaEventRecord(ev[3 * k], h->stream);
+    err = launch_step(h->D, h->M, h->cfg.precision, h->mech, a, h->stream, 0);
+    cudaEventRecord(ev[3 * k + 1], h->stream);
+    if (err == cudaSuccess)
+      err = launch_step(h->D, h->M, h->cfg.precision, h->mech, a, h->stream, 1);
+    cudaEventRecord(ev[3 * k + 2], h->stream);
+    h->cur = 1 - h->cur;
+    ++h->steps;
+  }
+  if (err == cudaSuccess) err = cudaStreamSynchronize(h->stream);
+  for (int k = 0; k < nsteps && err == cudaSuccess; ++k) {
+    float t0 = 0.f, t1 = 0.f;
+    cudaEventElapsedTime(&t0, ev[3 * k], ev[3 * k + 1]);
+    cudaEventElapsedTime(&t1, ev[3 * k + 1], ev[3 * k + 2]);
+    kernel_ms[0] += t0;
+    kernel_ms[1] += t1;
+  }
+  for (auto& e : ev) cudaEventDestroy(e);
+  if (err != cudaSuccess) return cuda_fail(h, err, "timed step");
+  return LBM_OK;
+}
+
+lbm_status lbm_moments(lbm_t h, double* rho, double* u, double* T, double* Y, double* E,
+                       int on_device) {
+  if (!h) return fail(nullptr, LBM_ERR_INVALID, "handle is NULL");
+  if (!h->initialized) return fail(h, LBM_ERR_STATE, "lbm_moments before lbm_init_fields");
+  DeviceGuard dg(h->cfg.device);
+  const long long N = h->g.N;
+  const int M = h->M;
+  if (on_device) {
+    cudaError_t e = launch_moments_out(h->D, M, h->cfg.precision, h->mech, h->g, h->un,
+                                       h->pops[h->cur], h->Tf, rho, u, T, Y, E, h->status,
+                                       h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "moments kernel");
+    return LBM_OK;
+  }
+  const size_t nb = N * sizeof(double);
+  lbm_status st = ensure_io(h, (size_t)(1 + 3 + 1 + M + 1) * nb);
+  if (st != LBM_OK) return st;
+  double* p = h->io;
+  double *drho = p, *du = p + N, *dT = p + 4 * N, *dY = p + 5 * N, *dE = p + (5 + M) * N;
+  cudaError_t e = launch_moments_out(h->D, M, h->cfg.precision, h->mech, h->g, h->un,
+                                     h->pops[h->cur], h->Tf, rho ? drho : nullptr,
+                                     u ? du : nullptr, T ? dT : nullptr, Y ? dY : nullptr,
+                                     E ? dE : nullptr, h->status, h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "moments kernel");
+  if (rho && e == cudaSuccess) e = cudaMemcpyAsync(rho, drho, nb, cudaMemcpyDeviceToHost, h->stream);
+  if (u && e == cudaSuccess) e = cudaMemcpyAsync(u, du, 3 * nb, cudaMemcpyDeviceToHost, h->stream);
+  if (T && e == cudaSuccess) e = cudaMemcpyAsync(T, dT, nb, cudaMemcpyDeviceToHost, h->stream);
+  if (Y && e == cudaSuccess) e = cudaMemcpyAsync(Y, dY, M * nb, cudaMemcpyDeviceToHost, h->stream);
+  if (E && e == cudaSuccess) e = cudaMemcpyAsync(E, dE, nb, cudaMemcpyDeviceToHost, h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "moments download");
+  return check_status(h);
+}
+
+lbm_status lbm_get_populations(lbm_t h, double* out, int on_device) {
+  if (!h) return fail(nullptr, LBM_ERR_INVALID, "handle is NULL");
+  if (!out) return fail(h, LBM_ERR_INVALID, "out is NULL");
+  if (!h->initialized) return fail(h, LBM_ERR_STATE, "no populations before lbm_init_fields");
+  DeviceGuard dg(h->cfg.device);
+  const long long count = (long long)h->L * h->Q * h->g.N;
+  if (on_device) {
+    cudaError_t e = launch_to_fp64(h->cfg.precision, h->pops[h->cur], out, count, h->stream);
+    return e == cudaSuccess ? LBM_OK : cuda_fail(h, e, "population conversion");
+  }
+  lbm_status st = ensure_io(h, (size_t)count * sizeof(double));
+  if (st != LBM_OK) return st;
+  cudaError_t e = launch_to_fp64(h->cfg.precision, h->pops[h->cur], h->io, count, h->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(out, h->io, (size_t)count * sizeof(double), cudaMemcpyDeviceToHost,
+                        h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "population download");
+  return check_status(h);
+}
+
+lbm_status lbm_synchronize(lbm_t h) {
+  if (!h) return fail(nullptr, LBM_ERR_INVALID, "handle is NULL");
+  DeviceGuard dg(h->cfg.device);
+  return check_status(h);
+}
+
+static const uint64_t STATE_MAGIC = 0x4c424d5354415445ull;   // "LBMSTATE"
+
+lbm_status lbm_get_state(lbm_t h, void* buf, size_t* bytes) {
+  if (!h || !bytes) return fail(h, LBM_ERR_INVALID, "handle or bytes is NULL");
+  const size_t pop_bytes = (size_t)h->L * h->Q * h->g.N * h->elem;
+  const size_t need = 64 + pop_bytes + h->g.N * sizeof(double);
+  if (!buf) { *bytes = need; return LBM_OK; }
+  if (*bytes < need) return fail(h, LBM_ERR_INVALID, "state buffer too small");
+  if (!h->initialized) return fail(h, LBM_ERR_STATE, "no state before lbm_init_fields");
+  DeviceGuard dg(h->cfg.device);
+  uint64_t hdr[8] = {STATE_MAGIC, (uint64_t)h->D, (uint64_t)h->M, (uint64_t)h->g.nx,
+                     (uint64_t)h->g.ny, (uint64_t)h->g.nz, (uint64_t)h->cfg.precision,
+                     (uint64_t)h->steps};
+  std::memcpy(buf, hdr, 64);
+  char* p = static_cast<char*>(buf) + 64;
+  cudaError_t e = cudaMemcpyAsync(p, h->pops[h->cur], pop_bytes, cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(p + pop_bytes, h->Tf, h->g.N * sizeof(double), cudaMemcpyDeviceToHost,
+                        h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "state download");
+  *bytes = need;
+  return check_status(h);
+}
+
+lbm_status lbm_set_state(lbm_t h, const void* buf, size_t bytes) {
+  if (!h || !buf) return fail(h, LBM_ERR_INVALID, "handle or buffer is NULL");
+  const size_t pop_bytes = (size_t)h->L * h->Q * h->g.N * h->elem;
+  const size_t need = 64 + pop_bytes + h->g.N * sizeof(double);
+  if (bytes != need) return fail(h, LBM_ERR_INVALID, "state size does not match this handle");
+  uint64_t hdr[8];
+  std::memcpy(hdr, buf, 64);
+  if (hdr[0] != STATE_MAGIC || hdr[1] != (uint64_t)h->D || hdr[2] != (uint64_t)h->M ||
+      hdr[3] != (uint64_t)h->g.nx || hdr[4] != (uint64_t)h->g.ny ||
+      hdr[5] != (uint64_t)h->g.nz || hdr[6] != (uint64_t)h->cfg.precision)
+    return fail(h, LBM_ERR_INVALID, "state was written by an incompatible handle");
+  DeviceGuard dg(h->cfg.device);
+  const char* p = static_cast<const char*>(buf) + 64;
+  cudaError_t e = cudaMemcpyAsync(h->pops[h->cur], p, pop_bytes, cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(h->Tf, p + pop_bytes, h->g.N * sizeof(double), cudaMemcpyHostToDevice,
+                        h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "state upload");
+  h->steps = (long long)hdr[7];
+  h->initialized = true;
+  return LBM_OK;
+}
+
+lbm_status lbm_get_info(lbm_t h, lbm_info* info) {
+  if (!h || !info) return fail(h, LBM_ERR_INVALID, "handle or info is NULL");
+  info->Q = h->Q;
+  info->D = h->D;
+  info->L = h->L;
+  info->M = h->M;
+  info->n_nodes = h->g.N;
+  info->c_ref = h->un.c;
+  info->dt = h->un.dt;
+  info->dx = h->un.dx;
+  info->bytes_per_population = h->elem;
+  info->device_bytes = h->bytes;
+  info->steps_done = h->steps;
+  return LBM_OK;
+}
+
+lbm_status lbm_destroy(lbm_t h) {
+  if (!h) return LBM_OK;
+  DeviceGuard dg(h->cfg.device);
+  lbm_status st = LBM_OK;
+  if (h->status) st = check_status(h);
+  cudaStreamSynchronize(h->stream);
+  dfree(h->cfg, h->pops[0]);
+  dfree(h->cfg, h->pops[1]);
+  dfree(h->cfg, h->rec);
+  dfree(h->cfg, h->Tf);
+  dfree(h->cfg, h->status);
+  dfree(h->cfg, h->io);
+  delete h;
+  return st;
+}
+
+const char* lbm_last_error(lbm_t h) {
+  return h ? h->err.c_str() : g_create_error.c_str();
+}
+
+}  // extern "C"

@@ -1,0 +1,175 @@
+// Device-side building blocks of the reactive-mixture LBM step.
+//
+// Lattice: D3Q27 / D2Q9 product-form velocity sets, index
+// i = (cz+1)*9 + (cy+1)*3 + (cx+1) (x fastest), opposite = Q-1-i (Sec. 2.2).
+// Thermodynamics, rates and transport are evaluated from the precomputed
+// polynomial forms in DevMech (filled on the host from lbm_mechanism).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "lbm_internal.h"
+
+namespace lbm {
+
+template <int D> struct Lat;
+template <> struct Lat<3> {
+  static constexpr int Q = 27;
+  static constexpr int NP = 6;   // xx, yy, zz, xy, xz, yz
+};
+template <> struct Lat<2> {
+  static constexpr int Q = 9;
+  static constexpr int NP = 3;   // xx, yy, xy
+};
+
+// component a (0 = x, 1 = y, 2 = z) of velocity i
+__host__ __device__ constexpr int cvel(int i, int a) {
+  return a == 0 ? (i % 3) - 1 : (a == 1 ? ((i / 3) % 3) - 1 : (i / 9) - 1);
+}
+__host__ __device__ constexpr int csq(int i, int D) {
+  return cvel(i, 0) * cvel(i, 0) + cvel(i, 1) * cvel(i, 1) +
+         (D == 3 ? cvel(i, 2) * cvel(i, 2) : 0);
+}
+// Isotropic stencil weights of the standard lattice: product of 2/3, 1/6.
+__host__ __device__ constexpr double wstd(int i, int D) {
+  return (cvel(i, 0) == 0 ? 2.0 / 3.0 : 1.0 / 6.0) *
+         (cvel(i, 1) == 0 ? 2.0 / 3.0 : 1.0 / 6.0) *
+         (D == 3 ? (cvel(i, 2) == 0 ? 2.0 / 3.0 : 1.0 / 6.0) : 1.0);
+}
+
+// Per-axis product-form factor Psi_c(xi, P), Eqs. phi0, phiPlus, phis.
+template <typename R>
+__device__ __forceinline__ R psi1(int c, R xi, R P) {
+  return c == 0 ? (R(1) - P) : (c == 1 ? R(0.5) * (P + xi) : R(0.5) * (P - xi));
+}
+
+// Moment-record field offsets ([field][N] FP64 scratch written by the
+// moments kernel, read by the collision kernel).
+template <int D, int M> struct Rec {
+  static constexpr int RHO = 0;
+  static constexpr int U = 1;
+  static constexpr int T = U + D;
+  static constexpr int P = T + 1;
+  static constexpr int QF = P + Lat<D>::NP;
+  static constexpr int E = QF + D;
+  static constexpr int Y = E + 1;
+  static constexpr int US = Y + M;
+  static constexpr int PHI = US + M * D;
+  static constexpr int NF = PHI + D;
+};
+
+// ------------------------------------------------------------------------
+// thermodynamics (Sec. 3.1)
+// U_a(T) = u0 + u1 T + u2 T^2 + u3 T^3 (J/kg), C_av = dU_a/dT.
+
+template <int M>
+__device__ __forceinline__ void mixture_energy_poly(const DevMech& m, const double* Y,
+                                                    double c[4]) {
+  c[0] = c[1] = c[2] = c[3] = 0.0;
+#pragma unroll
+  for (int a = 0; a < M; ++a) {
+    c[0] += Y[a] * m.u0[a];
+    c[1] += Y[a] * m.u1[a];
+    c[2] += Y[a] * m.u2[a];
+    c[3] += Y[a] * m.u3[a];
+  }
+}
+
+// Newton on sum_a Y_a U_a(T) = U (Eq. temperature); stops when the update
+// satisfies |dT| <= rtol |T| after it is applied; ok = false after max_iter.
+template <int M>
+__device__ __forceinline__ double newton_T(const DevMech& m, const double* Y, double U,
+                                           double T, int max_iter, double rtol, bool& ok) {
+  double c[4];
+  mixture_energy_poly<M>(m, Y, c);
+  ok = false;
+  for (int it = 0; it < max_iter; ++it) {
+    const double F = c[0] + T * (c[1] + T * (c[2] + T * c[3])) - U;
+    const double dF = c[1] + T * (2.0 * c[2] + 3.0 * T * c[3]);
+    const double dT = -F / dF;
+    T += dT;
+    if (fabs(dT) <= rtol * fabs(T)) { ok = true; break; }
+  }
+  return T;
+}
+
+__device__ __forceinline__ double species_U(const DevMech& m, int a, double T) {
+  return m.u0[a] + T * (m.u1[a] + T * (m.u2[a] + T * m.u3[a]));
+}
+
+// ------------------------------------------------------------------------
+// chemistry: mass production rates rho_dot_a (kg/(m^3 s)) at (T, rho_a).
+template <int M>
+__device__ void production_rates(const DevMech& m, double T, const double* r,
+                                 double* rdot) {
+  const double lnT = log(T);
+  const double invT = 1.0 / T;
+  double C[M], G[M], w[M];
+#pragma unroll
+  for (int a = 0; a < M; ++a) {
+    C[a] = r[a] * m.inv_mm[a];
+    G[a] = m.g_inv[a] * invT + m.g0[a] + T * (m.g1[a] + T * m.g2[a]) - m.a0[a] * lnT;
+    w[a] = 0.0;
+  }
+  const double ln_p0_rut = m.ln_p0_over_ru - lnT;   // ln(P0 / (R_U T))
+  for (int k = 0; k < m.R; ++k) {
+    const DevReaction& rx = m.rx[k];
+    const double lnkf = rx.lnA + rx.b * lnT - rx.EaR * invT;
+    double fwd = exp(lnkf);
+    for (int j = 0; j < rx.nr; ++j) fwd *= C[rx.reac[j]];
+    double rev = 0.0;
+    if (rx.reversible) {
+      double dG = 0.0;                               // sum_a nu_a G_a
+      for (int j = 0; j < rx.np; ++j) dG += G[rx.prod[j]];
+      for (int j = 0; j < rx.nr; ++j) dG -= G[rx.reac[j]];
+      // k_r = k_f / K_c, ln K_c = -dG + dn ln(P0/(R_U T))
+      rev = exp(lnkf + dG - rx.dn * ln_p0_rut);
+      for (int j = 0; j < rx.np; ++j) rev *= C[rx.prod[j]];
+    }
+    double q = fwd - rev;
+    if (rx.third_body) {
+      double cm = 0.0;
+#pragma unroll
+      for (int a = 0; a < M; ++a) cm += m.eff[k][a] * C[a];
+      q *= cm;
+    }
+    for (int j = 0; j < rx.nr; ++j) w[rx.reac[j]] -= q;
+    for (int j = 0; j < rx.np; ++j) w[rx.prod[j]] += q;
+  }
+#pragma unroll
+  for (int a = 0; a < M; ++a) rdot[a] = w[a] * m.mm[a];
+}
+
+// ------------------------------------------------------------------------
+// Gaussian elimination without pivoting for A V = B with 3 right-hand sides.
+// A is strictly row diagonally dominant (diagonal 1 + sum of |off-diagonal|),
+// so every pivot is at least 1.
+template <int M, int D>
+__device__ __forceinline__ void solve_dd(double (&A)[M][M], double (&B)[M][D]) {
+#pragma unroll
+  for (int k = 0; k < M; ++k) {
+    const double inv = 1.0 / A[k][k];
+#pragma unroll
+    for (int r = k + 1; r < M; ++r) {
+      const double f = A[r][k] * inv;
+#pragma unroll
+      for (int c = k + 1; c < M; ++c) A[r][c] -= f * A[k][c];
+#pragma unroll
+      for (int d = 0; d < D; ++d) B[r][d] -= f * B[k][d];
+    }
+  }
+#pragma unroll
+  for (int k = M - 1; k >= 0; --k) {
+    const double inv = 1.0 / A[k][k];
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+      double s = B[k][d];
+#pragma unroll
+      for (int c = k + 1; c < M; ++c) s -= A[k][c] * B[c][d];
+      B[k][d] = s * inv;
+    }
+  }
+}
+
+}  // namespace lbm

@@ -1,0 +1,91 @@
+// Internal declarations shared by the host API (lbm_capi.cu) and the kernels
+// (lbm_kernels.cu).  Not part of the C ABI.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/lbm.h"
+
+namespace lbm {
+
+constexpr double R_U = 8.314462618;       // J/(mol K)
+constexpr double T_REF = 298.15;          // K, T0 of Sec. 3.6
+constexpr double P_REF = 101325.0;        // Pa, P0 of Sec. 3.6
+constexpr double RHO_TINY = 1e-300;       // u_a := u below this species density
+
+// status bits written by kernels with atomicOr
+constexpr int ST_NEWTON = 1;
+constexpr int ST_NONFINITE = 2;
+constexpr int ST_RANGE = 4;
+
+struct DevReaction {
+  int nr, np;            // number of reactant / product molecules (<= 3)
+  int reac[3], prod[3];  // species index per molecule (repeated for nu = 2)
+  int dn;                // sum of product minus reactant coefficients
+  int reversible, third_body;
+  double lnA, b, EaR;    // ln A, temperature exponent, Ea / R_U
+};
+
+// Mechanism in the forms the kernels evaluate (built on the host).
+struct DevMech {
+  int M, R;
+  double mm[LBM_MAX_SPECIES], inv_mm[LBM_MAX_SPECIES], Ra[LBM_MAX_SPECIES];
+  // U_a(T) = u0 + u1 T + u2 T^2 + u3 T^3  (J/kg, incl. formation)
+  double u0[LBM_MAX_SPECIES], u1[LBM_MAX_SPECIES], u2[LBM_MAX_SPECIES],
+      u3[LBM_MAX_SPECIES];
+  // g_a/(R_U T) = g_inv/T + g0 + g1 T + g2 T^2 - a0 ln T
+  double g_inv[LBM_MAX_SPECIES], g0[LBM_MAX_SPECIES], g1[LBM_MAX_SPECIES],
+      g2[LBM_MAX_SPECIES], a0[LBM_MAX_SPECIES];
+  double ln_p0_over_ru;
+  DevReaction rx[LBM_MAX_REACTIONS];
+  double eff[LBM_MAX_REACTIONS][LBM_MAX_SPECIES];
+  // 1/tau_ab = s(node) * K[a][b], K = 1/(m_a m_b D0_ab)
+  double K[LBM_MAX_SPECIES][LBM_MAX_SPECIES];
+  double D_T_exp, mu0, mu_T_exp, inv_prandtl;
+};
+
+struct Units {
+  double c, inv_c, inv_c2, dx, dt;
+  double s_pref;         // R_U^2 dx / (c P0): 1/tau_ab = s_pref rho T^2 (T/T0)^-e K_ab
+  double nu_pref;        // 1 / (c dx):  nu_lat = mu / rho * nu_pref
+  int substeps;
+  int newton_max_iter;
+  double newton_rtol;
+};
+
+struct Geom {
+  int nx, ny, nz;
+  long long N;
+};
+
+// Kernel launchers (lbm_kernels.cu).  `S` is the storage type.
+struct StepArgs {
+  const void* src;
+  void* dst;
+  double* rec;           // moment records [NF][N]
+  double* Tfield;        // temperature guess [N]
+  int* status;
+  Geom g;
+  Units un;
+};
+
+// which: 0 = moments kernel only, 1 = collision kernel only, -1 = both.
+cudaError_t launch_step(int D, int M, lbm_precision prec, const DevMech& mech,
+                        const StepArgs& a, cudaStream_t s, int which = -1);
+cudaError_t launch_init(int D, int M, lbm_precision prec, const DevMech& mech,
+                        const Geom& g, const Units& un, const double* rho_or_P,
+                        int is_pressure, const double* u, const double* T,
+                        const double* Y, void* pops, double* Tfield, int* status,
+                        cudaStream_t s);
+cudaError_t launch_moments_out(int D, int M, lbm_precision prec, const DevMech& mech,
+                               const Geom& g, const Units& un, const void* pops,
+                               const double* Tfield, double* rho, double* u,
+                               double* T, double* Y, double* E, int* status,
+                               cudaStream_t s);
+cudaError_t launch_to_fp64(lbm_precision prec, const void* pops, double* out,
+                           long long count, cudaStream_t s);
+int record_fields(int D, int M);
+
+}  // namespace lbm

@@ -1,0 +1,604 @@
+// Kernels of the reactive-mixture LBM step (thread per node).
+//
+//   k_moments   pull-stream all lattices, moments, temperature Newton,
+//               write the per-node moment record (scratch) and T guess.
+//   k_collide   gradients from neighbour records, relaxation parameters,
+//               diffusion velocities, reaction sub-steps, collision of all
+//               lattices on a second pull gather, store to the other buffer.
+//   k_init      populations at the equilibria of given fields.
+//   k_out       fields of the stored state (SI units).
+//
+// Template parameters: D (2 or 3), M (species), S (storage type), RT (type
+// of the lattice arithmetic: moments, equilibria, collision).  Temperature,
+// transport, diffusion velocities and chemistry always run in FP64.
+#include <cmath>
+
+#include "lbm_device.cuh"
+
+namespace lbm {
+
+template <typename S>
+__device__ __forceinline__ double ldp(const S* p) { return static_cast<double>(__ldg(p)); }
+
+__device__ __forceinline__ int wrap1(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
+
+template <int D>
+__device__ __forceinline__ long long node_shift(int x, int y, int z, int i, int sgn,
+                                                const Geom& g) {
+  const int sx = wrap1(x + sgn * cvel(i, 0), g.nx);
+  const int sy = wrap1(y + sgn * cvel(i, 1), g.ny);
+  const int sz = D == 3 ? wrap1(z + sgn * cvel(i, 2), g.nz) : 0;
+  return sx + (long long)g.nx * (sy + (long long)g.ny * sz);
+}
+
+template <typename R>
+__device__ __forceinline__ R pick3(int c, const R (&v)[3]) {
+  return c == 0 ? v[1] : (c > 0 ? v[2] : v[0]);
+}
+
+template <int D>
+__device__ __forceinline__ constexpr int pidx(int a, int b) {
+  return a == b ? a : (D == 3 ? (a + b == 1 ? 3 : (a + b == 2 ? 4 : 5)) : 2);
+}
+
+// ---------------------------------------------------------------------------
+// Moments of the post-stream state + temperature (Sec. 2.1, Sec. 3.1-3.2,
+// Sec. 3.7 slaving, Sec. 4.1 pull streaming).
+template <int D, int M, typename S>
+__global__ void __launch_bounds__(128)
+k_moments(const S* __restrict__ src, double* __restrict__ rec, double* __restrict__ Tf,
+          int* __restrict__ status, Geom g, Units un, const __grid_constant__ DevMech mech) {
+  constexpr int Q = Lat<D>::Q, NP = Lat<D>::NP;
+  using RC = Rec<D, M>;
+  const long long N = g.N;
+  const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (n >= N) return;
+  const int x = (int)(n % g.nx);
+  const int y = (int)((n / g.nx) % g.ny);
+  const int z = (int)(n / ((long long)g.nx * g.ny));
+
+  double rho = 0.0, rhoE = 0.0, j[D], q[D], P[NP], rs[M], js[M][D];
+#pragma unroll
+  for (int d = 0; d < D; ++d) { j[d] = 0.0; q[d] = 0.0; }
+#pragma unroll
+  for (int k = 0; k < NP; ++k) P[k] = 0.0;
+#pragma unroll
+  for (int a = 0; a < M; ++a) {
+    rs[a] = 0.0;
+#pragma unroll
+    for (int d = 0; d < D; ++d) js[a][d] = 0.0;
+  }
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    const long long sn = node_shift<D>(x, y, z, i, -1, g);
+#pragma unroll
+    for (int a = 0; a < M - 1; ++a) {
+      const double v = ldp(src + (long long)(a * Q + i) * N + sn);
+      rs[a] += v;
+#pragma unroll
+      for (int d = 0; d < D; ++d)
+        if (cvel(i, d) != 0) js[a][d] += cvel(i, d) * v;
+    }
+    const double f = ldp(src + (long long)((M - 1) * Q + i) * N + sn);
+    rho += f;
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+      if (cvel(i, d) != 0) j[d] += cvel(i, d) * f;
+#pragma unroll
+      for (int e = d; e < D; ++e)
+        if (cvel(i, d) * cvel(i, e) != 0) P[pidx<D>(d, e)] += cvel(i, d) * cvel(i, e) * f;
+    }
+    const double gv = ldp(src + (long long)(M * Q + i) * N + sn);
+    rhoE += gv;
+#pragma unroll
+    for (int d = 0; d < D; ++d)
+      if (cvel(i, d) != 0) q[d] += cvel(i, d) * gv;
+  }
+  // slaved species M (Eq. strongest)
+  rs[M - 1] = rho;
+#pragma unroll
+  for (int d = 0; d < D; ++d) js[M - 1][d] = j[d];
+#pragma unroll
+  for (int a = 0; a < M - 1; ++a) {
+    rs[M - 1] -= rs[a];
+#pragma unroll
+    for (int d = 0; d < D; ++d) js[M - 1][d] -= js[a][d];
+  }
+  const double inv_rho = 1.0 / rho;
+  double u[D], usq = 0.0, Y[M];
+#pragma unroll
+  for (int d = 0; d < D; ++d) { u[d] = j[d] * inv_rho; usq += u[d] * u[d]; }
+#pragma unroll
+  for (int a = 0; a < M; ++a) Y[a] = rs[a] * inv_rho;
+  const double E = rhoE * inv_rho;
+  const double U = (E - 0.5 * usq) * un.c * un.c;
+  bool ok;
+  const double T = newton_T<M>(mech, Y, U, Tf[n], un.newton_max_iter, un.newton_rtol, ok);
+  if (!ok) atomicOr(status, ST_NEWTON);
+  if (!(rho > 0.0) || !isfinite(rho) || !isfinite(T)) atomicOr(status, ST_NONFINITE);
+  Tf[n] = T;
+  double Rmix = 0.0;
+#pragma unroll
+  for (int a = 0; a < M; ++a) Rmix += Y[a] * mech.inv_mm[a];
+  Rmix *= R_U;
+  const double theta = Rmix * T * un.inv_c2;
+
+  rec[RC::RHO * N + n] = rho;
+#pragma unroll
+  for (int d = 0; d < D; ++d) {
+    rec[(RC::U + d) * N + n] = u[d];
+    rec[(RC::QF + d) * N + n] = q[d];
+    rec[(RC::PHI + d) * N + n] = rho * u[d] * (1.0 - 3.0 * theta) - rho * u[d] * u[d] * u[d];
+  }
+  rec[RC::T * N + n] = T;
+#pragma unroll
+  for (int k = 0; k < NP; ++k) rec[(RC::P + k) * N + n] = P[k];
+  rec[RC::E * N + n] = E;
+#pragma unroll
+  for (int a = 0; a < M; ++a) {
+    rec[(RC::Y + a) * N + n] = Y[a];
+    const bool tiny = rs[a] <= RHO_TINY;
+    const double inv = tiny ? 0.0 : 1.0 / rs[a];
+#pragma unroll
+    for (int d = 0; d < D; ++d)
+      rec[(RC::US + a * D + d) * N + n] = tiny ? u[d] : js[a][d] * inv;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Collision of all lattices (Sec. 2.3 Eq. finalNumericalEquationsReactive;
+// Sec. 3.2 Eqs. f, g; Sec. 3.3 Eqs. feqmix, Pex; Sec. 3.4 Eqs. geq_i, gstar,
+// gstareq1mom, qdiff, corrFourier, qex; Sec. 2.4 Eq. R3).
+template <int D, int M, typename S, typename RT>
+__global__ void __launch_bounds__(128)
+k_collide(const S* __restrict__ src, S* __restrict__ dst, const double* __restrict__ rec,
+          int* __restrict__ status, Geom g, Units un, const __grid_constant__ DevMech mech) {
+  constexpr int Q = Lat<D>::Q, NP = Lat<D>::NP;
+  using RC = Rec<D, M>;
+  const long long N = g.N;
+  const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (n >= N) return;
+  const int x = (int)(n % g.nx);
+  const int y = (int)((n / g.nx) % g.ny);
+  const int z = (int)(n / ((long long)g.nx * g.ny));
+
+  const double rho = rec[RC::RHO * N + n];
+  const double T = rec[RC::T * N + n];
+  const double E = rec[RC::E * N + n];
+  double u[D], q[D], P[NP], Y[M], V[M][D];
+  double usq = 0.0;
+#pragma unroll
+  for (int d = 0; d < D; ++d) {
+    u[d] = rec[(RC::U + d) * N + n];
+    q[d] = rec[(RC::QF + d) * N + n];
+    usq += u[d] * u[d];
+  }
+#pragma unroll
+  for (int k = 0; k < NP; ++k) P[k] = rec[(RC::P + k) * N + n];
+#pragma unroll
+  for (int a = 0; a < M; ++a) {
+    Y[a] = rec[(RC::Y + a) * N + n];
+#pragma unroll
+    for (int d = 0; d < D; ++d) V[a][d] = rec[(RC::US + a * D + d) * N + n] - u[d];
+  }
+
+  // isotropic gradients d_a Phi_a and grad Y_a: 3 sum_i w_i c_ia phi(x + c_i)
+  double dPhi[D], gY[M][D];
+#pragma unroll
+  for (int d = 0; d < D; ++d) {
+    dPhi[d] = 0.0;
+#pragma unroll
+    for (int a = 0; a < M; ++a) gY[a][d] = 0.0;
+  }
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    if (csq(i, D) == 0) continue;
+    const long long nb = node_shift<D>(x, y, z, i, +1, g);
+    const double w3 = 3.0 * wstd(i, D);
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+      if (cvel(i, d) == 0) continue;
+      const double wc = w3 * cvel(i, d);
+      dPhi[d] += wc * __ldg(rec + (RC::PHI + d) * N + nb);
+#pragma unroll
+      for (int a = 0; a < M; ++a) gY[a][d] += wc * __ldg(rec + (RC::Y + a) * N + nb);
+    }
+  }
+
+  // relaxation parameters (Sec. 2.3 Eqs. betaa, taua; Sec. 3.5 Eqs. mu, lambda)
+  double Rmix = 0.0;
+#pragma unroll
+  for (int a = 0; a < M; ++a) Rmix += Y[a] * mech.inv_mm[a];
+  Rmix *= R_U;
+  const double theta = Rmix * T * un.inv_c2;
+  const double lnTr = log(T * (1.0 / T_REF));
+  const double s_tau = un.s_pref * rho * T * T * exp(-mech.D_T_exp * lnTr);
+  const double mu = mech.mu0 * exp(mech.mu_T_exp * lnTr);
+  const double nu = mu / rho * un.nu_pref;
+  const double omega = 1.0 / (nu / theta + 0.5);
+  const double omega1 = 1.0 / (nu * mech.inv_prandtl / theta + 0.5);
+  double inv_tau_a[M];
+#pragma unroll
+  for (int a = 0; a < M; ++a) {
+    double acc = 0.0;
+#pragma unroll
+    for (int b = 0; b < M; ++b)
+      if (b != a) acc += Y[b] * (s_tau * mech.K[a][b]);
+    inv_tau_a[a] = acc;
+  }
+
+  // diffusion velocities, Eq. transform1: A V = u_a - u  (V holds the rhs)
+  {
+    double A[M][M];
+#pragma unroll
+    for (int a = 0; a < M; ++a)
+#pragma unroll
+      for (int b = 0; b < M; ++b)
+        A[a][b] = a == b ? 1.0 + 0.5 * inv_tau_a[a] : -0.5 * Y[b] * (s_tau * mech.K[a][b]);
+    solve_dd<M, D>(A, V);
+  }
+
+  // reaction sub-steps at frozen U (Eq. R3); T_0 is the step's T
+  double rs[M], drho[M];
+#pragma unroll
+  for (int a = 0; a < M; ++a) rs[a] = rho * Y[a];
+  {
+    const double Uphys = (E - 0.5 * usq) * un.c * un.c;
+    const double dtr = un.dt / un.substeps;
+    double r[M], rdot[M];
+#pragma unroll
+    for (int a = 0; a < M; ++a) r[a] = rs[a];
+    double Ts = T;
+    for (int s = 0; s < un.substeps; ++s) {
+      if (s > 0) {
+        double Ys[M];
+        const double ir = 1.0 / rho;
+#pragma unroll
+        for (int a = 0; a < M; ++a) Ys[a] = r[a] * ir;
+        bool ok;
+        Ts = newton_T<M>(mech, Ys, Uphys, Ts, un.newton_max_iter, un.newton_rtol, ok);
+        if (!ok) atomicOr(status, ST_NEWTON);
+      }
+      production_rates<M>(mech, Ts, r, rdot);
+#pragma unroll
+      for (int a = 0; a < M; ++a) r[a] += dtr * rdot[a];
+    }
+#pragma unroll
+    for (int a = 0; a < M; ++a) drho[a] = r[a] - rs[a];
+  }
+
+  // energy-flux correction W = (omega - omega1)(q* - q^eq), folded form
+  const double U_lat = E - 0.5 * usq;
+  double W[D];
+  {
+    double diff[D], corr[D];
+#pragma unroll
+    for (int d = 0; d < D; ++d) { diff[d] = 0.0; corr[d] = 0.0; }
+#pragma unroll
+    for (int a = 0; a < M; ++a) {
+      const double Ha = (species_U(mech, a, T) + mech.Ra[a] * T) * un.inv_c2;
+#pragma unroll
+      for (int d = 0; d < D; ++d) {
+        diff[d] += Ha * Y[a] * V[a][d];
+        corr[d] += Ha * gY[a][d];
+      }
+    }
+    const double Pres = rho * theta;
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+      const double q_eq = rho * u[d] * (E + theta);
+      double uP = 0.0;
+#pragma unroll
+      for (int b = 0; b < D; ++b) {
+        const double Peq = rho * u[b] * u[d] + (b == d ? rho * theta : 0.0);
+        uP += u[b] * (P[pidx<D>(b, d)] - Peq);
+      }
+      const double q_ex = -0.5 * u[d] * dPhi[d];
+      W[d] = (omega - omega1) * (q[d] - q_eq - uP + q_ex) + omega1 * rho * diff[d] +
+             0.5 * (2.0 - omega1) * Pres * corr[d];
+    }
+  }
+
+  // per-lattice parameters in the collision type
+  RT th_a[M], beta[M], Pex[D], uR[D], VR[M][D];
+#pragma unroll
+  for (int a = 0; a < M; ++a) {
+    th_a[a] = RT(mech.Ra[a] * T * un.inv_c2);
+    beta[a] = RT(inv_tau_a[a] / (2.0 + inv_tau_a[a]));
+#pragma unroll
+    for (int d = 0; d < D; ++d) VR[a][d] = RT(V[a][d]);
+  }
+#pragma unroll
+  for (int d = 0; d < D; ++d) {
+    uR[d] = RT(u[d]);
+    Pex[d] = RT(theta + u[d] * u[d] + (2.0 - omega) / (2.0 * rho * omega) * dPhi[d]);
+  }
+  // energy equilibrium axis factors: A_c (acting on 1) and B_c (on u^2/2)
+  RT Af[D][3], Bf[D][3];
+#pragma unroll
+  for (int d = 0; d < D; ++d) {
+    const double ua = u[d];
+    const double O1 = theta * ua + 0.5 * ua * ua * ua;
+    const double O2 = theta * theta + 2.5 * theta * ua * ua + 0.5 * ua * ua * ua * ua;
+    const double Pd = theta + ua * ua;
+    Af[d][0] = RT(0.5 * (Pd - ua));
+    Af[d][1] = RT(1.0 - Pd);
+    Af[d][2] = RT(0.5 * (Pd + ua));
+    Bf[d][0] = RT(0.5 * (O2 - O1));
+    Bf[d][1] = RT(0.5 * ua * ua - O2);
+    Bf[d][2] = RT(0.5 * (O2 + O1));
+  }
+  const RT rhoR = RT(rho), omR = RT(omega), UR = RT(U_lat);
+
+#pragma unroll 1
+  for (int i = 0; i < Q; ++i) {
+    const long long sn = node_shift<D>(x, y, z, i, -1, g);
+    int c[3];
+    c[0] = cvel(i, 0); c[1] = cvel(i, 1); c[2] = D == 3 ? cvel(i, 2) : 0;
+    RT pe[M], dd[M];
+#pragma unroll
+    for (int b = 0; b < M; ++b) {
+      RT e = RT(1), st = RT(1);
+#pragma unroll
+      for (int d = 0; d < D; ++d) {
+        e *= psi1<RT>(c[d], uR[d], th_a[b] + uR[d] * uR[d]);
+        const RT xs = uR[d] + VR[b][d];
+        st *= psi1<RT>(c[d], xs, th_a[b] + xs * xs);
+      }
+      pe[b] = e;
+      dd[b] = RT(rs[b]) * (e - st);
+    }
+#pragma unroll
+    for (int a = 0; a < M - 1; ++a) {
+      RT F = RT(0);
+#pragma unroll
+      for (int b = 0; b < M; ++b)
+        if (b != a) F += RT(s_tau * mech.K[a][b]) * dd[b];
+      const long long off = (long long)(a * Q + i) * N;
+      const RT f = RT(ldp(src + off + sn));
+      const RT fn = f + RT(2) * beta[a] * (RT(rs[a]) * pe[a] - f) +
+                    (beta[a] - RT(1)) * RT(Y[a]) * F + RT(drho[a]) * pe[a];
+      dst[off + n] = S(fn);
+    }
+    {
+      RT fex = rhoR;
+#pragma unroll
+      for (int d = 0; d < D; ++d) fex *= psi1<RT>(c[d], uR[d], Pex[d]);
+      const long long off = (long long)((M - 1) * Q + i) * N;
+      const RT f = RT(ldp(src + off + sn));
+      dst[off + n] = S(f + omR * (fex - f));
+    }
+    {
+      RT prodA = RT(1);
+#pragma unroll
+      for (int d = 0; d < D; ++d) prodA *= pick3<RT>(c[d], Af[d]);
+      RT geq = UR * prodA;
+#pragma unroll
+      for (int d = 0; d < D; ++d) {
+        RT t = pick3<RT>(c[d], Bf[d]);
+#pragma unroll
+        for (int e = 0; e < D; ++e)
+          if (e != d) t *= pick3<RT>(c[e], Af[e]);
+        geq += t;
+      }
+      geq *= rhoR;
+      const long long off = (long long)(M * Q + i) * N;
+      const RT gv = RT(ldp(src + off + sn));
+      RT gn = gv + omR * (geq - gv);
+      if (csq(i, D) == 1) {
+#pragma unroll
+        for (int d = 0; d < D; ++d)
+          if (c[d] != 0) gn += RT(0.5 * c[d] * W[d]);
+      }
+      dst[off + n] = S(gn);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Initial populations at the equilibria of (rho or P, u, T, Y).
+template <int D, int M, typename S>
+__global__ void k_init(const double* __restrict__ rho_or_P, int is_pressure,
+                       const double* __restrict__ uin, const double* __restrict__ Tin,
+                       const double* __restrict__ Yin, S* __restrict__ pops,
+                       double* __restrict__ Tf, int* __restrict__ status, Geom g, Units un,
+                       const __grid_constant__ DevMech mech) {
+  constexpr int Q = Lat<D>::Q;
+  const long long N = g.N;
+  const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (n >= N) return;
+  const double T = Tin[n];
+  double Y[M], Rmix = 0.0, U = 0.0;
+#pragma unroll
+  for (int a = 0; a < M; ++a) {
+    Y[a] = Yin[a * N + n];
+    Rmix += Y[a] * mech.inv_mm[a];
+    U += Y[a] * species_U(mech, a, T);
+  }
+  Rmix *= R_U;
+  const double rho = is_pressure ? rho_or_P[n] / (Rmix * T) : rho_or_P[n];
+  if (!(rho > 0.0) || !isfinite(rho) || !(T > 0.0)) atomicOr(status, ST_NONFINITE);
+  double u[D], usq = 0.0;
+#pragma unroll
+  for (int d = 0; d < D; ++d) { u[d] = uin[d * N + n] * un.inv_c; usq += u[d] * u[d]; }
+  const double theta = Rmix * T * un.inv_c2;
+  const double U_lat = U * un.inv_c2;
+  for (int i = 0; i < Q; ++i) {
+    int c[3] = {cvel(i, 0), cvel(i, 1), D == 3 ? cvel(i, 2) : 0};
+    for (int a = 0; a < M - 1; ++a) {
+      const double th = mech.Ra[a] * T * un.inv_c2;
+      double p = rho * Y[a];
+      for (int d = 0; d < D; ++d) p *= psi1<double>(c[d], u[d], th + u[d] * u[d]);
+      pops[(long long)(a * Q + i) * N + n] = S(p);
+    }
+    double f = rho;
+    for (int d = 0; d < D; ++d) f *= psi1<double>(c[d], u[d], theta + u[d] * u[d]);
+    pops[(long long)((M - 1) * Q + i) * N + n] = S(f);
+    double prodA = 1.0, sumB = 0.0;
+    double A[3], B[3];
+    for (int d = 0; d < D; ++d) {
+      const double ua = u[d];
+      const double O1 = theta * ua + 0.5 * ua * ua * ua;
+      const double O2 = theta * theta + 2.5 * theta * ua * ua + 0.5 * ua * ua * ua * ua;
+      A[d] = psi1<double>(c[d], ua, theta + ua * ua);
+      B[d] = c[d] == 0 ? 0.5 * ua * ua - O2 : 0.5 * (O2 + c[d] * O1);
+      prodA *= A[d];
+    }
+    for (int d = 0; d < D; ++d) {
+      double t = B[d];
+      for (int e = 0; e < D; ++e)
+        if (e != d) t *= A[e];
+      sumB += t;
+    }
+    pops[(long long)(M * Q + i) * N + n] = S(rho * (U_lat * prodA + sumB));
+  }
+  (void)usq;
+  Tf[n] = T;
+}
+
+// ---------------------------------------------------------------------------
+// Fields of the stored state: rho, u (m/s), T (Newton, not stored), Y, E (J/kg).
+template <int D, int M, typename S>
+__global__ void k_out(const S* __restrict__ pops, const double* __restrict__ Tf,
+                      double* __restrict__ orho, double* __restrict__ ou,
+                      double* __restrict__ oT, double* __restrict__ oY,
+                      double* __restrict__ oE, int* __restrict__ status, Geom g, Units un,
+                      const __grid_constant__ DevMech mech) {
+  constexpr int Q = Lat<D>::Q;
+  const long long N = g.N;
+  const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (n >= N) return;
+  double rho = 0.0, rhoE = 0.0, j[D], rs[M];
+  for (int d = 0; d < D; ++d) j[d] = 0.0;
+  for (int a = 0; a < M; ++a) rs[a] = 0.0;
+  for (int i = 0; i < Q; ++i) {
+    for (int a = 0; a < M - 1; ++a) rs[a] += ldp(pops + (long long)(a * Q + i) * N + n);
+    const double f = ldp(pops + (long long)((M - 1) * Q + i) * N + n);
+    rho += f;
+    for (int d = 0; d < D; ++d) j[d] += cvel(i, d) * f;
+    rhoE += ldp(pops + (long long)(M * Q + i) * N + n);
+  }
+  rs[M - 1] = rho;
+  for (int a = 0; a < M - 1; ++a) rs[M - 1] -= rs[a];
+  double Y[M], u[D], usq = 0.0;
+  for (int a = 0; a < M; ++a) Y[a] = rs[a] / rho;
+  for (int d = 0; d < D; ++d) { u[d] = j[d] / rho; usq += u[d] * u[d]; }
+  const double E = rhoE / rho;
+  bool ok;
+  const double T = newton_T<M>(mech, Y, (E - 0.5 * usq) * un.c * un.c, Tf[n],
+                               un.newton_max_iter, un.newton_rtol, ok);
+  if (!ok) atomicOr(status, ST_NEWTON);
+  if (orho) orho[n] = rho;
+  if (ou) {
+    for (int d = 0; d < 3; ++d) ou[d * N + n] = d < D ? u[d] * un.c : 0.0;
+  }
+  if (oT) oT[n] = T;
+  if (oY)
+    for (int a = 0; a < M; ++a) oY[a * N + n] = Y[a];
+  if (oE) oE[n] = E * un.c * un.c;
+}
+
+template <typename S>
+__global__ void k_to_fp64(const S* __restrict__ in, double* __restrict__ out, long long count) {
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < count;
+       k += (long long)gridDim.x * blockDim.x)
+    out[k] = static_cast<double>(in[k]);
+}
+
+// ---------------------------------------------------------------------------
+// dispatch
+
+static inline unsigned blocks_for(long long N, int bs) { return (unsigned)((N + bs - 1) / bs); }
+
+template <int D, int M, typename S, typename RT>
+static cudaError_t step_impl(const DevMech& mech, const StepArgs& a, cudaStream_t s,
+                             int which) {
+  const int bs = 128;
+  const unsigned nb = blocks_for(a.g.N, bs);
+  if (which != 1)
+    k_moments<D, M, S><<<nb, bs, 0, s>>>(static_cast<const S*>(a.src), a.rec, a.Tfield,
+                                         a.status, a.g, a.un, mech);
+  if (which != 0)
+    k_collide<D, M, S, RT><<<nb, bs, 0, s>>>(static_cast<const S*>(a.src),
+                                             static_cast<S*>(a.dst), a.rec, a.status, a.g,
+                                             a.un, mech);
+  return cudaGetLastError();
+}
+
+#define LBM_DISPATCH(D_, M_, CALL)                                 \
+  if (D == D_ && M == M_) {                                        \
+    if (prec == LBM_FP64) return CALL(D_, M_, double, double);     \
+    if (prec == LBM_FP32_STORE) return CALL(D_, M_, float, float); \
+  }
+
+cudaError_t launch_step(int D, int M, lbm_precision prec, const DevMech& mech,
+                        const StepArgs& a, cudaStream_t s, int which) {
+#define CALL_STEP(D_, M_, S_, R_) step_impl<D_, M_, S_, R_>(mech, a, s, which)
+  LBM_DISPATCH(3, 9, CALL_STEP)
+  LBM_DISPATCH(3, 2, CALL_STEP)
+  LBM_DISPATCH(2, 9, CALL_STEP)
+  LBM_DISPATCH(2, 2, CALL_STEP)
+#undef CALL_STEP
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_init(int D, int M, lbm_precision prec, const DevMech& mech,
+                        const Geom& g, const Units& un, const double* rho_or_P,
+                        int is_pressure, const double* u, const double* T,
+                        const double* Y, void* pops, double* Tfield, int* status,
+                        cudaStream_t s) {
+  const unsigned nb = blocks_for(g.N, 128);
+#define CALL_INIT(D_, M_, S_, R_)                                                       \
+  (k_init<D_, M_, S_><<<nb, 128, 0, s>>>(rho_or_P, is_pressure, u, T, Y,               \
+                                         static_cast<S_*>(pops), Tfield, status, g, un, \
+                                         mech),                                         \
+   cudaGetLastError())
+  LBM_DISPATCH(3, 9, CALL_INIT)
+  LBM_DISPATCH(3, 2, CALL_INIT)
+  LBM_DISPATCH(2, 9, CALL_INIT)
+  LBM_DISPATCH(2, 2, CALL_INIT)
+#undef CALL_INIT
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_moments_out(int D, int M, lbm_precision prec, const DevMech& mech,
+                               const Geom& g, const Units& un, const void* pops,
+                               const double* Tfield, double* rho, double* u, double* T,
+                               double* Y, double* E, int* status, cudaStream_t s) {
+  const unsigned nb = blocks_for(g.N, 128);
+#define CALL_OUT(D_, M_, S_, R_)                                                         \
+  (k_out<D_, M_, S_><<<nb, 128, 0, s>>>(static_cast<const S_*>(pops), Tfield, rho, u, T, \
+                                        Y, E, status, g, un, mech),                      \
+   cudaGetLastError())
+  LBM_DISPATCH(3, 9, CALL_OUT)
+  LBM_DISPATCH(3, 2, CALL_OUT)
+  LBM_DISPATCH(2, 9, CALL_OUT)
+  LBM_DISPATCH(2, 2, CALL_OUT)
+#undef CALL_OUT
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_to_fp64(lbm_precision prec, const void* pops, double* out,
+                           long long count, cudaStream_t s) {
+  const unsigned nb = (unsigned)std::min<long long>(blocks_for(count, 256), 152LL * 16);
+  if (prec == LBM_FP64)
+    k_to_fp64<double><<<nb, 256, 0, s>>>(static_cast<const double*>(pops), out, count);
+  else if (prec == LBM_FP32_STORE)
+    k_to_fp64<float><<<nb, 256, 0, s>>>(static_cast<const float*>(pops), out, count);
+  else
+    return cudaErrorInvalidValue;
+  return cudaGetLastError();
+}
+
+int record_fields(int D, int M) {
+  if (D == 3) {
+    if (M == 9) return Rec<3, 9>::NF;
+    if (M == 2) return Rec<3, 2>::NF;
+  } else {
+    if (M == 9) return Rec<2, 9>::NF;
+    if (M == 2) return Rec<2, 2>::NF;
+  }
+  return -1;
+}
+
+}  // namespace lbm

@@ -1,0 +1,394 @@
+"""Python binding of the C ABI in include/lbm.h (argument marshalling only).
+
+Every computation runs in the CUDA library _lib/libpaper2108lbm.so; this
+module only converts arrays, structs and status codes.  If the library has
+not been built, importing raises: there is no CPU fallback.
+
+Functions carry the C names (lbm_create, lbm_init_fields, lbm_step,
+lbm_moments, lbm_destroy, ...).  ``Solver`` is a small convenience wrapper
+that owns one handle.  Device memory comes from PyTorch's caching allocator
+(through the allocation hooks of lbm_config) and the default stream is
+torch's current stream.
+"""
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+MAX_SPECIES = 9
+MAX_REACTIONS = 32
+NCP = 3
+
+LBM_D2Q9, LBM_D3Q27 = 0, 1
+LBM_FP64, LBM_FP32_STORE, LBM_FP16_OFFSET = 0, 1, 2
+LBM_PERIODIC, LBM_BOUNCE_BACK, LBM_TMS_WALL, LBM_INLET, LBM_OUTLET = 0, 1, 2, 3, 4
+STATUS_NAMES = {0: "LBM_OK", 1: "LBM_ERR_INVALID", 2: "LBM_ERR_OOM", 3: "LBM_ERR_CUDA",
+                4: "LBM_ERR_NEWTON", 5: "LBM_ERR_NONFINITE", 6: "LBM_ERR_RANGE",
+                7: "LBM_ERR_TIMEOUT", 8: "LBM_ERR_STATE"}
+FACE_KINDS = {"periodic": LBM_PERIODIC, "bounce_back": LBM_BOUNCE_BACK,
+              "tms": LBM_TMS_WALL, "inlet": LBM_INLET, "outlet": LBM_OUTLET}
+PRECISIONS = {"fp64": LBM_FP64, "fp32": LBM_FP32_STORE, "fp16": LBM_FP16_OFFSET}
+
+
+class lbm_mechanism(C.Structure):
+    _fields_ = [
+        ("n_species", C.c_int), ("n_reactions", C.c_int),
+        ("molar_mass", C.c_double * MAX_SPECIES),
+        ("cp", (C.c_double * NCP) * MAX_SPECIES),
+        ("h_formation", C.c_double * MAX_SPECIES),
+        ("s_standard", C.c_double * MAX_SPECIES),
+        ("nu_f", (C.c_int * MAX_SPECIES) * MAX_REACTIONS),
+        ("nu_r", (C.c_int * MAX_SPECIES) * MAX_REACTIONS),
+        ("arrhenius", (C.c_double * 3) * MAX_REACTIONS),
+        ("third_body", C.c_int * MAX_REACTIONS),
+        ("efficiency", (C.c_double * MAX_SPECIES) * MAX_REACTIONS),
+        ("reversible", C.c_int * MAX_REACTIONS),
+        ("D0", (C.c_double * MAX_SPECIES) * MAX_SPECIES),
+        ("D_T_exponent", C.c_double), ("mu0", C.c_double),
+        ("mu_T_exponent", C.c_double), ("prandtl", C.c_double),
+    ]
+
+
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
+
+
+class lbm_config(C.Structure):
+    _fields_ = [
+        ("lattice", C.c_int), ("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int),
+        ("precision", C.c_int), ("substeps", C.c_int), ("dx", C.c_double),
+        ("c_ref", C.c_double), ("T_max", C.c_double), ("mech", lbm_mechanism),
+        ("face_bc", C.c_int * 6), ("wall_T", C.c_double * 6),
+        ("inlet_u", C.POINTER(C.c_double)), ("inlet_u_uniform", C.c_double * 3),
+        ("inlet_Y", C.c_double * MAX_SPECIES), ("inlet_T", C.c_double),
+        ("inlet_P", C.c_double), ("outlet_P", C.c_double), ("outlet_sigma", C.c_double),
+        ("newton_max_iter", C.c_int), ("newton_rtol", C.c_double),
+        ("dev_alloc", ALLOC_FN), ("dev_free", FREE_FN), ("alloc_user", C.c_void_p),
+        ("stream", C.c_void_p), ("device", C.c_int),
+    ]
+
+
+class lbm_info(C.Structure):
+    _fields_ = [("Q", C.c_int), ("D", C.c_int), ("L", C.c_int), ("M", C.c_int),
+                ("n_nodes", C.c_longlong), ("c_ref", C.c_double), ("dt", C.c_double),
+                ("dx", C.c_double), ("bytes_per_population", C.c_size_t),
+                ("device_bytes", C.c_size_t), ("steps_done", C.c_longlong)]
+
+
+EXPORTS = {
+    # name: (restype, argtypes)
+    "lbm_config_defaults": (None, [C.POINTER(lbm_config)]),
+    "lbm_bytes_required": (C.c_size_t, [C.POINTER(lbm_config)]),
+    "lbm_create": (C.c_int, [C.POINTER(lbm_config), C.POINTER(C.c_void_p)]),
+    "lbm_init_fields": (C.c_int, [C.c_void_p] + [C.c_void_p] * 4 + [C.c_int]),
+    "lbm_init_fields_pressure": (C.c_int, [C.c_void_p] + [C.c_void_p] * 4 + [C.c_int]),
+    "lbm_step": (C.c_int, [C.c_void_p, C.c_int]),
+    "lbm_step_timed": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_double), C.c_int]),
+    "lbm_moments": (C.c_int, [C.c_void_p] + [C.c_void_p] * 5 + [C.c_int]),
+    "lbm_get_populations": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int]),
+    "lbm_synchronize": (C.c_int, [C.c_void_p]),
+    "lbm_get_state": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_size_t)]),
+    "lbm_set_state": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t]),
+    "lbm_get_info": (C.c_int, [C.c_void_p, C.POINTER(lbm_info)]),
+    "lbm_destroy": (C.c_int, [C.c_void_p]),
+    "lbm_last_error": (C.c_char_p, [C.c_void_p]),
+}
+
+_lib = None
+
+
+def library_path():
+    return _build.LIBPATH
+
+
+def load_library():
+    """Load the built library (never builds; run build.build() first)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = library_path()
+    if not os.path.exists(path):
+        raise ImportError(
+            f"CUDA library {path} is missing: build it with "
+            "`python -m paper_2108_07605_gb300.build` (no CPU fallback exists)")
+    lib = C.CDLL(path)
+    for name, (res, args) in EXPORTS.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+class LBMError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+def _check(status, handle=None):
+    if status != 0:
+        msg = load_library().lbm_last_error(handle)
+        raise LBMError(status, msg.decode() if msg else "")
+
+
+def mechanism_struct(mech):
+    """Marshal a mechanism table (lbm_workloads.mechanism.Mechanism or any
+    object with the same attributes) into lbm_mechanism."""
+    s = lbm_mechanism()
+    M, R = mech.n_species, mech.n_reactions
+    if M > MAX_SPECIES or R > MAX_REACTIONS:
+        raise ValueError("mechanism exceeds the library limits")
+    s.n_species, s.n_reactions = M, R
+    for a in range(M):
+        s.molar_mass[a] = float(mech.molar_mass[a])
+        for k in range(NCP):
+            s.cp[a][k] = float(mech.cp_coeffs[a][k])
+        s.h_formation[a] = float(mech.h_formation[a])
+        s.s_standard[a] = float(mech.s_standard[a])
+        for b in range(M):
+            s.D0[a][b] = float(mech.D0[a][b])
+    for r in range(R):
+        for a in range(M):
+            s.nu_f[r][a] = int(mech.nu_f[r][a])
+            s.nu_r[r][a] = int(mech.nu_r[r][a])
+            s.efficiency[r][a] = float(mech.efficiency[r][a])
+        for k in range(3):
+            s.arrhenius[r][k] = float(mech.arrhenius[r][k])
+        s.third_body[r] = int(mech.third_body[r])
+        s.reversible[r] = int(mech.reversible[r])
+    s.D_T_exponent = float(mech.D_T_exponent)
+    s.mu0 = float(mech.mu0)
+    s.mu_T_exponent = float(mech.mu_T_exponent)
+    s.prandtl = float(mech.prandtl)
+    return s
+
+
+# ---- same-name wrappers of the C entry points ---------------------------------
+def lbm_config_defaults():
+    cfg = lbm_config()
+    load_library().lbm_config_defaults(C.byref(cfg))
+    return cfg
+
+
+def lbm_bytes_required(cfg):
+    return int(load_library().lbm_bytes_required(C.byref(cfg)))
+
+
+def lbm_create(cfg):
+    h = C.c_void_p()
+    st = load_library().lbm_create(C.byref(cfg), C.byref(h))
+    _check(st, None)
+    return h
+
+
+def _ptr(arr):
+    """(pointer, on_device) of a host numpy array or a CUDA torch tensor."""
+    if arr is None:
+        return None, 0
+    if hasattr(arr, "data_ptr"):
+        if not arr.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        if arr.is_cuda:
+            return C.c_void_p(arr.data_ptr()), 1
+        return C.c_void_p(arr.data_ptr()), 0
+    if not (isinstance(arr, np.ndarray) and arr.flags["C_CONTIGUOUS"]):
+        raise ValueError("host arrays must be C-contiguous numpy arrays")
+    return arr.ctypes.data_as(C.c_void_p), 0
+
+
+def _same_side(*arrs):
+    sides = {_ptr(a)[1] for a in arrs if a is not None}
+    if len(sides) > 1:
+        raise ValueError("mix of host and device arrays")
+    return sides.pop() if sides else 0
+
+
+def lbm_init_fields(h, rho, u, T, Y):
+    on = _same_side(rho, u, T, Y)
+    _check(load_library().lbm_init_fields(h, _ptr(rho)[0], _ptr(u)[0], _ptr(T)[0],
+                                          _ptr(Y)[0], on), h)
+
+
+def lbm_init_fields_pressure(h, P, u, T, Y):
+    on = _same_side(P, u, T, Y)
+    _check(load_library().lbm_init_fields_pressure(h, _ptr(P)[0], _ptr(u)[0], _ptr(T)[0],
+                                                   _ptr(Y)[0], on), h)
+
+
+def lbm_step(h, nsteps):
+    _check(load_library().lbm_step(h, int(nsteps)), h)
+
+
+def lbm_step_timed(h, nsteps, kernel_ms=None):
+    """Returns per-kernel device milliseconds [moments, collision] (added to
+    kernel_ms when given)."""
+    arr = (C.c_double * 2)(*(kernel_ms or (0.0, 0.0)))
+    _check(load_library().lbm_step_timed(h, int(nsteps), arr, 2), h)
+    return [arr[0], arr[1]]
+
+
+def lbm_moments(h, rho=None, u=None, T=None, Y=None, E=None):
+    on = _same_side(rho, u, T, Y, E)
+    _check(load_library().lbm_moments(h, _ptr(rho)[0], _ptr(u)[0], _ptr(T)[0],
+                                      _ptr(Y)[0], _ptr(E)[0], on), h)
+
+
+def lbm_get_populations(h, out):
+    p, on = _ptr(out)
+    _check(load_library().lbm_get_populations(h, p, on), h)
+
+
+def lbm_synchronize(h):
+    _check(load_library().lbm_synchronize(h), h)
+
+
+def lbm_get_state(h):
+    n = C.c_size_t(0)
+    _check(load_library().lbm_get_state(h, None, C.byref(n)), h)
+    buf = np.empty(n.value, dtype=np.uint8)
+    _check(load_library().lbm_get_state(h, buf.ctypes.data_as(C.c_void_p), C.byref(n)), h)
+    return buf
+
+
+def lbm_set_state(h, buf):
+    buf = np.ascontiguousarray(buf, dtype=np.uint8)
+    _check(load_library().lbm_set_state(h, buf.ctypes.data_as(C.c_void_p), buf.size), h)
+
+
+def lbm_get_info(h):
+    info = lbm_info()
+    _check(load_library().lbm_get_info(h, C.byref(info)), h)
+    return info
+
+
+def lbm_destroy(h):
+    _check(load_library().lbm_destroy(h), None)
+
+
+def lbm_last_error(h=None):
+    msg = load_library().lbm_last_error(h)
+    return msg.decode() if msg else ""
+
+
+# ---- torch-backed allocation hooks -------------------------------------------------
+class _TorchAllocator:
+    """Allocation hooks that draw from torch's caching allocator on `device`."""
+
+    def __init__(self, device, stream_ptr):
+        import torch
+        self._torch = torch
+        self.device = device
+        self.stream_ptr = stream_ptr
+
+        def alloc(nbytes, user):
+            try:
+                return torch.cuda.caching_allocator_alloc(int(nbytes), self.device,
+                                                          self.stream_ptr)
+            except Exception:
+                return None
+
+        def free(ptr, user):
+            torch.cuda.caching_allocator_delete(ptr)
+
+        self.alloc = ALLOC_FN(alloc)
+        self.free = FREE_FN(free)
+
+
+def make_config(mech, lattice="D3Q27", shape=(16, 16, 16), dx=1e-3, precision="fp64",
+                substeps=2, c_ref=0.0, T_max=3000.0, faces=None, newton_max_iter=50,
+                newton_rtol=1e-13, device=0, stream=None, use_torch_allocator=True):
+    """Build an lbm_config from Python values.  Returns (cfg, keepalive)."""
+    cfg = lbm_config_defaults()
+    cfg.lattice = LBM_D3Q27 if lattice == "D3Q27" else LBM_D2Q9
+    cfg.nx, cfg.ny, cfg.nz = (int(v) for v in shape)
+    cfg.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    cfg.substeps = int(substeps)
+    cfg.dx = float(dx)
+    cfg.c_ref = float(c_ref)
+    cfg.T_max = float(T_max)
+    cfg.mech = mechanism_struct(mech)
+    for f, kind in enumerate(faces or ("periodic",) * 6):
+        cfg.face_bc[f] = FACE_KINDS[kind] if isinstance(kind, str) else int(kind)
+    cfg.newton_max_iter = int(newton_max_iter)
+    cfg.newton_rtol = float(newton_rtol)
+    cfg.device = int(device)
+    keep = []
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                stream = torch.cuda.current_stream(device).cuda_stream
+        except Exception:
+            stream = None
+    cfg.stream = C.c_void_p(stream) if stream else None
+    if use_torch_allocator:
+        alloc = _TorchAllocator(device, stream or 0)
+        cfg.dev_alloc = alloc.alloc
+        cfg.dev_free = alloc.free
+        keep.append(alloc)
+    return cfg, keep
+
+
+class Solver:
+    """One lbm_t handle with numpy/torch-friendly methods."""
+
+    def __init__(self, mech, **kw):
+        self.mech = mech
+        self.cfg, self._keep = make_config(mech, **kw)
+        self.h = lbm_create(self.cfg)
+        self.info = lbm_get_info(self.h)
+        self.N = int(self.info.n_nodes)
+        self.M = int(self.info.M)
+
+    def init_fields(self, rho, u, T, Y):
+        lbm_init_fields(self.h, *[_flat(a) for a in (rho, u, T, Y)])
+
+    def init_fields_pressure(self, P, u, T, Y):
+        lbm_init_fields_pressure(self.h, *[_flat(a) for a in (P, u, T, Y)])
+
+    def step(self, n=1):
+        lbm_step(self.h, n)
+
+    def moments(self):
+        N, M = self.N, self.M
+        out = dict(rho=np.empty(N), u=np.empty(3 * N), T=np.empty(N), Y=np.empty(M * N),
+                   E=np.empty(N))
+        lbm_moments(self.h, out["rho"], out["u"], out["T"], out["Y"], out["E"])
+        out["u"] = out["u"].reshape(3, N)
+        out["Y"] = out["Y"].reshape(M, N)
+        return out
+
+    def populations(self):
+        info = self.info
+        out = np.empty(info.L * info.Q * self.N)
+        lbm_get_populations(self.h, out)
+        return out.reshape(info.L, info.Q, self.N)
+
+    def synchronize(self):
+        lbm_synchronize(self.h)
+
+    def get_state(self):
+        return lbm_get_state(self.h)
+
+    def set_state(self, buf):
+        lbm_set_state(self.h, buf)
+
+    def close(self):
+        if self.h is not None:
+            h, self.h = self.h, None
+            lbm_destroy(h)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _flat(a):
+    if hasattr(a, "data_ptr"):
+        return a.contiguous()
+    return np.ascontiguousarray(a, dtype=np.float64).reshape(-1)
