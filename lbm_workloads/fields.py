@@ -91,3 +91,33 @@ def shear_wave(nx=32, ny=1, nz=1, amplitude=1e-3, background=0.0, T=300.0,
     w.update(lattice=lattice, shape=(nx, ny, nzz), dx=dx, T_max=T, substeps=1,
              faces=("periodic",) * 6, steps=0, name="shear wave")
     return w
+
+
+def perturbed_box(shape, lattice="D3Q27", seed=7, T0=1400.0, dx=1e-3, mech=None,
+                  amp_T=2e-2, amp_u=3.0, amp_Y=2e-3):
+    """A periodic box with seeded temperature, velocity and composition
+    perturbations, so that gradients, diffusion velocities and the energy
+    flux corrections are all exercised."""
+    mech = mech or h2_air_synthetic()
+    nx, ny, nz = shape
+    rng = philox(seed)
+    g = (nz, ny, nx)
+    M = mech.n_species
+    if "H2" in mech.species:
+        Y0 = mole_to_mass_fractions(mech, air_mole_fractions(mech, 0.5))
+    else:
+        Y0 = np.full(M, 1.0 / M)
+    w = dict(dx=dx, T_max=3000.0, substeps=2, faces=("periodic",) * 6, seed=seed)
+    Y = np.empty((M,) + g)
+    noise = rng.uniform(-1.0, 1.0, size=(M,) + g)
+    for a in range(M):
+        Y[a] = Y0[a] * (1.0 + amp_Y * noise[a]) + amp_Y * 1e-3 * (noise[a] + 1.0)
+    Y /= Y.sum(axis=0, keepdims=True)
+    u = amp_u * rng.uniform(-1.0, 1.0, size=(3,) + g)
+    if lattice == "D2Q9":
+        u[2] = 0.0
+    T = T0 * (1.0 + amp_T * rng.uniform(-1.0, 1.0, size=g))
+    P = np.full(g, 101325.0) * (1.0 + 1e-3 * rng.uniform(-1.0, 1.0, size=g))
+    w.update(shape=shape, lattice=lattice, P=P, T=T, u=u, Y=Y,
+             name=f"perturbed box {shape} {lattice}")
+    return w

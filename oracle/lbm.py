@@ -132,7 +132,8 @@ class OracleLBM:
         self.pops[self.M] = energy_equilibrium(self.vs, rho, u, theta, U)
         self.T = T.copy()
         if self.bc is not None:
-            self.bc.init_history(rho, u, T, Y)
+            self.bc.init_history(rho, u * self.units.c, T, Y)
+            self.solid_state = self.pops[:, :, self.bc.solid].copy()
 
     # ------------------------------------------------------------------ #
     def moments_of(self, pops):
@@ -180,6 +181,8 @@ class OracleLBM:
         # 2. boundary reconstruction at interface nodes
         if self.bc is not None:
             pops = self.bc.apply(post, pops)
+            if self.bc.solid.any():               # solid nodes stay frozen
+                pops[:, :, self.bc.solid] = self.solid_state
         # 3. moments
         mom = self.moments_of(pops)
         rho, rho_s, j_s = mom["rho"], mom["rho_s"], mom["j_s"]
@@ -260,6 +263,8 @@ class OracleLBM:
         # 10. store
         if self.bc is not None:
             self.bc.end_of_step(self, rho, u, T, Y)
+            if self.bc.solid.any():
+                new[:, :, self.bc.solid] = self.solid_state
         self.pops = new
         self.step_count += 1
 
