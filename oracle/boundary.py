@@ -29,8 +29,9 @@ and one forward-Euler step (dt = 1) from the previous values at x:
   T^out = p^out / (rho^out R(Y^out)).
 Mass fractions, Eq. convectiveBC with a backward difference along n:
   Y^out = Y - u_n d_n Y.
-"Previous step's fields" are the post-boundary moments of the previous step
-(the initial fields before the first step).
+"Previous step's fields" are the fields of the stored post-collision state
+at time t - dt (what the moments call reports), at x and x - n; before the
+first step these are the initial fields.
 
 Gradient ghost values for nodes outside the domain (reading): wall or solid
 -> Phi = 0 (the wall is at rest) and Y = Y(x); inlet -> Phi of the inlet
@@ -109,19 +110,7 @@ class Boundaries:
         self.incoming &= ~self.solid[None]
         if np.any((self.node_kind == 2) & (self.wall_T is None)):
             raise ValueError("TMS walls need wall_T")
-        self.hist = None
-        # non-periodic neighbours for the gradient ghosts
         self.ext = ext
-
-    # ------------------------------------------------------------------ #
-    def init_history(self, rho, u, T, Y):
-        c = self.lbm.units.c
-        self.hist = dict(rho=np.array(rho, dtype=float),
-                         u=np.asarray(u, dtype=float)[: self.lbm.vs.dim] / c,
-                         T=np.array(T, dtype=float), Y=np.array(Y, dtype=float))
-
-    def end_of_step(self, lbm, rho, u, T, Y):
-        self.hist = dict(rho=rho.copy(), u=u.copy(), T=T.copy(), Y=Y.copy())
 
     # ------------------------------------------------------------------ #
     def _equilibria(self, rho, Y, u, T, u_species=None):
@@ -189,7 +178,7 @@ class Boundaries:
             elif k == 3:
                 flat[:, :, idx] = self._inlet(p, D, Tguess[idx])
             else:
-                flat[:, :, idx] = self._outlet(p, D, idx, Tguess[idx])
+                flat[:, :, idx] = self._outlet(p, D, idx, Tguess[idx], post)
         return out
 
     def _tms(self, p, bb, D, idx, Tg):
@@ -230,25 +219,27 @@ class Boundaries:
         tgt = self._equilibria(rho_l, Y_l, u_in, T_in)                # Eqs. in_tgt_*
         return np.where(D, tgt + fin - loc, tgt + p - loc)            # Eqs. f_inlet-fa_inlet
 
-    def lodi_state(self, idx):
-        """LODI outlet data (rho, u, T, Y) at outlet nodes idx (flat)."""
+    def stored_fields(self, post, nodes):
+        """rho, u, T, Y of the stored post-collision state `post` at flat node
+        indices (the fields at time t - dt); Newton starts from the T field."""
+        lbm = self.lbm
+        p = post.reshape(lbm.L, lbm.vs.Q, -1)[:, :, nodes]
+        rho, u, Y, _, T = self._local_state(p, lbm.T.ravel()[nodes])
+        return rho, u, T, Y
+
+    def lodi_state(self, idx, post):
+        """LODI outlet data (rho, u, T, Y) at outlet nodes idx (flat), from the
+        stored state of the previous step at x and x - n."""
         lbm = self.lbm
         mech = lbm.mech
         dim = lbm.vs.dim
         nz, ny, nx = lbm.shape
         ax = self.out_axis.ravel()[idx]
         sg = self.out_sign.ravel()[idx]
-        h = {k: v.reshape((-1, nz * ny * nx)) if v.ndim > 3 else v.reshape(1, -1)
-             for k, v in self.hist.items()}
         stride = np.array([1, nx, nx * ny])
         up = idx - sg * stride[ax]                                    # upstream node x - n
-
-        def at(name, nodes):
-            return h[name][:, nodes]
-        rho0, rho1 = at("rho", idx)[0], at("rho", up)[0]
-        T0, T1 = at("T", idx)[0], at("T", up)[0]
-        Y0, Y1 = at("Y", idx), at("Y", up)
-        u0, u1 = at("u", idx), at("u", up)
+        rho0, u0, T0, Y0 = self.stored_fields(post, idx)
+        rho1, u1, T1, Y1 = self.stored_fields(post, up)
         c2 = lbm.units.c ** 2
         R0 = thermo.mixture_gas_constant(mech, Y0)
         R1 = thermo.mixture_gas_constant(mech, Y1)
@@ -282,9 +273,9 @@ class Boundaries:
         T_o = p_o * c2 / (rho_o * thermo.mixture_gas_constant(mech, Y_o))
         return rho_o, u_o, T_o, Y_o
 
-    def _outlet(self, p, D, idx, Tg):
+    def _outlet(self, p, D, idx, Tg, post):
         """Sec. 4.4, steps 1-3."""
-        rho_o, u_o, T_o, Y_o = self.lodi_state(idx)
+        rho_o, u_o, T_o, Y_o = self.lodi_state(idx, post)
         fout = self._equilibria(rho_o, Y_o, u_o, T_o)                 # Eqs. out_f-out_fa
         pl = np.where(D, fout, p)
         rho_l, u_l, Y_l, _, T_l = self._local_state(pl, Tg)           # Eqs. outletloc*

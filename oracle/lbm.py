@@ -132,7 +132,6 @@ class OracleLBM:
         self.pops[self.M] = energy_equilibrium(self.vs, rho, u, theta, U)
         self.T = T.copy()
         if self.bc is not None:
-            self.bc.init_history(rho, u * self.units.c, T, Y)
             self.solid_state = self.pops[:, :, self.bc.solid].copy()
 
     # ------------------------------------------------------------------ #
@@ -262,7 +261,6 @@ class OracleLBM:
         new[M] = gnew
         # 10. store
         if self.bc is not None:
-            self.bc.end_of_step(self, rho, u, T, Y)
             if self.bc.solid.any():
                 new[:, :, self.bc.solid] = self.solid_state
         self.pops = new
