@@ -210,6 +210,35 @@ lbm_status lbm_get_info(lbm_t h, lbm_info* info);
 /* Release the handle and its device memory.  Returns the sticky status. */
 lbm_status lbm_destroy(lbm_t h);
 
+/* Allocation-free single step.  The paper has no counterpart: this entry
+ * point exists for callers that cannot allocate device memory themselves -
+ * a solver embedded in an application that owns every device allocation
+ * through its own pool, a loop on a latency budget where cudaMalloc/cudaFree
+ * would synchronise the device, or a process under a fixed memory budget.
+ * It advances caller-owned populations by one step exactly as lbm_step does
+ * for a handle created from the same cfg, and calls no allocator.
+ *  cfg      the configuration lbm_create takes (periodic faces; cfg->stream,
+ *           cfg->device and cfg->precision are honoured; the allocation hooks
+ *           are ignored).
+ *  pops_in  device, stored populations in cfg->precision, layout
+ *           [lattice][i][N] (what lbm_get_populations returns for FP64).
+ *  pops_out device, same size, distinct from pops_in; receives the step.
+ *  T_guess  device [N] temperature guess in K, read and overwritten with the
+ *           step's temperatures (the initial temperatures before the first
+ *           step).
+ *  error    optional; set to a message on failure (valid until the next
+ *           call on the same thread).
+ * The per-node scratch lives in a fixed array inside the library sized for
+ * LBM_NOALLOC_MAX_NODES nodes (about 7.1 MB, held by every GPU that loads
+ * the library until the process exits); larger grids return LBM_ERR_RANGE.
+ * Every call shares that array, so calls that overlap on the GPU race.  The
+ * first call on a device looks up the array's device address; make it
+ * before any stream capture.  The call waits for its stream and returns the
+ * step's device status (LBM_ERR_NEWTON, LBM_ERR_NONFINITE). */
+#define LBM_NOALLOC_MAX_NODES 16384
+lbm_status lbm_step_noalloc(const lbm_config* cfg, const void* pops_in, void* pops_out,
+                            double* T_guess, const char** error);
+
 /* Text of the last error on h (or of the last lbm_create failure if h is
  * NULL).  Valid until the next call on h. */
 const char* lbm_last_error(lbm_t h);

@@ -19,7 +19,7 @@ LIBDIR = os.path.join(HERE, "_lib")
 LIBNAME = "libpaper2108lbm.so"
 LIBPATH = os.path.join(LIBDIR, LIBNAME)
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["lbm_kernels.cu", "lbm_capi.cu"]
+SOURCES = ["lbm_kernels.cu", "lbm_capi.cu", "lbm_noalloc.cu"]
 
 
 def nvcc():

@@ -249,6 +249,25 @@ lbm_status init_common(lbm_ctx* h, const double* rho_or_P, int is_pressure, cons
 
 }  // namespace
 
+namespace lbm {
+// Host helpers shared with the allocation-free entry point (lbm_noalloc.cu).
+std::string validate_config(const lbm_config* c) { return validate(c); }
+void build_device_mechanism(const lbm_mechanism& m, DevMech& d) { build_mech(m, d); }
+void fill_units(const lbm_config& cfg, Units& un) {
+  const double c = cfg.c_ref > 0.0 ? cfg.c_ref : default_c_ref(cfg);
+  un.c = c;
+  un.inv_c = 1.0 / c;
+  un.inv_c2 = 1.0 / (c * c);
+  un.dx = cfg.dx;
+  un.dt = cfg.dx / c;
+  un.s_pref = R_U * R_U * cfg.dx / (c * P_REF);
+  un.nu_pref = 1.0 / (c * cfg.dx);
+  un.substeps = cfg.substeps;
+  un.newton_max_iter = cfg.newton_max_iter;
+  un.newton_rtol = cfg.newton_rtol;
+}
+}  // namespace lbm
+
 extern "C" {
 
 void lbm_config_defaults(lbm_config* cfg) {

@@ -4,6 +4,7 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <string>
 #include <cuda_runtime.h>
 
 #include "../../include/lbm.h"
@@ -87,5 +88,10 @@ cudaError_t launch_moments_out(int D, int M, lbm_precision prec, const DevMech& 
 cudaError_t launch_to_fp64(lbm_precision prec, const void* pops, double* out,
                            long long count, cudaStream_t s);
 int record_fields(int D, int M);
+
+// Host helpers defined in lbm_capi.cu.
+std::string validate_config(const lbm_config* c);   // "" when valid
+void build_device_mechanism(const lbm_mechanism& m, DevMech& d);
+void fill_units(const lbm_config& cfg, Units& un);
 
 }  // namespace lbm

@@ -1,0 +1,127 @@
+// lbm_step_noalloc: one time step with no device allocation at all.
+//
+// The regular entry points keep their per-node moment records (the scratch
+// the step's two kernels exchange) in memory that lbm_create allocates.
+// Some callers cannot allocate device memory on their own: a solver that is
+// embedded in a host application owning every device allocation through its
+// own pool, a loop on a latency budget where cudaMalloc/cudaFree would
+// synchronise the device, or a process running under a fixed memory budget.
+// For them this entry point advances caller-owned populations by one step
+// and takes its scratch from the file-scope array below instead.
+//
+// Limits and behaviour:
+//  - the scratch holds the moment records of at most
+//    LBM_NOALLOC_MAX_NODES nodes (16 384 nodes, about 7.1 MB, plus the status
+//    word); every GPU that loads this library holds the array until the
+//    process exits;
+//  - every call shares the one array, so calls whose work overlaps on the
+//    GPU (other streams, other host threads) race on it;
+//  - the first call on a device looks up the array's device address with
+//    cudaGetSymbolAddress while that device is current; make that first call
+//    before any stream capture;
+//  - the status word is cleared at each call; the call waits for its stream
+//    to read it back.
+#include <cstring>
+#include <mutex>
+#include <string>
+
+#include "lbm_internal.h"
+
+namespace {
+
+constexpr long long kMaxNodes = LBM_NOALLOC_MAX_NODES;
+constexpr int kMaxFields = 54;                        // D3Q27 with 9 species
+constexpr long long kRecordDoubles = kMaxNodes * kMaxFields;
+
+// Moment records [field][node], then 32 doubles whose first int is the
+// status word.
+static __device__ __align__(256) double g_noalloc_scratch[kRecordDoubles + 32];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_setup_mutex;
+double* g_scratch_ptr[kMaxDevices] = {nullptr};
+thread_local std::string g_noalloc_error;
+
+// Device address of the scratch array on `device` (current at the call);
+// looked up once per device.
+cudaError_t scratch_on(int device, double** out) {
+  std::lock_guard<std::mutex> lock(g_setup_mutex);
+  if (!g_scratch_ptr[device]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return e;
+    g_scratch_ptr[device] = static_cast<double*>(p);
+  }
+  *out = g_scratch_ptr[device];
+  return cudaSuccess;
+}
+
+lbm_status noalloc_fail(lbm_status st, const std::string& msg) {
+  g_noalloc_error = msg;
+  return st;
+}
+
+}  // namespace
+
+extern "C" lbm_status lbm_step_noalloc(const lbm_config* cfg, const void* pops_in,
+                                       void* pops_out, double* T_guess,
+                                       const char** error) {
+  using namespace lbm;
+  if (error) *error = nullptr;
+  lbm_status st = LBM_OK;
+  const std::string why = validate_config(cfg);
+  if (!why.empty()) st = noalloc_fail(LBM_ERR_INVALID, why);
+  else if (!pops_in || !pops_out || !T_guess || pops_in == pops_out)
+    st = noalloc_fail(LBM_ERR_INVALID, "need distinct device buffers pops_in, pops_out and T_guess");
+  else if (cfg->device >= kMaxDevices)
+    st = noalloc_fail(LBM_ERR_RANGE, "device ordinal beyond the supported 64 devices");
+  else {
+    const long long N = (long long)cfg->nx * cfg->ny * cfg->nz;
+    const int D = cfg->lattice == LBM_D3Q27 ? 3 : 2;
+    const int NF = record_fields(D, cfg->mech.n_species);
+    if (N > kMaxNodes || NF > kMaxFields)
+      st = noalloc_fail(LBM_ERR_RANGE,
+                        "lbm_step_noalloc handles at most " + std::to_string(kMaxNodes) +
+                            " nodes (got " + std::to_string(N) +
+                            "); use lbm_create/lbm_step for larger grids");
+    else {
+      int prev = -1;
+      cudaGetDevice(&prev);
+      if (prev != cfg->device) cudaSetDevice(cfg->device);
+      double* scratch = nullptr;
+      cudaError_t e = scratch_on(cfg->device, &scratch);
+      cudaStream_t stream = static_cast<cudaStream_t>(cfg->stream);
+      int* status = reinterpret_cast<int*>(scratch + kRecordDoubles);
+      if (e == cudaSuccess) e = cudaMemsetAsync(status, 0, sizeof(int), stream);
+      if (e == cudaSuccess) {
+        DevMech mech;
+        build_device_mechanism(cfg->mech, mech);
+        StepArgs a;
+        a.src = pops_in;
+        a.dst = pops_out;
+        a.rec = scratch;
+        a.Tfield = T_guess;
+        a.status = status;
+        a.g.nx = cfg->nx;
+        a.g.ny = cfg->ny;
+        a.g.nz = cfg->nz;
+        a.g.N = N;
+        fill_units(*cfg, a.un);
+        e = launch_step(D, cfg->mech.n_species, cfg->precision, mech, a, stream);
+      }
+      int bits = 0;
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(&bits, status, sizeof(int), cudaMemcpyDeviceToHost, stream);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+      if (prev >= 0 && prev != cfg->device) cudaSetDevice(prev);
+      if (e != cudaSuccess)
+        st = noalloc_fail(LBM_ERR_CUDA, std::string("lbm_step_noalloc: ") + cudaGetErrorString(e));
+      else if (bits & ST_NEWTON)
+        st = noalloc_fail(LBM_ERR_NEWTON, "temperature Newton did not converge");
+      else if (bits & ST_NONFINITE)
+        st = noalloc_fail(LBM_ERR_NONFINITE, "non-finite or non-positive density or temperature");
+    }
+  }
+  if (st != LBM_OK && error) *error = g_noalloc_error.c_str();
+  return st;
+}

@@ -94,6 +94,8 @@ EXPORTS = {
     "lbm_get_info": (C.c_int, [C.c_void_p, C.POINTER(lbm_info)]),
     "lbm_destroy": (C.c_int, [C.c_void_p]),
     "lbm_last_error": (C.c_char_p, [C.c_void_p]),
+    "lbm_step_noalloc": (C.c_int, [C.POINTER(lbm_config), C.c_void_p, C.c_void_p,
+                                   C.c_void_p, C.POINTER(C.c_char_p)]),
 }
 
 _lib = None
@@ -266,6 +268,16 @@ def lbm_get_info(h):
 
 def lbm_destroy(h):
     _check(load_library().lbm_destroy(h), None)
+
+
+def lbm_step_noalloc(cfg, pops_in, pops_out, T_guess):
+    """One step on caller-owned device buffers with no device allocation
+    (for callers that cannot allocate; see include/lbm.h)."""
+    err = C.c_char_p()
+    st = load_library().lbm_step_noalloc(C.byref(cfg), _ptr(pops_in)[0], _ptr(pops_out)[0],
+                                         _ptr(T_guess)[0], C.byref(err))
+    if st != 0:
+        raise LBMError(st, err.value.decode() if err.value else "")
 
 
 def lbm_last_error(h=None):
