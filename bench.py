@@ -47,7 +47,7 @@ def parse():
     p.add_argument("--steps", type=int, default=20)
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--workload", default="reactor", choices=sorted(WORKLOADS))
+    p.add_argument("--workload", default="flame", choices=sorted(WORKLOADS))
     p.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -68,6 +68,15 @@ WORKLOADS = {"reactor": "homogeneous reactor 16^3 periodic D3Q27, M=9, 21 reacti
                       "21 reactions, phi=0.5, tanh ignition kernel at x=256",
              "box": "perturbed periodic box 128x64x64 D3Q27, M=9, 21 reactions, "
                     "1400 K +-2%, |u| <= 1 m/s (profiling case larger than L2)"}
+
+
+def boundary_spec(w):
+    """Boundary description of a workload (faces, inlet, outlet, walls,
+    solid nodes), or None for a periodic box."""
+    keys = ("faces", "inlet", "outlet", "wall_T", "solid", "solid_kind")
+    if all(f == "periodic" for f in w.get("faces", ("periodic",) * 6)) and w.get("solid") is None:
+        return None
+    return {k: w[k] for k in keys if k in w}
 
 
 def dist_env():
@@ -168,7 +177,7 @@ def run_reference(args, rank):
     mech = h2_air_synthetic()
     w = _workload(args.workload, 0)
     o = OracleLBM(mech, w["lattice"], w["shape"], w["dx"], T_max=w["T_max"],
-                  substeps=w["substeps"])
+                  substeps=w["substeps"], boundaries=boundary_spec(w))
     rho = thermo.density_from_pressure(mech, w["P"], w["T"], w["Y"])
     o.init_fields(rho, w["u"], w["T"], w["Y"])
     o.step(args.warmup)
@@ -198,7 +207,7 @@ def cpu_baseline(args, w, mech, budget_s=15.0):
     """Oracle timed on the host on a bounded number of steps of the same workload."""
     from oracle import OracleLBM, thermo
     o = OracleLBM(mech, w["lattice"], w["shape"], w["dx"], T_max=w["T_max"],
-                  substeps=w["substeps"])
+                  substeps=w["substeps"], boundaries=boundary_spec(w))
     rho = thermo.density_from_pressure(mech, w["P"], w["T"], w["Y"])
     o.init_fields(rho, w["u"], w["T"], w["Y"])
     t0 = time.perf_counter()
@@ -240,7 +249,7 @@ def main():
     M = mech.n_species
     solver = lbm.Solver(mech, lattice=w["lattice"], shape=w["shape"], dx=w["dx"],
                         precision=args.precision, substeps=w["substeps"], T_max=w["T_max"],
-                        faces=w["faces"], device=local)
+                        device=local, **(boundary_spec(w) or {}))
     solver.init_fields_pressure(w["P"], w["u"], w["T"], w["Y"])
     info = solver.info
     state_bytes = 2 * info.L * info.Q * N * info.bytes_per_population

@@ -118,8 +118,13 @@ typedef struct lbm_config {
   lbm_mechanism mech;
   lbm_bc face_bc[6];          /* faces -x, +x, -y, +y, -z, +z                  */
   double wall_T[6];           /* TMS wall temperature per face, K             */
-  const double* inlet_u;      /* host [3][face nodes] inlet velocity, m/s, or
-                                 NULL for the uniform inlet_u_uniform         */
+  const uint8_t* solid_mask;  /* optional host [N], 1 = solid node (staircase
+                                 walls); NULL = no solid nodes                */
+  lbm_bc solid_bc;            /* LBM_BOUNCE_BACK or LBM_TMS_WALL              */
+  const double* wall_T_nodes; /* optional host [N] TMS target temperature of
+                                 each interface node, K; NULL = face values   */
+  const double* inlet_u;      /* optional host [3][N] inlet velocity of each
+                                 inlet node, m/s; NULL = inlet_u_uniform      */
   double inlet_u_uniform[3];
   double inlet_Y[LBM_MAX_SPECIES];
   double inlet_T, inlet_P;

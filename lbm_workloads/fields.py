@@ -121,3 +121,65 @@ def perturbed_box(shape, lattice="D3Q27", seed=7, T0=1400.0, dx=1e-3, mech=None,
     w.update(shape=shape, lattice=lattice, P=P, T=T, u=u, Y=Y,
              name=f"perturbed box {shape} {lattice}")
     return w
+
+
+def wall_ramp(x, nx, T_cold=300.0, T_hot=1500.0, frac=0.25):
+    """Wall temperature: linear T_cold -> T_hot over the first `frac` of the
+    length, then T_hot."""
+    L = frac * nx
+    return np.where(x < L, T_cold + (T_hot - T_cold) * x / L, T_hot)
+
+
+def channel_2d(seed=0, nx=2000, ny=40, phi=0.5, T_in=300.0, dx=25e-6, steps=50000,
+               mech=None):
+    """2-D microchannel: D2Q9 nx x ny, Tamm-Mott-Smith walls beyond y = 0 and
+    y = ny-1 carrying the wall_ramp temperature, parabolic inlet
+    u = u_max 4 s (1 - s) (s = (y + 1/2)/ny, u_max drawn from the seed in
+    [0.2, 3] m/s) of fresh mixture at x = 0, pressure outlet at x = nx-1.
+    Initial state: T = wall temperature of the column, fresh mixture, the
+    inlet velocity profile everywhere."""
+    mech = mech or h2_air_synthetic()
+    u_max = float(philox(seed).uniform(0.2, 3.0))
+    Y = mole_to_mass_fractions(mech, air_mole_fractions(mech, phi))
+    w = _uniform_fields(mech, (nx, ny, 1), T_in, P_STANDARD, Y)
+    x = np.arange(nx, dtype=float)
+    s = (np.arange(ny) + 0.5) / ny
+    prof = u_max * 4.0 * s * (1.0 - s)
+    Tw = wall_ramp(x, nx)
+    w["T"] = np.broadcast_to(Tw[None, None, :], (1, ny, nx)).copy()
+    w["u"][0] = np.broadcast_to(prof[None, :, None], (1, ny, nx))
+    w.update(lattice="D2Q9", shape=(nx, ny, 1), dx=dx, T_max=3000.0, substeps=2,
+             faces=("inlet", "outlet", "tms", "tms", "periodic", "periodic"),
+             wall_T=w["T"].copy(),
+             inlet=dict(u=w["u"].copy(), T=T_in, Y=Y, P=P_STANDARD),
+             outlet=dict(P=P_STANDARD), steps=steps, seed=seed,
+             name=f"channel {nx}x{ny} D2Q9 phi={phi} u_max={u_max:.3f}")
+    return w
+
+
+def microtube(seed=0, nx=600, ny=40, nz=40, radius=19.0, phi=0.5, T_in=300.0,
+              u_in=1.0, dx=25e-6, steps=20000, mech=None):
+    """3-D microtube: D3Q27 nx x ny x nz, fluid where
+    (y - c)^2 + (z - c)^2 < radius^2 (c = (ny-1)/2), staircase solid elsewhere
+    with Tamm-Mott-Smith walls at the wall_ramp temperature; inlet of fresh
+    mixture at u_in at x = 0, pressure outlet at x = nx-1; initial velocity
+    u_in (1 + 0.01 N(0,1)) seeded, T = wall temperature of the column."""
+    mech = mech or h2_air_synthetic()
+    rng = philox(seed)
+    Y = mole_to_mass_fractions(mech, air_mole_fractions(mech, phi))
+    w = _uniform_fields(mech, (nx, ny, nz), T_in, P_STANDARD, Y)
+    x = np.arange(nx, dtype=float)
+    cy, cz = (ny - 1) / 2.0, (nz - 1) / 2.0
+    zz, yy = np.meshgrid(np.arange(nz), np.arange(ny), indexing="ij")
+    fluid2 = (yy - cy) ** 2 + (zz - cz) ** 2 < radius ** 2
+    solid = np.broadcast_to(~fluid2[:, :, None], (nz, ny, nx)).copy()
+    Tw = wall_ramp(x, nx)
+    w["T"] = np.broadcast_to(Tw[None, None, :], (nz, ny, nx)).copy()
+    w["u"][0] = u_in * (1.0 + 0.01 * rng.standard_normal((nz, ny, nx)))
+    w.update(lattice="D3Q27", shape=(nx, ny, nz), dx=dx, T_max=3000.0, substeps=2,
+             faces=("inlet", "outlet", "periodic", "periodic", "periodic", "periodic"),
+             solid=solid, solid_kind="tms", wall_T=w["T"].copy(),
+             inlet=dict(u=np.array([u_in, 0.0, 0.0]), T=T_in, Y=Y, P=P_STANDARD),
+             outlet=dict(P=P_STANDARD), steps=steps, seed=seed,
+             name=f"microtube {nx}x{ny}x{nz} D3Q27 r={radius} phi={phi}")
+    return w

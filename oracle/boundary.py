@@ -67,7 +67,10 @@ class Boundaries:
         self.outlet_P = float(outlet.get("P", 101325.0))
         self.outlet_sigma = float(outlet.get("sigma", 0.25))
         if inlet is not None:
-            self.u_in = np.asarray(inlet["u"], dtype=float)[:D] / lbm.units.c
+            u_in = np.asarray(inlet["u"], dtype=float)
+            if u_in.ndim == 1:                       # uniform, else one vector per node
+                u_in = np.broadcast_to(u_in[:, None, None, None], (3,) + lbm.shape)
+            self.u_in = u_in.reshape((3,) + lbm.shape)[:D] / lbm.units.c
             self.T_in = float(inlet["T"])
             self.Y_in = np.asarray(inlet["Y"], dtype=float)
             self.rho_in = float(thermo.density_from_pressure(
@@ -176,7 +179,7 @@ class Boundaries:
             elif k == 2:
                 flat[:, :, idx] = self._tms(p, post_flat[:, opp][:, :, idx], D, idx, Tguess[idx])
             elif k == 3:
-                flat[:, :, idx] = self._inlet(p, D, Tguess[idx])
+                flat[:, :, idx] = self._inlet(p, D, idx, Tguess[idx])
             else:
                 flat[:, :, idx] = self._outlet(p, D, idx, Tguess[idx], post)
         return out
@@ -204,13 +207,13 @@ class Boundaries:
         # step 4, Eqs. ftms, gtms, fatms
         return np.where(D, 2.0 * tgt - loc, tgt + p - loc)
 
-    def _inlet(self, p, D, Tg):
+    def _inlet(self, p, D, idx, Tg):
         """Sec. 4.3, steps 1-4."""
         lbm = self.lbm
         n = p.shape[-1]
         rho_in = np.full(n, self.rho_in)
         Y_in = np.repeat(self.Y_in[:, None], n, axis=1)
-        u_in = np.repeat(self.u_in[:, None], n, axis=1)
+        u_in = self.u_in.reshape(self.u_in.shape[0], -1)[:, idx]
         T_in = np.full(n, self.T_in)
         fin = self._equilibria(rho_in, Y_in, u_in, T_in)              # Eqs. in_f-in_fa
         pl = np.where(D, fin, p)
@@ -297,6 +300,7 @@ class Boundaries:
                 / lbm.units.c ** 2 if hasattr(self, "u_in") else 0.0
             phi_in = (self.rho_in * self.u_in * (1.0 - 3.0 * theta_in)
                       - self.rho_in * self.u_in ** 3) if hasattr(self, "u_in") else None
+            # phi_in: [D, z, y, x], the inlet state at each node's own inlet velocity
         grads = np.zeros((D,) + phi.shape)
         for i, ci in enumerate(vs.c):
             if not np.any(ci):
@@ -322,7 +326,7 @@ class Boundaries:
             if kind == "Phi":
                 ghost = np.where(wall[None], 0.0, nb)
                 if phi_in is not None:
-                    ghost = np.where(inl[None], phi_in.reshape((-1,) + (1,) * 3), ghost)
+                    ghost = np.where(inl[None], phi_in, ghost)
                 ghost = np.where(outl[None], phi, ghost)
             else:
                 ghost = np.where((wall | inl | outl)[None], phi, nb)

@@ -25,6 +25,8 @@ struct lbm_ctx {
   int* status = nullptr;    // sticky device status word
   double* io = nullptr;     // staging for host <-> device field copies
   size_t io_bytes = 0;
+  BCDev bc;                 // boundary data (device arrays owned by the handle)
+  void* bc_mem = nullptr;   // one allocation holding every boundary array
   cudaStream_t stream = nullptr;
   size_t bytes = 0;
   long long steps = 0;
@@ -60,6 +62,9 @@ void dfree(const lbm_config& c, void* p) {
 }
 
 int lattice_dim(lbm_lattice l) { return l == LBM_D3Q27 ? 3 : 2; }
+
+// component a of velocity i, i = (cz+1)*9 + (cy+1)*3 + (cx+1)
+int cvel_host(int i, int a) { return a == 0 ? i % 3 - 1 : (a == 1 ? (i / 3) % 3 - 1 : i / 9 - 1); }
 
 double default_c_ref(const lbm_config& c) {
   double rmax = 0.0;
@@ -99,9 +104,37 @@ std::string validate(const lbm_config* c) {
     if (!(m.arrhenius[r][0] > 0.0)) return "Arrhenius A must be positive";
   }
   if (!(m.mu0 > 0.0) || !(m.prandtl > 0.0)) return "mu0 and prandtl must be positive";
-  for (int f = 0; f < 6; ++f)
-    if (c->face_bc[f] != LBM_PERIODIC)
-      return "non-periodic faces are not supported by this build";
+  bool any_tms = c->solid_mask && c->solid_bc == LBM_TMS_WALL, any_in = false, any_out = false;
+  for (int f = 0; f < 6; ++f) {
+    const lbm_bc k = c->face_bc[f];
+    if (k < LBM_PERIODIC || k > LBM_OUTLET) return "unknown face boundary kind";
+    if (c->lattice == LBM_D2Q9 && f >= 4 && k != LBM_PERIODIC)
+      return "D2Q9 needs periodic z faces";
+    if (k == LBM_TMS_WALL) {
+      any_tms = true;
+      if (!c->wall_T_nodes && !(c->wall_T[f] > 0.0)) return "TMS face needs wall_T";
+    }
+    any_in |= k == LBM_INLET;
+    any_out |= k == LBM_OUTLET;
+  }
+  if (c->solid_mask && c->solid_bc != LBM_BOUNCE_BACK && c->solid_bc != LBM_TMS_WALL)
+    return "solid_bc must be LBM_BOUNCE_BACK or LBM_TMS_WALL";
+  if (c->solid_mask && c->solid_bc == LBM_TMS_WALL && !c->wall_T_nodes)
+    return "TMS solid walls need wall_T_nodes";
+  if (any_tms && c->wall_T_nodes)
+    for (long long n = 0; n < (long long)c->nx * c->ny * c->nz; ++n)
+      if (!(c->wall_T_nodes[n] > 0.0)) return "wall_T_nodes must be positive";
+  if (any_in) {
+    if (!(c->inlet_T > 0.0) || !(c->inlet_P > 0.0)) return "inlet needs inlet_T and inlet_P";
+    double ys = 0.0;
+    for (int a = 0; a < m.n_species; ++a) {
+      if (c->inlet_Y[a] < 0.0) return "inlet_Y must be >= 0";
+      ys += c->inlet_Y[a];
+    }
+    if (std::fabs(ys - 1.0) > 1e-9) return "inlet_Y must sum to 1";
+  }
+  if (any_out && !(c->outlet_P > 0.0 && c->outlet_sigma >= 0.0))
+    return "outlet needs outlet_P > 0 and outlet_sigma >= 0";
   if (c->newton_max_iter < 1 || !(c->newton_rtol >= 0.0)) return "bad Newton parameters";
   if (c->device < 0) return "device must be >= 0";
   return "";
@@ -156,11 +189,83 @@ void build_mech(const lbm_mechanism& m, DevMech& d) {
 
 size_t elem_size(lbm_precision p) { return p == LBM_FP64 ? 8 : 4; }
 
-struct Sizes {
-  size_t pops, rec, tf, status, io, total;
+// Interface-node classification (Sec. 4.1): a link i of node x is incoming
+// when x - c_i lies beyond a non-periodic face or on a solid node; the node's
+// procedure is the one of its incoming links with the highest precedence
+// (walls, then inlet, then outlet; the first such link in index order).
+struct HostBC {
+  bool needed = false, has_solid = false;
+  int n_if = 0;
+  std::vector<int> tag, if_node, if_info;
+  std::vector<unsigned> if_inc;
+  std::vector<double> wallT, uin;   // uin [3][n_if], lattice units
 };
 
-Sizes sizes_for(const lbm_config& c) {
+int precedence(int k) {
+  return (k == BK_BB || k == BK_TMS) ? 3 : (k == BK_INLET ? 2 : (k == BK_OUTLET ? 1 : 0));
+}
+
+HostBC classify(const lbm_config& c, double c_ref) {
+  HostBC h;
+  const int D = lattice_dim(c.lattice);
+  const int Q = D == 3 ? 27 : 9;
+  const int ext[3] = {c.nx, c.ny, c.nz};
+  const long long N = (long long)c.nx * c.ny * c.nz;
+  h.has_solid = c.solid_mask != nullptr;
+  h.needed = h.has_solid;
+  for (int f = 0; f < 6; ++f) h.needed |= c.face_bc[f] != LBM_PERIODIC;
+  if (!h.needed) return h;
+  h.tag.assign(N, TAG_BULK);
+  for (long long n = 0; n < N; ++n) {
+    if (h.has_solid && c.solid_mask[n]) { h.tag[n] = TAG_SOLID; continue; }
+    const int co[3] = {(int)(n % c.nx), (int)((n / c.nx) % c.ny), (int)(n / ((long long)c.nx * c.ny))};
+    int nk = 0, ax = 0, sg = 0, tms_face = -1;
+    unsigned inc = 0;
+    for (int i = 0; i < Q; ++i) {
+      int lk = 0, src[3] = {co[0], co[1], co[2]};
+      for (int a = 0; a < D; ++a) {
+        int sa = co[a] - cvel_host(i, a);
+        int face = -1;
+        if (sa < 0) { face = 2 * a; sa += ext[a]; }
+        else if (sa >= ext[a]) { face = 2 * a + 1; sa -= ext[a]; }
+        src[a] = sa;
+        if (face < 0) continue;
+        const int fk = c.face_bc[face];
+        if (fk == LBM_PERIODIC) continue;
+        if (precedence(fk) > precedence(lk)) lk = fk;
+        if (fk == LBM_OUTLET) { ax = a; sg = (face & 1) ? 1 : -1; }
+        if (fk == LBM_TMS_WALL && tms_face < 0) tms_face = face;
+      }
+      if (lk == 0 && h.has_solid &&
+          c.solid_mask[src[0] + (long long)c.nx * (src[1] + (long long)c.ny * src[2])])
+        lk = c.solid_bc;
+      if (lk) {
+        inc |= 1u << i;
+        if (precedence(lk) > precedence(nk)) nk = lk;
+      }
+    }
+    if (!nk) continue;
+    h.tag[n] = h.n_if++;
+    h.if_node.push_back((int)n);
+    h.if_info.push_back(nk | (ax << 4) | ((sg > 0) << 6));
+    h.if_inc.push_back(inc);
+    h.wallT.push_back(c.wall_T_nodes ? c.wall_T_nodes[n] : (tms_face >= 0 ? c.wall_T[tms_face] : 0.0));
+  }
+  h.uin.assign(3 * (size_t)h.n_if, 0.0);
+  for (int k = 0; k < h.n_if; ++k)
+    for (int d = 0; d < 3; ++d)
+      h.uin[(size_t)d * h.n_if + k] =
+          (c.inlet_u ? c.inlet_u[(long long)d * N + h.if_node[k]] : c.inlet_u_uniform[d]) / c_ref;
+  return h;
+}
+
+size_t align256(size_t b) { return (b + 255) / 256 * 256; }
+
+struct Sizes {
+  size_t pops, rec, tf, status, io, bc, total;
+};
+
+Sizes sizes_for(const lbm_config& c, const HostBC& hb) {
   const int D = lattice_dim(c.lattice);
   const int Q = D == 3 ? 27 : 9;
   const int M = c.mech.n_species;
@@ -171,7 +276,13 @@ Sizes sizes_for(const lbm_config& c) {
   s.tf = (size_t)N * sizeof(double);
   s.status = 256;
   s.io = 0;
-  s.total = 2 * s.pops + s.rec + s.tf + s.status;
+  s.bc = 0;
+  if (hb.needed) {
+    const size_t nif = (size_t)hb.n_if;
+    s.bc = align256(N * sizeof(int)) + 3 * align256(nif * sizeof(int)) +
+           4 * align256(nif * sizeof(double)) + align256((size_t)(M + 1) * Q * nif * sizeof(double));
+  }
+  s.total = 2 * s.pops + s.rec + s.tf + s.status + s.bc;
   return s;
 }
 
@@ -282,6 +393,7 @@ void lbm_config_defaults(lbm_config* cfg) {
   cfg->T_max = 3000.0;
   for (int f = 0; f < 6; ++f) cfg->face_bc[f] = LBM_PERIODIC;
   cfg->outlet_sigma = 0.25;
+  cfg->solid_bc = LBM_TMS_WALL;
   cfg->outlet_P = P_REF;
   cfg->inlet_P = P_REF;
   cfg->newton_max_iter = 50;
@@ -290,7 +402,8 @@ void lbm_config_defaults(lbm_config* cfg) {
 
 size_t lbm_bytes_required(const lbm_config* cfg) {
   if (!validate(cfg).empty()) return 0;
-  return sizes_for(*cfg).total;
+  const double c = cfg->c_ref > 0.0 ? cfg->c_ref : default_c_ref(*cfg);
+  return sizes_for(*cfg, classify(*cfg, c)).total;
 }
 
 lbm_status lbm_create(const lbm_config* cfg, lbm_t* out) {
@@ -326,13 +439,69 @@ lbm_status lbm_create(const lbm_config* cfg, lbm_t* out) {
   build_mech(cfg->mech, h->mech);
   h->elem = elem_size(cfg->precision);
   h->stream = static_cast<cudaStream_t>(cfg->stream);
-  const Sizes s = sizes_for(*cfg);
+  const HostBC hb = classify(*cfg, c);
+  const Sizes s = sizes_for(*cfg, hb);
   h->pops[0] = dalloc(h->cfg, s.pops);
   h->pops[1] = dalloc(h->cfg, s.pops);
   h->rec = static_cast<double*>(dalloc(h->cfg, s.rec));
   h->Tf = static_cast<double*>(dalloc(h->cfg, s.tf));
   h->status = static_cast<int*>(dalloc(h->cfg, s.status));
   h->bytes = s.total;
+  if (hb.needed) {
+    h->bc_mem = dalloc(h->cfg, s.bc);
+    if (!h->bc_mem) {
+      lbm_destroy(h);
+      return fail(nullptr, LBM_ERR_OOM, "device allocation failed (boundary data)");
+    }
+    char* p = static_cast<char*>(h->bc_mem);
+    const size_t nif = (size_t)hb.n_if;
+    const long long N = h->g.N;
+    BCDev& b = h->bc;
+    auto take = [&](size_t bytes) { char* q = p; p += align256(bytes); return q; };
+    int* tag = reinterpret_cast<int*>(take(N * sizeof(int)));
+    int* if_node = reinterpret_cast<int*>(take(nif * sizeof(int)));
+    int* if_info = reinterpret_cast<int*>(take(nif * sizeof(int)));
+    unsigned* if_inc = reinterpret_cast<unsigned*>(take(nif * sizeof(unsigned)));
+    double* wallT = reinterpret_cast<double*>(take(nif * sizeof(double)));
+    double* uin = reinterpret_cast<double*>(take(3 * nif * sizeof(double)));
+    b.pops = reinterpret_cast<double*>(take((size_t)h->L * h->Q * nif * sizeof(double)));
+    cudaError_t e = cudaMemcpy(tag, hb.tag.data(), N * sizeof(int), cudaMemcpyHostToDevice);
+    if (nif && e == cudaSuccess)
+      e = cudaMemcpy(if_node, hb.if_node.data(), nif * sizeof(int), cudaMemcpyHostToDevice);
+    if (nif && e == cudaSuccess)
+      e = cudaMemcpy(if_info, hb.if_info.data(), nif * sizeof(int), cudaMemcpyHostToDevice);
+    if (nif && e == cudaSuccess)
+      e = cudaMemcpy(if_inc, hb.if_inc.data(), nif * sizeof(unsigned), cudaMemcpyHostToDevice);
+    if (nif && e == cudaSuccess)
+      e = cudaMemcpy(wallT, hb.wallT.data(), nif * sizeof(double), cudaMemcpyHostToDevice);
+    if (nif && e == cudaSuccess)
+      e = cudaMemcpy(uin, hb.uin.data(), 3 * nif * sizeof(double), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+      lbm_destroy(h);
+      return fail(nullptr, LBM_ERR_CUDA, std::string("boundary upload: ") + cudaGetErrorString(e));
+    }
+    b.tag = tag;
+    b.if_node = if_node;
+    b.if_info = if_info;
+    b.if_inc = if_inc;
+    b.if_wallT = wallT;
+    b.if_uin = uin;
+    b.n_if = hb.n_if;
+    for (int f = 0; f < 6; ++f) b.face[f] = cfg->face_bc[f];
+    b.has_solid = hb.has_solid ? 1 : 0;
+    b.solid_kind = cfg->solid_bc;
+    b.sigma = cfg->outlet_sigma;
+    b.p_out_lat = cfg->outlet_P * h->un.inv_c2;
+    double Rin = 0.0;
+    for (int a = 0; a < h->M; ++a) {
+      b.Y_in[a] = cfg->inlet_Y[a];
+      Rin += cfg->inlet_Y[a] / cfg->mech.molar_mass[a];
+    }
+    Rin *= R_U;
+    b.T_in = cfg->inlet_T;
+    b.rho_in = cfg->inlet_T > 0.0 ? cfg->inlet_P / (Rin * cfg->inlet_T) : 0.0;
+    b.theta_in = Rin * cfg->inlet_T * h->un.inv_c2;
+  }
   if (!h->pops[0] || !h->pops[1] || !h->rec || !h->Tf || !h->status) {
     lbm_destroy(h);
     return fail(nullptr, LBM_ERR_OOM, "device allocation failed");
@@ -367,6 +536,7 @@ lbm_status lbm_step(lbm_t h, int nsteps) {
   a.status = h->status;
   a.g = h->g;
   a.un = h->un;
+  a.bc = h->bc;
   for (int k = 0; k < nsteps; ++k) {
     a.src = h->pops[h->cur];
     a.dst = h->pops[1 - h->cur];
@@ -393,6 +563,7 @@ lbm_status lbm_step_timed(lbm_t h, int nsteps, double* kernel_ms, int n_kernels)
   a.status = h->status;
   a.g = h->g;
   a.un = h->un;
+  a.bc = h->bc;
   cudaError_t err = cudaSuccess;
   for (int k = 0; k < nsteps && err == cudaSuccess; ++k) {
     a.src = h->pops[h->cur];
@@ -554,6 +725,7 @@ lbm_status lbm_destroy(lbm_t h) {
   dfree(h->cfg, h->Tf);
   dfree(h->cfg, h->status);
   dfree(h->cfg, h->io);
+  dfree(h->cfg, h->bc_mem);
   delete h;
   return st;
 }

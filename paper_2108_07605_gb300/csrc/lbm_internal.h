@@ -62,14 +62,38 @@ struct Geom {
 };
 
 // Kernel launchers (lbm_kernels.cu).  `S` is the storage type.
+// Boundary data of a handle (Sec. 4).  tag == nullptr: periodic box, no
+// interface or solid nodes.
+constexpr int TAG_BULK = -1;
+constexpr int TAG_SOLID = -2;
+enum { BK_NONE = 0, BK_BB = 1, BK_TMS = 2, BK_INLET = 3, BK_OUTLET = 4 };
+
+struct BCDev {
+  const int* tag = nullptr;        // [N] interface index, TAG_BULK or TAG_SOLID
+  const int* if_node = nullptr;    // [n_if] node index of each interface node
+  const int* if_info = nullptr;    // kind | outlet axis << 4 | (outlet sign > 0) << 6
+  const unsigned* if_inc = nullptr;  // incoming-link mask (bit i = link i)
+  const double* if_wallT = nullptr;  // [n_if] TMS target temperature (K)
+  const double* if_uin = nullptr;    // [3][n_if] inlet velocity, lattice units
+  double* pops = nullptr;            // [L][Q][n_if] reconstructed populations
+  int n_if = 0;
+  int face[6] = {0, 0, 0, 0, 0, 0};
+  int has_solid = 0;
+  int solid_kind = BK_TMS;
+  double rho_in = 0.0, T_in = 0.0, theta_in = 0.0;
+  double Y_in[LBM_MAX_SPECIES] = {0};
+  double p_out_lat = 0.0, sigma = 0.25;
+};
+
 struct StepArgs {
-  const void* src;
-  void* dst;
-  double* rec;           // moment records [NF][N]
-  double* Tfield;        // temperature guess [N]
-  int* status;
+  const void* src = nullptr;
+  void* dst = nullptr;
+  double* rec = nullptr;       // moment records [NF][N]
+  double* Tfield = nullptr;    // temperature guess [N]
+  int* status = nullptr;
   Geom g;
   Units un;
+  BCDev bc;                    // default: periodic box
 };
 
 // which: 0 = moments kernel only, 1 = collision kernel only, -1 = both.

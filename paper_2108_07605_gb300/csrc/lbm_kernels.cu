@@ -31,6 +31,14 @@ __device__ __forceinline__ long long node_shift(int x, int y, int z, int i, int 
   return sx + (long long)g.nx * (sy + (long long)g.ny * sz);
 }
 
+// Population (lattice l, direction i) entering node n's collision: the
+// reconstructed value for interface nodes (tag >= 0), else the streamed one.
+template <typename S>
+__device__ __forceinline__ double pop_in(const S* __restrict__ src, const BCDev& bc, int tag,
+                                         long long N, long long sn, int li) {
+  return tag >= 0 ? bc.pops[(long long)li * bc.n_if + tag] : ldp(src + (long long)li * N + sn);
+}
+
 template <typename R>
 __device__ __forceinline__ R pick3(int c, const R (&v)[3]) {
   return c == 0 ? v[1] : (c > 0 ? v[2] : v[0]);
@@ -47,12 +55,15 @@ __device__ __forceinline__ constexpr int pidx(int a, int b) {
 template <int D, int M, typename S>
 __global__ void __launch_bounds__(128)
 k_moments(const S* __restrict__ src, double* __restrict__ rec, double* __restrict__ Tf,
-          int* __restrict__ status, Geom g, Units un, const __grid_constant__ DevMech mech) {
+          int* __restrict__ status, Geom g, Units un, BCDev bc,
+          const __grid_constant__ DevMech mech) {
   constexpr int Q = Lat<D>::Q, NP = Lat<D>::NP;
   using RC = Rec<D, M>;
   const long long N = g.N;
   const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (n >= N) return;
+  const int tag = bc.tag ? bc.tag[n] : TAG_BULK;
+  if (tag == TAG_SOLID) return;
   const int x = (int)(n % g.nx);
   const int y = (int)((n / g.nx) % g.ny);
   const int z = (int)(n / ((long long)g.nx * g.ny));
@@ -73,13 +84,13 @@ k_moments(const S* __restrict__ src, double* __restrict__ rec, double* __restric
     const long long sn = node_shift<D>(x, y, z, i, -1, g);
 #pragma unroll
     for (int a = 0; a < M - 1; ++a) {
-      const double v = ldp(src + (long long)(a * Q + i) * N + sn);
+      const double v = pop_in(src, bc, tag, N, sn, a * Q + i);
       rs[a] += v;
 #pragma unroll
       for (int d = 0; d < D; ++d)
         if (cvel(i, d) != 0) js[a][d] += cvel(i, d) * v;
     }
-    const double f = ldp(src + (long long)((M - 1) * Q + i) * N + sn);
+    const double f = pop_in(src, bc, tag, N, sn, (M - 1) * Q + i);
     rho += f;
 #pragma unroll
     for (int d = 0; d < D; ++d) {
@@ -88,7 +99,7 @@ k_moments(const S* __restrict__ src, double* __restrict__ rec, double* __restric
       for (int e = d; e < D; ++e)
         if (cvel(i, d) * cvel(i, e) != 0) P[pidx<D>(d, e)] += cvel(i, d) * cvel(i, e) * f;
     }
-    const double gv = ldp(src + (long long)(M * Q + i) * N + sn);
+    const double gv = pop_in(src, bc, tag, N, sn, M * Q + i);
     rhoE += gv;
 #pragma unroll
     for (int d = 0; d < D; ++d)
@@ -152,12 +163,15 @@ k_moments(const S* __restrict__ src, double* __restrict__ rec, double* __restric
 template <int D, int M, typename S, typename RT>
 __global__ void __launch_bounds__(128)
 k_collide(const S* __restrict__ src, S* __restrict__ dst, const double* __restrict__ rec,
-          int* __restrict__ status, Geom g, Units un, const __grid_constant__ DevMech mech) {
+          int* __restrict__ status, Geom g, Units un, BCDev bc,
+          const __grid_constant__ DevMech mech) {
   constexpr int Q = Lat<D>::Q, NP = Lat<D>::NP;
   using RC = Rec<D, M>;
   const long long N = g.N;
   const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (n >= N) return;
+  const int tag = bc.tag ? bc.tag[n] : TAG_BULK;
+  if (tag == TAG_SOLID) return;
   const int x = (int)(n % g.nx);
   const int y = (int)((n / g.nx) % g.ny);
   const int z = (int)(n / ((long long)g.nx * g.ny));
@@ -190,18 +204,56 @@ k_collide(const S* __restrict__ src, S* __restrict__ dst, const double* __restri
 #pragma unroll
     for (int a = 0; a < M; ++a) gY[a][d] = 0.0;
   }
+  // ghost values beyond non-periodic faces and on solid nodes: walls Phi = 0,
+  // inlet the inlet state's Phi, outlet the node's own Phi; Y the node's own
+  double phi_self[D], phi_in[D];
+#pragma unroll
+  for (int d = 0; d < D; ++d) {
+    phi_self[d] = 0.0;
+    phi_in[d] = 0.0;
+  }
+  if (bc.tag) {
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+      phi_self[d] = rec[(RC::PHI + d) * N + n];
+      const double ui = tag >= 0 ? bc.if_uin[(long long)d * bc.n_if + tag] : 0.0;
+      phi_in[d] = bc.rho_in * ui * (1.0 - 3.0 * bc.theta_in) - bc.rho_in * ui * ui * ui;
+    }
+  }
 #pragma unroll
   for (int i = 0; i < Q; ++i) {
     if (csq(i, D) == 0) continue;
-    const long long nb = node_shift<D>(x, y, z, i, +1, g);
+    long long nb = 0;
+    int gk = BK_NONE;
+    if (!bc.tag) {
+      nb = node_shift<D>(x, y, z, i, +1, g);
+    } else {
+      int cc[3] = {x + cvel(i, 0), y + cvel(i, 1), D == 3 ? z + cvel(i, 2) : z};
+      const int ext[3] = {g.nx, g.ny, g.nz};
+#pragma unroll
+      for (int a = 0; a < D; ++a) {
+        if (cc[a] < 0) {
+          if (bc.face[2 * a]) { if (!gk) gk = bc.face[2 * a]; } else cc[a] += ext[a];
+        } else if (cc[a] >= ext[a]) {
+          if (bc.face[2 * a + 1]) { if (!gk) gk = bc.face[2 * a + 1]; } else cc[a] -= ext[a];
+        }
+      }
+      if (!gk) {
+        nb = cc[0] + (long long)g.nx * (cc[1] + (long long)g.ny * cc[2]);
+        if (bc.has_solid && bc.tag[nb] == TAG_SOLID) gk = bc.solid_kind;
+      }
+    }
     const double w3 = 3.0 * wstd(i, D);
 #pragma unroll
     for (int d = 0; d < D; ++d) {
       if (cvel(i, d) == 0) continue;
       const double wc = w3 * cvel(i, d);
-      dPhi[d] += wc * __ldg(rec + (RC::PHI + d) * N + nb);
+      const double pv = gk == BK_NONE ? __ldg(rec + (RC::PHI + d) * N + nb)
+                        : (gk == BK_INLET ? phi_in[d] : (gk == BK_OUTLET ? phi_self[d] : 0.0));
+      dPhi[d] += wc * pv;
 #pragma unroll
-      for (int a = 0; a < M; ++a) gY[a][d] += wc * __ldg(rec + (RC::Y + a) * N + nb);
+      for (int a = 0; a < M; ++a)
+        gY[a][d] += wc * (gk == BK_NONE ? __ldg(rec + (RC::Y + a) * N + nb) : Y[a]);
     }
   }
 
@@ -355,7 +407,7 @@ k_collide(const S* __restrict__ src, S* __restrict__ dst, const double* __restri
       for (int b = 0; b < M; ++b)
         if (b != a) F += RT(s_tau * mech.K[a][b]) * dd[b];
       const long long off = (long long)(a * Q + i) * N;
-      const RT f = RT(ldp(src + off + sn));
+      const RT f = RT(pop_in(src, bc, tag, N, sn, a * Q + i));
       const RT fn = f + RT(2) * beta[a] * (RT(rs[a]) * pe[a] - f) +
                     (beta[a] - RT(1)) * RT(Y[a]) * F + RT(drho[a]) * pe[a];
       dst[off + n] = S(fn);
@@ -365,7 +417,7 @@ k_collide(const S* __restrict__ src, S* __restrict__ dst, const double* __restri
 #pragma unroll
       for (int d = 0; d < D; ++d) fex *= psi1<RT>(c[d], uR[d], Pex[d]);
       const long long off = (long long)((M - 1) * Q + i) * N;
-      const RT f = RT(ldp(src + off + sn));
+      const RT f = RT(pop_in(src, bc, tag, N, sn, (M - 1) * Q + i));
       dst[off + n] = S(f + omR * (fex - f));
     }
     {
@@ -383,7 +435,7 @@ k_collide(const S* __restrict__ src, S* __restrict__ dst, const double* __restri
       }
       geq *= rhoR;
       const long long off = (long long)(M * Q + i) * N;
-      const RT gv = RT(ldp(src + off + sn));
+      const RT gv = RT(pop_in(src, bc, tag, N, sn, M * Q + i));
       RT gn = gv + omR * (geq - gv);
       if (csq(i, D) == 1) {
 #pragma unroll
@@ -393,6 +445,138 @@ k_collide(const S* __restrict__ src, S* __restrict__ dst, const double* __restri
       dst[off + n] = S(gn);
     }
   }
+}
+
+
+// ---------------------------------------------------------------------------
+// Boundary reconstruction at interface nodes (Sec. 4), one thread per
+// interface node; writes the node's full post-boundary population set to
+// bc.pops, which the moments and collision kernels read for that node.
+//   bounce-back (Eq. bb): incoming f_i = f_{-i}^post of the node itself;
+//   TMS wall (Sec. 4.2.2), flux inlet (Sec. 4.3), outlet (Sec. 4.4): put
+//   the first equilibrium A on the incoming links, take the local state
+//   `loc` of the result, then every population becomes B + f - f^loc with
+//   B = A (wall: target; outlet: outlet data) or, for the inlet, the
+//   target equilibrium at (rho^loc, Y^loc, u^in, T^in).
+template <int D, int M, typename S>
+__global__ void __launch_bounds__(64)
+k_boundary(const S* __restrict__ src, BCDev bc, const double* __restrict__ Tf,
+           int* __restrict__ status, Geom g, Units un, const __grid_constant__ DevMech mech) {
+  constexpr int Q = Lat<D>::Q, L = M + 1;
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= bc.n_if) return;
+  const long long N = g.N;
+  const long long n = bc.if_node[k];
+  const int info = bc.if_info[k];
+  const int kind = info & 15;
+  const unsigned inc = bc.if_inc[k];
+  const int x = (int)(n % g.nx);
+  const int y = (int)((n / g.nx) % g.ny);
+  const int z = (int)(n / ((long long)g.nx * g.ny));
+  const long long st = bc.n_if;
+  double* P = bc.pops + k;                       // element (l, i) at P[(l Q + i) st]
+  for (int i = 0; i < Q; ++i) {                  // pull streaming (wrapped address)
+    const long long sn = node_shift<D>(x, y, z, i, -1, g);
+    for (int l = 0; l < L; ++l) P[(long long)(l * Q + i) * st] = ldp(src + (long long)(l * Q + i) * N + sn);
+  }
+  if (kind == BK_BB) {
+    for (int i = 0; i < Q; ++i)
+      if (inc >> i & 1u)
+        for (int l = 0; l < L; ++l)
+          P[(long long)(l * Q + i) * st] = ldp(src + (long long)(l * Q + (Q - 1 - i)) * N + n);
+    return;
+  }
+  EqSet<D, M> A, B, loc;
+  A.own_species_u = B.own_species_u = false;
+  if (kind == BK_TMS) {
+    // step 1: bounce-back density and mass fractions (Eqs. BBrho, BBY)
+    double rho_bb = 0.0, rs[M];
+    for (int a = 0; a < M - 1; ++a) rs[a] = 0.0;
+    for (int i = 0; i < Q; ++i) {
+      const bool in = inc >> i & 1u;
+      for (int l = 0; l < M; ++l) {
+        const double v = in ? ldp(src + (long long)(l * Q + (Q - 1 - i)) * N + n)
+                            : P[(long long)(l * Q + i) * st];
+        if (l < M - 1) rs[l] += v; else rho_bb += v;
+      }
+    }
+    A.rho = rho_bb;
+    double ysum = 0.0;
+    for (int a = 0; a < M - 1; ++a) { A.Y[a] = rs[a] / rho_bb; ysum += A.Y[a]; }
+    A.Y[M - 1] = 1.0 - ysum;
+    for (int d = 0; d < D; ++d) A.u[d] = 0.0;      // u^tgt = u_a^tgt = 0
+    A.T = bc.if_wallT[k];
+    eq_prepare(A, mech, un);                         // step 2: target (Eqs. tgtf-tgtfa)
+  } else if (kind == BK_INLET) {
+    A.rho = bc.rho_in;
+    for (int a = 0; a < M; ++a) A.Y[a] = bc.Y_in[a];
+    for (int d = 0; d < D; ++d) A.u[d] = bc.if_uin[(long long)d * st + k];
+    A.T = bc.T_in;
+    eq_prepare(A, mech, un);                         // step 1 (Eqs. in_f-in_fa)
+  } else {
+    // LODI data from the stored state at x and x - n (Eq. convectiveBC)
+    const int ax = (info >> 4) & 3;
+    const int sg = (info >> 6) & 1 ? 1 : -1;
+    const long long stride = ax == 0 ? 1 : (ax == 1 ? (long long)g.nx : (long long)g.nx * g.ny);
+    const long long up = n - sg * stride;
+    EqSet<D, M> s0, s1;
+    state_of<D, M>([&](int l, int i) { return ldp(src + (long long)(l * Q + i) * N + n); },
+                   s0, Tf[n], mech, un, status);
+    state_of<D, M>([&](int l, int i) { return ldp(src + (long long)(l * Q + i) * N + up); },
+                   s1, Tf[up], mech, un, status);
+    double R0 = 0.0, R1 = 0.0, Cv = 0.0;
+    for (int a = 0; a < M; ++a) {
+      R0 += s0.Y[a] * mech.inv_mm[a];
+      R1 += s1.Y[a] * mech.inv_mm[a];
+      Cv += s0.Y[a] * (mech.u1[a] + s0.T * (2.0 * mech.u2[a] + 3.0 * s0.T * mech.u3[a]));
+    }
+    R0 *= R_U;
+    R1 *= R_U;
+    const double p0 = s0.rho * R0 * s0.T * un.inv_c2;
+    const double p1 = s1.rho * R1 * s1.T * un.inv_c2;
+    const double un0 = sg * s0.u[ax], un1 = sg * s1.u[ax];
+    const double gamma = (Cv + R0) / Cv;
+    const double cs = sqrt(gamma * R0 * s0.T * un.inv_c2);
+    const double Ma = un0 / cs;
+    const double Ln = ax == 0 ? g.nx : (ax == 1 ? g.ny : g.nz);
+    const double K = bc.sigma * (1.0 - Ma * Ma) * cs / Ln;
+    const double L1 = K * (p0 - bc.p_out_lat);
+    const double L2 = un0 * (cs * cs * (s0.rho - s1.rho) - (p0 - p1));
+    const double L5 = (un0 + cs) * ((p0 - p1) + s0.rho * cs * (un0 - un1));
+    A.rho = s0.rho - (L2 + 0.5 * (L5 + L1)) / (cs * cs);
+    const double p_o = p0 - 0.5 * (L5 + L1);
+    const double un_o = un0 - (L5 - L1) / (2.0 * s0.rho * cs);
+    for (int d = 0; d < D; ++d) A.u[d] = s0.u[d] - un0 * (s0.u[d] - s1.u[d]);
+    A.u[ax] = sg * un_o;
+    double Ro = 0.0;
+    for (int a = 0; a < M; ++a) {
+      A.Y[a] = s0.Y[a] - un0 * (s0.Y[a] - s1.Y[a]);
+      Ro += A.Y[a] * mech.inv_mm[a];
+    }
+    A.T = p_o * un.c * un.c / (A.rho * R_U * Ro);
+    eq_prepare(A, mech, un);                         // step 1 (Eqs. out_f-out_fa)
+  }
+  // incoming links at A, then the local state (Eqs. locRho-locT and analogues)
+  for (int i = 0; i < Q; ++i)
+    if (inc >> i & 1u)
+      for (int l = 0; l < L; ++l) P[(long long)(l * Q + i) * st] = eq_pop(A, l, i);
+  state_of<D, M>([&](int l, int i) { return P[(long long)(l * Q + i) * st]; }, loc, Tf[n],
+                 mech, un, status);
+  loc.own_species_u = kind == BK_TMS;             // TMS local species use u_a^loc
+  eq_prepare(loc, mech, un);
+  if (kind == BK_INLET) {                         // target (Eqs. in_tgt_*)
+    B.rho = loc.rho;
+    for (int a = 0; a < M; ++a) B.Y[a] = loc.Y[a];
+    for (int d = 0; d < D; ++d) B.u[d] = A.u[d];
+    B.T = bc.T_in;
+    eq_prepare(B, mech, un);
+  }
+  const EqSet<D, M>& Bref = kind == BK_INLET ? B : A;
+  for (int i = 0; i < Q; ++i)
+    for (int l = 0; l < L; ++l) {
+      double& p = P[(long long)(l * Q + i) * st];
+      p = eq_pop(Bref, l, i) + p - eq_pop(loc, l, i);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -515,13 +699,17 @@ static cudaError_t step_impl(const DevMech& mech, const StepArgs& a, cudaStream_
                              int which) {
   const int bs = 128;
   const unsigned nb = blocks_for(a.g.N, bs);
-  if (which != 1)
+  if (which != 1) {
+    if (a.bc.n_if > 0)
+      k_boundary<D, M, S><<<(a.bc.n_if + 63) / 64, 64, 0, s>>>(
+          static_cast<const S*>(a.src), a.bc, a.Tfield, a.status, a.g, a.un, mech);
     k_moments<D, M, S><<<nb, bs, 0, s>>>(static_cast<const S*>(a.src), a.rec, a.Tfield,
-                                         a.status, a.g, a.un, mech);
+                                         a.status, a.g, a.un, a.bc, mech);
+  }
   if (which != 0)
     k_collide<D, M, S, RT><<<nb, bs, 0, s>>>(static_cast<const S*>(a.src),
                                              static_cast<S*>(a.dst), a.rec, a.status, a.g,
-                                             a.un, mech);
+                                             a.un, a.bc, mech);
   return cudaGetLastError();
 }
 

@@ -61,6 +61,8 @@ class lbm_config(C.Structure):
         ("precision", C.c_int), ("substeps", C.c_int), ("dx", C.c_double),
         ("c_ref", C.c_double), ("T_max", C.c_double), ("mech", lbm_mechanism),
         ("face_bc", C.c_int * 6), ("wall_T", C.c_double * 6),
+        ("solid_mask", C.POINTER(C.c_uint8)), ("solid_bc", C.c_int),
+        ("wall_T_nodes", C.POINTER(C.c_double)),
         ("inlet_u", C.POINTER(C.c_double)), ("inlet_u_uniform", C.c_double * 3),
         ("inlet_Y", C.c_double * MAX_SPECIES), ("inlet_T", C.c_double),
         ("inlet_P", C.c_double), ("outlet_P", C.c_double), ("outlet_sigma", C.c_double),
@@ -311,8 +313,13 @@ class _TorchAllocator:
 
 def make_config(mech, lattice="D3Q27", shape=(16, 16, 16), dx=1e-3, precision="fp64",
                 substeps=2, c_ref=0.0, T_max=3000.0, faces=None, newton_max_iter=50,
-                newton_rtol=1e-13, device=0, stream=None, use_torch_allocator=True):
-    """Build an lbm_config from Python values.  Returns (cfg, keepalive)."""
+                newton_rtol=1e-13, device=0, stream=None, use_torch_allocator=True,
+                wall_T=None, solid=None, solid_kind="tms", inlet=None, outlet=None):
+    """Build an lbm_config from Python values.  Returns (cfg, keepalive).
+
+    wall_T: scalar (every TMS face) or a grid array [nz, ny, nx] (per node);
+    solid: optional grid array of solid nodes; inlet: dict(u, T, Y, P) with u
+    a 3-vector or a [3, nz, ny, nx] array (m/s); outlet: dict(P, sigma)."""
     cfg = lbm_config_defaults()
     cfg.lattice = LBM_D3Q27 if lattice == "D3Q27" else LBM_D2Q9
     cfg.nx, cfg.ny, cfg.nz = (int(v) for v in shape)
@@ -328,6 +335,36 @@ def make_config(mech, lattice="D3Q27", shape=(16, 16, 16), dx=1e-3, precision="f
     cfg.newton_rtol = float(newton_rtol)
     cfg.device = int(device)
     keep = []
+    if wall_T is not None:
+        wt = np.asarray(wall_T, dtype=np.float64)
+        if wt.ndim == 0:
+            for f in range(6):
+                cfg.wall_T[f] = float(wt)
+        else:
+            wt = np.ascontiguousarray(wt.reshape(-1))
+            keep.append(wt)
+            cfg.wall_T_nodes = wt.ctypes.data_as(C.POINTER(C.c_double))
+    if solid is not None:
+        sm = np.ascontiguousarray(np.asarray(solid, dtype=np.uint8).reshape(-1))
+        keep.append(sm)
+        cfg.solid_mask = sm.ctypes.data_as(C.POINTER(C.c_uint8))
+        cfg.solid_bc = FACE_KINDS[solid_kind] if isinstance(solid_kind, str) else int(solid_kind)
+    if inlet is not None:
+        u = np.asarray(inlet["u"], dtype=np.float64)
+        if u.ndim == 1:
+            for d in range(3):
+                cfg.inlet_u_uniform[d] = float(u[d])
+        else:
+            uu = np.ascontiguousarray(u.reshape(-1))
+            keep.append(uu)
+            cfg.inlet_u = uu.ctypes.data_as(C.POINTER(C.c_double))
+        cfg.inlet_T = float(inlet["T"])
+        cfg.inlet_P = float(inlet.get("P", 101325.0))
+        for a, y in enumerate(np.asarray(inlet["Y"], dtype=np.float64)):
+            cfg.inlet_Y[a] = float(y)
+    if outlet is not None:
+        cfg.outlet_P = float(outlet.get("P", 101325.0))
+        cfg.outlet_sigma = float(outlet.get("sigma", 0.25))
     if stream is None:
         try:
             import torch

@@ -52,10 +52,12 @@ def test_struct_layout_matches_c(lbm, tmp_path):
 #include <stddef.h>
 #include "{HEADER}"
 int main(void) {{
-  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(lbm_mechanism), sizeof(lbm_config),
-         sizeof(lbm_info), offsetof(lbm_config, mech), offsetof(lbm_config, face_bc),
-         offsetof(lbm_config, inlet_u), offsetof(lbm_config, dev_alloc),
-         offsetof(lbm_config, stream), offsetof(lbm_mechanism, D0));
+  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(lbm_mechanism),
+         sizeof(lbm_config), sizeof(lbm_info), offsetof(lbm_config, mech),
+         offsetof(lbm_config, face_bc), offsetof(lbm_config, inlet_u),
+         offsetof(lbm_config, dev_alloc), offsetof(lbm_config, stream),
+         offsetof(lbm_mechanism, D0), offsetof(lbm_config, solid_mask),
+         offsetof(lbm_config, wall_T_nodes));
   return 0;
 }}
 """)
@@ -66,7 +68,8 @@ int main(void) {{
     got = [C.sizeof(lbm.lbm_mechanism), C.sizeof(lbm.lbm_config), C.sizeof(lbm.lbm_info),
            lbm.lbm_config.mech.offset, lbm.lbm_config.face_bc.offset,
            lbm.lbm_config.inlet_u.offset, lbm.lbm_config.dev_alloc.offset,
-           lbm.lbm_config.stream.offset, lbm.lbm_mechanism.D0.offset]
+           lbm.lbm_config.stream.offset, lbm.lbm_mechanism.D0.offset,
+           lbm.lbm_config.solid_mask.offset, lbm.lbm_config.wall_T_nodes.offset]
     assert got == vals
 
 
