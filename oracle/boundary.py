@@ -41,6 +41,7 @@ import numpy as np
 
 from . import thermo
 from .lattice import normalised_equilibrium, energy_equilibrium
+from .lbm import species_velocity_undefined
 
 KINDS = {"periodic": 0, "bounce_back": 1, "tms": 2, "inlet": 3, "outlet": 4}
 PRECEDENCE = {1: 3, 2: 3, 3: 2, 4: 1}        # walls > inlet > outlet
@@ -150,7 +151,8 @@ class Boundaries:
         js[M - 1] = j - js[: M - 1].sum(axis=0)
         u = j / rho
         Y = rs / rho
-        us = np.where(rs[:, None] > 1e-300, js / np.where(rs > 1e-300, rs, 1.0)[:, None], u[None])
+        bad = np.array([species_velocity_undefined(rs[a], js[a]) for a in range(M)])
+        us = np.where(bad[:, None], u[None], js / np.where(bad, 1.0, rs)[:, None])
         E = p[M].sum(axis=0) / rho
         U = (E - 0.5 * np.sum(u ** 2, axis=0)) * lbm.units.c ** 2
         T = thermo.temperature_from_energy(lbm.mech, Y, U, T_guess, lbm.newton_rtol,

@@ -36,6 +36,17 @@ from .lattice import (VelocitySet, normalised_equilibrium, product_form,
 RHO_TINY = 1e-300   # below this species density, u_a := u (reading R5)
 
 
+def species_velocity_undefined(rho_a, j_a):
+    """Reading R5 of Eq. momentum1 (u_a = j_a / rho_a): the species velocity
+    is replaced by the mixture velocity when rho_a <= 1e-300, or when some
+    component satisfies |j_a| >= rho_a.  Non-negative populations always give
+    |j_a| <= rho_a, so a species velocity at or beyond the lattice speed only
+    arises from cancellation in near-zero densities (after a boundary
+    reconstruction); there j_a / rho_a is rounding noise, and the product
+    form evaluated at it is unbounded.  rho_a: [...], j_a: [D, ...]."""
+    return (rho_a <= RHO_TINY) | np.any(np.abs(j_a) >= rho_a[None], axis=0)
+
+
 class Units:
     """Acoustic scaling: dt = dx / c."""
 
@@ -190,7 +201,7 @@ class OracleLBM:
         self.T = T
         u_s = np.empty_like(j_s)
         for a in range(M):
-            tiny = rho_s[a] <= RHO_TINY
+            tiny = species_velocity_undefined(rho_s[a], j_s[a])
             safe = np.where(tiny, 1.0, rho_s[a])
             u_s[a] = np.where(tiny[None], u, j_s[a] / safe[None])
         # 5. relaxation parameters

@@ -272,7 +272,7 @@ Sizes sizes_for(const lbm_config& c, const HostBC& hb) {
   const long long N = (long long)c.nx * c.ny * c.nz;
   Sizes s;
   s.pops = (size_t)(M + 1) * Q * N * elem_size(c.precision);
-  s.rec = (size_t)record_fields(D, M) * N * sizeof(double);
+  s.rec = (size_t)record_fields(D, M) * N * elem_size(c.precision);
   s.tf = (size_t)N * sizeof(double);
   s.status = 256;
   s.io = 0;
@@ -352,6 +352,11 @@ lbm_status init_common(lbm_ctx* h, const double* rho_or_P, int is_pressure, cons
   e = launch_init(h->D, M, h->cfg.precision, h->mech, h->g, h->un, drho, is_pressure, du, dT,
                   dY, h->pops[h->cur], h->Tf, h->status, h->stream);
   if (e != cudaSuccess) return cuda_fail(h, e, "init kernel");
+  // Both buffers start equal: the kernels never write solid nodes, which
+  // keep their initial (equilibrium) populations in either buffer.
+  e = cudaMemcpyAsync(h->pops[1 - h->cur], h->pops[h->cur],
+                      (size_t)h->L * h->Q * N * h->elem, cudaMemcpyDeviceToDevice, h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "buffer copy");
   h->initialized = true;
   h->steps = 0;
   if (!on_device) return check_status(h);
@@ -690,6 +695,9 @@ lbm_status lbm_set_state(lbm_t h, const void* buf, size_t bytes) {
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(h->Tf, p + pop_bytes, h->g.N * sizeof(double), cudaMemcpyHostToDevice,
                         h->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(h->pops[1 - h->cur], h->pops[h->cur], pop_bytes,
+                        cudaMemcpyDeviceToDevice, h->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess) return cuda_fail(h, e, "state upload");
   h->steps = (long long)hdr[7];

@@ -44,13 +44,22 @@ __device__ __forceinline__ R psi1(int c, R xi, R P) {
   return c == 0 ? (R(1) - P) : (c == 1 ? R(0.5) * (P + xi) : R(0.5) * (P - xi));
 }
 
+// Reading R5 of Eq. momentum1: u_a := u when rho_a <= 1e-300 or when some
+// |j_a| >= rho_a (impossible for non-negative populations; it arises only
+// from cancellation in near-zero densities, where j_a / rho_a is noise).
+template <int D, typename R>
+__host__ __device__ __forceinline__ bool species_velocity_undefined(double rho_a, const R* j_a) {
+  bool bad = rho_a <= RHO_TINY;
+  for (int d = 0; d < D; ++d) bad |= fabs(double(j_a[d])) >= rho_a;
+  return bad;
+}
+
 // Moment-record field offsets ([field][N] FP64 scratch written by the
 // moments kernel, read by the collision kernel).
 template <int D, int M> struct Rec {
   static constexpr int RHO = 0;
   static constexpr int U = 1;
-  static constexpr int T = U + D;
-  static constexpr int P = T + 1;
+  static constexpr int P = U + D;
   static constexpr int QF = P + Lat<D>::NP;
   static constexpr int E = QF + D;
   static constexpr int Y = E + 1;
@@ -145,14 +154,14 @@ __device__ void production_rates(const DevMech& m, double T, const double* r,
 // Gaussian elimination without pivoting for A V = B with 3 right-hand sides.
 // A is strictly row diagonally dominant (diagonal 1 + sum of |off-diagonal|),
 // so every pivot is at least 1.
-template <int M, int D>
-__device__ __forceinline__ void solve_dd(double (&A)[M][M], double (&B)[M][D]) {
+template <int M, int D, typename R>
+__device__ __forceinline__ void solve_dd(R (&A)[M][M], R (&B)[M][D]) {
 #pragma unroll
   for (int k = 0; k < M; ++k) {
-    const double inv = 1.0 / A[k][k];
+    const R inv = R(1) / A[k][k];
 #pragma unroll
     for (int r = k + 1; r < M; ++r) {
-      const double f = A[r][k] * inv;
+      const R f = A[r][k] * inv;
 #pragma unroll
       for (int c = k + 1; c < M; ++c) A[r][c] -= f * A[k][c];
 #pragma unroll
@@ -161,10 +170,10 @@ __device__ __forceinline__ void solve_dd(double (&A)[M][M], double (&B)[M][D]) {
   }
 #pragma unroll
   for (int k = M - 1; k >= 0; --k) {
-    const double inv = 1.0 / A[k][k];
+    const R inv = R(1) / A[k][k];
 #pragma unroll
     for (int d = 0; d < D; ++d) {
-      double s = B[k][d];
+      R s = B[k][d];
 #pragma unroll
       for (int c = k + 1; c < M; ++c) s -= A[k][c] * B[c][d];
       B[k][d] = s * inv;
@@ -264,7 +273,7 @@ __device__ void state_of(F fetch, EqSet<D, M>& s, double T_guess, const DevMech&
   for (int d = 0; d < D; ++d) { s.u[d] = j[d] / rho; usq += s.u[d] * s.u[d]; }
   for (int a = 0; a < M; ++a) {
     s.Y[a] = rs[a] / rho;
-    const bool tiny = rs[a] <= RHO_TINY;
+    const bool tiny = species_velocity_undefined<D>(rs[a], js[a]);
     for (int d = 0; d < D; ++d) s.us[a][d] = tiny ? s.u[d] : js[a][d] / rs[a];
   }
   const double U = (rhoE / rho - 0.5 * usq) * un.c * un.c;

@@ -52,9 +52,9 @@ __device__ __forceinline__ constexpr int pidx(int a, int b) {
 // ---------------------------------------------------------------------------
 // Moments of the post-stream state + temperature (Sec. 2.1, Sec. 3.1-3.2,
 // Sec. 3.7 slaving, Sec. 4.1 pull streaming).
-template <int D, int M, typename S>
+template <int D, int M, typename S, typename RT>
 __global__ void __launch_bounds__(128)
-k_moments(const S* __restrict__ src, double* __restrict__ rec, double* __restrict__ Tf,
+k_moments(const S* __restrict__ src, RT* __restrict__ rec, double* __restrict__ Tf,
           int* __restrict__ status, Geom g, Units un, BCDev bc,
           const __grid_constant__ DevMech mech) {
   constexpr int Q = Lat<D>::Q, NP = Lat<D>::NP;
@@ -68,29 +68,30 @@ k_moments(const S* __restrict__ src, double* __restrict__ rec, double* __restric
   const int y = (int)((n / g.nx) % g.ny);
   const int z = (int)(n / ((long long)g.nx * g.ny));
 
-  double rho = 0.0, rhoE = 0.0, j[D], q[D], P[NP], rs[M], js[M][D];
+  // sums in the lattice compute type RT
+  RT rho = RT(0), rhoE = RT(0), j[D], q[D], P[NP], rs[M], js[M][D];
 #pragma unroll
-  for (int d = 0; d < D; ++d) { j[d] = 0.0; q[d] = 0.0; }
+  for (int d = 0; d < D; ++d) { j[d] = RT(0); q[d] = RT(0); }
 #pragma unroll
-  for (int k = 0; k < NP; ++k) P[k] = 0.0;
+  for (int k = 0; k < NP; ++k) P[k] = RT(0);
 #pragma unroll
   for (int a = 0; a < M; ++a) {
-    rs[a] = 0.0;
+    rs[a] = RT(0);
 #pragma unroll
-    for (int d = 0; d < D; ++d) js[a][d] = 0.0;
+    for (int d = 0; d < D; ++d) js[a][d] = RT(0);
   }
 #pragma unroll
   for (int i = 0; i < Q; ++i) {
     const long long sn = node_shift<D>(x, y, z, i, -1, g);
 #pragma unroll
     for (int a = 0; a < M - 1; ++a) {
-      const double v = pop_in(src, bc, tag, N, sn, a * Q + i);
+      const RT v = RT(pop_in(src, bc, tag, N, sn, a * Q + i));
       rs[a] += v;
 #pragma unroll
       for (int d = 0; d < D; ++d)
         if (cvel(i, d) != 0) js[a][d] += cvel(i, d) * v;
     }
-    const double f = pop_in(src, bc, tag, N, sn, (M - 1) * Q + i);
+    const RT f = RT(pop_in(src, bc, tag, N, sn, (M - 1) * Q + i));
     rho += f;
 #pragma unroll
     for (int d = 0; d < D; ++d) {
@@ -99,7 +100,7 @@ k_moments(const S* __restrict__ src, double* __restrict__ rec, double* __restric
       for (int e = d; e < D; ++e)
         if (cvel(i, d) * cvel(i, e) != 0) P[pidx<D>(d, e)] += cvel(i, d) * cvel(i, e) * f;
     }
-    const double gv = pop_in(src, bc, tag, N, sn, M * Q + i);
+    const RT gv = RT(pop_in(src, bc, tag, N, sn, M * Q + i));
     rhoE += gv;
 #pragma unroll
     for (int d = 0; d < D; ++d)
@@ -115,18 +116,19 @@ k_moments(const S* __restrict__ src, double* __restrict__ rec, double* __restric
 #pragma unroll
     for (int d = 0; d < D; ++d) js[M - 1][d] -= js[a][d];
   }
-  const double inv_rho = 1.0 / rho;
+  const double rho_d = double(rho);
+  const double inv_rho = 1.0 / rho_d;
   double u[D], usq = 0.0, Y[M];
 #pragma unroll
-  for (int d = 0; d < D; ++d) { u[d] = j[d] * inv_rho; usq += u[d] * u[d]; }
+  for (int d = 0; d < D; ++d) { u[d] = double(j[d]) * inv_rho; usq += u[d] * u[d]; }
 #pragma unroll
-  for (int a = 0; a < M; ++a) Y[a] = rs[a] * inv_rho;
-  const double E = rhoE * inv_rho;
+  for (int a = 0; a < M; ++a) Y[a] = double(rs[a]) * inv_rho;
+  const double E = double(rhoE) * inv_rho;
   const double U = (E - 0.5 * usq) * un.c * un.c;
   bool ok;
   const double T = newton_T<M>(mech, Y, U, Tf[n], un.newton_max_iter, un.newton_rtol, ok);
   if (!ok) atomicOr(status, ST_NEWTON);
-  if (!(rho > 0.0) || !isfinite(rho) || !isfinite(T)) atomicOr(status, ST_NONFINITE);
+  if (!(rho_d > 0.0) || !isfinite(rho_d) || !isfinite(T)) atomicOr(status, ST_NONFINITE);
   Tf[n] = T;
   double Rmix = 0.0;
 #pragma unroll
@@ -137,22 +139,23 @@ k_moments(const S* __restrict__ src, double* __restrict__ rec, double* __restric
   rec[RC::RHO * N + n] = rho;
 #pragma unroll
   for (int d = 0; d < D; ++d) {
-    rec[(RC::U + d) * N + n] = u[d];
+    rec[(RC::U + d) * N + n] = RT(u[d]);
     rec[(RC::QF + d) * N + n] = q[d];
-    rec[(RC::PHI + d) * N + n] = rho * u[d] * (1.0 - 3.0 * theta) - rho * u[d] * u[d] * u[d];
+    rec[(RC::PHI + d) * N + n] =
+        RT(rho_d * u[d] * (1.0 - 3.0 * theta) - rho_d * u[d] * u[d] * u[d]);
   }
-  rec[RC::T * N + n] = T;
 #pragma unroll
   for (int k = 0; k < NP; ++k) rec[(RC::P + k) * N + n] = P[k];
-  rec[RC::E * N + n] = E;
+  rec[RC::E * N + n] = RT(E);
 #pragma unroll
   for (int a = 0; a < M; ++a) {
-    rec[(RC::Y + a) * N + n] = Y[a];
-    const bool tiny = rs[a] <= RHO_TINY;
-    const double inv = tiny ? 0.0 : 1.0 / rs[a];
+    rec[(RC::Y + a) * N + n] = RT(Y[a]);
+    const double rsa = double(rs[a]);
+    const bool tiny = species_velocity_undefined<D>(rsa, js[a]);
+    const double inv = tiny ? 0.0 : 1.0 / rsa;
 #pragma unroll
     for (int d = 0; d < D; ++d)
-      rec[(RC::US + a * D + d) * N + n] = tiny ? u[d] : js[a][d] * inv;
+      rec[(RC::US + a * D + d) * N + n] = RT(tiny ? u[d] : double(js[a][d]) * inv);
   }
 }
 
@@ -162,8 +165,8 @@ k_moments(const S* __restrict__ src, double* __restrict__ rec, double* __restric
 // gstareq1mom, qdiff, corrFourier, qex; Sec. 2.4 Eq. R3).
 template <int D, int M, typename S, typename RT>
 __global__ void __launch_bounds__(128)
-k_collide(const S* __restrict__ src, S* __restrict__ dst, const double* __restrict__ rec,
-          int* __restrict__ status, Geom g, Units un, BCDev bc,
+k_collide(const S* __restrict__ src, S* __restrict__ dst, const RT* __restrict__ rec,
+          const double* __restrict__ Tf, int* __restrict__ status, Geom g, Units un, BCDev bc,
           const __grid_constant__ DevMech mech) {
   constexpr int Q = Lat<D>::Q, NP = Lat<D>::NP;
   using RC = Rec<D, M>;
@@ -176,14 +179,17 @@ k_collide(const S* __restrict__ src, S* __restrict__ dst, const double* __restri
   const int y = (int)((n / g.nx) % g.ny);
   const int z = (int)(n / ((long long)g.nx * g.ny));
 
-  const double rho = rec[RC::RHO * N + n];
-  const double T = rec[RC::T * N + n];
-  const double E = rec[RC::E * N + n];
-  double u[D], q[D], P[NP], Y[M], V[M][D];
+  // node scalars: FP64 copies for temperature, transport and chemistry;
+  // lattice-type values (RT) for gradients, the solve and the collision
+  const double rho = double(rec[RC::RHO * N + n]);
+  const double T = Tf[n];
+  const double E = double(rec[RC::E * N + n]);
+  double u[D], Y[M];
+  RT q[D], P[NP], V[M][D];
   double usq = 0.0;
 #pragma unroll
   for (int d = 0; d < D; ++d) {
-    u[d] = rec[(RC::U + d) * N + n];
+    u[d] = double(rec[(RC::U + d) * N + n]);
     q[d] = rec[(RC::QF + d) * N + n];
     usq += u[d] * u[d];
   }
@@ -191,33 +197,33 @@ k_collide(const S* __restrict__ src, S* __restrict__ dst, const double* __restri
   for (int k = 0; k < NP; ++k) P[k] = rec[(RC::P + k) * N + n];
 #pragma unroll
   for (int a = 0; a < M; ++a) {
-    Y[a] = rec[(RC::Y + a) * N + n];
+    Y[a] = double(rec[(RC::Y + a) * N + n]);
 #pragma unroll
-    for (int d = 0; d < D; ++d) V[a][d] = rec[(RC::US + a * D + d) * N + n] - u[d];
+    for (int d = 0; d < D; ++d) V[a][d] = rec[(RC::US + a * D + d) * N + n] - RT(u[d]);
   }
 
   // isotropic gradients d_a Phi_a and grad Y_a: 3 sum_i w_i c_ia phi(x + c_i)
-  double dPhi[D], gY[M][D];
+  RT dPhi[D], gY[M][D];
 #pragma unroll
   for (int d = 0; d < D; ++d) {
-    dPhi[d] = 0.0;
+    dPhi[d] = RT(0);
 #pragma unroll
-    for (int a = 0; a < M; ++a) gY[a][d] = 0.0;
+    for (int a = 0; a < M; ++a) gY[a][d] = RT(0);
   }
   // ghost values beyond non-periodic faces and on solid nodes: walls Phi = 0,
   // inlet the inlet state's Phi, outlet the node's own Phi; Y the node's own
-  double phi_self[D], phi_in[D];
+  RT phi_self[D], phi_in[D];
 #pragma unroll
   for (int d = 0; d < D; ++d) {
-    phi_self[d] = 0.0;
-    phi_in[d] = 0.0;
+    phi_self[d] = RT(0);
+    phi_in[d] = RT(0);
   }
   if (bc.tag) {
 #pragma unroll
     for (int d = 0; d < D; ++d) {
       phi_self[d] = rec[(RC::PHI + d) * N + n];
       const double ui = tag >= 0 ? bc.if_uin[(long long)d * bc.n_if + tag] : 0.0;
-      phi_in[d] = bc.rho_in * ui * (1.0 - 3.0 * bc.theta_in) - bc.rho_in * ui * ui * ui;
+      phi_in[d] = RT(bc.rho_in * ui * (1.0 - 3.0 * bc.theta_in) - bc.rho_in * ui * ui * ui);
     }
   }
 #pragma unroll
@@ -243,17 +249,17 @@ k_collide(const S* __restrict__ src, S* __restrict__ dst, const double* __restri
         if (bc.has_solid && bc.tag[nb] == TAG_SOLID) gk = bc.solid_kind;
       }
     }
-    const double w3 = 3.0 * wstd(i, D);
+    const RT w3 = RT(3.0 * wstd(i, D));
 #pragma unroll
     for (int d = 0; d < D; ++d) {
       if (cvel(i, d) == 0) continue;
-      const double wc = w3 * cvel(i, d);
-      const double pv = gk == BK_NONE ? __ldg(rec + (RC::PHI + d) * N + nb)
-                        : (gk == BK_INLET ? phi_in[d] : (gk == BK_OUTLET ? phi_self[d] : 0.0));
+      const RT wc = w3 * RT(cvel(i, d));
+      const RT pv = gk == BK_NONE ? __ldg(rec + (RC::PHI + d) * N + nb)
+                    : (gk == BK_INLET ? phi_in[d] : (gk == BK_OUTLET ? phi_self[d] : RT(0)));
       dPhi[d] += wc * pv;
 #pragma unroll
       for (int a = 0; a < M; ++a)
-        gY[a][d] += wc * (gk == BK_NONE ? __ldg(rec + (RC::Y + a) * N + nb) : Y[a]);
+        gY[a][d] += wc * (gk == BK_NONE ? __ldg(rec + (RC::Y + a) * N + nb) : RT(Y[a]));
     }
   }
 
@@ -281,13 +287,13 @@ k_collide(const S* __restrict__ src, S* __restrict__ dst, const double* __restri
 
   // diffusion velocities, Eq. transform1: A V = u_a - u  (V holds the rhs)
   {
-    double A[M][M];
+    RT A[M][M];
 #pragma unroll
     for (int a = 0; a < M; ++a)
 #pragma unroll
       for (int b = 0; b < M; ++b)
-        A[a][b] = a == b ? 1.0 + 0.5 * inv_tau_a[a] : -0.5 * Y[b] * (s_tau * mech.K[a][b]);
-    solve_dd<M, D>(A, V);
+        A[a][b] = RT(a == b ? 1.0 + 0.5 * inv_tau_a[a] : -0.5 * Y[b] * (s_tau * mech.K[a][b]));
+    solve_dd<M, D, RT>(A, V);
   }
 
   // reaction sub-steps at frozen U (Eq. R3); T_0 is the step's T
@@ -321,33 +327,37 @@ k_collide(const S* __restrict__ src, S* __restrict__ dst, const double* __restri
 
   // energy-flux correction W = (omega - omega1)(q* - q^eq), folded form
   const double U_lat = E - 0.5 * usq;
-  double W[D];
+  RT W[D];
   {
-    double diff[D], corr[D];
+    RT diff[D], corr[D];
 #pragma unroll
-    for (int d = 0; d < D; ++d) { diff[d] = 0.0; corr[d] = 0.0; }
+    for (int d = 0; d < D; ++d) { diff[d] = RT(0); corr[d] = RT(0); }
 #pragma unroll
     for (int a = 0; a < M; ++a) {
-      const double Ha = (species_U(mech, a, T) + mech.Ra[a] * T) * un.inv_c2;
+      const RT Ha = RT((species_U(mech, a, T) + mech.Ra[a] * T) * un.inv_c2);
+      const RT HY = Ha * RT(Y[a]);
 #pragma unroll
       for (int d = 0; d < D; ++d) {
-        diff[d] += Ha * Y[a] * V[a][d];
+        diff[d] += HY * V[a][d];
         corr[d] += Ha * gY[a][d];
       }
     }
-    const double Pres = rho * theta;
+    const RT rhoR = RT(rho), thR = RT(theta), ER = RT(E);
+    const RT Pres = rhoR * thR;
 #pragma unroll
     for (int d = 0; d < D; ++d) {
-      const double q_eq = rho * u[d] * (E + theta);
-      double uP = 0.0;
+      const RT ud = RT(u[d]);
+      const RT q_eq = rhoR * ud * (ER + thR);
+      RT uP = RT(0);
 #pragma unroll
       for (int b = 0; b < D; ++b) {
-        const double Peq = rho * u[b] * u[d] + (b == d ? rho * theta : 0.0);
-        uP += u[b] * (P[pidx<D>(b, d)] - Peq);
+        const RT ub = RT(u[b]);
+        const RT Peq = rhoR * ub * ud + (b == d ? Pres : RT(0));
+        uP += ub * (P[pidx<D>(b, d)] - Peq);
       }
-      const double q_ex = -0.5 * u[d] * dPhi[d];
-      W[d] = (omega - omega1) * (q[d] - q_eq - uP + q_ex) + omega1 * rho * diff[d] +
-             0.5 * (2.0 - omega1) * Pres * corr[d];
+      const RT q_ex = RT(-0.5) * ud * dPhi[d];
+      W[d] = RT(omega - omega1) * (q[d] - q_eq - uP + q_ex) + RT(omega1) * rhoR * diff[d] +
+             RT(0.5 * (2.0 - omega1)) * Pres * corr[d];
     }
   }
 
@@ -358,12 +368,12 @@ k_collide(const S* __restrict__ src, S* __restrict__ dst, const double* __restri
     th_a[a] = RT(mech.Ra[a] * T * un.inv_c2);
     beta[a] = RT(inv_tau_a[a] / (2.0 + inv_tau_a[a]));
 #pragma unroll
-    for (int d = 0; d < D; ++d) VR[a][d] = RT(V[a][d]);
+    for (int d = 0; d < D; ++d) VR[a][d] = V[a][d];
   }
 #pragma unroll
   for (int d = 0; d < D; ++d) {
     uR[d] = RT(u[d]);
-    Pex[d] = RT(theta + u[d] * u[d] + (2.0 - omega) / (2.0 * rho * omega) * dPhi[d]);
+    Pex[d] = RT(theta + u[d] * u[d] + (2.0 - omega) / (2.0 * rho * omega) * double(dPhi[d]));
   }
   // energy equilibrium axis factors: A_c (acting on 1) and B_c (on u^2/2)
   RT Af[D][3], Bf[D][3];
@@ -440,7 +450,7 @@ k_collide(const S* __restrict__ src, S* __restrict__ dst, const double* __restri
       if (csq(i, D) == 1) {
 #pragma unroll
         for (int d = 0; d < D; ++d)
-          if (c[d] != 0) gn += RT(0.5 * c[d] * W[d]);
+          if (c[d] != 0) gn += RT(0.5 * c[d]) * W[d];
       }
       dst[off + n] = S(gn);
     }
@@ -449,22 +459,84 @@ k_collide(const S* __restrict__ src, S* __restrict__ dst, const double* __restri
 
 
 // ---------------------------------------------------------------------------
-// Boundary reconstruction at interface nodes (Sec. 4), one thread per
-// interface node; writes the node's full post-boundary population set to
-// bc.pops, which the moments and collision kernels read for that node.
+// Boundary reconstruction at interface nodes (Sec. 4).  One warp per
+// interface node: lanes stride over the node's L*Q populations, moment sums
+// are reduced with warp shuffles, and the per-node scalars (local state,
+// Newton temperature, LODI data) are evaluated redundantly by every lane.
+// Writes the node's full post-boundary population set to bc.pops, which the
+// moments and collision kernels read for that node.
 //   bounce-back (Eq. bb): incoming f_i = f_{-i}^post of the node itself;
 //   TMS wall (Sec. 4.2.2), flux inlet (Sec. 4.3), outlet (Sec. 4.4): put
 //   the first equilibrium A on the incoming links, take the local state
 //   `loc` of the result, then every population becomes B + f - f^loc with
 //   B = A (wall: target; outlet: outlet data) or, for the inlet, the
 //   target equilibrium at (rho^loc, Y^loc, u^in, T^in).
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Warp-cooperative state_of: every lane returns the same state.
+template <int D, int M, typename F>
+__device__ void warp_state_of(F fetch, EqSet<D, M>& s, double T_guess, const DevMech& m,
+                              const Units& un, int* status, int lane) {
+  constexpr int Q = Lat<D>::Q, L = M + 1;
+  double rho = 0.0, rhoE = 0.0, j[D], rs[M], js[M][D];
+  for (int d = 0; d < D; ++d) j[d] = 0.0;
+  for (int a = 0; a < M; ++a) {
+    rs[a] = 0.0;
+    for (int d = 0; d < D; ++d) js[a][d] = 0.0;
+  }
+  for (int t = lane; t < L * Q; t += 32) {
+    const int l = t / Q, i = t % Q;
+    const double v = fetch(l, i);
+    if (l < M - 1) {
+      rs[l] += v;
+      for (int d = 0; d < D; ++d) js[l][d] += cvel(i, d) * v;
+    } else if (l == M - 1) {
+      rho += v;
+      for (int d = 0; d < D; ++d) j[d] += cvel(i, d) * v;
+    } else {
+      rhoE += v;
+    }
+  }
+  rho = warp_sum(rho);
+  rhoE = warp_sum(rhoE);
+  for (int d = 0; d < D; ++d) j[d] = warp_sum(j[d]);
+  for (int a = 0; a < M - 1; ++a) {
+    rs[a] = warp_sum(rs[a]);
+    for (int d = 0; d < D; ++d) js[a][d] = warp_sum(js[a][d]);
+  }
+  rs[M - 1] = rho;
+  for (int d = 0; d < D; ++d) js[M - 1][d] = j[d];
+  for (int a = 0; a < M - 1; ++a) {
+    rs[M - 1] -= rs[a];
+    for (int d = 0; d < D; ++d) js[M - 1][d] -= js[a][d];
+  }
+  s.rho = rho;
+  double usq = 0.0;
+  for (int d = 0; d < D; ++d) { s.u[d] = j[d] / rho; usq += s.u[d] * s.u[d]; }
+  for (int a = 0; a < M; ++a) {
+    s.Y[a] = rs[a] / rho;
+    const bool tiny = species_velocity_undefined<D>(rs[a], js[a]);
+    for (int d = 0; d < D; ++d) s.us[a][d] = tiny ? s.u[d] : js[a][d] / rs[a];
+  }
+  const double U = (rhoE / rho - 0.5 * usq) * un.c * un.c;
+  bool ok;
+  s.T = newton_T<M>(m, s.Y, U, T_guess, un.newton_max_iter, un.newton_rtol, ok);
+  if (!ok && lane == 0) atomicOr(status, ST_NEWTON);
+}
+
 template <int D, int M, typename S>
-__global__ void __launch_bounds__(64)
+__global__ void __launch_bounds__(128)
 k_boundary(const S* __restrict__ src, BCDev bc, const double* __restrict__ Tf,
            int* __restrict__ status, Geom g, Units un, const __grid_constant__ DevMech mech) {
   constexpr int Q = Lat<D>::Q, L = M + 1;
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= bc.n_if) return;
+  const int k = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;   // one warp per node
+  const int lane = threadIdx.x & 31;
+  if (k >= bc.n_if) return;                                         // whole warp leaves
   const long long N = g.N;
   const long long n = bc.if_node[k];
   const int info = bc.if_info[k];
@@ -475,31 +547,29 @@ k_boundary(const S* __restrict__ src, BCDev bc, const double* __restrict__ Tf,
   const int z = (int)(n / ((long long)g.nx * g.ny));
   const long long st = bc.n_if;
   double* P = bc.pops + k;                       // element (l, i) at P[(l Q + i) st]
-  for (int i = 0; i < Q; ++i) {                  // pull streaming (wrapped address)
+  for (int t = lane; t < L * Q; t += 32) {       // pull streaming (wrapped address)
+    const int l = t / Q, i = t % Q;
     const long long sn = node_shift<D>(x, y, z, i, -1, g);
-    for (int l = 0; l < L; ++l) P[(long long)(l * Q + i) * st] = ldp(src + (long long)(l * Q + i) * N + sn);
+    P[(long long)t * st] = (inc >> i & 1u) && kind == BK_BB
+                               ? ldp(src + (long long)(l * Q + (Q - 1 - i)) * N + n)
+                               : ldp(src + (long long)t * N + sn);
   }
-  if (kind == BK_BB) {
-    for (int i = 0; i < Q; ++i)
-      if (inc >> i & 1u)
-        for (int l = 0; l < L; ++l)
-          P[(long long)(l * Q + i) * st] = ldp(src + (long long)(l * Q + (Q - 1 - i)) * N + n);
-    return;
-  }
+  if (kind == BK_BB) return;
+  __syncwarp();
   EqSet<D, M> A, B, loc;
   A.own_species_u = B.own_species_u = false;
   if (kind == BK_TMS) {
     // step 1: bounce-back density and mass fractions (Eqs. BBrho, BBY)
     double rho_bb = 0.0, rs[M];
     for (int a = 0; a < M - 1; ++a) rs[a] = 0.0;
-    for (int i = 0; i < Q; ++i) {
-      const bool in = inc >> i & 1u;
-      for (int l = 0; l < M; ++l) {
-        const double v = in ? ldp(src + (long long)(l * Q + (Q - 1 - i)) * N + n)
-                            : P[(long long)(l * Q + i) * st];
-        if (l < M - 1) rs[l] += v; else rho_bb += v;
-      }
+    for (int t = lane; t < M * Q; t += 32) {
+      const int l = t / Q, i = t % Q;
+      const double v = (inc >> i & 1u) ? ldp(src + (long long)(l * Q + (Q - 1 - i)) * N + n)
+                                       : P[(long long)t * st];
+      if (l < M - 1) rs[l] += v; else rho_bb += v;
     }
+    rho_bb = warp_sum(rho_bb);
+    for (int a = 0; a < M - 1; ++a) rs[a] = warp_sum(rs[a]);
     A.rho = rho_bb;
     double ysum = 0.0;
     for (int a = 0; a < M - 1; ++a) { A.Y[a] = rs[a] / rho_bb; ysum += A.Y[a]; }
@@ -520,10 +590,10 @@ k_boundary(const S* __restrict__ src, BCDev bc, const double* __restrict__ Tf,
     const long long stride = ax == 0 ? 1 : (ax == 1 ? (long long)g.nx : (long long)g.nx * g.ny);
     const long long up = n - sg * stride;
     EqSet<D, M> s0, s1;
-    state_of<D, M>([&](int l, int i) { return ldp(src + (long long)(l * Q + i) * N + n); },
-                   s0, Tf[n], mech, un, status);
-    state_of<D, M>([&](int l, int i) { return ldp(src + (long long)(l * Q + i) * N + up); },
-                   s1, Tf[up], mech, un, status);
+    warp_state_of<D, M>([&](int l, int i) { return ldp(src + (long long)(l * Q + i) * N + n); },
+                        s0, Tf[n], mech, un, status, lane);
+    warp_state_of<D, M>([&](int l, int i) { return ldp(src + (long long)(l * Q + i) * N + up); },
+                        s1, Tf[up], mech, un, status, lane);
     double R0 = 0.0, R1 = 0.0, Cv = 0.0;
     for (int a = 0; a < M; ++a) {
       R0 += s0.Y[a] * mech.inv_mm[a];
@@ -557,11 +627,13 @@ k_boundary(const S* __restrict__ src, BCDev bc, const double* __restrict__ Tf,
     eq_prepare(A, mech, un);                         // step 1 (Eqs. out_f-out_fa)
   }
   // incoming links at A, then the local state (Eqs. locRho-locT and analogues)
-  for (int i = 0; i < Q; ++i)
-    if (inc >> i & 1u)
-      for (int l = 0; l < L; ++l) P[(long long)(l * Q + i) * st] = eq_pop(A, l, i);
-  state_of<D, M>([&](int l, int i) { return P[(long long)(l * Q + i) * st]; }, loc, Tf[n],
-                 mech, un, status);
+  for (int t = lane; t < L * Q; t += 32) {
+    const int l = t / Q, i = t % Q;
+    if (inc >> i & 1u) P[(long long)t * st] = eq_pop(A, l, i);
+  }
+  __syncwarp();
+  warp_state_of<D, M>([&](int l, int i) { return P[(long long)(l * Q + i) * st]; }, loc,
+                      Tf[n], mech, un, status, lane);
   loc.own_species_u = kind == BK_TMS;             // TMS local species use u_a^loc
   eq_prepare(loc, mech, un);
   if (kind == BK_INLET) {                         // target (Eqs. in_tgt_*)
@@ -572,11 +644,12 @@ k_boundary(const S* __restrict__ src, BCDev bc, const double* __restrict__ Tf,
     eq_prepare(B, mech, un);
   }
   const EqSet<D, M>& Bref = kind == BK_INLET ? B : A;
-  for (int i = 0; i < Q; ++i)
-    for (int l = 0; l < L; ++l) {
-      double& p = P[(long long)(l * Q + i) * st];
-      p = eq_pop(Bref, l, i) + p - eq_pop(loc, l, i);
-    }
+  __syncwarp();
+  for (int t = lane; t < L * Q; t += 32) {
+    const int l = t / Q, i = t % Q;
+    double& p = P[(long long)t * st];
+    p = eq_pop(Bref, l, i) + p - eq_pop(loc, l, i);
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -701,15 +774,17 @@ static cudaError_t step_impl(const DevMech& mech, const StepArgs& a, cudaStream_
   const unsigned nb = blocks_for(a.g.N, bs);
   if (which != 1) {
     if (a.bc.n_if > 0)
-      k_boundary<D, M, S><<<(a.bc.n_if + 63) / 64, 64, 0, s>>>(
+      k_boundary<D, M, S><<<(a.bc.n_if + 3) / 4, 128, 0, s>>>(
           static_cast<const S*>(a.src), a.bc, a.Tfield, a.status, a.g, a.un, mech);
-    k_moments<D, M, S><<<nb, bs, 0, s>>>(static_cast<const S*>(a.src), a.rec, a.Tfield,
-                                         a.status, a.g, a.un, a.bc, mech);
+    k_moments<D, M, S, RT><<<nb, bs, 0, s>>>(static_cast<const S*>(a.src),
+                                             reinterpret_cast<RT*>(a.rec), a.Tfield,
+                                             a.status, a.g, a.un, a.bc, mech);
   }
   if (which != 0)
     k_collide<D, M, S, RT><<<nb, bs, 0, s>>>(static_cast<const S*>(a.src),
-                                             static_cast<S*>(a.dst), a.rec, a.status, a.g,
-                                             a.un, a.bc, mech);
+                                             static_cast<S*>(a.dst),
+                                             reinterpret_cast<const RT*>(a.rec), a.Tfield,
+                                             a.status, a.g, a.un, a.bc, mech);
   return cudaGetLastError();
 }
 
