@@ -234,7 +234,7 @@ lbm_status lbm_destroy(lbm_t h);
  *  error    optional; set to a message on failure (valid until the next
  *           call on the same thread).
  * The per-node scratch lives in a fixed array inside the library sized for
- * LBM_NOALLOC_MAX_NODES nodes (about 7.1 MB, held by every GPU that loads
+ * LBM_NOALLOC_MAX_NODES nodes (about 8 MB, held by every GPU that loads
  * the library until the process exits); larger grids return LBM_ERR_RANGE.
  * Every call shares that array, so calls that overlap on the GPU race.  The
  * first call on a device looks up the array's device address; make it

@@ -161,8 +161,10 @@ void build_mech(const lbm_mechanism& m, DevMech& d) {
     d.g1[a] = -0.5 * a1;
     d.g2[a] = -a2 / 6.0;
     d.a0[a] = a0;
-    for (int b = 0; b < m.n_species; ++b)
+    for (int b = 0; b < m.n_species; ++b) {
       d.K[a][b] = a == b ? 0.0 : 1.0 / (mm * m.molar_mass[b] * m.D0[a][b]);
+      d.Kf[a][b] = (float)d.K[a][b];
+    }
   }
   d.ln_p0_over_ru = std::log(P_REF / R_U);
   for (int r = 0; r < m.n_reactions; ++r) {
@@ -180,11 +182,35 @@ void build_mech(const lbm_mechanism& m, DevMech& d) {
     x.lnA = std::log(m.arrhenius[r][0]);
     x.b = m.arrhenius[r][1];
     x.EaR = m.arrhenius[r][2] / R_U;
+    x.lnA_f = ff_host(x.lnA);
+    x.b_f = ff_host(x.b);
+    x.EaR_f = ff_host(x.EaR);
+    for (int a = 0; a < m.n_species; ++a) d.eff_f[r][a] = ff_host(m.efficiency[r][a]);
   }
   d.D_T_exp = m.D_T_exponent;
   d.mu0 = m.mu0;
   d.mu_T_exp = m.mu_T_exponent;
   d.inv_prandtl = 1.0 / m.prandtl;
+  for (int a = 0; a < m.n_species; ++a) {
+    d.mm_f[a] = ff_host(d.mm[a]);
+    d.inv_mm_f[a] = ff_host(d.inv_mm[a]);
+    d.u0_f[a] = ff_host(d.u0[a]);
+    d.u1_f[a] = ff_host(d.u1[a]);
+    d.u2_f[a] = ff_host(d.u2[a]);
+    d.u3_f[a] = ff_host(d.u3[a]);
+    d.g_inv_f[a] = ff_host(d.g_inv[a]);
+    d.g0_f[a] = ff_host(d.g0[a]);
+    d.g1_f[a] = ff_host(d.g1[a]);
+    d.g2_f[a] = ff_host(d.g2[a]);
+    d.a0_f[a] = ff_host(d.a0[a]);
+    d.inv_mm_s[a] = (float)d.inv_mm[a];
+    d.Ra_s[a] = (float)d.Ra[a];
+  }
+  d.ln_p0_over_ru_f = ff_host(d.ln_p0_over_ru);
+  d.D_T_exp_s = (float)d.D_T_exp;
+  d.mu0_s = (float)d.mu0;
+  d.mu_T_exp_s = (float)d.mu_T_exp;
+  d.inv_prandtl_s = (float)d.inv_prandtl;
 }
 
 size_t elem_size(lbm_precision p) { return p == LBM_FP64 ? 8 : 4; }
@@ -366,6 +392,15 @@ lbm_status init_common(lbm_ctx* h, const double* rho_or_P, int is_pressure, cons
 }  // namespace
 
 namespace lbm {
+void fill_mixed_units(Units& un) {
+  un.c2_f = ff_host(un.c * un.c);
+  un.inv_c2_f = ff_host(un.inv_c2);
+  un.dt_sub_f = ff_host(un.dt / un.substeps);
+  un.newton_rtol_f = (float)std::max(un.newton_rtol, 4e-13);
+  un.inv_c2_s = (float)un.inv_c2;
+  un.s_pref_s = (float)un.s_pref;
+  un.nu_pref_s = (float)un.nu_pref;
+}
 // Host helpers shared with the allocation-free entry point (lbm_noalloc.cu).
 std::string validate_config(const lbm_config* c) { return validate(c); }
 void build_device_mechanism(const lbm_mechanism& m, DevMech& d) { build_mech(m, d); }
@@ -381,6 +416,7 @@ void fill_units(const lbm_config& cfg, Units& un) {
   un.substeps = cfg.substeps;
   un.newton_max_iter = cfg.newton_max_iter;
   un.newton_rtol = cfg.newton_rtol;
+  fill_mixed_units(un);
 }
 }  // namespace lbm
 
@@ -441,6 +477,7 @@ lbm_status lbm_create(const lbm_config* cfg, lbm_t* out) {
   h->un.substeps = cfg->substeps;
   h->un.newton_max_iter = cfg->newton_max_iter;
   h->un.newton_rtol = cfg->newton_rtol;
+  fill_mixed_units(h->un);
   build_mech(cfg->mech, h->mech);
   h->elem = elem_size(cfg->precision);
   h->stream = static_cast<cudaStream_t>(cfg->stream);

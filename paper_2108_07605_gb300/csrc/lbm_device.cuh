@@ -48,14 +48,15 @@ __device__ __forceinline__ R psi1(int c, R xi, R P) {
 // |j_a| >= rho_a (impossible for non-negative populations; it arises only
 // from cancellation in near-zero densities, where j_a / rho_a is noise).
 template <int D, typename R>
-__host__ __device__ __forceinline__ bool species_velocity_undefined(double rho_a, const R* j_a) {
-  bool bad = rho_a <= RHO_TINY;
-  for (int d = 0; d < D; ++d) bad |= fabs(double(j_a[d])) >= rho_a;
+__host__ __device__ __forceinline__ bool species_velocity_undefined(R rho_a, const R* j_a) {
+  bool bad = sizeof(R) == 4 ? rho_a <= R(0)              // FP32: no value below 1e-300
+                            : double(rho_a) <= RHO_TINY;
+  for (int d = 0; d < D; ++d) bad |= fabs(j_a[d]) >= rho_a;
   return bad;
 }
 
-// Moment-record field offsets ([field][N] FP64 scratch written by the
-// moments kernel, read by the collision kernel).
+// Moment-record field offsets ([field][N] scratch in the lattice compute
+// type, written by the moments kernel, read by the collision kernel).
 template <int D, int M> struct Rec {
   static constexpr int RHO = 0;
   static constexpr int U = 1;
@@ -65,7 +66,8 @@ template <int D, int M> struct Rec {
   static constexpr int Y = E + 1;
   static constexpr int US = Y + M;
   static constexpr int PHI = US + M * D;
-  static constexpr int NF = PHI + D;
+  static constexpr int DRHO = PHI + D;          // reaction increments, species a < M
+  static constexpr int NF = DRHO + M - 1;
 };
 
 // ------------------------------------------------------------------------
@@ -151,6 +153,77 @@ __device__ void production_rates(const DevMech& m, double T, const double* r,
 }
 
 // ------------------------------------------------------------------------
+// The same temperature solve and rates in float-float (mixed path).  The
+// formulas are those of newton_T and production_rates; the stopping rule
+// uses max(rtol, 4e-13), the resolution of float-float sums of the
+// formation-energy-sized terms.
+__device__ __forceinline__ ff species_U_ff(const DevMech& m, int a, ff T) {
+  return m.u0_f[a] + T * (m.u1_f[a] + T * (m.u2_f[a] + T * m.u3_f[a]));
+}
+
+template <int M>
+__device__ ff newton_T_ff(const DevMech& m, const ff* Y, ff U, ff T, int max_iter,
+                          float rtol, bool& ok) {
+  ff c0, c1, c2, c3;
+#pragma unroll
+  for (int a = 0; a < M; ++a) {
+    c0 += Y[a] * m.u0_f[a];
+    c1 += Y[a] * m.u1_f[a];
+    c2 += Y[a] * m.u2_f[a];
+    c3 += Y[a] * m.u3_f[a];
+  }
+  const ff two(2.f), three(3.f);
+  ok = false;
+  for (int it = 0; it < max_iter; ++it) {
+    const ff F = c0 + T * (c1 + T * (c2 + T * c3)) - U;
+    const ff dF = c1 + T * (two * c2 + three * T * c3);
+    const ff dT = -(F / dF);
+    T += dT;
+    if (fabsf(dT.hi) <= rtol * fabsf(T.hi)) { ok = true; break; }
+  }
+  return T;
+}
+
+template <int M>
+__device__ void production_rates_ff(const DevMech& m, ff T, const ff* r, ff* rdot) {
+  const ff lnT = ff_log(T);
+  const ff invT = ff(1.f) / T;
+  ff C[M], G[M], w[M];
+#pragma unroll
+  for (int a = 0; a < M; ++a) {
+    C[a] = r[a] * m.inv_mm_f[a];
+    G[a] = m.g_inv_f[a] * invT + m.g0_f[a] + T * (m.g1_f[a] + T * m.g2_f[a]) - m.a0_f[a] * lnT;
+    w[a] = ff();
+  }
+  const ff ln_p0_rut = m.ln_p0_over_ru_f - lnT;
+  for (int k = 0; k < m.R; ++k) {
+    const DevReaction& rx = m.rx[k];
+    const ff lnkf = rx.lnA_f + rx.b_f * lnT - rx.EaR_f * invT;
+    ff fwd = ff_exp(lnkf);
+    for (int j = 0; j < rx.nr; ++j) fwd *= C[rx.reac[j]];
+    ff rev;
+    if (rx.reversible) {
+      ff dG;
+      for (int j = 0; j < rx.np; ++j) dG += G[rx.prod[j]];
+      for (int j = 0; j < rx.nr; ++j) dG -= G[rx.reac[j]];
+      rev = ff_exp(lnkf + dG - ff((float)rx.dn) * ln_p0_rut);
+      for (int j = 0; j < rx.np; ++j) rev *= C[rx.prod[j]];
+    }
+    ff q = fwd - rev;
+    if (rx.third_body) {
+      ff cm;
+#pragma unroll
+      for (int a = 0; a < M; ++a) cm += m.eff_f[k][a] * C[a];
+      q *= cm;
+    }
+    for (int j = 0; j < rx.nr; ++j) w[rx.reac[j]] -= q;
+    for (int j = 0; j < rx.np; ++j) w[rx.prod[j]] += q;
+  }
+#pragma unroll
+  for (int a = 0; a < M; ++a) rdot[a] = w[a] * m.mm_f[a];
+}
+
+// ------------------------------------------------------------------------
 // Gaussian elimination without pivoting for A V = B with 3 right-hand sides.
 // A is strictly row diagonally dominant (diagonal 1 + sum of |off-diagonal|),
 // so every pivot is at least 1.
@@ -176,6 +249,34 @@ __device__ __forceinline__ void solve_dd(R (&A)[M][M], R (&B)[M][D]) {
       R s = B[k][d];
 #pragma unroll
       for (int c = k + 1; c < M; ++c) s -= A[k][c] * B[c][d];
+      B[k][d] = s * inv;
+    }
+  }
+}
+
+// The same elimination on a matrix stored with entry (r, c) at A[(r M + c) st].
+template <int M, int D, typename R>
+__device__ __forceinline__ void solve_dd_strided(R* A, int st, R (&B)[M][D]) {
+#pragma unroll
+  for (int k = 0; k < M; ++k) {
+    const R inv = R(1) / A[(k * M + k) * st];
+#pragma unroll
+    for (int r = k + 1; r < M; ++r) {
+      const R f = A[(r * M + k) * st] * inv;
+#pragma unroll
+      for (int c = k + 1; c < M; ++c) A[(r * M + c) * st] -= f * A[(k * M + c) * st];
+#pragma unroll
+      for (int d = 0; d < D; ++d) B[r][d] -= f * B[k][d];
+    }
+  }
+#pragma unroll
+  for (int k = M - 1; k >= 0; --k) {
+    const R inv = R(1) / A[(k * M + k) * st];
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+      R s = B[k][d];
+#pragma unroll
+      for (int c = k + 1; c < M; ++c) s -= A[(k * M + c) * st] * B[c][d];
       B[k][d] = s * inv;
     }
   }
@@ -273,7 +374,7 @@ __device__ void state_of(F fetch, EqSet<D, M>& s, double T_guess, const DevMech&
   for (int d = 0; d < D; ++d) { s.u[d] = j[d] / rho; usq += s.u[d] * s.u[d]; }
   for (int a = 0; a < M; ++a) {
     s.Y[a] = rs[a] / rho;
-    const bool tiny = species_velocity_undefined<D>(rs[a], js[a]);
+    const bool tiny = species_velocity_undefined<D, double>(rs[a], js[a]);
     for (int d = 0; d < D; ++d) s.us[a][d] = tiny ? s.u[d] : js[a][d] / rs[a];
   }
   const double U = (rhoE / rho - 0.5 * usq) * un.c * un.c;

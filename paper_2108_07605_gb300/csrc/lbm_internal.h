@@ -8,6 +8,7 @@
 #include <cuda_runtime.h>
 
 #include "../../include/lbm.h"
+#include "ff.cuh"
 
 namespace lbm {
 
@@ -27,6 +28,7 @@ struct DevReaction {
   int dn;                // sum of product minus reactant coefficients
   int reversible, third_body;
   double lnA, b, EaR;    // ln A, temperature exponent, Ea / R_U
+  ff lnA_f, b_f, EaR_f;  // the same as float-float (mixed path)
 };
 
 // Mechanism in the forms the kernels evaluate (built on the host).
@@ -44,7 +46,18 @@ struct DevMech {
   double eff[LBM_MAX_REACTIONS][LBM_MAX_SPECIES];
   // 1/tau_ab = s(node) * K[a][b], K = 1/(m_a m_b D0_ab)
   double K[LBM_MAX_SPECIES][LBM_MAX_SPECIES];
+  float Kf[LBM_MAX_SPECIES][LBM_MAX_SPECIES];   // K rounded to FP32 (mixed path)
   double D_T_exp, mu0, mu_T_exp, inv_prandtl;
+  // float-float copies for the mixed path's temperature solve and chemistry
+  ff mm_f[LBM_MAX_SPECIES], inv_mm_f[LBM_MAX_SPECIES];
+  ff u0_f[LBM_MAX_SPECIES], u1_f[LBM_MAX_SPECIES], u2_f[LBM_MAX_SPECIES], u3_f[LBM_MAX_SPECIES];
+  ff g_inv_f[LBM_MAX_SPECIES], g0_f[LBM_MAX_SPECIES], g1_f[LBM_MAX_SPECIES],
+      g2_f[LBM_MAX_SPECIES], a0_f[LBM_MAX_SPECIES];
+  ff ln_p0_over_ru_f;
+  ff eff_f[LBM_MAX_REACTIONS][LBM_MAX_SPECIES];
+  // FP32 copies for the mixed path's transport and energy-flux terms
+  float inv_mm_s[LBM_MAX_SPECIES], Ra_s[LBM_MAX_SPECIES];
+  float D_T_exp_s, mu0_s, mu_T_exp_s, inv_prandtl_s;
 };
 
 struct Units {
@@ -54,6 +67,10 @@ struct Units {
   int substeps;
   int newton_max_iter;
   double newton_rtol;
+  // mixed path: float-float and FP32 copies
+  ff c2_f, inv_c2_f, dt_sub_f;   // c^2, 1/c^2, dt / substeps
+  float newton_rtol_f;           // max(newton_rtol, 4e-13): float-float resolution
+  float inv_c2_s, s_pref_s, nu_pref_s;
 };
 
 struct Geom {
@@ -117,5 +134,6 @@ int record_fields(int D, int M);
 std::string validate_config(const lbm_config* c);   // "" when valid
 void build_device_mechanism(const lbm_mechanism& m, DevMech& d);
 void fill_units(const lbm_config& cfg, Units& un);
+void fill_mixed_units(Units& un);
 
 }  // namespace lbm

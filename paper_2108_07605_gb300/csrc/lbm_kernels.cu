@@ -33,10 +33,20 @@ __device__ __forceinline__ long long node_shift(int x, int y, int z, int i, int 
 
 // Population (lattice l, direction i) entering node n's collision: the
 // reconstructed value for interface nodes (tag >= 0), else the streamed one.
-template <typename S>
-__device__ __forceinline__ double pop_in(const S* __restrict__ src, const BCDev& bc, int tag,
-                                         long long N, long long sn, int li) {
-  return tag >= 0 ? bc.pops[(long long)li * bc.n_if + tag] : ldp(src + (long long)li * N + sn);
+template <typename RT, typename S>
+__device__ __forceinline__ RT pop_in(const S* __restrict__ src, const BCDev& bc, int tag,
+                                     long long N, long long sn, int li) {
+  return tag >= 0 ? RT(bc.pops[(long long)li * bc.n_if + tag])
+                  : RT(__ldg(src + (long long)li * N + sn));
+}
+
+// 1/tau_ab = s * K_ab: the coefficient table in the lattice compute type
+template <typename RT> __device__ __forceinline__ RT kcoef(const DevMech& m, int a, int b);
+template <> __device__ __forceinline__ double kcoef<double>(const DevMech& m, int a, int b) {
+  return m.K[a][b];
+}
+template <> __device__ __forceinline__ float kcoef<float>(const DevMech& m, int a, int b) {
+  return m.Kf[a][b];
 }
 
 template <typename R>
@@ -85,13 +95,13 @@ k_moments(const S* __restrict__ src, RT* __restrict__ rec, double* __restrict__ 
     const long long sn = node_shift<D>(x, y, z, i, -1, g);
 #pragma unroll
     for (int a = 0; a < M - 1; ++a) {
-      const RT v = RT(pop_in(src, bc, tag, N, sn, a * Q + i));
+      const RT v = pop_in<RT>(src, bc, tag, N, sn, a * Q + i);
       rs[a] += v;
 #pragma unroll
       for (int d = 0; d < D; ++d)
         if (cvel(i, d) != 0) js[a][d] += cvel(i, d) * v;
     }
-    const RT f = RT(pop_in(src, bc, tag, N, sn, (M - 1) * Q + i));
+    const RT f = pop_in<RT>(src, bc, tag, N, sn, (M - 1) * Q + i);
     rho += f;
 #pragma unroll
     for (int d = 0; d < D; ++d) {
@@ -100,7 +110,7 @@ k_moments(const S* __restrict__ src, RT* __restrict__ rec, double* __restrict__ 
       for (int e = d; e < D; ++e)
         if (cvel(i, d) * cvel(i, e) != 0) P[pidx<D>(d, e)] += cvel(i, d) * cvel(i, e) * f;
     }
-    const RT gv = RT(pop_in(src, bc, tag, N, sn, M * Q + i));
+    const RT gv = pop_in<RT>(src, bc, tag, N, sn, M * Q + i);
     rhoE += gv;
 #pragma unroll
     for (int d = 0; d < D; ++d)
@@ -116,48 +126,145 @@ k_moments(const S* __restrict__ src, RT* __restrict__ rec, double* __restrict__ 
 #pragma unroll
     for (int d = 0; d < D; ++d) js[M - 1][d] -= js[a][d];
   }
-  const double rho_d = double(rho);
-  const double inv_rho = 1.0 / rho_d;
-  double u[D], usq = 0.0, Y[M];
+  // node fields in the lattice type; FP64 only for the temperature solve
+  const RT inv_rho = RT(1) / rho;
+  RT uR[D], YR[M], usqR = RT(0);
 #pragma unroll
-  for (int d = 0; d < D; ++d) { u[d] = double(j[d]) * inv_rho; usq += u[d] * u[d]; }
+  for (int d = 0; d < D; ++d) { uR[d] = j[d] * inv_rho; usqR += uR[d] * uR[d]; }
 #pragma unroll
-  for (int a = 0; a < M; ++a) Y[a] = double(rs[a]) * inv_rho;
-  const double E = double(rhoE) * inv_rho;
-  const double U = (E - 0.5 * usq) * un.c * un.c;
+  for (int a = 0; a < M; ++a) YR[a] = rs[a] * inv_rho;
+  const RT ER = rhoE * inv_rho;
   bool ok;
-  const double T = newton_T<M>(mech, Y, U, Tf[n], un.newton_max_iter, un.newton_rtol, ok);
-  if (!ok) atomicOr(status, ST_NEWTON);
-  if (!(rho_d > 0.0) || !isfinite(rho_d) || !isfinite(T)) atomicOr(status, ST_NONFINITE);
-  Tf[n] = T;
-  double Rmix = 0.0;
+  double T;
+  RT thR;
+  if constexpr (sizeof(RT) == 4) {
+    // mixed path: the temperature solve in float-float
+    ff Yf[M];
+    float Rm = 0.f;
 #pragma unroll
-  for (int a = 0; a < M; ++a) Rmix += Y[a] * mech.inv_mm[a];
-  Rmix *= R_U;
-  const double theta = Rmix * T * un.inv_c2;
+    for (int a = 0; a < M; ++a) {
+      Yf[a] = ff(YR[a]);
+      Rm += YR[a] * mech.inv_mm_s[a];
+    }
+    const ff U = (ff(ER) + ff(-0.5f * usqR)) * un.c2_f;
+    const ff Tx = newton_T_ff<M>(mech, Yf, U, ff_from_double(Tf[n]), un.newton_max_iter,
+                                 un.newton_rtol_f, ok);
+    T = ff_to_double(Tx);
+    thR = Rm * float(R_U) * Tx.hi * un.inv_c2_s;
+  } else {
+    double Y[M];
+#pragma unroll
+    for (int a = 0; a < M; ++a) Y[a] = double(YR[a]);
+    const double U = (double(ER) - 0.5 * double(usqR)) * un.c * un.c;
+    T = newton_T<M>(mech, Y, U, Tf[n], un.newton_max_iter, un.newton_rtol, ok);
+    double Rmix = 0.0;
+#pragma unroll
+    for (int a = 0; a < M; ++a) Rmix += Y[a] * mech.inv_mm[a];
+    Rmix *= R_U;
+    thR = RT(Rmix * T * un.inv_c2);
+  }
+  if (!ok) atomicOr(status, ST_NEWTON);
+  if (!(rho > RT(0)) || !isfinite(double(rho)) || !isfinite(T)) atomicOr(status, ST_NONFINITE);
+  Tf[n] = T;
+
+  // reaction sub-steps at frozen U (Sec. 2.4 Eq. R3): a zero-dimensional
+  // reactor per node from its post-stream species densities; T_0 is the T
+  // just solved.  The increments drho_a (a < M) go to the record.
+  if constexpr (sizeof(RT) == 4) {
+    const ff Uphys = (ff(ER) + ff(-0.5f * usqR)) * un.c2_f;
+    ff r[M], rdot[M];
+#pragma unroll
+    for (int a = 0; a < M; ++a) r[a] = ff(rs[a]);
+    ff Ts = ff_from_double(T);
+    const ff rho_f(rho);
+    for (int s = 0; s < un.substeps; ++s) {
+      if (s > 0) {
+        ff Ys[M];
+#pragma unroll
+        for (int a = 0; a < M; ++a) Ys[a] = r[a] / rho_f;
+        bool oks;
+        Ts = newton_T_ff<M>(mech, Ys, Uphys, Ts, un.newton_max_iter, un.newton_rtol_f, oks);
+        if (!oks) atomicOr(status, ST_NEWTON);
+      }
+      production_rates_ff<M>(mech, Ts, r, rdot);
+#pragma unroll
+      for (int a = 0; a < M; ++a) r[a] += un.dt_sub_f * rdot[a];
+    }
+#pragma unroll
+    for (int a = 0; a < M - 1; ++a) rec[(RC::DRHO + a) * N + n] = (r[a] - ff(rs[a])).hi;
+  } else {
+    const double Uphys = (double(ER) - 0.5 * double(usqR)) * un.c * un.c;
+    const double dtr = un.dt / un.substeps;
+    const double rho_d = double(rho);
+    double r[M], rdot[M];
+#pragma unroll
+    for (int a = 0; a < M; ++a) r[a] = double(rs[a]);
+    double Ts = T;
+    for (int s = 0; s < un.substeps; ++s) {
+      if (s > 0) {
+        double Ys[M];
+        const double ir = 1.0 / rho_d;
+#pragma unroll
+        for (int a = 0; a < M; ++a) Ys[a] = r[a] * ir;
+        bool oks;
+        Ts = newton_T<M>(mech, Ys, Uphys, Ts, un.newton_max_iter, un.newton_rtol, oks);
+        if (!oks) atomicOr(status, ST_NEWTON);
+      }
+      production_rates<M>(mech, Ts, r, rdot);
+#pragma unroll
+      for (int a = 0; a < M; ++a) r[a] += dtr * rdot[a];
+    }
+#pragma unroll
+    for (int a = 0; a < M - 1; ++a) rec[(RC::DRHO + a) * N + n] = RT(r[a] - double(rs[a]));
+  }
 
   rec[RC::RHO * N + n] = rho;
 #pragma unroll
   for (int d = 0; d < D; ++d) {
-    rec[(RC::U + d) * N + n] = RT(u[d]);
+    rec[(RC::U + d) * N + n] = uR[d];
     rec[(RC::QF + d) * N + n] = q[d];
-    rec[(RC::PHI + d) * N + n] =
-        RT(rho_d * u[d] * (1.0 - 3.0 * theta) - rho_d * u[d] * u[d] * u[d]);
+    rec[(RC::PHI + d) * N + n] = rho * uR[d] * (RT(1) - RT(3) * thR) - rho * uR[d] * uR[d] * uR[d];
   }
 #pragma unroll
   for (int k = 0; k < NP; ++k) rec[(RC::P + k) * N + n] = P[k];
-  rec[RC::E * N + n] = RT(E);
+  rec[RC::E * N + n] = ER;
 #pragma unroll
   for (int a = 0; a < M; ++a) {
-    rec[(RC::Y + a) * N + n] = RT(Y[a]);
-    const double rsa = double(rs[a]);
-    const bool tiny = species_velocity_undefined<D>(rsa, js[a]);
-    const double inv = tiny ? 0.0 : 1.0 / rsa;
+    rec[(RC::Y + a) * N + n] = YR[a];
+    // where defined, |j_a| < rho_a, so the quotient lies in (-1, 1) even when
+    // rho_a is denormal in FP32 (its reciprocal would overflow)
+    const bool tiny = species_velocity_undefined<D, RT>(rs[a], js[a]);
 #pragma unroll
     for (int d = 0; d < D; ++d)
-      rec[(RC::US + a * D + d) * N + n] = RT(tiny ? u[d] : double(js[a][d]) * inv);
+      rec[(RC::US + a * D + d) * N + n] = tiny ? uR[d] : js[a][d] / rs[a];
   }
 }
+
+// Transport and lattice constants in the parameter type: FP64 for the FP64
+// path, FP32 for the mixed path.
+template <typename PT> struct MixParams;
+template <> struct MixParams<double> {
+  __device__ static double inv_mm(const DevMech& m, int a) { return m.inv_mm[a]; }
+  __device__ static double Ra(const DevMech& m, int a) { return m.Ra[a]; }
+  __device__ static double D_T_exp(const DevMech& m) { return m.D_T_exp; }
+  __device__ static double mu0(const DevMech& m) { return m.mu0; }
+  __device__ static double mu_T_exp(const DevMech& m) { return m.mu_T_exp; }
+  __device__ static double inv_prandtl(const DevMech& m) { return m.inv_prandtl; }
+  __device__ static double inv_c2(const Units& u) { return u.inv_c2; }
+  __device__ static double s_pref(const Units& u) { return u.s_pref; }
+  __device__ static double nu_pref(const Units& u) { return u.nu_pref; }
+};
+template <> struct MixParams<float> {
+  __device__ static float inv_mm(const DevMech& m, int a) { return m.inv_mm_s[a]; }
+  __device__ static float Ra(const DevMech& m, int a) { return m.Ra_s[a]; }
+  __device__ static float D_T_exp(const DevMech& m) { return m.D_T_exp_s; }
+  __device__ static float mu0(const DevMech& m) { return m.mu0_s; }
+  __device__ static float mu_T_exp(const DevMech& m) { return m.mu_T_exp_s; }
+  __device__ static float inv_prandtl(const DevMech& m) { return m.inv_prandtl_s; }
+  __device__ static float inv_c2(const Units& u) { return u.inv_c2_s; }
+  __device__ static float s_pref(const Units& u) { return u.s_pref_s; }
+  __device__ static float nu_pref(const Units& u) { return u.nu_pref_s; }
+};
 
 // ---------------------------------------------------------------------------
 // Collision of all lattices (Sec. 2.3 Eq. finalNumericalEquationsReactive;
@@ -179,17 +286,21 @@ k_collide(const S* __restrict__ src, S* __restrict__ dst, const RT* __restrict__
   const int y = (int)((n / g.nx) % g.ny);
   const int z = (int)(n / ((long long)g.nx * g.ny));
 
-  // node scalars: FP64 copies for temperature, transport and chemistry;
+  // node scalars in the parameter type PT (FP64 in the FP64 path, FP32 in
+  // the mixed path, whose temperature and chemistry run in float-float);
   // lattice-type values (RT) for gradients, the solve and the collision
-  const double rho = double(rec[RC::RHO * N + n]);
-  const double T = Tf[n];
-  const double E = double(rec[RC::E * N + n]);
-  double u[D], Y[M];
+  using PT = RT;
+  using MP = MixParams<PT>;
+  const PT rho = PT(rec[RC::RHO * N + n]);
+  const double T_d = Tf[n];
+  const PT T = PT(T_d);
+  const PT E = PT(rec[RC::E * N + n]);
+  PT u[D], Y[M];
   RT q[D], P[NP], V[M][D];
-  double usq = 0.0;
+  PT usq = PT(0);
 #pragma unroll
   for (int d = 0; d < D; ++d) {
-    u[d] = double(rec[(RC::U + d) * N + n]);
+    u[d] = PT(rec[(RC::U + d) * N + n]);
     q[d] = rec[(RC::QF + d) * N + n];
     usq += u[d] * u[d];
   }
@@ -197,7 +308,7 @@ k_collide(const S* __restrict__ src, S* __restrict__ dst, const RT* __restrict__
   for (int k = 0; k < NP; ++k) P[k] = rec[(RC::P + k) * N + n];
 #pragma unroll
   for (int a = 0; a < M; ++a) {
-    Y[a] = double(rec[(RC::Y + a) * N + n]);
+    Y[a] = PT(rec[(RC::Y + a) * N + n]);
 #pragma unroll
     for (int d = 0; d < D; ++d) V[a][d] = rec[(RC::US + a * D + d) * N + n] - RT(u[d]);
   }
@@ -264,66 +375,48 @@ k_collide(const S* __restrict__ src, S* __restrict__ dst, const RT* __restrict__
   }
 
   // relaxation parameters (Sec. 2.3 Eqs. betaa, taua; Sec. 3.5 Eqs. mu, lambda)
-  double Rmix = 0.0;
+  PT Rmix = PT(0);
 #pragma unroll
-  for (int a = 0; a < M; ++a) Rmix += Y[a] * mech.inv_mm[a];
-  Rmix *= R_U;
-  const double theta = Rmix * T * un.inv_c2;
-  const double lnTr = log(T * (1.0 / T_REF));
-  const double s_tau = un.s_pref * rho * T * T * exp(-mech.D_T_exp * lnTr);
-  const double mu = mech.mu0 * exp(mech.mu_T_exp * lnTr);
-  const double nu = mu / rho * un.nu_pref;
-  const double omega = 1.0 / (nu / theta + 0.5);
-  const double omega1 = 1.0 / (nu * mech.inv_prandtl / theta + 0.5);
-  double inv_tau_a[M];
+  for (int a = 0; a < M; ++a) Rmix += Y[a] * MP::inv_mm(mech, a);
+  Rmix *= PT(R_U);
+  const PT theta = Rmix * T * MP::inv_c2(un);
+  const PT lnTr = log(T * PT(1.0 / T_REF));
+  const PT s_tau = MP::s_pref(un) * rho * T * T * exp(-MP::D_T_exp(mech) * lnTr);
+  const PT mu = MP::mu0(mech) * exp(MP::mu_T_exp(mech) * lnTr);
+  const PT nu = mu / rho * MP::nu_pref(un);
+  const PT omega = PT(1) / (nu / theta + PT(0.5));
+  const PT omega1 = PT(1) / (nu * MP::inv_prandtl(mech) / theta + PT(0.5));
+  PT inv_tau_a[M];
 #pragma unroll
   for (int a = 0; a < M; ++a) {
-    double acc = 0.0;
+    PT acc = PT(0);
 #pragma unroll
     for (int b = 0; b < M; ++b)
-      if (b != a) acc += Y[b] * (s_tau * mech.K[a][b]);
+      if (b != a) acc += Y[b] * (s_tau * kcoef<PT>(mech, a, b));
     inv_tau_a[a] = acc;
   }
 
-  // diffusion velocities, Eq. transform1: A V = u_a - u  (V holds the rhs)
+  // diffusion velocities, Eq. transform1: A V = u_a - u  (V holds the rhs).
+  // Each thread's matrix lives in shared memory, entry-major with the block's
+  // threads contiguous (no bank conflicts): in registers it would not fit
+  // beside the node's other state and spills to local memory.
   {
-    RT A[M][M];
+    extern __shared__ unsigned char smem_raw[];
+    RT* As = reinterpret_cast<RT*>(smem_raw) + threadIdx.x;
+    const int st = blockDim.x;
 #pragma unroll
     for (int a = 0; a < M; ++a)
 #pragma unroll
       for (int b = 0; b < M; ++b)
-        A[a][b] = RT(a == b ? 1.0 + 0.5 * inv_tau_a[a] : -0.5 * Y[b] * (s_tau * mech.K[a][b]));
-    solve_dd<M, D, RT>(A, V);
+        As[(a * M + b) * st] = RT(a == b ? PT(1) + PT(0.5) * inv_tau_a[a]
+                                         : PT(-0.5) * Y[b] * (s_tau * kcoef<PT>(mech, a, b)));
+    solve_dd_strided<M, D, RT>(As, st, V);
   }
 
-  // reaction sub-steps at frozen U (Eq. R3); T_0 is the step's T
-  double rs[M], drho[M];
+  // species densities; the reaction increments come from the moments kernel
+  PT rs[M];
 #pragma unroll
   for (int a = 0; a < M; ++a) rs[a] = rho * Y[a];
-  {
-    const double Uphys = (E - 0.5 * usq) * un.c * un.c;
-    const double dtr = un.dt / un.substeps;
-    double r[M], rdot[M];
-#pragma unroll
-    for (int a = 0; a < M; ++a) r[a] = rs[a];
-    double Ts = T;
-    for (int s = 0; s < un.substeps; ++s) {
-      if (s > 0) {
-        double Ys[M];
-        const double ir = 1.0 / rho;
-#pragma unroll
-        for (int a = 0; a < M; ++a) Ys[a] = r[a] * ir;
-        bool ok;
-        Ts = newton_T<M>(mech, Ys, Uphys, Ts, un.newton_max_iter, un.newton_rtol, ok);
-        if (!ok) atomicOr(status, ST_NEWTON);
-      }
-      production_rates<M>(mech, Ts, r, rdot);
-#pragma unroll
-      for (int a = 0; a < M; ++a) r[a] += dtr * rdot[a];
-    }
-#pragma unroll
-    for (int a = 0; a < M; ++a) drho[a] = r[a] - rs[a];
-  }
 
   // energy-flux correction W = (omega - omega1)(q* - q^eq), folded form
   const double U_lat = E - 0.5 * usq;
@@ -334,7 +427,13 @@ k_collide(const S* __restrict__ src, S* __restrict__ dst, const RT* __restrict__
     for (int d = 0; d < D; ++d) { diff[d] = RT(0); corr[d] = RT(0); }
 #pragma unroll
     for (int a = 0; a < M; ++a) {
-      const RT Ha = RT((species_U(mech, a, T) + mech.Ra[a] * T) * un.inv_c2);
+      RT Ha;
+      if constexpr (sizeof(RT) == 4) {
+        const ff Tf_(T);
+        Ha = ((species_U_ff(mech, a, Tf_) + ff(mech.Ra_s[a]) * Tf_) * un.inv_c2_f).hi;
+      } else {
+        Ha = RT((species_U(mech, a, T_d) + mech.Ra[a] * T_d) * un.inv_c2);
+      }
       const RT HY = Ha * RT(Y[a]);
 #pragma unroll
       for (int d = 0; d < D; ++d) {
@@ -365,7 +464,7 @@ k_collide(const S* __restrict__ src, S* __restrict__ dst, const RT* __restrict__
   RT th_a[M], beta[M], Pex[D], uR[D], VR[M][D];
 #pragma unroll
   for (int a = 0; a < M; ++a) {
-    th_a[a] = RT(mech.Ra[a] * T * un.inv_c2);
+    th_a[a] = RT(MP::Ra(mech, a) * T * MP::inv_c2(un));
     beta[a] = RT(inv_tau_a[a] / (2.0 + inv_tau_a[a]));
 #pragma unroll
     for (int d = 0; d < D; ++d) VR[a][d] = V[a][d];
@@ -373,7 +472,7 @@ k_collide(const S* __restrict__ src, S* __restrict__ dst, const RT* __restrict__
 #pragma unroll
   for (int d = 0; d < D; ++d) {
     uR[d] = RT(u[d]);
-    Pex[d] = RT(theta + u[d] * u[d] + (2.0 - omega) / (2.0 * rho * omega) * double(dPhi[d]));
+    Pex[d] = RT(theta + u[d] * u[d] + (PT(2) - omega) / (PT(2) * rho * omega) * PT(dPhi[d]));
   }
   // energy equilibrium axis factors: A_c (acting on 1) and B_c (on u^2/2)
   RT Af[D][3], Bf[D][3];
@@ -391,6 +490,18 @@ k_collide(const S* __restrict__ src, S* __restrict__ dst, const RT* __restrict__
     Bf[d][2] = RT(0.5 * (O2 + O1));
   }
   const RT rhoR = RT(rho), omR = RT(omega), UR = RT(U_lat);
+  // species coefficients of the update, hoisted out of the direction loop:
+  // f_a += 2 beta_a (rho_a psi_a - f_a) + cF_a sum_b K_ab d_b + drho_a psi_a
+  // with cF_a = (beta_a - 1) Y_a s (1/tau_ab = s K_ab)
+  RT rsR[M], cF[M - 1], drR[M - 1], two_beta[M - 1];
+#pragma unroll
+  for (int b = 0; b < M; ++b) rsR[b] = RT(rs[b]);
+#pragma unroll
+  for (int a = 0; a < M - 1; ++a) {
+    cF[a] = RT((inv_tau_a[a] / (PT(2) + inv_tau_a[a]) - PT(1)) * Y[a] * s_tau);
+    drR[a] = rec[(RC::DRHO + a) * N + n];
+    two_beta[a] = RT(2) * beta[a];
+  }
 
 #pragma unroll 1
   for (int i = 0; i < Q; ++i) {
@@ -408,18 +519,17 @@ k_collide(const S* __restrict__ src, S* __restrict__ dst, const RT* __restrict__
         st *= psi1<RT>(c[d], xs, th_a[b] + xs * xs);
       }
       pe[b] = e;
-      dd[b] = RT(rs[b]) * (e - st);
+      dd[b] = rsR[b] * (e - st);
     }
 #pragma unroll
     for (int a = 0; a < M - 1; ++a) {
       RT F = RT(0);
 #pragma unroll
       for (int b = 0; b < M; ++b)
-        if (b != a) F += RT(s_tau * mech.K[a][b]) * dd[b];
+        if (b != a) F += kcoef<RT>(mech, a, b) * dd[b];
       const long long off = (long long)(a * Q + i) * N;
-      const RT f = RT(pop_in(src, bc, tag, N, sn, a * Q + i));
-      const RT fn = f + RT(2) * beta[a] * (RT(rs[a]) * pe[a] - f) +
-                    (beta[a] - RT(1)) * RT(Y[a]) * F + RT(drho[a]) * pe[a];
+      const RT f = pop_in<RT>(src, bc, tag, N, sn, a * Q + i);
+      const RT fn = f + two_beta[a] * (rsR[a] * pe[a] - f) + cF[a] * F + drR[a] * pe[a];
       dst[off + n] = S(fn);
     }
     {
@@ -427,7 +537,7 @@ k_collide(const S* __restrict__ src, S* __restrict__ dst, const RT* __restrict__
 #pragma unroll
       for (int d = 0; d < D; ++d) fex *= psi1<RT>(c[d], uR[d], Pex[d]);
       const long long off = (long long)((M - 1) * Q + i) * N;
-      const RT f = RT(pop_in(src, bc, tag, N, sn, (M - 1) * Q + i));
+      const RT f = pop_in<RT>(src, bc, tag, N, sn, (M - 1) * Q + i);
       dst[off + n] = S(f + omR * (fex - f));
     }
     {
@@ -445,7 +555,7 @@ k_collide(const S* __restrict__ src, S* __restrict__ dst, const RT* __restrict__
       }
       geq *= rhoR;
       const long long off = (long long)(M * Q + i) * N;
-      const RT gv = RT(pop_in(src, bc, tag, N, sn, M * Q + i));
+      const RT gv = pop_in<RT>(src, bc, tag, N, sn, M * Q + i);
       RT gn = gv + omR * (geq - gv);
       if (csq(i, D) == 1) {
 #pragma unroll
@@ -520,7 +630,7 @@ __device__ void warp_state_of(F fetch, EqSet<D, M>& s, double T_guess, const Dev
   for (int d = 0; d < D; ++d) { s.u[d] = j[d] / rho; usq += s.u[d] * s.u[d]; }
   for (int a = 0; a < M; ++a) {
     s.Y[a] = rs[a] / rho;
-    const bool tiny = species_velocity_undefined<D>(rs[a], js[a]);
+    const bool tiny = species_velocity_undefined<D, double>(rs[a], js[a]);
     for (int d = 0; d < D; ++d) s.us[a][d] = tiny ? s.u[d] : js[a][d] / rs[a];
   }
   const double U = (rhoE / rho - 0.5 * usq) * un.c * un.c;
@@ -780,11 +890,19 @@ static cudaError_t step_impl(const DevMech& mech, const StepArgs& a, cudaStream_
                                              reinterpret_cast<RT*>(a.rec), a.Tfield,
                                              a.status, a.g, a.un, a.bc, mech);
   }
-  if (which != 0)
-    k_collide<D, M, S, RT><<<nb, bs, 0, s>>>(static_cast<const S*>(a.src),
+  if (which != 0) {
+    const size_t smem = (size_t)M * M * bs * sizeof(RT);
+    if (smem > 48 * 1024) {
+      const cudaError_t e = cudaFuncSetAttribute(
+          k_collide<D, M, S, RT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+    }
+    k_collide<D, M, S, RT><<<nb, bs, smem, s>>>(
+                                             static_cast<const S*>(a.src),
                                              static_cast<S*>(a.dst),
                                              reinterpret_cast<const RT*>(a.rec), a.Tfield,
                                              a.status, a.g, a.un, a.bc, mech);
+  }
   return cudaGetLastError();
 }
 

@@ -11,7 +11,7 @@
 //
 // Limits and behaviour:
 //  - the scratch holds the moment records of at most
-//    LBM_NOALLOC_MAX_NODES nodes (16 384 nodes, about 7.1 MB, plus the status
+//    LBM_NOALLOC_MAX_NODES nodes (16 384 nodes, about 8 MB, plus the status
 //    word); every GPU that loads this library holds the array until the
 //    process exits;
 //  - every call shares the one array, so calls whose work overlaps on the
@@ -30,7 +30,7 @@
 namespace {
 
 constexpr long long kMaxNodes = LBM_NOALLOC_MAX_NODES;
-constexpr int kMaxFields = 54;                        // D3Q27 with 9 species
+constexpr int kMaxFields = 61;                        // D3Q27 with 9 species
 constexpr long long kRecordDoubles = kMaxNodes * kMaxFields;
 
 // Moment records [field][node], then 32 doubles whose first int is the

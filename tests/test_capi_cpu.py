@@ -86,7 +86,7 @@ def test_defaults_and_bytes_required(lbm):
     assert n >= 2 * L * Q * N * 8
     cfg.precision = lbm.LBM_FP32_STORE
     n32 = lbm.lbm_bytes_required(cfg)
-    NF = 53                       # moment-record fields of D3Q27 with 9 species
+    NF = 61                       # moment-record fields of D3Q27 with 9 species
     assert n - n32 == (2 * L * Q + NF) * N * 4   # populations and records halve
 
 
