@@ -49,6 +49,8 @@ def parse():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--workload", default="flame", choices=sorted(WORKLOADS))
     p.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
+    p.add_argument("--substeps", type=int, default=0,
+                   help="reaction sub-steps l (Eq. R3); 0 keeps the workload's value")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
     return p.parse_args()
@@ -245,6 +247,8 @@ def main():
 
     mech = h2_air_synthetic()
     w = _workload(args.workload, seed=rank)
+    if args.substeps:
+        w["substeps"] = args.substeps
     N = int(w["P"].size)
     M = mech.n_species
     solver = lbm.Solver(mech, lattice=w["lattice"], shape=w["shape"], dx=w["dx"],
@@ -348,7 +352,7 @@ def main():
         "dtype": "f64" if args.precision == "fp64" else "f32 (chemistry, Newton, transport f64)",
         "data": "synthetic",
         "config": {"workload": WORKLOADS[args.workload], "nodes": N, "lattice": w["lattice"],
-                   "species": M, "precision": args.precision,
+                   "species": M, "precision": args.precision, "substeps": w["substeps"],
                    "node_steps_per_s": node_steps / (total_ms * 1e-3),
                    "l2": "256 MB buffer overwritten between timed steps" if flush
                    else "state larger than L2", "parallelism": f"replicas x{world}"},

@@ -65,7 +65,9 @@ typedef enum { LBM_D2Q9 = 0, LBM_D3Q27 = 1 } lbm_lattice;
 
 /* Storage precision of the populations.  LBM_FP64: every operation in FP64
  * (the path checked against the oracle to 1e-10).  LBM_FP32_STORE:
- * populations stored in FP32; chemistry, Newton and transport in FP64. */
+ * populations, moments and collision in FP32; the temperature Newton solve
+ * and the chemistry in float-float (pairs of FP32, ~48 significant bits);
+ * transport in FP32.  Field tolerances vs FP64 are stated in the tests. */
 typedef enum { LBM_FP64 = 0, LBM_FP32_STORE = 1, LBM_FP16_OFFSET = 2 } lbm_precision;
 
 /* Face boundary kinds (Sec. 4): periodic; bounce-back wall (Eq. bb);
@@ -183,6 +185,17 @@ lbm_status lbm_init_fields_pressure(lbm_t h, const double* P, const double* u,
  * reaction sub-steps, collision of all lattices; Sec. 2.3, Sec. 3, Sec. 4).
  * Asynchronous on the handle's stream. */
 lbm_status lbm_step(lbm_t h, int nsteps);
+
+/* Advance several handles by nsteps steps together: each step is one launch
+ * per kernel over the concatenated tiles of all handles (128-node tiles; the
+ * boundary kernel over 4-interface-node tiles), so many small domains fill
+ * the GPU.  The handles must share lattice, species count, precision and
+ * device; each keeps its own mechanism, units and boundaries.  The work runs
+ * on hs[0]'s stream after the earlier work of every handle's stream, and
+ * every handle's stream waits for it.  Results equal n separate lbm_step
+ * calls to rounding (the same per-node arithmetic in separately compiled
+ * kernels). */
+lbm_status lbm_batch_step(lbm_t* hs, int n, int nsteps);
 
 /* As lbm_step, and adds each kernel's device time in milliseconds, measured
  * with CUDA events recorded on the handle's stream around every launch:

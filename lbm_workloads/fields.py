@@ -183,3 +183,47 @@ def microtube(seed=0, nx=600, ny=40, nz=40, radius=19.0, phi=0.5, T_in=300.0,
              outlet=dict(P=P_STANDARD), steps=steps, seed=seed,
              name=f"microtube {nx}x{ny}x{nz} D3Q27 r={radius} phi={phi}")
     return w
+
+
+def serving_mix(seed=0, n_requests=64, mean_interarrival=0.05, steps=(1000, 10000),
+                max_nodes=256 * 32 * 32, mech=None):
+    """Seeded request stream for the serving loop: Poisson arrivals (mean
+    `mean_interarrival` s), each request a reactor, a flame or a channel solve
+    with its type, grid, equivalence ratio in [0.4, 0.7], inlet speed in
+    [0.2, 3] m/s and step count drawn from the seed.  Grids range from 16^3
+    to max_nodes nodes.  Returns [(arrival_s, workload), ...] sorted by
+    arrival; workload["steps"] is the request's step count."""
+    mech = mech or h2_air_synthetic()
+    rng = philox(seed)
+    t = 0.0
+    out = []
+    for k in range(n_requests):
+        t += float(rng.exponential(mean_interarrival))
+        kind = ("reactor", "flame", "channel")[int(rng.integers(0, 3))]
+        phi = float(rng.uniform(0.4, 0.7))
+        u_in = float(rng.uniform(0.2, 3.0))
+        nsteps = int(rng.integers(steps[0], steps[1] + 1))
+        if kind == "reactor":
+            nn = int(rng.integers(16, 33))
+            w = reactor(seed=seed * 1000 + k, n=nn, phi=phi, mech=mech)
+        elif kind == "flame":
+            nx = int(rng.choice([256, 512, 1024]))
+            ny = int(rng.choice([4, 8, 16, 32]))
+            while nx * ny * ny > max_nodes:
+                ny //= 2
+            w = flame_1d(seed=seed * 1000 + k, nx=nx, ny=ny, nz=ny, phi=phi,
+                         x_ign=nx // 4, mech=mech)
+            w["inlet"]["u"] = np.array([u_in, 0.0, 0.0])
+            w["u"][0] = u_in
+        else:
+            nx = int(rng.choice([250, 500, 1000, 2000]))
+            ny = int(rng.choice([20, 40]))
+            w = channel_2d(seed=seed * 1000 + k, nx=nx, ny=ny, phi=phi, mech=mech)
+            s = (np.arange(ny) + 0.5) / ny
+            prof = u_in * 4.0 * s * (1.0 - s)
+            w["u"][0] = np.broadcast_to(prof[None, :, None], w["u"][0].shape)
+            w["inlet"]["u"] = w["u"].copy()
+        w["steps"] = nsteps
+        w["kind"] = kind
+        out.append((t, w))
+    return out

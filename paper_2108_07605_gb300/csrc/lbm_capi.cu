@@ -26,6 +26,7 @@ struct lbm_ctx {
   double* io = nullptr;     // staging for host <-> device field copies
   size_t io_bytes = 0;
   BCDev bc;                 // boundary data (device arrays owned by the handle)
+  DevMech* mech_dev = nullptr;  // device copy of the mechanism (batched steps)
   void* bc_mem = nullptr;   // one allocation holding every boundary array
   cudaStream_t stream = nullptr;
   size_t bytes = 0;
@@ -489,6 +490,16 @@ lbm_status lbm_create(const lbm_config* cfg, lbm_t* out) {
   h->Tf = static_cast<double*>(dalloc(h->cfg, s.tf));
   h->status = static_cast<int*>(dalloc(h->cfg, s.status));
   h->bytes = s.total;
+  h->mech_dev = static_cast<DevMech*>(dalloc(h->cfg, sizeof(DevMech)));
+  if (!h->mech_dev) {
+    lbm_destroy(h);
+    return fail(nullptr, LBM_ERR_OOM, "device allocation failed (mechanism)");
+  }
+  if (cudaMemcpy(h->mech_dev, &h->mech, sizeof(DevMech), cudaMemcpyHostToDevice) != cudaSuccess) {
+    lbm_destroy(h);
+    return fail(nullptr, LBM_ERR_CUDA, "mechanism upload failed");
+  }
+  h->bytes += sizeof(DevMech);
   if (hb.needed) {
     h->bc_mem = dalloc(h->cfg, s.bc);
     if (!h->bc_mem) {
@@ -632,6 +643,76 @@ lbm_status lbm_step_timed(lbm_t h, int nsteps, double* kernel_ms, int n_kernels)
   return LBM_OK;
 }
 
+lbm_status lbm_batch_step(lbm_t* hs, int n, int nsteps) {
+  if (!hs || n < 1) return fail(nullptr, LBM_ERR_INVALID, "need at least one handle");
+  for (int k = 0; k < n; ++k)
+    if (!hs[k]) return fail(nullptr, LBM_ERR_INVALID, "handle is NULL");
+  lbm_ctx* h0 = hs[0];
+  if (nsteps < 0) return fail(h0, LBM_ERR_INVALID, "nsteps must be >= 0");
+  for (int k = 0; k < n; ++k) {
+    lbm_ctx* h = hs[k];
+    if (!h->initialized) return fail(h0, LBM_ERR_STATE, "lbm_batch_step before lbm_init_fields");
+    if (h->D != h0->D || h->M != h0->M || h->cfg.precision != h0->cfg.precision ||
+        h->cfg.device != h0->cfg.device)
+      return fail(h0, LBM_ERR_INVALID,
+                  "batched handles must share lattice, species count, precision and device");
+    for (int j = 0; j < k; ++j)
+      if (hs[j] == h) return fail(h0, LBM_ERR_INVALID, "a handle appears twice in the batch");
+  }
+  if (nsteps == 0) return LBM_OK;
+  DeviceGuard dg(h0->cfg.device);
+  std::vector<DomainDev> doms(n);
+  int nblocks = 0, nbblocks = 0;
+  for (int k = 0; k < n; ++k) {
+    lbm_ctx* h = hs[k];
+    DomainDev& d = doms[k];
+    d.pops[0] = h->pops[0];
+    d.pops[1] = h->pops[1];
+    d.cur0 = h->cur;
+    d.rec = h->rec;
+    d.Tf = h->Tf;
+    d.status = h->status;
+    d.g = h->g;
+    d.un = h->un;
+    d.bc = h->bc;
+    d.mech = h->mech_dev;
+    d.block_begin = nblocks;
+    d.bblock_begin = nbblocks;
+    nblocks += (int)((h->g.N + 127) / 128);
+    nbblocks += (h->bc.n_if + 3) / 4;
+  }
+  // every handle's earlier work precedes the batch; the batch runs on the
+  // first handle's stream and each handle's stream waits for it afterwards
+  cudaStream_t s0 = h0->stream;
+  cudaEvent_t ev = nullptr;
+  cudaError_t e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+  for (int k = 1; k < n && e == cudaSuccess; ++k)
+    if (hs[k]->stream != s0) {
+      e = cudaEventRecord(ev, hs[k]->stream);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(s0, ev, 0);
+    }
+  DomainDev* ddev = static_cast<DomainDev*>(dalloc(h0->cfg, n * sizeof(DomainDev)));
+  if (!ddev) e = cudaErrorMemoryAllocation;
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(ddev, doms.data(), n * sizeof(DomainDev), cudaMemcpyHostToDevice, s0);
+  for (int step = 0; step < nsteps && e == cudaSuccess; ++step)
+    e = launch_batch_step(h0->D, h0->M, h0->cfg.precision, ddev, n, nblocks, nbblocks, step & 1, s0);
+  if (e == cudaSuccess) e = cudaEventRecord(ev, s0);
+  for (int k = 1; k < n && e == cudaSuccess; ++k)
+    if (hs[k]->stream != s0) e = cudaStreamWaitEvent(hs[k]->stream, ev, 0);
+  if (ddev) {
+    if (!h0->cfg.dev_free) cudaStreamSynchronize(s0);  // plain cudaFree is not stream-ordered
+    dfree(h0->cfg, ddev);
+  }
+  if (ev) cudaEventDestroy(ev);
+  if (e != cudaSuccess) return cuda_fail(h0, e, "batched step");
+  for (int k = 0; k < n; ++k) {
+    hs[k]->cur ^= (nsteps & 1);
+    hs[k]->steps += nsteps;
+  }
+  return LBM_OK;
+}
+
 lbm_status lbm_moments(lbm_t h, double* rho, double* u, double* T, double* Y, double* E,
                        int on_device) {
   if (!h) return fail(nullptr, LBM_ERR_INVALID, "handle is NULL");
@@ -771,6 +852,7 @@ lbm_status lbm_destroy(lbm_t h) {
   dfree(h->cfg, h->status);
   dfree(h->cfg, h->io);
   dfree(h->cfg, h->bc_mem);
+  dfree(h->cfg, h->mech_dev);
   delete h;
   return st;
 }

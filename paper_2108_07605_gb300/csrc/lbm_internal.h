@@ -113,6 +113,29 @@ struct StepArgs {
   BCDev bc;                    // default: periodic box
 };
 
+// One domain of a batched step (lbm_batch_step): every block of the batched
+// grids belongs to exactly one domain (a tile of 128 nodes, or 4 interface
+// nodes for the boundary kernel).
+struct DomainDev {
+  const void* pops[2] = {nullptr, nullptr};   // the handle's two buffers
+  int cur0 = 0;                // buffer holding the state at batch parity 0
+  void* rec = nullptr;
+  double* Tf = nullptr;
+  int* status = nullptr;
+  Geom g;
+  Units un;
+  BCDev bc;
+  const DevMech* mech = nullptr;   // device copy of the handle's mechanism
+  int block_begin = 0;         // first block of this domain in the node grids
+  int bblock_begin = 0;        // first block in the boundary grid
+};
+
+// Batched step: doms is a device array of ndom domains sharing (D, M, prec);
+// nblocks / nbblocks are the totals of the node and boundary grids.
+cudaError_t launch_batch_step(int D, int M, lbm_precision prec, const DomainDev* doms,
+                              int ndom, int nblocks, int nbblocks, int parity,
+                              cudaStream_t s);
+
 // which: 0 = moments kernel only, 1 = collision kernel only, -1 = both.
 cudaError_t launch_step(int D, int M, lbm_precision prec, const DevMech& mech,
                         const StepArgs& a, cudaStream_t s, int which = -1);

@@ -63,14 +63,13 @@ __device__ __forceinline__ constexpr int pidx(int a, int b) {
 // Moments of the post-stream state + temperature (Sec. 2.1, Sec. 3.1-3.2,
 // Sec. 3.7 slaving, Sec. 4.1 pull streaming).
 template <int D, int M, typename S, typename RT>
-__global__ void __launch_bounds__(128)
-k_moments(const S* __restrict__ src, RT* __restrict__ rec, double* __restrict__ Tf,
-          int* __restrict__ status, Geom g, Units un, BCDev bc,
-          const __grid_constant__ DevMech mech) {
+__device__ __forceinline__ void moments_body(const S* __restrict__ src, RT* __restrict__ rec,
+                                             double* __restrict__ Tf, int* __restrict__ status,
+                                             const Geom& g, const Units& un, const BCDev& bc,
+                                             const DevMech& mech, long long n) {
   constexpr int Q = Lat<D>::Q, NP = Lat<D>::NP;
   using RC = Rec<D, M>;
   const long long N = g.N;
-  const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (n >= N) return;
   const int tag = bc.tag ? bc.tag[n] : TAG_BULK;
   if (tag == TAG_SOLID) return;
@@ -271,14 +270,15 @@ template <> struct MixParams<float> {
 // Sec. 3.2 Eqs. f, g; Sec. 3.3 Eqs. feqmix, Pex; Sec. 3.4 Eqs. geq_i, gstar,
 // gstareq1mom, qdiff, corrFourier, qex; Sec. 2.4 Eq. R3).
 template <int D, int M, typename S, typename RT>
-__global__ void __launch_bounds__(128)
-k_collide(const S* __restrict__ src, S* __restrict__ dst, const RT* __restrict__ rec,
-          const double* __restrict__ Tf, int* __restrict__ status, Geom g, Units un, BCDev bc,
-          const __grid_constant__ DevMech mech) {
+__device__ __forceinline__ void collide_body(const S* __restrict__ src, S* __restrict__ dst,
+                                             const RT* __restrict__ rec,
+                                             const double* __restrict__ Tf,
+                                             int* __restrict__ status, const Geom& g,
+                                             const Units& un, const BCDev& bc,
+                                             const DevMech& mech, long long n) {
   constexpr int Q = Lat<D>::Q, NP = Lat<D>::NP;
   using RC = Rec<D, M>;
   const long long N = g.N;
-  const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (n >= N) return;
   const int tag = bc.tag ? bc.tag[n] : TAG_BULK;
   if (tag == TAG_SOLID) return;
@@ -640,12 +640,12 @@ __device__ void warp_state_of(F fetch, EqSet<D, M>& s, double T_guess, const Dev
 }
 
 template <int D, int M, typename S>
-__global__ void __launch_bounds__(128)
-k_boundary(const S* __restrict__ src, BCDev bc, const double* __restrict__ Tf,
-           int* __restrict__ status, Geom g, Units un, const __grid_constant__ DevMech mech) {
+__device__ __forceinline__ void boundary_body(const S* __restrict__ src, const BCDev& bc,
+                                              const double* __restrict__ Tf,
+                                              int* __restrict__ status, const Geom& g,
+                                              const Units& un, const DevMech& mech, int k,
+                                              int lane) {
   constexpr int Q = Lat<D>::Q, L = M + 1;
-  const int k = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;   // one warp per node
-  const int lane = threadIdx.x & 31;
   if (k >= bc.n_if) return;                                         // whole warp leaves
   const long long N = g.N;
   const long long n = bc.if_node[k];
@@ -760,6 +760,85 @@ k_boundary(const S* __restrict__ src, BCDev bc, const double* __restrict__ Tf,
     double& p = P[(long long)t * st];
     p = eq_pop(Bref, l, i) + p - eq_pop(loc, l, i);
   }
+}
+
+// ---------------------------------------------------------------------------
+// Single-domain kernels: one thread per node (moments, collision), one warp
+// per interface node (boundary).
+template <int D, int M, typename S, typename RT>
+__global__ void __launch_bounds__(128)
+k_moments(const S* __restrict__ src, RT* __restrict__ rec, double* __restrict__ Tf,
+          int* __restrict__ status, const __grid_constant__ Geom g,
+          const __grid_constant__ Units un, const __grid_constant__ BCDev bc,
+          const __grid_constant__ DevMech mech) {
+  moments_body<D, M, S, RT>(src, rec, Tf, status, g, un, bc, mech,
+                            blockIdx.x * (long long)blockDim.x + threadIdx.x);
+}
+
+template <int D, int M, typename S, typename RT>
+__global__ void __launch_bounds__(128)
+k_collide(const S* __restrict__ src, S* __restrict__ dst, const RT* __restrict__ rec,
+          const double* __restrict__ Tf, int* __restrict__ status,
+          const __grid_constant__ Geom g, const __grid_constant__ Units un,
+          const __grid_constant__ BCDev bc, const __grid_constant__ DevMech mech) {
+  collide_body<D, M, S, RT>(src, dst, rec, Tf, status, g, un, bc, mech,
+                            blockIdx.x * (long long)blockDim.x + threadIdx.x);
+}
+
+template <int D, int M, typename S>
+__global__ void __launch_bounds__(128)
+k_boundary(const S* __restrict__ src, const __grid_constant__ BCDev bc,
+           const double* __restrict__ Tf, int* __restrict__ status,
+           const __grid_constant__ Geom g, const __grid_constant__ Units un,
+           const __grid_constant__ DevMech mech) {
+  boundary_body<D, M, S>(src, bc, Tf, status, g, un, mech,
+                         blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32, threadIdx.x & 31);
+}
+
+// ---------------------------------------------------------------------------
+// Batched kernels: the grid is the concatenation of every domain's tiles; a
+// block finds its domain by binary search over the domains' first blocks.
+__device__ __forceinline__ int domain_of_block(const DomainDev* __restrict__ d, int ndom,
+                                               int b, bool boundary) {
+  int lo = 0, hi = ndom - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    const int first = boundary ? d[mid].bblock_begin : d[mid].block_begin;
+    if (first <= b) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+template <int D, int M, typename S, typename RT>
+__global__ void __launch_bounds__(128)
+k_moments_batch(const DomainDev* __restrict__ doms, int ndom, int parity) {
+  const DomainDev& d = doms[domain_of_block(doms, ndom, blockIdx.x, false)];
+  const int c = d.cur0 ^ parity;
+  moments_body<D, M, S, RT>(static_cast<const S*>(d.pops[c]), static_cast<RT*>(d.rec), d.Tf,
+                            d.status, d.g, d.un, d.bc, *d.mech,
+                            (blockIdx.x - d.block_begin) * (long long)blockDim.x + threadIdx.x);
+}
+
+template <int D, int M, typename S, typename RT>
+__global__ void __launch_bounds__(128)
+k_collide_batch(const DomainDev* __restrict__ doms, int ndom, int parity) {
+  const DomainDev& d = doms[domain_of_block(doms, ndom, blockIdx.x, false)];
+  const int c = d.cur0 ^ parity;
+  collide_body<D, M, S, RT>(static_cast<const S*>(d.pops[c]),
+                            static_cast<S*>(const_cast<void*>(d.pops[1 - c])),
+                            static_cast<const RT*>(d.rec), d.Tf, d.status, d.g, d.un, d.bc,
+                            *d.mech,
+                            (blockIdx.x - d.block_begin) * (long long)blockDim.x + threadIdx.x);
+}
+
+template <int D, int M, typename S>
+__global__ void __launch_bounds__(128)
+k_boundary_batch(const DomainDev* __restrict__ doms, int ndom, int parity) {
+  const DomainDev& d = doms[domain_of_block(doms, ndom, blockIdx.x, true)];
+  const int c = d.cur0 ^ parity;
+  boundary_body<D, M, S>(static_cast<const S*>(d.pops[c]), d.bc, d.Tf, d.status, d.g, d.un,
+                         *d.mech, (blockIdx.x - d.bblock_begin) * 4 + threadIdx.x / 32,
+                         threadIdx.x & 31);
 }
 
 // ---------------------------------------------------------------------------
@@ -969,6 +1048,35 @@ cudaError_t launch_to_fp64(lbm_precision prec, const void* pops, double* out,
   else
     return cudaErrorInvalidValue;
   return cudaGetLastError();
+}
+
+template <int D, int M, typename S, typename RT>
+static cudaError_t batch_impl(const DomainDev* doms, int ndom, int nblocks, int nbblocks,
+                              int parity, cudaStream_t s) {
+  const int bs = 128;
+  if (nbblocks > 0)
+    k_boundary_batch<D, M, S><<<nbblocks, bs, 0, s>>>(doms, ndom, parity);
+  k_moments_batch<D, M, S, RT><<<nblocks, bs, 0, s>>>(doms, ndom, parity);
+  const size_t smem = (size_t)M * M * bs * sizeof(RT);
+  if (smem > 48 * 1024) {
+    const cudaError_t e = cudaFuncSetAttribute(
+        k_collide_batch<D, M, S, RT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  k_collide_batch<D, M, S, RT><<<nblocks, bs, smem, s>>>(doms, ndom, parity);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_batch_step(int D, int M, lbm_precision prec, const DomainDev* doms,
+                              int ndom, int nblocks, int nbblocks, int parity,
+                              cudaStream_t s) {
+#define CALL_BATCH(D_, M_, S_, R_) batch_impl<D_, M_, S_, R_>(doms, ndom, nblocks, nbblocks, parity, s)
+  LBM_DISPATCH(3, 9, CALL_BATCH)
+  LBM_DISPATCH(3, 2, CALL_BATCH)
+  LBM_DISPATCH(2, 9, CALL_BATCH)
+  LBM_DISPATCH(2, 2, CALL_BATCH)
+#undef CALL_BATCH
+  return cudaErrorInvalidValue;
 }
 
 int record_fields(int D, int M) {

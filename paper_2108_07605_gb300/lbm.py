@@ -88,6 +88,7 @@ EXPORTS = {
     "lbm_init_fields_pressure": (C.c_int, [C.c_void_p] + [C.c_void_p] * 4 + [C.c_int]),
     "lbm_step": (C.c_int, [C.c_void_p, C.c_int]),
     "lbm_step_timed": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_double), C.c_int]),
+    "lbm_batch_step": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.c_int]),
     "lbm_moments": (C.c_int, [C.c_void_p] + [C.c_void_p] * 5 + [C.c_int]),
     "lbm_get_populations": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int]),
     "lbm_synchronize": (C.c_int, [C.c_void_p]),
@@ -224,6 +225,13 @@ def lbm_init_fields_pressure(h, P, u, T, Y):
 
 def lbm_step(h, nsteps):
     _check(load_library().lbm_step(h, int(nsteps)), h)
+
+
+def lbm_batch_step(handles, nsteps):
+    """Advance several handles together (one launch per kernel per step)."""
+    hs = (C.c_void_p * len(handles))(*[h.value if isinstance(h, C.c_void_p) else h
+                                       for h in handles])
+    _check(load_library().lbm_batch_step(hs, len(handles), int(nsteps)), hs[0])
 
 
 def lbm_step_timed(h, nsteps, kernel_ms=None):

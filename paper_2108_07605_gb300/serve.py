@@ -1,0 +1,200 @@
+"""Continuous-batching request loop for independent reactive-flow solves.
+
+    python -m paper_2108_07605_gb300.serve [--requests 64] [--seed 0]
+        [--budget-gb 40] [--chunk 100] [--precision fp32] [--step-scale 1.0]
+
+Requests (reactor, flame or channel solves of different grid sizes) arrive
+over time.  The loop admits a request as soon as it has arrived and its
+device memory (lbm_bytes_required) fits the remaining budget, initialises
+its populations on the GPU and keeps them resident.  Every tick advances all
+resident requests together with lbm_batch_step - one launch per kernel per
+step over the tiles of every request that shares a lattice and precision -
+for a chunk of steps no longer than the shortest remaining request, so no
+request runs past its step count.  A request that has completed its steps is
+read back (lbm_moments), its handle destroyed and its memory returned, and
+waiting requests are admitted at the next tick.  Reported: time-to-result
+(completion minus arrival) p50/p99 and aggregate node-updates/s.
+
+All arithmetic runs in the CUDA library; this module only schedules.
+"""
+import argparse
+import json
+import time
+
+import numpy as np
+
+from . import lbm
+
+
+def _bc_kwargs(w):
+    keys = ("faces", "inlet", "outlet", "wall_T", "solid", "solid_kind")
+    if all(f == "periodic" for f in w.get("faces", ("periodic",) * 6)) and w.get("solid") is None:
+        return {}
+    return {k: w[k] for k in keys if k in w}
+
+
+class Request:
+    def __init__(self, rid, arrival, workload):
+        self.rid = rid
+        self.arrival = arrival
+        self.w = workload
+        self.remaining = int(workload["steps"])
+        self.solver = None
+        self.bytes = 0
+        self.admitted = None
+        self.finished = None
+        self.result = None
+
+    @property
+    def nodes(self):
+        return int(self.w["P"].size)
+
+
+class Server:
+    """Admission by device memory, continuous batching by lattice/precision."""
+
+    def __init__(self, mech, budget_bytes, chunk=100, precision="fp32", device=0):
+        self.mech = mech
+        self.budget = int(budget_bytes)
+        self.used = 0
+        self.chunk = int(chunk)
+        self.precision = precision
+        self.device = device
+
+    def _config_bytes(self, req):
+        cfg, _keep = lbm.make_config(self.mech, lattice=req.w["lattice"], shape=req.w["shape"],
+                                     dx=req.w["dx"], precision=self.precision,
+                                     substeps=req.w["substeps"], T_max=req.w["T_max"],
+                                     use_torch_allocator=False, stream=0,
+                                     **_bc_kwargs(req.w))
+        return lbm.lbm_bytes_required(cfg)
+
+    def _admit(self, req, now):
+        w = req.w
+        req.solver = lbm.Solver(self.mech, lattice=w["lattice"], shape=w["shape"], dx=w["dx"],
+                                precision=self.precision, substeps=w["substeps"],
+                                T_max=w["T_max"], device=self.device, **_bc_kwargs(w))
+        req.solver.init_fields_pressure(w["P"], w["u"], w["T"], w["Y"])
+        req.admitted = now
+        self.used += req.bytes
+
+    def run(self, stream, clock=time.perf_counter, on_tick=None):
+        """stream: [(arrival_s, workload), ...] sorted by arrival.  Returns the
+        finished requests (with .result = moments) in completion order."""
+        import torch
+        pending = [Request(k, a, w) for k, (a, w) in enumerate(stream)]
+        for r in pending:
+            r.bytes = self._config_bytes(r)
+            if r.bytes > self.budget:
+                raise ValueError(f"request {r.rid} needs {r.bytes} B, above the budget")
+        active, done = [], []
+        t0 = clock()
+        node_updates = 0
+        while pending or active:
+            now = clock() - t0
+            while pending and pending[0].arrival <= now and \
+                    self.used + pending[0].bytes <= self.budget:
+                r = pending.pop(0)
+                self._admit(r, now)
+                active.append(r)
+            if not active:
+                if pending:
+                    time.sleep(max(0.0, min(0.005, pending[0].arrival - now)))
+                continue
+            groups = {}
+            for r in active:
+                groups.setdefault((r.w["lattice"], self.precision), []).append(r)
+            for grp in groups.values():
+                n = min(self.chunk, min(r.remaining for r in grp))
+                lbm.lbm_batch_step([r.solver.h for r in grp], n)
+                for r in grp:
+                    r.remaining -= n
+                    node_updates += n * r.nodes * (self.mech.n_species + 2)
+            torch.cuda.synchronize(self.device)
+            now = clock() - t0
+            still = []
+            for r in active:
+                if r.remaining == 0:
+                    r.result = r.solver.moments()
+                    r.finished = clock() - t0
+                    r.solver.close()
+                    r.solver = None
+                    self.used -= r.bytes
+                    done.append(r)
+                else:
+                    still.append(r)
+            active = still
+            if on_tick:
+                on_tick(now, active, pending, done)
+        self.elapsed = clock() - t0
+        self.node_updates = node_updates
+        return done
+
+
+def summarize(done, elapsed, node_updates):
+    ttr = np.array([r.finished - r.arrival for r in done])
+    return {
+        "requests": len(done),
+        "p50_time_to_result_s": float(np.percentile(ttr, 50)),
+        "p99_time_to_result_s": float(np.percentile(ttr, 99)),
+        "mean_time_to_result_s": float(ttr.mean()),
+        "makespan_s": float(elapsed),
+        "node_updates_per_s": float(node_updates / elapsed),
+        "node_updates": int(node_updates),
+    }
+
+
+def main():
+    p = argparse.ArgumentParser()
+    p.add_argument("--requests", type=int, default=64)
+    p.add_argument("--seed", type=int, default=0)
+    p.add_argument("--budget-gb", type=float, default=40.0)
+    p.add_argument("--chunk", type=int, default=100)
+    p.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    p.add_argument("--step-scale", type=float, default=1.0,
+                   help="multiply every request's step count (1.0 = the stated 1k-10k)")
+    p.add_argument("--serial", action="store_true",
+                   help="one request at a time (no batching), for comparison")
+    args = p.parse_args()
+    from . import build
+    build.build()
+    from lbm_workloads.fields import serving_mix
+    from lbm_workloads.mechanism import h2_air_synthetic
+    mech = h2_air_synthetic()
+    stream = serving_mix(seed=args.seed, n_requests=args.requests, mech=mech)
+    for _, w in stream:
+        w["steps"] = max(1, int(round(w["steps"] * args.step_scale)))
+    budget = int(args.budget_gb * 1e9)
+    if args.serial:
+        # serial baseline: the same requests, one after another, unbatched
+        t0 = time.perf_counter()
+        srv = Server(mech, budget, chunk=args.chunk, precision=args.precision)
+        done = []
+        node_updates = 0
+        import torch
+        for k, (arr, w) in enumerate(stream):
+            r = Request(k, arr, w)
+            now = time.perf_counter() - t0
+            if now < arr:
+                time.sleep(arr - now)
+            srv._admit(r, time.perf_counter() - t0)
+            r.solver.step(r.remaining)
+            torch.cuda.synchronize()
+            node_updates += r.remaining * r.nodes * (mech.n_species + 2)
+            r.result = r.solver.moments()
+            r.finished = time.perf_counter() - t0
+            r.solver.close()
+            done.append(r)
+        out = summarize(done, time.perf_counter() - t0, node_updates)
+    else:
+        srv = Server(mech, budget, chunk=args.chunk, precision=args.precision)
+        done = srv.run(stream)
+        out = summarize(done, srv.elapsed, srv.node_updates)
+    out.update(mode="serial" if args.serial else "continuous batching",
+               precision=args.precision, step_scale=args.step_scale, seed=args.seed,
+               chunk=args.chunk, budget_gb=args.budget_gb)
+    print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    main()
