@@ -197,6 +197,17 @@ lbm_status lbm_step(lbm_t h, int nsteps);
  * kernels). */
 lbm_status lbm_batch_step(lbm_t* hs, int n, int nsteps);
 
+/* A batch plan: the batched step of lbm_batch_step for a fixed set of
+ * handles, captured once as CUDA graphs (one step and two steps, from either
+ * buffer parity) and replayed by lbm_batch_run.  The plan owns a stream; a
+ * run waits for every handle's stream and every handle's stream waits for
+ * the run.  If a handle is advanced on its own between runs, the next run
+ * refreshes the plan's view of it.  Handles must outlive the plan. */
+typedef struct lbm_batch_ctx* lbm_batch_t;
+lbm_status lbm_batch_create(lbm_t* hs, int n, lbm_batch_t* out);
+lbm_status lbm_batch_run(lbm_batch_t b, int nsteps);
+lbm_status lbm_batch_destroy(lbm_batch_t b);
+
 /* As lbm_step, and adds each kernel's device time in milliseconds, measured
  * with CUDA events recorded on the handle's stream around every launch:
  * kernel_ms[0] += moments/temperature kernel, kernel_ms[1] += collision

@@ -10,9 +10,9 @@
 //   two_sum       Knuth, TAOCP vol. 2: s + e = a + b exactly;
 //   fast_two_sum  Dekker 1971: the same when |a| >= |b|;
 //   two_prod      with a fused multiply-add: p + e = a * b exactly.
-// exp: x = k ln2 + r (|r| <= ln2/2, ln2 carried in three parts so k*ln2 is
-// exact), e^r = (e^(r/4))^4 with the Taylor series of e^(r/4) to degree 11
-// (truncation below 1e-21), times 2^k.  log: one Newton step
+// exp: Tang's table-driven reduction to |r| <= ln2/128 with a 64-entry
+// float-float table of 2^(j/64) and a degree-6 polynomial for e^r.
+// log: one Newton step
 // y <- y + x e^(-y) - 1 from the FP32 logarithm (quadratic convergence takes
 // the 1e-7 start to the float-float precision).
 // Intrinsics with explicit rounding keep the compiler from contracting or
@@ -78,34 +78,68 @@ __device__ __forceinline__ ff ff_ldexp(ff a, int k) {
   return ff(ldexpf(a.hi, k), ldexpf(a.lo, k));
 }
 
+// 2^(j/64), j = 0..63, each as the nearest float plus the nearest float to
+// the remainder (generated in 40-digit arithmetic)
+static __device__ const float2 kExp2Tab64[64] = {
+    {1.000000000e+00f, 0.000000000e+00f}, {1.010889292e+00f, -5.711605411e-09f},
+    {1.021897197e+00f, -4.811559862e-08f}, {1.033024907e+00f, -2.809089317e-08f},
+    {1.044273734e+00f, 4.833470157e-08f}, {1.055645227e+00f, -4.907169426e-08f},
+    {1.067140460e+00f, -5.933751979e-08f}, {1.078760743e+00f, 5.461594554e-08f},
+    {1.090507746e+00f, -1.307753994e-08f}, {1.102382541e+00f, 4.260501996e-08f},
+    {1.114386797e+00f, -5.435540018e-08f}, {1.126521587e+00f, 3.123641434e-08f},
+    {1.138788581e+00f, 5.386222313e-08f}, {1.151189208e+00f, 2.192228266e-08f},
+    {1.163724899e+00f, -4.051441493e-08f}, {1.176396966e+00f, 2.566975077e-08f},
+    {1.189207077e+00f, 3.797635273e-08f}, {1.202156782e+00f, -5.069756526e-08f},
+    {1.215247393e+00f, -3.267394888e-08f}, {1.228480577e+00f, -4.136200360e-08f},
+    {1.241857767e+00f, 4.496838102e-08f}, {1.255380750e+00f, 7.322237483e-09f},
+    {1.269050956e+00f, 1.419333318e-09f}, {1.282870054e+00f, -3.816621685e-08f},
+    {1.296839595e+00f, -4.018999533e-08f}, {1.310961246e+00f, -3.496571566e-08f},
+    {1.325236678e+00f, -3.496373324e-08f}, {1.339667559e+00f, -3.461673970e-08f},
+    {1.354255557e+00f, -1.012334927e-08f}, {1.369002461e+00f, -3.845881835e-08f},
+    {1.383909941e+00f, -5.875577358e-08f}, {1.398979664e+00f, 8.689434061e-09f},
+    {1.414213538e+00f, 2.420323497e-08f}, {1.429613352e+00f, -1.342992917e-08f},
+    {1.445180774e+00f, 3.324199938e-08f}, {1.460917830e+00f, -3.628657552e-08f},
+    {1.476826191e+00f, -4.500898854e-08f}, {1.492907763e+00f, -3.423620143e-08f},
+    {1.509164453e+00f, -2.495937323e-08f}, {1.525598168e+00f, -1.762856883e-08f},
+    {1.542210817e+00f, 8.070904833e-09f}, {1.559004426e+00f, -2.576466507e-08f},
+    {1.575980902e+00f, -5.661025426e-08f}, {1.593142152e+00f, -4.903136785e-10f},
+    {1.610490322e+00f, 9.836217174e-09f}, {1.628027439e+00f, -1.726008314e-08f},
+    {1.645755529e+00f, -5.124972091e-08f}, {1.663676620e+00f, -3.920298752e-08f},
+    {1.681792855e+00f, -2.475532668e-08f}, {1.700106382e+00f, -2.865147231e-08f},
+    {1.718619347e+00f, -4.849617596e-08f}, {1.737333894e+00f, -5.850223417e-08f},
+    {1.756252170e+00f, -9.235770371e-09f}, {1.775376439e+00f, 5.343197884e-08f},
+    {1.794709086e+00f, -1.141504491e-08f}, {1.814252138e+00f, 3.736258236e-08f},
+    {1.834008098e+00f, -1.123927795e-08f}, {1.853979111e+00f, 1.436561181e-08f},
+    {1.874167681e+00f, -4.663005626e-08f}, {1.894575953e+00f, 2.810338451e-08f},
+    {1.915206552e+00f, 9.845328108e-09f}, {1.936061740e+00f, 5.357072297e-08f},
+    {1.957144141e+00f, -1.702180441e-08f}, {1.978456020e+00f, 6.032726318e-09f},
+};
+
 __device__ __forceinline__ ff ff_exp(ff x) {
   if (x.hi > 88.7f) return ff(__int_as_float(0x7f800000), 0.f);   // +inf
   if (x.hi < -103.0f) return ff(0.f, 0.f);
-  // ln2 = L1 + L2 + L3, L1 with 15 significant bits so k * L1 is exact
-  const float L1 = 0.693145751953125f, L2 = 1.428606765330187e-06f,
-              L3 = 5.497923148104107e-14f;
-  const float k = rintf(__fmul_rn(x.hi, 1.4426950408889634f));
+  // Table-driven reduction (Tang, ACM TOMS 15(2), 1989): x = (64 n + j) ln2/64
+  // + r with |r| <= ln2/128; ln2/64 = L1 + L2 + L3, L1 with 9 significant
+  // bits so that k * L1 is exact for every k reached here.
+  const float L1 = 0.010833740234375f, L2 = -3.3155381515825866e-06f,
+              L3 = 2.572804640231345e-14f;
+  const float k = rintf(__fmul_rn(x.hi, 92.33248138427734f));   // 64 / ln2
   ff r = x - ff(__fmul_rn(k, L1));
   r = r - two_prod(k, L2);
   r = r - ff(__fmul_rn(k, L3));
-  const ff s = ff_ldexp(r, -2);
-  // Taylor coefficients 1/n!, n = 11..0, split hi + lo
-  const float ch[12] = {2.5052107943679403e-08f, 2.755731998149713e-07f,
-                        2.7557318844628753e-06f, 2.4801587642286904e-05f,
-                        0.00019841270113829523f, 0.0013888889225199819f,
-                        0.008333333767950535f, 0.0416666679084301f,
-                        0.1666666716337204f, 0.5f, 1.0f, 1.0f};
-  const float cl[12] = {4.4176230446483665e-16f, -7.575112209051195e-15f,
-                        3.793571224297229e-14f, -3.40699609366682e-13f,
-                        -2.725596874933456e-12f, -3.3631094437103215e-11f,
-                        -4.34617203337595e-10f, -1.2417634698280722e-09f,
-                        -4.967053879312289e-09f, 0.f, 0.f, 0.f};
-  ff p(ch[0], cl[0]);
-#pragma unroll
-  for (int n = 1; n < 12; ++n) p = p * s + ff(ch[n], cl[n]);
-  p = p * p;
-  p = p * p;
-  return ff_ldexp(p, (int)k);
+  // e^r - 1 = r + r^2 (1/2 + c), c = r/6 + r^2/24 + r^3/120 + r^4/720: c is
+  // below 1e-3 and needs only FP32 (its rounding is below 1e-15 of e^r);
+  // the Taylor remainder r^7/5040 is below 1e-19.
+  const float rh = r.hi;
+  const float c = __fmul_rn(rh, __fmaf_rn(rh, __fmaf_rn(rh, __fmaf_rn(rh, 1.3888889225e-3f,
+                                                                           8.3333337680e-3f),
+                                                       4.1666667908e-2f),
+                                          1.6666667163e-1f));
+  const ff em1 = r + (r * r) * two_sum(0.5f, c);
+  const int ki = (int)k;
+  const float2 t = __ldg(&kExp2Tab64[ki & 63]);
+  const ff tj(t.x, t.y);
+  return ff_ldexp(tj + tj * em1, ki >> 6);
 }
 
 __device__ __forceinline__ ff ff_log(ff x) {

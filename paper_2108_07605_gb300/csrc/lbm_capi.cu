@@ -713,6 +713,148 @@ lbm_status lbm_batch_step(lbm_t* hs, int n, int nsteps) {
   return LBM_OK;
 }
 
+}  // extern "C"
+
+struct lbm_batch_ctx {
+  std::vector<lbm_ctx*> hs;
+  std::vector<int> cur;        // each handle's buffer parity the plan expects
+  DomainDev* ddev = nullptr;
+  int nblocks = 0, nbblocks = 0;
+  int parity = 0;
+  cudaStream_t stream = nullptr;
+  cudaGraphExec_t one[2] = {nullptr, nullptr}, two[2] = {nullptr, nullptr};
+};
+
+namespace {
+
+cudaError_t batch_upload(lbm_batch_ctx* b) {
+  std::vector<DomainDev> doms(b->hs.size());
+  b->nblocks = b->nbblocks = 0;
+  for (size_t k = 0; k < b->hs.size(); ++k) {
+    lbm_ctx* h = b->hs[k];
+    DomainDev& d = doms[k];
+    d.pops[0] = h->pops[0];
+    d.pops[1] = h->pops[1];
+    d.cur0 = h->cur;
+    d.rec = h->rec;
+    d.Tf = h->Tf;
+    d.status = h->status;
+    d.g = h->g;
+    d.un = h->un;
+    d.bc = h->bc;
+    d.mech = h->mech_dev;
+    d.block_begin = b->nblocks;
+    d.bblock_begin = b->nbblocks;
+    b->nblocks += (int)((h->g.N + 127) / 128);
+    b->nbblocks += (h->bc.n_if + 3) / 4;
+    b->cur[k] = h->cur;
+  }
+  b->parity = 0;
+  cudaError_t e = cudaMemcpyAsync(b->ddev, doms.data(), doms.size() * sizeof(DomainDev),
+                                  cudaMemcpyHostToDevice, b->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  return e;
+}
+
+cudaError_t batch_capture(lbm_batch_ctx* b, int first_parity, int nsteps, cudaGraphExec_t* out) {
+  lbm_ctx* h0 = b->hs[0];
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
+  for (int k = 0; k < nsteps && e == cudaSuccess; ++k)
+    e = launch_batch_step(h0->D, h0->M, h0->cfg.precision, b->ddev, (int)b->hs.size(),
+                          b->nblocks, b->nbblocks, (first_parity + k) & 1, b->stream);
+  const cudaError_t e2 = cudaStreamEndCapture(b->stream, &graph);
+  if (e == cudaSuccess) e = e2;
+  if (e == cudaSuccess) e = cudaGraphInstantiate(out, graph, 0);
+  if (graph) cudaGraphDestroy(graph);
+  return e;
+}
+
+}  // namespace
+
+extern "C" {
+
+lbm_status lbm_batch_destroy(lbm_batch_t b) {
+  if (!b) return LBM_OK;
+  if (b->stream) cudaStreamSynchronize(b->stream);
+  for (int p = 0; p < 2; ++p) {
+    if (b->one[p]) cudaGraphExecDestroy(b->one[p]);
+    if (b->two[p]) cudaGraphExecDestroy(b->two[p]);
+  }
+  if (b->ddev && !b->hs.empty()) dfree(b->hs[0]->cfg, b->ddev);
+  if (b->stream) cudaStreamDestroy(b->stream);
+  delete b;
+  return LBM_OK;
+}
+
+lbm_status lbm_batch_create(lbm_t* hs, int n, lbm_batch_t* out) {
+  if (!out) return fail(nullptr, LBM_ERR_INVALID, "out is NULL");
+  *out = nullptr;
+  lbm_status st = lbm_batch_step(hs, n, 0);          // validation only
+  if (st != LBM_OK) return st;
+  lbm_ctx* h0 = hs[0];
+  DeviceGuard dg(h0->cfg.device);
+  lbm_batch_ctx* b = new lbm_batch_ctx();
+  b->hs.assign(hs, hs + n);
+  b->cur.assign(n, 0);
+  cudaError_t e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
+  if (e == cudaSuccess) {
+    b->ddev = static_cast<DomainDev*>(dalloc(h0->cfg, n * sizeof(DomainDev)));
+    if (!b->ddev) e = cudaErrorMemoryAllocation;
+  }
+  if (e == cudaSuccess) e = batch_upload(b);
+  if (e == cudaSuccess) e = prepare_batch_step(h0->D, h0->M, h0->cfg.precision);
+  for (int p = 0; p < 2 && e == cudaSuccess; ++p) {
+    e = batch_capture(b, p, 1, &b->one[p]);
+    if (e == cudaSuccess) e = batch_capture(b, p, 2, &b->two[p]);
+  }
+  if (e != cudaSuccess) {
+    lbm_batch_destroy(b);
+    return cuda_fail(h0, e, "batch plan");
+  }
+  *out = b;
+  return LBM_OK;
+}
+
+lbm_status lbm_batch_run(lbm_batch_t b, int nsteps) {
+  if (!b) return fail(nullptr, LBM_ERR_INVALID, "plan is NULL");
+  lbm_ctx* h0 = b->hs[0];
+  if (nsteps < 0) return fail(h0, LBM_ERR_INVALID, "nsteps must be >= 0");
+  if (nsteps == 0) return LBM_OK;
+  DeviceGuard dg(h0->cfg.device);
+  cudaError_t e = cudaSuccess;
+  // a handle stepped on its own since the last run: refresh the plan's view
+  bool stale = false;
+  for (size_t k = 0; k < b->hs.size(); ++k)
+    stale |= (b->hs[k]->cur != (b->cur[k] ^ b->parity));
+  cudaEvent_t ev = nullptr;
+  e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+  for (size_t k = 0; k < b->hs.size() && e == cudaSuccess; ++k) {
+    e = cudaEventRecord(ev, b->hs[k]->stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(b->stream, ev, 0);
+  }
+  if (e == cudaSuccess && stale) e = batch_upload(b);
+  int left = nsteps;
+  while (e == cudaSuccess && left >= 2) {
+    e = cudaGraphLaunch(b->two[b->parity], b->stream);
+    left -= 2;
+  }
+  if (e == cudaSuccess && left == 1) {
+    e = cudaGraphLaunch(b->one[b->parity], b->stream);
+    b->parity ^= 1;
+  }
+  if (e == cudaSuccess) e = cudaEventRecord(ev, b->stream);
+  for (size_t k = 0; k < b->hs.size() && e == cudaSuccess; ++k)
+    e = cudaStreamWaitEvent(b->hs[k]->stream, ev, 0);
+  if (ev) cudaEventDestroy(ev);
+  if (e != cudaSuccess) return cuda_fail(h0, e, "batch run");
+  for (lbm_ctx* h : b->hs) {
+    h->cur ^= (nsteps & 1);
+    h->steps += nsteps;
+  }
+  return LBM_OK;
+}
+
 lbm_status lbm_moments(lbm_t h, double* rho, double* u, double* T, double* Y, double* E,
                        int on_device) {
   if (!h) return fail(nullptr, LBM_ERR_INVALID, "handle is NULL");

@@ -31,11 +31,14 @@ __host__ __device__ constexpr int csq(int i, int D) {
   return cvel(i, 0) * cvel(i, 0) + cvel(i, 1) * cvel(i, 1) +
          (D == 3 ? cvel(i, 2) * cvel(i, 2) : 0);
 }
-// Isotropic stencil weights of the standard lattice: product of 2/3, 1/6.
-__host__ __device__ constexpr double wstd(int i, int D) {
-  return (cvel(i, 0) == 0 ? 2.0 / 3.0 : 1.0 / 6.0) *
-         (cvel(i, 1) == 0 ? 2.0 / 3.0 : 1.0 / 6.0) *
-         (D == 3 ? (cvel(i, 2) == 0 ? 2.0 / 3.0 : 1.0 / 6.0) : 1.0);
+// Isotropic stencil weights of the standard lattice: product of 2/3, 1/6,
+// evaluated in the caller's type R (a constant once the direction loop is
+// unrolled).
+template <typename R = double>
+__host__ __device__ constexpr R wstd(int i, int D) {
+  return (cvel(i, 0) == 0 ? R(2.0 / 3.0) : R(1.0 / 6.0)) *
+         (cvel(i, 1) == 0 ? R(2.0 / 3.0) : R(1.0 / 6.0)) *
+         (D == 3 ? (cvel(i, 2) == 0 ? R(2.0 / 3.0) : R(1.0 / 6.0)) : R(1));
 }
 
 // Per-axis product-form factor Psi_c(xi, P), Eqs. phi0, phiPlus, phis.

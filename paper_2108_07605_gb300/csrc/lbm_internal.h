@@ -135,6 +135,9 @@ struct DomainDev {
 cudaError_t launch_batch_step(int D, int M, lbm_precision prec, const DomainDev* doms,
                               int ndom, int nblocks, int nbblocks, int parity,
                               cudaStream_t s);
+// Set the batched kernels' attributes (large shared memory) ahead of a
+// stream capture, where such calls are not recorded.
+cudaError_t prepare_batch_step(int D, int M, lbm_precision prec);
 
 // which: 0 = moments kernel only, 1 = collision kernel only, -1 = both.
 cudaError_t launch_step(int D, int M, lbm_precision prec, const DevMech& mech,

@@ -49,6 +49,16 @@ template <> __device__ __forceinline__ float kcoef<float>(const DevMech& m, int 
   return m.Kf[a][b];
 }
 
+// threads per block of the node kernels (the shared-memory columns use it)
+constexpr int kBS = 128;
+
+// shared memory of the collision kernel per thread: the diffusion-velocity
+// matrix, then the axis-factor tables
+// (tables only in the FP32 path: in FP64 they would halve the occupancy)
+template <int D, int M, typename RT> constexpr int collide_smem_entries() {
+  return (sizeof(RT) == 4 && 2 * M * D * 3 > M * M) ? 2 * M * D * 3 : M * M;
+}
+
 template <typename R>
 __device__ __forceinline__ R pick3(int c, const R (&v)[3]) {
   return c == 0 ? v[1] : (c > 0 ? v[2] : v[0]);
@@ -333,8 +343,9 @@ __device__ __forceinline__ void collide_body(const S* __restrict__ src, S* __res
 #pragma unroll
     for (int d = 0; d < D; ++d) {
       phi_self[d] = rec[(RC::PHI + d) * N + n];
-      const double ui = tag >= 0 ? bc.if_uin[(long long)d * bc.n_if + tag] : 0.0;
-      phi_in[d] = RT(bc.rho_in * ui * (1.0 - 3.0 * bc.theta_in) - bc.rho_in * ui * ui * ui);
+      const RT ui = tag >= 0 ? RT(bc.if_uin[(long long)d * bc.n_if + tag]) : RT(0);
+      const RT rin = RT(bc.rho_in);
+      phi_in[d] = rin * ui * (RT(1) - RT(3) * RT(bc.theta_in)) - rin * ui * ui * ui;
     }
   }
 #pragma unroll
@@ -360,7 +371,7 @@ __device__ __forceinline__ void collide_body(const S* __restrict__ src, S* __res
         if (bc.has_solid && bc.tag[nb] == TAG_SOLID) gk = bc.solid_kind;
       }
     }
-    const RT w3 = RT(3.0 * wstd(i, D));
+    const RT w3 = RT(3) * wstd<RT>(i, D);
 #pragma unroll
     for (int d = 0; d < D; ++d) {
       if (cvel(i, d) == 0) continue;
@@ -403,7 +414,7 @@ __device__ __forceinline__ void collide_body(const S* __restrict__ src, S* __res
   {
     extern __shared__ unsigned char smem_raw[];
     RT* As = reinterpret_cast<RT*>(smem_raw) + threadIdx.x;
-    const int st = blockDim.x;
+    const int st = kBS;
 #pragma unroll
     for (int a = 0; a < M; ++a)
 #pragma unroll
@@ -419,7 +430,7 @@ __device__ __forceinline__ void collide_body(const S* __restrict__ src, S* __res
   for (int a = 0; a < M; ++a) rs[a] = rho * Y[a];
 
   // energy-flux correction W = (omega - omega1)(q* - q^eq), folded form
-  const double U_lat = E - 0.5 * usq;
+  const PT U_lat = E - PT(0.5) * usq;
   RT W[D];
   {
     RT diff[D], corr[D];
@@ -456,7 +467,7 @@ __device__ __forceinline__ void collide_body(const S* __restrict__ src, S* __res
       }
       const RT q_ex = RT(-0.5) * ud * dPhi[d];
       W[d] = RT(omega - omega1) * (q[d] - q_eq - uP + q_ex) + RT(omega1) * rhoR * diff[d] +
-             RT(0.5 * (2.0 - omega1)) * Pres * corr[d];
+             RT(PT(0.5) * (PT(2) - omega1)) * Pres * corr[d];
     }
   }
 
@@ -465,7 +476,7 @@ __device__ __forceinline__ void collide_body(const S* __restrict__ src, S* __res
 #pragma unroll
   for (int a = 0; a < M; ++a) {
     th_a[a] = RT(MP::Ra(mech, a) * T * MP::inv_c2(un));
-    beta[a] = RT(inv_tau_a[a] / (2.0 + inv_tau_a[a]));
+    beta[a] = RT(inv_tau_a[a] / (PT(2) + inv_tau_a[a]));
 #pragma unroll
     for (int d = 0; d < D; ++d) VR[a][d] = V[a][d];
   }
@@ -478,16 +489,16 @@ __device__ __forceinline__ void collide_body(const S* __restrict__ src, S* __res
   RT Af[D][3], Bf[D][3];
 #pragma unroll
   for (int d = 0; d < D; ++d) {
-    const double ua = u[d];
-    const double O1 = theta * ua + 0.5 * ua * ua * ua;
-    const double O2 = theta * theta + 2.5 * theta * ua * ua + 0.5 * ua * ua * ua * ua;
-    const double Pd = theta + ua * ua;
-    Af[d][0] = RT(0.5 * (Pd - ua));
-    Af[d][1] = RT(1.0 - Pd);
-    Af[d][2] = RT(0.5 * (Pd + ua));
-    Bf[d][0] = RT(0.5 * (O2 - O1));
-    Bf[d][1] = RT(0.5 * ua * ua - O2);
-    Bf[d][2] = RT(0.5 * (O2 + O1));
+    const PT ua = u[d];
+    const PT O1 = theta * ua + PT(0.5) * ua * ua * ua;
+    const PT O2 = theta * theta + PT(2.5) * theta * ua * ua + PT(0.5) * ua * ua * ua * ua;
+    const PT Pd = theta + ua * ua;
+    Af[d][0] = RT(PT(0.5) * (Pd - ua));
+    Af[d][1] = RT(PT(1) - Pd);
+    Af[d][2] = RT(PT(0.5) * (Pd + ua));
+    Bf[d][0] = RT(PT(0.5) * (O2 - O1));
+    Bf[d][1] = RT(PT(0.5) * ua * ua - O2);
+    Bf[d][2] = RT(PT(0.5) * (O2 + O1));
   }
   const RT rhoR = RT(rho), omR = RT(omega), UR = RT(U_lat);
   // species coefficients of the update, hoisted out of the direction loop:
@@ -503,23 +514,65 @@ __device__ __forceinline__ void collide_body(const S* __restrict__ src, S* __res
     two_beta[a] = RT(2) * beta[a];
   }
 
+  // Per-species axis factors of psi(u, theta_b) and psi(u + V_b, theta_b)
+  // (Eq. prod), tabulated once per node in this thread's shared-memory column
+  // (the solve's space, now free): entry ((set*M + b)*D + d)*3 + c + 1.
+  extern __shared__ unsigned char smem_raw[];
+  RT* tab = reinterpret_cast<RT*>(smem_raw) + threadIdx.x;
+  constexpr bool kTab = sizeof(RT) == 4;
+  if constexpr (kTab) {
+#pragma unroll
+    for (int b = 0; b < M; ++b)
+#pragma unroll
+      for (int d = 0; d < D; ++d) {
+        const RT ud = uR[d], Pe = th_a[b] + ud * ud;
+        RT* te = tab + ((b * D + d) * 3) * kBS;
+        te[0] = RT(0.5) * (Pe - ud);
+        te[kBS] = RT(1) - Pe;
+        te[2 * kBS] = RT(0.5) * (Pe + ud);
+        const RT xs = ud + VR[b][d], Ps = th_a[b] + xs * xs;
+        RT* ts = tab + (((M + b) * D + d) * 3) * kBS;
+        ts[0] = RT(0.5) * (Ps - xs);
+        ts[kBS] = RT(1) - Ps;
+        ts[2 * kBS] = RT(0.5) * (Ps + xs);
+      }
+  }
 #pragma unroll 1
   for (int i = 0; i < Q; ++i) {
     const long long sn = node_shift<D>(x, y, z, i, -1, g);
     int c[3];
     c[0] = cvel(i, 0); c[1] = cvel(i, 1); c[2] = D == 3 ? cvel(i, 2) : 0;
     RT pe[M], dd[M];
+    if constexpr (kTab) {
+      int off[3];
 #pragma unroll
-    for (int b = 0; b < M; ++b) {
-      RT e = RT(1), st = RT(1);
+      for (int d = 0; d < D; ++d) off[d] = (d * 3 + c[d] + 1) * kBS;
 #pragma unroll
-      for (int d = 0; d < D; ++d) {
-        e *= psi1<RT>(c[d], uR[d], th_a[b] + uR[d] * uR[d]);
-        const RT xs = uR[d] + VR[b][d];
-        st *= psi1<RT>(c[d], xs, th_a[b] + xs * xs);
+      for (int b = 0; b < M; ++b) {
+        const RT* te = tab + b * D * 3 * kBS;
+        const RT* ts = tab + (M + b) * D * 3 * kBS;
+        RT e = te[off[0]], st = ts[off[0]];
+#pragma unroll
+        for (int d = 1; d < D; ++d) {
+          e *= te[off[d]];
+          st *= ts[off[d]];
+        }
+        pe[b] = e;
+        dd[b] = rsR[b] * (e - st);
       }
-      pe[b] = e;
-      dd[b] = rsR[b] * (e - st);
+    } else {
+#pragma unroll
+      for (int b = 0; b < M; ++b) {
+        RT e = RT(1), st = RT(1);
+#pragma unroll
+        for (int d = 0; d < D; ++d) {
+          e *= psi1<RT>(c[d], uR[d], th_a[b] + uR[d] * uR[d]);
+          const RT xs = uR[d] + VR[b][d];
+          st *= psi1<RT>(c[d], xs, th_a[b] + xs * xs);
+        }
+        pe[b] = e;
+        dd[b] = rsR[b] * (e - st);
+      }
     }
 #pragma unroll
     for (int a = 0; a < M - 1; ++a) {
@@ -560,7 +613,7 @@ __device__ __forceinline__ void collide_body(const S* __restrict__ src, S* __res
       if (csq(i, D) == 1) {
 #pragma unroll
         for (int d = 0; d < D; ++d)
-          if (c[d] != 0) gn += RT(0.5 * c[d]) * W[d];
+          if (c[d] != 0) gn += (c[d] > 0 ? RT(0.5) : RT(-0.5)) * W[d];
       }
       dst[off + n] = S(gn);
     }
@@ -970,7 +1023,7 @@ static cudaError_t step_impl(const DevMech& mech, const StepArgs& a, cudaStream_
                                              a.status, a.g, a.un, a.bc, mech);
   }
   if (which != 0) {
-    const size_t smem = (size_t)M * M * bs * sizeof(RT);
+    const size_t smem = (size_t)collide_smem_entries<D, M, RT>() * bs * sizeof(RT);
     if (smem > 48 * 1024) {
       const cudaError_t e = cudaFuncSetAttribute(
           k_collide<D, M, S, RT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -1057,7 +1110,7 @@ static cudaError_t batch_impl(const DomainDev* doms, int ndom, int nblocks, int 
   if (nbblocks > 0)
     k_boundary_batch<D, M, S><<<nbblocks, bs, 0, s>>>(doms, ndom, parity);
   k_moments_batch<D, M, S, RT><<<nblocks, bs, 0, s>>>(doms, ndom, parity);
-  const size_t smem = (size_t)M * M * bs * sizeof(RT);
+  const size_t smem = (size_t)collide_smem_entries<D, M, RT>() * bs * sizeof(RT);
   if (smem > 48 * 1024) {
     const cudaError_t e = cudaFuncSetAttribute(
         k_collide_batch<D, M, S, RT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -1065,6 +1118,24 @@ static cudaError_t batch_impl(const DomainDev* doms, int ndom, int nblocks, int 
   }
   k_collide_batch<D, M, S, RT><<<nblocks, bs, smem, s>>>(doms, ndom, parity);
   return cudaGetLastError();
+}
+
+template <int D, int M, typename S, typename RT>
+static cudaError_t batch_prepare_impl() {
+  const size_t smem = (size_t)collide_smem_entries<D, M, RT>() * 128 * sizeof(RT);
+  if (smem <= 48 * 1024) return cudaSuccess;
+  return cudaFuncSetAttribute(k_collide_batch<D, M, S, RT>,
+                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+cudaError_t prepare_batch_step(int D, int M, lbm_precision prec) {
+#define CALL_PREP(D_, M_, S_, R_) batch_prepare_impl<D_, M_, S_, R_>()
+  LBM_DISPATCH(3, 9, CALL_PREP)
+  LBM_DISPATCH(3, 2, CALL_PREP)
+  LBM_DISPATCH(2, 9, CALL_PREP)
+  LBM_DISPATCH(2, 2, CALL_PREP)
+#undef CALL_PREP
+  return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_batch_step(int D, int M, lbm_precision prec, const DomainDev* doms,

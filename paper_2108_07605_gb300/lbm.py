@@ -89,6 +89,9 @@ EXPORTS = {
     "lbm_step": (C.c_int, [C.c_void_p, C.c_int]),
     "lbm_step_timed": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_double), C.c_int]),
     "lbm_batch_step": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.c_int]),
+    "lbm_batch_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.POINTER(C.c_void_p)]),
+    "lbm_batch_run": (C.c_int, [C.c_void_p, C.c_int]),
+    "lbm_batch_destroy": (C.c_int, [C.c_void_p]),
     "lbm_moments": (C.c_int, [C.c_void_p] + [C.c_void_p] * 5 + [C.c_int]),
     "lbm_get_populations": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int]),
     "lbm_synchronize": (C.c_int, [C.c_void_p]),
@@ -232,6 +235,23 @@ def lbm_batch_step(handles, nsteps):
     hs = (C.c_void_p * len(handles))(*[h.value if isinstance(h, C.c_void_p) else h
                                        for h in handles])
     _check(load_library().lbm_batch_step(hs, len(handles), int(nsteps)), hs[0])
+
+
+def lbm_batch_create(handles):
+    """Capture a batch plan (CUDA graphs of the batched step) for handles."""
+    hs = (C.c_void_p * len(handles))(*[h.value if isinstance(h, C.c_void_p) else h
+                                       for h in handles])
+    out = C.c_void_p()
+    _check(load_library().lbm_batch_create(hs, len(handles), C.byref(out)), hs[0])
+    return out
+
+
+def lbm_batch_run(plan, nsteps):
+    _check(load_library().lbm_batch_run(plan, int(nsteps)), None)
+
+
+def lbm_batch_destroy(plan):
+    _check(load_library().lbm_batch_destroy(plan), None)
 
 
 def lbm_step_timed(h, nsteps, kernel_ms=None):

@@ -69,3 +69,24 @@ def test_batch_rejects_mixed_lattices(mech):
     assert e.value.status == 1
     a.close()
     b.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_batch_plan_graph_replay(mech, precision):
+    """A captured plan (CUDA graphs) replays the batched step; odd step
+    counts, and a handle advanced on its own between runs, keep it right."""
+    from paper_2108_07605_gb300 import lbm
+    ws = [fields.flame_1d(nx=40, ny=3, nz=2, x_ign=10), fields.reactor(n=6)]
+    pairs = [_pair(mech, w, precision) for w in ws]
+    plan = lbm.lbm_batch_create([a.h for a, _ in pairs])
+    lbm.lbm_batch_run(plan, 3)
+    pairs[1][0].step(2)                 # outside the plan
+    lbm.lbm_batch_run(plan, 4)
+    lbm.lbm_batch_destroy(plan)
+    pairs[0][1].step(7)
+    pairs[1][1].step(9)
+    for a, b in pairs:
+        err = max_rel_err_per_lattice(a.populations(), b.populations())
+        assert np.all(err <= TOL[precision]), err.max()
+        a.close()
+        b.close()
