@@ -208,9 +208,41 @@ lbm_status lbm_batch_create(lbm_t* hs, int n, lbm_batch_t* out);
 lbm_status lbm_batch_run(lbm_batch_t b, int nsteps);
 lbm_status lbm_batch_destroy(lbm_batch_t b);
 
+/* Kernel placement of a step.  A performance choice only: every placement
+ * evaluates the same formulas in the same order, so results agree to the
+ * last bit or to rounding.
+ *   chem_per_warp  1: the reaction sub-steps (Sec. 2.4, Eq. R3) run in their
+ *                  own kernel with one warp per node - lanes take the
+ *                  reactions' rates of progress, then the species - for
+ *                  grids too small to fill the GPU at one thread per node;
+ *                  0: inside the moments kernel, one thread per node;
+ *                  -1 (lbm_set_launch only, the default): chosen by grid size
+ *                  (1 below 77,824 nodes, four 128-thread blocks per SM). */
+typedef struct {
+  int chem_per_warp;
+} lbm_launch;
+
+/* Set / read the handle's placement (lbm_get_launch reports the resolved
+ * value).  LBM_ERR_INVALID for a value out of range. */
+lbm_status lbm_set_launch(lbm_t h, const lbm_launch* l);
+lbm_status lbm_get_launch(lbm_t h, lbm_launch* l);
+
+/* Autotuner: times trial_steps steps of every placement on the handle's own
+ * state and keeps the fastest (written to *chosen when not NULL).  The trial
+ * steps read the current populations and write the spare buffer without
+ * advancing the handle; the temperature guesses they update are restored,
+ * so the solve continues exactly as without the call.  Synchronises. */
+lbm_status lbm_autotune(lbm_t h, int trial_steps, lbm_launch* chosen);
+
+/* The same for a batch plan: times each placement over the whole batch, keeps
+ * the fastest and captures the plan's graphs again with it.  A new plan
+ * starts with the placement chosen by the batch's total node count. */
+lbm_status lbm_batch_autotune(lbm_batch_t b, int trial_steps, lbm_launch* chosen);
+
 /* As lbm_step, and adds each kernel's device time in milliseconds, measured
  * with CUDA events recorded on the handle's stream around every launch:
- * kernel_ms[0] += moments/temperature kernel, kernel_ms[1] += collision
+ * kernel_ms[0] += boundary + moments/temperature (+ chemistry) kernels,
+ * kernel_ms[1] += collision
  * kernel (n_kernels >= 2).  Synchronises the stream before returning. */
 lbm_status lbm_step_timed(lbm_t h, int nsteps, double* kernel_ms, int n_kernels);
 

@@ -205,7 +205,9 @@ def serving_mix(seed=0, n_requests=64, mean_interarrival=0.05, steps=(1000, 1000
         nsteps = int(rng.integers(steps[0], steps[1] + 1))
         if kind == "reactor":
             nn = int(rng.integers(16, 33))
-            w = reactor(seed=seed * 1000 + k, n=nn, phi=phi, mech=mech)
+            # dx = 50 um keeps the explicit reaction sub-steps stable through
+            # ignition (at 1 mm the time step is 20x longer)
+            w = reactor(seed=seed * 1000 + k, n=nn, phi=phi, dx=5.0e-5, mech=mech)
         elif kind == "flame":
             nx = int(rng.choice([256, 512, 1024]))
             ny = int(rng.choice([4, 8, 16, 32]))

@@ -32,6 +32,7 @@ struct lbm_ctx {
   size_t bytes = 0;
   long long steps = 0;
   bool initialized = false;
+  int chem_warp_opt = -1;   // lbm_launch.chem_per_warp as set (-1: by grid size)
   std::string err;
 };
 
@@ -46,6 +47,51 @@ lbm_status fail(lbm_ctx* h, lbm_status st, const std::string& msg) {
 
 lbm_status cuda_fail(lbm_ctx* h, cudaError_t e, const char* where) {
   return fail(h, LBM_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+// Grids below this many nodes run the reaction sub-steps one warp per node:
+// at one thread per node they would hold fewer than four 128-thread blocks
+// per SM of a 152-SM GB300, too few warps to hide the latency of the long
+// per-node chemistry.
+constexpr long long kChemWarpBelow = 152LL * 4 * 128;
+
+int resolve_chem_warp(int opt, long long nodes) {
+  return opt >= 0 ? opt : (nodes < kChemWarpBelow ? 1 : 0);
+}
+
+// Domains of a batched step: each handle's tiles follow the previous
+// handle's in every grid (128 nodes per node-kernel block, 4 interface nodes
+// per boundary block, kChemNodesPerBlock nodes per chemistry block).
+void fill_domains(lbm_ctx* const* hs, int n, int chem_warp, std::vector<DomainDev>& doms,
+                  int& nblocks, int& nbblocks, int& ncblocks) {
+  doms.assign(n, DomainDev());
+  nblocks = nbblocks = ncblocks = 0;
+  for (int k = 0; k < n; ++k) {
+    lbm_ctx* h = hs[k];
+    DomainDev& d = doms[k];
+    d.pops[0] = h->pops[0];
+    d.pops[1] = h->pops[1];
+    d.cur0 = h->cur;
+    d.rec = h->rec;
+    d.Tf = h->Tf;
+    d.status = h->status;
+    d.g = h->g;
+    d.un = h->un;
+    d.bc = h->bc;
+    d.mech = h->mech_dev;
+    d.block_begin = nblocks;
+    d.bblock_begin = nbblocks;
+    d.cblock_begin = ncblocks;
+    nblocks += (int)((h->g.N + 127) / 128);
+    nbblocks += (h->bc.n_if + 3) / 4;
+    if (chem_warp) ncblocks += (int)((h->g.N + kChemNodesPerBlock - 1) / kChemNodesPerBlock);
+  }
+}
+
+long long total_nodes(lbm_ctx* const* hs, int n) {
+  long long t = 0;
+  for (int k = 0; k < n; ++k) t += hs[k]->g.N;
+  return t;
 }
 
 void* dalloc(const lbm_config& c, size_t bytes) {
@@ -590,6 +636,8 @@ lbm_status lbm_step(lbm_t h, int nsteps) {
   a.g = h->g;
   a.un = h->un;
   a.bc = h->bc;
+  a.chem_warp = resolve_chem_warp(h->chem_warp_opt, h->g.N);
+  a.mech_dev = h->mech_dev;
   for (int k = 0; k < nsteps; ++k) {
     a.src = h->pops[h->cur];
     a.dst = h->pops[1 - h->cur];
@@ -617,6 +665,8 @@ lbm_status lbm_step_timed(lbm_t h, int nsteps, double* kernel_ms, int n_kernels)
   a.g = h->g;
   a.un = h->un;
   a.bc = h->bc;
+  a.chem_warp = resolve_chem_warp(h->chem_warp_opt, h->g.N);
+  a.mech_dev = h->mech_dev;
   cudaError_t err = cudaSuccess;
   for (int k = 0; k < nsteps && err == cudaSuccess; ++k) {
     a.src = h->pops[h->cur];
@@ -643,6 +693,75 @@ lbm_status lbm_step_timed(lbm_t h, int nsteps, double* kernel_ms, int n_kernels)
   return LBM_OK;
 }
 
+lbm_status lbm_set_launch(lbm_t h, const lbm_launch* l) {
+  if (!h || !l) return fail(h, LBM_ERR_INVALID, "handle or launch is NULL");
+  if (l->chem_per_warp < -1 || l->chem_per_warp > 1)
+    return fail(h, LBM_ERR_INVALID, "chem_per_warp must be -1, 0 or 1");
+  h->chem_warp_opt = l->chem_per_warp;
+  return LBM_OK;
+}
+
+lbm_status lbm_get_launch(lbm_t h, lbm_launch* l) {
+  if (!h || !l) return fail(h, LBM_ERR_INVALID, "handle or launch is NULL");
+  l->chem_per_warp = resolve_chem_warp(h->chem_warp_opt, h->g.N);
+  return LBM_OK;
+}
+
+lbm_status lbm_autotune(lbm_t h, int trial_steps, lbm_launch* chosen) {
+  if (!h) return fail(nullptr, LBM_ERR_INVALID, "handle is NULL");
+  if (trial_steps < 1) return fail(h, LBM_ERR_INVALID, "trial_steps must be >= 1");
+  if (!h->initialized) return fail(h, LBM_ERR_STATE, "lbm_autotune before lbm_init_fields");
+  DeviceGuard dg(h->cfg.device);
+  const size_t tbytes = (size_t)h->g.N * sizeof(double);
+  double* Tsave = static_cast<double*>(dalloc(h->cfg, tbytes));
+  if (!Tsave) return fail(h, LBM_ERR_OOM, "autotune scratch allocation failed");
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(Tsave, h->Tf, tbytes, cudaMemcpyDeviceToDevice, h->stream);
+  // trial steps read the current buffer and write the other without
+  // advancing the handle; only the temperature guess changes, and it is
+  // restored after every candidate
+  StepArgs a;
+  a.src = h->pops[h->cur];
+  a.dst = h->pops[1 - h->cur];
+  a.rec = h->rec;
+  a.Tfield = h->Tf;
+  a.status = h->status;
+  a.g = h->g;
+  a.un = h->un;
+  a.bc = h->bc;
+  a.mech_dev = h->mech_dev;
+  float best_ms = 0.f;
+  int best = 0;
+  for (int cand = 0; cand < 2 && e == cudaSuccess; ++cand) {
+    a.chem_warp = cand;
+    e = launch_step(h->D, h->M, h->cfg.precision, h->mech, a, h->stream);   // warm-up
+    if (e == cudaSuccess) e = cudaEventRecord(e0, h->stream);
+    for (int t = 0; t < trial_steps && e == cudaSuccess; ++t)
+      e = launch_step(h->D, h->M, h->cfg.precision, h->mech, a, h->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(e1, h->stream);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(h->Tf, Tsave, tbytes, cudaMemcpyDeviceToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (e == cudaSuccess && (cand == 0 || ms < best_ms)) {
+      best_ms = ms;
+      best = cand;
+    }
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaStreamSynchronize(h->stream);
+  dfree(h->cfg, Tsave);
+  if (e != cudaSuccess) return cuda_fail(h, e, "autotune");
+  h->chem_warp_opt = best;
+  if (chosen) chosen->chem_per_warp = best;
+  return LBM_OK;
+}
+
 lbm_status lbm_batch_step(lbm_t* hs, int n, int nsteps) {
   if (!hs || n < 1) return fail(nullptr, LBM_ERR_INVALID, "need at least one handle");
   for (int k = 0; k < n; ++k)
@@ -661,26 +780,10 @@ lbm_status lbm_batch_step(lbm_t* hs, int n, int nsteps) {
   }
   if (nsteps == 0) return LBM_OK;
   DeviceGuard dg(h0->cfg.device);
-  std::vector<DomainDev> doms(n);
-  int nblocks = 0, nbblocks = 0;
-  for (int k = 0; k < n; ++k) {
-    lbm_ctx* h = hs[k];
-    DomainDev& d = doms[k];
-    d.pops[0] = h->pops[0];
-    d.pops[1] = h->pops[1];
-    d.cur0 = h->cur;
-    d.rec = h->rec;
-    d.Tf = h->Tf;
-    d.status = h->status;
-    d.g = h->g;
-    d.un = h->un;
-    d.bc = h->bc;
-    d.mech = h->mech_dev;
-    d.block_begin = nblocks;
-    d.bblock_begin = nbblocks;
-    nblocks += (int)((h->g.N + 127) / 128);
-    nbblocks += (h->bc.n_if + 3) / 4;
-  }
+  std::vector<DomainDev> doms;
+  int nblocks = 0, nbblocks = 0, ncblocks = 0;
+  fill_domains(hs, n, resolve_chem_warp(-1, total_nodes(hs, n)), doms, nblocks, nbblocks,
+               ncblocks);
   // every handle's earlier work precedes the batch; the batch runs on the
   // first handle's stream and each handle's stream waits for it afterwards
   cudaStream_t s0 = h0->stream;
@@ -696,7 +799,8 @@ lbm_status lbm_batch_step(lbm_t* hs, int n, int nsteps) {
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(ddev, doms.data(), n * sizeof(DomainDev), cudaMemcpyHostToDevice, s0);
   for (int step = 0; step < nsteps && e == cudaSuccess; ++step)
-    e = launch_batch_step(h0->D, h0->M, h0->cfg.precision, ddev, n, nblocks, nbblocks, step & 1, s0);
+    e = launch_batch_step(h0->D, h0->M, h0->cfg.precision, ddev, n, nblocks, nbblocks,
+                          ncblocks, step & 1, s0);
   if (e == cudaSuccess) e = cudaEventRecord(ev, s0);
   for (int k = 1; k < n && e == cudaSuccess; ++k)
     if (hs[k]->stream != s0) e = cudaStreamWaitEvent(hs[k]->stream, ev, 0);
@@ -719,7 +823,8 @@ struct lbm_batch_ctx {
   std::vector<lbm_ctx*> hs;
   std::vector<int> cur;        // each handle's buffer parity the plan expects
   DomainDev* ddev = nullptr;
-  int nblocks = 0, nbblocks = 0;
+  int nblocks = 0, nbblocks = 0, ncblocks = 0;
+  int chem_warp = 0;           // reaction sub-steps one warp per node
   int parity = 0;
   cudaStream_t stream = nullptr;
   cudaGraphExec_t one[2] = {nullptr, nullptr}, two[2] = {nullptr, nullptr};
@@ -728,27 +833,10 @@ struct lbm_batch_ctx {
 namespace {
 
 cudaError_t batch_upload(lbm_batch_ctx* b) {
-  std::vector<DomainDev> doms(b->hs.size());
-  b->nblocks = b->nbblocks = 0;
-  for (size_t k = 0; k < b->hs.size(); ++k) {
-    lbm_ctx* h = b->hs[k];
-    DomainDev& d = doms[k];
-    d.pops[0] = h->pops[0];
-    d.pops[1] = h->pops[1];
-    d.cur0 = h->cur;
-    d.rec = h->rec;
-    d.Tf = h->Tf;
-    d.status = h->status;
-    d.g = h->g;
-    d.un = h->un;
-    d.bc = h->bc;
-    d.mech = h->mech_dev;
-    d.block_begin = b->nblocks;
-    d.bblock_begin = b->nbblocks;
-    b->nblocks += (int)((h->g.N + 127) / 128);
-    b->nbblocks += (h->bc.n_if + 3) / 4;
-    b->cur[k] = h->cur;
-  }
+  std::vector<DomainDev> doms;
+  fill_domains(b->hs.data(), (int)b->hs.size(), b->chem_warp, doms, b->nblocks, b->nbblocks,
+               b->ncblocks);
+  for (size_t k = 0; k < b->hs.size(); ++k) b->cur[k] = b->hs[k]->cur;
   b->parity = 0;
   cudaError_t e = cudaMemcpyAsync(b->ddev, doms.data(), doms.size() * sizeof(DomainDev),
                                   cudaMemcpyHostToDevice, b->stream);
@@ -762,11 +850,31 @@ cudaError_t batch_capture(lbm_batch_ctx* b, int first_parity, int nsteps, cudaGr
   cudaError_t e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
   for (int k = 0; k < nsteps && e == cudaSuccess; ++k)
     e = launch_batch_step(h0->D, h0->M, h0->cfg.precision, b->ddev, (int)b->hs.size(),
-                          b->nblocks, b->nbblocks, (first_parity + k) & 1, b->stream);
+                          b->nblocks, b->nbblocks, b->ncblocks, (first_parity + k) & 1,
+                          b->stream);
   const cudaError_t e2 = cudaStreamEndCapture(b->stream, &graph);
   if (e == cudaSuccess) e = e2;
   if (e == cudaSuccess) e = cudaGraphInstantiate(out, graph, 0);
   if (graph) cudaGraphDestroy(graph);
+  return e;
+}
+
+void batch_release_graphs(lbm_batch_ctx* b) {
+  for (int p = 0; p < 2; ++p) {
+    if (b->one[p]) cudaGraphExecDestroy(b->one[p]);
+    if (b->two[p]) cudaGraphExecDestroy(b->two[p]);
+    b->one[p] = b->two[p] = nullptr;
+  }
+}
+
+// graphs of one and of two steps from either buffer parity
+cudaError_t batch_capture_all(lbm_batch_ctx* b) {
+  batch_release_graphs(b);
+  cudaError_t e = cudaSuccess;
+  for (int p = 0; p < 2 && e == cudaSuccess; ++p) {
+    e = batch_capture(b, p, 1, &b->one[p]);
+    if (e == cudaSuccess) e = batch_capture(b, p, 2, &b->two[p]);
+  }
   return e;
 }
 
@@ -777,10 +885,7 @@ extern "C" {
 lbm_status lbm_batch_destroy(lbm_batch_t b) {
   if (!b) return LBM_OK;
   if (b->stream) cudaStreamSynchronize(b->stream);
-  for (int p = 0; p < 2; ++p) {
-    if (b->one[p]) cudaGraphExecDestroy(b->one[p]);
-    if (b->two[p]) cudaGraphExecDestroy(b->two[p]);
-  }
+  batch_release_graphs(b);
   if (b->ddev && !b->hs.empty()) dfree(b->hs[0]->cfg, b->ddev);
   if (b->stream) cudaStreamDestroy(b->stream);
   delete b;
@@ -802,12 +907,10 @@ lbm_status lbm_batch_create(lbm_t* hs, int n, lbm_batch_t* out) {
     b->ddev = static_cast<DomainDev*>(dalloc(h0->cfg, n * sizeof(DomainDev)));
     if (!b->ddev) e = cudaErrorMemoryAllocation;
   }
+  b->chem_warp = resolve_chem_warp(-1, total_nodes(hs, n));
   if (e == cudaSuccess) e = batch_upload(b);
   if (e == cudaSuccess) e = prepare_batch_step(h0->D, h0->M, h0->cfg.precision);
-  for (int p = 0; p < 2 && e == cudaSuccess; ++p) {
-    e = batch_capture(b, p, 1, &b->one[p]);
-    if (e == cudaSuccess) e = batch_capture(b, p, 2, &b->two[p]);
-  }
+  if (e == cudaSuccess) e = batch_capture_all(b);
   if (e != cudaSuccess) {
     lbm_batch_destroy(b);
     return cuda_fail(h0, e, "batch plan");
@@ -852,6 +955,66 @@ lbm_status lbm_batch_run(lbm_batch_t b, int nsteps) {
     h->cur ^= (nsteps & 1);
     h->steps += nsteps;
   }
+  return LBM_OK;
+}
+
+lbm_status lbm_batch_autotune(lbm_batch_t b, int trial_steps, lbm_launch* chosen) {
+  if (!b) return fail(nullptr, LBM_ERR_INVALID, "plan is NULL");
+  lbm_ctx* h0 = b->hs[0];
+  if (trial_steps < 1) return fail(h0, LBM_ERR_INVALID, "trial_steps must be >= 1");
+  DeviceGuard dg(h0->cfg.device);
+  const int n = (int)b->hs.size();
+  cudaError_t e = cudaSuccess;
+  for (int k = 0; k < n && e == cudaSuccess; ++k) e = cudaStreamSynchronize(b->hs[k]->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  // temperature guesses of every handle, restored after each candidate
+  std::vector<double*> Tsave(n, nullptr);
+  for (int k = 0; k < n && e == cudaSuccess; ++k) {
+    const size_t tb = (size_t)b->hs[k]->g.N * sizeof(double);
+    Tsave[k] = static_cast<double*>(dalloc(h0->cfg, tb));
+    if (!Tsave[k]) e = cudaErrorMemoryAllocation;
+    else e = cudaMemcpyAsync(Tsave[k], b->hs[k]->Tf, tb, cudaMemcpyDeviceToDevice, b->stream);
+  }
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (e == cudaSuccess) e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  float best_ms = 0.f;
+  int best = 0;
+  for (int cand = 0; cand < 2 && e == cudaSuccess; ++cand) {
+    b->chem_warp = cand;
+    e = batch_upload(b);
+    // parity 0 every time: each trial step recomputes the next state of every
+    // handle from its current buffer, advancing none of them
+    if (e == cudaSuccess)
+      e = launch_batch_step(h0->D, h0->M, h0->cfg.precision, b->ddev, n, b->nblocks,
+                            b->nbblocks, b->ncblocks, 0, b->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(e0, b->stream);
+    for (int t = 0; t < trial_steps && e == cudaSuccess; ++t)
+      e = launch_batch_step(h0->D, h0->M, h0->cfg.precision, b->ddev, n, b->nblocks,
+                            b->nbblocks, b->ncblocks, 0, b->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(e1, b->stream);
+    for (int k = 0; k < n && e == cudaSuccess; ++k)
+      e = cudaMemcpyAsync(b->hs[k]->Tf, Tsave[k], (size_t)b->hs[k]->g.N * sizeof(double),
+                          cudaMemcpyDeviceToDevice, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (e == cudaSuccess && (cand == 0 || ms < best_ms)) {
+      best_ms = ms;
+      best = cand;
+    }
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaStreamSynchronize(b->stream);
+  for (int k = 0; k < n; ++k) dfree(h0->cfg, Tsave[k]);
+  if (e == cudaSuccess) {
+    b->chem_warp = best;
+    e = batch_upload(b);
+  }
+  if (e == cudaSuccess) e = batch_capture_all(b);
+  if (e != cudaSuccess) return cuda_fail(h0, e, "batch autotune");
+  if (chosen) chosen->chem_per_warp = best;
   return LBM_OK;
 }
 

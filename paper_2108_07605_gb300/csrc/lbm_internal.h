@@ -111,6 +111,8 @@ struct StepArgs {
   Geom g;
   Units un;
   BCDev bc;                    // default: periodic box
+  int chem_warp = 0;           // reaction sub-steps in k_chem (one warp per node)
+  const DevMech* mech_dev = nullptr;   // device copy of the mechanism (k_chem)
 };
 
 // One domain of a batched step (lbm_batch_step): every block of the batched
@@ -128,13 +130,17 @@ struct DomainDev {
   const DevMech* mech = nullptr;   // device copy of the handle's mechanism
   int block_begin = 0;         // first block of this domain in the node grids
   int bblock_begin = 0;        // first block in the boundary grid
+  int cblock_begin = 0;        // first block in the warp-per-node chemistry grid
 };
 
 // Batched step: doms is a device array of ndom domains sharing (D, M, prec);
-// nblocks / nbblocks are the totals of the node and boundary grids.
+// nblocks / nbblocks / ncblocks are the totals of the node, boundary and
+// chemistry grids (ncblocks = 0: reaction sub-steps inside the moments kernel).
 cudaError_t launch_batch_step(int D, int M, lbm_precision prec, const DomainDev* doms,
-                              int ndom, int nblocks, int nbblocks, int parity,
+                              int ndom, int nblocks, int nbblocks, int ncblocks, int parity,
                               cudaStream_t s);
+// nodes per block of the warp-per-node chemistry kernel
+constexpr int kChemNodesPerBlock = 4;
 // Set the batched kernels' attributes (large shared memory) ahead of a
 // stream capture, where such calls are not recorded.
 cudaError_t prepare_batch_step(int D, int M, lbm_precision prec);

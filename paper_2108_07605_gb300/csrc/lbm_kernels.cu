@@ -72,11 +72,15 @@ __device__ __forceinline__ constexpr int pidx(int a, int b) {
 // ---------------------------------------------------------------------------
 // Moments of the post-stream state + temperature (Sec. 2.1, Sec. 3.1-3.2,
 // Sec. 3.7 slaving, Sec. 4.1 pull streaming).
+// chem_inline = 0: the reaction sub-steps run in k_chem (one warp per node);
+// this kernel then leaves the post-stream species densities rho_a (a < M) in
+// the record's increment slots for it.
 template <int D, int M, typename S, typename RT>
 __device__ __forceinline__ void moments_body(const S* __restrict__ src, RT* __restrict__ rec,
                                              double* __restrict__ Tf, int* __restrict__ status,
                                              const Geom& g, const Units& un, const BCDev& bc,
-                                             const DevMech& mech, long long n) {
+                                             const DevMech& mech, long long n,
+                                             int chem_inline) {
   constexpr int Q = Lat<D>::Q, NP = Lat<D>::NP;
   using RC = Rec<D, M>;
   const long long N = g.N;
@@ -179,7 +183,10 @@ __device__ __forceinline__ void moments_body(const S* __restrict__ src, RT* __re
   // reaction sub-steps at frozen U (Sec. 2.4 Eq. R3): a zero-dimensional
   // reactor per node from its post-stream species densities; T_0 is the T
   // just solved.  The increments drho_a (a < M) go to the record.
-  if constexpr (sizeof(RT) == 4) {
+  if (!chem_inline) {
+#pragma unroll
+    for (int a = 0; a < M - 1; ++a) rec[(RC::DRHO + a) * N + n] = rs[a];
+  } else if constexpr (sizeof(RT) == 4) {
     const ff Uphys = (ff(ER) + ff(-0.5f * usqR)) * un.c2_f;
     ff r[M], rdot[M];
 #pragma unroll
@@ -246,6 +253,182 @@ __device__ __forceinline__ void moments_body(const S* __restrict__ src, RT* __re
 #pragma unroll
     for (int d = 0; d < D; ++d)
       rec[(RC::US + a * D + d) * N + n] = tiny ? uR[d] : js[a][d] / rs[a];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Reaction sub-steps with one warp per node (Sec. 2.4 Eq. R3), for grids too
+// small to fill the GPU at one thread per node: the lanes take the reactions'
+// rates of progress, then lanes a < M sum them into the species production
+// rates and advance rho_a.  The formulas and their order of evaluation are
+// those of production_rates / production_rates_ff, so both placements give
+// the same increments.  CT: double (FP64 path) or float-float (mixed path).
+template <typename CT> struct Chem;
+template <> struct Chem<double> {
+  __device__ static double ex(double x) { return exp(x); }
+  __device__ static double ln(double x) { return log(x); }
+  __device__ static double inv(double x) { return 1.0 / x; }
+  __device__ static double inv_mm(const DevMech& m, int a) { return m.inv_mm[a]; }
+  __device__ static double mm(const DevMech& m, int a) { return m.mm[a]; }
+  __device__ static double gibbs(const DevMech& m, int a, double T, double invT, double lnT) {
+    return m.g_inv[a] * invT + m.g0[a] + T * (m.g1[a] + T * m.g2[a]) - m.a0[a] * lnT;
+  }
+  __device__ static double lnkf(const DevReaction& rx, double lnT, double invT) {
+    return rx.lnA + rx.b * lnT - rx.EaR * invT;
+  }
+  __device__ static double rev_arg(const DevReaction& rx, double lk, double dG, double lp) {
+    return lk + dG - rx.dn * lp;
+  }
+  __device__ static double ln_p0(const DevMech& m) { return m.ln_p0_over_ru; }
+  __device__ static double eff(const DevMech& m, int k, int a) { return m.eff[k][a]; }
+  __device__ static double dt_sub(const Units& u) { return u.dt / u.substeps; }
+  __device__ static double of(double v) { return v; }
+  __device__ static double of_T(double T) { return T; }
+  template <int M>
+  __device__ static double newton(const DevMech& m, const double (&r)[M], double rho, double U,
+                                  double T, const Units& un, bool& ok) {
+    double Ys[M];
+    const double ir = 1.0 / rho;
+#pragma unroll
+    for (int a = 0; a < M; ++a) Ys[a] = r[a] * ir;
+    return newton_T<M>(m, Ys, U, T, un.newton_max_iter, un.newton_rtol, ok);
+  }
+};
+template <> struct Chem<ff> {
+  __device__ static ff ex(ff x) { return ff_exp(x); }
+  __device__ static ff ln(ff x) { return ff_log(x); }
+  __device__ static ff inv(ff x) { return ff(1.f) / x; }
+  __device__ static ff inv_mm(const DevMech& m, int a) { return m.inv_mm_f[a]; }
+  __device__ static ff mm(const DevMech& m, int a) { return m.mm_f[a]; }
+  __device__ static ff gibbs(const DevMech& m, int a, ff T, ff invT, ff lnT) {
+    return m.g_inv_f[a] * invT + m.g0_f[a] + T * (m.g1_f[a] + T * m.g2_f[a]) - m.a0_f[a] * lnT;
+  }
+  __device__ static ff lnkf(const DevReaction& rx, ff lnT, ff invT) {
+    return rx.lnA_f + rx.b_f * lnT - rx.EaR_f * invT;
+  }
+  __device__ static ff rev_arg(const DevReaction& rx, ff lk, ff dG, ff lp) {
+    return lk + dG - ff((float)rx.dn) * lp;
+  }
+  __device__ static ff ln_p0(const DevMech& m) { return m.ln_p0_over_ru_f; }
+  __device__ static ff eff(const DevMech& m, int k, int a) { return m.eff_f[k][a]; }
+  __device__ static ff dt_sub(const Units& u) { return u.dt_sub_f; }
+  __device__ static ff of(float v) { return ff(v); }
+  __device__ static ff of_T(double T) { return ff_from_double(T); }
+  template <int M>
+  __device__ static ff newton(const DevMech& m, const ff (&r)[M], ff rho, ff U, ff T,
+                              const Units& un, bool& ok) {
+    ff Ys[M];
+#pragma unroll
+    for (int a = 0; a < M; ++a) Ys[a] = r[a] / rho;
+    return newton_T_ff<M>(m, Ys, U, T, un.newton_max_iter, un.newton_rtol_f, ok);
+  }
+};
+
+template <typename RT> struct ChemType { using type = double; };
+template <> struct ChemType<float> { using type = ff; };
+
+// warp scratch entries of k_chem: r, C, G per species and q per reaction
+constexpr int kChemScratch = 3 * LBM_MAX_SPECIES + LBM_MAX_REACTIONS;
+
+template <int D, int M, typename RT>
+__device__ __forceinline__ void chem_warp_body(RT* __restrict__ rec,
+                                               const double* __restrict__ Tf,
+                                               int* __restrict__ status, long long N,
+                                               const int* __restrict__ tag, const Units& un,
+                                               const DevMech& m, long long n, int lane,
+                                               typename ChemType<RT>::type* __restrict__ sc) {
+  using CT = typename ChemType<RT>::type;
+  using X = Chem<CT>;
+  using RC = Rec<D, M>;
+  if (n >= N) return;
+  if (tag && tag[n] == TAG_SOLID) return;
+  CT* r = sc;
+  CT* C = sc + LBM_MAX_SPECIES;
+  CT* G = sc + 2 * LBM_MAX_SPECIES;
+  CT* q = sc + 3 * LBM_MAX_SPECIES;
+  // the node's post-stream species densities and internal energy, as the
+  // moments kernel formed them
+  const RT rho = rec[RC::RHO * N + n];
+  RT usq = RT(0);
+#pragma unroll
+  for (int d = 0; d < D; ++d) {
+    const RT ud = rec[(RC::U + d) * N + n];
+    usq += ud * ud;
+  }
+  const RT ER = rec[RC::E * N + n];
+  CT U;
+  if constexpr (sizeof(RT) == 4) U = (ff(ER) + ff(-0.5f * usq)) * un.c2_f;
+  else U = (double(ER) - 0.5 * double(usq)) * un.c * un.c;
+  CT r0 = CT();
+  if (lane < M - 1) {
+    const RT v = rec[(RC::DRHO + lane) * N + n];
+    r0 = X::of(v);
+    r[lane] = r0;
+  } else if (lane == M - 1) {
+    RT last = rho;
+#pragma unroll
+    for (int a = 0; a < M - 1; ++a) last -= rec[(RC::DRHO + a) * N + n];
+    r[lane] = X::of(last);
+  }
+  __syncwarp();
+  const CT rho_c = X::of(rho);
+  CT Ts = X::of_T(Tf[n]);
+  for (int s = 0; s < un.substeps; ++s) {
+    if (s > 0) {
+      CT rl[M];
+#pragma unroll
+      for (int a = 0; a < M; ++a) rl[a] = r[a];
+      bool ok;
+      Ts = X::template newton<M>(m, rl, rho_c, U, Ts, un, ok);
+      if (!ok && lane == 0) atomicOr(status, ST_NEWTON);
+    }
+    const CT lnT = X::ln(Ts);
+    const CT invT = X::inv(Ts);
+    if (lane < M) {
+      C[lane] = r[lane] * X::inv_mm(m, lane);
+      G[lane] = X::gibbs(m, lane, Ts, invT, lnT);
+    }
+    __syncwarp();
+    const CT lp = X::ln_p0(m) - lnT;   // ln(P0 / (R_U T))
+    for (int k = lane; k < m.R; k += 32) {
+      const DevReaction& rx = m.rx[k];
+      const CT lk = X::lnkf(rx, lnT, invT);
+      CT fwd = X::ex(lk);
+      for (int j = 0; j < rx.nr; ++j) fwd *= C[rx.reac[j]];
+      CT rev = CT();
+      if (rx.reversible) {
+        CT dG = CT();
+        for (int j = 0; j < rx.np; ++j) dG += G[rx.prod[j]];
+        for (int j = 0; j < rx.nr; ++j) dG -= G[rx.reac[j]];
+        rev = X::ex(X::rev_arg(rx, lk, dG, lp));
+        for (int j = 0; j < rx.np; ++j) rev *= C[rx.prod[j]];
+      }
+      CT qk = fwd - rev;
+      if (rx.third_body) {
+        CT cm = CT();
+#pragma unroll
+        for (int a = 0; a < M; ++a) cm += X::eff(m, k, a) * C[a];
+        qk *= cm;
+      }
+      q[k] = qk;
+    }
+    __syncwarp();
+    if (lane < M) {
+      CT w = CT();
+      for (int k = 0; k < m.R; ++k) {
+        const DevReaction& rx = m.rx[k];
+        for (int j = 0; j < rx.nr; ++j)
+          if (rx.reac[j] == lane) w -= q[k];
+        for (int j = 0; j < rx.np; ++j)
+          if (rx.prod[j] == lane) w += q[k];
+      }
+      r[lane] += X::dt_sub(un) * (w * X::mm(m, lane));
+    }
+    __syncwarp();
+  }
+  if (lane < M - 1) {
+    if constexpr (sizeof(RT) == 4) rec[(RC::DRHO + lane) * N + n] = (r[lane] - r0).hi;
+    else rec[(RC::DRHO + lane) * N + n] = RT(r[lane] - r0);
   }
 }
 
@@ -823,9 +1006,25 @@ __global__ void __launch_bounds__(128)
 k_moments(const S* __restrict__ src, RT* __restrict__ rec, double* __restrict__ Tf,
           int* __restrict__ status, const __grid_constant__ Geom g,
           const __grid_constant__ Units un, const __grid_constant__ BCDev bc,
-          const __grid_constant__ DevMech mech) {
+          const __grid_constant__ DevMech mech, int chem_inline) {
   moments_body<D, M, S, RT>(src, rec, Tf, status, g, un, bc, mech,
-                            blockIdx.x * (long long)blockDim.x + threadIdx.x);
+                            blockIdx.x * (long long)blockDim.x + threadIdx.x, chem_inline);
+}
+
+// one warp per node, kChemWarps nodes per block
+constexpr int kChemWarps = kChemNodesPerBlock;
+
+template <int D, int M, typename RT>
+__global__ void __launch_bounds__(32 * kChemWarps)
+k_chem(RT* __restrict__ rec, const double* __restrict__ Tf, int* __restrict__ status,
+       long long N, const int* __restrict__ tag, const __grid_constant__ Units un,
+       const DevMech* __restrict__ mech) {
+  using CT = typename ChemType<RT>::type;
+  __shared__ __align__(16) unsigned char raw[kChemWarps * kChemScratch * sizeof(CT)];
+  const int w = threadIdx.x >> 5;
+  chem_warp_body<D, M, RT>(rec, Tf, status, N, tag, un, *mech,
+                           blockIdx.x * (long long)kChemWarps + w, threadIdx.x & 31,
+                           reinterpret_cast<CT*>(raw) + w * kChemScratch);
 }
 
 template <int D, int M, typename S, typename RT>
@@ -851,12 +1050,14 @@ k_boundary(const S* __restrict__ src, const __grid_constant__ BCDev bc,
 // ---------------------------------------------------------------------------
 // Batched kernels: the grid is the concatenation of every domain's tiles; a
 // block finds its domain by binary search over the domains' first blocks.
+// grid: 0 = node kernels, 1 = boundary kernel, 2 = warp-per-node chemistry
 __device__ __forceinline__ int domain_of_block(const DomainDev* __restrict__ d, int ndom,
-                                               int b, bool boundary) {
+                                               int b, int grid) {
   int lo = 0, hi = ndom - 1;
   while (lo < hi) {
     const int mid = (lo + hi + 1) >> 1;
-    const int first = boundary ? d[mid].bblock_begin : d[mid].block_begin;
+    const int first = grid == 1 ? d[mid].bblock_begin
+                                : (grid == 2 ? d[mid].cblock_begin : d[mid].block_begin);
     if (first <= b) lo = mid; else hi = mid - 1;
   }
   return lo;
@@ -864,18 +1065,32 @@ __device__ __forceinline__ int domain_of_block(const DomainDev* __restrict__ d, 
 
 template <int D, int M, typename S, typename RT>
 __global__ void __launch_bounds__(128)
-k_moments_batch(const DomainDev* __restrict__ doms, int ndom, int parity) {
-  const DomainDev& d = doms[domain_of_block(doms, ndom, blockIdx.x, false)];
+k_moments_batch(const DomainDev* __restrict__ doms, int ndom, int parity, int chem_inline) {
+  const DomainDev& d = doms[domain_of_block(doms, ndom, blockIdx.x, 0)];
   const int c = d.cur0 ^ parity;
   moments_body<D, M, S, RT>(static_cast<const S*>(d.pops[c]), static_cast<RT*>(d.rec), d.Tf,
                             d.status, d.g, d.un, d.bc, *d.mech,
-                            (blockIdx.x - d.block_begin) * (long long)blockDim.x + threadIdx.x);
+                            (blockIdx.x - d.block_begin) * (long long)blockDim.x + threadIdx.x,
+                            chem_inline);
+}
+
+template <int D, int M, typename RT>
+__global__ void __launch_bounds__(32 * kChemWarps)
+k_chem_batch(const DomainDev* __restrict__ doms, int ndom) {
+  using CT = typename ChemType<RT>::type;
+  __shared__ __align__(16) unsigned char raw[kChemWarps * kChemScratch * sizeof(CT)];
+  const DomainDev& d = doms[domain_of_block(doms, ndom, blockIdx.x, 2)];
+  const int w = threadIdx.x >> 5;
+  chem_warp_body<D, M, RT>(static_cast<RT*>(d.rec), d.Tf, d.status, d.g.N, d.bc.tag, d.un,
+                           *d.mech,
+                           (blockIdx.x - d.cblock_begin) * (long long)kChemWarps + w,
+                           threadIdx.x & 31, reinterpret_cast<CT*>(raw) + w * kChemScratch);
 }
 
 template <int D, int M, typename S, typename RT>
 __global__ void __launch_bounds__(128)
 k_collide_batch(const DomainDev* __restrict__ doms, int ndom, int parity) {
-  const DomainDev& d = doms[domain_of_block(doms, ndom, blockIdx.x, false)];
+  const DomainDev& d = doms[domain_of_block(doms, ndom, blockIdx.x, 0)];
   const int c = d.cur0 ^ parity;
   collide_body<D, M, S, RT>(static_cast<const S*>(d.pops[c]),
                             static_cast<S*>(const_cast<void*>(d.pops[1 - c])),
@@ -887,7 +1102,7 @@ k_collide_batch(const DomainDev* __restrict__ doms, int ndom, int parity) {
 template <int D, int M, typename S>
 __global__ void __launch_bounds__(128)
 k_boundary_batch(const DomainDev* __restrict__ doms, int ndom, int parity) {
-  const DomainDev& d = doms[domain_of_block(doms, ndom, blockIdx.x, true)];
+  const DomainDev& d = doms[domain_of_block(doms, ndom, blockIdx.x, 1)];
   const int c = d.cur0 ^ parity;
   boundary_body<D, M, S>(static_cast<const S*>(d.pops[c]), d.bc, d.Tf, d.status, d.g, d.un,
                          *d.mech, (blockIdx.x - d.bblock_begin) * 4 + threadIdx.x / 32,
@@ -1018,9 +1233,13 @@ static cudaError_t step_impl(const DevMech& mech, const StepArgs& a, cudaStream_
     if (a.bc.n_if > 0)
       k_boundary<D, M, S><<<(a.bc.n_if + 3) / 4, 128, 0, s>>>(
           static_cast<const S*>(a.src), a.bc, a.Tfield, a.status, a.g, a.un, mech);
+    const int chem_warp = a.chem_warp && a.mech_dev;
     k_moments<D, M, S, RT><<<nb, bs, 0, s>>>(static_cast<const S*>(a.src),
                                              reinterpret_cast<RT*>(a.rec), a.Tfield,
-                                             a.status, a.g, a.un, a.bc, mech);
+                                             a.status, a.g, a.un, a.bc, mech, !chem_warp);
+    if (chem_warp)
+      k_chem<D, M, RT><<<blocks_for(a.g.N, kChemWarps), 32 * kChemWarps, 0, s>>>(
+          reinterpret_cast<RT*>(a.rec), a.Tfield, a.status, a.g.N, a.bc.tag, a.un, a.mech_dev);
   }
   if (which != 0) {
     const size_t smem = (size_t)collide_smem_entries<D, M, RT>() * bs * sizeof(RT);
@@ -1105,11 +1324,13 @@ cudaError_t launch_to_fp64(lbm_precision prec, const void* pops, double* out,
 
 template <int D, int M, typename S, typename RT>
 static cudaError_t batch_impl(const DomainDev* doms, int ndom, int nblocks, int nbblocks,
-                              int parity, cudaStream_t s) {
+                              int ncblocks, int parity, cudaStream_t s) {
   const int bs = 128;
   if (nbblocks > 0)
     k_boundary_batch<D, M, S><<<nbblocks, bs, 0, s>>>(doms, ndom, parity);
-  k_moments_batch<D, M, S, RT><<<nblocks, bs, 0, s>>>(doms, ndom, parity);
+  k_moments_batch<D, M, S, RT><<<nblocks, bs, 0, s>>>(doms, ndom, parity, ncblocks == 0);
+  if (ncblocks > 0)
+    k_chem_batch<D, M, RT><<<ncblocks, 32 * kChemWarps, 0, s>>>(doms, ndom);
   const size_t smem = (size_t)collide_smem_entries<D, M, RT>() * bs * sizeof(RT);
   if (smem > 48 * 1024) {
     const cudaError_t e = cudaFuncSetAttribute(
@@ -1139,9 +1360,10 @@ cudaError_t prepare_batch_step(int D, int M, lbm_precision prec) {
 }
 
 cudaError_t launch_batch_step(int D, int M, lbm_precision prec, const DomainDev* doms,
-                              int ndom, int nblocks, int nbblocks, int parity,
+                              int ndom, int nblocks, int nbblocks, int ncblocks, int parity,
                               cudaStream_t s) {
-#define CALL_BATCH(D_, M_, S_, R_) batch_impl<D_, M_, S_, R_>(doms, ndom, nblocks, nbblocks, parity, s)
+#define CALL_BATCH(D_, M_, S_, R_) \
+  batch_impl<D_, M_, S_, R_>(doms, ndom, nblocks, nbblocks, ncblocks, parity, s)
   LBM_DISPATCH(3, 9, CALL_BATCH)
   LBM_DISPATCH(3, 2, CALL_BATCH)
   LBM_DISPATCH(2, 9, CALL_BATCH)

@@ -72,6 +72,10 @@ class lbm_config(C.Structure):
     ]
 
 
+class lbm_launch(C.Structure):
+    _fields_ = [("chem_per_warp", C.c_int)]
+
+
 class lbm_info(C.Structure):
     _fields_ = [("Q", C.c_int), ("D", C.c_int), ("L", C.c_int), ("M", C.c_int),
                 ("n_nodes", C.c_longlong), ("c_ref", C.c_double), ("dt", C.c_double),
@@ -92,6 +96,10 @@ EXPORTS = {
     "lbm_batch_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.POINTER(C.c_void_p)]),
     "lbm_batch_run": (C.c_int, [C.c_void_p, C.c_int]),
     "lbm_batch_destroy": (C.c_int, [C.c_void_p]),
+    "lbm_batch_autotune": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(lbm_launch)]),
+    "lbm_set_launch": (C.c_int, [C.c_void_p, C.POINTER(lbm_launch)]),
+    "lbm_get_launch": (C.c_int, [C.c_void_p, C.POINTER(lbm_launch)]),
+    "lbm_autotune": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(lbm_launch)]),
     "lbm_moments": (C.c_int, [C.c_void_p] + [C.c_void_p] * 5 + [C.c_int]),
     "lbm_get_populations": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int]),
     "lbm_synchronize": (C.c_int, [C.c_void_p]),
@@ -237,21 +245,55 @@ def lbm_batch_step(handles, nsteps):
     _check(load_library().lbm_batch_step(hs, len(handles), int(nsteps)), hs[0])
 
 
+class BatchPlan:
+    """lbm_batch_t with the handles it was made for (errors of the plan's calls
+    are reported on its first handle)."""
+
+    def __init__(self, ptr, handles):
+        self._as_parameter_ = ptr
+        self.handles = handles
+
+
 def lbm_batch_create(handles):
     """Capture a batch plan (CUDA graphs of the batched step) for handles."""
     hs = (C.c_void_p * len(handles))(*[h.value if isinstance(h, C.c_void_p) else h
                                        for h in handles])
     out = C.c_void_p()
     _check(load_library().lbm_batch_create(hs, len(handles), C.byref(out)), hs[0])
-    return out
+    return BatchPlan(out, list(hs))
 
 
 def lbm_batch_run(plan, nsteps):
-    _check(load_library().lbm_batch_run(plan, int(nsteps)), None)
+    _check(load_library().lbm_batch_run(plan, int(nsteps)), plan.handles[0])
 
 
 def lbm_batch_destroy(plan):
-    _check(load_library().lbm_batch_destroy(plan), None)
+    _check(load_library().lbm_batch_destroy(plan), plan.handles[0])
+
+
+def lbm_batch_autotune(plan, trial_steps=3):
+    """Returns the chosen placement: {"chem_per_warp": 0 or 1}."""
+    out = lbm_launch()
+    _check(load_library().lbm_batch_autotune(plan, int(trial_steps), C.byref(out)),
+           plan.handles[0])
+    return {"chem_per_warp": out.chem_per_warp}
+
+
+def lbm_set_launch(h, chem_per_warp=-1):
+    l = lbm_launch(chem_per_warp=int(chem_per_warp))
+    _check(load_library().lbm_set_launch(h, C.byref(l)), h)
+
+
+def lbm_get_launch(h):
+    out = lbm_launch()
+    _check(load_library().lbm_get_launch(h, C.byref(out)), h)
+    return {"chem_per_warp": out.chem_per_warp}
+
+
+def lbm_autotune(h, trial_steps=3):
+    out = lbm_launch()
+    _check(load_library().lbm_autotune(h, int(trial_steps), C.byref(out)), h)
+    return {"chem_per_warp": out.chem_per_warp}
 
 
 def lbm_step_timed(h, nsteps, kernel_ms=None):
@@ -428,6 +470,15 @@ class Solver:
 
     def step(self, n=1):
         lbm_step(self.h, n)
+
+    def set_launch(self, chem_per_warp=-1):
+        lbm_set_launch(self.h, chem_per_warp)
+
+    def launch(self):
+        return lbm_get_launch(self.h)
+
+    def autotune(self, trial_steps=3):
+        return lbm_autotune(self.h, trial_steps)
 
     def moments(self):
         N, M = self.N, self.M

@@ -7,13 +7,18 @@ Requests (reactor, flame or channel solves of different grid sizes) arrive
 over time.  The loop admits a request as soon as it has arrived and its
 device memory (lbm_bytes_required) fits the remaining budget, initialises
 its populations on the GPU and keeps them resident.  Every tick advances all
-resident requests together with lbm_batch_step - one launch per kernel per
-step over the tiles of every request that shares a lattice and precision -
-for a chunk of steps no longer than the shortest remaining request, so no
-request runs past its step count.  A request that has completed its steps is
-read back (lbm_moments), its handle destroyed and its memory returned, and
-waiting requests are admitted at the next tick.  Reported: time-to-result
-(completion minus arrival) p50/p99 and aggregate node-updates/s.
+resident requests together: the requests that share a lattice and precision
+form a batch plan (lbm_batch_create: the batched kernels - one launch per
+kernel per step over the tiles of every request - captured as CUDA graphs),
+rebuilt only when the batch's membership changes and replayed for a chunk of
+steps no longer than the shortest remaining request, so no request runs past
+its step count.  A request that has completed its steps is read back
+(lbm_moments), its handle destroyed and its memory returned, and waiting
+requests are admitted at the next tick.  A request whose solve fails (a
+sticky device error such as a temperature Newton failure) is reported as
+failed with the library's message; the others are unaffected.  Reported:
+time-to-result (completion minus arrival) p50/p99 over the completed requests
+and aggregate node-updates/s.
 
 All arithmetic runs in the CUDA library; this module only schedules.
 """
@@ -44,6 +49,7 @@ class Request:
         self.admitted = None
         self.finished = None
         self.result = None
+        self.error = None
 
     @property
     def nodes(self):
@@ -88,6 +94,7 @@ class Server:
             if r.bytes > self.budget:
                 raise ValueError(f"request {r.rid} needs {r.bytes} B, above the budget")
         active, done = [], []
+        plans = {}          # batch key -> (handles of the plan, plan)
         t0 = clock()
         node_updates = 0
         while pending or active:
@@ -104,9 +111,14 @@ class Server:
             groups = {}
             for r in active:
                 groups.setdefault((r.w["lattice"], self.precision), []).append(r)
-            for grp in groups.values():
+            for key, grp in groups.items():
                 n = min(self.chunk, min(r.remaining for r in grp))
-                lbm.lbm_batch_step([r.solver.h for r in grp], n)
+                ids = tuple(r.rid for r in grp)
+                if key not in plans or plans[key][0] != ids:
+                    if key in plans:
+                        lbm.lbm_batch_destroy(plans[key][1])
+                    plans[key] = (ids, lbm.lbm_batch_create([r.solver.h for r in grp]))
+                lbm.lbm_batch_run(plans[key][1], n)
                 for r in grp:
                     r.remaining -= n
                     node_updates += n * r.nodes * (self.mech.n_species + 2)
@@ -115,10 +127,10 @@ class Server:
             still = []
             for r in active:
                 if r.remaining == 0:
-                    r.result = r.solver.moments()
-                    r.finished = clock() - t0
-                    r.solver.close()
-                    r.solver = None
+                    still_planned = [k for k, (ids, _p) in plans.items() if r.rid in ids]
+                    for k in still_planned:   # a plan must not outlive its handles
+                        lbm.lbm_batch_destroy(plans.pop(k)[1])
+                    self._finish(r, clock, t0)
                     self.used -= r.bytes
                     done.append(r)
                 else:
@@ -126,15 +138,33 @@ class Server:
             active = still
             if on_tick:
                 on_tick(now, active, pending, done)
+        for _ids, plan in plans.values():
+            lbm.lbm_batch_destroy(plan)
         self.elapsed = clock() - t0
         self.node_updates = node_updates
         return done
 
+    @staticmethod
+    def _finish(r, clock, t0):
+        try:
+            r.result = r.solver.moments()
+        except lbm.LBMError as e:
+            r.error = str(e)
+        r.finished = clock() - t0
+        try:
+            r.solver.close()
+        except lbm.LBMError:
+            pass
+        r.solver = None
+
 
 def summarize(done, elapsed, node_updates):
-    ttr = np.array([r.finished - r.arrival for r in done])
+    ok = [r for r in done if r.error is None]
+    ttr = np.array([r.finished - r.arrival for r in ok]) if ok else np.array([np.nan])
     return {
         "requests": len(done),
+        "failed": [{"request": r.rid, "kind": r.w.get("kind"), "error": r.error}
+                   for r in done if r.error is not None],
         "p50_time_to_result_s": float(np.percentile(ttr, 50)),
         "p99_time_to_result_s": float(np.percentile(ttr, 99)),
         "mean_time_to_result_s": float(ttr.mean()),
@@ -181,9 +211,7 @@ def main():
             r.solver.step(r.remaining)
             torch.cuda.synchronize()
             node_updates += r.remaining * r.nodes * (mech.n_species + 2)
-            r.result = r.solver.moments()
-            r.finished = time.perf_counter() - t0
-            r.solver.close()
+            Server._finish(r, time.perf_counter, t0)
             done.append(r)
         out = summarize(done, time.perf_counter() - t0, node_updates)
     else:

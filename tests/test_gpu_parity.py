@@ -42,10 +42,12 @@ def test_init_matches_oracle(lattice, shape, mechname):
     ("D3Q27", (10, 7, 5), 12),      # 350 nodes: three blocks and a ragged tail
     ("D2Q9", (23, 17, 1), 15),
 ])
-def test_perturbed_box_fp64(mech, lattice, shape, nsteps):
+@pytest.mark.parametrize("chem_per_warp", [0, 1])
+def test_perturbed_box_fp64(mech, lattice, shape, nsteps, chem_per_warp):
     w = perturbed_box(shape, lattice, mech=mech)
     o = make_oracle(mech, w)
     g = make_gpu(mech, w)
+    g.set_launch(chem_per_warp)
     o.step(nsteps)
     g.step(nsteps)
     err = max_rel_err_per_lattice(g.populations(), oracle_populations(o))

@@ -42,6 +42,7 @@ def test_results_alone_equal_results_in_the_mix(precision):
     done = srv.run(stream, on_tick=lambda now, act, pend, fin: used.append(srv.used))
     assert len(done) == len(stream)
     for r in done:
+        assert r.error is None, r.error
         w = r.w
         alone = lbm.Solver(mech, lattice=w["lattice"], shape=w["shape"], dx=w["dx"],
                            precision=precision, substeps=w["substeps"], T_max=w["T_max"],
@@ -71,5 +72,6 @@ def test_admission_waits_for_memory():
     resident = []
     done = srv.run(stream, on_tick=lambda now, act, pend, fin: resident.append(len(act)))
     assert len(done) == 4
+    assert all(r.error is None for r in done)
     assert max(resident) <= 1 + 0        # one at a time fits
     assert srv.used == 0
