@@ -298,14 +298,15 @@ def main():
     ms_per_step = total_ms / args.steps
     node_steps = N * args.steps * world
     # kernels per step: boundary (when the domain has interface nodes),
-    # moments, chemistry (warp-per-node placement), collision
+    # moments, chemistry (its own kernel when chem_lanes > 1), collision (one
+    # kernel, or two when split)
     launches_per_step = 2 + (1 if boundary_spec(w) else 0) + \
-        (1 if launch["chem_per_warp"] == 1 else 0)
+        (1 if launch["chem_lanes"] > 1 else 0) + (1 if launch["collide_split"] else 0)
     value = node_steps * (M + 2) / (total_ms * 1e-3)
 
     # roofline of the dominant kernel
-    chem_warp = launch["chem_per_warp"] == 1
-    names = ["k_moments+k_chem" if chem_warp else "k_moments", "k_collide"]
+    names = ["k_moments+k_chem" if launch["chem_lanes"] > 1 else "k_moments",
+             "k_prep+k_coll" if launch["collide_split"] else "k_collide"]
     dom = int(np.argmax(kms))
     dom_ms = kms[dom] / args.steps
     alg_bytes = 2 * info.L * info.Q * info.bytes_per_population   # per node-step

@@ -209,29 +209,35 @@ lbm_status lbm_batch_run(lbm_batch_t b, int nsteps);
 lbm_status lbm_batch_destroy(lbm_batch_t b);
 
 /* Kernel placement of a step.  A performance choice only: every placement
- * evaluates the same formulas in the same order, so results agree to the
- * last bit or to rounding.
- *   chem_per_warp  1: the reaction sub-steps (Sec. 2.4, Eq. R3) run in their
- *                  own kernel with one warp per node - lanes take the
- *                  reactions' rates of progress, then the species - for
- *                  grids too small to fill the GPU at one thread per node;
- *                  0: inside the moments kernel, one thread per node;
- *                  -1 (lbm_set_launch only, the default): chosen by grid size
- *                  (1 below 77,824 nodes, four 128-thread blocks per SM). */
+ * evaluates the same formulas; they agree to rounding.
+ *   chem_lanes     threads per node of the reaction sub-steps (Sec. 2.4,
+ *                  Eq. R3): 1 = inside the moments kernel; 4 or 8 = in their
+ *                  own kernel, the node's reactions dealt out over that many
+ *                  lanes (for grids too small to fill the GPU at one thread
+ *                  per node); -1 = by grid size.
+ *   collide_split  0 = one thread per node does the whole collision; 1 = a
+ *                  per-node kernel stores the collision parameters and a
+ *                  second kernel updates the directions with nine threads
+ *                  per node; -1 = default.
+ * Defaults: collide_split 1; chem_lanes 4 for FP32 storage below 77,824
+ * nodes (four 128-thread blocks per SM of a 152-SM GPU), else 1.
+ * lbm_set_launch rejects other values with LBM_ERR_INVALID. */
 typedef struct {
-  int chem_per_warp;
+  int chem_lanes;
+  int collide_split;
 } lbm_launch;
 
 /* Set / read the handle's placement (lbm_get_launch reports the resolved
- * value).  LBM_ERR_INVALID for a value out of range. */
+ * values). */
 lbm_status lbm_set_launch(lbm_t h, const lbm_launch* l);
 lbm_status lbm_get_launch(lbm_t h, lbm_launch* l);
 
-/* Autotuner: times trial_steps steps of every placement on the handle's own
- * state and keeps the fastest (written to *chosen when not NULL).  The trial
- * steps read the current populations and write the spare buffer without
- * advancing the handle; the temperature guesses they update are restored,
- * so the solve continues exactly as without the call.  Synchronises. */
+/* Autotuner: times trial_steps steps of each placement (chem_lanes 1, 4, 8
+ * x collide_split 0, 1) on the handle's own state and keeps the fastest
+ * (written to *chosen when not NULL).  The trial steps read the current
+ * populations and write the spare buffer without advancing the handle; the
+ * temperature guesses they update are restored, so the solve continues
+ * exactly as without the call.  Synchronises. */
 lbm_status lbm_autotune(lbm_t h, int trial_steps, lbm_launch* chosen);
 
 /* The same for a batch plan: times each placement over the whole batch, keeps

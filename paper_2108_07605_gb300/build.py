@@ -19,7 +19,17 @@ LIBDIR = os.path.join(HERE, "_lib")
 LIBNAME = "libpaper2108lbm.so"
 LIBPATH = os.path.join(LIBDIR, LIBNAME)
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["lbm_kernels.cu", "lbm_capi.cu", "lbm_noalloc.cu"]
+# (source, object, defines): the kernel templates are instantiated once per
+# (lattice, species count, precision) in their own translation unit, so the
+# longest compile is one instantiation, not all of them
+UNITS = [("lbm_capi.cu", "lbm_capi.o", []),
+         ("lbm_noalloc.cu", "lbm_noalloc.o", []),
+         ("lbm_dispatch.cu", "lbm_dispatch.o", [])]
+for _d, _m in ((3, 9), (3, 2), (2, 9), (2, 2)):
+    for _f64, _tag in ((1, "f64"), (0, "f32")):
+        UNITS.append(("lbm_inst.cu", f"lbm_inst_{_d}_{_m}_{_tag}.o",
+                      [f"-DLBM_D={_d}", f"-DLBM_M={_m}", f"-DLBM_F64={_f64}",
+                       f"-DLBM_KSET=kernel_set_{_d}_{_m}_{_tag}"]))
 
 
 def nvcc():
@@ -53,16 +63,20 @@ def build(force=False, verbose=False):
     if verbose:
         common += ["-Xptxas", "-v"]
 
-    def compile_one(src):
-        obj = os.path.join(LIBDIR, os.path.splitext(src)[0] + ".o")
-        cmd = [cc] + common + ["-c", os.path.join(CSRC, src), "-o", obj]
+    def compile_one(unit):
+        src, objname, defs = unit
+        obj = os.path.join(LIBDIR, objname)
+        cmd = [cc] + common + defs + ["-c", os.path.join(CSRC, src), "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
-            raise RuntimeError(f"nvcc failed for {src}:\n{r.stdout}\n{r.stderr}")
+            raise RuntimeError(f"nvcc failed for {objname}:\n{r.stdout}\n{r.stderr}")
         return obj, r.stderr
 
-    with cf.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
-        results = list(ex.map(compile_one, SOURCES))
+    # the longest units first
+    order = sorted(UNITS, key=lambda u: ("_3_9_" not in u[1], "lbm_inst" not in u[1]))
+    workers = max(1, min(len(UNITS), os.cpu_count() or 1))
+    with cf.ThreadPoolExecutor(max_workers=workers) as ex:
+        results = list(ex.map(compile_one, order))
     if verbose:
         for _, log in results:
             sys.stderr.write(log)

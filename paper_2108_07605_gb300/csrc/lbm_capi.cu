@@ -32,7 +32,8 @@ struct lbm_ctx {
   size_t bytes = 0;
   long long steps = 0;
   bool initialized = false;
-  int chem_warp_opt = -1;   // lbm_launch.chem_per_warp as set (-1: by grid size)
+  lbm_launch opt = {-1, -1};  // placement as set (-1: by grid size)
+  void* cpar = nullptr;     // per-node collision parameters (split collision)
   std::string err;
 };
 
@@ -49,23 +50,34 @@ lbm_status cuda_fail(lbm_ctx* h, cudaError_t e, const char* where) {
   return fail(h, LBM_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
 }
 
-// Grids below this many nodes run the reaction sub-steps one warp per node:
-// at one thread per node they would hold fewer than four 128-thread blocks
-// per SM of a 152-SM GB300, too few warps to hide the latency of the long
-// per-node chemistry.
-constexpr long long kChemWarpBelow = 152LL * 4 * 128;
+// Default placement.  The split collision measured faster than the fused
+// one on every grid tried (FP32 and FP64, 16k to 524k nodes).  Below
+// kSmallGrid nodes a thread-per-node grid holds fewer than four 128-thread
+// blocks per SM of a 152-SM GB300, too few warps to hide the latency of the
+// float-float chemistry, which then runs with four lanes per node; in FP64
+// the extra redundant work of the lanes costs more than it hides.
+constexpr long long kSmallGrid = 152LL * 4 * 128;
 
-int resolve_chem_warp(int opt, long long nodes) {
-  return opt >= 0 ? opt : (nodes < kChemWarpBelow ? 1 : 0);
+Launch resolve_launch(const lbm_launch& opt, long long nodes, lbm_precision prec) {
+  Launch lc;
+  const bool small = nodes < kSmallGrid;
+  lc.chem_lanes = opt.chem_lanes > 0 ? opt.chem_lanes
+                                     : (small && prec == LBM_FP32_STORE ? 4 : 1);
+  lc.coll_split = opt.collide_split >= 0 ? opt.collide_split : 1;
+  return lc;
 }
+
+// every placement the autotuners try
+const Launch kCandidates[] = {{1, 0}, {4, 0}, {8, 0}, {1, 1}, {4, 1}, {8, 1}};
 
 // Domains of a batched step: each handle's tiles follow the previous
 // handle's in every grid (128 nodes per node-kernel block, 4 interface nodes
-// per boundary block, kChemNodesPerBlock nodes per chemistry block).
-void fill_domains(lbm_ctx* const* hs, int n, int chem_warp, std::vector<DomainDev>& doms,
-                  int& nblocks, int& nbblocks, int& ncblocks) {
+// per boundary block, 128 / chem_lanes nodes per chemistry block, 32 nodes
+// per split-collision block).
+void fill_domains(lbm_ctx* const* hs, int n, const Launch& lc, std::vector<DomainDev>& doms,
+                  BatchGrids& gr) {
   doms.assign(n, DomainDev());
-  nblocks = nbblocks = ncblocks = 0;
+  gr = BatchGrids();
   for (int k = 0; k < n; ++k) {
     lbm_ctx* h = hs[k];
     DomainDev& d = doms[k];
@@ -73,18 +85,25 @@ void fill_domains(lbm_ctx* const* hs, int n, int chem_warp, std::vector<DomainDe
     d.pops[1] = h->pops[1];
     d.cur0 = h->cur;
     d.rec = h->rec;
+    d.cpar = h->cpar;
     d.Tf = h->Tf;
     d.status = h->status;
     d.g = h->g;
     d.un = h->un;
     d.bc = h->bc;
     d.mech = h->mech_dev;
-    d.block_begin = nblocks;
-    d.bblock_begin = nbblocks;
-    d.cblock_begin = ncblocks;
-    nblocks += (int)((h->g.N + 127) / 128);
-    nbblocks += (h->bc.n_if + 3) / 4;
-    if (chem_warp) ncblocks += (int)((h->g.N + kChemNodesPerBlock - 1) / kChemNodesPerBlock);
+    d.block_begin = gr.nblocks;
+    d.bblock_begin = gr.nbblocks;
+    d.cblock_begin = gr.ncblocks;
+    d.kblock_begin = gr.nkblocks;
+    gr.nblocks += (int)((h->g.N + 127) / 128);
+    gr.nbblocks += (h->bc.n_if + 3) / 4;
+    if (lc.chem_lanes > 1) {
+      const int per = 128 / lc.chem_lanes;
+      gr.ncblocks += (int)((h->g.N + per - 1) / per);
+    }
+    if (lc.coll_split)
+      gr.nkblocks += (int)((h->g.N + kCollNodesPerBlock - 1) / kCollNodesPerBlock);
   }
 }
 
@@ -335,7 +354,7 @@ HostBC classify(const lbm_config& c, double c_ref) {
 size_t align256(size_t b) { return (b + 255) / 256 * 256; }
 
 struct Sizes {
-  size_t pops, rec, tf, status, io, bc, total;
+  size_t pops, rec, cpar, tf, status, io, bc, total;
 };
 
 Sizes sizes_for(const lbm_config& c, const HostBC& hb) {
@@ -346,6 +365,7 @@ Sizes sizes_for(const lbm_config& c, const HostBC& hb) {
   Sizes s;
   s.pops = (size_t)(M + 1) * Q * N * elem_size(c.precision);
   s.rec = (size_t)record_fields(D, M) * N * elem_size(c.precision);
+  s.cpar = (size_t)collide_param_fields(D, M) * N * elem_size(c.precision);
   s.tf = (size_t)N * sizeof(double);
   s.status = 256;
   s.io = 0;
@@ -355,7 +375,7 @@ Sizes sizes_for(const lbm_config& c, const HostBC& hb) {
     s.bc = align256(N * sizeof(int)) + 3 * align256(nif * sizeof(int)) +
            4 * align256(nif * sizeof(double)) + align256((size_t)(M + 1) * Q * nif * sizeof(double));
   }
-  s.total = 2 * s.pops + s.rec + s.tf + s.status + s.bc;
+  s.total = 2 * s.pops + s.rec + s.cpar + s.tf + s.status + s.bc;
   return s;
 }
 
@@ -533,6 +553,7 @@ lbm_status lbm_create(const lbm_config* cfg, lbm_t* out) {
   h->pops[0] = dalloc(h->cfg, s.pops);
   h->pops[1] = dalloc(h->cfg, s.pops);
   h->rec = static_cast<double*>(dalloc(h->cfg, s.rec));
+  h->cpar = dalloc(h->cfg, s.cpar);
   h->Tf = static_cast<double*>(dalloc(h->cfg, s.tf));
   h->status = static_cast<int*>(dalloc(h->cfg, s.status));
   h->bytes = s.total;
@@ -601,7 +622,7 @@ lbm_status lbm_create(const lbm_config* cfg, lbm_t* out) {
     b.rho_in = cfg->inlet_T > 0.0 ? cfg->inlet_P / (Rin * cfg->inlet_T) : 0.0;
     b.theta_in = Rin * cfg->inlet_T * h->un.inv_c2;
   }
-  if (!h->pops[0] || !h->pops[1] || !h->rec || !h->Tf || !h->status) {
+  if (!h->pops[0] || !h->pops[1] || !h->rec || !h->cpar || !h->Tf || !h->status) {
     lbm_destroy(h);
     return fail(nullptr, LBM_ERR_OOM, "device allocation failed");
   }
@@ -636,8 +657,9 @@ lbm_status lbm_step(lbm_t h, int nsteps) {
   a.g = h->g;
   a.un = h->un;
   a.bc = h->bc;
-  a.chem_warp = resolve_chem_warp(h->chem_warp_opt, h->g.N);
+  a.lc = resolve_launch(h->opt, h->g.N, h->cfg.precision);
   a.mech_dev = h->mech_dev;
+  a.cpar = h->cpar;
   for (int k = 0; k < nsteps; ++k) {
     a.src = h->pops[h->cur];
     a.dst = h->pops[1 - h->cur];
@@ -665,8 +687,9 @@ lbm_status lbm_step_timed(lbm_t h, int nsteps, double* kernel_ms, int n_kernels)
   a.g = h->g;
   a.un = h->un;
   a.bc = h->bc;
-  a.chem_warp = resolve_chem_warp(h->chem_warp_opt, h->g.N);
+  a.lc = resolve_launch(h->opt, h->g.N, h->cfg.precision);
   a.mech_dev = h->mech_dev;
+  a.cpar = h->cpar;
   cudaError_t err = cudaSuccess;
   for (int k = 0; k < nsteps && err == cudaSuccess; ++k) {
     a.src = h->pops[h->cur];
@@ -695,15 +718,19 @@ lbm_status lbm_step_timed(lbm_t h, int nsteps, double* kernel_ms, int n_kernels)
 
 lbm_status lbm_set_launch(lbm_t h, const lbm_launch* l) {
   if (!h || !l) return fail(h, LBM_ERR_INVALID, "handle or launch is NULL");
-  if (l->chem_per_warp < -1 || l->chem_per_warp > 1)
-    return fail(h, LBM_ERR_INVALID, "chem_per_warp must be -1, 0 or 1");
-  h->chem_warp_opt = l->chem_per_warp;
+  if (l->chem_lanes != -1 && l->chem_lanes != 1 && l->chem_lanes != 4 && l->chem_lanes != 8)
+    return fail(h, LBM_ERR_INVALID, "chem_lanes must be -1, 1, 4 or 8");
+  if (l->collide_split < -1 || l->collide_split > 1)
+    return fail(h, LBM_ERR_INVALID, "collide_split must be -1, 0 or 1");
+  h->opt = *l;
   return LBM_OK;
 }
 
 lbm_status lbm_get_launch(lbm_t h, lbm_launch* l) {
   if (!h || !l) return fail(h, LBM_ERR_INVALID, "handle or launch is NULL");
-  l->chem_per_warp = resolve_chem_warp(h->chem_warp_opt, h->g.N);
+  const Launch lc = resolve_launch(h->opt, h->g.N, h->cfg.precision);
+  l->chem_lanes = lc.chem_lanes;
+  l->collide_split = lc.coll_split;
   return LBM_OK;
 }
 
@@ -733,10 +760,13 @@ lbm_status lbm_autotune(lbm_t h, int trial_steps, lbm_launch* chosen) {
   a.un = h->un;
   a.bc = h->bc;
   a.mech_dev = h->mech_dev;
+  a.cpar = h->cpar;
   float best_ms = 0.f;
-  int best = 0;
-  for (int cand = 0; cand < 2 && e == cudaSuccess; ++cand) {
-    a.chem_warp = cand;
+  Launch best;
+  bool first = true;
+  for (const Launch& cand : kCandidates) {
+    if (e != cudaSuccess) break;
+    a.lc = cand;
     e = launch_step(h->D, h->M, h->cfg.precision, h->mech, a, h->stream);   // warm-up
     if (e == cudaSuccess) e = cudaEventRecord(e0, h->stream);
     for (int t = 0; t < trial_steps && e == cudaSuccess; ++t)
@@ -747,9 +777,10 @@ lbm_status lbm_autotune(lbm_t h, int trial_steps, lbm_launch* chosen) {
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     float ms = 0.f;
     if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
-    if (e == cudaSuccess && (cand == 0 || ms < best_ms)) {
+    if (e == cudaSuccess && (first || ms < best_ms)) {
       best_ms = ms;
       best = cand;
+      first = false;
     }
   }
   if (e0) cudaEventDestroy(e0);
@@ -757,8 +788,9 @@ lbm_status lbm_autotune(lbm_t h, int trial_steps, lbm_launch* chosen) {
   cudaStreamSynchronize(h->stream);
   dfree(h->cfg, Tsave);
   if (e != cudaSuccess) return cuda_fail(h, e, "autotune");
-  h->chem_warp_opt = best;
-  if (chosen) chosen->chem_per_warp = best;
+  h->opt.chem_lanes = best.chem_lanes;
+  h->opt.collide_split = best.coll_split;
+  if (chosen) *chosen = h->opt;
   return LBM_OK;
 }
 
@@ -781,9 +813,9 @@ lbm_status lbm_batch_step(lbm_t* hs, int n, int nsteps) {
   if (nsteps == 0) return LBM_OK;
   DeviceGuard dg(h0->cfg.device);
   std::vector<DomainDev> doms;
-  int nblocks = 0, nbblocks = 0, ncblocks = 0;
-  fill_domains(hs, n, resolve_chem_warp(-1, total_nodes(hs, n)), doms, nblocks, nbblocks,
-               ncblocks);
+  BatchGrids gr;
+  const Launch lc = resolve_launch(lbm_launch{-1, -1}, total_nodes(hs, n), hs[0]->cfg.precision);
+  fill_domains(hs, n, lc, doms, gr);
   // every handle's earlier work precedes the batch; the batch runs on the
   // first handle's stream and each handle's stream waits for it afterwards
   cudaStream_t s0 = h0->stream;
@@ -799,8 +831,7 @@ lbm_status lbm_batch_step(lbm_t* hs, int n, int nsteps) {
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(ddev, doms.data(), n * sizeof(DomainDev), cudaMemcpyHostToDevice, s0);
   for (int step = 0; step < nsteps && e == cudaSuccess; ++step)
-    e = launch_batch_step(h0->D, h0->M, h0->cfg.precision, ddev, n, nblocks, nbblocks,
-                          ncblocks, step & 1, s0);
+    e = launch_batch_step(h0->D, h0->M, h0->cfg.precision, ddev, n, gr, lc, step & 1, s0);
   if (e == cudaSuccess) e = cudaEventRecord(ev, s0);
   for (int k = 1; k < n && e == cudaSuccess; ++k)
     if (hs[k]->stream != s0) e = cudaStreamWaitEvent(hs[k]->stream, ev, 0);
@@ -823,8 +854,8 @@ struct lbm_batch_ctx {
   std::vector<lbm_ctx*> hs;
   std::vector<int> cur;        // each handle's buffer parity the plan expects
   DomainDev* ddev = nullptr;
-  int nblocks = 0, nbblocks = 0, ncblocks = 0;
-  int chem_warp = 0;           // reaction sub-steps one warp per node
+  BatchGrids gr;
+  Launch lc;                   // placement of the captured step
   int parity = 0;
   cudaStream_t stream = nullptr;
   cudaGraphExec_t one[2] = {nullptr, nullptr}, two[2] = {nullptr, nullptr};
@@ -834,8 +865,7 @@ namespace {
 
 cudaError_t batch_upload(lbm_batch_ctx* b) {
   std::vector<DomainDev> doms;
-  fill_domains(b->hs.data(), (int)b->hs.size(), b->chem_warp, doms, b->nblocks, b->nbblocks,
-               b->ncblocks);
+  fill_domains(b->hs.data(), (int)b->hs.size(), b->lc, doms, b->gr);
   for (size_t k = 0; k < b->hs.size(); ++k) b->cur[k] = b->hs[k]->cur;
   b->parity = 0;
   cudaError_t e = cudaMemcpyAsync(b->ddev, doms.data(), doms.size() * sizeof(DomainDev),
@@ -849,9 +879,8 @@ cudaError_t batch_capture(lbm_batch_ctx* b, int first_parity, int nsteps, cudaGr
   cudaGraph_t graph = nullptr;
   cudaError_t e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
   for (int k = 0; k < nsteps && e == cudaSuccess; ++k)
-    e = launch_batch_step(h0->D, h0->M, h0->cfg.precision, b->ddev, (int)b->hs.size(),
-                          b->nblocks, b->nbblocks, b->ncblocks, (first_parity + k) & 1,
-                          b->stream);
+    e = launch_batch_step(h0->D, h0->M, h0->cfg.precision, b->ddev, (int)b->hs.size(), b->gr,
+                          b->lc, (first_parity + k) & 1, b->stream);
   const cudaError_t e2 = cudaStreamEndCapture(b->stream, &graph);
   if (e == cudaSuccess) e = e2;
   if (e == cudaSuccess) e = cudaGraphInstantiate(out, graph, 0);
@@ -907,7 +936,7 @@ lbm_status lbm_batch_create(lbm_t* hs, int n, lbm_batch_t* out) {
     b->ddev = static_cast<DomainDev*>(dalloc(h0->cfg, n * sizeof(DomainDev)));
     if (!b->ddev) e = cudaErrorMemoryAllocation;
   }
-  b->chem_warp = resolve_chem_warp(-1, total_nodes(hs, n));
+  b->lc = resolve_launch(lbm_launch{-1, -1}, total_nodes(hs, n), hs[0]->cfg.precision);
   if (e == cudaSuccess) e = batch_upload(b);
   if (e == cudaSuccess) e = prepare_batch_step(h0->D, h0->M, h0->cfg.precision);
   if (e == cudaSuccess) e = batch_capture_all(b);
@@ -979,19 +1008,21 @@ lbm_status lbm_batch_autotune(lbm_batch_t b, int trial_steps, lbm_launch* chosen
   if (e == cudaSuccess) e = cudaEventCreate(&e0);
   if (e == cudaSuccess) e = cudaEventCreate(&e1);
   float best_ms = 0.f;
-  int best = 0;
-  for (int cand = 0; cand < 2 && e == cudaSuccess; ++cand) {
-    b->chem_warp = cand;
+  Launch best = b->lc;
+  bool first = true;
+  for (const Launch& cand : kCandidates) {
+    if (e != cudaSuccess) break;
+    b->lc = cand;
     e = batch_upload(b);
     // parity 0 every time: each trial step recomputes the next state of every
     // handle from its current buffer, advancing none of them
     if (e == cudaSuccess)
-      e = launch_batch_step(h0->D, h0->M, h0->cfg.precision, b->ddev, n, b->nblocks,
-                            b->nbblocks, b->ncblocks, 0, b->stream);
+      e = launch_batch_step(h0->D, h0->M, h0->cfg.precision, b->ddev, n, b->gr, b->lc, 0,
+                            b->stream);
     if (e == cudaSuccess) e = cudaEventRecord(e0, b->stream);
     for (int t = 0; t < trial_steps && e == cudaSuccess; ++t)
-      e = launch_batch_step(h0->D, h0->M, h0->cfg.precision, b->ddev, n, b->nblocks,
-                            b->nbblocks, b->ncblocks, 0, b->stream);
+      e = launch_batch_step(h0->D, h0->M, h0->cfg.precision, b->ddev, n, b->gr, b->lc, 0,
+                            b->stream);
     if (e == cudaSuccess) e = cudaEventRecord(e1, b->stream);
     for (int k = 0; k < n && e == cudaSuccess; ++k)
       e = cudaMemcpyAsync(b->hs[k]->Tf, Tsave[k], (size_t)b->hs[k]->g.N * sizeof(double),
@@ -999,9 +1030,10 @@ lbm_status lbm_batch_autotune(lbm_batch_t b, int trial_steps, lbm_launch* chosen
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
     float ms = 0.f;
     if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
-    if (e == cudaSuccess && (cand == 0 || ms < best_ms)) {
+    if (e == cudaSuccess && (first || ms < best_ms)) {
       best_ms = ms;
       best = cand;
+      first = false;
     }
   }
   if (e0) cudaEventDestroy(e0);
@@ -1009,12 +1041,15 @@ lbm_status lbm_batch_autotune(lbm_batch_t b, int trial_steps, lbm_launch* chosen
   cudaStreamSynchronize(b->stream);
   for (int k = 0; k < n; ++k) dfree(h0->cfg, Tsave[k]);
   if (e == cudaSuccess) {
-    b->chem_warp = best;
+    b->lc = best;
     e = batch_upload(b);
   }
   if (e == cudaSuccess) e = batch_capture_all(b);
   if (e != cudaSuccess) return cuda_fail(h0, e, "batch autotune");
-  if (chosen) chosen->chem_per_warp = best;
+  if (chosen) {
+    chosen->chem_lanes = best.chem_lanes;
+    chosen->collide_split = best.coll_split;
+  }
   return LBM_OK;
 }
 
@@ -1153,6 +1188,7 @@ lbm_status lbm_destroy(lbm_t h) {
   dfree(h->cfg, h->pops[0]);
   dfree(h->cfg, h->pops[1]);
   dfree(h->cfg, h->rec);
+  dfree(h->cfg, h->cpar);
   dfree(h->cfg, h->Tf);
   dfree(h->cfg, h->status);
   dfree(h->cfg, h->io);

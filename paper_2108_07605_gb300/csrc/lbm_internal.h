@@ -1,5 +1,5 @@
 // Internal declarations shared by the host API (lbm_capi.cu) and the kernels
-// (lbm_kernels.cu).  Not part of the C ABI.
+// (lbm_kernels.cuh and its instantiations).  Not part of the C ABI.
 #pragma once
 
 #include <cstddef>
@@ -78,7 +78,7 @@ struct Geom {
   long long N;
 };
 
-// Kernel launchers (lbm_kernels.cu).  `S` is the storage type.
+// Kernel launchers (lbm_dispatch.cu).  `S` is the storage type.
 // Boundary data of a handle (Sec. 4).  tag == nullptr: periodic box, no
 // interface or solid nodes.
 constexpr int TAG_BULK = -1;
@@ -102,6 +102,12 @@ struct BCDev {
   double p_out_lat = 0.0, sigma = 0.25;
 };
 
+// Kernel placement of a step (lbm_launch, resolved).
+struct Launch {
+  int chem_lanes = 1;    // 1: chemistry inside the moments kernel; 4 or 8: k_chem lanes per node
+  int coll_split = 0;    // 0: fused collision; 1: k_prep + k_coll
+};
+
 struct StepArgs {
   const void* src = nullptr;
   void* dst = nullptr;
@@ -111,8 +117,9 @@ struct StepArgs {
   Geom g;
   Units un;
   BCDev bc;                    // default: periodic box
-  int chem_warp = 0;           // reaction sub-steps in k_chem (one warp per node)
+  Launch lc;                   // default: chemistry and collision one thread per node
   const DevMech* mech_dev = nullptr;   // device copy of the mechanism (k_chem)
+  void* cpar = nullptr;        // per-node collision parameters [NF][N] (split collision)
 };
 
 // One domain of a batched step (lbm_batch_step): every block of the batched
@@ -128,22 +135,53 @@ struct DomainDev {
   Units un;
   BCDev bc;
   const DevMech* mech = nullptr;   // device copy of the handle's mechanism
+  void* cpar = nullptr;        // per-node collision parameters (split collision)
   int block_begin = 0;         // first block of this domain in the node grids
   int bblock_begin = 0;        // first block in the boundary grid
-  int cblock_begin = 0;        // first block in the warp-per-node chemistry grid
+  int cblock_begin = 0;        // first block in the chemistry grid (k_chem)
+  int kblock_begin = 0;        // first block in the split-collision grid (k_coll)
 };
 
-// Batched step: doms is a device array of ndom domains sharing (D, M, prec);
-// nblocks / nbblocks / ncblocks are the totals of the node, boundary and
-// chemistry grids (ncblocks = 0: reaction sub-steps inside the moments kernel).
+// Block totals of the batched grids.
+struct BatchGrids {
+  int nblocks = 0;    // node kernels, 128 nodes per block
+  int nbblocks = 0;   // boundary kernel, 4 interface nodes per block
+  int ncblocks = 0;   // k_chem, 128 / chem_lanes nodes per block (0 without it)
+  int nkblocks = 0;   // k_coll, 32 nodes per block (0 without it)
+};
+
+// Batched step: doms is a device array of ndom domains sharing (D, M, prec)
+// and laid out for the placement lc.
 cudaError_t launch_batch_step(int D, int M, lbm_precision prec, const DomainDev* doms,
-                              int ndom, int nblocks, int nbblocks, int ncblocks, int parity,
+                              int ndom, const BatchGrids& gr, const Launch& lc, int parity,
                               cudaStream_t s);
-// nodes per block of the warp-per-node chemistry kernel
-constexpr int kChemNodesPerBlock = 4;
-// Set the batched kernels' attributes (large shared memory) ahead of a
-// stream capture, where such calls are not recorded.
+// nodes per block of the split-collision kernel k_coll
+constexpr int kCollNodesPerBlock = 32;
+// fields of the per-node collision parameters (split collision)
+int collide_param_fields(int D, int M);
+// Set the kernels' attributes (large shared memory) ahead of a stream
+// capture, where such calls are not recorded.
 cudaError_t prepare_batch_step(int D, int M, lbm_precision prec);
+
+// Host entry points of one instantiation (lattice, species count, precision)
+// of the kernel templates; see lbm_inst.cu.
+struct KernelSet {
+  cudaError_t (*step)(const DevMech& mech, const StepArgs& a, cudaStream_t s, int which);
+  cudaError_t (*batch)(const DomainDev* doms, int ndom, const BatchGrids& gr, const Launch& lc,
+                       int parity, cudaStream_t s);
+  cudaError_t (*prepare)();
+  cudaError_t (*init)(const DevMech& mech, const Geom& g, const Units& un,
+                      const double* rho_or_P, int is_pressure, const double* u,
+                      const double* T, const double* Y, void* pops, double* Tfield,
+                      int* status, cudaStream_t s);
+  cudaError_t (*out)(const DevMech& mech, const Geom& g, const Units& un, const void* pops,
+                     const double* Tfield, double* rho, double* u, double* T, double* Y,
+                     double* E, int* status, cudaStream_t s);
+  int record_fields;   // moment-record fields
+  int param_fields;    // collision-parameter fields
+};
+// nullptr for an unsupported combination
+const KernelSet* kernel_set(int D, int M, lbm_precision prec);
 
 // which: 0 = moments kernel only, 1 = collision kernel only, -1 = both.
 cudaError_t launch_step(int D, int M, lbm_precision prec, const DevMech& mech,

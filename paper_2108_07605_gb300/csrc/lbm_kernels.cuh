@@ -1,4 +1,5 @@
-// Kernels of the reactive-mixture LBM step (thread per node).
+// Kernels of the reactive-mixture LBM step (templates; instantiated per
+// lattice, species count and precision by lbm_inst.cu).
 //
 //   k_moments   pull-stream all lattices, moments, temperature Newton,
 //               write the per-node moment record (scratch) and T guess.
@@ -11,7 +12,10 @@
 // Template parameters: D (2 or 3), M (species), S (storage type), RT (type
 // of the lattice arithmetic: moments, equilibria, collision).  Temperature,
 // transport, diffusion velocities and chemistry always run in FP64.
+#include <atomic>
 #include <cmath>
+
+#pragma once
 
 #include "lbm_device.cuh"
 
@@ -57,11 +61,6 @@ constexpr int kBS = 128;
 // (tables only in the FP32 path: in FP64 they would halve the occupancy)
 template <int D, int M, typename RT> constexpr int collide_smem_entries() {
   return (sizeof(RT) == 4 && 2 * M * D * 3 > M * M) ? 2 * M * D * 3 : M * M;
-}
-
-template <typename R>
-__device__ __forceinline__ R pick3(int c, const R (&v)[3]) {
-  return c == 0 ? v[1] : (c > 0 ? v[2] : v[0]);
 }
 
 template <int D>
@@ -257,12 +256,20 @@ __device__ __forceinline__ void moments_body(const S* __restrict__ src, RT* __re
 }
 
 // ---------------------------------------------------------------------------
-// Reaction sub-steps with one warp per node (Sec. 2.4 Eq. R3), for grids too
-// small to fill the GPU at one thread per node: the lanes take the reactions'
-// rates of progress, then lanes a < M sum them into the species production
-// rates and advance rho_a.  The formulas and their order of evaluation are
-// those of production_rates / production_rates_ff, so both placements give
-// the same increments.  CT: double (FP64 path) or float-float (mixed path).
+// Reaction sub-steps with several lanes per node (Sec. 2.4 Eq. R3), for
+// grids too small to fill the GPU at one thread per node: the node's
+// reactions are dealt out over the lanes, which cuts the latency of a node's
+// chemistry by about the lane count.  The formulas are those of
+// production_rates / production_rates_ff; only the production rates are
+// summed in another order (partial sums per lane), so the placements agree
+// to rounding.  CT: double (FP64 path) or float-float (mixed path).
+__device__ __forceinline__ double shfl_xor_ct(unsigned mask, double v, int o) {
+  return __shfl_xor_sync(mask, v, o);
+}
+__device__ __forceinline__ ff shfl_xor_ct(unsigned mask, ff v, int o) {
+  return ff(__shfl_xor_sync(mask, v.hi, o), __shfl_xor_sync(mask, v.lo, o));
+}
+
 template <typename CT> struct Chem;
 template <> struct Chem<double> {
   __device__ static double ex(double x) { return exp(x); }
@@ -327,27 +334,21 @@ template <> struct Chem<ff> {
 template <typename RT> struct ChemType { using type = double; };
 template <> struct ChemType<float> { using type = ff; };
 
-// warp scratch entries of k_chem: r, C, G per species and q per reaction
-constexpr int kChemScratch = 3 * LBM_MAX_SPECIES + LBM_MAX_REACTIONS;
-
-template <int D, int M, typename RT>
-__device__ __forceinline__ void chem_warp_body(RT* __restrict__ rec,
-                                               const double* __restrict__ Tf,
-                                               int* __restrict__ status, long long N,
-                                               const int* __restrict__ tag, const Units& un,
-                                               const DevMech& m, long long n, int lane,
-                                               typename ChemType<RT>::type* __restrict__ sc) {
+// Reaction sub-steps of node n by a group of L lanes (L = 4 or 8, aligned
+// within the warp): every lane forms the node's state, temperature,
+// concentrations and Gibbs functions; lane `sub` takes the reactions
+// k = sub, sub + L, ...; the species production rates are summed across the
+// group with shuffles, after which every lane holds the same densities.
+template <int D, int M, typename RT, int L>
+__device__ __forceinline__ void chem_lanes_body(RT* __restrict__ rec,
+                                                const double* __restrict__ Tf,
+                                                int* __restrict__ status, long long N,
+                                                const int* __restrict__ tag, const Units& un,
+                                                const DevMech& m, long long n, int sub,
+                                                unsigned gmask) {
   using CT = typename ChemType<RT>::type;
   using X = Chem<CT>;
   using RC = Rec<D, M>;
-  if (n >= N) return;
-  if (tag && tag[n] == TAG_SOLID) return;
-  CT* r = sc;
-  CT* C = sc + LBM_MAX_SPECIES;
-  CT* G = sc + 2 * LBM_MAX_SPECIES;
-  CT* q = sc + 3 * LBM_MAX_SPECIES;
-  // the node's post-stream species densities and internal energy, as the
-  // moments kernel formed them
   const RT rho = rec[RC::RHO * N + n];
   RT usq = RT(0);
 #pragma unroll
@@ -359,38 +360,37 @@ __device__ __forceinline__ void chem_warp_body(RT* __restrict__ rec,
   CT U;
   if constexpr (sizeof(RT) == 4) U = (ff(ER) + ff(-0.5f * usq)) * un.c2_f;
   else U = (double(ER) - 0.5 * double(usq)) * un.c * un.c;
-  CT r0 = CT();
-  if (lane < M - 1) {
-    const RT v = rec[(RC::DRHO + lane) * N + n];
-    r0 = X::of(v);
-    r[lane] = r0;
-  } else if (lane == M - 1) {
-    RT last = rho;
+  // the post-stream species densities the moments kernel left in the
+  // increment slots; the slaved species from the mixture density
+  CT r[M], r0[M - 1];
+  RT last = rho;
 #pragma unroll
-    for (int a = 0; a < M - 1; ++a) last -= rec[(RC::DRHO + a) * N + n];
-    r[lane] = X::of(last);
+  for (int a = 0; a < M - 1; ++a) {
+    const RT v = rec[(RC::DRHO + a) * N + n];
+    last -= v;
+    r0[a] = X::of(v);
+    r[a] = r0[a];
   }
-  __syncwarp();
+  r[M - 1] = X::of(last);
   const CT rho_c = X::of(rho);
   CT Ts = X::of_T(Tf[n]);
   for (int s = 0; s < un.substeps; ++s) {
     if (s > 0) {
-      CT rl[M];
-#pragma unroll
-      for (int a = 0; a < M; ++a) rl[a] = r[a];
       bool ok;
-      Ts = X::template newton<M>(m, rl, rho_c, U, Ts, un, ok);
-      if (!ok && lane == 0) atomicOr(status, ST_NEWTON);
+      Ts = X::template newton<M>(m, r, rho_c, U, Ts, un, ok);
+      if (!ok && sub == 0) atomicOr(status, ST_NEWTON);
     }
     const CT lnT = X::ln(Ts);
     const CT invT = X::inv(Ts);
-    if (lane < M) {
-      C[lane] = r[lane] * X::inv_mm(m, lane);
-      G[lane] = X::gibbs(m, lane, Ts, invT, lnT);
+    CT C[M], G[M], w[M];
+#pragma unroll
+    for (int a = 0; a < M; ++a) {
+      C[a] = r[a] * X::inv_mm(m, a);
+      G[a] = X::gibbs(m, a, Ts, invT, lnT);
+      w[a] = CT();
     }
-    __syncwarp();
     const CT lp = X::ln_p0(m) - lnT;   // ln(P0 / (R_U T))
-    for (int k = lane; k < m.R; k += 32) {
+    for (int k = sub; k < m.R; k += L) {
       const DevReaction& rx = m.rx[k];
       const CT lk = X::lnkf(rx, lnT, invT);
       CT fwd = X::ex(lk);
@@ -403,32 +403,29 @@ __device__ __forceinline__ void chem_warp_body(RT* __restrict__ rec,
         rev = X::ex(X::rev_arg(rx, lk, dG, lp));
         for (int j = 0; j < rx.np; ++j) rev *= C[rx.prod[j]];
       }
-      CT qk = fwd - rev;
+      CT q = fwd - rev;
       if (rx.third_body) {
         CT cm = CT();
 #pragma unroll
         for (int a = 0; a < M; ++a) cm += X::eff(m, k, a) * C[a];
-        qk *= cm;
+        q *= cm;
       }
-      q[k] = qk;
+      for (int j = 0; j < rx.nr; ++j) w[rx.reac[j]] -= q;
+      for (int j = 0; j < rx.np; ++j) w[rx.prod[j]] += q;
     }
-    __syncwarp();
-    if (lane < M) {
-      CT w = CT();
-      for (int k = 0; k < m.R; ++k) {
-        const DevReaction& rx = m.rx[k];
-        for (int j = 0; j < rx.nr; ++j)
-          if (rx.reac[j] == lane) w -= q[k];
-        for (int j = 0; j < rx.np; ++j)
-          if (rx.prod[j] == lane) w += q[k];
-      }
-      r[lane] += X::dt_sub(un) * (w * X::mm(m, lane));
-    }
-    __syncwarp();
+    // butterfly sums over the group: every lane ends with the same total
+#pragma unroll
+    for (int o = 1; o < L; o <<= 1)
+#pragma unroll
+      for (int a = 0; a < M; ++a) w[a] += shfl_xor_ct(gmask, w[a], o);
+#pragma unroll
+    for (int a = 0; a < M; ++a) r[a] += X::dt_sub(un) * (w[a] * X::mm(m, a));
   }
-  if (lane < M - 1) {
-    if constexpr (sizeof(RT) == 4) rec[(RC::DRHO + lane) * N + n] = (r[lane] - r0).hi;
-    else rec[(RC::DRHO + lane) * N + n] = RT(r[lane] - r0);
+#pragma unroll
+  for (int a = 0; a < M - 1; ++a) {
+    if (a % L != sub) continue;
+    if constexpr (sizeof(RT) == 4) rec[(RC::DRHO + a) * N + n] = (r[a] - r0[a]).hi;
+    else rec[(RC::DRHO + a) * N + n] = RT(r[a] - r0[a]);
   }
 }
 
@@ -459,22 +456,47 @@ template <> struct MixParams<float> {
 };
 
 // ---------------------------------------------------------------------------
-// Collision of all lattices (Sec. 2.3 Eq. finalNumericalEquationsReactive;
-// Sec. 3.2 Eqs. f, g; Sec. 3.3 Eqs. feqmix, Pex; Sec. 3.4 Eqs. geq_i, gstar,
-// gstareq1mom, qdiff, corrFourier, qex; Sec. 2.4 Eq. R3).
-template <int D, int M, typename S, typename RT>
-__device__ __forceinline__ void collide_body(const S* __restrict__ src, S* __restrict__ dst,
-                                             const RT* __restrict__ rec,
-                                             const double* __restrict__ Tf,
-                                             int* __restrict__ status, const Geom& g,
-                                             const Units& un, const BCDev& bc,
-                                             const DevMech& mech, long long n) {
+// Per-node collision parameters: everything the direction loop needs
+// (Sec. 2.3 Eqs. betaa, taua, transform1; Sec. 3.3 Eq. Pex; Sec. 3.4 Eqs.
+// gstar, qdiff, corrFourier; Sec. 2.4 Eq. R3).
+template <int D, int M, typename RT> struct NodePar {
+  RT rho, om, U, theta;          // density, omega, internal energy, R T (lattice)
+  RT u[D], Pex[D], W[D];         // velocity, extended diagonal pressure, energy-flux term
+  RT th[M], V[M][D], rs[M];      // theta_b, diffusion velocities, rho_b
+  RT cF[M - 1], tb[M - 1], dr[M - 1];   // (beta_a - 1) Y_a s, 2 beta_a, reaction increments
+};
+
+// Field offsets of NodePar stored field-major [field][N] (split collision).
+template <int D, int M> struct CPar {
+  static constexpr int TH = 0;
+  static constexpr int V = TH + M;
+  static constexpr int RS = V + M * D;
+  static constexpr int CF = RS + M;
+  static constexpr int TB = CF + M - 1;
+  static constexpr int DR = TB + M - 1;
+  static constexpr int U = DR + M - 1;
+  static constexpr int PEX = U + D;
+  static constexpr int W = PEX + D;
+  static constexpr int RHO = W + D;
+  static constexpr int OM = RHO + 1;
+  static constexpr int UL = OM + 1;
+  static constexpr int THETA = UL + 1;
+  static constexpr int NF = THETA + 1;
+};
+
+// The per-node part of the collision of node n (not solid, n < N):
+// moments from the record, isotropic gradients, relaxation parameters,
+// diffusion velocities, energy-flux correction.  The diffusion-velocity
+// solve uses this thread's shared-memory column (M*M entries, stride kBS).
+template <int D, int M, typename RT>
+__device__ __forceinline__ void node_params(const RT* __restrict__ rec,
+                                            const double* __restrict__ Tf, const Geom& g,
+                                            const Units& un, const BCDev& bc,
+                                            const DevMech& mech, long long n, int tag,
+                                            NodePar<D, M, RT>& p) {
   constexpr int Q = Lat<D>::Q, NP = Lat<D>::NP;
   using RC = Rec<D, M>;
   const long long N = g.N;
-  if (n >= N) return;
-  const int tag = bc.tag ? bc.tag[n] : TAG_BULK;
-  if (tag == TAG_SOLID) return;
   const int x = (int)(n % g.nx);
   const int y = (int)((n / g.nx) % g.ny);
   const int z = (int)(n / ((long long)g.nx * g.ny));
@@ -655,78 +677,153 @@ __device__ __forceinline__ void collide_body(const S* __restrict__ src, S* __res
   }
 
   // per-lattice parameters in the collision type
-  RT th_a[M], beta[M], Pex[D], uR[D], VR[M][D];
 #pragma unroll
   for (int a = 0; a < M; ++a) {
-    th_a[a] = RT(MP::Ra(mech, a) * T * MP::inv_c2(un));
-    beta[a] = RT(inv_tau_a[a] / (PT(2) + inv_tau_a[a]));
+    p.th[a] = RT(MP::Ra(mech, a) * T * MP::inv_c2(un));
+    p.rs[a] = RT(rs[a]);
 #pragma unroll
-    for (int d = 0; d < D; ++d) VR[a][d] = V[a][d];
+    for (int d = 0; d < D; ++d) p.V[a][d] = V[a][d];
   }
 #pragma unroll
   for (int d = 0; d < D; ++d) {
-    uR[d] = RT(u[d]);
-    Pex[d] = RT(theta + u[d] * u[d] + (PT(2) - omega) / (PT(2) * rho * omega) * PT(dPhi[d]));
+    p.u[d] = RT(u[d]);
+    p.Pex[d] = RT(theta + u[d] * u[d] + (PT(2) - omega) / (PT(2) * rho * omega) * PT(dPhi[d]));
+    p.W[d] = W[d];
   }
-  // energy equilibrium axis factors: A_c (acting on 1) and B_c (on u^2/2)
-  RT Af[D][3], Bf[D][3];
-#pragma unroll
-  for (int d = 0; d < D; ++d) {
-    const PT ua = u[d];
-    const PT O1 = theta * ua + PT(0.5) * ua * ua * ua;
-    const PT O2 = theta * theta + PT(2.5) * theta * ua * ua + PT(0.5) * ua * ua * ua * ua;
-    const PT Pd = theta + ua * ua;
-    Af[d][0] = RT(PT(0.5) * (Pd - ua));
-    Af[d][1] = RT(PT(1) - Pd);
-    Af[d][2] = RT(PT(0.5) * (Pd + ua));
-    Bf[d][0] = RT(PT(0.5) * (O2 - O1));
-    Bf[d][1] = RT(PT(0.5) * ua * ua - O2);
-    Bf[d][2] = RT(PT(0.5) * (O2 + O1));
-  }
-  const RT rhoR = RT(rho), omR = RT(omega), UR = RT(U_lat);
-  // species coefficients of the update, hoisted out of the direction loop:
+  p.rho = RT(rho);
+  p.om = RT(omega);
+  p.U = RT(U_lat);
+  p.theta = RT(theta);
+  // species coefficients of the update:
   // f_a += 2 beta_a (rho_a psi_a - f_a) + cF_a sum_b K_ab d_b + drho_a psi_a
   // with cF_a = (beta_a - 1) Y_a s (1/tau_ab = s K_ab)
-  RT rsR[M], cF[M - 1], drR[M - 1], two_beta[M - 1];
-#pragma unroll
-  for (int b = 0; b < M; ++b) rsR[b] = RT(rs[b]);
 #pragma unroll
   for (int a = 0; a < M - 1; ++a) {
-    cF[a] = RT((inv_tau_a[a] / (PT(2) + inv_tau_a[a]) - PT(1)) * Y[a] * s_tau);
-    drR[a] = rec[(RC::DRHO + a) * N + n];
-    two_beta[a] = RT(2) * beta[a];
+    const RT beta = RT(inv_tau_a[a] / (PT(2) + inv_tau_a[a]));
+    p.cF[a] = RT((inv_tau_a[a] / (PT(2) + inv_tau_a[a]) - PT(1)) * Y[a] * s_tau);
+    p.dr[a] = rec[(RC::DRHO + a) * N + n];
+    p.tb[a] = RT(2) * beta;
   }
+}
 
-  // Per-species axis factors of psi(u, theta_b) and psi(u + V_b, theta_b)
-  // (Eq. prod), tabulated once per node in this thread's shared-memory column
-  // (the solve's space, now free): entry ((set*M + b)*D + d)*3 + c + 1.
-  extern __shared__ unsigned char smem_raw[];
-  RT* tab = reinterpret_cast<RT*>(smem_raw) + threadIdx.x;
-  constexpr bool kTab = sizeof(RT) == 4;
-  if constexpr (kTab) {
+// Energy-equilibrium axis factors (the closed form of g^eq, Sec. 3.4 Eq.
+// geq_i): A_c acting on 1 and B_c acting on u^2/2, c = -1, 0, 1.
+template <int D, typename RT>
+__device__ __forceinline__ void energy_factors(const RT (&u)[D], RT theta, RT (&Af)[D][3],
+                                               RT (&Bf)[D][3]) {
+#pragma unroll
+  for (int d = 0; d < D; ++d) {
+    const RT ua = u[d];
+    const RT O1 = theta * ua + RT(0.5) * ua * ua * ua;
+    const RT O2 = theta * theta + RT(2.5) * theta * ua * ua + RT(0.5) * ua * ua * ua * ua;
+    const RT Pd = theta + ua * ua;
+    Af[d][0] = RT(0.5) * (Pd - ua);
+    Af[d][1] = RT(1) - Pd;
+    Af[d][2] = RT(0.5) * (Pd + ua);
+    Bf[d][0] = RT(0.5) * (O2 - O1);
+    Bf[d][1] = RT(0.5) * ua * ua - O2;
+    Bf[d][2] = RT(0.5) * (O2 + O1);
+  }
+}
+
+// Axis factors of psi(u, theta_b) (set 0) and psi(u + V_b, theta_b) (set 1)
+// (Eq. prod): entry e = ((set*M + b)*D + d)*3 + c + 1 of a table.
+template <int D, int M, typename RT>
+__device__ __forceinline__ RT axis_factor(int e, const RT* th, const RT* u, const RT* V) {
+  const int c = e % 3 - 1;
+  const int d = (e / 3) % D;
+  const int b = (e / (3 * D)) % M;
+  const int set = e / (3 * D * M);
+  const RT xs = set ? u[d] + V[b * D + d] : u[d];
+  const RT Ps = th[b] + xs * xs;
+  return c == 0 ? RT(1) - Ps : (c > 0 ? RT(0.5) * (Ps + xs) : RT(0.5) * (Ps - xs));
+}
+
+// Collision of every lattice in direction i of node n (Sec. 2.3 Eq.
+// finalNumericalEquationsReactive; Sec. 3.2 Eqs. f, g; Sec. 3.3 Eq. feqmix):
+// PS supplies the node's parameters (registers, or the block's shared memory
+// in the split placement).
+template <int D, int M, typename S, typename RT, typename PS>
+__device__ __forceinline__ void collide_direction(const PS& ps, int i,
+                                                  const S* __restrict__ src,
+                                                  S* __restrict__ dst, const BCDev& bc,
+                                                  int tag, long long N, long long n,
+                                                  long long sn, const DevMech& mech) {
+  constexpr int Q = Lat<D>::Q;
+  int c[3];
+  c[0] = cvel(i, 0); c[1] = cvel(i, 1); c[2] = D == 3 ? cvel(i, 2) : 0;
+  RT pe[M], dd[M];
+  ps.factors(c, pe, dd);
+#pragma unroll
+  for (int a = 0; a < M - 1; ++a) {
+    RT F = RT(0);
 #pragma unroll
     for (int b = 0; b < M; ++b)
-#pragma unroll
-      for (int d = 0; d < D; ++d) {
-        const RT ud = uR[d], Pe = th_a[b] + ud * ud;
-        RT* te = tab + ((b * D + d) * 3) * kBS;
-        te[0] = RT(0.5) * (Pe - ud);
-        te[kBS] = RT(1) - Pe;
-        te[2 * kBS] = RT(0.5) * (Pe + ud);
-        const RT xs = ud + VR[b][d], Ps = th_a[b] + xs * xs;
-        RT* ts = tab + (((M + b) * D + d) * 3) * kBS;
-        ts[0] = RT(0.5) * (Ps - xs);
-        ts[kBS] = RT(1) - Ps;
-        ts[2 * kBS] = RT(0.5) * (Ps + xs);
-      }
+      if (b != a) F += kcoef<RT>(mech, a, b) * dd[b];
+    const long long off = (long long)(a * Q + i) * N;
+    const RT f = pop_in<RT>(src, bc, tag, N, sn, a * Q + i);
+    const RT fn = f + ps.tb(a) * (ps.rs(a) * pe[a] - f) + ps.cF(a) * F + ps.dr(a) * pe[a];
+    dst[off + n] = S(fn);
   }
-#pragma unroll 1
-  for (int i = 0; i < Q; ++i) {
-    const long long sn = node_shift<D>(x, y, z, i, -1, g);
-    int c[3];
-    c[0] = cvel(i, 0); c[1] = cvel(i, 1); c[2] = D == 3 ? cvel(i, 2) : 0;
-    RT pe[M], dd[M];
-    if constexpr (kTab) {
+  {
+    RT fex = ps.rho();
+#pragma unroll
+    for (int d = 0; d < D; ++d) fex *= psi1<RT>(c[d], ps.u(d), ps.Pex(d));
+    const long long off = (long long)((M - 1) * Q + i) * N;
+    const RT f = pop_in<RT>(src, bc, tag, N, sn, (M - 1) * Q + i);
+    dst[off + n] = S(f + ps.om() * (fex - f));
+  }
+  {
+    RT prodA = RT(1);
+#pragma unroll
+    for (int d = 0; d < D; ++d) prodA *= ps.Af(d, c[d]);
+    RT geq = ps.U() * prodA;
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+      RT t = ps.Bf(d, c[d]);
+#pragma unroll
+      for (int e = 0; e < D; ++e)
+        if (e != d) t *= ps.Af(e, c[e]);
+      geq += t;
+    }
+    geq *= ps.rho();
+    const long long off = (long long)(M * Q + i) * N;
+    const RT gv = pop_in<RT>(src, bc, tag, N, sn, M * Q + i);
+    RT gn = gv + ps.om() * (geq - gv);
+    if (csq(i, D) == 1) {
+#pragma unroll
+      for (int d = 0; d < D; ++d)
+        if (c[d] != 0) gn += (c[d] > 0 ? RT(0.5) : RT(-0.5)) * ps.W(d);
+    }
+    dst[off + n] = S(gn);
+  }
+}
+
+// Parameters held in registers (fused placement).  The species factor
+// products come from a table in this thread's shared-memory column (FP32:
+// entry stride kBS) or are formed directly (FP64, where the table would
+// halve the occupancy).
+template <int D, int M, typename RT> struct RegPar {
+  const NodePar<D, M, RT>& p;
+  RT Afv[D][3], Bfv[D][3];
+  const RT* tab;
+  __device__ RegPar(const NodePar<D, M, RT>& p_, const RT* tab_) : p(p_), tab(tab_) {
+    energy_factors<D, RT>(p.u, p.theta, Afv, Bfv);
+  }
+  __device__ RT rho() const { return p.rho; }
+  __device__ RT om() const { return p.om; }
+  __device__ RT U() const { return p.U; }
+  __device__ RT u(int d) const { return p.u[d]; }
+  __device__ RT Pex(int d) const { return p.Pex[d]; }
+  __device__ RT W(int d) const { return p.W[d]; }
+  __device__ RT rs(int a) const { return p.rs[a]; }
+  __device__ RT cF(int a) const { return p.cF[a]; }
+  __device__ RT tb(int a) const { return p.tb[a]; }
+  __device__ RT dr(int a) const { return p.dr[a]; }
+  __device__ RT Af(int d, int c) const { return c == 0 ? Afv[d][1] : (c > 0 ? Afv[d][2] : Afv[d][0]); }
+  __device__ RT Bf(int d, int c) const { return c == 0 ? Bfv[d][1] : (c > 0 ? Bfv[d][2] : Bfv[d][0]); }
+  __device__ void factors(const int (&c)[3], RT (&pe)[M], RT (&dd)[M]) const {
+    if (tab) {
       int off[3];
 #pragma unroll
       for (int d = 0; d < D; ++d) off[d] = (d * 3 + c[d] + 1) * kBS;
@@ -741,7 +838,7 @@ __device__ __forceinline__ void collide_body(const S* __restrict__ src, S* __res
           st *= ts[off[d]];
         }
         pe[b] = e;
-        dd[b] = rsR[b] * (e - st);
+        dd[b] = p.rs[b] * (e - st);
       }
     } else {
 #pragma unroll
@@ -749,58 +846,195 @@ __device__ __forceinline__ void collide_body(const S* __restrict__ src, S* __res
         RT e = RT(1), st = RT(1);
 #pragma unroll
         for (int d = 0; d < D; ++d) {
-          e *= psi1<RT>(c[d], uR[d], th_a[b] + uR[d] * uR[d]);
-          const RT xs = uR[d] + VR[b][d];
-          st *= psi1<RT>(c[d], xs, th_a[b] + xs * xs);
+          e *= psi1<RT>(c[d], p.u[d], p.th[b] + p.u[d] * p.u[d]);
+          const RT xs = p.u[d] + p.V[b][d];
+          st *= psi1<RT>(c[d], xs, p.th[b] + xs * xs);
         }
         pe[b] = e;
-        dd[b] = rsR[b] * (e - st);
+        dd[b] = p.rs[b] * (e - st);
       }
-    }
-#pragma unroll
-    for (int a = 0; a < M - 1; ++a) {
-      RT F = RT(0);
-#pragma unroll
-      for (int b = 0; b < M; ++b)
-        if (b != a) F += kcoef<RT>(mech, a, b) * dd[b];
-      const long long off = (long long)(a * Q + i) * N;
-      const RT f = pop_in<RT>(src, bc, tag, N, sn, a * Q + i);
-      const RT fn = f + two_beta[a] * (rsR[a] * pe[a] - f) + cF[a] * F + drR[a] * pe[a];
-      dst[off + n] = S(fn);
-    }
-    {
-      RT fex = rhoR;
-#pragma unroll
-      for (int d = 0; d < D; ++d) fex *= psi1<RT>(c[d], uR[d], Pex[d]);
-      const long long off = (long long)((M - 1) * Q + i) * N;
-      const RT f = pop_in<RT>(src, bc, tag, N, sn, (M - 1) * Q + i);
-      dst[off + n] = S(f + omR * (fex - f));
-    }
-    {
-      RT prodA = RT(1);
-#pragma unroll
-      for (int d = 0; d < D; ++d) prodA *= pick3<RT>(c[d], Af[d]);
-      RT geq = UR * prodA;
-#pragma unroll
-      for (int d = 0; d < D; ++d) {
-        RT t = pick3<RT>(c[d], Bf[d]);
-#pragma unroll
-        for (int e = 0; e < D; ++e)
-          if (e != d) t *= pick3<RT>(c[e], Af[e]);
-        geq += t;
-      }
-      geq *= rhoR;
-      const long long off = (long long)(M * Q + i) * N;
-      const RT gv = pop_in<RT>(src, bc, tag, N, sn, M * Q + i);
-      RT gn = gv + omR * (geq - gv);
-      if (csq(i, D) == 1) {
-#pragma unroll
-        for (int d = 0; d < D; ++d)
-          if (c[d] != 0) gn += (c[d] > 0 ? RT(0.5) : RT(-0.5)) * W[d];
-      }
-      dst[off + n] = S(gn);
     }
   }
+};
+
+// Fused placement: one thread per node does the per-node part and then every
+// direction (Sec. 2.3, 3.2-3.4).
+template <int D, int M, typename S, typename RT>
+__device__ __forceinline__ void collide_body(const S* __restrict__ src, S* __restrict__ dst,
+                                             const RT* __restrict__ rec,
+                                             const double* __restrict__ Tf,
+                                             int* __restrict__ status, const Geom& g,
+                                             const Units& un, const BCDev& bc,
+                                             const DevMech& mech, long long n) {
+  constexpr int Q = Lat<D>::Q;
+  const long long N = g.N;
+  if (n >= N) return;
+  const int tag = bc.tag ? bc.tag[n] : TAG_BULK;
+  if (tag == TAG_SOLID) return;
+  NodePar<D, M, RT> p;
+  node_params<D, M, RT>(rec, Tf, g, un, bc, mech, n, tag, p);
+  const int x = (int)(n % g.nx);
+  const int y = (int)((n / g.nx) % g.ny);
+  const int z = (int)(n / ((long long)g.nx * g.ny));
+  // FP32: the species axis factors tabulated once per node in this thread's
+  // shared-memory column (the solve's space, now free)
+  extern __shared__ unsigned char smem_raw[];
+  RT* tab = nullptr;
+  if constexpr (sizeof(RT) == 4) {
+    tab = reinterpret_cast<RT*>(smem_raw) + threadIdx.x;
+    constexpr int NT = 2 * M * D * 3;
+#pragma unroll
+    for (int e = 0; e < NT; ++e)
+      tab[e * kBS] = axis_factor<D, M, RT>(e, p.th, p.u, &p.V[0][0]);
+  }
+  const RegPar<D, M, RT> ps(p, tab);
+#pragma unroll 1
+  for (int i = 0; i < Q; ++i)
+    collide_direction<D, M, S, RT>(ps, i, src, dst, bc, tag, N, n,
+                                   node_shift<D>(x, y, z, i, -1, g), mech);
+}
+
+// ---------------------------------------------------------------------------
+// Split placement of the collision, for grids too small to fill the GPU at
+// one thread per node: k_prep (one thread per node) stores each node's
+// parameters field-major; k_coll gives every node kCollTPN threads (one warp
+// per direction group, lanes over 32 consecutive nodes), stages the block's
+// parameters and axis-factor tables in shared memory, and updates each
+// direction as the fused kernel does.
+template <int D, int M, typename RT>
+__device__ __forceinline__ void prep_body(const RT* __restrict__ rec,
+                                          const double* __restrict__ Tf, RT* __restrict__ cp,
+                                          const Geom& g, const Units& un, const BCDev& bc,
+                                          const DevMech& mech, long long n) {
+  using CP = CPar<D, M>;
+  const long long N = g.N;
+  if (n >= N) return;
+  const int tag = bc.tag ? bc.tag[n] : TAG_BULK;
+  if (tag == TAG_SOLID) return;
+  NodePar<D, M, RT> p;
+  node_params<D, M, RT>(rec, Tf, g, un, bc, mech, n, tag, p);
+#pragma unroll
+  for (int b = 0; b < M; ++b) {
+    cp[(CP::TH + b) * N + n] = p.th[b];
+    cp[(CP::RS + b) * N + n] = p.rs[b];
+#pragma unroll
+    for (int d = 0; d < D; ++d) cp[(CP::V + b * D + d) * N + n] = p.V[b][d];
+  }
+#pragma unroll
+  for (int a = 0; a < M - 1; ++a) {
+    cp[(CP::CF + a) * N + n] = p.cF[a];
+    cp[(CP::TB + a) * N + n] = p.tb[a];
+    cp[(CP::DR + a) * N + n] = p.dr[a];
+  }
+#pragma unroll
+  for (int d = 0; d < D; ++d) {
+    cp[(CP::U + d) * N + n] = p.u[d];
+    cp[(CP::PEX + d) * N + n] = p.Pex[d];
+    cp[(CP::W + d) * N + n] = p.W[d];
+  }
+  cp[CP::RHO * N + n] = p.rho;
+  cp[CP::OM * N + n] = p.om;
+  cp[CP::UL * N + n] = p.U;
+  cp[CP::THETA * N + n] = p.theta;
+}
+
+constexpr int kCollNodes = kCollNodesPerBlock;   // nodes per block of k_coll (the lanes)
+constexpr int kCollTPN = 9;      // threads per node (warps per block)
+
+// shared-memory entries per node of k_coll: parameters, energy factors,
+// species axis-factor tables
+template <int D, int M> constexpr int coll_smem_entries() {
+  return CPar<D, M>::NF + 6 * D + 2 * M * D * 3;
+}
+
+// Parameters of node j of the block, field f at s[f * kCollNodes + j].
+template <int D, int M, typename RT> struct SmemPar {
+  using CP = CPar<D, M>;
+  static constexpr int AF = CP::NF, BF = CP::NF + 3 * D, TAB = CP::NF + 6 * D;
+  const RT* s;
+  int j;
+  __device__ RT get(int f) const { return s[f * kCollNodes + j]; }
+  __device__ RT rho() const { return get(CP::RHO); }
+  __device__ RT om() const { return get(CP::OM); }
+  __device__ RT U() const { return get(CP::UL); }
+  __device__ RT u(int d) const { return get(CP::U + d); }
+  __device__ RT Pex(int d) const { return get(CP::PEX + d); }
+  __device__ RT W(int d) const { return get(CP::W + d); }
+  __device__ RT rs(int a) const { return get(CP::RS + a); }
+  __device__ RT cF(int a) const { return get(CP::CF + a); }
+  __device__ RT tb(int a) const { return get(CP::TB + a); }
+  __device__ RT dr(int a) const { return get(CP::DR + a); }
+  __device__ RT Af(int d, int c) const { return get(AF + d * 3 + c + 1); }
+  __device__ RT Bf(int d, int c) const { return get(BF + d * 3 + c + 1); }
+  __device__ void factors(const int (&c)[3], RT (&pe)[M], RT (&dd)[M]) const {
+#pragma unroll
+    for (int b = 0; b < M; ++b) {
+      RT e = get(TAB + (b * D) * 3 + c[0] + 1);
+      RT st = get(TAB + ((M + b) * D) * 3 + c[0] + 1);
+#pragma unroll
+      for (int d = 1; d < D; ++d) {
+        e *= get(TAB + (b * D + d) * 3 + c[d] + 1);
+        st *= get(TAB + ((M + b) * D + d) * 3 + c[d] + 1);
+      }
+      pe[b] = e;
+      dd[b] = rs(b) * (e - st);
+    }
+  }
+};
+
+// One block: nodes n0 .. n0 + 31.  sm holds coll_smem_entries * kCollNodes.
+template <int D, int M, typename S, typename RT>
+__device__ __forceinline__ void coll_block(const S* __restrict__ src, S* __restrict__ dst,
+                                           const RT* __restrict__ cp, const Geom& g,
+                                           const BCDev& bc, const DevMech& mech, long long n0,
+                                           RT* __restrict__ sm) {
+  using CP = CPar<D, M>;
+  using SP = SmemPar<D, M, RT>;
+  constexpr int Q = Lat<D>::Q;
+  constexpr int NT = 2 * M * D * 3;
+  const long long N = g.N;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const long long n = n0 + lane;
+  const int tag = n < N ? (bc.tag ? bc.tag[n] : TAG_BULK) : TAG_SOLID;
+  const bool valid = tag != TAG_SOLID;
+  for (int f = w; f < CP::NF; f += kCollTPN)
+    sm[f * kCollNodes + lane] = valid ? cp[f * N + n] : RT(0);
+  __syncthreads();
+  if (valid) {
+    if (w == 0) {
+      RT u[D], Af[D][3], Bf[D][3];
+#pragma unroll
+      for (int d = 0; d < D; ++d) u[d] = sm[(CP::U + d) * kCollNodes + lane];
+      energy_factors<D, RT>(u, sm[CP::THETA * kCollNodes + lane], Af, Bf);
+#pragma unroll
+      for (int d = 0; d < D; ++d)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          sm[(SP::AF + d * 3 + k) * kCollNodes + lane] = Af[d][k];
+          sm[(SP::BF + d * 3 + k) * kCollNodes + lane] = Bf[d][k];
+        }
+    }
+    for (int e = w; e < NT; e += kCollTPN) {
+      const int c = e % 3 - 1;
+      const int d = (e / 3) % D;
+      const int b = (e / (3 * D)) % M;
+      const int set = e / (3 * D * M);
+      const RT ud = sm[(CP::U + d) * kCollNodes + lane];
+      const RT xs = set ? ud + sm[(CP::V + b * D + d) * kCollNodes + lane] : ud;
+      const RT Ps = sm[(CP::TH + b) * kCollNodes + lane] + xs * xs;
+      sm[(SP::TAB + e) * kCollNodes + lane] =
+          c == 0 ? RT(1) - Ps : (c > 0 ? RT(0.5) * (Ps + xs) : RT(0.5) * (Ps - xs));
+    }
+  }
+  __syncthreads();
+  if (!valid) return;
+  const SP ps{sm, lane};
+  const int x = (int)(n % g.nx);
+  const int y = (int)((n / g.nx) % g.ny);
+  const int z = (int)(n / ((long long)g.nx * g.ny));
+  for (int i = w; i < Q; i += kCollTPN)
+    collide_direction<D, M, S, RT>(ps, i, src, dst, bc, tag, N, n,
+                                   node_shift<D>(x, y, z, i, -1, g), mech);
 }
 
 
@@ -1011,20 +1245,24 @@ k_moments(const S* __restrict__ src, RT* __restrict__ rec, double* __restrict__ 
                             blockIdx.x * (long long)blockDim.x + threadIdx.x, chem_inline);
 }
 
-// one warp per node, kChemWarps nodes per block
-constexpr int kChemWarps = kChemNodesPerBlock;
+// reaction sub-steps, L lanes per node, 128 threads per block
+template <int D, int M, typename RT, int L>
+__device__ __forceinline__ void chem_entry(RT* rec, const double* Tf, int* status, long long N,
+                                           const int* tag, const Units& un, const DevMech& m,
+                                           long long first_node) {
+  const int lane = threadIdx.x & 31;
+  const long long n = first_node + threadIdx.x / L;
+  if (n >= N || (tag && tag[n] == TAG_SOLID)) return;   // the whole group leaves
+  const unsigned gmask = (L == 32 ? 0xffffffffu : ((1u << L) - 1u) << (lane & ~(L - 1)));
+  chem_lanes_body<D, M, RT, L>(rec, Tf, status, N, tag, un, m, n, lane & (L - 1), gmask);
+}
 
-template <int D, int M, typename RT>
-__global__ void __launch_bounds__(32 * kChemWarps)
+template <int D, int M, typename RT, int L>
+__global__ void __launch_bounds__(128)
 k_chem(RT* __restrict__ rec, const double* __restrict__ Tf, int* __restrict__ status,
        long long N, const int* __restrict__ tag, const __grid_constant__ Units un,
        const DevMech* __restrict__ mech) {
-  using CT = typename ChemType<RT>::type;
-  __shared__ __align__(16) unsigned char raw[kChemWarps * kChemScratch * sizeof(CT)];
-  const int w = threadIdx.x >> 5;
-  chem_warp_body<D, M, RT>(rec, Tf, status, N, tag, un, *mech,
-                           blockIdx.x * (long long)kChemWarps + w, threadIdx.x & 31,
-                           reinterpret_cast<CT*>(raw) + w * kChemScratch);
+  chem_entry<D, M, RT, L>(rec, Tf, status, N, tag, un, *mech, blockIdx.x * (128LL / L));
 }
 
 template <int D, int M, typename S, typename RT>
@@ -1035,6 +1273,25 @@ k_collide(const S* __restrict__ src, S* __restrict__ dst, const RT* __restrict__
           const __grid_constant__ BCDev bc, const __grid_constant__ DevMech mech) {
   collide_body<D, M, S, RT>(src, dst, rec, Tf, status, g, un, bc, mech,
                             blockIdx.x * (long long)blockDim.x + threadIdx.x);
+}
+
+template <int D, int M, typename RT>
+__global__ void __launch_bounds__(128)
+k_prep(const RT* __restrict__ rec, const double* __restrict__ Tf, RT* __restrict__ cp,
+       const __grid_constant__ Geom g, const __grid_constant__ Units un,
+       const __grid_constant__ BCDev bc, const __grid_constant__ DevMech mech) {
+  prep_body<D, M, RT>(rec, Tf, cp, g, un, bc, mech,
+                      blockIdx.x * (long long)blockDim.x + threadIdx.x);
+}
+
+template <int D, int M, typename S, typename RT>
+__global__ void __launch_bounds__(32 * kCollTPN)
+k_coll(const S* __restrict__ src, S* __restrict__ dst, const RT* __restrict__ cp,
+       const __grid_constant__ Geom g, const __grid_constant__ BCDev bc,
+       const __grid_constant__ DevMech mech) {
+  extern __shared__ __align__(16) unsigned char coll_raw[];
+  coll_block<D, M, S, RT>(src, dst, cp, g, bc, mech, blockIdx.x * (long long)kCollNodes,
+                          reinterpret_cast<RT*>(coll_raw));
 }
 
 template <int D, int M, typename S>
@@ -1050,14 +1307,16 @@ k_boundary(const S* __restrict__ src, const __grid_constant__ BCDev bc,
 // ---------------------------------------------------------------------------
 // Batched kernels: the grid is the concatenation of every domain's tiles; a
 // block finds its domain by binary search over the domains' first blocks.
-// grid: 0 = node kernels, 1 = boundary kernel, 2 = warp-per-node chemistry
+enum { GRID_NODE = 0, GRID_BOUNDARY = 1, GRID_CHEM = 2, GRID_COLL = 3 };
 __device__ __forceinline__ int domain_of_block(const DomainDev* __restrict__ d, int ndom,
                                                int b, int grid) {
   int lo = 0, hi = ndom - 1;
   while (lo < hi) {
     const int mid = (lo + hi + 1) >> 1;
-    const int first = grid == 1 ? d[mid].bblock_begin
-                                : (grid == 2 ? d[mid].cblock_begin : d[mid].block_begin);
+    const int first = grid == GRID_BOUNDARY ? d[mid].bblock_begin
+                      : grid == GRID_CHEM   ? d[mid].cblock_begin
+                      : grid == GRID_COLL   ? d[mid].kblock_begin
+                                            : d[mid].block_begin;
     if (first <= b) lo = mid; else hi = mid - 1;
   }
   return lo;
@@ -1066,7 +1325,7 @@ __device__ __forceinline__ int domain_of_block(const DomainDev* __restrict__ d, 
 template <int D, int M, typename S, typename RT>
 __global__ void __launch_bounds__(128)
 k_moments_batch(const DomainDev* __restrict__ doms, int ndom, int parity, int chem_inline) {
-  const DomainDev& d = doms[domain_of_block(doms, ndom, blockIdx.x, 0)];
+  const DomainDev& d = doms[domain_of_block(doms, ndom, blockIdx.x, GRID_NODE)];
   const int c = d.cur0 ^ parity;
   moments_body<D, M, S, RT>(static_cast<const S*>(d.pops[c]), static_cast<RT*>(d.rec), d.Tf,
                             d.status, d.g, d.un, d.bc, *d.mech,
@@ -1074,23 +1333,18 @@ k_moments_batch(const DomainDev* __restrict__ doms, int ndom, int parity, int ch
                             chem_inline);
 }
 
-template <int D, int M, typename RT>
-__global__ void __launch_bounds__(32 * kChemWarps)
+template <int D, int M, typename RT, int L>
+__global__ void __launch_bounds__(128)
 k_chem_batch(const DomainDev* __restrict__ doms, int ndom) {
-  using CT = typename ChemType<RT>::type;
-  __shared__ __align__(16) unsigned char raw[kChemWarps * kChemScratch * sizeof(CT)];
-  const DomainDev& d = doms[domain_of_block(doms, ndom, blockIdx.x, 2)];
-  const int w = threadIdx.x >> 5;
-  chem_warp_body<D, M, RT>(static_cast<RT*>(d.rec), d.Tf, d.status, d.g.N, d.bc.tag, d.un,
-                           *d.mech,
-                           (blockIdx.x - d.cblock_begin) * (long long)kChemWarps + w,
-                           threadIdx.x & 31, reinterpret_cast<CT*>(raw) + w * kChemScratch);
+  const DomainDev& d = doms[domain_of_block(doms, ndom, blockIdx.x, GRID_CHEM)];
+  chem_entry<D, M, RT, L>(static_cast<RT*>(d.rec), d.Tf, d.status, d.g.N, d.bc.tag, d.un,
+                          *d.mech, (blockIdx.x - d.cblock_begin) * (128LL / L));
 }
 
 template <int D, int M, typename S, typename RT>
 __global__ void __launch_bounds__(128)
 k_collide_batch(const DomainDev* __restrict__ doms, int ndom, int parity) {
-  const DomainDev& d = doms[domain_of_block(doms, ndom, blockIdx.x, 0)];
+  const DomainDev& d = doms[domain_of_block(doms, ndom, blockIdx.x, GRID_NODE)];
   const int c = d.cur0 ^ parity;
   collide_body<D, M, S, RT>(static_cast<const S*>(d.pops[c]),
                             static_cast<S*>(const_cast<void*>(d.pops[1 - c])),
@@ -1099,10 +1353,32 @@ k_collide_batch(const DomainDev* __restrict__ doms, int ndom, int parity) {
                             (blockIdx.x - d.block_begin) * (long long)blockDim.x + threadIdx.x);
 }
 
+template <int D, int M, typename RT>
+__global__ void __launch_bounds__(128)
+k_prep_batch(const DomainDev* __restrict__ doms, int ndom) {
+  const DomainDev& d = doms[domain_of_block(doms, ndom, blockIdx.x, GRID_NODE)];
+  prep_body<D, M, RT>(static_cast<const RT*>(d.rec), d.Tf, static_cast<RT*>(d.cpar), d.g,
+                      d.un, d.bc, *d.mech,
+                      (blockIdx.x - d.block_begin) * (long long)blockDim.x + threadIdx.x);
+}
+
+template <int D, int M, typename S, typename RT>
+__global__ void __launch_bounds__(32 * kCollTPN)
+k_coll_batch(const DomainDev* __restrict__ doms, int ndom, int parity) {
+  extern __shared__ __align__(16) unsigned char coll_raw[];
+  const DomainDev& d = doms[domain_of_block(doms, ndom, blockIdx.x, GRID_COLL)];
+  const int c = d.cur0 ^ parity;
+  coll_block<D, M, S, RT>(static_cast<const S*>(d.pops[c]),
+                          static_cast<S*>(const_cast<void*>(d.pops[1 - c])),
+                          static_cast<const RT*>(d.cpar), d.g, d.bc, *d.mech,
+                          (blockIdx.x - d.kblock_begin) * (long long)kCollNodes,
+                          reinterpret_cast<RT*>(coll_raw));
+}
+
 template <int D, int M, typename S>
 __global__ void __launch_bounds__(128)
 k_boundary_batch(const DomainDev* __restrict__ doms, int ndom, int parity) {
-  const DomainDev& d = doms[domain_of_block(doms, ndom, blockIdx.x, 1)];
+  const DomainDev& d = doms[domain_of_block(doms, ndom, blockIdx.x, GRID_BOUNDARY)];
   const int c = d.cur0 ^ parity;
   boundary_body<D, M, S>(static_cast<const S*>(d.pops[c]), d.bc, d.Tf, d.status, d.g, d.un,
                          *d.mech, (blockIdx.x - d.bblock_begin) * 4 + threadIdx.x / 32,
@@ -1212,175 +1488,157 @@ __global__ void k_out(const S* __restrict__ pops, const double* __restrict__ Tf,
   if (oE) oE[n] = E * un.c * un.c;
 }
 
-template <typename S>
-__global__ void k_to_fp64(const S* __restrict__ in, double* __restrict__ out, long long count) {
-  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < count;
-       k += (long long)gridDim.x * blockDim.x)
-    out[k] = static_cast<double>(in[k]);
-}
 
 // ---------------------------------------------------------------------------
 // dispatch
 
 static inline unsigned blocks_for(long long N, int bs) { return (unsigned)((N + bs - 1) / bs); }
 
+// dynamic shared memory of the collision kernels and of k_prep (bytes)
+template <int D, int M, typename RT> constexpr size_t fused_smem() {
+  return (size_t)collide_smem_entries<D, M, RT>() * kBS * sizeof(RT);
+}
+template <int D, int M, typename RT> constexpr size_t prep_smem() {
+  return (size_t)M * M * kBS * sizeof(RT);
+}
+template <int D, int M, typename RT> constexpr size_t coll_smem() {
+  return (size_t)coll_smem_entries<D, M>() * kCollNodes * sizeof(RT);
+}
+
+// Kernel attributes (shared memory above the 48 KB default) of every kernel a
+// step may launch; idempotent, and required before a stream capture, where
+// attribute calls are not recorded.
+template <int D, int M, typename S, typename RT>
+static cudaError_t prepare_impl() {
+  cudaError_t e = cudaSuccess;
+  auto big = [&](const void* f, size_t bytes) {
+    if (e == cudaSuccess && bytes > 48 * 1024)
+      e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  };
+  big((const void*)k_collide<D, M, S, RT>, fused_smem<D, M, RT>());
+  big((const void*)k_collide_batch<D, M, S, RT>, fused_smem<D, M, RT>());
+  big((const void*)k_prep<D, M, RT>, prep_smem<D, M, RT>());
+  big((const void*)k_prep_batch<D, M, RT>, prep_smem<D, M, RT>());
+  big((const void*)k_coll<D, M, S, RT>, coll_smem<D, M, RT>());
+  big((const void*)k_coll_batch<D, M, S, RT>, coll_smem<D, M, RT>());
+  return e;
+}
+
+template <int D, int M, typename RT>
+static void launch_chem(const Launch& lc, unsigned nblk, cudaStream_t s, RT* rec,
+                        const double* Tf, int* status, long long N, const int* tag,
+                        const Units& un, const DevMech* mech) {
+  if (lc.chem_lanes == 4)
+    k_chem<D, M, RT, 4><<<nblk, 128, 0, s>>>(rec, Tf, status, N, tag, un, mech);
+  else
+    k_chem<D, M, RT, 8><<<nblk, 128, 0, s>>>(rec, Tf, status, N, tag, un, mech);
+}
+
+// prepare_impl once per device and instantiation
+template <int D, int M, typename S, typename RT>
+static cudaError_t prepare_once() {
+  static std::atomic<unsigned long long> done{0};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const unsigned long long bit = 1ull << (dev & 63);
+  if (done.load() & bit) return cudaSuccess;
+  e = prepare_impl<D, M, S, RT>();
+  if (e == cudaSuccess) done.fetch_or(bit);
+  return e;
+}
+
 template <int D, int M, typename S, typename RT>
 static cudaError_t step_impl(const DevMech& mech, const StepArgs& a, cudaStream_t s,
                              int which) {
-  const int bs = 128;
+  const int bs = kBS;
   const unsigned nb = blocks_for(a.g.N, bs);
+  const cudaError_t pe = prepare_once<D, M, S, RT>();
+  if (pe != cudaSuccess) return pe;
+  const Launch& lc = a.lc;
+  const bool chem_sep = lc.chem_lanes > 1 && a.mech_dev;
+  const bool split = lc.coll_split && a.cpar;
   if (which != 1) {
     if (a.bc.n_if > 0)
       k_boundary<D, M, S><<<(a.bc.n_if + 3) / 4, 128, 0, s>>>(
           static_cast<const S*>(a.src), a.bc, a.Tfield, a.status, a.g, a.un, mech);
-    const int chem_warp = a.chem_warp && a.mech_dev;
     k_moments<D, M, S, RT><<<nb, bs, 0, s>>>(static_cast<const S*>(a.src),
                                              reinterpret_cast<RT*>(a.rec), a.Tfield,
-                                             a.status, a.g, a.un, a.bc, mech, !chem_warp);
-    if (chem_warp)
-      k_chem<D, M, RT><<<blocks_for(a.g.N, kChemWarps), 32 * kChemWarps, 0, s>>>(
-          reinterpret_cast<RT*>(a.rec), a.Tfield, a.status, a.g.N, a.bc.tag, a.un, a.mech_dev);
+                                             a.status, a.g, a.un, a.bc, mech, !chem_sep);
+    if (chem_sep)
+      launch_chem<D, M, RT>(lc, blocks_for(a.g.N, 128 / lc.chem_lanes), s,
+                            reinterpret_cast<RT*>(a.rec), a.Tfield, a.status, a.g.N, a.bc.tag,
+                            a.un, a.mech_dev);
   }
   if (which != 0) {
-    const size_t smem = (size_t)collide_smem_entries<D, M, RT>() * bs * sizeof(RT);
-    if (smem > 48 * 1024) {
-      const cudaError_t e = cudaFuncSetAttribute(
-          k_collide<D, M, S, RT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (e != cudaSuccess) return e;
+    if (split) {
+      k_prep<D, M, RT><<<nb, bs, prep_smem<D, M, RT>(), s>>>(
+          reinterpret_cast<const RT*>(a.rec), a.Tfield, static_cast<RT*>(a.cpar), a.g, a.un,
+          a.bc, mech);
+      k_coll<D, M, S, RT><<<blocks_for(a.g.N, kCollNodes), 32 * kCollTPN, coll_smem<D, M, RT>(),
+                            s>>>(static_cast<const S*>(a.src), static_cast<S*>(a.dst),
+                                 static_cast<const RT*>(a.cpar), a.g, a.bc, mech);
+    } else {
+      k_collide<D, M, S, RT><<<nb, bs, fused_smem<D, M, RT>(), s>>>(
+          static_cast<const S*>(a.src), static_cast<S*>(a.dst),
+          reinterpret_cast<const RT*>(a.rec), a.Tfield, a.status, a.g, a.un, a.bc, mech);
     }
-    k_collide<D, M, S, RT><<<nb, bs, smem, s>>>(
-                                             static_cast<const S*>(a.src),
-                                             static_cast<S*>(a.dst),
-                                             reinterpret_cast<const RT*>(a.rec), a.Tfield,
-                                             a.status, a.g, a.un, a.bc, mech);
   }
   return cudaGetLastError();
 }
 
-#define LBM_DISPATCH(D_, M_, CALL)                                 \
-  if (D == D_ && M == M_) {                                        \
-    if (prec == LBM_FP64) return CALL(D_, M_, double, double);     \
-    if (prec == LBM_FP32_STORE) return CALL(D_, M_, float, float); \
-  }
-
-cudaError_t launch_step(int D, int M, lbm_precision prec, const DevMech& mech,
-                        const StepArgs& a, cudaStream_t s, int which) {
-#define CALL_STEP(D_, M_, S_, R_) step_impl<D_, M_, S_, R_>(mech, a, s, which)
-  LBM_DISPATCH(3, 9, CALL_STEP)
-  LBM_DISPATCH(3, 2, CALL_STEP)
-  LBM_DISPATCH(2, 9, CALL_STEP)
-  LBM_DISPATCH(2, 2, CALL_STEP)
-#undef CALL_STEP
-  return cudaErrorInvalidValue;
+template <int D, int M, typename S>
+static cudaError_t init_impl(const DevMech& mech, const Geom& g, const Units& un,
+                             const double* rho_or_P, int is_pressure, const double* u,
+                             const double* T, const double* Y, void* pops, double* Tfield,
+                             int* status, cudaStream_t s) {
+  k_init<D, M, S><<<blocks_for(g.N, 128), 128, 0, s>>>(rho_or_P, is_pressure, u, T, Y,
+                                                        static_cast<S*>(pops), Tfield, status,
+                                                        g, un, mech);
+  return cudaGetLastError();
 }
 
-cudaError_t launch_init(int D, int M, lbm_precision prec, const DevMech& mech,
-                        const Geom& g, const Units& un, const double* rho_or_P,
-                        int is_pressure, const double* u, const double* T,
-                        const double* Y, void* pops, double* Tfield, int* status,
-                        cudaStream_t s) {
-  const unsigned nb = blocks_for(g.N, 128);
-#define CALL_INIT(D_, M_, S_, R_)                                                       \
-  (k_init<D_, M_, S_><<<nb, 128, 0, s>>>(rho_or_P, is_pressure, u, T, Y,               \
-                                         static_cast<S_*>(pops), Tfield, status, g, un, \
-                                         mech),                                         \
-   cudaGetLastError())
-  LBM_DISPATCH(3, 9, CALL_INIT)
-  LBM_DISPATCH(3, 2, CALL_INIT)
-  LBM_DISPATCH(2, 9, CALL_INIT)
-  LBM_DISPATCH(2, 2, CALL_INIT)
-#undef CALL_INIT
-  return cudaErrorInvalidValue;
-}
-
-cudaError_t launch_moments_out(int D, int M, lbm_precision prec, const DevMech& mech,
-                               const Geom& g, const Units& un, const void* pops,
-                               const double* Tfield, double* rho, double* u, double* T,
-                               double* Y, double* E, int* status, cudaStream_t s) {
-  const unsigned nb = blocks_for(g.N, 128);
-#define CALL_OUT(D_, M_, S_, R_)                                                         \
-  (k_out<D_, M_, S_><<<nb, 128, 0, s>>>(static_cast<const S_*>(pops), Tfield, rho, u, T, \
-                                        Y, E, status, g, un, mech),                      \
-   cudaGetLastError())
-  LBM_DISPATCH(3, 9, CALL_OUT)
-  LBM_DISPATCH(3, 2, CALL_OUT)
-  LBM_DISPATCH(2, 9, CALL_OUT)
-  LBM_DISPATCH(2, 2, CALL_OUT)
-#undef CALL_OUT
-  return cudaErrorInvalidValue;
-}
-
-cudaError_t launch_to_fp64(lbm_precision prec, const void* pops, double* out,
-                           long long count, cudaStream_t s) {
-  const unsigned nb = (unsigned)std::min<long long>(blocks_for(count, 256), 152LL * 16);
-  if (prec == LBM_FP64)
-    k_to_fp64<double><<<nb, 256, 0, s>>>(static_cast<const double*>(pops), out, count);
-  else if (prec == LBM_FP32_STORE)
-    k_to_fp64<float><<<nb, 256, 0, s>>>(static_cast<const float*>(pops), out, count);
-  else
-    return cudaErrorInvalidValue;
+template <int D, int M, typename S>
+static cudaError_t out_impl(const DevMech& mech, const Geom& g, const Units& un,
+                            const void* pops, const double* Tfield, double* rho, double* u,
+                            double* T, double* Y, double* E, int* status, cudaStream_t s) {
+  k_out<D, M, S><<<blocks_for(g.N, 128), 128, 0, s>>>(static_cast<const S*>(pops), Tfield,
+                                                       rho, u, T, Y, E, status, g, un, mech);
   return cudaGetLastError();
 }
 
 template <int D, int M, typename S, typename RT>
-static cudaError_t batch_impl(const DomainDev* doms, int ndom, int nblocks, int nbblocks,
-                              int ncblocks, int parity, cudaStream_t s) {
-  const int bs = 128;
-  if (nbblocks > 0)
-    k_boundary_batch<D, M, S><<<nbblocks, bs, 0, s>>>(doms, ndom, parity);
-  k_moments_batch<D, M, S, RT><<<nblocks, bs, 0, s>>>(doms, ndom, parity, ncblocks == 0);
-  if (ncblocks > 0)
-    k_chem_batch<D, M, RT><<<ncblocks, 32 * kChemWarps, 0, s>>>(doms, ndom);
-  const size_t smem = (size_t)collide_smem_entries<D, M, RT>() * bs * sizeof(RT);
-  if (smem > 48 * 1024) {
-    const cudaError_t e = cudaFuncSetAttribute(
-        k_collide_batch<D, M, S, RT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-  }
-  k_collide_batch<D, M, S, RT><<<nblocks, bs, smem, s>>>(doms, ndom, parity);
-  return cudaGetLastError();
-}
-
-template <int D, int M, typename S, typename RT>
-static cudaError_t batch_prepare_impl() {
-  const size_t smem = (size_t)collide_smem_entries<D, M, RT>() * 128 * sizeof(RT);
-  if (smem <= 48 * 1024) return cudaSuccess;
-  return cudaFuncSetAttribute(k_collide_batch<D, M, S, RT>,
-                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-}
-
-cudaError_t prepare_batch_step(int D, int M, lbm_precision prec) {
-#define CALL_PREP(D_, M_, S_, R_) batch_prepare_impl<D_, M_, S_, R_>()
-  LBM_DISPATCH(3, 9, CALL_PREP)
-  LBM_DISPATCH(3, 2, CALL_PREP)
-  LBM_DISPATCH(2, 9, CALL_PREP)
-  LBM_DISPATCH(2, 2, CALL_PREP)
-#undef CALL_PREP
-  return cudaErrorInvalidValue;
-}
-
-cudaError_t launch_batch_step(int D, int M, lbm_precision prec, const DomainDev* doms,
-                              int ndom, int nblocks, int nbblocks, int ncblocks, int parity,
-                              cudaStream_t s) {
-#define CALL_BATCH(D_, M_, S_, R_) \
-  batch_impl<D_, M_, S_, R_>(doms, ndom, nblocks, nbblocks, ncblocks, parity, s)
-  LBM_DISPATCH(3, 9, CALL_BATCH)
-  LBM_DISPATCH(3, 2, CALL_BATCH)
-  LBM_DISPATCH(2, 9, CALL_BATCH)
-  LBM_DISPATCH(2, 2, CALL_BATCH)
-#undef CALL_BATCH
-  return cudaErrorInvalidValue;
-}
-
-int record_fields(int D, int M) {
-  if (D == 3) {
-    if (M == 9) return Rec<3, 9>::NF;
-    if (M == 2) return Rec<3, 2>::NF;
+static cudaError_t batch_impl(const DomainDev* doms, int ndom, const BatchGrids& gr,
+                              const Launch& lc, int parity, cudaStream_t s) {
+  const int bs = kBS;
+  const cudaError_t pe = prepare_once<D, M, S, RT>();
+  if (pe != cudaSuccess) return pe;
+  if (gr.nbblocks > 0)
+    k_boundary_batch<D, M, S><<<gr.nbblocks, bs, 0, s>>>(doms, ndom, parity);
+  k_moments_batch<D, M, S, RT><<<gr.nblocks, bs, 0, s>>>(doms, ndom, parity,
+                                                         lc.chem_lanes <= 1);
+  if (lc.chem_lanes == 4)
+    k_chem_batch<D, M, RT, 4><<<gr.ncblocks, 128, 0, s>>>(doms, ndom);
+  else if (lc.chem_lanes == 8)
+    k_chem_batch<D, M, RT, 8><<<gr.ncblocks, 128, 0, s>>>(doms, ndom);
+  if (lc.coll_split) {
+    k_prep_batch<D, M, RT><<<gr.nblocks, bs, prep_smem<D, M, RT>(), s>>>(doms, ndom);
+    k_coll_batch<D, M, S, RT><<<gr.nkblocks, 32 * kCollTPN, coll_smem<D, M, RT>(), s>>>(
+        doms, ndom, parity);
   } else {
-    if (M == 9) return Rec<2, 9>::NF;
-    if (M == 2) return Rec<2, 2>::NF;
+    k_collide_batch<D, M, S, RT><<<gr.nblocks, bs, fused_smem<D, M, RT>(), s>>>(doms, ndom,
+                                                                              parity);
   }
-  return -1;
+  return cudaGetLastError();
+}
+
+// The kernel set of one (D, M, precision).
+template <int D, int M, typename S, typename RT>
+const KernelSet* make_kernel_set() {
+  static const KernelSet ks = {&step_impl<D, M, S, RT>, &batch_impl<D, M, S, RT>,
+                               &prepare_once<D, M, S, RT>, &init_impl<D, M, S>,
+                               &out_impl<D, M, S>, Rec<D, M>::NF, CPar<D, M>::NF};
+  return &ks;
 }
 
 }  // namespace lbm

@@ -73,7 +73,7 @@ class lbm_config(C.Structure):
 
 
 class lbm_launch(C.Structure):
-    _fields_ = [("chem_per_warp", C.c_int)]
+    _fields_ = [("chem_lanes", C.c_int), ("collide_split", C.c_int)]
 
 
 class lbm_info(C.Structure):
@@ -271,29 +271,33 @@ def lbm_batch_destroy(plan):
     _check(load_library().lbm_batch_destroy(plan), plan.handles[0])
 
 
+def _launch_dict(l):
+    return {"chem_lanes": l.chem_lanes, "collide_split": l.collide_split}
+
+
 def lbm_batch_autotune(plan, trial_steps=3):
-    """Returns the chosen placement: {"chem_per_warp": 0 or 1}."""
+    """Returns the chosen placement {"chem_lanes": 1/4/8, "collide_split": 0/1}."""
     out = lbm_launch()
     _check(load_library().lbm_batch_autotune(plan, int(trial_steps), C.byref(out)),
            plan.handles[0])
-    return {"chem_per_warp": out.chem_per_warp}
+    return _launch_dict(out)
 
 
-def lbm_set_launch(h, chem_per_warp=-1):
-    l = lbm_launch(chem_per_warp=int(chem_per_warp))
+def lbm_set_launch(h, chem_lanes=-1, collide_split=-1):
+    l = lbm_launch(chem_lanes=int(chem_lanes), collide_split=int(collide_split))
     _check(load_library().lbm_set_launch(h, C.byref(l)), h)
 
 
 def lbm_get_launch(h):
     out = lbm_launch()
     _check(load_library().lbm_get_launch(h, C.byref(out)), h)
-    return {"chem_per_warp": out.chem_per_warp}
+    return _launch_dict(out)
 
 
 def lbm_autotune(h, trial_steps=3):
     out = lbm_launch()
     _check(load_library().lbm_autotune(h, int(trial_steps), C.byref(out)), h)
-    return {"chem_per_warp": out.chem_per_warp}
+    return _launch_dict(out)
 
 
 def lbm_step_timed(h, nsteps, kernel_ms=None):
@@ -471,8 +475,8 @@ class Solver:
     def step(self, n=1):
         lbm_step(self.h, n)
 
-    def set_launch(self, chem_per_warp=-1):
-        lbm_set_launch(self.h, chem_per_warp)
+    def set_launch(self, chem_lanes=-1, collide_split=-1):
+        lbm_set_launch(self.h, chem_lanes, collide_split)
 
     def launch(self):
         return lbm_get_launch(self.h)

@@ -87,7 +87,10 @@ def test_defaults_and_bytes_required(lbm):
     cfg.precision = lbm.LBM_FP32_STORE
     n32 = lbm.lbm_bytes_required(cfg)
     NF = 61                       # moment-record fields of D3Q27 with 9 species
-    assert n - n32 == (2 * L * Q + NF) * N * 4   # populations and records halve
+    # collision-parameter fields (split collision): theta_b, V_b, rho_b (M, M*D, M),
+    # cF, 2 beta, drho (M-1 each), u, P^ex, W (D each), rho, omega, U, theta
+    NP = 9 + 27 + 9 + 3 * 8 + 3 * 3 + 4
+    assert n - n32 == (2 * L * Q + NF + NP) * N * 4   # populations and scratch halve
 
 
 @pytest.mark.parametrize("mutate, text", [

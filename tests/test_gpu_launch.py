@@ -1,12 +1,14 @@
-"""Kernel placement of the reaction sub-steps (thread per node inside the
-moments kernel, or one warp per node in their own kernel) and the
-autotuner that chooses between them.
+"""Kernel placement (reaction sub-steps inside the moments kernel or with
+4 / 8 lanes per node in their own kernel; collision fused or split into a
+per-node parameter kernel and a nine-threads-per-node direction kernel) and
+the autotuner that chooses among them.
 
-Both placements evaluate the same rate formulas in the same order, so they
-agree to rounding: 1e-13 relative per lattice in FP64, 1e-5 in FP32 storage
-(the batching tolerance).  The autotuner's trial steps leave the handle's
-state untouched: a solve that was autotuned continues bit for bit like one
-that was not, given the same placement."""
+The placements evaluate the same formulas; only the species production rates
+are summed in another order when the reactions are dealt out over lanes, so
+they agree to rounding: 1e-13 relative per lattice in FP64, 1e-5 in FP32
+storage (the batching tolerance).  The autotuner's trial steps leave the
+handle's state untouched: a solve that was autotuned continues bit for bit
+like one that was not, given the same placement."""
 import numpy as np
 import pytest
 
@@ -17,6 +19,7 @@ from helpers import make_gpu, max_rel_err_per_lattice, perturbed_box
 
 pytestmark = pytest.mark.gpu
 TOL = {"fp64": 1e-13, "fp32": 1e-5}
+PLACEMENTS = [(1, 0), (4, 0), (8, 0), (1, 1), (4, 1), (8, 1)]
 
 
 @pytest.fixture(scope="module")
@@ -27,36 +30,53 @@ def mech():
 def _cases(mech):
     flame = fields.flame_1d(seed=2, nx=48, ny=4, nz=4, x_ign=12, mech=mech)
     chan = fields.channel_2d(seed=4, nx=40, ny=10, mech=mech)
-    box = perturbed_box((9, 6, 5), "D3Q27", mech=mech)
-    return [("flame", flame), ("channel", chan), ("box", box)]
+    box = perturbed_box((9, 6, 5), "D3Q27", mech=mech)      # 270 nodes: a ragged k_coll block
+    tube = fields.microtube(seed=6, nx=12, ny=10, nz=10, radius=4.5, mech=mech)
+    return [("flame", flame), ("channel", chan), ("box", box), ("tube", tube)]
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
-def test_chemistry_placements_agree(mech, precision):
+def test_placements_agree(mech, precision):
     for name, w in _cases(mech):
         got = []
-        for cpw in (0, 1):
+        for cl, cs in PLACEMENTS:
             g = make_gpu(mech, w, precision=precision)
-            g.set_launch(cpw)
-            assert g.launch()["chem_per_warp"] == cpw
+            g.set_launch(cl, cs)
+            assert g.launch() == {"chem_lanes": cl, "collide_split": cs}
             g.step(10)
             got.append(g.populations())
             g.close()
-        err = max_rel_err_per_lattice(got[1], got[0])
-        assert np.all(err < TOL[precision]), (name, err)
+        mask = None
+        if w.get("solid") is not None:
+            mask = ~np.asarray(w["solid"], bool).reshape(-1)
+        for k in range(1, len(got)):
+            err = max_rel_err_per_lattice(got[k], got[0], mask)
+            assert np.all(err < TOL[precision]), (name, PLACEMENTS[k], err)
 
 
 def test_default_placement_follows_grid_size(mech):
-    small = make_gpu(mech, perturbed_box((8, 8, 8), "D3Q27", mech=mech))
-    assert small.launch()["chem_per_warp"] == 1
-    small.set_launch(0)
-    assert small.launch()["chem_per_warp"] == 0
-    small.set_launch(-1)
-    assert small.launch()["chem_per_warp"] == 1
+    small = make_gpu(mech, perturbed_box((8, 8, 8), "D3Q27", mech=mech), precision="fp32")
+    assert small.launch() == {"chem_lanes": 4, "collide_split": 1}
+    small.set_launch(1, 0)
+    assert small.launch() == {"chem_lanes": 1, "collide_split": 0}
+    small.set_launch(-1, -1)
+    assert small.launch() == {"chem_lanes": 4, "collide_split": 1}
     small.close()
-    big = make_gpu(mech, fields.reactor(seed=1, n=48, mech=mech))   # 110,592 nodes
-    assert big.launch()["chem_per_warp"] == 0
+    small64 = make_gpu(mech, perturbed_box((8, 8, 8), "D3Q27", mech=mech))
+    assert small64.launch() == {"chem_lanes": 1, "collide_split": 1}
+    small64.close()
+    big = make_gpu(mech, fields.reactor(seed=1, n=48, mech=mech), precision="fp32")
+    assert big.launch() == {"chem_lanes": 1, "collide_split": 1}     # 110,592 nodes
     big.close()
+
+
+def test_invalid_placement_rejected(mech):
+    from paper_2108_07605_gb300 import lbm
+    g = make_gpu(mech, perturbed_box((4, 4, 4), "D3Q27", mech=mech))
+    for cl, cs in [(2, 0), (0, 0), (4, 2), (16, -1)]:
+        with pytest.raises(lbm.LBMError):
+            g.set_launch(cl, cs)
+    g.close()
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
@@ -65,12 +85,13 @@ def test_autotune_leaves_the_solve_unchanged(mech, precision):
     a = make_gpu(mech, w, precision=precision)
     a.step(3)
     chosen = a.autotune(trial_steps=2)
-    assert chosen["chem_per_warp"] in (0, 1)
+    assert (chosen["chem_lanes"], chosen["collide_split"]) in PLACEMENTS
     assert a.launch() == chosen
     a.step(6)
-    b = make_gpu(mech, w, precision=precision)
-    b.set_launch(chosen["chem_per_warp"])
-    b.step(9)
+    b = make_gpu(mech, w, precision=precision)       # the same history, untuned
+    b.step(3)
+    b.set_launch(chosen["chem_lanes"], chosen["collide_split"])
+    b.step(6)
     pa, pb = a.populations(), b.populations()
     ma, mb = a.moments(), b.moments()
     a.close()
@@ -87,12 +108,12 @@ def test_batch_autotune_then_run_matches_separate_solves(mech):
     batched = [make_gpu(mech, w) for w in ws]
     plan = lbm.lbm_batch_create([g.h for g in batched])
     chosen = lbm.lbm_batch_autotune(plan, trial_steps=2)
-    assert chosen["chem_per_warp"] in (0, 1)
+    assert (chosen["chem_lanes"], chosen["collide_split"]) in PLACEMENTS
     lbm.lbm_batch_run(plan, 5)
     lbm.lbm_batch_destroy(plan)
     for g, w in zip(batched, ws):
         s = make_gpu(mech, w)
-        s.set_launch(chosen["chem_per_warp"])
+        s.set_launch(chosen["chem_lanes"], chosen["collide_split"])
         s.step(5)
         err = max_rel_err_per_lattice(g.populations(), s.populations())
         s.close()

@@ -42,12 +42,12 @@ def test_init_matches_oracle(lattice, shape, mechname):
     ("D3Q27", (10, 7, 5), 12),      # 350 nodes: three blocks and a ragged tail
     ("D2Q9", (23, 17, 1), 15),
 ])
-@pytest.mark.parametrize("chem_per_warp", [0, 1])
-def test_perturbed_box_fp64(mech, lattice, shape, nsteps, chem_per_warp):
+@pytest.mark.parametrize("chem_lanes,collide_split", [(1, 0), (4, 1), (8, 0)])
+def test_perturbed_box_fp64(mech, lattice, shape, nsteps, chem_lanes, collide_split):
     w = perturbed_box(shape, lattice, mech=mech)
     o = make_oracle(mech, w)
     g = make_gpu(mech, w)
-    g.set_launch(chem_per_warp)
+    g.set_launch(chem_lanes, collide_split)
     o.step(nsteps)
     g.step(nsteps)
     err = max_rel_err_per_lattice(g.populations(), oracle_populations(o))
