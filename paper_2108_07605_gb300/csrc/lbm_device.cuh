@@ -288,102 +288,74 @@ __device__ __forceinline__ void solve_dd_strided(R* A, int st, R (&B)[M][D]) {
 // ------------------------------------------------------------------------
 // Equilibrium populations of a macroscopic state (Sec. 4.1, Eqs.
 // faEqGeneral, fEqGeneral, gEqGeneral), used by the boundary procedures.
-template <int D, int M> struct EqSet {
-  double rho, T, th, U;
-  double Y[M], th_a[M], u[D];
-  double us[M][D];   // species velocities, used when own_species_u
+template <int D, int M, typename R = double> struct EqSet {
+  R rho, T, th, U;
+  R Y[M], th_a[M], u[D];
+  R us[M][D];   // species velocities, used when own_species_u
   bool own_species_u;
 };
 
-template <int D, int M>
-__device__ void eq_prepare(EqSet<D, M>& s, const DevMech& m, const Units& un) {
-  double R = 0.0, U = 0.0;
-  for (int a = 0; a < M; ++a) {
-    R += s.Y[a] * m.inv_mm[a];
-    U += s.Y[a] * species_U(m, a, s.T);
-    s.th_a[a] = m.Ra[a] * s.T * un.inv_c2;
+// theta_a, theta and U/c^2 of the state.  FP32 (mixed path): the
+// mixture energy, a sum of formation-energy-sized terms, in float-float.
+template <int D, int M, typename R>
+__device__ void eq_prepare(EqSet<D, M, R>& s, const DevMech& m, const Units& un) {
+  if constexpr (sizeof(R) == 8) {
+    double Rm = 0.0, U = 0.0;
+    for (int a = 0; a < M; ++a) {
+      Rm += s.Y[a] * m.inv_mm[a];
+      U += s.Y[a] * species_U(m, a, s.T);
+      s.th_a[a] = m.Ra[a] * s.T * un.inv_c2;
+    }
+    s.th = R_U * Rm * s.T * un.inv_c2;
+    s.U = U * un.inv_c2;
+  } else {
+    float Rm = 0.f;
+    ff U;
+    const ff T(s.T);
+    for (int a = 0; a < M; ++a) {
+      Rm += s.Y[a] * m.inv_mm_s[a];
+      U += ff(s.Y[a]) * species_U_ff(m, a, T);
+      s.th_a[a] = m.Ra_s[a] * s.T * un.inv_c2_s;
+    }
+    s.th = float(R_U) * Rm * s.T * un.inv_c2_s;
+    s.U = (U * un.inv_c2_f).hi;
   }
-  s.th = R_U * R * s.T * un.inv_c2;
-  s.U = U * un.inv_c2;
 }
 
 // Population l (0..M-2 species, M-1 momentum, M energy) in direction i.
-template <int D, int M>
-__device__ double eq_pop(const EqSet<D, M>& s, int l, int i) {
+template <int D, int M, typename R>
+__device__ R eq_pop(const EqSet<D, M, R>& s, int l, int i) {
   int c[3] = {cvel(i, 0), cvel(i, 1), D == 3 ? cvel(i, 2) : 0};
   if (l < M - 1) {
-    double p = s.rho * s.Y[l];
+    R p = s.rho * s.Y[l];
     for (int d = 0; d < D; ++d) {
-      const double ud = s.own_species_u ? s.us[l][d] : s.u[d];
-      p *= psi1<double>(c[d], ud, s.th_a[l] + ud * ud);
+      const R ud = s.own_species_u ? s.us[l][d] : s.u[d];
+      p *= psi1<R>(c[d], ud, s.th_a[l] + ud * ud);
     }
     return p;
   }
   if (l == M - 1) {
-    double p = s.rho;
-    for (int d = 0; d < D; ++d) p *= psi1<double>(c[d], s.u[d], s.th + s.u[d] * s.u[d]);
+    R p = s.rho;
+    for (int d = 0; d < D; ++d) p *= psi1<R>(c[d], s.u[d], s.th + s.u[d] * s.u[d]);
     return p;
   }
-  double A[3], B[3], prodA = 1.0;
+  R A[3], B[3], prodA = R(1);
   for (int d = 0; d < D; ++d) {
-    const double ua = s.u[d];
-    const double O1 = s.th * ua + 0.5 * ua * ua * ua;
-    const double O2 = s.th * s.th + 2.5 * s.th * ua * ua + 0.5 * ua * ua * ua * ua;
-    A[d] = psi1<double>(c[d], ua, s.th + ua * ua);
-    B[d] = c[d] == 0 ? 0.5 * ua * ua - O2 : 0.5 * (O2 + c[d] * O1);
+    const R ua = s.u[d];
+    const R O1 = s.th * ua + R(0.5) * ua * ua * ua;
+    const R O2 = s.th * s.th + R(2.5) * s.th * ua * ua + R(0.5) * ua * ua * ua * ua;
+    A[d] = psi1<R>(c[d], ua, s.th + ua * ua);
+    B[d] = c[d] == 0 ? R(0.5) * ua * ua - O2 : R(0.5) * (O2 + R(c[d]) * O1);
     prodA *= A[d];
   }
-  double sumB = 0.0;
+  R sumB = R(0);
   for (int d = 0; d < D; ++d) {
-    double t = B[d];
+    R t = B[d];
     for (int e = 0; e < D; ++e)
       if (e != d) t *= A[e];
     sumB += t;
   }
   return s.rho * (s.U * prodA + sumB);
-}
-
-// Macroscopic state of populations given by fetch(l, i): rho, u, Y, u_a
-// (u_a := u below RHO_TINY), T by Newton from T_guess.
-template <int D, int M, typename F>
-__device__ void state_of(F fetch, EqSet<D, M>& s, double T_guess, const DevMech& m,
-                         const Units& un, int* status) {
-  constexpr int Q = Lat<D>::Q;
-  double rho = 0.0, rhoE = 0.0, j[D], rs[M], js[M][D];
-  for (int d = 0; d < D; ++d) j[d] = 0.0;
-  for (int a = 0; a < M; ++a) {
-    rs[a] = 0.0;
-    for (int d = 0; d < D; ++d) js[a][d] = 0.0;
-  }
-  for (int i = 0; i < Q; ++i) {
-    for (int a = 0; a < M - 1; ++a) {
-      const double v = fetch(a, i);
-      rs[a] += v;
-      for (int d = 0; d < D; ++d) js[a][d] += cvel(i, d) * v;
-    }
-    const double f = fetch(M - 1, i);
-    rho += f;
-    for (int d = 0; d < D; ++d) j[d] += cvel(i, d) * f;
-    rhoE += fetch(M, i);
-  }
-  rs[M - 1] = rho;
-  for (int d = 0; d < D; ++d) js[M - 1][d] = j[d];
-  for (int a = 0; a < M - 1; ++a) {
-    rs[M - 1] -= rs[a];
-    for (int d = 0; d < D; ++d) js[M - 1][d] -= js[a][d];
-  }
-  s.rho = rho;
-  double usq = 0.0;
-  for (int d = 0; d < D; ++d) { s.u[d] = j[d] / rho; usq += s.u[d] * s.u[d]; }
-  for (int a = 0; a < M; ++a) {
-    s.Y[a] = rs[a] / rho;
-    const bool tiny = species_velocity_undefined<D, double>(rs[a], js[a]);
-    for (int d = 0; d < D; ++d) s.us[a][d] = tiny ? s.u[d] : js[a][d] / rs[a];
-  }
-  const double U = (rhoE / rho - 0.5 * usq) * un.c * un.c;
-  bool ok;
-  s.T = newton_T<M>(m, s.Y, U, T_guess, un.newton_max_iter, un.newton_rtol, ok);
-  if (!ok) atomicOr(status, ST_NEWTON);
 }
 
 }  // namespace lbm

@@ -1052,32 +1052,36 @@ __device__ __forceinline__ void coll_block(const S* __restrict__ src, S* __restr
 //   B = A (wall: target; outlet: outlet data) or, for the inlet, the
 //   target equilibrium at (rho^loc, Y^loc, u^in, T^in).
 
-__device__ __forceinline__ double warp_sum(double v) {
+template <typename R>
+__device__ __forceinline__ R warp_sum(R v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
 }
 
-// Warp-cooperative state_of: every lane returns the same state.
-template <int D, int M, typename F>
-__device__ void warp_state_of(F fetch, EqSet<D, M>& s, double T_guess, const DevMech& m,
+// Warp-cooperative macroscopic state of populations fetch(l, i): rho, u, Y,
+// u_a (Eq. momentum1 with reading R5), T by Newton on Eq. temperature from
+// T_guess; every lane returns the same state.  R = float (mixed path): sums
+// in FP32, the Newton solve in float-float as in the moments kernel.
+template <int D, int M, typename R, typename F>
+__device__ void warp_state_of(F fetch, EqSet<D, M, R>& s, double T_guess, const DevMech& m,
                               const Units& un, int* status, int lane) {
   constexpr int Q = Lat<D>::Q, L = M + 1;
-  double rho = 0.0, rhoE = 0.0, j[D], rs[M], js[M][D];
-  for (int d = 0; d < D; ++d) j[d] = 0.0;
+  R rho = R(0), rhoE = R(0), j[D], rs[M], js[M][D];
+  for (int d = 0; d < D; ++d) j[d] = R(0);
   for (int a = 0; a < M; ++a) {
-    rs[a] = 0.0;
-    for (int d = 0; d < D; ++d) js[a][d] = 0.0;
+    rs[a] = R(0);
+    for (int d = 0; d < D; ++d) js[a][d] = R(0);
   }
   for (int t = lane; t < L * Q; t += 32) {
     const int l = t / Q, i = t % Q;
-    const double v = fetch(l, i);
+    const R v = fetch(l, i);
     if (l < M - 1) {
       rs[l] += v;
-      for (int d = 0; d < D; ++d) js[l][d] += cvel(i, d) * v;
+      for (int d = 0; d < D; ++d) js[l][d] += R(cvel(i, d)) * v;
     } else if (l == M - 1) {
       rho += v;
-      for (int d = 0; d < D; ++d) j[d] += cvel(i, d) * v;
+      for (int d = 0; d < D; ++d) j[d] += R(cvel(i, d)) * v;
     } else {
       rhoE += v;
     }
@@ -1096,20 +1100,31 @@ __device__ void warp_state_of(F fetch, EqSet<D, M>& s, double T_guess, const Dev
     for (int d = 0; d < D; ++d) js[M - 1][d] -= js[a][d];
   }
   s.rho = rho;
-  double usq = 0.0;
+  R usq = R(0);
   for (int d = 0; d < D; ++d) { s.u[d] = j[d] / rho; usq += s.u[d] * s.u[d]; }
   for (int a = 0; a < M; ++a) {
     s.Y[a] = rs[a] / rho;
-    const bool tiny = species_velocity_undefined<D, double>(rs[a], js[a]);
+    const bool tiny = species_velocity_undefined<D, R>(rs[a], js[a]);
     for (int d = 0; d < D; ++d) s.us[a][d] = tiny ? s.u[d] : js[a][d] / rs[a];
   }
-  const double U = (rhoE / rho - 0.5 * usq) * un.c * un.c;
   bool ok;
-  s.T = newton_T<M>(m, s.Y, U, T_guess, un.newton_max_iter, un.newton_rtol, ok);
+  if constexpr (sizeof(R) == 8) {
+    const double U = (rhoE / rho - 0.5 * usq) * un.c * un.c;
+    s.T = newton_T<M>(m, s.Y, U, T_guess, un.newton_max_iter, un.newton_rtol, ok);
+  } else {
+    ff Yf[M];
+    for (int a = 0; a < M; ++a) Yf[a] = ff(s.Y[a]);
+    const ff U = (ff(rhoE / rho) + ff(-0.5f * usq)) * un.c2_f;
+    s.T = newton_T_ff<M>(m, Yf, U, ff_from_double(T_guess), un.newton_max_iter,
+                         un.newton_rtol_f, ok).hi;
+  }
   if (!ok && lane == 0) atomicOr(status, ST_NEWTON);
 }
 
-template <int D, int M, typename S>
+// Boundary reconstruction of interface node k by one warp (Sec. 4).  R is
+// the lattice type of the path (FP64, or FP32 for FP32 storage); the
+// reconstructed populations are kept in FP64 scratch.
+template <int D, int M, typename S, typename R>
 __device__ __forceinline__ void boundary_body(const S* __restrict__ src, const BCDev& bc,
                                               const double* __restrict__ Tf,
                                               int* __restrict__ status, const Geom& g,
@@ -1126,42 +1141,43 @@ __device__ __forceinline__ void boundary_body(const S* __restrict__ src, const B
   const int y = (int)((n / g.nx) % g.ny);
   const int z = (int)(n / ((long long)g.nx * g.ny));
   const long long st = bc.n_if;
+  auto ld = [&](long long idx) { return R(__ldg(src + idx)); };
   double* P = bc.pops + k;                       // element (l, i) at P[(l Q + i) st]
   for (int t = lane; t < L * Q; t += 32) {       // pull streaming (wrapped address)
     const int l = t / Q, i = t % Q;
     const long long sn = node_shift<D>(x, y, z, i, -1, g);
     P[(long long)t * st] = (inc >> i & 1u) && kind == BK_BB
-                               ? ldp(src + (long long)(l * Q + (Q - 1 - i)) * N + n)
-                               : ldp(src + (long long)t * N + sn);
+                               ? double(__ldg(src + (long long)(l * Q + (Q - 1 - i)) * N + n))
+                               : double(__ldg(src + (long long)t * N + sn));
   }
   if (kind == BK_BB) return;
   __syncwarp();
-  EqSet<D, M> A, B, loc;
+  EqSet<D, M, R> A, B, loc;
   A.own_species_u = B.own_species_u = false;
   if (kind == BK_TMS) {
     // step 1: bounce-back density and mass fractions (Eqs. BBrho, BBY)
-    double rho_bb = 0.0, rs[M];
-    for (int a = 0; a < M - 1; ++a) rs[a] = 0.0;
+    R rho_bb = R(0), rs[M];
+    for (int a = 0; a < M - 1; ++a) rs[a] = R(0);
     for (int t = lane; t < M * Q; t += 32) {
       const int l = t / Q, i = t % Q;
-      const double v = (inc >> i & 1u) ? ldp(src + (long long)(l * Q + (Q - 1 - i)) * N + n)
-                                       : P[(long long)t * st];
+      const R v = (inc >> i & 1u) ? ld((long long)(l * Q + (Q - 1 - i)) * N + n)
+                                  : R(P[(long long)t * st]);
       if (l < M - 1) rs[l] += v; else rho_bb += v;
     }
     rho_bb = warp_sum(rho_bb);
     for (int a = 0; a < M - 1; ++a) rs[a] = warp_sum(rs[a]);
     A.rho = rho_bb;
-    double ysum = 0.0;
+    R ysum = R(0);
     for (int a = 0; a < M - 1; ++a) { A.Y[a] = rs[a] / rho_bb; ysum += A.Y[a]; }
-    A.Y[M - 1] = 1.0 - ysum;
-    for (int d = 0; d < D; ++d) A.u[d] = 0.0;      // u^tgt = u_a^tgt = 0
-    A.T = bc.if_wallT[k];
+    A.Y[M - 1] = R(1) - ysum;
+    for (int d = 0; d < D; ++d) A.u[d] = R(0);     // u^tgt = u_a^tgt = 0
+    A.T = R(bc.if_wallT[k]);
     eq_prepare(A, mech, un);                         // step 2: target (Eqs. tgtf-tgtfa)
   } else if (kind == BK_INLET) {
-    A.rho = bc.rho_in;
-    for (int a = 0; a < M; ++a) A.Y[a] = bc.Y_in[a];
-    for (int d = 0; d < D; ++d) A.u[d] = bc.if_uin[(long long)d * st + k];
-    A.T = bc.T_in;
+    A.rho = R(bc.rho_in);
+    for (int a = 0; a < M; ++a) A.Y[a] = R(bc.Y_in[a]);
+    for (int d = 0; d < D; ++d) A.u[d] = R(bc.if_uin[(long long)d * st + k]);
+    A.T = R(bc.T_in);
     eq_prepare(A, mech, un);                         // step 1 (Eqs. in_f-in_fa)
   } else {
     // LODI data from the stored state at x and x - n (Eq. convectiveBC)
@@ -1169,66 +1185,72 @@ __device__ __forceinline__ void boundary_body(const S* __restrict__ src, const B
     const int sg = (info >> 6) & 1 ? 1 : -1;
     const long long stride = ax == 0 ? 1 : (ax == 1 ? (long long)g.nx : (long long)g.nx * g.ny);
     const long long up = n - sg * stride;
-    EqSet<D, M> s0, s1;
-    warp_state_of<D, M>([&](int l, int i) { return ldp(src + (long long)(l * Q + i) * N + n); },
-                        s0, Tf[n], mech, un, status, lane);
-    warp_state_of<D, M>([&](int l, int i) { return ldp(src + (long long)(l * Q + i) * N + up); },
-                        s1, Tf[up], mech, un, status, lane);
+    EqSet<D, M, R> s0, s1;
+    warp_state_of<D, M, R>([&](int l, int i) { return ld((long long)(l * Q + i) * N + n); },
+                           s0, Tf[n], mech, un, status, lane);
+    warp_state_of<D, M, R>([&](int l, int i) { return ld((long long)(l * Q + i) * N + up); },
+                           s1, Tf[up], mech, un, status, lane);
+    // LODI wave amplitudes (reading R13) in FP64 from the two states: a few
+    // scalars per node
     double R0 = 0.0, R1 = 0.0, Cv = 0.0;
+    const double T0 = s0.T, T1 = s1.T;
     for (int a = 0; a < M; ++a) {
-      R0 += s0.Y[a] * mech.inv_mm[a];
-      R1 += s1.Y[a] * mech.inv_mm[a];
-      Cv += s0.Y[a] * (mech.u1[a] + s0.T * (2.0 * mech.u2[a] + 3.0 * s0.T * mech.u3[a]));
+      R0 += double(s0.Y[a]) * mech.inv_mm[a];
+      R1 += double(s1.Y[a]) * mech.inv_mm[a];
+      Cv += double(s0.Y[a]) * (mech.u1[a] + T0 * (2.0 * mech.u2[a] + 3.0 * T0 * mech.u3[a]));
     }
     R0 *= R_U;
     R1 *= R_U;
-    const double p0 = s0.rho * R0 * s0.T * un.inv_c2;
-    const double p1 = s1.rho * R1 * s1.T * un.inv_c2;
-    const double un0 = sg * s0.u[ax], un1 = sg * s1.u[ax];
+    const double r0 = s0.rho, r1 = s1.rho;
+    const double p0 = r0 * R0 * T0 * un.inv_c2;
+    const double p1 = r1 * R1 * T1 * un.inv_c2;
+    const double un0 = sg * double(s0.u[ax]), un1 = sg * double(s1.u[ax]);
     const double gamma = (Cv + R0) / Cv;
-    const double cs = sqrt(gamma * R0 * s0.T * un.inv_c2);
+    const double cs = sqrt(gamma * R0 * T0 * un.inv_c2);
     const double Ma = un0 / cs;
     const double Ln = ax == 0 ? g.nx : (ax == 1 ? g.ny : g.nz);
     const double K = bc.sigma * (1.0 - Ma * Ma) * cs / Ln;
     const double L1 = K * (p0 - bc.p_out_lat);
-    const double L2 = un0 * (cs * cs * (s0.rho - s1.rho) - (p0 - p1));
-    const double L5 = (un0 + cs) * ((p0 - p1) + s0.rho * cs * (un0 - un1));
-    A.rho = s0.rho - (L2 + 0.5 * (L5 + L1)) / (cs * cs);
+    const double L2 = un0 * (cs * cs * (r0 - r1) - (p0 - p1));
+    const double L5 = (un0 + cs) * ((p0 - p1) + r0 * cs * (un0 - un1));
+    const double rho_o = r0 - (L2 + 0.5 * (L5 + L1)) / (cs * cs);
+    A.rho = R(rho_o);
     const double p_o = p0 - 0.5 * (L5 + L1);
-    const double un_o = un0 - (L5 - L1) / (2.0 * s0.rho * cs);
-    for (int d = 0; d < D; ++d) A.u[d] = s0.u[d] - un0 * (s0.u[d] - s1.u[d]);
-    A.u[ax] = sg * un_o;
+    const double un_o = un0 - (L5 - L1) / (2.0 * r0 * cs);
+    for (int d = 0; d < D; ++d) A.u[d] = R(double(s0.u[d]) - un0 * double(s0.u[d] - s1.u[d]));
+    A.u[ax] = R(sg * un_o);
     double Ro = 0.0;
     for (int a = 0; a < M; ++a) {
-      A.Y[a] = s0.Y[a] - un0 * (s0.Y[a] - s1.Y[a]);
-      Ro += A.Y[a] * mech.inv_mm[a];
+      const double Ya = double(s0.Y[a]) - un0 * double(s0.Y[a] - s1.Y[a]);
+      A.Y[a] = R(Ya);
+      Ro += Ya * mech.inv_mm[a];
     }
-    A.T = p_o * un.c * un.c / (A.rho * R_U * Ro);
+    A.T = R(p_o * un.c * un.c / (rho_o * R_U * Ro));
     eq_prepare(A, mech, un);                         // step 1 (Eqs. out_f-out_fa)
   }
   // incoming links at A, then the local state (Eqs. locRho-locT and analogues)
   for (int t = lane; t < L * Q; t += 32) {
     const int l = t / Q, i = t % Q;
-    if (inc >> i & 1u) P[(long long)t * st] = eq_pop(A, l, i);
+    if (inc >> i & 1u) P[(long long)t * st] = double(eq_pop(A, l, i));
   }
   __syncwarp();
-  warp_state_of<D, M>([&](int l, int i) { return P[(long long)(l * Q + i) * st]; }, loc,
-                      Tf[n], mech, un, status, lane);
+  warp_state_of<D, M, R>([&](int l, int i) { return R(P[(long long)(l * Q + i) * st]); }, loc,
+                         Tf[n], mech, un, status, lane);
   loc.own_species_u = kind == BK_TMS;             // TMS local species use u_a^loc
   eq_prepare(loc, mech, un);
   if (kind == BK_INLET) {                         // target (Eqs. in_tgt_*)
     B.rho = loc.rho;
     for (int a = 0; a < M; ++a) B.Y[a] = loc.Y[a];
     for (int d = 0; d < D; ++d) B.u[d] = A.u[d];
-    B.T = bc.T_in;
+    B.T = R(bc.T_in);
     eq_prepare(B, mech, un);
   }
-  const EqSet<D, M>& Bref = kind == BK_INLET ? B : A;
+  const EqSet<D, M, R>& Bref = kind == BK_INLET ? B : A;
   __syncwarp();
   for (int t = lane; t < L * Q; t += 32) {
     const int l = t / Q, i = t % Q;
     double& p = P[(long long)t * st];
-    p = eq_pop(Bref, l, i) + p - eq_pop(loc, l, i);
+    p = double(eq_pop(Bref, l, i) + R(p) - eq_pop(loc, l, i));
   }
 }
 
@@ -1300,8 +1322,8 @@ k_boundary(const S* __restrict__ src, const __grid_constant__ BCDev bc,
            const double* __restrict__ Tf, int* __restrict__ status,
            const __grid_constant__ Geom g, const __grid_constant__ Units un,
            const __grid_constant__ DevMech mech) {
-  boundary_body<D, M, S>(src, bc, Tf, status, g, un, mech,
-                         blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32, threadIdx.x & 31);
+  boundary_body<D, M, S, S>(src, bc, Tf, status, g, un, mech,
+                            blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32, threadIdx.x & 31);
 }
 
 // ---------------------------------------------------------------------------
@@ -1380,9 +1402,9 @@ __global__ void __launch_bounds__(128)
 k_boundary_batch(const DomainDev* __restrict__ doms, int ndom, int parity) {
   const DomainDev& d = doms[domain_of_block(doms, ndom, blockIdx.x, GRID_BOUNDARY)];
   const int c = d.cur0 ^ parity;
-  boundary_body<D, M, S>(static_cast<const S*>(d.pops[c]), d.bc, d.Tf, d.status, d.g, d.un,
-                         *d.mech, (blockIdx.x - d.bblock_begin) * 4 + threadIdx.x / 32,
-                         threadIdx.x & 31);
+  boundary_body<D, M, S, S>(static_cast<const S*>(d.pops[c]), d.bc, d.Tf, d.status, d.g,
+                            d.un, *d.mech, (blockIdx.x - d.bblock_begin) * 4 + threadIdx.x / 32,
+                            threadIdx.x & 31);
 }
 
 // ---------------------------------------------------------------------------

