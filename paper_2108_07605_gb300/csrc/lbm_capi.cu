@@ -33,6 +33,8 @@ struct lbm_ctx {
   long long steps = 0;
   bool initialized = false;
   lbm_launch opt = {-1, -1};  // placement as set (-1: by grid size)
+  cudaStream_t side = nullptr;  // boundary kernel, concurrent with the bulk moments
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   void* cpar = nullptr;     // per-node collision parameters (split collision)
   std::string err;
 };
@@ -567,6 +569,15 @@ lbm_status lbm_create(const lbm_config* cfg, lbm_t* out) {
     return fail(nullptr, LBM_ERR_CUDA, "mechanism upload failed");
   }
   h->bytes += sizeof(DevMech);
+  if (hb.n_if > 0) {
+    cudaError_t e = cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+      lbm_destroy(h);
+      return fail(nullptr, LBM_ERR_CUDA, std::string("side stream: ") + cudaGetErrorString(e));
+    }
+  }
   if (hb.needed) {
     h->bc_mem = dalloc(h->cfg, s.bc);
     if (!h->bc_mem) {
@@ -660,6 +671,9 @@ lbm_status lbm_step(lbm_t h, int nsteps) {
   a.lc = resolve_launch(h->opt, h->g.N, h->cfg.precision);
   a.mech_dev = h->mech_dev;
   a.cpar = h->cpar;
+  a.side = h->side;
+  a.ev_fork = h->ev_fork;
+  a.ev_join = h->ev_join;
   for (int k = 0; k < nsteps; ++k) {
     a.src = h->pops[h->cur];
     a.dst = h->pops[1 - h->cur];
@@ -690,6 +704,9 @@ lbm_status lbm_step_timed(lbm_t h, int nsteps, double* kernel_ms, int n_kernels)
   a.lc = resolve_launch(h->opt, h->g.N, h->cfg.precision);
   a.mech_dev = h->mech_dev;
   a.cpar = h->cpar;
+  a.side = h->side;
+  a.ev_fork = h->ev_fork;
+  a.ev_join = h->ev_join;
   cudaError_t err = cudaSuccess;
   for (int k = 0; k < nsteps && err == cudaSuccess; ++k) {
     a.src = h->pops[h->cur];
@@ -761,6 +778,9 @@ lbm_status lbm_autotune(lbm_t h, int trial_steps, lbm_launch* chosen) {
   a.bc = h->bc;
   a.mech_dev = h->mech_dev;
   a.cpar = h->cpar;
+  a.side = h->side;
+  a.ev_fork = h->ev_fork;
+  a.ev_join = h->ev_join;
   float best_ms = 0.f;
   Launch best;
   bool first = true;
@@ -856,6 +876,7 @@ struct lbm_batch_ctx {
   DomainDev* ddev = nullptr;
   BatchGrids gr;
   Launch lc;                   // placement of the captured step
+  SideStream side;             // boundary branch of the captured step
   int parity = 0;
   cudaStream_t stream = nullptr;
   cudaGraphExec_t one[2] = {nullptr, nullptr}, two[2] = {nullptr, nullptr};
@@ -880,7 +901,7 @@ cudaError_t batch_capture(lbm_batch_ctx* b, int first_parity, int nsteps, cudaGr
   cudaError_t e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
   for (int k = 0; k < nsteps && e == cudaSuccess; ++k)
     e = launch_batch_step(h0->D, h0->M, h0->cfg.precision, b->ddev, (int)b->hs.size(), b->gr,
-                          b->lc, (first_parity + k) & 1, b->stream);
+                          b->lc, (first_parity + k) & 1, b->stream, b->side);
   const cudaError_t e2 = cudaStreamEndCapture(b->stream, &graph);
   if (e == cudaSuccess) e = e2;
   if (e == cudaSuccess) e = cudaGraphInstantiate(out, graph, 0);
@@ -915,6 +936,9 @@ lbm_status lbm_batch_destroy(lbm_batch_t b) {
   if (!b) return LBM_OK;
   if (b->stream) cudaStreamSynchronize(b->stream);
   batch_release_graphs(b);
+  if (b->side.fork) cudaEventDestroy(b->side.fork);
+  if (b->side.join) cudaEventDestroy(b->side.join);
+  if (b->side.stream) cudaStreamDestroy(b->side.stream);
   if (b->ddev && !b->hs.empty()) dfree(b->hs[0]->cfg, b->ddev);
   if (b->stream) cudaStreamDestroy(b->stream);
   delete b;
@@ -932,6 +956,9 @@ lbm_status lbm_batch_create(lbm_t* hs, int n, lbm_batch_t* out) {
   b->hs.assign(hs, hs + n);
   b->cur.assign(n, 0);
   cudaError_t e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->side.stream, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->side.fork, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->side.join, cudaEventDisableTiming);
   if (e == cudaSuccess) {
     b->ddev = static_cast<DomainDev*>(dalloc(h0->cfg, n * sizeof(DomainDev)));
     if (!b->ddev) e = cudaErrorMemoryAllocation;
@@ -1018,11 +1045,11 @@ lbm_status lbm_batch_autotune(lbm_batch_t b, int trial_steps, lbm_launch* chosen
     // handle from its current buffer, advancing none of them
     if (e == cudaSuccess)
       e = launch_batch_step(h0->D, h0->M, h0->cfg.precision, b->ddev, n, b->gr, b->lc, 0,
-                            b->stream);
+                            b->stream, b->side);
     if (e == cudaSuccess) e = cudaEventRecord(e0, b->stream);
     for (int t = 0; t < trial_steps && e == cudaSuccess; ++t)
       e = launch_batch_step(h0->D, h0->M, h0->cfg.precision, b->ddev, n, b->gr, b->lc, 0,
-                            b->stream);
+                            b->stream, b->side);
     if (e == cudaSuccess) e = cudaEventRecord(e1, b->stream);
     for (int k = 0; k < n && e == cudaSuccess; ++k)
       e = cudaMemcpyAsync(b->hs[k]->Tf, Tsave[k], (size_t)b->hs[k]->g.N * sizeof(double),
@@ -1194,6 +1221,9 @@ lbm_status lbm_destroy(lbm_t h) {
   dfree(h->cfg, h->io);
   dfree(h->cfg, h->bc_mem);
   dfree(h->cfg, h->mech_dev);
+  if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+  if (h->ev_join) cudaEventDestroy(h->ev_join);
+  if (h->side) cudaStreamDestroy(h->side);
   delete h;
   return st;
 }

@@ -57,9 +57,9 @@ cudaError_t prepare_batch_step(int D, int M, lbm_precision prec) {
 
 cudaError_t launch_batch_step(int D, int M, lbm_precision prec, const DomainDev* doms,
                               int ndom, const BatchGrids& gr, const Launch& lc, int parity,
-                              cudaStream_t s) {
+                              cudaStream_t s, const SideStream& side) {
   const KernelSet* k = kernel_set(D, M, prec);
-  return k ? k->batch(doms, ndom, gr, lc, parity, s) : cudaErrorInvalidValue;
+  return k ? k->batch(doms, ndom, gr, lc, parity, s, side) : cudaErrorInvalidValue;
 }
 
 int record_fields(int D, int M) {

@@ -120,6 +120,10 @@ struct StepArgs {
   Launch lc;                   // default: chemistry and collision one thread per node
   const DevMech* mech_dev = nullptr;   // device copy of the mechanism (k_chem)
   void* cpar = nullptr;        // per-node collision parameters [NF][N] (split collision)
+  // optional side stream for the boundary kernel, forked from and joined to
+  // the step's stream with these events (all three or none)
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 };
 
 // One domain of a batched step (lbm_batch_step): every block of the batched
@@ -142,6 +146,13 @@ struct DomainDev {
   int kblock_begin = 0;        // first block in the split-collision grid (k_coll)
 };
 
+// A side stream with fork / join events (all set, or the step runs on one
+// stream).
+struct SideStream {
+  cudaStream_t stream = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr;
+};
+
 // Block totals of the batched grids.
 struct BatchGrids {
   int nblocks = 0;    // node kernels, 128 nodes per block
@@ -154,7 +165,7 @@ struct BatchGrids {
 // and laid out for the placement lc.
 cudaError_t launch_batch_step(int D, int M, lbm_precision prec, const DomainDev* doms,
                               int ndom, const BatchGrids& gr, const Launch& lc, int parity,
-                              cudaStream_t s);
+                              cudaStream_t s, const SideStream& side = SideStream());
 // nodes per block of the split-collision kernel k_coll
 constexpr int kCollNodesPerBlock = 32;
 // fields of the per-node collision parameters (split collision)
@@ -168,7 +179,7 @@ cudaError_t prepare_batch_step(int D, int M, lbm_precision prec);
 struct KernelSet {
   cudaError_t (*step)(const DevMech& mech, const StepArgs& a, cudaStream_t s, int which);
   cudaError_t (*batch)(const DomainDev* doms, int ndom, const BatchGrids& gr, const Launch& lc,
-                       int parity, cudaStream_t s);
+                       int parity, cudaStream_t s, const SideStream& side);
   cudaError_t (*prepare)();
   cudaError_t (*init)(const DevMech& mech, const Geom& g, const Units& un,
                       const double* rho_or_P, int is_pressure, const double* u,

@@ -1188,8 +1188,10 @@ __device__ __forceinline__ void boundary_body(const S* __restrict__ src, const B
     EqSet<D, M, R> s0, s1;
     warp_state_of<D, M, R>([&](int l, int i) { return ld((long long)(l * Q + i) * N + n); },
                            s0, Tf[n], mech, un, status, lane);
+    // (the upstream node's Newton starts from this node's T guess: the bulk
+    // moments kernel may be rewriting the upstream one concurrently)
     warp_state_of<D, M, R>([&](int l, int i) { return ld((long long)(l * Q + i) * N + up); },
-                           s1, Tf[up], mech, un, status, lane);
+                           s1, Tf[n], mech, un, status, lane);
     // LODI wave amplitudes (reading R13) in FP64 from the two states: a few
     // scalars per node
     double R0 = 0.0, R1 = 0.0, Cv = 0.0;
@@ -1257,14 +1259,26 @@ __device__ __forceinline__ void boundary_body(const S* __restrict__ src, const B
 // ---------------------------------------------------------------------------
 // Single-domain kernels: one thread per node (moments, collision), one warp
 // per interface node (boundary).
+// node sets of the moments kernel: every node, the nodes without boundary
+// reconstruction, or the interface nodes (after the boundary kernel, which a
+// side stream runs concurrently with the bulk)
+enum { NODES_ALL = 0, NODES_BULK = 1, NODES_INTERFACE = 2 };
+
 template <int D, int M, typename S, typename RT>
 __global__ void __launch_bounds__(128)
 k_moments(const S* __restrict__ src, RT* __restrict__ rec, double* __restrict__ Tf,
           int* __restrict__ status, const __grid_constant__ Geom g,
           const __grid_constant__ Units un, const __grid_constant__ BCDev bc,
-          const __grid_constant__ DevMech mech, int chem_inline) {
-  moments_body<D, M, S, RT>(src, rec, Tf, status, g, un, bc, mech,
-                            blockIdx.x * (long long)blockDim.x + threadIdx.x, chem_inline);
+          const __grid_constant__ DevMech mech, int chem_inline, int node_set) {
+  const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  long long n = idx;
+  if (node_set == NODES_INTERFACE) {
+    if (idx >= bc.n_if) return;
+    n = bc.if_node[idx];
+  } else if (node_set == NODES_BULK && bc.tag && n < g.N && bc.tag[n] >= 0) {
+    return;
+  }
+  moments_body<D, M, S, RT>(src, rec, Tf, status, g, un, bc, mech, n, chem_inline);
 }
 
 // reaction sub-steps, L lanes per node, 128 threads per block
@@ -1346,13 +1360,25 @@ __device__ __forceinline__ int domain_of_block(const DomainDev* __restrict__ d, 
 
 template <int D, int M, typename S, typename RT>
 __global__ void __launch_bounds__(128)
-k_moments_batch(const DomainDev* __restrict__ doms, int ndom, int parity, int chem_inline) {
-  const DomainDev& d = doms[domain_of_block(doms, ndom, blockIdx.x, GRID_NODE)];
+k_moments_batch(const DomainDev* __restrict__ doms, int ndom, int parity, int chem_inline,
+                int node_set) {
+  // NODES_INTERFACE: the boundary grid (four interface nodes per block), one
+  // thread per interface node
+  const DomainDev& d = doms[domain_of_block(
+      doms, ndom, blockIdx.x, node_set == NODES_INTERFACE ? GRID_BOUNDARY : GRID_NODE)];
   const int c = d.cur0 ^ parity;
+  long long n;
+  if (node_set == NODES_INTERFACE) {
+    if (threadIdx.x & 31) return;
+    const long long k = (blockIdx.x - d.bblock_begin) * 4LL + (threadIdx.x >> 5);
+    if (k >= d.bc.n_if) return;
+    n = d.bc.if_node[k];
+  } else {
+    n = (blockIdx.x - d.block_begin) * (long long)blockDim.x + threadIdx.x;
+    if (node_set == NODES_BULK && d.bc.tag && n < d.g.N && d.bc.tag[n] >= 0) return;
+  }
   moments_body<D, M, S, RT>(static_cast<const S*>(d.pops[c]), static_cast<RT*>(d.rec), d.Tf,
-                            d.status, d.g, d.un, d.bc, *d.mech,
-                            (blockIdx.x - d.block_begin) * (long long)blockDim.x + threadIdx.x,
-                            chem_inline);
+                            d.status, d.g, d.un, d.bc, *d.mech, n, chem_inline);
 }
 
 template <int D, int M, typename RT, int L>
@@ -1581,12 +1607,32 @@ static cudaError_t step_impl(const DevMech& mech, const StepArgs& a, cudaStream_
   const bool chem_sep = lc.chem_lanes > 1 && a.mech_dev;
   const bool split = lc.coll_split && a.cpar;
   if (which != 1) {
-    if (a.bc.n_if > 0)
-      k_boundary<D, M, S><<<(a.bc.n_if + 3) / 4, 128, 0, s>>>(
-          static_cast<const S*>(a.src), a.bc, a.Tfield, a.status, a.g, a.un, mech);
-    k_moments<D, M, S, RT><<<nb, bs, 0, s>>>(static_cast<const S*>(a.src),
-                                             reinterpret_cast<RT*>(a.rec), a.Tfield,
-                                             a.status, a.g, a.un, a.bc, mech, !chem_sep);
+    const S* src = static_cast<const S*>(a.src);
+    RT* rec = reinterpret_cast<RT*>(a.rec);
+    // the boundary kernel (a few warps, latency-bound) and the moments of
+    // the interface nodes run on the side stream while the bulk moments run
+    const bool fork = a.bc.n_if > 0 && a.side && a.ev_fork && a.ev_join;
+    if (fork) {
+      cudaError_t e = cudaEventRecord(a.ev_fork, s);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(a.side, a.ev_fork, 0);
+      if (e != cudaSuccess) return e;
+      k_boundary<D, M, S><<<(a.bc.n_if + 3) / 4, 128, 0, a.side>>>(src, a.bc, a.Tfield,
+                                                                  a.status, a.g, a.un, mech);
+      k_moments<D, M, S, RT><<<blocks_for(a.bc.n_if, bs), bs, 0, a.side>>>(
+          src, rec, a.Tfield, a.status, a.g, a.un, a.bc, mech, !chem_sep, NODES_INTERFACE);
+      e = cudaEventRecord(a.ev_join, a.side);
+      if (e != cudaSuccess) return e;
+      k_moments<D, M, S, RT><<<nb, bs, 0, s>>>(src, rec, a.Tfield, a.status, a.g, a.un, a.bc,
+                                               mech, !chem_sep, NODES_BULK);
+      e = cudaStreamWaitEvent(s, a.ev_join, 0);
+      if (e != cudaSuccess) return e;
+    } else {
+      if (a.bc.n_if > 0)
+        k_boundary<D, M, S><<<(a.bc.n_if + 3) / 4, 128, 0, s>>>(src, a.bc, a.Tfield, a.status,
+                                                                a.g, a.un, mech);
+      k_moments<D, M, S, RT><<<nb, bs, 0, s>>>(src, rec, a.Tfield, a.status, a.g, a.un, a.bc,
+                                               mech, !chem_sep, NODES_ALL);
+    }
     if (chem_sep)
       launch_chem<D, M, RT>(lc, blocks_for(a.g.N, 128 / lc.chem_lanes), s,
                             reinterpret_cast<RT*>(a.rec), a.Tfield, a.status, a.g.N, a.bc.tag,
@@ -1631,14 +1677,33 @@ static cudaError_t out_impl(const DevMech& mech, const Geom& g, const Units& un,
 
 template <int D, int M, typename S, typename RT>
 static cudaError_t batch_impl(const DomainDev* doms, int ndom, const BatchGrids& gr,
-                              const Launch& lc, int parity, cudaStream_t s) {
+                              const Launch& lc, int parity, cudaStream_t s,
+                              const SideStream& side) {
   const int bs = kBS;
   const cudaError_t pe = prepare_once<D, M, S, RT>();
   if (pe != cudaSuccess) return pe;
-  if (gr.nbblocks > 0)
-    k_boundary_batch<D, M, S><<<gr.nbblocks, bs, 0, s>>>(doms, ndom, parity);
-  k_moments_batch<D, M, S, RT><<<gr.nblocks, bs, 0, s>>>(doms, ndom, parity,
-                                                         lc.chem_lanes <= 1);
+  const int chem_inline = lc.chem_lanes <= 1;
+  if (gr.nbblocks > 0 && side.stream && side.fork && side.join) {
+    // boundary kernel and the interface nodes' moments on the side stream,
+    // concurrent with the bulk moments
+    cudaError_t e = cudaEventRecord(side.fork, s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(side.stream, side.fork, 0);
+    if (e != cudaSuccess) return e;
+    k_boundary_batch<D, M, S><<<gr.nbblocks, bs, 0, side.stream>>>(doms, ndom, parity);
+    k_moments_batch<D, M, S, RT><<<gr.nbblocks, bs, 0, side.stream>>>(
+        doms, ndom, parity, chem_inline, NODES_INTERFACE);
+    e = cudaEventRecord(side.join, side.stream);
+    if (e != cudaSuccess) return e;
+    k_moments_batch<D, M, S, RT><<<gr.nblocks, bs, 0, s>>>(doms, ndom, parity, chem_inline,
+                                                           NODES_BULK);
+    e = cudaStreamWaitEvent(s, side.join, 0);
+    if (e != cudaSuccess) return e;
+  } else {
+    if (gr.nbblocks > 0)
+      k_boundary_batch<D, M, S><<<gr.nbblocks, bs, 0, s>>>(doms, ndom, parity);
+    k_moments_batch<D, M, S, RT><<<gr.nblocks, bs, 0, s>>>(doms, ndom, parity, chem_inline,
+                                                           NODES_ALL);
+  }
   if (lc.chem_lanes == 4)
     k_chem_batch<D, M, RT, 4><<<gr.ncblocks, 128, 0, s>>>(doms, ndom);
   else if (lc.chem_lanes == 8)
