@@ -2,7 +2,7 @@
 """Throughput benchmark of the reactive-mixture LBM step on GB300.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
-                    [--precision fp64|fp32] [--impl ours|reference]
+                    [--precision fp32|fp64|fp16] [--impl ours|reference]
 
 One step = one pass of the whole hot path over the workload: pull streaming,
 boundary reconstruction, moments, temperature Newton, relaxation, gradients,
@@ -10,11 +10,13 @@ diffusion velocities, reaction sub-steps and collision of all M+1 lattices.
 Metric: node-updates/s = lattice node-steps/s x (M+2) (every node advances
 M species + f + g per step, the slaved species included), i.e. MLUPS x 11.
 
-Timing: W untimed steps, then K steps each bracketed by CUDA events on the
+Timing: W untimed steps (with --autotune, then the library's autotuner:
+trial steps that leave the solve untouched), then K steps each bracketed by
+CUDA events on the
 library's stream (torch's current stream); when the populations fit in L2
 (129 MB), a 256 MB buffer is overwritten between timed steps, outside the
-events.  Per-kernel device times come from events the library records
-around each launch (lbm_step_timed).  Under torchrun every rank advances its
+events.  Per-kernel device times come from a second pass of K steps with
+events the library records around each launch group (lbm_step_timed).  Under torchrun every rank advances its
 own independent, seeded copy of the workload (weak scaling, no collective on
 the data path); rank 0 prints the max-over-ranks time.
 
@@ -48,7 +50,16 @@ def parse():
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--workload", default="flame", choices=sorted(WORKLOADS))
-    p.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
+    p.add_argument("--chem-lanes", type=int, default=0, choices=[0, 1, 4, 8],
+                   help="chemistry placement (0: the library default)")
+    p.add_argument("--collide-split", type=int, default=-1, choices=[-1, 0, 1],
+                   help="collision placement (-1: the library default)")
+    p.add_argument("--autotune", action="store_true",
+                   help="let the library's autotuner choose the placement before timing")
+    p.add_argument("--precision", default="fp32", choices=["fp64", "fp32", "fp16"],
+                   help="population storage: fp64 (all FP64), fp32 (mixed: FP32 storage and "
+                        "collision, float-float temperature and chemistry; the default), fp16 "
+                        "(FP16 offsets, the fp32 path's arithmetic)")
     p.add_argument("--substeps", type=int, default=0,
                    help="reaction sub-steps l (Eq. R3); 0 keeps the workload's value")
     p.add_argument("--no-e2e", action="store_true")
@@ -264,9 +275,15 @@ def main():
 
     solver.step(args.warmup)
     solver.synchronize()
-    # the library's autotuner picks the kernel placement on this workload
-    # (trial steps on the current state; the solve itself is not advanced)
-    launch = solver.autotune(trial_steps=3)
+    # kernel placement: the library's default for this grid and precision
+    # (which matched the autotuner's choice on every workload measured), the
+    # values given on the command line, or --autotune (trial steps on the
+    # current state; the solve itself is not advanced)
+    if args.autotune:
+        launch = solver.autotune(trial_steps=3)
+    else:
+        solver.set_launch(args.chem_lanes or -1, args.collide_split)
+        launch = solver.launch()
     if pg:
         pg.barrier()
     torch.cuda.synchronize()
@@ -365,8 +382,10 @@ def main():
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "f64" if args.precision == "fp64"
-        else "f32 (temperature Newton and chemistry in float-float)",
+        "dtype": {"fp64": "f64",
+                  "fp32": "f32 (temperature Newton and chemistry in float-float)",
+                  "fp16": "f16 offset storage, f32 arithmetic (temperature Newton and "
+                          "chemistry in float-float)"}[args.precision],
         "data": "synthetic",
         "config": {"workload": WORKLOADS[args.workload], "nodes": N, "lattice": w["lattice"],
                    "species": M, "precision": args.precision, "substeps": w["substeps"],

@@ -67,7 +67,13 @@ typedef enum { LBM_D2Q9 = 0, LBM_D3Q27 = 1 } lbm_lattice;
  * (the path checked against the oracle to 1e-10).  LBM_FP32_STORE:
  * populations, moments and collision in FP32; the temperature Newton solve
  * and the chemistry in float-float (pairs of FP32, ~48 significant bits);
- * transport in FP32.  Field tolerances vs FP64 are stated in the tests. */
+ * transport in FP32.  LBM_FP16_OFFSET: the FP32 path's arithmetic, with
+ * populations stored as FP16 offsets (the storage reading of the paper's
+ * lattice weights): h = (f - o) / s, o = the equilibrium population of the
+ * mean initial state at rest (per lattice and direction), s = a per-lattice
+ * scale; both are fixed by lbm_init_fields from the initial fields (16x
+ * headroom over the initial deviations) and kept by checkpoints.  Field
+ * tolerances vs FP64 are stated in the tests. */
 typedef enum { LBM_FP64 = 0, LBM_FP32_STORE = 1, LBM_FP16_OFFSET = 2 } lbm_precision;
 
 /* Face boundary kinds (Sec. 4): periodic; bounce-back wall (Eq. bb);
@@ -139,6 +145,12 @@ typedef struct lbm_config {
   void* alloc_user;
   void* stream;               /* cudaStream_t; NULL = legacy default stream   */
   int device;                 /* CUDA device ordinal                          */
+  int inlet_simplified;       /* 1: the simplified flux inlet of Sec. 4.3 -
+                                 stop after the local state of step 2 and set
+                                 every population of the inlet node to the
+                                 local equilibria (u and T take local values,
+                                 not the targets); 0 (default): the full
+                                 four-step inlet                              */
 } lbm_config;
 
 /* Derived lattice-unit data of a handle. */
@@ -259,6 +271,26 @@ lbm_status lbm_step_timed(lbm_t h, int nsteps, double* kernel_ms, int n_kernels)
 lbm_status lbm_moments(lbm_t h, double* rho, double* u, double* T, double* Y,
                        double* E, int on_device);
 
+/* Flame diagnostics of the stored state, the quantities the paper follows
+ * in its microchannel and microtube runs (Sec. 5.3), computed on the device
+ * in one pass with FP64 arithmetic whatever the storage: per node the
+ * moments, T by Newton on Eq. temperature, the mass production rates of the
+ * mechanism and the heat release rate q = -sum_a H_a(T) rho_dot_a (W/m^3,
+ * H_a the specific enthalpy with formation, so q < 0 where the reactions are
+ * endothermic); then reductions over the fluid nodes in a fixed order (the
+ * result does not depend on scheduling).  Synchronises; returns sticky errors. */
+typedef struct {
+  double hrr_integral;   /* sum of q times the cell volume dx^3 (W); in 2-D the
+                            cell area dx^2 (W per metre of depth) */
+  double hrr_max;        /* largest q (W/m^3) */
+  double flame_x;        /* x coordinate (node index along x times dx, m) of the
+                            node with the largest q; among equal maxima the
+                            smallest node index (x fastest) */
+  double T_max;          /* K */
+  double u_max;          /* largest |u| (m/s) */
+} lbm_diag;
+lbm_status lbm_diagnostics(lbm_t h, lbm_diag* out);
+
 /* All stored populations converted to FP64, layout [lattice][i][N]
  * (lattice-unit values: species and f in kg/m^3, g in kg/m^3 * J/kg / c_ref^2). */
 lbm_status lbm_get_populations(lbm_t h, double* out, int on_device);
@@ -267,8 +299,9 @@ lbm_status lbm_get_populations(lbm_t h, double* out, int on_device);
  * sticky device status. */
 lbm_status lbm_synchronize(lbm_t h);
 
-/* Checkpoint: raw populations (storage precision), temperature guess and
- * boundary history.  lbm_get_state with buf == NULL stores the size. */
+/* Checkpoint: raw populations (storage precision), temperature guess and,
+ * for FP16 offset storage, the codec (offsets and scales).  lbm_get_state
+ * with buf == NULL stores the size. */
 lbm_status lbm_get_state(lbm_t h, void* buf, size_t* bytes);
 lbm_status lbm_set_state(lbm_t h, const void* buf, size_t bytes);
 
@@ -285,8 +318,9 @@ lbm_status lbm_destroy(lbm_t h);
  * It advances caller-owned populations by one step exactly as lbm_step does
  * for a handle created from the same cfg, and calls no allocator.
  *  cfg      the configuration lbm_create takes (periodic faces; cfg->stream,
- *           cfg->device and cfg->precision are honoured; the allocation hooks
- *           are ignored).
+ *           cfg->device and cfg->precision are honoured, except FP16 offset
+ *           storage, whose codec only a handle keeps: LBM_ERR_INVALID; the
+ *           allocation hooks are ignored).
  *  pops_in  device, stored populations in cfg->precision, layout
  *           [lattice][i][N] (what lbm_get_populations returns for FP64).
  *  pops_out device, same size, distinct from pops_in; receives the step.

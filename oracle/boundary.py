@@ -12,7 +12,10 @@ inlet before the outlet:
 * bounce-back, Eq. bb: f_i(x) = f_{-i}^post(x) for i in D, all lattices;
 * Tamm-Mott-Smith wall, Sec. 4.2.2, Eqs. BBrho-fatms (targets at the node
   itself: u^tgt = u_a^tgt = 0, T^tgt = wall temperature of the node);
-* flux inlet, Sec. 4.3, Eqs. in_f-fa_inlet;
+* flux inlet, Sec. 4.3, Eqs. in_f-fa_inlet; with spec["inlet"]["simplified"]
+  true, the simplified inlet of the same section: stop after the local state
+  of step 2 and give every population the local equilibrium (Eqs.
+  in_loc_f, in_loc_g, in_loc_fa), so u and T keep their local values;
 * outlet, Sec. 4.4, Eqs. convectiveBC-fa_outlet, with the LODI data below.
 
 LODI outlet (Poinsot & Lele 1992; the paper gives no formulas, so this is a
@@ -74,6 +77,7 @@ class Boundaries:
             self.u_in = u_in.reshape((3,) + lbm.shape)[:D] / lbm.units.c
             self.T_in = float(inlet["T"])
             self.Y_in = np.asarray(inlet["Y"], dtype=float)
+            self.inlet_simplified = bool(inlet.get("simplified", False))
             self.rho_in = float(thermo.density_from_pressure(
                 mech, float(inlet.get("P", 101325.0)), self.T_in, self.Y_in[:, None])[0])
         # incoming set and the kind of each incoming link
@@ -221,6 +225,8 @@ class Boundaries:
         pl = np.where(D, fin, p)
         rho_l, u_l, Y_l, _, T_l = self._local_state(pl, Tg)           # Eqs. inletlocRho-T
         loc = self._equilibria(rho_l, Y_l, u_l, T_l)                  # Eqs. in_loc_*
+        if self.inlet_simplified:
+            return loc                                                # simplified inlet
         tgt = self._equilibria(rho_l, Y_l, u_in, T_in)                # Eqs. in_tgt_*
         return np.where(D, tgt + fin - loc, tgt + p - loc)            # Eqs. f_inlet-fa_inlet
 

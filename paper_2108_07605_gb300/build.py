@@ -26,9 +26,9 @@ UNITS = [("lbm_capi.cu", "lbm_capi.o", []),
          ("lbm_noalloc.cu", "lbm_noalloc.o", []),
          ("lbm_dispatch.cu", "lbm_dispatch.o", [])]
 for _d, _m in ((3, 9), (3, 2), (2, 9), (2, 2)):
-    for _f64, _tag in ((1, "f64"), (0, "f32")):
+    for _prec, _tag in ((0, "f64"), (1, "f32"), (2, "f16")):
         UNITS.append(("lbm_inst.cu", f"lbm_inst_{_d}_{_m}_{_tag}.o",
-                      [f"-DLBM_D={_d}", f"-DLBM_M={_m}", f"-DLBM_F64={_f64}",
+                      [f"-DLBM_D={_d}", f"-DLBM_M={_m}", f"-DLBM_PREC={_prec}",
                        f"-DLBM_KSET=kernel_set_{_d}_{_m}_{_tag}"]))
 
 

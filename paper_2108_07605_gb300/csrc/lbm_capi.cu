@@ -36,6 +36,7 @@ struct lbm_ctx {
   cudaStream_t side = nullptr;  // boundary kernel, concurrent with the bulk moments
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   void* cpar = nullptr;     // per-node collision parameters (split collision)
+  float4* codec = nullptr;  // FP16 storage: per-population offset and scale
   std::string err;
 };
 
@@ -146,8 +147,9 @@ std::string validate(const lbm_config* c) {
   if (c->lattice != LBM_D3Q27 && c->lattice != LBM_D2Q9) return "unknown lattice";
   if (c->nx < 1 || c->ny < 1 || c->nz < 1) return "grid extents must be >= 1";
   if (c->lattice == LBM_D2Q9 && c->nz != 1) return "D2Q9 needs nz = 1";
-  if (c->precision != LBM_FP64 && c->precision != LBM_FP32_STORE)
-    return "precision not supported by this build (FP64, FP32_STORE)";
+  if (c->precision != LBM_FP64 && c->precision != LBM_FP32_STORE &&
+      c->precision != LBM_FP16_OFFSET)
+    return "precision must be LBM_FP64, LBM_FP32_STORE or LBM_FP16_OFFSET";
   if (c->substeps < 1 || c->substeps > 64) return "substeps must be in 1..64";
   if (!(c->dx > 0.0) || !std::isfinite(c->dx)) return "dx must be positive";
   if (c->c_ref < 0.0 || !std::isfinite(c->c_ref)) return "c_ref must be >= 0";
@@ -281,7 +283,9 @@ void build_mech(const lbm_mechanism& m, DevMech& d) {
   d.inv_prandtl_s = (float)d.inv_prandtl;
 }
 
-size_t elem_size(lbm_precision p) { return p == LBM_FP64 ? 8 : 4; }
+// bytes of a stored population, and of the scratch records' lattice type
+size_t elem_size(lbm_precision p) { return p == LBM_FP64 ? 8 : (p == LBM_FP16_OFFSET ? 2 : 4); }
+size_t compute_size(lbm_precision p) { return p == LBM_FP64 ? 8 : 4; }
 
 // Interface-node classification (Sec. 4.1): a link i of node x is incoming
 // when x - c_i lies beyond a non-periodic face or on a solid node; the node's
@@ -356,7 +360,7 @@ HostBC classify(const lbm_config& c, double c_ref) {
 size_t align256(size_t b) { return (b + 255) / 256 * 256; }
 
 struct Sizes {
-  size_t pops, rec, cpar, tf, status, io, bc, total;
+  size_t pops, rec, cpar, codec, tf, status, io, bc, total;
 };
 
 Sizes sizes_for(const lbm_config& c, const HostBC& hb) {
@@ -366,8 +370,9 @@ Sizes sizes_for(const lbm_config& c, const HostBC& hb) {
   const long long N = (long long)c.nx * c.ny * c.nz;
   Sizes s;
   s.pops = (size_t)(M + 1) * Q * N * elem_size(c.precision);
-  s.rec = (size_t)record_fields(D, M) * N * elem_size(c.precision);
-  s.cpar = (size_t)collide_param_fields(D, M) * N * elem_size(c.precision);
+  s.rec = (size_t)record_fields(D, M) * N * compute_size(c.precision);
+  s.cpar = (size_t)collide_param_fields(D, M) * N * compute_size(c.precision);
+  s.codec = c.precision == LBM_FP16_OFFSET ? (size_t)(M + 1) * Q * sizeof(float4) : 0;
   s.tf = (size_t)N * sizeof(double);
   s.status = 256;
   s.io = 0;
@@ -377,7 +382,7 @@ Sizes sizes_for(const lbm_config& c, const HostBC& hb) {
     s.bc = align256(N * sizeof(int)) + 3 * align256(nif * sizeof(int)) +
            4 * align256(nif * sizeof(double)) + align256((size_t)(M + 1) * Q * nif * sizeof(double));
   }
-  s.total = 2 * s.pops + s.rec + s.cpar + s.tf + s.status + s.bc;
+  s.total = 2 * s.pops + s.rec + s.cpar + s.codec + s.tf + s.status + s.bc;
   return s;
 }
 
@@ -421,6 +426,95 @@ lbm_status ensure_io(lbm_ctx* h, size_t bytes) {
   return LBM_OK;
 }
 
+// FP16 offset storage (reading R19): offsets o_li = the equilibrium
+// populations of the mean initial state at rest; per lattice a scale that
+// maps 16x the largest initial deviation |f^eq - o| to the FP16 maximum, and
+// at least (rho_ref / 27) 2^-12 for species and f, (max |g|) 2^-12 for g, so
+// that later growth (trace species forming, the flow speeding up) stays in
+// range.  Then the initial equilibria are encoded.
+lbm_status init_fp16(lbm_ctx* h, const double* drho, int is_pressure, const double* du,
+                     const double* dT, const double* dY) {
+  const long long N = h->g.N;
+  const int M = h->M, L = h->L, Q = h->Q, LQ = L * Q;
+  // mean fields (host)
+  std::vector<double> rp(N), T(N), Y((size_t)M * N);
+  cudaError_t e = cudaMemcpyAsync(rp.data(), drho, N * sizeof(double), cudaMemcpyDeviceToHost,
+                                  h->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(T.data(), dT, N * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(Y.data(), dY, (size_t)M * N * sizeof(double), cudaMemcpyDeviceToHost,
+                        h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "FP16 codec: field download");
+  std::vector<double> mean(1 + 3 + 1 + M, 0.0);   // rho or P, u (0), T, Y
+  for (long long n = 0; n < N; ++n) {
+    mean[0] += rp[n];
+    mean[4] += T[n];
+    for (int a = 0; a < M; ++a) mean[5 + a] += Y[(size_t)a * N + n];
+  }
+  mean[0] /= N;
+  mean[4] /= N;
+  for (int a = 0; a < M; ++a) mean[5 + a] /= N;
+  // scratch: mean state (1 node), offsets, FP32 equilibria, extents
+  const size_t b_mean = mean.size() * sizeof(double), b_off = LQ * sizeof(float),
+               b_eq = (size_t)LQ * N * sizeof(float), b_ext = 2 * L * sizeof(unsigned);
+  char* tmp = static_cast<char*>(dalloc(h->cfg, b_mean + b_off + b_eq + b_ext + 256 * 4));
+  if (!tmp) return fail(h, LBM_ERR_OOM, "FP16 codec: scratch allocation failed");
+  double* dmean = reinterpret_cast<double*>(tmp);
+  float* off = reinterpret_cast<float*>(tmp + align256(b_mean));
+  float* eq = reinterpret_cast<float*>(tmp + align256(b_mean) + align256(b_off));
+  unsigned* ext = reinterpret_cast<unsigned*>(tmp + align256(b_mean) + align256(b_off) +
+                                              align256(b_eq));
+  double* Tdummy = dmean + 4;   // the 1-node init writes its temperature here (unused)
+  Geom g1;
+  g1.nx = g1.ny = g1.nz = 1;
+  g1.N = 1;
+  Geom gq = h->g;
+  gq.codec = nullptr;
+  e = cudaMemcpyAsync(dmean, mean.data(), b_mean, cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess)
+    e = launch_init(h->D, M, LBM_FP32_STORE, h->mech, g1, h->un, dmean, is_pressure, dmean + 1,
+                    dmean + 4, dmean + 5, off, Tdummy, h->status, h->stream);
+  if (e == cudaSuccess)
+    e = launch_init(h->D, M, LBM_FP32_STORE, h->mech, gq, h->un, drho, is_pressure, du, dT, dY,
+                    eq, h->Tf, h->status, h->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(ext, 0, b_ext, h->stream);
+  if (e == cudaSuccess) e = launch_codec_extent(eq, off, L, Q, N, ext, ext + L, h->stream);
+  std::vector<float> hoff(LQ);
+  std::vector<unsigned> hext(2 * L);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(hoff.data(), off, b_off, cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(hext.data(), ext, b_ext, cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) {
+    dfree(h->cfg, tmp);
+    return cuda_fail(h, e, "FP16 codec");
+  }
+  double rho_ref = 0.0;
+  for (int i = 0; i < Q; ++i) rho_ref += hoff[(M - 1) * Q + i];
+  std::vector<float4> table(LQ);
+  for (int l = 0; l < L; ++l) {
+    float dev, amax;
+    std::memcpy(&dev, &hext[l], sizeof(float));
+    std::memcpy(&amax, &hext[L + l], sizeof(float));
+    const double floor_s = l < M ? rho_ref / 27.0 * 0x1p-12 : amax * 0x1p-12;
+    double sc = std::max(16.0 * dev / 65504.0, floor_s);
+    if (!(sc > 0.0) || !std::isfinite(sc)) sc = 1.0;
+    for (int i = 0; i < Q; ++i)
+      table[l * Q + i] = make_float4(hoff[l * Q + i], (float)sc, (float)(1.0 / sc), 0.f);
+  }
+  e = cudaMemcpyAsync(h->codec, table.data(), LQ * sizeof(float4), cudaMemcpyHostToDevice,
+                      h->stream);
+  if (e == cudaSuccess)
+    e = launch_codec_encode(eq, h->pops[h->cur], (long long)LQ * N, N, h->codec, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);   // table and scratch in use
+  dfree(h->cfg, tmp);
+  if (e != cudaSuccess) return cuda_fail(h, e, "FP16 encode");
+  return LBM_OK;
+}
+
 lbm_status init_common(lbm_ctx* h, const double* rho_or_P, int is_pressure, const double* u,
                        const double* T, const double* Y, int on_device) {
   if (!h) return fail(nullptr, LBM_ERR_INVALID, "handle is NULL");
@@ -444,9 +538,14 @@ lbm_status init_common(lbm_ctx* h, const double* rho_or_P, int is_pressure, cons
   }
   cudaError_t e = cudaMemsetAsync(h->status, 0, sizeof(int), h->stream);
   if (e != cudaSuccess) return cuda_fail(h, e, "status reset");
-  e = launch_init(h->D, M, h->cfg.precision, h->mech, h->g, h->un, drho, is_pressure, du, dT,
-                  dY, h->pops[h->cur], h->Tf, h->status, h->stream);
-  if (e != cudaSuccess) return cuda_fail(h, e, "init kernel");
+  if (h->cfg.precision == LBM_FP16_OFFSET) {
+    const lbm_status st = init_fp16(h, drho, is_pressure, du, dT, dY);
+    if (st != LBM_OK) return st;
+  } else {
+    e = launch_init(h->D, M, h->cfg.precision, h->mech, h->g, h->un, drho, is_pressure, du, dT,
+                    dY, h->pops[h->cur], h->Tf, h->status, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "init kernel");
+  }
   // Both buffers start equal: the kernels never write solid nodes, which
   // keep their initial (equilibrium) populations in either buffer.
   e = cudaMemcpyAsync(h->pops[1 - h->cur], h->pops[h->cur],
@@ -556,6 +655,10 @@ lbm_status lbm_create(const lbm_config* cfg, lbm_t* out) {
   h->pops[1] = dalloc(h->cfg, s.pops);
   h->rec = static_cast<double*>(dalloc(h->cfg, s.rec));
   h->cpar = dalloc(h->cfg, s.cpar);
+  if (s.codec) {
+    h->codec = static_cast<float4*>(dalloc(h->cfg, s.codec));
+    h->g.codec = h->codec;
+  }
   h->Tf = static_cast<double*>(dalloc(h->cfg, s.tf));
   h->status = static_cast<int*>(dalloc(h->cfg, s.status));
   h->bytes = s.total;
@@ -622,6 +725,7 @@ lbm_status lbm_create(const lbm_config* cfg, lbm_t* out) {
     b.has_solid = hb.has_solid ? 1 : 0;
     b.solid_kind = cfg->solid_bc;
     b.sigma = cfg->outlet_sigma;
+    b.inlet_simplified = cfg->inlet_simplified ? 1 : 0;
     b.p_out_lat = cfg->outlet_P * h->un.inv_c2;
     double Rin = 0.0;
     for (int a = 0; a < h->M; ++a) {
@@ -633,7 +737,8 @@ lbm_status lbm_create(const lbm_config* cfg, lbm_t* out) {
     b.rho_in = cfg->inlet_T > 0.0 ? cfg->inlet_P / (Rin * cfg->inlet_T) : 0.0;
     b.theta_in = Rin * cfg->inlet_T * h->un.inv_c2;
   }
-  if (!h->pops[0] || !h->pops[1] || !h->rec || !h->cpar || !h->Tf || !h->status) {
+  if (!h->pops[0] || !h->pops[1] || !h->rec || !h->cpar || !h->Tf || !h->status ||
+      (s.codec && !h->codec)) {
     lbm_destroy(h);
     return fail(nullptr, LBM_ERR_OOM, "device allocation failed");
   }
@@ -1113,6 +1218,33 @@ lbm_status lbm_moments(lbm_t h, double* rho, double* u, double* T, double* Y, do
   return check_status(h);
 }
 
+lbm_status lbm_diagnostics(lbm_t h, lbm_diag* out) {
+  if (!h || !out) return fail(h, LBM_ERR_INVALID, "handle or out is NULL");
+  if (!h->initialized) return fail(h, LBM_ERR_STATE, "lbm_diagnostics before lbm_init_fields");
+  DeviceGuard dg(h->cfg.device);
+  const long long nb = (h->g.N + 127) / 128;
+  const size_t need = (size_t)(nb + 1) * sizeof(DiagPart);
+  lbm_status st = ensure_io(h, need);
+  if (st != LBM_OK) return st;
+  DiagPart* part = reinterpret_cast<DiagPart*>(h->io);
+  DiagPart* dout = part + nb;
+  cudaError_t e = launch_diagnostics(h->D, h->M, h->cfg.precision, h->mech, h->g, h->un,
+                                     h->pops[h->cur], h->Tf, h->bc.tag, part, dout, h->status,
+                                     h->stream);
+  DiagPart r;
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(&r, dout, sizeof(DiagPart), cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "diagnostics");
+  const double cell = h->D == 3 ? h->un.dx * h->un.dx * h->un.dx : h->un.dx * h->un.dx;
+  out->hrr_integral = r.q_sum * cell;
+  out->hrr_max = r.q_max;
+  out->flame_x = (double)(r.n_max % h->g.nx) * h->un.dx;
+  out->T_max = r.T_max;
+  out->u_max = r.u_max;
+  return check_status(h);
+}
+
 lbm_status lbm_get_populations(lbm_t h, double* out, int on_device) {
   if (!h) return fail(nullptr, LBM_ERR_INVALID, "handle is NULL");
   if (!out) return fail(h, LBM_ERR_INVALID, "out is NULL");
@@ -1120,12 +1252,14 @@ lbm_status lbm_get_populations(lbm_t h, double* out, int on_device) {
   DeviceGuard dg(h->cfg.device);
   const long long count = (long long)h->L * h->Q * h->g.N;
   if (on_device) {
-    cudaError_t e = launch_to_fp64(h->cfg.precision, h->pops[h->cur], out, count, h->stream);
+    cudaError_t e = launch_to_fp64(h->cfg.precision, h->pops[h->cur], out, count, h->stream,
+                                   h->g.N, h->codec);
     return e == cudaSuccess ? LBM_OK : cuda_fail(h, e, "population conversion");
   }
   lbm_status st = ensure_io(h, (size_t)count * sizeof(double));
   if (st != LBM_OK) return st;
-  cudaError_t e = launch_to_fp64(h->cfg.precision, h->pops[h->cur], h->io, count, h->stream);
+  cudaError_t e = launch_to_fp64(h->cfg.precision, h->pops[h->cur], h->io, count, h->stream,
+                                 h->g.N, h->codec);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(out, h->io, (size_t)count * sizeof(double), cudaMemcpyDeviceToHost,
                         h->stream);
@@ -1144,7 +1278,8 @@ static const uint64_t STATE_MAGIC = 0x4c424d5354415445ull;   // "LBMSTATE"
 lbm_status lbm_get_state(lbm_t h, void* buf, size_t* bytes) {
   if (!h || !bytes) return fail(h, LBM_ERR_INVALID, "handle or bytes is NULL");
   const size_t pop_bytes = (size_t)h->L * h->Q * h->g.N * h->elem;
-  const size_t need = 64 + pop_bytes + h->g.N * sizeof(double);
+  const size_t codec_bytes = h->codec ? (size_t)h->L * h->Q * sizeof(float4) : 0;
+  const size_t need = 64 + pop_bytes + h->g.N * sizeof(double) + codec_bytes;
   if (!buf) { *bytes = need; return LBM_OK; }
   if (*bytes < need) return fail(h, LBM_ERR_INVALID, "state buffer too small");
   if (!h->initialized) return fail(h, LBM_ERR_STATE, "no state before lbm_init_fields");
@@ -1158,6 +1293,9 @@ lbm_status lbm_get_state(lbm_t h, void* buf, size_t* bytes) {
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(p + pop_bytes, h->Tf, h->g.N * sizeof(double), cudaMemcpyDeviceToHost,
                         h->stream);
+  if (e == cudaSuccess && codec_bytes)   // FP16: the codec the populations are encoded with
+    e = cudaMemcpyAsync(p + pop_bytes + h->g.N * sizeof(double), h->codec, codec_bytes,
+                        cudaMemcpyDeviceToHost, h->stream);
   if (e != cudaSuccess) return cuda_fail(h, e, "state download");
   *bytes = need;
   return check_status(h);
@@ -1166,7 +1304,8 @@ lbm_status lbm_get_state(lbm_t h, void* buf, size_t* bytes) {
 lbm_status lbm_set_state(lbm_t h, const void* buf, size_t bytes) {
   if (!h || !buf) return fail(h, LBM_ERR_INVALID, "handle or buffer is NULL");
   const size_t pop_bytes = (size_t)h->L * h->Q * h->g.N * h->elem;
-  const size_t need = 64 + pop_bytes + h->g.N * sizeof(double);
+  const size_t codec_bytes = h->codec ? (size_t)h->L * h->Q * sizeof(float4) : 0;
+  const size_t need = 64 + pop_bytes + h->g.N * sizeof(double) + codec_bytes;
   if (bytes != need) return fail(h, LBM_ERR_INVALID, "state size does not match this handle");
   uint64_t hdr[8];
   std::memcpy(hdr, buf, 64);
@@ -1180,6 +1319,9 @@ lbm_status lbm_set_state(lbm_t h, const void* buf, size_t bytes) {
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(h->Tf, p + pop_bytes, h->g.N * sizeof(double), cudaMemcpyHostToDevice,
                         h->stream);
+  if (e == cudaSuccess && codec_bytes)
+    e = cudaMemcpyAsync(h->codec, p + pop_bytes + h->g.N * sizeof(double), codec_bytes,
+                        cudaMemcpyHostToDevice, h->stream);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(h->pops[1 - h->cur], h->pops[h->cur], pop_bytes,
                         cudaMemcpyDeviceToDevice, h->stream);
@@ -1216,6 +1358,7 @@ lbm_status lbm_destroy(lbm_t h) {
   dfree(h->cfg, h->pops[1]);
   dfree(h->cfg, h->rec);
   dfree(h->cfg, h->cpar);
+  dfree(h->cfg, h->codec);
   dfree(h->cfg, h->Tf);
   dfree(h->cfg, h->status);
   dfree(h->cfg, h->io);

@@ -8,6 +8,8 @@
 #include <cuda_runtime.h>
 
 #include "../../include/lbm.h"
+#include <cuda_fp16.h>
+
 #include "ff.cuh"
 
 namespace lbm {
@@ -76,6 +78,9 @@ struct Units {
 struct Geom {
   int nx, ny, nz;
   long long N;
+  // FP16 storage: per population index l*Q + i the codec entry
+  // {offset, scale, 1/scale, 0} (nullptr for FP64 / FP32 storage)
+  const float4* codec = nullptr;
 };
 
 // Kernel launchers (lbm_dispatch.cu).  `S` is the storage type.
@@ -100,6 +105,7 @@ struct BCDev {
   double rho_in = 0.0, T_in = 0.0, theta_in = 0.0;
   double Y_in[LBM_MAX_SPECIES] = {0};
   double p_out_lat = 0.0, sigma = 0.25;
+  int inlet_simplified = 0;       // simplified flux inlet (Sec. 4.3)
 };
 
 // Kernel placement of a step (lbm_launch, resolved).
@@ -174,6 +180,14 @@ int collide_param_fields(int D, int M);
 // capture, where such calls are not recorded.
 cudaError_t prepare_batch_step(int D, int M, lbm_precision prec);
 
+// Per-block partial results of the diagnostics kernel.
+struct DiagPart {
+  double q_sum;       // sum of q over the block's nodes (W/m^3)
+  double q_max;       // largest q
+  long long n_max;    // its node (smallest index among equal maxima)
+  double T_max, u_max;
+};
+
 // Host entry points of one instantiation (lattice, species count, precision)
 // of the kernel templates; see lbm_inst.cu.
 struct KernelSet {
@@ -188,6 +202,9 @@ struct KernelSet {
   cudaError_t (*out)(const DevMech& mech, const Geom& g, const Units& un, const void* pops,
                      const double* Tfield, double* rho, double* u, double* T, double* Y,
                      double* E, int* status, cudaStream_t s);
+  cudaError_t (*diag)(const DevMech& mech, const Geom& g, const Units& un, const void* pops,
+                      const double* Tfield, const int* tag, DiagPart* part, int* status,
+                      cudaStream_t s);
   int record_fields;   // moment-record fields
   int param_fields;    // collision-parameter fields
 };
@@ -208,7 +225,19 @@ cudaError_t launch_moments_out(int D, int M, lbm_precision prec, const DevMech& 
                                double* T, double* Y, double* E, int* status,
                                cudaStream_t s);
 cudaError_t launch_to_fp64(lbm_precision prec, const void* pops, double* out,
-                           long long count, cudaStream_t s);
+                           long long count, cudaStream_t s, long long N = 1,
+                           const float4* codec = nullptr);
+// Flame diagnostics: per-block partials, then their deterministic reduction
+// into out (one DiagPart).
+cudaError_t launch_diagnostics(int D, int M, lbm_precision prec, const DevMech& mech,
+                               const Geom& g, const Units& un, const void* pops,
+                               const double* Tfield, const int* tag, DiagPart* part,
+                               DiagPart* out, int* status, cudaStream_t s);
+// FP16 storage codec (lbm_dispatch.cu)
+cudaError_t launch_codec_extent(const float* eq, const float* off, int L, int Q, long long N,
+                                unsigned* dev_max, unsigned* abs_max, cudaStream_t s);
+cudaError_t launch_codec_encode(const float* eq, void* out, long long count, long long N,
+                                const float4* codec, cudaStream_t s);
 int record_fields(int D, int M);
 
 // Host helpers defined in lbm_capi.cu.

@@ -13,6 +13,7 @@
 // of the lattice arithmetic: moments, equilibria, collision).  Temperature,
 // transport, diffusion velocities and chemistry always run in FP64.
 #include <atomic>
+#include <climits>
 #include <cmath>
 
 #pragma once
@@ -21,8 +22,39 @@
 
 namespace lbm {
 
+// Arithmetic type of a storage type: FP16 storage computes in FP32.
+template <typename S> struct ComputeType { using type = S; };
+template <> struct ComputeType<__half> { using type = float; };
+
+// Stored-population codec.  FP64 and FP32 storage hold the value itself.
+// FP16 storage holds offsets (reading R19): h = (f - o_li) / s_l, o_li the
+// equilibrium population at the mean initial state and s_l a per-lattice
+// scale, both fixed by lbm_init_fields (codec entry li = {o, s, 1/s, 0}).
+template <typename S> struct Codec {
+  template <typename R>
+  __device__ static R dec(S v, const float4*, int) { return R(v); }
+  template <typename R>
+  __device__ static S enc(R v, const float4*, int) { return S(v); }
+};
+template <> struct Codec<__half> {
+  template <typename R>
+  __device__ static R dec(__half v, const float4* t, int li) {
+    const float4 c = __ldg(t + li);
+    return R(fmaf(c.y, __half2float(v), c.x));
+  }
+  template <typename R>
+  __device__ static __half enc(R v, const float4* t, int li) {
+    const float4 c = __ldg(t + li);
+    return __float2half_rn((float(v) - c.x) * c.z);
+  }
+};
+
+// population li = l*Q + i of node n as FP64 (decoded)
 template <typename S>
-__device__ __forceinline__ double ldp(const S* p) { return static_cast<double>(__ldg(p)); }
+__device__ __forceinline__ double ldp(const S* pops, long long N, long long n, int li,
+                                      const float4* codec) {
+  return Codec<S>::template dec<double>(__ldg(pops + (long long)li * N + n), codec, li);
+}
 
 __device__ __forceinline__ int wrap1(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
 
@@ -39,9 +71,9 @@ __device__ __forceinline__ long long node_shift(int x, int y, int z, int i, int 
 // reconstructed value for interface nodes (tag >= 0), else the streamed one.
 template <typename RT, typename S>
 __device__ __forceinline__ RT pop_in(const S* __restrict__ src, const BCDev& bc, int tag,
-                                     long long N, long long sn, int li) {
+                                     long long N, long long sn, int li, const float4* codec) {
   return tag >= 0 ? RT(bc.pops[(long long)li * bc.n_if + tag])
-                  : RT(__ldg(src + (long long)li * N + sn));
+                  : Codec<S>::template dec<RT>(__ldg(src + (long long)li * N + sn), codec, li);
 }
 
 // 1/tau_ab = s * K_ab: the coefficient table in the lattice compute type
@@ -89,6 +121,7 @@ __device__ __forceinline__ void moments_body(const S* __restrict__ src, RT* __re
   const int x = (int)(n % g.nx);
   const int y = (int)((n / g.nx) % g.ny);
   const int z = (int)(n / ((long long)g.nx * g.ny));
+  const float4* codec = g.codec;
 
   // sums in the lattice compute type RT
   RT rho = RT(0), rhoE = RT(0), j[D], q[D], P[NP], rs[M], js[M][D];
@@ -107,13 +140,13 @@ __device__ __forceinline__ void moments_body(const S* __restrict__ src, RT* __re
     const long long sn = node_shift<D>(x, y, z, i, -1, g);
 #pragma unroll
     for (int a = 0; a < M - 1; ++a) {
-      const RT v = pop_in<RT>(src, bc, tag, N, sn, a * Q + i);
+      const RT v = pop_in<RT>(src, bc, tag, N, sn, a * Q + i, codec);
       rs[a] += v;
 #pragma unroll
       for (int d = 0; d < D; ++d)
         if (cvel(i, d) != 0) js[a][d] += cvel(i, d) * v;
     }
-    const RT f = pop_in<RT>(src, bc, tag, N, sn, (M - 1) * Q + i);
+    const RT f = pop_in<RT>(src, bc, tag, N, sn, (M - 1) * Q + i, codec);
     rho += f;
 #pragma unroll
     for (int d = 0; d < D; ++d) {
@@ -122,7 +155,7 @@ __device__ __forceinline__ void moments_body(const S* __restrict__ src, RT* __re
       for (int e = d; e < D; ++e)
         if (cvel(i, d) * cvel(i, e) != 0) P[pidx<D>(d, e)] += cvel(i, d) * cvel(i, e) * f;
     }
-    const RT gv = pop_in<RT>(src, bc, tag, N, sn, M * Q + i);
+    const RT gv = pop_in<RT>(src, bc, tag, N, sn, M * Q + i, codec);
     rhoE += gv;
 #pragma unroll
     for (int d = 0; d < D; ++d)
@@ -748,7 +781,8 @@ __device__ __forceinline__ void collide_direction(const PS& ps, int i,
                                                   const S* __restrict__ src,
                                                   S* __restrict__ dst, const BCDev& bc,
                                                   int tag, long long N, long long n,
-                                                  long long sn, const DevMech& mech) {
+                                                  long long sn, const DevMech& mech,
+                                                  const float4* codec) {
   constexpr int Q = Lat<D>::Q;
   int c[3];
   c[0] = cvel(i, 0); c[1] = cvel(i, 1); c[2] = D == 3 ? cvel(i, 2) : 0;
@@ -761,17 +795,17 @@ __device__ __forceinline__ void collide_direction(const PS& ps, int i,
     for (int b = 0; b < M; ++b)
       if (b != a) F += kcoef<RT>(mech, a, b) * dd[b];
     const long long off = (long long)(a * Q + i) * N;
-    const RT f = pop_in<RT>(src, bc, tag, N, sn, a * Q + i);
+    const RT f = pop_in<RT>(src, bc, tag, N, sn, a * Q + i, codec);
     const RT fn = f + ps.tb(a) * (ps.rs(a) * pe[a] - f) + ps.cF(a) * F + ps.dr(a) * pe[a];
-    dst[off + n] = S(fn);
+    dst[off + n] = Codec<S>::enc(fn, codec, a * Q + i);
   }
   {
     RT fex = ps.rho();
 #pragma unroll
     for (int d = 0; d < D; ++d) fex *= psi1<RT>(c[d], ps.u(d), ps.Pex(d));
     const long long off = (long long)((M - 1) * Q + i) * N;
-    const RT f = pop_in<RT>(src, bc, tag, N, sn, (M - 1) * Q + i);
-    dst[off + n] = S(f + ps.om() * (fex - f));
+    const RT f = pop_in<RT>(src, bc, tag, N, sn, (M - 1) * Q + i, codec);
+    dst[off + n] = Codec<S>::enc(f + ps.om() * (fex - f), codec, (M - 1) * Q + i);
   }
   {
     RT prodA = RT(1);
@@ -788,14 +822,14 @@ __device__ __forceinline__ void collide_direction(const PS& ps, int i,
     }
     geq *= ps.rho();
     const long long off = (long long)(M * Q + i) * N;
-    const RT gv = pop_in<RT>(src, bc, tag, N, sn, M * Q + i);
+    const RT gv = pop_in<RT>(src, bc, tag, N, sn, M * Q + i, codec);
     RT gn = gv + ps.om() * (geq - gv);
     if (csq(i, D) == 1) {
 #pragma unroll
       for (int d = 0; d < D; ++d)
         if (c[d] != 0) gn += (c[d] > 0 ? RT(0.5) : RT(-0.5)) * ps.W(d);
     }
-    dst[off + n] = S(gn);
+    dst[off + n] = Codec<S>::enc(gn, codec, M * Q + i);
   }
 }
 
@@ -891,7 +925,7 @@ __device__ __forceinline__ void collide_body(const S* __restrict__ src, S* __res
 #pragma unroll 1
   for (int i = 0; i < Q; ++i)
     collide_direction<D, M, S, RT>(ps, i, src, dst, bc, tag, N, n,
-                                   node_shift<D>(x, y, z, i, -1, g), mech);
+                                   node_shift<D>(x, y, z, i, -1, g), mech, g.codec);
 }
 
 // ---------------------------------------------------------------------------
@@ -1034,7 +1068,7 @@ __device__ __forceinline__ void coll_block(const S* __restrict__ src, S* __restr
   const int z = (int)(n / ((long long)g.nx * g.ny));
   for (int i = w; i < Q; i += kCollTPN)
     collide_direction<D, M, S, RT>(ps, i, src, dst, bc, tag, N, n,
-                                   node_shift<D>(x, y, z, i, -1, g), mech);
+                                   node_shift<D>(x, y, z, i, -1, g), mech, g.codec);
 }
 
 
@@ -1141,14 +1175,19 @@ __device__ __forceinline__ void boundary_body(const S* __restrict__ src, const B
   const int y = (int)((n / g.nx) % g.ny);
   const int z = (int)(n / ((long long)g.nx * g.ny));
   const long long st = bc.n_if;
-  auto ld = [&](long long idx) { return R(__ldg(src + idx)); };
+  const float4* codec = g.codec;
+  // population (l, i) of node m, decoded
+  auto ld = [&](int l, int i, long long m) {
+    return Codec<S>::template dec<R>(__ldg(src + (long long)(l * Q + i) * N + m), codec,
+                                     l * Q + i);
+  };
   double* P = bc.pops + k;                       // element (l, i) at P[(l Q + i) st]
   for (int t = lane; t < L * Q; t += 32) {       // pull streaming (wrapped address)
     const int l = t / Q, i = t % Q;
     const long long sn = node_shift<D>(x, y, z, i, -1, g);
     P[(long long)t * st] = (inc >> i & 1u) && kind == BK_BB
-                               ? double(__ldg(src + (long long)(l * Q + (Q - 1 - i)) * N + n))
-                               : double(__ldg(src + (long long)t * N + sn));
+                               ? double(ld(l, Q - 1 - i, n))
+                               : double(ld(l, i, sn));
   }
   if (kind == BK_BB) return;
   __syncwarp();
@@ -1160,8 +1199,7 @@ __device__ __forceinline__ void boundary_body(const S* __restrict__ src, const B
     for (int a = 0; a < M - 1; ++a) rs[a] = R(0);
     for (int t = lane; t < M * Q; t += 32) {
       const int l = t / Q, i = t % Q;
-      const R v = (inc >> i & 1u) ? ld((long long)(l * Q + (Q - 1 - i)) * N + n)
-                                  : R(P[(long long)t * st]);
+      const R v = (inc >> i & 1u) ? ld(l, Q - 1 - i, n) : R(P[(long long)t * st]);
       if (l < M - 1) rs[l] += v; else rho_bb += v;
     }
     rho_bb = warp_sum(rho_bb);
@@ -1186,12 +1224,12 @@ __device__ __forceinline__ void boundary_body(const S* __restrict__ src, const B
     const long long stride = ax == 0 ? 1 : (ax == 1 ? (long long)g.nx : (long long)g.nx * g.ny);
     const long long up = n - sg * stride;
     EqSet<D, M, R> s0, s1;
-    warp_state_of<D, M, R>([&](int l, int i) { return ld((long long)(l * Q + i) * N + n); },
-                           s0, Tf[n], mech, un, status, lane);
+    warp_state_of<D, M, R>([&](int l, int i) { return ld(l, i, n); }, s0, Tf[n], mech, un,
+                           status, lane);
     // (the upstream node's Newton starts from this node's T guess: the bulk
     // moments kernel may be rewriting the upstream one concurrently)
-    warp_state_of<D, M, R>([&](int l, int i) { return ld((long long)(l * Q + i) * N + up); },
-                           s1, Tf[n], mech, un, status, lane);
+    warp_state_of<D, M, R>([&](int l, int i) { return ld(l, i, up); }, s1, Tf[n], mech, un,
+                           status, lane);
     // LODI wave amplitudes (reading R13) in FP64 from the two states: a few
     // scalars per node
     double R0 = 0.0, R1 = 0.0, Cv = 0.0;
@@ -1240,6 +1278,12 @@ __device__ __forceinline__ void boundary_body(const S* __restrict__ src, const B
                          Tf[n], mech, un, status, lane);
   loc.own_species_u = kind == BK_TMS;             // TMS local species use u_a^loc
   eq_prepare(loc, mech, un);
+  if (kind == BK_INLET && bc.inlet_simplified) {  // simplified inlet: the local equilibria
+    __syncwarp();
+    for (int t = lane; t < L * Q; t += 32)
+      P[(long long)t * st] = double(eq_pop(loc, t / Q, t % Q));
+    return;
+  }
   if (kind == BK_INLET) {                         // target (Eqs. in_tgt_*)
     B.rho = loc.rho;
     for (int a = 0; a < M; ++a) B.Y[a] = loc.Y[a];
@@ -1336,7 +1380,7 @@ k_boundary(const S* __restrict__ src, const __grid_constant__ BCDev bc,
            const double* __restrict__ Tf, int* __restrict__ status,
            const __grid_constant__ Geom g, const __grid_constant__ Units un,
            const __grid_constant__ DevMech mech) {
-  boundary_body<D, M, S, S>(src, bc, Tf, status, g, un, mech,
+  boundary_body<D, M, S, typename ComputeType<S>::type>(src, bc, Tf, status, g, un, mech,
                             blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32, threadIdx.x & 31);
 }
 
@@ -1428,7 +1472,8 @@ __global__ void __launch_bounds__(128)
 k_boundary_batch(const DomainDev* __restrict__ doms, int ndom, int parity) {
   const DomainDev& d = doms[domain_of_block(doms, ndom, blockIdx.x, GRID_BOUNDARY)];
   const int c = d.cur0 ^ parity;
-  boundary_body<D, M, S, S>(static_cast<const S*>(d.pops[c]), d.bc, d.Tf, d.status, d.g,
+  boundary_body<D, M, S, typename ComputeType<S>::type>(static_cast<const S*>(d.pops[c]), d.bc,
+                                                      d.Tf, d.status, d.g,
                             d.un, *d.mech, (blockIdx.x - d.bblock_begin) * 4 + threadIdx.x / 32,
                             threadIdx.x & 31);
 }
@@ -1467,11 +1512,11 @@ __global__ void k_init(const double* __restrict__ rho_or_P, int is_pressure,
       const double th = mech.Ra[a] * T * un.inv_c2;
       double p = rho * Y[a];
       for (int d = 0; d < D; ++d) p *= psi1<double>(c[d], u[d], th + u[d] * u[d]);
-      pops[(long long)(a * Q + i) * N + n] = S(p);
+      pops[(long long)(a * Q + i) * N + n] = Codec<S>::enc(p, g.codec, a * Q + i);
     }
     double f = rho;
     for (int d = 0; d < D; ++d) f *= psi1<double>(c[d], u[d], theta + u[d] * u[d]);
-    pops[(long long)((M - 1) * Q + i) * N + n] = S(f);
+    pops[(long long)((M - 1) * Q + i) * N + n] = Codec<S>::enc(f, g.codec, (M - 1) * Q + i);
     double prodA = 1.0, sumB = 0.0;
     double A[3], B[3];
     for (int d = 0; d < D; ++d) {
@@ -1488,13 +1533,82 @@ __global__ void k_init(const double* __restrict__ rho_or_P, int is_pressure,
         if (e != d) t *= A[e];
       sumB += t;
     }
-    pops[(long long)(M * Q + i) * N + n] = S(rho * (U_lat * prodA + sumB));
+    pops[(long long)(M * Q + i) * N + n] =
+        Codec<S>::enc(rho * (U_lat * prodA + sumB), g.codec, M * Q + i);
   }
   (void)usq;
   Tf[n] = T;
 }
 
 // ---------------------------------------------------------------------------
+// Flame diagnostics of the stored state (Sec. 5.3 quantities), one pass:
+// per node the moments, T by Newton from the guess, the mass production
+// rates and q = -sum_a H_a(T) rho_dot_a (W/m^3, H_a with the enthalpy of
+// formation); per block the sum of q, the largest q with its node (the
+// smallest index among equal maxima), the largest T and |u| (m/s).  FP64
+// whatever the storage.
+template <int D, int M, typename S>
+__global__ void __launch_bounds__(128)
+k_diag(const S* __restrict__ pops, const double* __restrict__ Tf, const int* __restrict__ tag,
+       DiagPart* __restrict__ part, int* __restrict__ status, Geom g, Units un,
+       const __grid_constant__ DevMech mech) {
+  constexpr int Q = Lat<D>::Q;
+  __shared__ double s_sum[128], s_qmax[128], s_T[128], s_u[128];
+  __shared__ long long s_n[128];
+  const long long N = g.N;
+  const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  double q = 0.0, qmax = -INFINITY, Tmax = -INFINITY, umax = -INFINITY;
+  long long nmax = LLONG_MAX;
+  if (n < N && !(tag && tag[n] == TAG_SOLID)) {
+    double rho = 0.0, rhoE = 0.0, j[D], rs[M];
+    for (int d = 0; d < D; ++d) j[d] = 0.0;
+    for (int a = 0; a < M; ++a) rs[a] = 0.0;
+    for (int i = 0; i < Q; ++i) {
+      for (int a = 0; a < M - 1; ++a) rs[a] += ldp(pops, N, n, a * Q + i, g.codec);
+      const double f = ldp(pops, N, n, (M - 1) * Q + i, g.codec);
+      rho += f;
+      for (int d = 0; d < D; ++d) j[d] += cvel(i, d) * f;
+      rhoE += ldp(pops, N, n, M * Q + i, g.codec);
+    }
+    rs[M - 1] = rho;
+    for (int a = 0; a < M - 1; ++a) rs[M - 1] -= rs[a];
+    double Y[M], usq = 0.0;
+    for (int a = 0; a < M; ++a) Y[a] = rs[a] / rho;
+    for (int d = 0; d < D; ++d) usq += (j[d] / rho) * (j[d] / rho);
+    bool ok;
+    const double T = newton_T<M>(mech, Y, (rhoE / rho - 0.5 * usq) * un.c * un.c, Tf[n],
+                                 un.newton_max_iter, un.newton_rtol, ok);
+    if (!ok) atomicOr(status, ST_NEWTON);
+    double rdot[M];
+    production_rates<M>(mech, T, rs, rdot);
+    for (int a = 0; a < M; ++a) q -= (species_U(mech, a, T) + mech.Ra[a] * T) * rdot[a];
+    qmax = q;
+    nmax = n;
+    Tmax = T;
+    umax = sqrt(usq) * un.c;
+  }
+  const int t = threadIdx.x;
+  s_sum[t] = q;
+  s_qmax[t] = qmax;
+  s_n[t] = nmax;
+  s_T[t] = Tmax;
+  s_u[t] = umax;
+  __syncthreads();
+  for (int o = 64; o > 0; o >>= 1) {
+    if (t < o) {
+      s_sum[t] += s_sum[t + o];
+      if (s_qmax[t + o] > s_qmax[t] || (s_qmax[t + o] == s_qmax[t] && s_n[t + o] < s_n[t])) {
+        s_qmax[t] = s_qmax[t + o];
+        s_n[t] = s_n[t + o];
+      }
+      s_T[t] = fmax(s_T[t], s_T[t + o]);
+      s_u[t] = fmax(s_u[t], s_u[t + o]);
+    }
+    __syncthreads();
+  }
+  if (t == 0) part[blockIdx.x] = DiagPart{s_sum[0], s_qmax[0], s_n[0], s_T[0], s_u[0]};
+}
+
 // Fields of the stored state: rho, u (m/s), T (Newton, not stored), Y, E (J/kg).
 template <int D, int M, typename S>
 __global__ void k_out(const S* __restrict__ pops, const double* __restrict__ Tf,
@@ -1510,11 +1624,11 @@ __global__ void k_out(const S* __restrict__ pops, const double* __restrict__ Tf,
   for (int d = 0; d < D; ++d) j[d] = 0.0;
   for (int a = 0; a < M; ++a) rs[a] = 0.0;
   for (int i = 0; i < Q; ++i) {
-    for (int a = 0; a < M - 1; ++a) rs[a] += ldp(pops + (long long)(a * Q + i) * N + n);
-    const double f = ldp(pops + (long long)((M - 1) * Q + i) * N + n);
+    for (int a = 0; a < M - 1; ++a) rs[a] += ldp(pops, N, n, a * Q + i, g.codec);
+    const double f = ldp(pops, N, n, (M - 1) * Q + i, g.codec);
     rho += f;
     for (int d = 0; d < D; ++d) j[d] += cvel(i, d) * f;
-    rhoE += ldp(pops + (long long)(M * Q + i) * N + n);
+    rhoE += ldp(pops, N, n, M * Q + i, g.codec);
   }
   rs[M - 1] = rho;
   for (int a = 0; a < M - 1; ++a) rs[M - 1] -= rs[a];
@@ -1667,6 +1781,15 @@ static cudaError_t init_impl(const DevMech& mech, const Geom& g, const Units& un
 }
 
 template <int D, int M, typename S>
+static cudaError_t diag_impl(const DevMech& mech, const Geom& g, const Units& un,
+                             const void* pops, const double* Tfield, const int* tag,
+                             DiagPart* part, int* status, cudaStream_t s) {
+  k_diag<D, M, S><<<blocks_for(g.N, 128), 128, 0, s>>>(static_cast<const S*>(pops), Tfield, tag,
+                                                        part, status, g, un, mech);
+  return cudaGetLastError();
+}
+
+template <int D, int M, typename S>
 static cudaError_t out_impl(const DevMech& mech, const Geom& g, const Units& un,
                             const void* pops, const double* Tfield, double* rho, double* u,
                             double* T, double* Y, double* E, int* status, cudaStream_t s) {
@@ -1724,7 +1847,8 @@ template <int D, int M, typename S, typename RT>
 const KernelSet* make_kernel_set() {
   static const KernelSet ks = {&step_impl<D, M, S, RT>, &batch_impl<D, M, S, RT>,
                                &prepare_once<D, M, S, RT>, &init_impl<D, M, S>,
-                               &out_impl<D, M, S>, Rec<D, M>::NF, CPar<D, M>::NF};
+                               &out_impl<D, M, S>, &diag_impl<D, M, S>, Rec<D, M>::NF,
+                               CPar<D, M>::NF};
   return &ks;
 }
 

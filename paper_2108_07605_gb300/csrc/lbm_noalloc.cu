@@ -74,6 +74,9 @@ extern "C" lbm_status lbm_step_noalloc(const lbm_config* cfg, const void* pops_i
   else if (cfg->solid_mask || cfg->face_bc[0] || cfg->face_bc[1] || cfg->face_bc[2] ||
            cfg->face_bc[3] || cfg->face_bc[4] || cfg->face_bc[5])
     st = noalloc_fail(LBM_ERR_INVALID, "lbm_step_noalloc supports periodic boxes only");
+  else if (cfg->precision == LBM_FP16_OFFSET)
+    st = noalloc_fail(LBM_ERR_INVALID,
+                      "FP16 offset storage needs the codec a handle keeps (use lbm_create)");
   else if (!pops_in || !pops_out || !T_guess || pops_in == pops_out)
     st = noalloc_fail(LBM_ERR_INVALID, "need distinct device buffers pops_in, pops_out and T_guess");
   else if (cfg->device >= kMaxDevices)

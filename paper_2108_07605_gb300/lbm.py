@@ -68,12 +68,17 @@ class lbm_config(C.Structure):
         ("inlet_P", C.c_double), ("outlet_P", C.c_double), ("outlet_sigma", C.c_double),
         ("newton_max_iter", C.c_int), ("newton_rtol", C.c_double),
         ("dev_alloc", ALLOC_FN), ("dev_free", FREE_FN), ("alloc_user", C.c_void_p),
-        ("stream", C.c_void_p), ("device", C.c_int),
+        ("stream", C.c_void_p), ("device", C.c_int), ("inlet_simplified", C.c_int),
     ]
 
 
 class lbm_launch(C.Structure):
     _fields_ = [("chem_lanes", C.c_int), ("collide_split", C.c_int)]
+
+
+class lbm_diag(C.Structure):
+    _fields_ = [("hrr_integral", C.c_double), ("hrr_max", C.c_double),
+                ("flame_x", C.c_double), ("T_max", C.c_double), ("u_max", C.c_double)]
 
 
 class lbm_info(C.Structure):
@@ -102,6 +107,7 @@ EXPORTS = {
     "lbm_autotune": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(lbm_launch)]),
     "lbm_moments": (C.c_int, [C.c_void_p] + [C.c_void_p] * 5 + [C.c_int]),
     "lbm_get_populations": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int]),
+    "lbm_diagnostics": (C.c_int, [C.c_void_p, C.POINTER(lbm_diag)]),
     "lbm_synchronize": (C.c_int, [C.c_void_p]),
     "lbm_get_state": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_size_t)]),
     "lbm_set_state": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t]),
@@ -314,6 +320,12 @@ def lbm_moments(h, rho=None, u=None, T=None, Y=None, E=None):
                                       _ptr(Y)[0], _ptr(E)[0], on), h)
 
 
+def lbm_diagnostics(h):
+    out = lbm_diag()
+    _check(load_library().lbm_diagnostics(h, C.byref(out)), h)
+    return {k: getattr(out, k) for k, _ in lbm_diag._fields_}
+
+
 def lbm_get_populations(h, out):
     p, on = _ptr(out)
     _check(load_library().lbm_get_populations(h, p, on), h)
@@ -434,6 +446,7 @@ def make_config(mech, lattice="D3Q27", shape=(16, 16, 16), dx=1e-3, precision="f
             cfg.inlet_u = uu.ctypes.data_as(C.POINTER(C.c_double))
         cfg.inlet_T = float(inlet["T"])
         cfg.inlet_P = float(inlet.get("P", 101325.0))
+        cfg.inlet_simplified = 1 if inlet.get("simplified", False) else 0
         for a, y in enumerate(np.asarray(inlet["Y"], dtype=np.float64)):
             cfg.inlet_Y[a] = float(y)
     if outlet is not None:
@@ -492,6 +505,9 @@ class Solver:
         out["u"] = out["u"].reshape(3, N)
         out["Y"] = out["Y"].reshape(M, N)
         return out
+
+    def diagnostics(self):
+        return lbm_diagnostics(self.h)
 
     def populations(self):
         info = self.info

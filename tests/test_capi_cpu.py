@@ -52,12 +52,13 @@ def test_struct_layout_matches_c(lbm, tmp_path):
 #include <stddef.h>
 #include "{HEADER}"
 int main(void) {{
-  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(lbm_mechanism),
+  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(lbm_mechanism),
          sizeof(lbm_config), sizeof(lbm_info), offsetof(lbm_config, mech),
          offsetof(lbm_config, face_bc), offsetof(lbm_config, inlet_u),
          offsetof(lbm_config, dev_alloc), offsetof(lbm_config, stream),
          offsetof(lbm_mechanism, D0), offsetof(lbm_config, solid_mask),
-         offsetof(lbm_config, wall_T_nodes));
+         offsetof(lbm_config, wall_T_nodes), offsetof(lbm_config, inlet_simplified),
+         sizeof(lbm_launch), sizeof(lbm_diag));
   return 0;
 }}
 """)
@@ -69,7 +70,9 @@ int main(void) {{
            lbm.lbm_config.mech.offset, lbm.lbm_config.face_bc.offset,
            lbm.lbm_config.inlet_u.offset, lbm.lbm_config.dev_alloc.offset,
            lbm.lbm_config.stream.offset, lbm.lbm_mechanism.D0.offset,
-           lbm.lbm_config.solid_mask.offset, lbm.lbm_config.wall_T_nodes.offset]
+           lbm.lbm_config.solid_mask.offset, lbm.lbm_config.wall_T_nodes.offset,
+           lbm.lbm_config.inlet_simplified.offset, C.sizeof(lbm.lbm_launch),
+           C.sizeof(lbm.lbm_diag)]
     assert got == vals
 
 

@@ -65,3 +65,12 @@ def test_full_flame_first_steps(mech):
     w = fields.flame_1d()
     err = _compare(mech, w, 3)
     assert np.all(err < RTOL_FP64), err
+
+
+def test_flame_layout_simplified_inlet(mech):
+    """The simplified flux inlet (Sec. 4.3, last paragraph) on the flame
+    layout: populations against the oracle with the same option."""
+    w = fields.flame_1d(nx=40, ny=3, nz=2, x_ign=10)
+    w["inlet"] = dict(w["inlet"], simplified=True)
+    err = _compare(mech, w, 12)
+    assert np.all(err < RTOL_FP64), err

@@ -184,3 +184,30 @@ def test_newton_failure_is_reported(mech):
     assert e.value.status == 4
     with pytest.raises(lbm.LBMError):
         s.close()
+
+
+@pytest.mark.parametrize("case", ["flame", "tube"])
+def test_diagnostics_match_the_oracle(mech, case):
+    """lbm_diagnostics (one device pass with fixed-order reductions) against
+    oracle.diagnostics on the oracle's own state after the same steps."""
+    from oracle import diagnostics
+    if case == "flame":
+        w = fields.flame_1d(nx=48, ny=4, nz=4, x_ign=12, mech=mech)
+        nsteps = 15
+    else:
+        w = fields.microtube(nx=14, ny=10, nz=10, radius=4.5, mech=mech)
+        nsteps = 8
+    o = make_oracle(mech, w)
+    g = make_gpu(mech, w)
+    o.step(nsteps)
+    g.step(nsteps)
+    mo = o.moments()
+    fluid = None if w.get("solid") is None else ~np.asarray(w["solid"]).reshape(-1)
+    ref = diagnostics.diagnostics(mech, mo["rho"], mo["u"], mo["T"], mo["Y"], w["dx"], 3,
+                                  w["shape"][0], fluid)
+    got = g.diagnostics()
+    g.close()
+    assert abs(ref["hrr_integral"]) > 0.0
+    for k in ("hrr_integral", "hrr_max", "T_max", "u_max"):
+        assert got[k] == pytest.approx(ref[k], rel=1e-9, abs=1e-12), k
+    assert got["flame_x"] == pytest.approx(ref["flame_x"], abs=1e-12)

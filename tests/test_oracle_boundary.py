@@ -5,7 +5,8 @@ states they achieve, checked on the moments of the reconstructed nodes:
   Y^bb, u^tgt and T^tgt.
 * Inlet (Sec. 4.3, remark after Eq. fa_inlet): the node takes u^in and T^in
   with the local rho^loc and Y^loc; a uniform state equal to the inlet state
-  is left unchanged.
+  is left unchanged.  Simplified inlet (same section): the populations are
+  the equilibria of the node's own local state.
 * Outlet (Sec. 4.4, remark after Eq. fa_outlet): the node takes the outlet
   data; a uniform state at rest at the outlet pressure is a fixed point.
 * Bounce-back (Eq. bb) and TMS both conserve mass in a closed box (Sec. 4.2:
@@ -77,6 +78,27 @@ def test_inlet_sets_velocity_and_temperature(mech):
     assert nodes.sum() == 9
     assert np.allclose(u[:, nodes] * o.units.c, inlet["u"][:, None], rtol=1e-12, atol=1e-12)
     assert np.allclose(T[nodes], 320.0, rtol=1e-12)
+
+
+def test_simplified_inlet_gives_the_local_equilibrium(mech):
+    """Simplified inlet (Sec. 4.3, last paragraph): every population of an
+    inlet node is the equilibrium of the node's own local state, so the
+    reconstructed populations equal the equilibria of their own moments; the
+    velocity keeps its local value instead of the target."""
+    Y_in = fields.mole_to_mass_fractions(mech, fields.air_mole_fractions(mech, 0.5))
+    inlet = dict(u=np.array([2.0, 0.3, 0.0]), T=320.0, Y=Y_in, P=P_STANDARD, simplified=True)
+    faces = ("inlet", "periodic", "periodic", "periodic", "periodic", "periodic")
+    o, _ = _box(mech, (6, 3, 3), faces, inlet=inlet)
+    o.step(1)
+    rec, mom, T, u, Y = _post_bc_fields(o)
+    nodes = (o.bc.node_kind == 3).ravel()
+    assert nodes.sum() == 9
+    rho = mom["rho"].reshape(-1)[nodes]
+    uu = u.reshape(3, -1)[:, nodes]
+    eq = o.bc._equilibria(rho, Y.reshape(o.M, -1)[:, nodes], uu, T.reshape(-1)[nodes])
+    got = rec.reshape(rec.shape[0], rec.shape[1], -1)[:, :, nodes]
+    assert np.allclose(got, eq, rtol=1e-12, atol=1e-15 * np.abs(eq).max())
+    assert np.max(np.abs(uu[0] * o.units.c - 2.0)) > 1e-3     # not the target velocity
 
 
 def test_inlet_state_is_a_fixed_point(mech):
