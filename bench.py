@@ -92,6 +92,23 @@ def boundary_spec(w):
     return {k: w[k] for k in keys if k in w}
 
 
+def max_over_ranks(x, pg):
+    """The largest x over all ranks (x itself without a process group)."""
+    if pg is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t[0])
+
+
+def node_updates_per_s(nodes_per_rank, steps, world, species, seconds):
+    """Whole-job throughput: every rank advances its own copy of the
+    workload (weak scaling); a node update is one lattice of one node, M + 2
+    per node-step."""
+    return nodes_per_rank * steps * world * (species + 2) / seconds
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -307,10 +324,8 @@ def main():
             flush_buf.zero_()
         kms = lbm.lbm_step_timed(solver.h, 1, kms)
     torch.cuda.synchronize()
+    total_ms = max_over_ranks(total_ms, pg)
     if pg:
-        t = torch.tensor([total_ms], dtype=torch.float64)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        total_ms = float(t[0])
         pg.barrier()
     ms_per_step = total_ms / args.steps
     node_steps = N * args.steps * world
@@ -319,7 +334,7 @@ def main():
     # kernel, or two when split)
     launches_per_step = 2 + (1 if boundary_spec(w) else 0) + \
         (1 if launch["chem_lanes"] > 1 else 0) + (1 if launch["collide_split"] else 0)
-    value = node_steps * (M + 2) / (total_ms * 1e-3)
+    value = node_updates_per_s(N, args.steps, world, M, total_ms * 1e-3)
 
     # roofline of the dominant kernel
     names = ["k_moments+k_chem" if launch["chem_lanes"] > 1 else "k_moments",
@@ -360,14 +375,11 @@ def main():
                                      pinned["Y"])
         lbm.lbm_step(solver.h, args.steps)
         lbm.lbm_moments(solver.h, outs["rho"], outs["u"], outs["T"], outs["Y"], outs["E"])
-        e2e_s = time.perf_counter() - t0
-        if pg:
-            t = torch.tensor([e2e_s], dtype=torch.float64)
-            pg.all_reduce(t, op=pg.ReduceOp.MAX)
-            e2e_s = float(t[0])
+        e2e_s = max_over_ranks(time.perf_counter() - t0, pg)
         h2d = sum(v.numel() * 8 for v in pinned.values())
         d2h = sum(v.numel() * 8 for v in outs.values())
-        e2e = {"value": node_steps * (M + 2) / e2e_s, "unit": "node-updates/s",
+        e2e = {"value": node_updates_per_s(N, args.steps, world, M, e2e_s),
+               "unit": "node-updates/s",
                "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
                "timed": "init from host fields + K steps + all fields read back to host"}
 
