@@ -112,6 +112,14 @@ typedef struct lbm_mechanism {
   double mu0;                                      /* Pa s at T0            */
   double mu_T_exponent;
   double prandtl;
+  /* viscosity_model 0: mu = mu0 (T/T0)^mu_T_exponent; 1: Wilke's mixing rule
+   * over the species viscosities mu0_species[a] (T/T0)^mu_T_exponent (Pa s at
+   * T0): mu = sum_a X_a mu_a / sum_b X_b Phi_ab, Phi_ab = [1 + (mu_a/mu_b)^1/2
+   * (m_b/m_a)^1/4]^2 / [8 (1 + m_a/m_b)]^1/2, X the mole fractions.  In
+   * both, lambda = mu C_p / Pr (the paper's transport comes from Cantera,
+   * which this library does not carry). */
+  int viscosity_model;
+  double mu0_species[LBM_MAX_SPECIES];
 } lbm_mechanism;
 
 typedef struct lbm_config {
@@ -237,6 +245,10 @@ lbm_status lbm_batch_destroy(lbm_batch_t b);
 typedef struct {
   int chem_lanes;
   int collide_split;
+  int persistent;     /* batch plans only: 1 = every batched kernel runs a grid
+                         of the blocks the GPU holds at once, each block
+                         looping over tiles of the work-list; 0 / -1 (the
+                         default) = one block per tile */
 } lbm_launch;
 
 /* Set / read the handle's placement (lbm_get_launch reports the resolved
@@ -256,6 +268,13 @@ lbm_status lbm_autotune(lbm_t h, int trial_steps, lbm_launch* chosen);
  * the fastest and captures the plan's graphs again with it.  A new plan
  * starts with the placement chosen by the batch's total node count. */
 lbm_status lbm_batch_autotune(lbm_batch_t b, int trial_steps, lbm_launch* chosen);
+
+/* Set a plan's placement (-1 fields: the default for the batch's total node
+ * count) and capture its graphs again; read the placement in use.  The
+ * handles' own lbm_set_launch values do not apply to plans.  LBM_ERR_INVALID
+ * for values out of range. */
+lbm_status lbm_batch_set_launch(lbm_batch_t b, const lbm_launch* l);
+lbm_status lbm_batch_get_launch(lbm_batch_t b, lbm_launch* l);
 
 /* As lbm_step, and adds each kernel's device time in milliseconds, measured
  * with CUDA events recorded on the handle's stream around every launch:

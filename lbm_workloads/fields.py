@@ -205,9 +205,10 @@ def serving_mix(seed=0, n_requests=64, mean_interarrival=0.05, steps=(1000, 1000
         nsteps = int(rng.integers(steps[0], steps[1] + 1))
         if kind == "reactor":
             nn = int(rng.integers(16, 33))
-            # dx = 50 um keeps the explicit reaction sub-steps stable through
-            # ignition (at 1 mm the time step is 20x longer)
-            w = reactor(seed=seed * 1000 + k, n=nn, phi=phi, dx=5.0e-5, mech=mech)
+            # dx = 12.5 um (the flame's spacing) keeps the explicit reaction
+            # sub-steps stable through ignition over the full 1k-10k steps:
+            # at 1 mm they diverge at ignition, at 50 um within 10k steps
+            w = reactor(seed=seed * 1000 + k, n=nn, phi=phi, dx=12.5e-6, mech=mech)
         elif kind == "flame":
             nx = int(rng.choice([256, 512, 1024]))
             ny = int(rng.choice([4, 8, 16, 32]))
@@ -220,7 +221,12 @@ def serving_mix(seed=0, n_requests=64, mean_interarrival=0.05, steps=(1000, 1000
         else:
             nx = int(rng.choice([250, 500, 1000, 2000]))
             ny = int(rng.choice([20, 40]))
-            w = channel_2d(seed=seed * 1000 + k, nx=nx, ny=ny, phi=phi, mech=mech)
+            # 12.5 um as for the reactors (the channel's own 25 um loses the
+            # explicit sub-steps near the hot walls within 10k steps)
+            w = channel_2d(seed=seed * 1000 + k, nx=nx, ny=ny, phi=phi, dx=12.5e-6, mech=mech)
+            # the mixture preheated by the 1500 K walls burns to about 3600 K;
+            # the lattice speed must admit that temperature (theta < 1 for H2)
+            w["T_max"] = 4000.0
             s = (np.arange(ny) + 0.5) / ny
             prof = u_in * 4.0 * s * (1.0 - s)
             w["u"][0] = np.broadcast_to(prof[None, :, None], w["u"][0].shape)

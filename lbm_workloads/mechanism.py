@@ -67,6 +67,10 @@ class Mechanism:
     mu0: float = 1.8e-5            # Pa s at T0
     mu_T_exponent: float = 0.7
     prandtl: float = 0.7
+    # per-species viscosities at T0 (Pa s) for the Wilke mixing rule; the
+    # model in use: "mixture" (mu0 power law) or "wilke"
+    mu0_species: np.ndarray = None
+    viscosity_model: str = "mixture"
     label: str = ""
     equations: List[str] = field(default_factory=list)
 
@@ -170,6 +174,24 @@ def _binary_diffusion_table(species, molar_mass, sigma, d_ref=2.0e-5,
     return D
 
 
+def _species_viscosities(species, molar_mass, sigma, mu_ref=1.78e-5, ref="N2"):
+    """Synthetic species viscosities at T0 by kinetic-theory scaling
+    mu ~ sqrt(m) / sigma^2, normalised so mu(ref) = mu_ref."""
+    mr = molar_mass[species.index(ref)]
+    sr = sigma[species.index(ref)]
+    return mu_ref * np.sqrt(molar_mass / mr) * (sr / sigma) ** 2
+
+
+def with_viscosity_model(mech: Mechanism, model: str) -> Mechanism:
+    """A copy of mech with the viscosity model set ("mixture" or "wilke")."""
+    import dataclasses
+    if model not in ("mixture", "wilke"):
+        raise ValueError(model)
+    if model == "wilke" and mech.mu0_species is None:
+        raise ValueError("the mechanism has no species viscosities")
+    return dataclasses.replace(mech, viscosity_model=model)
+
+
 def h2_air_synthetic() -> Mechanism:
     """Synthetic 9-species / 21-reaction H2/air-shaped mechanism (see module
     docstring).  N2 is last, so it is the slaved species."""
@@ -204,6 +226,7 @@ def h2_air_synthetic() -> Mechanism:
                      h_formation=hf, s_standard=s0, nu_f=nu_f, nu_r=nu_r,
                      arrhenius=arr, third_body=tb, efficiency=eff,
                      reversible=np.ones(R, dtype=np.int32), D0=D0,
+                     mu0_species=_species_viscosities(sp, mm, sigma),
                      label="synthetic H2/air-shaped, 9 species, 21 reactions",
                      equations=eqs)
 
@@ -223,7 +246,8 @@ def binary_inert(molar_mass=28.0e-3, D0=2.0e-5, cp_over_R=3.5,
         nu_f=np.zeros((0, 2)), nu_r=np.zeros((0, 2)), arrhenius=np.zeros((0, 3)),
         third_body=np.zeros(0, dtype=np.int32), efficiency=np.ones((0, 2)),
         reversible=np.zeros(0, dtype=np.int32),
-        D0=np.full((2, 2), D0), mu0=mu0, label="binary inert, equal masses")
+        D0=np.full((2, 2), D0), mu0=mu0, mu0_species=np.array([mu0, mu0]),
+        label="binary inert, equal masses")
 
 
 def air_mole_fractions(mech: Mechanism, phi: float) -> np.ndarray:

@@ -4,7 +4,8 @@ Test infrastructure: plain FP64 numpy.
 
 The paper takes mu, lambda and D_ab from Cantera (Sec. 3.5 end, Sec. 3.6).
 Cantera is not available, so the mechanism table carries a power-law model:
-D_ab = D0_ab (T/T0)^{D_T_exponent} (P0/P), mu = mu0 (T/T0)^{mu_T_exponent},
+D_ab = D0_ab (T/T0)^{D_T_exponent} (P0/P), mu = mu0 (T/T0)^{mu_T_exponent}
+(or, as an option, Wilke's mixing rule over species viscosities),
 lambda = mu C_p / Pr.
 
 Relaxation parameters in lattice units (dx = dt = 1, velocities scaled by
@@ -32,8 +33,32 @@ def diffusion_coefficients(mech, T, P):
     return mech.D0.reshape(mech.D0.shape + (1,) * T.ndim) * s
 
 
-def viscosity(mech, T):
-    return mech.mu0 * (np.asarray(T, dtype=float) / T_STANDARD) ** mech.mu_T_exponent
+def viscosity(mech, T, Y=None):
+    """Mixture viscosity (Pa s).  "mixture" model: mu0 (T/T0)^e.  "wilke"
+    model (Wilke's mixing rule, J. Chem. Phys. 18, 1950) over the species
+    viscosities mu_a = mu0_a (T/T0)^e:
+      mu = sum_a X_a mu_a / sum_b X_b Phi_ab,
+      Phi_ab = [1 + (mu_a/mu_b)^(1/2) (m_b/m_a)^(1/4)]^2 / [8 (1 + m_a/m_b)]^(1/2),
+    with X the mole fractions of Y [M, ...]."""
+    T = np.asarray(T, dtype=float)
+    scale = (T / T_STANDARD) ** mech.mu_T_exponent
+    if mech.viscosity_model != "wilke":
+        return mech.mu0 * scale
+    M = mech.n_species
+    m = mech.molar_mass
+    Y = np.asarray(Y, dtype=float)
+    n = Y / m.reshape((-1,) + (1,) * (Y.ndim - 1))
+    X = n / np.sum(n, axis=0)
+    mu_a = [mech.mu0_species[a] * scale for a in range(M)]
+    total = np.zeros(T.shape)
+    for a in range(M):
+        den = np.zeros(T.shape)
+        for b in range(M):
+            phi = (1.0 + np.sqrt(mu_a[a] / mu_a[b]) * (m[b] / m[a]) ** 0.25) ** 2 \
+                / np.sqrt(8.0 * (1.0 + m[a] / m[b]))
+            den = den + X[b] * phi
+        total = total + X[a] * mu_a[a] / den
+    return total
 
 
 def relaxation(mech, units, rho, Y, T):
@@ -66,7 +91,7 @@ def relaxation(mech, units, rho, Y, T):
                 inv_tau_a[a] = inv_tau_a[a] + Y[b] * inv_tau_ab[a, b]
     beta = inv_tau_a / (2.0 + inv_tau_a)                     # = 1/(2 tau_a + 1)
     theta = R * T / c2
-    nu_lat = viscosity(mech, T) / rho * units.dt / units.dx ** 2
+    nu_lat = viscosity(mech, T, Y) / rho * units.dt / units.dx ** 2
     omega = 1.0 / (nu_lat / theta + 0.5)
     omega1 = 1.0 / (nu_lat / (mech.prandtl * theta) + 0.5)
     return dict(inv_tau_ab=inv_tau_ab, inv_tau_a=inv_tau_a, beta=beta,

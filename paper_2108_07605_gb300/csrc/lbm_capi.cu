@@ -32,7 +32,7 @@ struct lbm_ctx {
   size_t bytes = 0;
   long long steps = 0;
   bool initialized = false;
-  lbm_launch opt = {-1, -1};  // placement as set (-1: by grid size)
+  lbm_launch opt = {-1, -1, -1};  // placement as set (-1: default)
   cudaStream_t side = nullptr;  // boundary kernel, concurrent with the bulk moments
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   void* cpar = nullptr;     // per-node collision parameters (split collision)
@@ -67,6 +67,7 @@ Launch resolve_launch(const lbm_launch& opt, long long nodes, lbm_precision prec
   lc.chem_lanes = opt.chem_lanes > 0 ? opt.chem_lanes
                                      : (small && prec == LBM_FP32_STORE ? 4 : 1);
   lc.coll_split = opt.collide_split >= 0 ? opt.collide_split : 1;
+  lc.persistent = opt.persistent > 0 ? 1 : 0;
   return lc;
 }
 
@@ -174,6 +175,10 @@ std::string validate(const lbm_config* c) {
     if (!(m.arrhenius[r][0] > 0.0)) return "Arrhenius A must be positive";
   }
   if (!(m.mu0 > 0.0) || !(m.prandtl > 0.0)) return "mu0 and prandtl must be positive";
+  if (m.viscosity_model != 0 && m.viscosity_model != 1) return "viscosity_model must be 0 or 1";
+  if (m.viscosity_model == 1)
+    for (int a = 0; a < m.n_species; ++a)
+      if (!(m.mu0_species[a] > 0.0)) return "Wilke viscosity needs positive mu0_species";
   bool any_tms = c->solid_mask && c->solid_bc == LBM_TMS_WALL, any_in = false, any_out = false;
   for (int f = 0; f < 6; ++f) {
     const lbm_bc k = c->face_bc[f];
@@ -281,6 +286,20 @@ void build_mech(const lbm_mechanism& m, DevMech& d) {
   d.mu0_s = (float)d.mu0;
   d.mu_T_exp_s = (float)d.mu_T_exp;
   d.inv_prandtl_s = (float)d.inv_prandtl;
+  d.wilke = m.viscosity_model == 1 ? 1 : 0;
+  for (int a = 0; a < m.n_species; ++a) {
+    d.mu0_sp[a] = d.wilke ? m.mu0_species[a] : m.mu0;
+    d.mu0_sp_s[a] = (float)d.mu0_sp[a];
+  }
+  for (int a = 0; a < m.n_species; ++a)
+    for (int b = 0; b < m.n_species; ++b) {
+      // Wilke's Phi_ab: the species viscosities share the T exponent, so the
+      // ratio mu_a/mu_b, and Phi, are the same at every T
+      const double ma = m.molar_mass[a], mb = m.molar_mass[b];
+      const double r = std::sqrt(d.mu0_sp[a] / d.mu0_sp[b]) * std::pow(mb / ma, 0.25);
+      d.wilke_phi[a][b] = (1.0 + r) * (1.0 + r) / std::sqrt(8.0 * (1.0 + ma / mb));
+      d.wilke_phi_s[a][b] = (float)d.wilke_phi[a][b];
+    }
 }
 
 // bytes of a stored population, and of the scratch records' lattice type
@@ -844,6 +863,8 @@ lbm_status lbm_set_launch(lbm_t h, const lbm_launch* l) {
     return fail(h, LBM_ERR_INVALID, "chem_lanes must be -1, 1, 4 or 8");
   if (l->collide_split < -1 || l->collide_split > 1)
     return fail(h, LBM_ERR_INVALID, "collide_split must be -1, 0 or 1");
+  if (l->persistent < -1 || l->persistent > 1)
+    return fail(h, LBM_ERR_INVALID, "persistent must be -1, 0 or 1");
   h->opt = *l;
   return LBM_OK;
 }
@@ -853,6 +874,7 @@ lbm_status lbm_get_launch(lbm_t h, lbm_launch* l) {
   const Launch lc = resolve_launch(h->opt, h->g.N, h->cfg.precision);
   l->chem_lanes = lc.chem_lanes;
   l->collide_split = lc.coll_split;
+  l->persistent = lc.persistent;
   return LBM_OK;
 }
 
@@ -915,7 +937,10 @@ lbm_status lbm_autotune(lbm_t h, int trial_steps, lbm_launch* chosen) {
   if (e != cudaSuccess) return cuda_fail(h, e, "autotune");
   h->opt.chem_lanes = best.chem_lanes;
   h->opt.collide_split = best.coll_split;
-  if (chosen) *chosen = h->opt;
+  if (chosen) {
+    *chosen = h->opt;
+    chosen->persistent = resolve_launch(h->opt, h->g.N, h->cfg.precision).persistent;
+  }
   return LBM_OK;
 }
 
@@ -939,7 +964,7 @@ lbm_status lbm_batch_step(lbm_t* hs, int n, int nsteps) {
   DeviceGuard dg(h0->cfg.device);
   std::vector<DomainDev> doms;
   BatchGrids gr;
-  const Launch lc = resolve_launch(lbm_launch{-1, -1}, total_nodes(hs, n), hs[0]->cfg.precision);
+  const Launch lc = resolve_launch(lbm_launch{-1, -1, -1}, total_nodes(hs, n), hs[0]->cfg.precision);
   fill_domains(hs, n, lc, doms, gr);
   // every handle's earlier work precedes the batch; the batch runs on the
   // first handle's stream and each handle's stream waits for it afterwards
@@ -1068,7 +1093,7 @@ lbm_status lbm_batch_create(lbm_t* hs, int n, lbm_batch_t* out) {
     b->ddev = static_cast<DomainDev*>(dalloc(h0->cfg, n * sizeof(DomainDev)));
     if (!b->ddev) e = cudaErrorMemoryAllocation;
   }
-  b->lc = resolve_launch(lbm_launch{-1, -1}, total_nodes(hs, n), hs[0]->cfg.precision);
+  b->lc = resolve_launch(lbm_launch{-1, -1, -1}, total_nodes(hs, n), hs[0]->cfg.precision);
   if (e == cudaSuccess) e = batch_upload(b);
   if (e == cudaSuccess) e = prepare_batch_step(h0->D, h0->M, h0->cfg.precision);
   if (e == cudaSuccess) e = batch_capture_all(b);
@@ -1119,6 +1144,28 @@ lbm_status lbm_batch_run(lbm_batch_t b, int nsteps) {
   return LBM_OK;
 }
 
+lbm_status lbm_batch_set_launch(lbm_batch_t b, const lbm_launch* l) {
+  if (!b || !l) return fail(nullptr, LBM_ERR_INVALID, "plan or launch is NULL");
+  lbm_ctx* h0 = b->hs[0];
+  if ((l->chem_lanes != -1 && l->chem_lanes != 1 && l->chem_lanes != 4 && l->chem_lanes != 8) ||
+      l->collide_split < -1 || l->collide_split > 1 || l->persistent < -1 || l->persistent > 1)
+    return fail(h0, LBM_ERR_INVALID, "placement out of range");
+  DeviceGuard dg(h0->cfg.device);
+  cudaError_t e = cudaStreamSynchronize(b->stream);
+  b->lc = resolve_launch(*l, total_nodes(b->hs.data(), (int)b->hs.size()), h0->cfg.precision);
+  if (e == cudaSuccess) e = batch_upload(b);
+  if (e == cudaSuccess) e = batch_capture_all(b);
+  return e == cudaSuccess ? LBM_OK : cuda_fail(h0, e, "batch placement");
+}
+
+lbm_status lbm_batch_get_launch(lbm_batch_t b, lbm_launch* l) {
+  if (!b || !l) return fail(nullptr, LBM_ERR_INVALID, "plan or launch is NULL");
+  l->chem_lanes = b->lc.chem_lanes;
+  l->collide_split = b->lc.coll_split;
+  l->persistent = b->lc.persistent;
+  return LBM_OK;
+}
+
 lbm_status lbm_batch_autotune(lbm_batch_t b, int trial_steps, lbm_launch* chosen) {
   if (!b) return fail(nullptr, LBM_ERR_INVALID, "plan is NULL");
   lbm_ctx* h0 = b->hs[0];
@@ -1142,8 +1189,18 @@ lbm_status lbm_batch_autotune(lbm_batch_t b, int trial_steps, lbm_launch* chosen
   float best_ms = 0.f;
   Launch best = b->lc;
   bool first = true;
-  for (const Launch& cand : kCandidates) {
+  // stage 1: the six placements with one block per tile; stage 2: the best
+  // of them with persistent grids
+  const size_t nc = sizeof(kCandidates) / sizeof(kCandidates[0]);
+  for (size_t ci = 0; ci <= nc; ++ci) {
     if (e != cudaSuccess) break;
+    Launch cand;
+    if (ci < nc) {
+      cand = kCandidates[ci];
+    } else {
+      cand = best;
+      cand.persistent = 1;
+    }
     b->lc = cand;
     e = batch_upload(b);
     // parity 0 every time: each trial step recomputes the next state of every
@@ -1181,6 +1238,7 @@ lbm_status lbm_batch_autotune(lbm_batch_t b, int trial_steps, lbm_launch* chosen
   if (chosen) {
     chosen->chem_lanes = best.chem_lanes;
     chosen->collide_split = best.coll_split;
+    chosen->persistent = best.persistent;
   }
   return LBM_OK;
 }

@@ -50,6 +50,13 @@ struct DevMech {
   double K[LBM_MAX_SPECIES][LBM_MAX_SPECIES];
   float Kf[LBM_MAX_SPECIES][LBM_MAX_SPECIES];   // K rounded to FP32 (mixed path)
   double D_T_exp, mu0, mu_T_exp, inv_prandtl;
+  // Wilke's mixing rule (wilke = 1): species viscosities at T0 and the
+  // T-independent Phi_ab (the species share the T exponent)
+  int wilke;
+  double mu0_sp[LBM_MAX_SPECIES];
+  double wilke_phi[LBM_MAX_SPECIES][LBM_MAX_SPECIES];
+  float mu0_sp_s[LBM_MAX_SPECIES];
+  float wilke_phi_s[LBM_MAX_SPECIES][LBM_MAX_SPECIES];
   // float-float copies for the mixed path's temperature solve and chemistry
   ff mm_f[LBM_MAX_SPECIES], inv_mm_f[LBM_MAX_SPECIES];
   ff u0_f[LBM_MAX_SPECIES], u1_f[LBM_MAX_SPECIES], u2_f[LBM_MAX_SPECIES], u3_f[LBM_MAX_SPECIES];
@@ -112,6 +119,7 @@ struct BCDev {
 struct Launch {
   int chem_lanes = 1;    // 1: chemistry inside the moments kernel; 4 or 8: k_chem lanes per node
   int coll_split = 0;    // 0: fused collision; 1: k_prep + k_coll
+  int persistent = 0;    // batched kernels: 1 = grids of the resident blocks, looping over tiles
 };
 
 struct StepArgs {

@@ -475,6 +475,10 @@ template <> struct MixParams<double> {
   __device__ static double inv_c2(const Units& u) { return u.inv_c2; }
   __device__ static double s_pref(const Units& u) { return u.s_pref; }
   __device__ static double nu_pref(const Units& u) { return u.nu_pref; }
+  __device__ static double mu0_sp(const DevMech& m, int a) { return m.mu0_sp[a]; }
+  __device__ static double wilke_phi(const DevMech& m, int a, int b) {
+    return m.wilke_phi[a][b];
+  }
 };
 template <> struct MixParams<float> {
   __device__ static float inv_mm(const DevMech& m, int a) { return m.inv_mm_s[a]; }
@@ -486,6 +490,10 @@ template <> struct MixParams<float> {
   __device__ static float inv_c2(const Units& u) { return u.inv_c2_s; }
   __device__ static float s_pref(const Units& u) { return u.s_pref_s; }
   __device__ static float nu_pref(const Units& u) { return u.nu_pref_s; }
+  __device__ static float mu0_sp(const DevMech& m, int a) { return m.mu0_sp_s[a]; }
+  __device__ static float wilke_phi(const DevMech& m, int a, int b) {
+    return m.wilke_phi_s[a][b];
+  }
 };
 
 // ---------------------------------------------------------------------------
@@ -631,7 +639,23 @@ __device__ __forceinline__ void node_params(const RT* __restrict__ rec,
   const PT theta = Rmix * T * MP::inv_c2(un);
   const PT lnTr = log(T * PT(1.0 / T_REF));
   const PT s_tau = MP::s_pref(un) * rho * T * T * exp(-MP::D_T_exp(mech) * lnTr);
-  const PT mu = MP::mu0(mech) * exp(MP::mu_T_exp(mech) * lnTr);
+  PT mu = MP::mu0(mech);
+  if (mech.wilke) {
+    // Wilke's mixing rule over the species viscosities (the mole fractions'
+    // normalisation cancels between numerator and denominator)
+    PT X[M];
+#pragma unroll
+    for (int a = 0; a < M; ++a) X[a] = Y[a] * MP::inv_mm(mech, a);
+    mu = PT(0);
+#pragma unroll
+    for (int a = 0; a < M; ++a) {
+      PT den = PT(0);
+#pragma unroll
+      for (int b = 0; b < M; ++b) den += X[b] * MP::wilke_phi(mech, a, b);
+      mu += X[a] * MP::mu0_sp(mech, a) / den;
+    }
+  }
+  mu *= exp(MP::mu_T_exp(mech) * lnTr);
   const PT nu = mu / rho * MP::nu_pref(un);
   const PT omega = PT(1) / (nu / theta + PT(0.5));
   const PT omega1 = PT(1) / (nu * MP::inv_prandtl(mech) / theta + PT(0.5));
@@ -1402,80 +1426,96 @@ __device__ __forceinline__ int domain_of_block(const DomainDev* __restrict__ d, 
   return lo;
 }
 
+// Every batched kernel walks its grid's blocks b = blockIdx.x, + gridDim.x,
+// ... below nblk: launched with one block per tile it runs each tile once;
+// launched persistent (a grid sized to the blocks resident on the GPU) each
+// block processes several tiles in turn.
 template <int D, int M, typename S, typename RT>
 __global__ void __launch_bounds__(128)
 k_moments_batch(const DomainDev* __restrict__ doms, int ndom, int parity, int chem_inline,
-                int node_set) {
-  // NODES_INTERFACE: the boundary grid (four interface nodes per block), one
-  // thread per interface node
-  const DomainDev& d = doms[domain_of_block(
-      doms, ndom, blockIdx.x, node_set == NODES_INTERFACE ? GRID_BOUNDARY : GRID_NODE)];
-  const int c = d.cur0 ^ parity;
-  long long n;
-  if (node_set == NODES_INTERFACE) {
-    if (threadIdx.x & 31) return;
-    const long long k = (blockIdx.x - d.bblock_begin) * 4LL + (threadIdx.x >> 5);
-    if (k >= d.bc.n_if) return;
-    n = d.bc.if_node[k];
-  } else {
-    n = (blockIdx.x - d.block_begin) * (long long)blockDim.x + threadIdx.x;
-    if (node_set == NODES_BULK && d.bc.tag && n < d.g.N && d.bc.tag[n] >= 0) return;
+                int node_set, int nblk) {
+  for (int b = blockIdx.x; b < nblk; b += gridDim.x) {
+    // NODES_INTERFACE: the boundary grid (four interface nodes per block), one
+    // thread per interface node
+    const DomainDev& d = doms[domain_of_block(
+        doms, ndom, b, node_set == NODES_INTERFACE ? GRID_BOUNDARY : GRID_NODE)];
+    const int c = d.cur0 ^ parity;
+    long long n;
+    if (node_set == NODES_INTERFACE) {
+      if (threadIdx.x & 31) continue;
+      const long long k = (b - d.bblock_begin) * 4LL + (threadIdx.x >> 5);
+      if (k >= d.bc.n_if) continue;
+      n = d.bc.if_node[k];
+    } else {
+      n = (b - d.block_begin) * (long long)blockDim.x + threadIdx.x;
+      if (node_set == NODES_BULK && d.bc.tag && n < d.g.N && d.bc.tag[n] >= 0) continue;
+    }
+    moments_body<D, M, S, RT>(static_cast<const S*>(d.pops[c]), static_cast<RT*>(d.rec), d.Tf,
+                              d.status, d.g, d.un, d.bc, *d.mech, n, chem_inline);
   }
-  moments_body<D, M, S, RT>(static_cast<const S*>(d.pops[c]), static_cast<RT*>(d.rec), d.Tf,
-                            d.status, d.g, d.un, d.bc, *d.mech, n, chem_inline);
 }
 
 template <int D, int M, typename RT, int L>
 __global__ void __launch_bounds__(128)
-k_chem_batch(const DomainDev* __restrict__ doms, int ndom) {
-  const DomainDev& d = doms[domain_of_block(doms, ndom, blockIdx.x, GRID_CHEM)];
-  chem_entry<D, M, RT, L>(static_cast<RT*>(d.rec), d.Tf, d.status, d.g.N, d.bc.tag, d.un,
-                          *d.mech, (blockIdx.x - d.cblock_begin) * (128LL / L));
+k_chem_batch(const DomainDev* __restrict__ doms, int ndom, int nblk) {
+  for (int b = blockIdx.x; b < nblk; b += gridDim.x) {
+    const DomainDev& d = doms[domain_of_block(doms, ndom, b, GRID_CHEM)];
+    chem_entry<D, M, RT, L>(static_cast<RT*>(d.rec), d.Tf, d.status, d.g.N, d.bc.tag, d.un,
+                            *d.mech, (b - d.cblock_begin) * (128LL / L));
+  }
 }
 
 template <int D, int M, typename S, typename RT>
 __global__ void __launch_bounds__(128)
-k_collide_batch(const DomainDev* __restrict__ doms, int ndom, int parity) {
-  const DomainDev& d = doms[domain_of_block(doms, ndom, blockIdx.x, GRID_NODE)];
-  const int c = d.cur0 ^ parity;
-  collide_body<D, M, S, RT>(static_cast<const S*>(d.pops[c]),
-                            static_cast<S*>(const_cast<void*>(d.pops[1 - c])),
-                            static_cast<const RT*>(d.rec), d.Tf, d.status, d.g, d.un, d.bc,
-                            *d.mech,
-                            (blockIdx.x - d.block_begin) * (long long)blockDim.x + threadIdx.x);
+k_collide_batch(const DomainDev* __restrict__ doms, int ndom, int parity, int nblk) {
+  for (int b = blockIdx.x; b < nblk; b += gridDim.x) {
+    const DomainDev& d = doms[domain_of_block(doms, ndom, b, GRID_NODE)];
+    const int c = d.cur0 ^ parity;
+    collide_body<D, M, S, RT>(static_cast<const S*>(d.pops[c]),
+                              static_cast<S*>(const_cast<void*>(d.pops[1 - c])),
+                              static_cast<const RT*>(d.rec), d.Tf, d.status, d.g, d.un, d.bc,
+                              *d.mech, (b - d.block_begin) * (long long)blockDim.x + threadIdx.x);
+  }
 }
 
 template <int D, int M, typename RT>
 __global__ void __launch_bounds__(128)
-k_prep_batch(const DomainDev* __restrict__ doms, int ndom) {
-  const DomainDev& d = doms[domain_of_block(doms, ndom, blockIdx.x, GRID_NODE)];
-  prep_body<D, M, RT>(static_cast<const RT*>(d.rec), d.Tf, static_cast<RT*>(d.cpar), d.g,
-                      d.un, d.bc, *d.mech,
-                      (blockIdx.x - d.block_begin) * (long long)blockDim.x + threadIdx.x);
+k_prep_batch(const DomainDev* __restrict__ doms, int ndom, int nblk) {
+  for (int b = blockIdx.x; b < nblk; b += gridDim.x) {
+    const DomainDev& d = doms[domain_of_block(doms, ndom, b, GRID_NODE)];
+    prep_body<D, M, RT>(static_cast<const RT*>(d.rec), d.Tf, static_cast<RT*>(d.cpar), d.g,
+                        d.un, d.bc, *d.mech,
+                        (b - d.block_begin) * (long long)blockDim.x + threadIdx.x);
+  }
 }
 
 template <int D, int M, typename S, typename RT>
 __global__ void __launch_bounds__(32 * kCollTPN)
-k_coll_batch(const DomainDev* __restrict__ doms, int ndom, int parity) {
+k_coll_batch(const DomainDev* __restrict__ doms, int ndom, int parity, int nblk) {
   extern __shared__ __align__(16) unsigned char coll_raw[];
-  const DomainDev& d = doms[domain_of_block(doms, ndom, blockIdx.x, GRID_COLL)];
-  const int c = d.cur0 ^ parity;
-  coll_block<D, M, S, RT>(static_cast<const S*>(d.pops[c]),
-                          static_cast<S*>(const_cast<void*>(d.pops[1 - c])),
-                          static_cast<const RT*>(d.cpar), d.g, d.bc, *d.mech,
-                          (blockIdx.x - d.kblock_begin) * (long long)kCollNodes,
-                          reinterpret_cast<RT*>(coll_raw));
+  for (int b = blockIdx.x; b < nblk; b += gridDim.x) {
+    const DomainDev& d = doms[domain_of_block(doms, ndom, b, GRID_COLL)];
+    const int c = d.cur0 ^ parity;
+    // the previous tile's threads are done with the shared memory
+    if (b != blockIdx.x) __syncthreads();
+    coll_block<D, M, S, RT>(static_cast<const S*>(d.pops[c]),
+                            static_cast<S*>(const_cast<void*>(d.pops[1 - c])),
+                            static_cast<const RT*>(d.cpar), d.g, d.bc, *d.mech,
+                            (b - d.kblock_begin) * (long long)kCollNodes,
+                            reinterpret_cast<RT*>(coll_raw));
+  }
 }
 
 template <int D, int M, typename S>
 __global__ void __launch_bounds__(128)
-k_boundary_batch(const DomainDev* __restrict__ doms, int ndom, int parity) {
-  const DomainDev& d = doms[domain_of_block(doms, ndom, blockIdx.x, GRID_BOUNDARY)];
-  const int c = d.cur0 ^ parity;
-  boundary_body<D, M, S, typename ComputeType<S>::type>(static_cast<const S*>(d.pops[c]), d.bc,
-                                                      d.Tf, d.status, d.g,
-                            d.un, *d.mech, (blockIdx.x - d.bblock_begin) * 4 + threadIdx.x / 32,
-                            threadIdx.x & 31);
+k_boundary_batch(const DomainDev* __restrict__ doms, int ndom, int parity, int nblk) {
+  for (int b = blockIdx.x; b < nblk; b += gridDim.x) {
+    const DomainDev& d = doms[domain_of_block(doms, ndom, b, GRID_BOUNDARY)];
+    const int c = d.cur0 ^ parity;
+    boundary_body<D, M, S, typename ComputeType<S>::type>(
+        static_cast<const S*>(d.pops[c]), d.bc, d.Tf, d.status, d.g, d.un, *d.mech,
+        (b - d.bblock_begin) * 4 + threadIdx.x / 32, threadIdx.x & 31);
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -1798,6 +1838,21 @@ static cudaError_t out_impl(const DevMech& mech, const Geom& g, const Units& un,
   return cudaGetLastError();
 }
 
+// Grid of a batched kernel: one block per tile, or (persistent) at most the
+// blocks the GPU holds at once, from the occupancy calculator.
+template <typename K>
+static int batch_grid(K kernel, int nblk, int threads, size_t smem, bool persistent) {
+  if (!persistent || nblk <= 0) return nblk;
+  int dev = 0, sms = 0, per_sm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem) !=
+          cudaSuccess ||
+      per_sm <= 0)
+    return nblk;
+  return std::min(nblk, sms * per_sm);
+}
+
 template <int D, int M, typename S, typename RT>
 static cudaError_t batch_impl(const DomainDev* doms, int ndom, const BatchGrids& gr,
                               const Launch& lc, int parity, cudaStream_t s,
@@ -1806,38 +1861,50 @@ static cudaError_t batch_impl(const DomainDev* doms, int ndom, const BatchGrids&
   const cudaError_t pe = prepare_once<D, M, S, RT>();
   if (pe != cudaSuccess) return pe;
   const int chem_inline = lc.chem_lanes <= 1;
+  const bool ps = lc.persistent != 0;
+  auto kmom = k_moments_batch<D, M, S, RT>;
+  auto kbnd = k_boundary_batch<D, M, S>;
   if (gr.nbblocks > 0 && side.stream && side.fork && side.join) {
     // boundary kernel and the interface nodes' moments on the side stream,
     // concurrent with the bulk moments
     cudaError_t e = cudaEventRecord(side.fork, s);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(side.stream, side.fork, 0);
     if (e != cudaSuccess) return e;
-    k_boundary_batch<D, M, S><<<gr.nbblocks, bs, 0, side.stream>>>(doms, ndom, parity);
-    k_moments_batch<D, M, S, RT><<<gr.nbblocks, bs, 0, side.stream>>>(
-        doms, ndom, parity, chem_inline, NODES_INTERFACE);
+    kbnd<<<batch_grid(kbnd, gr.nbblocks, bs, 0, ps), bs, 0, side.stream>>>(doms, ndom, parity,
+                                                                          gr.nbblocks);
+    kmom<<<batch_grid(kmom, gr.nbblocks, bs, 0, ps), bs, 0, side.stream>>>(
+        doms, ndom, parity, chem_inline, NODES_INTERFACE, gr.nbblocks);
     e = cudaEventRecord(side.join, side.stream);
     if (e != cudaSuccess) return e;
-    k_moments_batch<D, M, S, RT><<<gr.nblocks, bs, 0, s>>>(doms, ndom, parity, chem_inline,
-                                                           NODES_BULK);
+    kmom<<<batch_grid(kmom, gr.nblocks, bs, 0, ps), bs, 0, s>>>(doms, ndom, parity, chem_inline,
+                                                                NODES_BULK, gr.nblocks);
     e = cudaStreamWaitEvent(s, side.join, 0);
     if (e != cudaSuccess) return e;
   } else {
     if (gr.nbblocks > 0)
-      k_boundary_batch<D, M, S><<<gr.nbblocks, bs, 0, s>>>(doms, ndom, parity);
-    k_moments_batch<D, M, S, RT><<<gr.nblocks, bs, 0, s>>>(doms, ndom, parity, chem_inline,
-                                                           NODES_ALL);
+      kbnd<<<batch_grid(kbnd, gr.nbblocks, bs, 0, ps), bs, 0, s>>>(doms, ndom, parity,
+                                                                   gr.nbblocks);
+    kmom<<<batch_grid(kmom, gr.nblocks, bs, 0, ps), bs, 0, s>>>(doms, ndom, parity, chem_inline,
+                                                                NODES_ALL, gr.nblocks);
   }
-  if (lc.chem_lanes == 4)
-    k_chem_batch<D, M, RT, 4><<<gr.ncblocks, 128, 0, s>>>(doms, ndom);
-  else if (lc.chem_lanes == 8)
-    k_chem_batch<D, M, RT, 8><<<gr.ncblocks, 128, 0, s>>>(doms, ndom);
+  if (lc.chem_lanes == 4) {
+    auto k = k_chem_batch<D, M, RT, 4>;
+    k<<<batch_grid(k, gr.ncblocks, 128, 0, ps), 128, 0, s>>>(doms, ndom, gr.ncblocks);
+  } else if (lc.chem_lanes == 8) {
+    auto k = k_chem_batch<D, M, RT, 8>;
+    k<<<batch_grid(k, gr.ncblocks, 128, 0, ps), 128, 0, s>>>(doms, ndom, gr.ncblocks);
+  }
   if (lc.coll_split) {
-    k_prep_batch<D, M, RT><<<gr.nblocks, bs, prep_smem<D, M, RT>(), s>>>(doms, ndom);
-    k_coll_batch<D, M, S, RT><<<gr.nkblocks, 32 * kCollTPN, coll_smem<D, M, RT>(), s>>>(
-        doms, ndom, parity);
+    auto kp = k_prep_batch<D, M, RT>;
+    auto kc = k_coll_batch<D, M, S, RT>;
+    const size_t sp = prep_smem<D, M, RT>(), sc = coll_smem<D, M, RT>();
+    kp<<<batch_grid(kp, gr.nblocks, bs, sp, ps), bs, sp, s>>>(doms, ndom, gr.nblocks);
+    kc<<<batch_grid(kc, gr.nkblocks, 32 * kCollTPN, sc, ps), 32 * kCollTPN, sc, s>>>(
+        doms, ndom, parity, gr.nkblocks);
   } else {
-    k_collide_batch<D, M, S, RT><<<gr.nblocks, bs, fused_smem<D, M, RT>(), s>>>(doms, ndom,
-                                                                              parity);
+    auto kf = k_collide_batch<D, M, S, RT>;
+    const size_t sf = fused_smem<D, M, RT>();
+    kf<<<batch_grid(kf, gr.nblocks, bs, sf, ps), bs, sf, s>>>(doms, ndom, parity, gr.nblocks);
   }
   return cudaGetLastError();
 }

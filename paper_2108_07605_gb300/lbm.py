@@ -48,6 +48,7 @@ class lbm_mechanism(C.Structure):
         ("D0", (C.c_double * MAX_SPECIES) * MAX_SPECIES),
         ("D_T_exponent", C.c_double), ("mu0", C.c_double),
         ("mu_T_exponent", C.c_double), ("prandtl", C.c_double),
+        ("viscosity_model", C.c_int), ("mu0_species", C.c_double * MAX_SPECIES),
     ]
 
 
@@ -73,7 +74,7 @@ class lbm_config(C.Structure):
 
 
 class lbm_launch(C.Structure):
-    _fields_ = [("chem_lanes", C.c_int), ("collide_split", C.c_int)]
+    _fields_ = [("chem_lanes", C.c_int), ("collide_split", C.c_int), ("persistent", C.c_int)]
 
 
 class lbm_diag(C.Structure):
@@ -102,6 +103,8 @@ EXPORTS = {
     "lbm_batch_run": (C.c_int, [C.c_void_p, C.c_int]),
     "lbm_batch_destroy": (C.c_int, [C.c_void_p]),
     "lbm_batch_autotune": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(lbm_launch)]),
+    "lbm_batch_set_launch": (C.c_int, [C.c_void_p, C.POINTER(lbm_launch)]),
+    "lbm_batch_get_launch": (C.c_int, [C.c_void_p, C.POINTER(lbm_launch)]),
     "lbm_set_launch": (C.c_int, [C.c_void_p, C.POINTER(lbm_launch)]),
     "lbm_get_launch": (C.c_int, [C.c_void_p, C.POINTER(lbm_launch)]),
     "lbm_autotune": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(lbm_launch)]),
@@ -185,6 +188,11 @@ def mechanism_struct(mech):
     s.mu0 = float(mech.mu0)
     s.mu_T_exponent = float(mech.mu_T_exponent)
     s.prandtl = float(mech.prandtl)
+    s.viscosity_model = 1 if getattr(mech, "viscosity_model", "mixture") == "wilke" else 0
+    mu_sp = getattr(mech, "mu0_species", None)
+    if mu_sp is not None:
+        for a, v in enumerate(np.asarray(mu_sp, dtype=np.float64)):
+            s.mu0_species[a] = float(v)
     return s
 
 
@@ -278,7 +286,8 @@ def lbm_batch_destroy(plan):
 
 
 def _launch_dict(l):
-    return {"chem_lanes": l.chem_lanes, "collide_split": l.collide_split}
+    return {"chem_lanes": l.chem_lanes, "collide_split": l.collide_split,
+            "persistent": l.persistent}
 
 
 def lbm_batch_autotune(plan, trial_steps=3):
@@ -289,8 +298,21 @@ def lbm_batch_autotune(plan, trial_steps=3):
     return _launch_dict(out)
 
 
-def lbm_set_launch(h, chem_lanes=-1, collide_split=-1):
-    l = lbm_launch(chem_lanes=int(chem_lanes), collide_split=int(collide_split))
+def lbm_batch_set_launch(plan, chem_lanes=-1, collide_split=-1, persistent=-1):
+    l = lbm_launch(chem_lanes=int(chem_lanes), collide_split=int(collide_split),
+                   persistent=int(persistent))
+    _check(load_library().lbm_batch_set_launch(plan, C.byref(l)), plan.handles[0])
+
+
+def lbm_batch_get_launch(plan):
+    out = lbm_launch()
+    _check(load_library().lbm_batch_get_launch(plan, C.byref(out)), plan.handles[0])
+    return _launch_dict(out)
+
+
+def lbm_set_launch(h, chem_lanes=-1, collide_split=-1, persistent=-1):
+    l = lbm_launch(chem_lanes=int(chem_lanes), collide_split=int(collide_split),
+                   persistent=int(persistent))
     _check(load_library().lbm_set_launch(h, C.byref(l)), h)
 
 
@@ -488,8 +510,8 @@ class Solver:
     def step(self, n=1):
         lbm_step(self.h, n)
 
-    def set_launch(self, chem_lanes=-1, collide_split=-1):
-        lbm_set_launch(self.h, chem_lanes, collide_split)
+    def set_launch(self, chem_lanes=-1, collide_split=-1, persistent=-1):
+        lbm_set_launch(self.h, chem_lanes, collide_split, persistent)
 
     def launch(self):
         return lbm_get_launch(self.h)

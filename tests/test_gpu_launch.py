@@ -13,7 +13,10 @@ trace species' chemistry and the wall reconstruction of the staircase tube
 there is 1e-4, far inside the FP32 path's field tolerances against the FP64
 oracle.  The autotuner's trial steps leave the
 handle's state untouched: a solve that was autotuned continues bit for bit
-like one that was not, given the same placement."""
+like one that was not, given the same placement.  Persistent grids for
+batch plans (each block looping over work-list tiles) change only which
+block updates a tile, so a plan gives bit-identical results with and
+without them."""
 import numpy as np
 import pytest
 
@@ -25,6 +28,10 @@ from helpers import make_gpu, max_rel_err_per_lattice, perturbed_box
 pytestmark = pytest.mark.gpu
 TOL = {"fp64": 1e-13, "fp32": 1e-4}
 PLACEMENTS = [(1, 0), (4, 0), (8, 0), (1, 1), (4, 1), (8, 1)]
+
+
+def _pl(cl, cs, persistent=0):
+    return {"chem_lanes": cl, "collide_split": cs, "persistent": persistent}
 
 
 @pytest.fixture(scope="module")
@@ -47,7 +54,7 @@ def test_placements_agree(mech, precision):
         for cl, cs in PLACEMENTS:
             g = make_gpu(mech, w, precision=precision)
             g.set_launch(cl, cs)
-            assert g.launch() == {"chem_lanes": cl, "collide_split": cs}
+            assert g.launch() == _pl(cl, cs)
             g.step(10)
             got.append(g.populations())
             g.close()
@@ -61,26 +68,26 @@ def test_placements_agree(mech, precision):
 
 def test_default_placement_follows_grid_size(mech):
     small = make_gpu(mech, perturbed_box((8, 8, 8), "D3Q27", mech=mech), precision="fp32")
-    assert small.launch() == {"chem_lanes": 4, "collide_split": 1}
+    assert small.launch() == _pl(4, 1)
     small.set_launch(1, 0)
-    assert small.launch() == {"chem_lanes": 1, "collide_split": 0}
+    assert small.launch() == _pl(1, 0)
     small.set_launch(-1, -1)
-    assert small.launch() == {"chem_lanes": 4, "collide_split": 1}
+    assert small.launch() == _pl(4, 1)
     small.close()
     small64 = make_gpu(mech, perturbed_box((8, 8, 8), "D3Q27", mech=mech))
-    assert small64.launch() == {"chem_lanes": 1, "collide_split": 1}
+    assert small64.launch() == _pl(1, 1)
     small64.close()
     big = make_gpu(mech, fields.reactor(seed=1, n=48, mech=mech), precision="fp32")
-    assert big.launch() == {"chem_lanes": 1, "collide_split": 1}     # 110,592 nodes
+    assert big.launch() == _pl(1, 1)     # 110,592 nodes
     big.close()
 
 
 def test_invalid_placement_rejected(mech):
     from paper_2108_07605_gb300 import lbm
     g = make_gpu(mech, perturbed_box((4, 4, 4), "D3Q27", mech=mech))
-    for cl, cs in [(2, 0), (0, 0), (4, 2), (16, -1)]:
+    for cl, cs, p in [(2, 0, 0), (0, 0, 0), (4, 2, 0), (16, -1, 0), (1, 1, 2), (4, 0, -2)]:
         with pytest.raises(lbm.LBMError):
-            g.set_launch(cl, cs)
+            g.set_launch(cl, cs, p)
     g.close()
 
 
@@ -91,6 +98,7 @@ def test_autotune_leaves_the_solve_unchanged(mech, precision):
     a.step(3)
     chosen = a.autotune(trial_steps=2)
     assert (chosen["chem_lanes"], chosen["collide_split"]) in PLACEMENTS
+    assert chosen["persistent"] == 0
     assert a.launch() == chosen
     a.step(6)
     b = make_gpu(mech, w, precision=precision)       # the same history, untuned
@@ -124,3 +132,25 @@ def test_batch_autotune_then_run_matches_separate_solves(mech):
         s.close()
         g.close()
         assert np.all(err < 1e-12), err
+
+
+def test_persistent_batched_grids_match(mech):
+    """A 40^3 reactor puts about 2,000 tiles on the collision work-list, more
+    than the GPU holds at once, so the persistent blocks loop several times."""
+    from paper_2108_07605_gb300 import lbm
+    ws = [fields.reactor(seed=9, n=40, mech=mech),
+          perturbed_box((9, 6, 5), "D3Q27", mech=mech),
+          fields.flame_1d(seed=10, nx=64, ny=4, nz=4, x_ign=16, mech=mech)]
+    out = {}
+    for persistent in (0, 1):
+        gs = [make_gpu(mech, w) for w in ws]
+        plan = lbm.lbm_batch_create([g.h for g in gs])
+        lbm.lbm_batch_set_launch(plan, 1, 1, persistent)
+        assert lbm.lbm_batch_get_launch(plan) == _pl(1, 1, persistent)
+        lbm.lbm_batch_run(plan, 4)
+        lbm.lbm_batch_destroy(plan)
+        out[persistent] = [g.populations() for g in gs]
+        for g in gs:
+            g.close()
+    for a, b in zip(out[0], out[1]):
+        assert np.array_equal(a, b)

@@ -211,3 +211,20 @@ def test_diagnostics_match_the_oracle(mech, case):
     for k in ("hrr_integral", "hrr_max", "T_max", "u_max"):
         assert got[k] == pytest.approx(ref[k], rel=1e-9, abs=1e-12), k
     assert got["flame_x"] == pytest.approx(ref["flame_x"], abs=1e-12)
+
+
+@pytest.mark.parametrize("collide_split", [0, 1])
+def test_wilke_viscosity_option(collide_split):
+    """The Wilke mixing-rule viscosity option, element-wise against the
+    oracle with the same option (FP64, 1e-10), in both collision kernels."""
+    from lbm_workloads.mechanism import with_viscosity_model
+    mech = with_viscosity_model(h2_air_synthetic(), "wilke")
+    w = perturbed_box((9, 6, 5), "D3Q27", mech=mech)
+    o = make_oracle(mech, w)
+    g = make_gpu(mech, w)
+    g.set_launch(-1, collide_split)
+    o.step(10)
+    g.step(10)
+    err = max_rel_err_per_lattice(g.populations(), oracle_populations(o))
+    g.close()
+    assert np.all(err < RTOL_FP64), err

@@ -152,3 +152,50 @@ def test_substeps_converge_to_stiff_reactor_solution(mech):
     order1 = np.log2(errs[0] / errs[1])
     order2 = np.log2(errs[1] / errs[2])
     assert 0.8 < order1 < 1.3 and 0.8 < order2 < 1.3, errs
+
+
+# --- Wilke mixing rule (the transport option of the viscosity model) -------
+
+def test_wilke_single_species_is_its_own_viscosity():
+    """Phi_aa = 1, so a pure species has its own viscosity at any T."""
+    from lbm_workloads.mechanism import h2_air_synthetic, with_viscosity_model
+    from oracle import transport
+    m = with_viscosity_model(h2_air_synthetic(), "wilke")
+    for a in range(m.n_species):
+        Y = np.zeros((m.n_species, 1))
+        Y[a] = 1.0
+        mu = transport.viscosity(m, np.array([900.0]), Y)[0]
+        want = m.mu0_species[a] * (900.0 / 298.15) ** m.mu_T_exponent
+        assert mu == pytest.approx(want, rel=1e-14)
+
+
+def test_wilke_binary_mixture_textbook_form():
+    """Two species: mu = X1 mu1/(X1 + X2 Phi12) + X2 mu2/(X1 Phi21 + X2),
+    with Phi21 = Phi12 (mu2/mu1)(m1/m2) (the symmetry of Wilke's Phi)."""
+    from lbm_workloads.mechanism import h2_air_synthetic, with_viscosity_model
+    from oracle import transport
+    m = with_viscosity_model(h2_air_synthetic(), "wilke")
+    i, j = m.species.index("H2"), m.species.index("N2")
+    Y = np.zeros((m.n_species, 1))
+    Y[i], Y[j] = 0.03, 0.97
+    mu = transport.viscosity(m, np.array([298.15]), Y)[0]
+    m1, m2 = m.molar_mass[i], m.molar_mass[j]
+    u1, u2 = m.mu0_species[i], m.mu0_species[j]
+    x1 = (0.03 / m1) / (0.03 / m1 + 0.97 / m2)
+    x2 = 1.0 - x1
+    phi12 = (1 + np.sqrt(u1 / u2) * (m2 / m1) ** 0.25) ** 2 / np.sqrt(8 * (1 + m1 / m2))
+    phi21 = phi12 * (u2 / u1) * (m1 / m2)
+    want = x1 * u1 / (x1 + x2 * phi12) + x2 * u2 / (x1 * phi21 + x2)
+    assert mu == pytest.approx(want, rel=1e-13)
+    assert min(u1, u2) < mu < max(u1, u2)
+
+
+def test_wilke_equal_species_recover_the_mixture_model():
+    """Species of equal mass and viscosity: Phi = 1 everywhere, mu = mu_a."""
+    from lbm_workloads.mechanism import binary_inert, with_viscosity_model
+    from oracle import transport
+    m = with_viscosity_model(binary_inert(), "wilke")
+    Y = np.array([[0.3], [0.7]])
+    mu_w = transport.viscosity(m, np.array([700.0]), Y)[0]
+    mu_m = transport.viscosity(binary_inert(), np.array([700.0]))[0]
+    assert mu_w == pytest.approx(mu_m, rel=1e-15)
