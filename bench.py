@@ -329,10 +329,13 @@ def main():
         pg.barrier()
     ms_per_step = total_ms / args.steps
     node_steps = N * args.steps * world
-    # kernels per step: boundary (when the domain has interface nodes),
-    # moments, chemistry (its own kernel when chem_lanes > 1), collision (one
-    # kernel, or two when split)
-    launches_per_step = 2 + (1 if boundary_spec(w) else 0) + \
+    # kernels per step: boundary (when the domain has interface nodes; with
+    # the reaction sub-steps inline the interface nodes' moments follow it as
+    # a second moments launch), moments, chemistry (its own kernel when
+    # chem_lanes > 1), collision (one kernel, or two when split)
+    has_bnd = boundary_spec(w) is not None
+    launches_per_step = 2 + (1 if has_bnd else 0) + \
+        (1 if has_bnd and launch["chem_lanes"] == 1 else 0) + \
         (1 if launch["chem_lanes"] > 1 else 0) + (1 if launch["collide_split"] else 0)
     value = node_updates_per_s(N, args.steps, world, M, total_ms * 1e-3)
 

@@ -101,66 +101,21 @@ __device__ __forceinline__ constexpr int pidx(int a, int b) {
 }
 
 // ---------------------------------------------------------------------------
-// Moments of the post-stream state + temperature (Sec. 2.1, Sec. 3.1-3.2,
-// Sec. 3.7 slaving, Sec. 4.1 pull streaming).
-// chem_inline = 0: the reaction sub-steps run in k_chem (one warp per node);
-// this kernel then leaves the post-stream species densities rho_a (a < M) in
-// the record's increment slots for it.
-template <int D, int M, typename S, typename RT>
-__device__ __forceinline__ void moments_body(const S* __restrict__ src, RT* __restrict__ rec,
-                                             double* __restrict__ Tf, int* __restrict__ status,
-                                             const Geom& g, const Units& un, const BCDev& bc,
-                                             const DevMech& mech, long long n,
-                                             int chem_inline) {
-  constexpr int Q = Lat<D>::Q, NP = Lat<D>::NP;
+// The node's record from its population sums (Sec. 2.1, Sec. 3.1-3.2, Sec.
+// 3.7 slaving): fields, temperature by Newton from the node's previous T,
+// and the reaction sub-steps when chem_inline (else the species densities go
+// to the increment slots for k_chem).  Shared by the moments kernel (one
+// thread per node) and the boundary kernel (interface nodes, one warp each).
+template <int D, int M, typename RT>
+__device__ __forceinline__ void moments_finish(RT* __restrict__ rec, double* __restrict__ Tf,
+                                               int* __restrict__ status, long long N,
+                                               const Units& un, const DevMech& mech,
+                                               long long n, int chem_inline, RT rho, RT rhoE,
+                                               const RT (&j)[D], const RT (&q)[D],
+                                               const RT (&P)[Lat<D>::NP], RT (&rs)[M],
+                                               RT (&js)[M][D]) {
+  constexpr int NP = Lat<D>::NP;
   using RC = Rec<D, M>;
-  const long long N = g.N;
-  if (n >= N) return;
-  const int tag = bc.tag ? bc.tag[n] : TAG_BULK;
-  if (tag == TAG_SOLID) return;
-  const int x = (int)(n % g.nx);
-  const int y = (int)((n / g.nx) % g.ny);
-  const int z = (int)(n / ((long long)g.nx * g.ny));
-  const float4* codec = g.codec;
-
-  // sums in the lattice compute type RT
-  RT rho = RT(0), rhoE = RT(0), j[D], q[D], P[NP], rs[M], js[M][D];
-#pragma unroll
-  for (int d = 0; d < D; ++d) { j[d] = RT(0); q[d] = RT(0); }
-#pragma unroll
-  for (int k = 0; k < NP; ++k) P[k] = RT(0);
-#pragma unroll
-  for (int a = 0; a < M; ++a) {
-    rs[a] = RT(0);
-#pragma unroll
-    for (int d = 0; d < D; ++d) js[a][d] = RT(0);
-  }
-#pragma unroll
-  for (int i = 0; i < Q; ++i) {
-    const long long sn = node_shift<D>(x, y, z, i, -1, g);
-#pragma unroll
-    for (int a = 0; a < M - 1; ++a) {
-      const RT v = pop_in<RT>(src, bc, tag, N, sn, a * Q + i, codec);
-      rs[a] += v;
-#pragma unroll
-      for (int d = 0; d < D; ++d)
-        if (cvel(i, d) != 0) js[a][d] += cvel(i, d) * v;
-    }
-    const RT f = pop_in<RT>(src, bc, tag, N, sn, (M - 1) * Q + i, codec);
-    rho += f;
-#pragma unroll
-    for (int d = 0; d < D; ++d) {
-      if (cvel(i, d) != 0) j[d] += cvel(i, d) * f;
-#pragma unroll
-      for (int e = d; e < D; ++e)
-        if (cvel(i, d) * cvel(i, e) != 0) P[pidx<D>(d, e)] += cvel(i, d) * cvel(i, e) * f;
-    }
-    const RT gv = pop_in<RT>(src, bc, tag, N, sn, M * Q + i, codec);
-    rhoE += gv;
-#pragma unroll
-    for (int d = 0; d < D; ++d)
-      if (cvel(i, d) != 0) q[d] += cvel(i, d) * gv;
-  }
   // slaved species M (Eq. strongest)
   rs[M - 1] = rho;
 #pragma unroll
@@ -286,6 +241,82 @@ __device__ __forceinline__ void moments_body(const S* __restrict__ src, RT* __re
     for (int d = 0; d < D; ++d)
       rec[(RC::US + a * D + d) * N + n] = tiny ? uR[d] : js[a][d] / rs[a];
   }
+}
+
+// ---------------------------------------------------------------------------
+// Moments of the post-stream state + temperature (Sec. 2.1, Sec. 3.1-3.2,
+// Sec. 3.7 slaving, Sec. 4.1 pull streaming).
+// chem_inline = 0: the reaction sub-steps run in k_chem (one warp per node);
+// this kernel then leaves the post-stream species densities rho_a (a < M) in
+// the record's increment slots for it.
+template <int D, int M, typename S, typename RT>
+__device__ __forceinline__ void moments_body(const S* __restrict__ src, RT* __restrict__ rec,
+                                             double* __restrict__ Tf, int* __restrict__ status,
+                                             const Geom& g, const Units& un, const BCDev& bc,
+                                             const DevMech& mech, long long n,
+                                             int chem_inline) {
+  constexpr int Q = Lat<D>::Q, NP = Lat<D>::NP;
+  using RC = Rec<D, M>;
+  const long long N = g.N;
+  if (n >= N) return;
+  const int tag = bc.tag ? bc.tag[n] : TAG_BULK;
+  if (tag == TAG_SOLID) return;
+  const int x = (int)(n % g.nx);
+  const int y = (int)((n / g.nx) % g.ny);
+  const int z = (int)(n / ((long long)g.nx * g.ny));
+  const float4* codec = g.codec;
+
+  // sums in the lattice compute type RT
+  RT rho = RT(0), rhoE = RT(0), j[D], q[D], P[NP], rs[M], js[M][D];
+#pragma unroll
+  for (int d = 0; d < D; ++d) { j[d] = RT(0); q[d] = RT(0); }
+#pragma unroll
+  for (int k = 0; k < NP; ++k) P[k] = RT(0);
+#pragma unroll
+  for (int a = 0; a < M; ++a) {
+    rs[a] = RT(0);
+#pragma unroll
+    for (int d = 0; d < D; ++d) js[a][d] = RT(0);
+  }
+  // x-rows of three velocities unrolled (c_x a constant), rows rolled: the
+  // fully unrolled loop is ~27 copies of the body, whose instruction fetch
+  // dominates grids too small to keep many warps per SM
+#pragma unroll 1
+  for (int r = 0; r < Q / 3; ++r) {
+    const RT cy = RT(r % 3 - 1), cz = RT(D == 3 ? r / 3 - 1 : 0);
+    const RT cyc[3] = {RT(0), cy, cz};
+#pragma unroll
+    for (int ix = 0; ix < 3; ++ix) {
+      const int i = 3 * r + ix;
+      const RT cx = RT(ix - 1);
+      const RT cv[3] = {cx, cy, cz};
+      const long long sn = node_shift<D>(x, y, z, i, -1, g);
+#pragma unroll
+      for (int a = 0; a < M - 1; ++a) {
+        const RT v = pop_in<RT>(src, bc, tag, N, sn, a * Q + i, codec);
+        rs[a] += v;
+        if (ix != 1) js[a][0] += cx * v;
+#pragma unroll
+        for (int d = 1; d < D; ++d) js[a][d] += cyc[d] * v;
+      }
+      const RT f = pop_in<RT>(src, bc, tag, N, sn, (M - 1) * Q + i, codec);
+      rho += f;
+#pragma unroll
+      for (int d = 0; d < D; ++d) {
+        if (d != 0 || ix != 1) j[d] += cv[d] * f;
+#pragma unroll
+        for (int e = d; e < D; ++e)
+          if (d != 0 || ix != 1) P[pidx<D>(d, e)] += cv[d] * cv[e] * f;
+      }
+      const RT gv = pop_in<RT>(src, bc, tag, N, sn, M * Q + i, codec);
+      rhoE += gv;
+#pragma unroll
+      for (int d = 0; d < D; ++d)
+        if (d != 0 || ix != 1) q[d] += cv[d] * gv;
+    }
+  }
+  moments_finish<D, M, RT>(rec, Tf, status, N, un, mech, n, chem_inline, rho, rhoE, j, q, P, rs,
+                           js);
 }
 
 // ---------------------------------------------------------------------------
@@ -594,40 +625,51 @@ __device__ __forceinline__ void node_params(const RT* __restrict__ rec,
       phi_in[d] = rin * ui * (RT(1) - RT(3) * RT(bc.theta_in)) - rin * ui * ui * ui;
     }
   }
+  // x-rows of neighbours unrolled, rows rolled (instruction footprint, as in
+  // the moments kernel)
+#pragma unroll 1
+  for (int r = 0; r < Q / 3; ++r) {
+    const int cyi = r % 3 - 1, czi = D == 3 ? r / 3 - 1 : 0;
 #pragma unroll
-  for (int i = 0; i < Q; ++i) {
-    if (csq(i, D) == 0) continue;
-    long long nb = 0;
-    int gk = BK_NONE;
-    if (!bc.tag) {
-      nb = node_shift<D>(x, y, z, i, +1, g);
-    } else {
-      int cc[3] = {x + cvel(i, 0), y + cvel(i, 1), D == 3 ? z + cvel(i, 2) : z};
-      const int ext[3] = {g.nx, g.ny, g.nz};
+    for (int ix = 0; ix < 3; ++ix) {
+      const int cxi = ix - 1;
+      if (ix == 1 && cyi == 0 && czi == 0) continue;          // the rest velocity
+      const int cvi[3] = {cxi, cyi, czi};
+      long long nb = 0;
+      int gk = BK_NONE;
+      if (!bc.tag) {
+        nb = node_shift<D>(x, y, z, 3 * r + ix, +1, g);
+      } else {
+        int cc[3] = {x + cxi, y + cyi, D == 3 ? z + czi : z};
+        const int ext[3] = {g.nx, g.ny, g.nz};
 #pragma unroll
-      for (int a = 0; a < D; ++a) {
-        if (cc[a] < 0) {
-          if (bc.face[2 * a]) { if (!gk) gk = bc.face[2 * a]; } else cc[a] += ext[a];
-        } else if (cc[a] >= ext[a]) {
-          if (bc.face[2 * a + 1]) { if (!gk) gk = bc.face[2 * a + 1]; } else cc[a] -= ext[a];
+        for (int a = 0; a < D; ++a) {
+          if (cc[a] < 0) {
+            if (bc.face[2 * a]) { if (!gk) gk = bc.face[2 * a]; } else cc[a] += ext[a];
+          } else if (cc[a] >= ext[a]) {
+            if (bc.face[2 * a + 1]) { if (!gk) gk = bc.face[2 * a + 1]; } else cc[a] -= ext[a];
+          }
+        }
+        if (!gk) {
+          nb = cc[0] + (long long)g.nx * (cc[1] + (long long)g.ny * cc[2]);
+          if (bc.has_solid && bc.tag[nb] == TAG_SOLID) gk = bc.solid_kind;
         }
       }
-      if (!gk) {
-        nb = cc[0] + (long long)g.nx * (cc[1] + (long long)g.ny * cc[2]);
-        if (bc.has_solid && bc.tag[nb] == TAG_SOLID) gk = bc.solid_kind;
+      // 3 w_i: the product of 2/3 (c = 0) and 1/6 (c = +-1) per axis
+      const RT wy = cyi == 0 ? RT(2.0 / 3.0) : RT(1.0 / 6.0);
+      const RT wz = D == 3 ? (czi == 0 ? RT(2.0 / 3.0) : RT(1.0 / 6.0)) : RT(1);
+      const RT w3 = RT(3) * ((ix == 1 ? RT(2.0 / 3.0) : RT(1.0 / 6.0)) * wy * wz);
+#pragma unroll
+      for (int d = 0; d < D; ++d) {
+        if (cvi[d] == 0) continue;
+        const RT wc = w3 * RT(cvi[d]);
+        const RT pv = gk == BK_NONE ? __ldg(rec + (RC::PHI + d) * N + nb)
+                      : (gk == BK_INLET ? phi_in[d] : (gk == BK_OUTLET ? phi_self[d] : RT(0)));
+        dPhi[d] += wc * pv;
+#pragma unroll
+        for (int a = 0; a < M; ++a)
+          gY[a][d] += wc * (gk == BK_NONE ? __ldg(rec + (RC::Y + a) * N + nb) : RT(Y[a]));
       }
-    }
-    const RT w3 = RT(3) * wstd<RT>(i, D);
-#pragma unroll
-    for (int d = 0; d < D; ++d) {
-      if (cvel(i, d) == 0) continue;
-      const RT wc = w3 * RT(cvel(i, d));
-      const RT pv = gk == BK_NONE ? __ldg(rec + (RC::PHI + d) * N + nb)
-                    : (gk == BK_INLET ? phi_in[d] : (gk == BK_OUTLET ? phi_self[d] : RT(0)));
-      dPhi[d] += wc * pv;
-#pragma unroll
-      for (int a = 0; a < M; ++a)
-        gY[a][d] += wc * (gk == BK_NONE ? __ldg(rec + (RC::Y + a) * N + nb) : RT(Y[a]));
     }
   }
 
@@ -1117,52 +1159,62 @@ __device__ __forceinline__ R warp_sum(R v) {
   return v;
 }
 
-// Warp-cooperative macroscopic state of populations fetch(l, i): rho, u, Y,
-// u_a (Eq. momentum1 with reading R5), T by Newton on Eq. temperature from
+// Warp-cooperative macroscopic state of a node: lane i < Q holds v[l], the
+// population of lattice l in direction i (lanes >= Q hold zeros).  rho, u,
+// Y, u_a (Eq. momentum1 with reading R5), T by Newton on Eq. temperature from
 // T_guess; every lane returns the same state.  R = float (mixed path): sums
-// in FP32, the Newton solve in float-float as in the moments kernel.
-template <int D, int M, typename R, typename F>
-__device__ void warp_state_of(F fetch, EqSet<D, M, R>& s, double T_guess, const DevMech& m,
-                              const Units& un, int* status, int lane) {
-  constexpr int Q = Lat<D>::Q, L = M + 1;
-  R rho = R(0), rhoE = R(0), j[D], rs[M], js[M][D];
-  for (int d = 0; d < D; ++d) j[d] = R(0);
-  for (int a = 0; a < M; ++a) {
-    rs[a] = R(0);
-    for (int d = 0; d < D; ++d) js[a][d] = R(0);
+// in FP32, the Newton solve in float-float as in the moments kernel.  Not
+// inlined: the boundary kernel calls it up to three times, and one shared
+// copy keeps its instruction footprint small.
+template <int D, int M, typename R>
+__device__ __noinline__ void warp_state_of(const R (&v)[M + 1], EqSet<D, M, R>& s,
+                                           double T_guess, const DevMech& m, const Units& un,
+                                           int* status, int lane) {
+  constexpr int Q = Lat<D>::Q;
+  const bool act = lane < Q;
+  const int i = act ? lane : 0;
+  R c[D];
+#pragma unroll
+  for (int d = 0; d < D; ++d) c[d] = act ? R(cvel(i, d)) : R(0);
+  R rho, rhoE, j[D], rs[M], js[M][D];
+#pragma unroll
+  for (int l = 0; l < M - 1; ++l) {
+    rs[l] = v[l];
+#pragma unroll
+    for (int d = 0; d < D; ++d) js[l][d] = c[d] * v[l];
   }
-  for (int t = lane; t < L * Q; t += 32) {
-    const int l = t / Q, i = t % Q;
-    const R v = fetch(l, i);
-    if (l < M - 1) {
-      rs[l] += v;
-      for (int d = 0; d < D; ++d) js[l][d] += R(cvel(i, d)) * v;
-    } else if (l == M - 1) {
-      rho += v;
-      for (int d = 0; d < D; ++d) j[d] += R(cvel(i, d)) * v;
-    } else {
-      rhoE += v;
-    }
-  }
+  rho = v[M - 1];
+#pragma unroll
+  for (int d = 0; d < D; ++d) j[d] = c[d] * v[M - 1];
+  rhoE = v[M];
   rho = warp_sum(rho);
   rhoE = warp_sum(rhoE);
+#pragma unroll
   for (int d = 0; d < D; ++d) j[d] = warp_sum(j[d]);
+#pragma unroll
   for (int a = 0; a < M - 1; ++a) {
     rs[a] = warp_sum(rs[a]);
+#pragma unroll
     for (int d = 0; d < D; ++d) js[a][d] = warp_sum(js[a][d]);
   }
   rs[M - 1] = rho;
+#pragma unroll
   for (int d = 0; d < D; ++d) js[M - 1][d] = j[d];
+#pragma unroll
   for (int a = 0; a < M - 1; ++a) {
     rs[M - 1] -= rs[a];
+#pragma unroll
     for (int d = 0; d < D; ++d) js[M - 1][d] -= js[a][d];
   }
   s.rho = rho;
   R usq = R(0);
+#pragma unroll
   for (int d = 0; d < D; ++d) { s.u[d] = j[d] / rho; usq += s.u[d] * s.u[d]; }
+#pragma unroll
   for (int a = 0; a < M; ++a) {
     s.Y[a] = rs[a] / rho;
     const bool tiny = species_velocity_undefined<D, R>(rs[a], js[a]);
+#pragma unroll
     for (int d = 0; d < D; ++d) s.us[a][d] = tiny ? s.u[d] : js[a][d] / rs[a];
   }
   bool ok;
@@ -1184,7 +1236,7 @@ __device__ void warp_state_of(F fetch, EqSet<D, M, R>& s, double T_guess, const 
 // reconstructed populations are kept in FP64 scratch.
 template <int D, int M, typename S, typename R>
 __device__ __forceinline__ void boundary_body(const S* __restrict__ src, const BCDev& bc,
-                                              const double* __restrict__ Tf,
+                                              const double* Tf,
                                               int* __restrict__ status, const Geom& g,
                                               const Units& un, const DevMech& mech, int k,
                                               int lane) {
@@ -1206,12 +1258,16 @@ __device__ __forceinline__ void boundary_body(const S* __restrict__ src, const B
                                      l * Q + i);
   };
   double* P = bc.pops + k;                       // element (l, i) at P[(l Q + i) st]
-  for (int t = lane; t < L * Q; t += 32) {       // pull streaming (wrapped address)
-    const int l = t / Q, i = t % Q;
+  // lane i < Q works on direction i, every lattice l (unrolled)
+  const bool act = lane < Q;
+  const int i = act ? lane : 0;
+  const bool in_i = act && (inc >> i & 1u);      // an incoming (unknown) link
+  if (act) {                                     // pull streaming (wrapped address)
     const long long sn = node_shift<D>(x, y, z, i, -1, g);
-    P[(long long)t * st] = (inc >> i & 1u) && kind == BK_BB
-                               ? double(ld(l, Q - 1 - i, n))
-                               : double(ld(l, i, sn));
+    const bool bb = in_i && kind == BK_BB;
+#pragma unroll
+    for (int l = 0; l < L; ++l)
+      P[(long long)(l * Q + i) * st] = bb ? double(ld(l, Q - 1 - i, n)) : double(ld(l, i, sn));
   }
   if (kind == BK_BB) return;
   __syncwarp();
@@ -1219,14 +1275,14 @@ __device__ __forceinline__ void boundary_body(const S* __restrict__ src, const B
   A.own_species_u = B.own_species_u = false;
   if (kind == BK_TMS) {
     // step 1: bounce-back density and mass fractions (Eqs. BBrho, BBY)
-    R rho_bb = R(0), rs[M];
-    for (int a = 0; a < M - 1; ++a) rs[a] = R(0);
-    for (int t = lane; t < M * Q; t += 32) {
-      const int l = t / Q, i = t % Q;
-      const R v = (inc >> i & 1u) ? ld(l, Q - 1 - i, n) : R(P[(long long)t * st]);
-      if (l < M - 1) rs[l] += v; else rho_bb += v;
+    R rho_bb, rs[M];
+#pragma unroll
+    for (int l = 0; l < M; ++l) {
+      const R v = !act ? R(0) : (in_i ? ld(l, Q - 1 - i, n) : R(P[(long long)(l * Q + i) * st]));
+      if (l < M - 1) rs[l] = v; else rho_bb = v;
     }
     rho_bb = warp_sum(rho_bb);
+#pragma unroll
     for (int a = 0; a < M - 1; ++a) rs[a] = warp_sum(rs[a]);
     A.rho = rho_bb;
     R ysum = R(0);
@@ -1248,12 +1304,15 @@ __device__ __forceinline__ void boundary_body(const S* __restrict__ src, const B
     const long long stride = ax == 0 ? 1 : (ax == 1 ? (long long)g.nx : (long long)g.nx * g.ny);
     const long long up = n - sg * stride;
     EqSet<D, M, R> s0, s1;
-    warp_state_of<D, M, R>([&](int l, int i) { return ld(l, i, n); }, s0, Tf[n], mech, un,
-                           status, lane);
+    R v[L];
+#pragma unroll
+    for (int l = 0; l < L; ++l) v[l] = act ? ld(l, i, n) : R(0);
+    warp_state_of<D, M, R>(v, s0, Tf[n], mech, un, status, lane);
     // (the upstream node's Newton starts from this node's T guess: the bulk
     // moments kernel may be rewriting the upstream one concurrently)
-    warp_state_of<D, M, R>([&](int l, int i) { return ld(l, i, up); }, s1, Tf[n], mech, un,
-                           status, lane);
+#pragma unroll
+    for (int l = 0; l < L; ++l) v[l] = act ? ld(l, i, up) : R(0);
+    warp_state_of<D, M, R>(v, s1, Tf[n], mech, un, status, lane);
     // LODI wave amplitudes (reading R13) in FP64 from the two states: a few
     // scalars per node
     double R0 = 0.0, R1 = 0.0, Cv = 0.0;
@@ -1293,19 +1352,25 @@ __device__ __forceinline__ void boundary_body(const S* __restrict__ src, const B
     eq_prepare(A, mech, un);                         // step 1 (Eqs. out_f-out_fa)
   }
   // incoming links at A, then the local state (Eqs. locRho-locT and analogues)
-  for (int t = lane; t < L * Q; t += 32) {
-    const int l = t / Q, i = t % Q;
-    if (inc >> i & 1u) P[(long long)t * st] = double(eq_pop(A, l, i));
+  if (in_i) {
+#pragma unroll 1
+    for (int l = 0; l < L; ++l) P[(long long)(l * Q + i) * st] = double(eq_pop(A, l, i));
   }
   __syncwarp();
-  warp_state_of<D, M, R>([&](int l, int i) { return R(P[(long long)(l * Q + i) * st]); }, loc,
-                         Tf[n], mech, un, status, lane);
+  {
+    R v[L];
+#pragma unroll
+    for (int l = 0; l < L; ++l) v[l] = act ? R(P[(long long)(l * Q + i) * st]) : R(0);
+    warp_state_of<D, M, R>(v, loc, Tf[n], mech, un, status, lane);
+  }
   loc.own_species_u = kind == BK_TMS;             // TMS local species use u_a^loc
   eq_prepare(loc, mech, un);
   if (kind == BK_INLET && bc.inlet_simplified) {  // simplified inlet: the local equilibria
     __syncwarp();
-    for (int t = lane; t < L * Q; t += 32)
-      P[(long long)t * st] = double(eq_pop(loc, t / Q, t % Q));
+    if (act) {
+#pragma unroll 1
+      for (int l = 0; l < L; ++l) P[(long long)(l * Q + i) * st] = double(eq_pop(loc, l, i));
+    }
     return;
   }
   if (kind == BK_INLET) {                         // target (Eqs. in_tgt_*)
@@ -1317,11 +1382,70 @@ __device__ __forceinline__ void boundary_body(const S* __restrict__ src, const B
   }
   const EqSet<D, M, R>& Bref = kind == BK_INLET ? B : A;
   __syncwarp();
-  for (int t = lane; t < L * Q; t += 32) {
-    const int l = t / Q, i = t % Q;
-    double& p = P[(long long)t * st];
-    p = double(eq_pop(Bref, l, i) + R(p) - eq_pop(loc, l, i));
+  if (act) {
+#pragma unroll 1
+    for (int l = 0; l < L; ++l) {
+      double& p = P[(long long)(l * Q + i) * st];
+      p = double(eq_pop(Bref, l, i) + R(p) - eq_pop(loc, l, i));
+    }
   }
+}
+
+// The record of interface node k from its reconstructed populations, by the
+// warp that reconstructed them: lane i sums direction i, the sums are reduced
+// across the warp, and lane 0 completes the record as the moments kernel
+// does (moments_finish; the reaction sub-steps are left to k_chem).  Takes
+// the interface nodes' moments off the side stream's critical path.
+template <int D, int M, typename R>
+__device__ __forceinline__ void boundary_record(const BCDev& bc, R* __restrict__ rec,
+                                                double* __restrict__ Tf,
+                                                int* __restrict__ status, const Geom& g,
+                                                const Units& un, const DevMech& mech, int k,
+                                                int lane) {
+  constexpr int Q = Lat<D>::Q, NP = Lat<D>::NP;
+  if (k >= bc.n_if) return;                                         // whole warp leaves
+  __syncwarp();
+  const long long n = bc.if_node[k];
+  const double* P = bc.pops + k;
+  const long long st = bc.n_if;
+  const bool act = lane < Q;
+  const int i = act ? lane : 0;
+  R c[D];
+#pragma unroll
+  for (int d = 0; d < D; ++d) c[d] = act ? R(cvel(i, d)) : R(0);
+  R rho, rhoE, j[D], q[D], Pt[NP], rs[M], js[M][D];
+#pragma unroll
+  for (int l = 0; l < M - 1; ++l) {
+    rs[l] = act ? R(P[(long long)(l * Q + i) * st]) : R(0);
+#pragma unroll
+    for (int d = 0; d < D; ++d) js[l][d] = c[d] * rs[l];
+  }
+  rho = act ? R(P[(long long)((M - 1) * Q + i) * st]) : R(0);
+  rhoE = act ? R(P[(long long)(M * Q + i) * st]) : R(0);
+#pragma unroll
+  for (int d = 0; d < D; ++d) {
+    j[d] = c[d] * rho;
+    q[d] = c[d] * rhoE;
+#pragma unroll
+    for (int e = d; e < D; ++e) Pt[pidx<D>(d, e)] = c[d] * c[e] * rho;
+  }
+  rho = warp_sum(rho);
+  rhoE = warp_sum(rhoE);
+#pragma unroll
+  for (int d = 0; d < D; ++d) {
+    j[d] = warp_sum(j[d]);
+    q[d] = warp_sum(q[d]);
+  }
+#pragma unroll
+  for (int p = 0; p < NP; ++p) Pt[p] = warp_sum(Pt[p]);
+#pragma unroll
+  for (int a = 0; a < M - 1; ++a) {
+    rs[a] = warp_sum(rs[a]);
+#pragma unroll
+    for (int d = 0; d < D; ++d) js[a][d] = warp_sum(js[a][d]);
+  }
+  if (lane == 0)
+    moments_finish<D, M, R>(rec, Tf, status, g.N, un, mech, n, 0, rho, rhoE, j, q, Pt, rs, js);
 }
 
 // ---------------------------------------------------------------------------
@@ -1398,14 +1522,18 @@ k_coll(const S* __restrict__ src, S* __restrict__ dst, const RT* __restrict__ cp
                           reinterpret_cast<RT*>(coll_raw));
 }
 
+// rec != nullptr: the warp also writes its interface node's record
+// (reaction sub-steps in k_chem); else the moments kernel does.
 template <int D, int M, typename S>
 __global__ void __launch_bounds__(128)
 k_boundary(const S* __restrict__ src, const __grid_constant__ BCDev bc,
-           const double* __restrict__ Tf, int* __restrict__ status,
+           double* __restrict__ Tf, int* __restrict__ status,
            const __grid_constant__ Geom g, const __grid_constant__ Units un,
-           const __grid_constant__ DevMech mech) {
-  boundary_body<D, M, S, typename ComputeType<S>::type>(src, bc, Tf, status, g, un, mech,
-                            blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32, threadIdx.x & 31);
+           const __grid_constant__ DevMech mech, typename ComputeType<S>::type* rec) {
+  using R = typename ComputeType<S>::type;
+  const int k = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32, lane = threadIdx.x & 31;
+  boundary_body<D, M, S, R>(src, bc, Tf, status, g, un, mech, k, lane);
+  if (rec) boundary_record<D, M, R>(bc, rec, Tf, status, g, un, mech, k, lane);
 }
 
 // ---------------------------------------------------------------------------
@@ -1508,13 +1636,18 @@ k_coll_batch(const DomainDev* __restrict__ doms, int ndom, int parity, int nblk)
 
 template <int D, int M, typename S>
 __global__ void __launch_bounds__(128)
-k_boundary_batch(const DomainDev* __restrict__ doms, int ndom, int parity, int nblk) {
+k_boundary_batch(const DomainDev* __restrict__ doms, int ndom, int parity, int with_rec,
+                 int nblk) {
+  using R = typename ComputeType<S>::type;
   for (int b = blockIdx.x; b < nblk; b += gridDim.x) {
     const DomainDev& d = doms[domain_of_block(doms, ndom, b, GRID_BOUNDARY)];
     const int c = d.cur0 ^ parity;
-    boundary_body<D, M, S, typename ComputeType<S>::type>(
-        static_cast<const S*>(d.pops[c]), d.bc, d.Tf, d.status, d.g, d.un, *d.mech,
-        (b - d.bblock_begin) * 4 + threadIdx.x / 32, threadIdx.x & 31);
+    const int k = (b - d.bblock_begin) * 4 + threadIdx.x / 32, lane = threadIdx.x & 31;
+    boundary_body<D, M, S, R>(static_cast<const S*>(d.pops[c]), d.bc, d.Tf, d.status, d.g,
+                              d.un, *d.mech, k, lane);
+    if (with_rec)
+      boundary_record<D, M, R>(d.bc, static_cast<R*>(d.rec), d.Tf, d.status, d.g, d.un,
+                               *d.mech, k, lane);
   }
 }
 
@@ -1770,10 +1903,13 @@ static cudaError_t step_impl(const DevMech& mech, const StepArgs& a, cudaStream_
       cudaError_t e = cudaEventRecord(a.ev_fork, s);
       if (e == cudaSuccess) e = cudaStreamWaitEvent(a.side, a.ev_fork, 0);
       if (e != cudaSuccess) return e;
-      k_boundary<D, M, S><<<(a.bc.n_if + 3) / 4, 128, 0, a.side>>>(src, a.bc, a.Tfield,
-                                                                  a.status, a.g, a.un, mech);
-      k_moments<D, M, S, RT><<<blocks_for(a.bc.n_if, bs), bs, 0, a.side>>>(
-          src, rec, a.Tfield, a.status, a.g, a.un, a.bc, mech, !chem_sep, NODES_INTERFACE);
+      // with the reaction sub-steps in k_chem the boundary warps also write
+      // their nodes' records; else the interface moments follow them
+      k_boundary<D, M, S><<<(a.bc.n_if + 3) / 4, 128, 0, a.side>>>(
+          src, a.bc, a.Tfield, a.status, a.g, a.un, mech, chem_sep ? rec : nullptr);
+      if (!chem_sep)
+        k_moments<D, M, S, RT><<<blocks_for(a.bc.n_if, bs), bs, 0, a.side>>>(
+            src, rec, a.Tfield, a.status, a.g, a.un, a.bc, mech, 1, NODES_INTERFACE);
       e = cudaEventRecord(a.ev_join, a.side);
       if (e != cudaSuccess) return e;
       k_moments<D, M, S, RT><<<nb, bs, 0, s>>>(src, rec, a.Tfield, a.status, a.g, a.un, a.bc,
@@ -1781,11 +1917,13 @@ static cudaError_t step_impl(const DevMech& mech, const StepArgs& a, cudaStream_
       e = cudaStreamWaitEvent(s, a.ev_join, 0);
       if (e != cudaSuccess) return e;
     } else {
+      const bool bnd_rec = a.bc.n_if > 0 && chem_sep;
       if (a.bc.n_if > 0)
-        k_boundary<D, M, S><<<(a.bc.n_if + 3) / 4, 128, 0, s>>>(src, a.bc, a.Tfield, a.status,
-                                                                a.g, a.un, mech);
+        k_boundary<D, M, S><<<(a.bc.n_if + 3) / 4, 128, 0, s>>>(
+            src, a.bc, a.Tfield, a.status, a.g, a.un, mech, bnd_rec ? rec : nullptr);
       k_moments<D, M, S, RT><<<nb, bs, 0, s>>>(src, rec, a.Tfield, a.status, a.g, a.un, a.bc,
-                                               mech, !chem_sep, NODES_ALL);
+                                               mech, !chem_sep,
+                                               bnd_rec ? NODES_BULK : NODES_ALL);
     }
     if (chem_sep)
       launch_chem<D, M, RT>(lc, blocks_for(a.g.N, 128 / lc.chem_lanes), s,
@@ -1870,10 +2008,13 @@ static cudaError_t batch_impl(const DomainDev* doms, int ndom, const BatchGrids&
     cudaError_t e = cudaEventRecord(side.fork, s);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(side.stream, side.fork, 0);
     if (e != cudaSuccess) return e;
-    kbnd<<<batch_grid(kbnd, gr.nbblocks, bs, 0, ps), bs, 0, side.stream>>>(doms, ndom, parity,
-                                                                          gr.nbblocks);
-    kmom<<<batch_grid(kmom, gr.nbblocks, bs, 0, ps), bs, 0, side.stream>>>(
-        doms, ndom, parity, chem_inline, NODES_INTERFACE, gr.nbblocks);
+    // with the reaction sub-steps in k_chem the boundary warps also write
+    // their nodes' records; else the interface moments follow them
+    kbnd<<<batch_grid(kbnd, gr.nbblocks, bs, 0, ps), bs, 0, side.stream>>>(
+        doms, ndom, parity, !chem_inline, gr.nbblocks);
+    if (chem_inline)
+      kmom<<<batch_grid(kmom, gr.nbblocks, bs, 0, ps), bs, 0, side.stream>>>(
+          doms, ndom, parity, chem_inline, NODES_INTERFACE, gr.nbblocks);
     e = cudaEventRecord(side.join, side.stream);
     if (e != cudaSuccess) return e;
     kmom<<<batch_grid(kmom, gr.nblocks, bs, 0, ps), bs, 0, s>>>(doms, ndom, parity, chem_inline,
@@ -1881,11 +2022,12 @@ static cudaError_t batch_impl(const DomainDev* doms, int ndom, const BatchGrids&
     e = cudaStreamWaitEvent(s, side.join, 0);
     if (e != cudaSuccess) return e;
   } else {
+    const bool bnd_rec = gr.nbblocks > 0 && !chem_inline;
     if (gr.nbblocks > 0)
       kbnd<<<batch_grid(kbnd, gr.nbblocks, bs, 0, ps), bs, 0, s>>>(doms, ndom, parity,
-                                                                   gr.nbblocks);
-    kmom<<<batch_grid(kmom, gr.nblocks, bs, 0, ps), bs, 0, s>>>(doms, ndom, parity, chem_inline,
-                                                                NODES_ALL, gr.nblocks);
+                                                                   !chem_inline, gr.nbblocks);
+    kmom<<<batch_grid(kmom, gr.nblocks, bs, 0, ps), bs, 0, s>>>(
+        doms, ndom, parity, chem_inline, bnd_rec ? NODES_BULK : NODES_ALL, gr.nblocks);
   }
   if (lc.chem_lanes == 4) {
     auto k = k_chem_batch<D, M, RT, 4>;
