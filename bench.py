@@ -329,13 +329,12 @@ def main():
         pg.barrier()
     ms_per_step = total_ms / args.steps
     node_steps = N * args.steps * world
-    # kernels per step: boundary (when the domain has interface nodes; with
-    # the reaction sub-steps inline the interface nodes' moments follow it as
-    # a second moments launch), moments, chemistry (its own kernel when
-    # chem_lanes > 1), collision (one kernel, or two when split)
+    # kernels per step: moments, chemistry (its own kernel when
+    # chem_lanes > 1), collision (one kernel, or two when split); with
+    # interface nodes also the boundary kernel and, after it on the side
+    # stream, the interface nodes' moments (sub-steps inline) or chemistry
     has_bnd = boundary_spec(w) is not None
-    launches_per_step = 2 + (1 if has_bnd else 0) + \
-        (1 if has_bnd and launch["chem_lanes"] == 1 else 0) + \
+    launches_per_step = 2 + (2 if has_bnd else 0) + \
         (1 if launch["chem_lanes"] > 1 else 0) + (1 if launch["collide_split"] else 0)
     value = node_updates_per_s(N, args.steps, world, M, total_ms * 1e-3)
 

@@ -120,26 +120,40 @@ __device__ __forceinline__ ff ff_exp(ff x) {
   if (x.hi < -103.0f) return ff(0.f, 0.f);
   // Table-driven reduction (Tang, ACM TOMS 15(2), 1989): x = (64 n + j) ln2/64
   // + r with |r| <= ln2/128; ln2/64 = L1 + L2 + L3, L1 with 9 significant
-  // bits so that k * L1 is exact for every k reached here.
+  // bits so that k * L1 is exact for every k reached here, and x.hi - k L1
+  // is exact too (the operands are within a factor 2 of each other, Sterbenz
+  // lemma, or k = 0).  k L3 is below 3e-10 and goes into the low part.
   const float L1 = 0.010833740234375f, L2 = -3.3155381515825866e-06f,
               L3 = 2.572804640231345e-14f;
   const float k = rintf(__fmul_rn(x.hi, 92.33248138427734f));   // 64 / ln2
-  ff r = x - ff(__fmul_rn(k, L1));
+  ff r = two_sum(__fsub_rn(x.hi, __fmul_rn(k, L1)), x.lo);
   r = r - two_prod(k, L2);
-  r = r - ff(__fmul_rn(k, L3));
+  r.lo = __fmaf_rn(-k, L3, r.lo);
   // e^r - 1 = r + r^2 (1/2 + c), c = r/6 + r^2/24 + r^3/120 + r^4/720: c is
   // below 1e-3 and needs only FP32 (its rounding is below 1e-15 of e^r);
-  // the Taylor remainder r^7/5040 is below 1e-19.
+  // the Taylor remainder r^7/5040 is below 1e-19.  r^2 (~3e-5 at most)
+  // in float-float from an exact product; its product with c (below 3e-8)
+  // in FP32.
   const float rh = r.hi;
   const float c = __fmul_rn(rh, __fmaf_rn(rh, __fmaf_rn(rh, __fmaf_rn(rh, 1.3888889225e-3f,
                                                                            8.3333337680e-3f),
                                                        4.1666667908e-2f),
                                           1.6666667163e-1f));
-  const ff em1 = r + (r * r) * two_sum(0.5f, c);
+  ff r2 = two_prod(rh, rh);
+  r2.lo = __fmaf_rn(__fmul_rn(2.f, rh), r.lo, r2.lo);
+  ff em1 = r + ff(__fmul_rn(0.5f, r2.hi), __fmul_rn(0.5f, r2.lo));
+  em1 = fast_two_sum(em1.hi, __fmaf_rn(r2.hi, c, em1.lo));
   const int ki = (int)k;
   const float2 t = __ldg(&kExp2Tab64[ki & 63]);
   const ff tj(t.x, t.y);
-  return ff_ldexp(tj + tj * em1, ki >> 6);
+  const ff y = tj + tj * em1;
+  // scale by 2^e: an exact multiply while 2^e is a normal float
+  const int e = ki >> 6;
+  if (e >= -126) {
+    const float sc = __int_as_float((e + 127) << 23);
+    return ff(__fmul_rn(y.hi, sc), __fmul_rn(y.lo, sc));
+  }
+  return ff_ldexp(y, e);
 }
 
 __device__ __forceinline__ ff ff_log(ff x) {

@@ -355,6 +355,11 @@ template <> struct Chem<double> {
   __device__ static double dt_sub(const Units& u) { return u.dt / u.substeps; }
   __device__ static double of(double v) { return v; }
   __device__ static double of_T(double T) { return T; }
+  __device__ static double ucoef(const DevMech& m, int k, int a) {
+    return k == 0 ? m.u0[a] : (k == 1 ? m.u1[a] : (k == 2 ? m.u2[a] : m.u3[a]));
+  }
+  __device__ static double mag(double x) { return fabs(x); }
+  __device__ static double rtol(const Units& u) { return u.newton_rtol; }
   template <int M>
   __device__ static double newton(const DevMech& m, const double (&r)[M], double rho, double U,
                                   double T, const Units& un, bool& ok) {
@@ -385,6 +390,11 @@ template <> struct Chem<ff> {
   __device__ static ff dt_sub(const Units& u) { return u.dt_sub_f; }
   __device__ static ff of(float v) { return ff(v); }
   __device__ static ff of_T(double T) { return ff_from_double(T); }
+  __device__ static ff ucoef(const DevMech& m, int k, int a) {
+    return k == 0 ? m.u0_f[a] : (k == 1 ? m.u1_f[a] : (k == 2 ? m.u2_f[a] : m.u3_f[a]));
+  }
+  __device__ static float mag(ff x) { return fabsf(x.hi); }
+  __device__ static float rtol(const Units& u) { return u.newton_rtol_f; }
   template <int M>
   __device__ static ff newton(const DevMech& m, const ff (&r)[M], ff rho, ff U, ff T,
                               const Units& un, bool& ok) {
@@ -397,6 +407,60 @@ template <> struct Chem<ff> {
 
 template <typename RT> struct ChemType { using type = double; };
 template <> struct ChemType<float> { using type = ff; };
+
+__device__ __forceinline__ double shfl_ct(unsigned mask, double v, int src) {
+  return __shfl_sync(mask, v, src);
+}
+__device__ __forceinline__ ff shfl_ct(unsigned mask, ff v, int src) {
+  return ff(__shfl_sync(mask, v.hi, src), __shfl_sync(mask, v.lo, src));
+}
+
+// Register r[a] for a lane-dependent species index a (a select per species:
+// a runtime index into a register array would put it in local memory).
+template <int M, typename CT>
+__device__ __forceinline__ CT pick(const CT (&r)[M], int a) {
+  CT v = r[0];
+#pragma unroll
+  for (int b = 1; b < M; ++b)
+    if (b == a) v = r[b];
+  return v;
+}
+
+// Temperature Newton on Eq. temperature for a lane group (the formulas of
+// newton_T / newton_T_ff): lane `sub` sums the mixture energy polynomial's
+// coefficients over the species a = sub, sub + L, ..., the group adds them
+// with a butterfly (every lane ends with the same sums, so every lane takes
+// the same iterates), and every lane iterates.
+template <int M, int L, typename CT>
+__device__ __forceinline__ CT group_newton(const DevMech& m, const CT (&r)[M], CT irho, CT U,
+                                           CT T, const Units& un, int sub, unsigned gmask,
+                                           bool& ok) {
+  using X = Chem<CT>;
+  CT c[4] = {CT(), CT(), CT(), CT()};
+#pragma unroll
+  for (int j = 0; j < (M + L - 1) / L; ++j) {
+    const int a = sub + j * L;
+    if (a < M) {
+      const CT Ya = pick<M, CT>(r, a) * irho;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) c[k] += Ya * X::ucoef(m, k, a);
+    }
+  }
+#pragma unroll
+  for (int o = 1; o < L; o <<= 1)
+#pragma unroll
+    for (int k = 0; k < 4; ++k) c[k] += shfl_xor_ct(gmask, c[k], o);
+  const CT two = X::of(2.f), three = X::of(3.f);
+  ok = false;
+  for (int it = 0; it < un.newton_max_iter; ++it) {
+    const CT F = c[0] + T * (c[1] + T * (c[2] + T * c[3])) - U;
+    const CT dF = c[1] + T * (two * c[2] + three * T * c[3]);
+    const CT dT = -(F / dF);
+    T += dT;
+    if (X::mag(dT) <= X::rtol(un) * X::mag(T)) { ok = true; break; }
+  }
+  return T;
+}
 
 // Reaction sub-steps of node n by a group of L lanes (L = 4 or 8, aligned
 // within the warp): every lane forms the node's state, temperature,
@@ -436,21 +500,30 @@ __device__ __forceinline__ void chem_lanes_body(RT* __restrict__ rec,
     r[a] = r0[a];
   }
   r[M - 1] = X::of(last);
-  const CT rho_c = X::of(rho);
+  const CT irho = X::inv(X::of(rho));
+  const int base = (int)(threadIdx.x & 31) - sub;      // the group's first lane
   CT Ts = X::of_T(Tf[n]);
   for (int s = 0; s < un.substeps; ++s) {
     if (s > 0) {
       bool ok;
-      Ts = X::template newton<M>(m, r, rho_c, U, Ts, un, ok);
+      Ts = group_newton<M, L, CT>(m, r, irho, U, Ts, un, sub, gmask, ok);
       if (!ok && sub == 0) atomicOr(status, ST_NEWTON);
     }
     const CT lnT = X::ln(Ts);
     const CT invT = X::inv(Ts);
+    // Gibbs functions: lane `sub` evaluates species sub, sub + L, ...; the
+    // group exchanges them with shuffles
+    CT Gown[(M + L - 1) / L];
+#pragma unroll
+    for (int j = 0; j < (M + L - 1) / L; ++j) {
+      const int a = sub + j * L;
+      Gown[j] = a < M ? X::gibbs(m, a, Ts, invT, lnT) : CT();
+    }
     CT C[M], G[M], w[M];
 #pragma unroll
     for (int a = 0; a < M; ++a) {
       C[a] = r[a] * X::inv_mm(m, a);
-      G[a] = X::gibbs(m, a, Ts, invT, lnT);
+      G[a] = shfl_ct(gmask, Gown[a / L], base + a % L);
       w[a] = CT();
     }
     const CT lp = X::ln_p0(m) - lnT;   // ln(P0 / (R_U T))
@@ -1473,14 +1546,25 @@ k_moments(const S* __restrict__ src, RT* __restrict__ rec, double* __restrict__ 
   moments_body<D, M, S, RT>(src, rec, Tf, status, g, un, bc, mech, n, chem_inline);
 }
 
-// reaction sub-steps, L lanes per node, 128 threads per block
+// reaction sub-steps, L lanes per node, 128 threads per block.  Node sets:
+// every node, the nodes without boundary reconstruction (their chemistry
+// runs beside the boundary kernel on the side stream), or the interface
+// nodes (entry `first` of the interface list, after the boundary kernel)
 template <int D, int M, typename RT, int L>
 __device__ __forceinline__ void chem_entry(RT* rec, const double* Tf, int* status, long long N,
                                            const int* tag, const Units& un, const DevMech& m,
-                                           long long first_node) {
+                                           long long first, int node_set, const int* if_node,
+                                           int n_if) {
   const int lane = threadIdx.x & 31;
-  const long long n = first_node + threadIdx.x / L;
-  if (n >= N || (tag && tag[n] == TAG_SOLID)) return;   // the whole group leaves
+  const long long idx = first + threadIdx.x / L;
+  long long n = idx;
+  if (node_set == NODES_INTERFACE) {                    // the whole group leaves
+    if (idx >= n_if) return;
+    n = if_node[idx];
+  } else {
+    if (n >= N) return;
+    if (tag && (tag[n] == TAG_SOLID || (node_set == NODES_BULK && tag[n] >= 0))) return;
+  }
   const unsigned gmask = (L == 32 ? 0xffffffffu : ((1u << L) - 1u) << (lane & ~(L - 1)));
   chem_lanes_body<D, M, RT, L>(rec, Tf, status, N, tag, un, m, n, lane & (L - 1), gmask);
 }
@@ -1489,8 +1573,10 @@ template <int D, int M, typename RT, int L>
 __global__ void __launch_bounds__(128)
 k_chem(RT* __restrict__ rec, const double* __restrict__ Tf, int* __restrict__ status,
        long long N, const int* __restrict__ tag, const __grid_constant__ Units un,
-       const DevMech* __restrict__ mech) {
-  chem_entry<D, M, RT, L>(rec, Tf, status, N, tag, un, *mech, blockIdx.x * (128LL / L));
+       const DevMech* __restrict__ mech, int node_set, const int* __restrict__ if_node,
+       int n_if) {
+  chem_entry<D, M, RT, L>(rec, Tf, status, N, tag, un, *mech, blockIdx.x * (128LL / L), node_set,
+                          if_node, n_if);
 }
 
 template <int D, int M, typename S, typename RT>
@@ -1583,13 +1669,25 @@ k_moments_batch(const DomainDev* __restrict__ doms, int ndom, int parity, int ch
   }
 }
 
+// NODES_INTERFACE: the boundary grid (four interface nodes per block), the
+// first L lanes of warp w on the block's interface node w
 template <int D, int M, typename RT, int L>
 __global__ void __launch_bounds__(128)
-k_chem_batch(const DomainDev* __restrict__ doms, int ndom, int nblk) {
+k_chem_batch(const DomainDev* __restrict__ doms, int ndom, int node_set, int nblk) {
   for (int b = blockIdx.x; b < nblk; b += gridDim.x) {
-    const DomainDev& d = doms[domain_of_block(doms, ndom, b, GRID_CHEM)];
-    chem_entry<D, M, RT, L>(static_cast<RT*>(d.rec), d.Tf, d.status, d.g.N, d.bc.tag, d.un,
-                            *d.mech, (b - d.cblock_begin) * (128LL / L));
+    if (node_set == NODES_INTERFACE) {
+      const DomainDev& d = doms[domain_of_block(doms, ndom, b, GRID_BOUNDARY)];
+      const int lane = threadIdx.x & 31;
+      const int k = (b - d.bblock_begin) * 4 + threadIdx.x / 32;
+      if (lane >= L || k >= d.bc.n_if) continue;
+      chem_lanes_body<D, M, RT, L>(static_cast<RT*>(d.rec), d.Tf, d.status, d.g.N, d.bc.tag,
+                                   d.un, *d.mech, d.bc.if_node[k], lane, (1u << L) - 1u);
+    } else {
+      const DomainDev& d = doms[domain_of_block(doms, ndom, b, GRID_CHEM)];
+      chem_entry<D, M, RT, L>(static_cast<RT*>(d.rec), d.Tf, d.status, d.g.N, d.bc.tag, d.un,
+                              *d.mech, (b - d.cblock_begin) * (128LL / L), node_set, nullptr,
+                              0);
+    }
   }
 }
 
@@ -1860,13 +1958,20 @@ static cudaError_t prepare_impl() {
 }
 
 template <int D, int M, typename RT>
-static void launch_chem(const Launch& lc, unsigned nblk, cudaStream_t s, RT* rec,
-                        const double* Tf, int* status, long long N, const int* tag,
-                        const Units& un, const DevMech* mech) {
-  if (lc.chem_lanes == 4)
-    k_chem<D, M, RT, 4><<<nblk, 128, 0, s>>>(rec, Tf, status, N, tag, un, mech);
+static void launch_chem(const Launch& lc, cudaStream_t s, RT* rec, const double* Tf,
+                        int* status, long long N, const BCDev& bc, const Units& un,
+                        const DevMech* mech, int node_set) {
+  // the interface nodes are few and on the critical path: 8 lanes each
+  const int lanes = node_set == NODES_INTERFACE ? 8 : lc.chem_lanes;
+  const long long n = node_set == NODES_INTERFACE ? bc.n_if : N;
+  const unsigned nblk = blocks_for(n, 128 / lanes);
+  if (nblk == 0) return;
+  if (lanes == 4)
+    k_chem<D, M, RT, 4><<<nblk, 128, 0, s>>>(rec, Tf, status, N, bc.tag, un, mech, node_set,
+                                             bc.if_node, bc.n_if);
   else
-    k_chem<D, M, RT, 8><<<nblk, 128, 0, s>>>(rec, Tf, status, N, tag, un, mech);
+    k_chem<D, M, RT, 8><<<nblk, 128, 0, s>>>(rec, Tf, status, N, bc.tag, un, mech, node_set,
+                                             bc.if_node, bc.n_if);
 }
 
 // prepare_impl once per device and instantiation
@@ -1905,15 +2010,23 @@ static cudaError_t step_impl(const DevMech& mech, const StepArgs& a, cudaStream_
       if (e != cudaSuccess) return e;
       // with the reaction sub-steps in k_chem the boundary warps also write
       // their nodes' records; else the interface moments follow them
+      // and the interface nodes' reaction sub-steps after them; the bulk
+      // nodes' sub-steps follow the bulk moments on the main stream
       k_boundary<D, M, S><<<(a.bc.n_if + 3) / 4, 128, 0, a.side>>>(
           src, a.bc, a.Tfield, a.status, a.g, a.un, mech, chem_sep ? rec : nullptr);
       if (!chem_sep)
         k_moments<D, M, S, RT><<<blocks_for(a.bc.n_if, bs), bs, 0, a.side>>>(
             src, rec, a.Tfield, a.status, a.g, a.un, a.bc, mech, 1, NODES_INTERFACE);
+      else
+        launch_chem<D, M, RT>(lc, a.side, rec, a.Tfield, a.status, a.g.N, a.bc, a.un,
+                              a.mech_dev, NODES_INTERFACE);
       e = cudaEventRecord(a.ev_join, a.side);
       if (e != cudaSuccess) return e;
       k_moments<D, M, S, RT><<<nb, bs, 0, s>>>(src, rec, a.Tfield, a.status, a.g, a.un, a.bc,
                                                mech, !chem_sep, NODES_BULK);
+      if (chem_sep)
+        launch_chem<D, M, RT>(lc, s, rec, a.Tfield, a.status, a.g.N, a.bc, a.un, a.mech_dev,
+                              NODES_BULK);
       e = cudaStreamWaitEvent(s, a.ev_join, 0);
       if (e != cudaSuccess) return e;
     } else {
@@ -1924,11 +2037,10 @@ static cudaError_t step_impl(const DevMech& mech, const StepArgs& a, cudaStream_
       k_moments<D, M, S, RT><<<nb, bs, 0, s>>>(src, rec, a.Tfield, a.status, a.g, a.un, a.bc,
                                                mech, !chem_sep,
                                                bnd_rec ? NODES_BULK : NODES_ALL);
+      if (chem_sep)
+        launch_chem<D, M, RT>(lc, s, rec, a.Tfield, a.status, a.g.N, a.bc, a.un, a.mech_dev,
+                              NODES_ALL);
     }
-    if (chem_sep)
-      launch_chem<D, M, RT>(lc, blocks_for(a.g.N, 128 / lc.chem_lanes), s,
-                            reinterpret_cast<RT*>(a.rec), a.Tfield, a.status, a.g.N, a.bc.tag,
-                            a.un, a.mech_dev);
   }
   if (which != 0) {
     if (split) {
@@ -2002,23 +2114,38 @@ static cudaError_t batch_impl(const DomainDev* doms, int ndom, const BatchGrids&
   const bool ps = lc.persistent != 0;
   auto kmom = k_moments_batch<D, M, S, RT>;
   auto kbnd = k_boundary_batch<D, M, S>;
+  // the reaction sub-steps in k_chem over a node set (the grid of the set)
+  auto chem = [&](int node_set, cudaStream_t st) {
+    const int nb = node_set == NODES_INTERFACE ? gr.nbblocks : gr.ncblocks;
+    if (nb == 0) return;
+    // the interface nodes are few and on the critical path: 8 lanes each
+    if (lc.chem_lanes == 4 && node_set != NODES_INTERFACE) {
+      auto k = k_chem_batch<D, M, RT, 4>;
+      k<<<batch_grid(k, nb, 128, 0, ps), 128, 0, st>>>(doms, ndom, node_set, nb);
+    } else {
+      auto k = k_chem_batch<D, M, RT, 8>;
+      k<<<batch_grid(k, nb, 128, 0, ps), 128, 0, st>>>(doms, ndom, node_set, nb);
+    }
+  };
   if (gr.nbblocks > 0 && side.stream && side.fork && side.join) {
-    // boundary kernel and the interface nodes' moments on the side stream,
-    // concurrent with the bulk moments
+    // on the side stream, concurrent with the bulk moments: the boundary
+    // kernel, then the interface nodes' moments (reaction sub-steps inline)
+    // or, with the boundary warps writing the records, their sub-steps
     cudaError_t e = cudaEventRecord(side.fork, s);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(side.stream, side.fork, 0);
     if (e != cudaSuccess) return e;
-    // with the reaction sub-steps in k_chem the boundary warps also write
-    // their nodes' records; else the interface moments follow them
     kbnd<<<batch_grid(kbnd, gr.nbblocks, bs, 0, ps), bs, 0, side.stream>>>(
         doms, ndom, parity, !chem_inline, gr.nbblocks);
     if (chem_inline)
       kmom<<<batch_grid(kmom, gr.nbblocks, bs, 0, ps), bs, 0, side.stream>>>(
           doms, ndom, parity, chem_inline, NODES_INTERFACE, gr.nbblocks);
+    else
+      chem(NODES_INTERFACE, side.stream);
     e = cudaEventRecord(side.join, side.stream);
     if (e != cudaSuccess) return e;
     kmom<<<batch_grid(kmom, gr.nblocks, bs, 0, ps), bs, 0, s>>>(doms, ndom, parity, chem_inline,
                                                                 NODES_BULK, gr.nblocks);
+    if (!chem_inline) chem(NODES_BULK, s);
     e = cudaStreamWaitEvent(s, side.join, 0);
     if (e != cudaSuccess) return e;
   } else {
@@ -2028,13 +2155,7 @@ static cudaError_t batch_impl(const DomainDev* doms, int ndom, const BatchGrids&
                                                                    !chem_inline, gr.nbblocks);
     kmom<<<batch_grid(kmom, gr.nblocks, bs, 0, ps), bs, 0, s>>>(
         doms, ndom, parity, chem_inline, bnd_rec ? NODES_BULK : NODES_ALL, gr.nblocks);
-  }
-  if (lc.chem_lanes == 4) {
-    auto k = k_chem_batch<D, M, RT, 4>;
-    k<<<batch_grid(k, gr.ncblocks, 128, 0, ps), 128, 0, s>>>(doms, ndom, gr.ncblocks);
-  } else if (lc.chem_lanes == 8) {
-    auto k = k_chem_batch<D, M, RT, 8>;
-    k<<<batch_grid(k, gr.ncblocks, 128, 0, ps), 128, 0, s>>>(doms, ndom, gr.ncblocks);
+    if (!chem_inline) chem(NODES_ALL, s);
   }
   if (lc.coll_split) {
     auto kp = k_prep_batch<D, M, RT>;
