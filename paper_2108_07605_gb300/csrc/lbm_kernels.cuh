@@ -915,13 +915,21 @@ __device__ __forceinline__ RT axis_factor(int e, const RT* th, const RT* u, cons
 // finalNumericalEquationsReactive; Sec. 3.2 Eqs. f, g; Sec. 3.3 Eq. feqmix):
 // PS supplies the node's parameters (registers, or the block's shared memory
 // in the split placement).
+// The M + 1 populations of direction i entering node n's collision (pulled
+// from node sn, or the boundary-reconstructed ones).
+template <int D, int M, typename S, typename RT>
+__device__ __forceinline__ void load_direction(const S* __restrict__ src, const BCDev& bc,
+                                               int tag, long long N, long long sn, int i,
+                                               const float4* codec, RT (&fin)[M + 1]) {
+  constexpr int Q = Lat<D>::Q;
+#pragma unroll
+  for (int l = 0; l <= M; ++l) fin[l] = pop_in<RT>(src, bc, tag, N, sn, l * Q + i, codec);
+}
+
 template <int D, int M, typename S, typename RT, typename PS>
-__device__ __forceinline__ void collide_direction(const PS& ps, int i,
-                                                  const S* __restrict__ src,
-                                                  S* __restrict__ dst, const BCDev& bc,
-                                                  int tag, long long N, long long n,
-                                                  long long sn, const DevMech& mech,
-                                                  const float4* codec) {
+__device__ __forceinline__ void collide_direction(const PS& ps, int i, const RT (&fin)[M + 1],
+                                                  S* __restrict__ dst, long long N, long long n,
+                                                  const DevMech& mech, const float4* codec) {
   constexpr int Q = Lat<D>::Q;
   int c[3];
   c[0] = cvel(i, 0); c[1] = cvel(i, 1); c[2] = D == 3 ? cvel(i, 2) : 0;
@@ -934,7 +942,7 @@ __device__ __forceinline__ void collide_direction(const PS& ps, int i,
     for (int b = 0; b < M; ++b)
       if (b != a) F += kcoef<RT>(mech, a, b) * dd[b];
     const long long off = (long long)(a * Q + i) * N;
-    const RT f = pop_in<RT>(src, bc, tag, N, sn, a * Q + i, codec);
+    const RT f = fin[a];
     const RT fn = f + ps.tb(a) * (ps.rs(a) * pe[a] - f) + ps.cF(a) * F + ps.dr(a) * pe[a];
     dst[off + n] = Codec<S>::enc(fn, codec, a * Q + i);
   }
@@ -943,7 +951,7 @@ __device__ __forceinline__ void collide_direction(const PS& ps, int i,
 #pragma unroll
     for (int d = 0; d < D; ++d) fex *= psi1<RT>(c[d], ps.u(d), ps.Pex(d));
     const long long off = (long long)((M - 1) * Q + i) * N;
-    const RT f = pop_in<RT>(src, bc, tag, N, sn, (M - 1) * Q + i, codec);
+    const RT f = fin[M - 1];
     dst[off + n] = Codec<S>::enc(f + ps.om() * (fex - f), codec, (M - 1) * Q + i);
   }
   {
@@ -961,7 +969,7 @@ __device__ __forceinline__ void collide_direction(const PS& ps, int i,
     }
     geq *= ps.rho();
     const long long off = (long long)(M * Q + i) * N;
-    const RT gv = pop_in<RT>(src, bc, tag, N, sn, M * Q + i, codec);
+    const RT gv = fin[M];
     RT gn = gv + ps.om() * (geq - gv);
     if (csq(i, D) == 1) {
 #pragma unroll
@@ -1062,9 +1070,12 @@ __device__ __forceinline__ void collide_body(const S* __restrict__ src, S* __res
   }
   const RegPar<D, M, RT> ps(p, tab);
 #pragma unroll 1
-  for (int i = 0; i < Q; ++i)
-    collide_direction<D, M, S, RT>(ps, i, src, dst, bc, tag, N, n,
-                                   node_shift<D>(x, y, z, i, -1, g), mech, g.codec);
+  for (int i = 0; i < Q; ++i) {
+    RT fin[M + 1];
+    load_direction<D, M, S, RT>(src, bc, tag, N, node_shift<D>(x, y, z, i, -1, g), i, g.codec,
+                                fin);
+    collide_direction<D, M, S, RT>(ps, i, fin, dst, N, n, mech, g.codec);
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -1205,9 +1216,22 @@ __device__ __forceinline__ void coll_block(const S* __restrict__ src, S* __restr
   const int x = (int)(n % g.nx);
   const int y = (int)((n / g.nx) % g.ny);
   const int z = (int)(n / ((long long)g.nx * g.ny));
-  for (int i = w; i < Q; i += kCollTPN)
-    collide_direction<D, M, S, RT>(ps, i, src, dst, bc, tag, N, n,
-                                   node_shift<D>(x, y, z, i, -1, g), mech, g.codec);
+  // software pipeline: the next direction's populations are in flight while
+  // this one collides (each thread has Q / kCollTPN directions)
+  RT fa[M + 1], fb[M + 1];
+  if (w < Q)
+    load_direction<D, M, S, RT>(src, bc, tag, N, node_shift<D>(x, y, z, w, -1, g), w, g.codec,
+                                fa);
+#pragma unroll 1
+  for (int i = w; i < Q; i += kCollTPN) {
+    const int inext = i + kCollTPN;
+    if (inext < Q)
+      load_direction<D, M, S, RT>(src, bc, tag, N, node_shift<D>(x, y, z, inext, -1, g), inext,
+                                  g.codec, fb);
+    collide_direction<D, M, S, RT>(ps, i, fa, dst, N, n, mech, g.codec);
+#pragma unroll
+    for (int l = 0; l <= M; ++l) fa[l] = fb[l];
+  }
 }
 
 
@@ -1232,6 +1256,49 @@ __device__ __forceinline__ R warp_sum(R v) {
   return v;
 }
 
+// Sum over the species lanes 0..M-1 of a warp (the other lanes hold zero):
+// a butterfly over the lanes that can hold species, then lane 0's total to
+// every lane, so that every lane continues with the same value.
+template <int M, typename T>
+__device__ __forceinline__ T species_sum(T v) {
+#pragma unroll
+  for (int o = 1; o < (M > 16 ? 32 : 16); o <<= 1) v += shfl_xor_ct(0xffffffffu, v, o);
+  return shfl_ct(0xffffffffu, v, 0);
+}
+
+// theta_a, theta and U/c^2 of an equilibrium state (eq_prepare) by a warp:
+// lane a < M evaluates species a's energy, the warp sums.  m: the mechanism
+// for compile-time species indices; mp: the same at an address the lanes
+// may index by species.
+template <int D, int M, typename R>
+__device__ __forceinline__ void eq_prepare_warp(EqSet<D, M, R>& s, const DevMech& m,
+                                                const DevMech& mp, const Units& un, int lane) {
+  const bool own = lane < M;
+  const int a = own ? lane : 0;
+  if constexpr (sizeof(R) == 8) {
+    double Rm = 0.0;
+#pragma unroll
+    for (int b = 0; b < M; ++b) {
+      Rm += s.Y[b] * m.inv_mm[b];
+      s.th_a[b] = m.Ra[b] * s.T * un.inv_c2;
+    }
+    const double U = species_sum<M>(own ? s.Y[a] * species_U(mp, a, s.T) : 0.0);
+    s.th = R_U * Rm * s.T * un.inv_c2;
+    s.U = U * un.inv_c2;
+  } else {
+    float Rm = 0.f;
+    const ff T(s.T);
+#pragma unroll
+    for (int b = 0; b < M; ++b) {
+      Rm += s.Y[b] * m.inv_mm_s[b];
+      s.th_a[b] = m.Ra_s[b] * s.T * un.inv_c2_s;
+    }
+    const ff U = species_sum<M>(own ? ff(s.Y[a]) * species_U_ff(mp, a, T) : ff());
+    s.th = float(R_U) * Rm * s.T * un.inv_c2_s;
+    s.U = (U * un.inv_c2_f).hi;
+  }
+}
+
 // Warp-cooperative macroscopic state of a node: lane i < Q holds v[l], the
 // population of lattice l in direction i (lanes >= Q hold zeros).  rho, u,
 // Y, u_a (Eq. momentum1 with reading R5), T by Newton on Eq. temperature from
@@ -1241,8 +1308,9 @@ __device__ __forceinline__ R warp_sum(R v) {
 // copy keeps its instruction footprint small.
 template <int D, int M, typename R>
 __device__ __noinline__ void warp_state_of(const R (&v)[M + 1], EqSet<D, M, R>& s,
-                                           double T_guess, const DevMech& m, const Units& un,
-                                           int* status, int lane) {
+                                           double T_guess, const DevMech& m,
+                                           const DevMech& mp, const Units& un, int* status,
+                                           int lane) {
   constexpr int Q = Lat<D>::Q;
   const bool act = lane < Q;
   const int i = act ? lane : 0;
@@ -1283,23 +1351,65 @@ __device__ __noinline__ void warp_state_of(const R (&v)[M + 1], EqSet<D, M, R>& 
   R usq = R(0);
 #pragma unroll
   for (int d = 0; d < D; ++d) { s.u[d] = j[d] / rho; usq += s.u[d] * s.u[d]; }
+  // species a = lane: Y_a and u_a (reading R5), then shared by shuffles
+  const bool own = lane < M;
+  const int a = own ? lane : 0;
+  R ra = rs[0], ja[D];
 #pragma unroll
-  for (int a = 0; a < M; ++a) {
-    s.Y[a] = rs[a] / rho;
-    const bool tiny = species_velocity_undefined<D, R>(rs[a], js[a]);
+  for (int d = 0; d < D; ++d) ja[d] = js[0][d];
 #pragma unroll
-    for (int d = 0; d < D; ++d) s.us[a][d] = tiny ? s.u[d] : js[a][d] / rs[a];
+  for (int b = 1; b < M; ++b)
+    if (b == a) {
+      ra = rs[b];
+#pragma unroll
+      for (int d = 0; d < D; ++d) ja[d] = js[b][d];
+    }
+  const R Ya = own ? ra / rho : R(0);
+  const bool tiny = species_velocity_undefined<D, R>(ra, ja);
+  R usa[D];
+#pragma unroll
+  for (int d = 0; d < D; ++d) usa[d] = tiny ? s.u[d] : ja[d] / ra;
+#pragma unroll
+  for (int b = 0; b < M; ++b) {
+    s.Y[b] = __shfl_sync(0xffffffffu, Ya, b);
+#pragma unroll
+    for (int d = 0; d < D; ++d) s.us[b][d] = __shfl_sync(0xffffffffu, usa[d], b);
   }
-  bool ok;
+  // temperature: the mixture energy polynomial's coefficients summed over
+  // the species lanes, then the Newton iterates of newton_T / newton_T_ff
+  // (same formulas and stopping rule) on every lane
+  bool ok = false;
   if constexpr (sizeof(R) == 8) {
+    using X = Chem<double>;
     const double U = (rhoE / rho - 0.5 * usq) * un.c * un.c;
-    s.T = newton_T<M>(m, s.Y, U, T_guess, un.newton_max_iter, un.newton_rtol, ok);
+    double c[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) c[k] = species_sum<M>(own ? Ya * X::ucoef(mp, k, a) : 0.0);
+    double T = T_guess;
+    for (int it = 0; it < un.newton_max_iter; ++it) {
+      const double F = c[0] + T * (c[1] + T * (c[2] + T * c[3])) - U;
+      const double dF = c[1] + T * (2.0 * c[2] + 3.0 * T * c[3]);
+      const double dT = -F / dF;
+      T += dT;
+      if (fabs(dT) <= un.newton_rtol * fabs(T)) { ok = true; break; }
+    }
+    s.T = T;
   } else {
-    ff Yf[M];
-    for (int a = 0; a < M; ++a) Yf[a] = ff(s.Y[a]);
+    using X = Chem<ff>;
     const ff U = (ff(rhoE / rho) + ff(-0.5f * usq)) * un.c2_f;
-    s.T = newton_T_ff<M>(m, Yf, U, ff_from_double(T_guess), un.newton_max_iter,
-                         un.newton_rtol_f, ok).hi;
+    ff c[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) c[k] = species_sum<M>(own ? ff(Ya) * X::ucoef(mp, k, a) : ff());
+    const ff two(2.f), three(3.f);
+    ff T = ff_from_double(T_guess);
+    for (int it = 0; it < un.newton_max_iter; ++it) {
+      const ff F = c[0] + T * (c[1] + T * (c[2] + T * c[3])) - U;
+      const ff dF = c[1] + T * (two * c[2] + three * T * c[3]);
+      const ff dT = -(F / dF);
+      T += dT;
+      if (fabsf(dT.hi) <= un.newton_rtol_f * fabsf(T.hi)) { ok = true; break; }
+    }
+    s.T = T.hi;
   }
   if (!ok && lane == 0) atomicOr(status, ST_NEWTON);
 }
@@ -1311,8 +1421,8 @@ template <int D, int M, typename S, typename R>
 __device__ __forceinline__ void boundary_body(const S* __restrict__ src, const BCDev& bc,
                                               const double* Tf,
                                               int* __restrict__ status, const Geom& g,
-                                              const Units& un, const DevMech& mech, int k,
-                                              int lane) {
+                                              const Units& un, const DevMech& mech,
+                                              const DevMech& mp, int k, int lane) {
   constexpr int Q = Lat<D>::Q, L = M + 1;
   if (k >= bc.n_if) return;                                         // whole warp leaves
   const long long N = g.N;
@@ -1363,13 +1473,13 @@ __device__ __forceinline__ void boundary_body(const S* __restrict__ src, const B
     A.Y[M - 1] = R(1) - ysum;
     for (int d = 0; d < D; ++d) A.u[d] = R(0);     // u^tgt = u_a^tgt = 0
     A.T = R(bc.if_wallT[k]);
-    eq_prepare(A, mech, un);                         // step 2: target (Eqs. tgtf-tgtfa)
+    eq_prepare_warp(A, mech, mp, un, lane);                         // step 2: target (Eqs. tgtf-tgtfa)
   } else if (kind == BK_INLET) {
     A.rho = R(bc.rho_in);
     for (int a = 0; a < M; ++a) A.Y[a] = R(bc.Y_in[a]);
     for (int d = 0; d < D; ++d) A.u[d] = R(bc.if_uin[(long long)d * st + k]);
     A.T = R(bc.T_in);
-    eq_prepare(A, mech, un);                         // step 1 (Eqs. in_f-in_fa)
+    eq_prepare_warp(A, mech, mp, un, lane);                         // step 1 (Eqs. in_f-in_fa)
   } else {
     // LODI data from the stored state at x and x - n (Eq. convectiveBC)
     const int ax = (info >> 4) & 3;
@@ -1380,12 +1490,12 @@ __device__ __forceinline__ void boundary_body(const S* __restrict__ src, const B
     R v[L];
 #pragma unroll
     for (int l = 0; l < L; ++l) v[l] = act ? ld(l, i, n) : R(0);
-    warp_state_of<D, M, R>(v, s0, Tf[n], mech, un, status, lane);
+    warp_state_of<D, M, R>(v, s0, Tf[n], mech, mp, un, status, lane);
     // (the upstream node's Newton starts from this node's T guess: the bulk
     // moments kernel may be rewriting the upstream one concurrently)
 #pragma unroll
     for (int l = 0; l < L; ++l) v[l] = act ? ld(l, i, up) : R(0);
-    warp_state_of<D, M, R>(v, s1, Tf[n], mech, un, status, lane);
+    warp_state_of<D, M, R>(v, s1, Tf[n], mech, mp, un, status, lane);
     // LODI wave amplitudes (reading R13) in FP64 from the two states: a few
     // scalars per node
     double R0 = 0.0, R1 = 0.0, Cv = 0.0;
@@ -1422,7 +1532,7 @@ __device__ __forceinline__ void boundary_body(const S* __restrict__ src, const B
       Ro += Ya * mech.inv_mm[a];
     }
     A.T = R(p_o * un.c * un.c / (rho_o * R_U * Ro));
-    eq_prepare(A, mech, un);                         // step 1 (Eqs. out_f-out_fa)
+    eq_prepare_warp(A, mech, mp, un, lane);                         // step 1 (Eqs. out_f-out_fa)
   }
   // incoming links at A, then the local state (Eqs. locRho-locT and analogues)
   if (in_i) {
@@ -1434,10 +1544,10 @@ __device__ __forceinline__ void boundary_body(const S* __restrict__ src, const B
     R v[L];
 #pragma unroll
     for (int l = 0; l < L; ++l) v[l] = act ? R(P[(long long)(l * Q + i) * st]) : R(0);
-    warp_state_of<D, M, R>(v, loc, Tf[n], mech, un, status, lane);
+    warp_state_of<D, M, R>(v, loc, Tf[n], mech, mp, un, status, lane);
   }
   loc.own_species_u = kind == BK_TMS;             // TMS local species use u_a^loc
-  eq_prepare(loc, mech, un);
+  eq_prepare_warp(loc, mech, mp, un, lane);
   if (kind == BK_INLET && bc.inlet_simplified) {  // simplified inlet: the local equilibria
     __syncwarp();
     if (act) {
@@ -1451,7 +1561,7 @@ __device__ __forceinline__ void boundary_body(const S* __restrict__ src, const B
     for (int a = 0; a < M; ++a) B.Y[a] = loc.Y[a];
     for (int d = 0; d < D; ++d) B.u[d] = A.u[d];
     B.T = R(bc.T_in);
-    eq_prepare(B, mech, un);
+    eq_prepare_warp(B, mech, mp, un, lane);
   }
   const EqSet<D, M, R>& Bref = kind == BK_INLET ? B : A;
   __syncwarp();
@@ -1615,10 +1725,12 @@ __global__ void __launch_bounds__(128)
 k_boundary(const S* __restrict__ src, const __grid_constant__ BCDev bc,
            double* __restrict__ Tf, int* __restrict__ status,
            const __grid_constant__ Geom g, const __grid_constant__ Units un,
-           const __grid_constant__ DevMech mech, typename ComputeType<S>::type* rec) {
+           const __grid_constant__ DevMech mech, typename ComputeType<S>::type* rec,
+           const DevMech* __restrict__ mech_g) {
   using R = typename ComputeType<S>::type;
   const int k = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32, lane = threadIdx.x & 31;
-  boundary_body<D, M, S, R>(src, bc, Tf, status, g, un, mech, k, lane);
+  // species-indexed reads by lane from the global copy where there is one
+  boundary_body<D, M, S, R>(src, bc, Tf, status, g, un, mech, mech_g ? *mech_g : mech, k, lane);
   if (rec) boundary_record<D, M, R>(bc, rec, Tf, status, g, un, mech, k, lane);
 }
 
@@ -1742,7 +1854,7 @@ k_boundary_batch(const DomainDev* __restrict__ doms, int ndom, int parity, int w
     const int c = d.cur0 ^ parity;
     const int k = (b - d.bblock_begin) * 4 + threadIdx.x / 32, lane = threadIdx.x & 31;
     boundary_body<D, M, S, R>(static_cast<const S*>(d.pops[c]), d.bc, d.Tf, d.status, d.g,
-                              d.un, *d.mech, k, lane);
+                              d.un, *d.mech, *d.mech, k, lane);
     if (with_rec)
       boundary_record<D, M, R>(d.bc, static_cast<R*>(d.rec), d.Tf, d.status, d.g, d.un,
                                *d.mech, k, lane);
@@ -2013,7 +2125,7 @@ static cudaError_t step_impl(const DevMech& mech, const StepArgs& a, cudaStream_
       // and the interface nodes' reaction sub-steps after them; the bulk
       // nodes' sub-steps follow the bulk moments on the main stream
       k_boundary<D, M, S><<<(a.bc.n_if + 3) / 4, 128, 0, a.side>>>(
-          src, a.bc, a.Tfield, a.status, a.g, a.un, mech, chem_sep ? rec : nullptr);
+          src, a.bc, a.Tfield, a.status, a.g, a.un, mech, chem_sep ? rec : nullptr, a.mech_dev);
       if (!chem_sep)
         k_moments<D, M, S, RT><<<blocks_for(a.bc.n_if, bs), bs, 0, a.side>>>(
             src, rec, a.Tfield, a.status, a.g, a.un, a.bc, mech, 1, NODES_INTERFACE);
@@ -2033,7 +2145,8 @@ static cudaError_t step_impl(const DevMech& mech, const StepArgs& a, cudaStream_
       const bool bnd_rec = a.bc.n_if > 0 && chem_sep;
       if (a.bc.n_if > 0)
         k_boundary<D, M, S><<<(a.bc.n_if + 3) / 4, 128, 0, s>>>(
-            src, a.bc, a.Tfield, a.status, a.g, a.un, mech, bnd_rec ? rec : nullptr);
+            src, a.bc, a.Tfield, a.status, a.g, a.un, mech, bnd_rec ? rec : nullptr,
+            a.mech_dev);
       k_moments<D, M, S, RT><<<nb, bs, 0, s>>>(src, rec, a.Tfield, a.status, a.g, a.un, a.bc,
                                                mech, !chem_sep,
                                                bnd_rec ? NODES_BULK : NODES_ALL);
