@@ -41,6 +41,9 @@ CLOCK_QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.ac
                "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
                "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 FP64_PEAK_TFLOPS = 1.25     # nominal FP64 rate of GB300 (152 SMs), per the pool's recipe
+# FP32 rate from the unit counts and the clock: 152 SMs x 128 FP32 lanes x 2
+# FLOP per FMA x 2.07 GHz (the maximum SM clock)
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 
 
 def parse():
@@ -170,31 +173,20 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def traffic_per_node(kernel, workload, precision):
-    """DRAM bytes per node from the committed ncu summary, or None."""
-    path = os.path.join(ROOT, "profiles", "dram_traffic.txt")
+def group_counters(group, workload, precision):
+    """Per-node counters of a launch group from the committed ncu summary
+    (profiles/group_counters.txt): {"fp32_flop", "fp64_flop", "dram_bytes"},
+    or None when the summary has no line for it."""
+    path = os.path.join(ROOT, "profiles", "group_counters.txt")
     if not os.path.exists(path):
         return None
     for line in open(path):
         if line.startswith("#") or not line.strip():
             continue
-        k, w, p, b = line.split()[:4]
-        if (k, w, p) == (kernel, workload, precision):
-            return float(b)
-    return None
-
-
-def flops_per_node(kernel, workload, precision):
-    """FP64 FLOPs per node of `kernel`, from the committed ncu summary."""
-    path = os.path.join(ROOT, "profiles", "fp64_flops.txt")
-    if not os.path.exists(path):
-        return None
-    for line in open(path):
-        if line.startswith("#") or not line.strip():
-            continue
-        k, w, p, f = line.split()[:4]
-        if (k, w, p) == (kernel, workload, precision):
-            return float(f)
+        f = line.split()
+        if tuple(f[:3]) == (group, workload, precision):
+            return {"fp32_flop": float(f[3]), "fp64_flop": float(f[4]),
+                    "dram_bytes": float(f[5])}
     return None
 
 
@@ -329,38 +321,48 @@ def main():
         pg.barrier()
     ms_per_step = total_ms / args.steps
     node_steps = N * args.steps * world
-    # kernels per step: moments, chemistry (its own kernel when
-    # chem_lanes > 1), collision (one kernel, or two when split); with
-    # interface nodes also the boundary kernel and, after it on the side
-    # stream, the interface nodes' moments (sub-steps inline) or chemistry
+    # kernels per step: the moments with the reaction sub-steps (k_moments,
+    # one thread per node, or k_mchem, chem_lanes lanes per node), the
+    # collision (one kernel, or two when split); with interface nodes also
+    # the boundary kernel and, after it on the side stream, the interface
+    # nodes' moments (k_moments) or sub-steps (k_chem)
     has_bnd = boundary_spec(w) is not None
-    launches_per_step = 2 + (2 if has_bnd else 0) + \
-        (1 if launch["chem_lanes"] > 1 else 0) + (1 if launch["collide_split"] else 0)
+    lanes = launch["chem_lanes"] > 1
+    launches_per_step = 1 + (2 if has_bnd else 0) + (2 if launch["collide_split"] else 1)
     value = node_updates_per_s(N, args.steps, world, M, total_ms * 1e-3)
 
-    # roofline of the dominant kernel
-    names = ["k_moments+k_chem" if launch["chem_lanes"] > 1 else "k_moments",
+    # roofline of the dominant launch group.  Both paths are bound by
+    # arithmetic, not by HBM: a node-step executes ~60k FP32 FLOP (mixed
+    # path, float-float chemistry and Newton) or ~17k FP64 FLOP for ~2.2 /
+    # 4.3 kB of populations, far above the machine balance (80.6 TFLOP/s FP32
+    # or 1.25 FP64 against ~6.7 TB/s).  The ALU roof is the bound; the HBM
+    # figures of the same group are reported beside it.
+    group0 = (["k_boundary", "k_chem" if lanes else "k_moments"] if has_bnd else []) + \
+        ["k_mchem" if lanes else "k_moments"]
+    names = ["+".join(dict.fromkeys(group0)),
              "k_prep+k_coll" if launch["collide_split"] else "k_collide"]
     dom = int(np.argmax(kms))
     dom_ms = kms[dom] / args.steps
     alg_bytes = 2 * info.L * info.Q * info.bytes_per_population   # per node-step
-    if args.precision == "fp64":
-        fl = flops_per_node(names[dom], args.workload, args.precision)
-        achieved = fl * N / (dom_ms * 1e-3) / 1e12 if fl else None
-        roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
-                "unit": "TFLOP/s", "frac": (achieved / FP64_PEAK_TFLOPS) if achieved else None,
-                "traffic": None, "kernel": names[dom],
-                "peak_source": "nominal FP64 1.25 TFLOP/s (recipe); FMA probe measured 1.25"}
-    else:
-        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) \
-            if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
-        peak = peaks.get("hbm_gbs", 6800.0)
-        achieved = alg_bytes * N / (dom_ms * 1e-3) / 1e9
-        roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": None, "kernel": names[dom],
-                "peak_source": "MEASURED_PEAKS.json hbm_gbs" if peaks else "fallback"}
-    tpn = traffic_per_node(names[dom], args.workload, args.precision)
-    roof["traffic"] = tpn * N if tpn else None
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) \
+        if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    hbm_gbs = alg_bytes * N / (dom_ms * 1e-3) / 1e9
+    cnt = group_counters(names[dom], args.workload, args.precision)
+    key = "fp64_flop" if args.precision == "fp64" else "fp32_flop"
+    peak = FP64_PEAK_TFLOPS if args.precision == "fp64" else FP32_PEAK_TFLOPS
+    achieved = cnt[key] * N / (dom_ms * 1e-3) / 1e12 if cnt else None
+    roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak if achieved else None,
+            "traffic": cnt["dram_bytes"] * N if cnt else None, "kernel": names[dom],
+            "flop_per_node": cnt[key] if cnt else None,
+            "peak_source": ("nominal FP64 1.25 TFLOP/s (recipe); FMA probe measured 1.25"
+                            if args.precision == "fp64" else
+                            "FP32: 152 SMs x 128 lanes x 2 FLOP x 2.07 GHz (unit counts, "
+                            "maximum clock)"),
+            "hbm": {"achieved": hbm_gbs, "peak": hbm_peak, "unit": "GB/s",
+                    "frac": hbm_gbs / hbm_peak, "alg_bytes_per_node": alg_bytes,
+                    "peak_source": "MEASURED_PEAKS.json hbm_gbs" if peaks else "fallback"}}
 
     # end to end through the C ABI with host buffers
     e2e = None

@@ -293,6 +293,7 @@ template <int D, int M, typename R = double> struct EqSet {
   R Y[M], th_a[M], u[D];
   R us[M][D];   // species velocities, used when own_species_u
   bool own_species_u;
+  double T_full;  // T of a solved state to the solve's precision (float-float in FP32)
 };
 
 // theta_a, theta and U/c^2 of the state.  FP32 (mixed path): the

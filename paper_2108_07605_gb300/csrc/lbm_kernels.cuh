@@ -462,47 +462,17 @@ __device__ __forceinline__ CT group_newton(const DevMech& m, const CT (&r)[M], C
   return T;
 }
 
-// Reaction sub-steps of node n by a group of L lanes (L = 4 or 8, aligned
-// within the warp): every lane forms the node's state, temperature,
-// concentrations and Gibbs functions; lane `sub` takes the reactions
-// k = sub, sub + L, ...; the species production rates are summed across the
-// group with shuffles, after which every lane holds the same densities.
-template <int D, int M, typename RT, int L>
-__device__ __forceinline__ void chem_lanes_body(RT* __restrict__ rec,
-                                                const double* __restrict__ Tf,
-                                                int* __restrict__ status, long long N,
-                                                const int* __restrict__ tag, const Units& un,
-                                                const DevMech& m, long long n, int sub,
-                                                unsigned gmask) {
-  using CT = typename ChemType<RT>::type;
+// The reaction sub-steps of one node by its lane group (Sec. 2.4 Eq. R3),
+// from the post-stream species densities r (replaced by the densities after
+// the sub-steps), 1/rho, the internal energy U and the temperature T_0 of
+// the moments.
+template <int M, typename CT, int L>
+__device__ __forceinline__ void chem_group_substeps(CT (&r)[M], const CT irho, const CT U,
+                                                    CT Ts, const Units& un, const DevMech& m,
+                                                    int sub, unsigned gmask,
+                                                    int* __restrict__ status) {
   using X = Chem<CT>;
-  using RC = Rec<D, M>;
-  const RT rho = rec[RC::RHO * N + n];
-  RT usq = RT(0);
-#pragma unroll
-  for (int d = 0; d < D; ++d) {
-    const RT ud = rec[(RC::U + d) * N + n];
-    usq += ud * ud;
-  }
-  const RT ER = rec[RC::E * N + n];
-  CT U;
-  if constexpr (sizeof(RT) == 4) U = (ff(ER) + ff(-0.5f * usq)) * un.c2_f;
-  else U = (double(ER) - 0.5 * double(usq)) * un.c * un.c;
-  // the post-stream species densities the moments kernel left in the
-  // increment slots; the slaved species from the mixture density
-  CT r[M], r0[M - 1];
-  RT last = rho;
-#pragma unroll
-  for (int a = 0; a < M - 1; ++a) {
-    const RT v = rec[(RC::DRHO + a) * N + n];
-    last -= v;
-    r0[a] = X::of(v);
-    r[a] = r0[a];
-  }
-  r[M - 1] = X::of(last);
-  const CT irho = X::inv(X::of(rho));
   const int base = (int)(threadIdx.x & 31) - sub;      // the group's first lane
-  CT Ts = X::of_T(Tf[n]);
   for (int s = 0; s < un.substeps; ++s) {
     if (s > 0) {
       bool ok;
@@ -558,11 +528,212 @@ __device__ __forceinline__ void chem_lanes_body(RT* __restrict__ rec,
 #pragma unroll
     for (int a = 0; a < M; ++a) r[a] += X::dt_sub(un) * (w[a] * X::mm(m, a));
   }
+}
+
+// Reaction sub-steps of node n by a group of L lanes (L = 4 or 8, aligned
+// within the warp): every lane forms the node's state, temperature,
+// concentrations and Gibbs functions; lane `sub` takes the reactions
+// k = sub, sub + L, ...; the species production rates are summed across the
+// group with shuffles, after which every lane holds the same densities.
+template <int D, int M, typename RT, int L>
+__device__ __forceinline__ void chem_lanes_body(RT* __restrict__ rec,
+                                                const double* __restrict__ Tf,
+                                                int* __restrict__ status, long long N,
+                                                const int* __restrict__ tag, const Units& un,
+                                                const DevMech& m, long long n, int sub,
+                                                unsigned gmask) {
+  using CT = typename ChemType<RT>::type;
+  using X = Chem<CT>;
+  using RC = Rec<D, M>;
+  const RT rho = rec[RC::RHO * N + n];
+  RT usq = RT(0);
+#pragma unroll
+  for (int d = 0; d < D; ++d) {
+    const RT ud = rec[(RC::U + d) * N + n];
+    usq += ud * ud;
+  }
+  const RT ER = rec[RC::E * N + n];
+  CT U;
+  if constexpr (sizeof(RT) == 4) U = (ff(ER) + ff(-0.5f * usq)) * un.c2_f;
+  else U = (double(ER) - 0.5 * double(usq)) * un.c * un.c;
+  // the post-stream species densities the moments kernel left in the
+  // increment slots; the slaved species from the mixture density
+  CT r[M], r0[M - 1];
+  RT last = rho;
+#pragma unroll
+  for (int a = 0; a < M - 1; ++a) {
+    const RT v = rec[(RC::DRHO + a) * N + n];
+    last -= v;
+    r0[a] = X::of(v);
+    r[a] = r0[a];
+  }
+  r[M - 1] = X::of(last);
+  chem_group_substeps<M, CT, L>(r, X::inv(X::of(rho)), U, X::of_T(Tf[n]), un, m, sub, gmask,
+                                status);
 #pragma unroll
   for (int a = 0; a < M - 1; ++a) {
     if (a % L != sub) continue;
     if constexpr (sizeof(RT) == 4) rec[(RC::DRHO + a) * N + n] = (r[a] - r0[a]).hi;
     else rec[(RC::DRHO + a) * N + n] = RT(r[a] - r0[a]);
+  }
+}
+
+// Moments and reaction sub-steps of node n by a group of L lanes (grids too
+// small to fill the GPU at one thread per node; chem_lanes = L).  Lane `sub`
+// pulls the directions sub, sub + L, ... of every lattice, the group adds the
+// partial sums with a butterfly, every lane forms the node's fields (the
+// formulas of moments_finish), the temperature solve is shared as in
+// group_newton, the lanes split the record's stores, and the group runs the
+// sub-steps from the post-stream densities (chem_group_substeps).  m: the
+// mechanism for compile-time indices; mg: its global copy, indexed by lane.
+template <int D, int M, typename S, typename RT, int L>
+__device__ __forceinline__ void mchem_body(const S* __restrict__ src, RT* __restrict__ rec,
+                                           double* __restrict__ Tf, int* __restrict__ status,
+                                           const Geom& g, const Units& un, const BCDev& bc,
+                                           const DevMech& m, const DevMech& mg, long long n,
+                                           int tag, int sub, unsigned gmask) {
+  constexpr int Q = Lat<D>::Q, NP = Lat<D>::NP;
+  using RC = Rec<D, M>;
+  using CT = typename ChemType<RT>::type;
+  using X = Chem<CT>;
+  const long long N = g.N;
+  const int x = (int)(n % g.nx);
+  const int y = (int)((n / g.nx) % g.ny);
+  const int z = (int)(n / ((long long)g.nx * g.ny));
+  RT rho = RT(0), rhoE = RT(0), j[D], q[D], P[NP], rs[M], js[M][D];
+#pragma unroll
+  for (int d = 0; d < D; ++d) { j[d] = RT(0); q[d] = RT(0); }
+#pragma unroll
+  for (int k = 0; k < NP; ++k) P[k] = RT(0);
+#pragma unroll
+  for (int a = 0; a < M; ++a) {
+    rs[a] = RT(0);
+#pragma unroll
+    for (int d = 0; d < D; ++d) js[a][d] = RT(0);
+  }
+#pragma unroll
+  for (int jd = 0; jd < (Q + L - 1) / L; ++jd) {
+    const int i = sub + jd * L;
+    if (i < Q) {
+      RT c[D];
+#pragma unroll
+      for (int d = 0; d < D; ++d) c[d] = RT(cvel(i, d));
+      const long long sn = node_shift<D>(x, y, z, i, -1, g);
+#pragma unroll
+      for (int a = 0; a < M - 1; ++a) {
+        const RT v = pop_in<RT>(src, bc, tag, N, sn, a * Q + i, g.codec);
+        rs[a] += v;
+#pragma unroll
+        for (int d = 0; d < D; ++d) js[a][d] += c[d] * v;
+      }
+      const RT f = pop_in<RT>(src, bc, tag, N, sn, (M - 1) * Q + i, g.codec);
+      rho += f;
+#pragma unroll
+      for (int d = 0; d < D; ++d) {
+        j[d] += c[d] * f;
+#pragma unroll
+        for (int e = d; e < D; ++e) P[pidx<D>(d, e)] += c[d] * c[e] * f;
+      }
+      const RT gv = pop_in<RT>(src, bc, tag, N, sn, M * Q + i, g.codec);
+      rhoE += gv;
+#pragma unroll
+      for (int d = 0; d < D; ++d) q[d] += c[d] * gv;
+    }
+  }
+#pragma unroll
+  for (int o = 1; o < L; o <<= 1) {
+    rho += __shfl_xor_sync(gmask, rho, o);
+    rhoE += __shfl_xor_sync(gmask, rhoE, o);
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+      j[d] += __shfl_xor_sync(gmask, j[d], o);
+      q[d] += __shfl_xor_sync(gmask, q[d], o);
+    }
+#pragma unroll
+    for (int k = 0; k < NP; ++k) P[k] += __shfl_xor_sync(gmask, P[k], o);
+#pragma unroll
+    for (int a = 0; a < M - 1; ++a) {
+      rs[a] += __shfl_xor_sync(gmask, rs[a], o);
+#pragma unroll
+      for (int d = 0; d < D; ++d) js[a][d] += __shfl_xor_sync(gmask, js[a][d], o);
+    }
+  }
+  // slaved species M (Eq. strongest)
+  rs[M - 1] = rho;
+#pragma unroll
+  for (int d = 0; d < D; ++d) js[M - 1][d] = j[d];
+#pragma unroll
+  for (int a = 0; a < M - 1; ++a) {
+    rs[M - 1] -= rs[a];
+#pragma unroll
+    for (int d = 0; d < D; ++d) js[M - 1][d] -= js[a][d];
+  }
+  const RT inv_rho = RT(1) / rho;
+  RT uR[D], YR[M], usqR = RT(0);
+#pragma unroll
+  for (int d = 0; d < D; ++d) { uR[d] = j[d] * inv_rho; usqR += uR[d] * uR[d]; }
+#pragma unroll
+  for (int a = 0; a < M; ++a) YR[a] = rs[a] * inv_rho;
+  const RT ER = rhoE * inv_rho;
+  // temperature (Eq. temperature) from the node's previous T, shared solve
+  CT U, r[M];
+  if constexpr (sizeof(RT) == 4) U = (ff(ER) + ff(-0.5f * usqR)) * un.c2_f;
+  else U = (double(ER) - 0.5 * double(usqR)) * un.c * un.c;
+#pragma unroll
+  for (int a = 0; a < M; ++a) r[a] = X::of(rs[a]);
+  const CT irho = X::inv(X::of(rho));
+  bool ok;
+  const CT Tx = group_newton<M, L, CT>(mg, r, irho, U, X::of_T(Tf[n]), un, sub, gmask, ok);
+  double T;
+  RT thR;
+  if constexpr (sizeof(RT) == 4) {
+    float Rm = 0.f;
+#pragma unroll
+    for (int a = 0; a < M; ++a) Rm += YR[a] * m.inv_mm_s[a];
+    T = ff_to_double(Tx);
+    thR = Rm * float(R_U) * Tx.hi * un.inv_c2_s;
+  } else {
+    double Rmix = 0.0;
+#pragma unroll
+    for (int a = 0; a < M; ++a) Rmix += double(YR[a]) * m.inv_mm[a];
+    T = Tx;
+    thR = RT(Rmix * R_U * T * un.inv_c2);
+  }
+  if (sub == 0) {
+    if (!ok) atomicOr(status, ST_NEWTON);
+    if (!(rho > RT(0)) || !isfinite(double(rho)) || !isfinite(T)) atomicOr(status, ST_NONFINITE);
+    Tf[n] = T;
+  }
+  // the record's fields, each stored by one lane of the group
+  auto put = [&](int f, RT v) {
+    if (f % L == sub) rec[(long long)f * N + n] = v;
+  };
+  put(RC::RHO, rho);
+#pragma unroll
+  for (int d = 0; d < D; ++d) {
+    put(RC::U + d, uR[d]);
+    put(RC::QF + d, q[d]);
+    put(RC::PHI + d, rho * uR[d] * (RT(1) - RT(3) * thR) - rho * uR[d] * uR[d] * uR[d]);
+  }
+#pragma unroll
+  for (int k = 0; k < NP; ++k) put(RC::P + k, P[k]);
+  put(RC::E, ER);
+#pragma unroll
+  for (int a = 0; a < M; ++a) {
+    put(RC::Y + a, YR[a]);
+    const bool tiny = species_velocity_undefined<D, RT>(rs[a], js[a]);
+#pragma unroll
+    for (int d = 0; d < D; ++d) put(RC::US + a * D + d, tiny ? uR[d] : js[a][d] / rs[a]);
+  }
+  // reaction sub-steps at frozen U (Sec. 2.4 Eq. R3), T_0 the T just solved
+  CT r0[M - 1];
+#pragma unroll
+  for (int a = 0; a < M - 1; ++a) r0[a] = r[a];
+  chem_group_substeps<M, CT, L>(r, irho, U, X::of_T(T), un, mg, sub, gmask, status);
+#pragma unroll
+  for (int a = 0; a < M - 1; ++a) {
+    if constexpr (sizeof(RT) == 4) put(RC::DRHO + a, (r[a] - r0[a]).hi);
+    else put(RC::DRHO + a, RT(r[a] - r0[a]));
   }
 }
 
@@ -1394,6 +1565,7 @@ __device__ __noinline__ void warp_state_of(const R (&v)[M + 1], EqSet<D, M, R>& 
       if (fabs(dT) <= un.newton_rtol * fabs(T)) { ok = true; break; }
     }
     s.T = T;
+    s.T_full = T;
   } else {
     using X = Chem<ff>;
     const ff U = (ff(rhoE / rho) + ff(-0.5f * usq)) * un.c2_f;
@@ -1410,6 +1582,7 @@ __device__ __noinline__ void warp_state_of(const R (&v)[M + 1], EqSet<D, M, R>& 
       if (fabsf(dT.hi) <= un.newton_rtol_f * fabsf(T.hi)) { ok = true; break; }
     }
     s.T = T.hi;
+    s.T_full = ff_to_double(T);
   }
   if (!ok && lane == 0) atomicOr(status, ST_NEWTON);
 }
@@ -1583,52 +1756,74 @@ template <int D, int M, typename R>
 __device__ __forceinline__ void boundary_record(const BCDev& bc, R* __restrict__ rec,
                                                 double* __restrict__ Tf,
                                                 int* __restrict__ status, const Geom& g,
-                                                const Units& un, const DevMech& mech, int k,
-                                                int lane) {
-  constexpr int Q = Lat<D>::Q, NP = Lat<D>::NP;
+                                                const Units& un, const DevMech& mech,
+                                                const DevMech& mp, int k, int lane) {
+  constexpr int Q = Lat<D>::Q, NP = Lat<D>::NP, L = M + 1;
+  using RC = Rec<D, M>;
   if (k >= bc.n_if) return;                                         // whole warp leaves
   __syncwarp();
+  const long long N = g.N;
   const long long n = bc.if_node[k];
   const double* P = bc.pops + k;
   const long long st = bc.n_if;
   const bool act = lane < Q;
   const int i = act ? lane : 0;
+  // rho, u, Y, u_a and T (Newton from the node's previous T) by the shared
+  // warp routine; the energy flux and the momentum flux tensor beside it
+  R v[L];
+#pragma unroll
+  for (int l = 0; l < L; ++l) v[l] = act ? R(P[(long long)(l * Q + i) * st]) : R(0);
+  EqSet<D, M, R> s;
+  s.own_species_u = false;
+  warp_state_of<D, M, R>(v, s, Tf[n], mech, mp, un, status, lane);
   R c[D];
 #pragma unroll
   for (int d = 0; d < D; ++d) c[d] = act ? R(cvel(i, d)) : R(0);
-  R rho, rhoE, j[D], q[D], Pt[NP], rs[M], js[M][D];
-#pragma unroll
-  for (int l = 0; l < M - 1; ++l) {
-    rs[l] = act ? R(P[(long long)(l * Q + i) * st]) : R(0);
-#pragma unroll
-    for (int d = 0; d < D; ++d) js[l][d] = c[d] * rs[l];
-  }
-  rho = act ? R(P[(long long)((M - 1) * Q + i) * st]) : R(0);
-  rhoE = act ? R(P[(long long)(M * Q + i) * st]) : R(0);
+  R rhoE = v[M], q[D], Pt[NP];
 #pragma unroll
   for (int d = 0; d < D; ++d) {
-    j[d] = c[d] * rho;
-    q[d] = c[d] * rhoE;
+    q[d] = warp_sum(c[d] * v[M]);
 #pragma unroll
-    for (int e = d; e < D; ++e) Pt[pidx<D>(d, e)] = c[d] * c[e] * rho;
+    for (int e = d; e < D; ++e) Pt[pidx<D>(d, e)] = warp_sum(c[d] * c[e] * v[M - 1]);
   }
-  rho = warp_sum(rho);
   rhoE = warp_sum(rhoE);
+  if (lane != 0) return;
+  // the record as the moments kernel writes it (moments_finish), the
+  // reaction sub-steps left to k_chem
+  const R rho = s.rho;
+  if (!(rho > R(0)) || !isfinite(double(rho)) || !isfinite(s.T_full))
+    atomicOr(status, ST_NONFINITE);
+  Tf[n] = s.T_full;
+  R thR;
+  if constexpr (sizeof(R) == 4) {
+    float Rm = 0.f;
+#pragma unroll
+    for (int a = 0; a < M; ++a) Rm += s.Y[a] * mech.inv_mm_s[a];
+    thR = Rm * float(R_U) * s.T * un.inv_c2_s;
+  } else {
+    double Rmix = 0.0;
+#pragma unroll
+    for (int a = 0; a < M; ++a) Rmix += s.Y[a] * mech.inv_mm[a];
+    thR = R(Rmix * R_U * s.T * un.inv_c2);
+  }
+#pragma unroll
+  for (int a = 0; a < M - 1; ++a) rec[(RC::DRHO + a) * N + n] = s.Y[a] * rho;
+  rec[RC::RHO * N + n] = rho;
 #pragma unroll
   for (int d = 0; d < D; ++d) {
-    j[d] = warp_sum(j[d]);
-    q[d] = warp_sum(q[d]);
+    rec[(RC::U + d) * N + n] = s.u[d];
+    rec[(RC::QF + d) * N + n] = q[d];
+    rec[(RC::PHI + d) * N + n] = rho * s.u[d] * (R(1) - R(3) * thR) - rho * s.u[d] * s.u[d] * s.u[d];
   }
 #pragma unroll
-  for (int p = 0; p < NP; ++p) Pt[p] = warp_sum(Pt[p]);
+  for (int p = 0; p < NP; ++p) rec[(RC::P + p) * N + n] = Pt[p];
+  rec[RC::E * N + n] = rhoE * (R(1) / rho);
 #pragma unroll
-  for (int a = 0; a < M - 1; ++a) {
-    rs[a] = warp_sum(rs[a]);
+  for (int a = 0; a < M; ++a) {
+    rec[(RC::Y + a) * N + n] = s.Y[a];
 #pragma unroll
-    for (int d = 0; d < D; ++d) js[a][d] = warp_sum(js[a][d]);
+    for (int d = 0; d < D; ++d) rec[(RC::US + a * D + d) * N + n] = s.us[a][d];
   }
-  if (lane == 0)
-    moments_finish<D, M, R>(rec, Tf, status, g.N, un, mech, n, 0, rho, rhoE, j, q, Pt, rs, js);
 }
 
 // ---------------------------------------------------------------------------
@@ -1689,6 +1884,25 @@ k_chem(RT* __restrict__ rec, const double* __restrict__ Tf, int* __restrict__ st
                           if_node, n_if);
 }
 
+// moments and reaction sub-steps, L lanes per node, 128 threads per block,
+// over every node or the nodes without boundary reconstruction
+template <int D, int M, typename S, typename RT, int L>
+__global__ void __launch_bounds__(128)
+k_mchem(const S* __restrict__ src, RT* __restrict__ rec, double* __restrict__ Tf,
+        int* __restrict__ status, const __grid_constant__ Geom g,
+        const __grid_constant__ Units un, const __grid_constant__ BCDev bc,
+        const __grid_constant__ DevMech mech, const DevMech* __restrict__ mech_g,
+        int node_set) {
+  const int lane = threadIdx.x & 31;
+  const long long n = blockIdx.x * (128LL / L) + threadIdx.x / L;
+  if (n >= g.N) return;                                  // the whole group leaves
+  const int tag = bc.tag ? bc.tag[n] : TAG_BULK;
+  if (tag == TAG_SOLID || (node_set == NODES_BULK && tag >= 0)) return;
+  const unsigned gmask = ((1u << L) - 1u) << (lane & ~(L - 1));
+  mchem_body<D, M, S, RT, L>(src, rec, Tf, status, g, un, bc, mech, *mech_g, n, tag,
+                             lane & (L - 1), gmask);
+}
+
 template <int D, int M, typename S, typename RT>
 __global__ void __launch_bounds__(128)
 k_collide(const S* __restrict__ src, S* __restrict__ dst, const RT* __restrict__ rec,
@@ -1731,7 +1945,9 @@ k_boundary(const S* __restrict__ src, const __grid_constant__ BCDev bc,
   const int k = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32, lane = threadIdx.x & 31;
   // species-indexed reads by lane from the global copy where there is one
   boundary_body<D, M, S, R>(src, bc, Tf, status, g, un, mech, mech_g ? *mech_g : mech, k, lane);
-  if (rec) boundary_record<D, M, R>(bc, rec, Tf, status, g, un, mech, k, lane);
+  if (rec)
+    boundary_record<D, M, R>(bc, rec, Tf, status, g, un, mech, mech_g ? *mech_g : mech, k,
+                             lane);
 }
 
 // ---------------------------------------------------------------------------
@@ -1803,6 +2019,26 @@ k_chem_batch(const DomainDev* __restrict__ doms, int ndom, int node_set, int nbl
   }
 }
 
+// the chemistry grid (128 / L nodes per block)
+template <int D, int M, typename S, typename RT, int L>
+__global__ void __launch_bounds__(128)
+k_mchem_batch(const DomainDev* __restrict__ doms, int ndom, int parity, int node_set,
+              int nblk) {
+  for (int b = blockIdx.x; b < nblk; b += gridDim.x) {
+    const DomainDev& d = doms[domain_of_block(doms, ndom, b, GRID_CHEM)];
+    const int c = d.cur0 ^ parity;
+    const int lane = threadIdx.x & 31;
+    const long long n = (b - d.cblock_begin) * (128LL / L) + threadIdx.x / L;
+    if (n >= d.g.N) continue;
+    const int tag = d.bc.tag ? d.bc.tag[n] : TAG_BULK;
+    if (tag == TAG_SOLID || (node_set == NODES_BULK && tag >= 0)) continue;
+    const unsigned gmask = ((1u << L) - 1u) << (lane & ~(L - 1));
+    mchem_body<D, M, S, RT, L>(static_cast<const S*>(d.pops[c]), static_cast<RT*>(d.rec), d.Tf,
+                               d.status, d.g, d.un, d.bc, *d.mech, *d.mech, n, tag,
+                               lane & (L - 1), gmask);
+  }
+}
+
 template <int D, int M, typename S, typename RT>
 __global__ void __launch_bounds__(128)
 k_collide_batch(const DomainDev* __restrict__ doms, int ndom, int parity, int nblk) {
@@ -1857,7 +2093,7 @@ k_boundary_batch(const DomainDev* __restrict__ doms, int ndom, int parity, int w
                               d.un, *d.mech, *d.mech, k, lane);
     if (with_rec)
       boundary_record<D, M, R>(d.bc, static_cast<R*>(d.rec), d.Tf, d.status, d.g, d.un,
-                               *d.mech, k, lane);
+                               *d.mech, *d.mech, k, lane);
   }
 }
 
@@ -2113,17 +2349,27 @@ static cudaError_t step_impl(const DevMech& mech, const StepArgs& a, cudaStream_
   if (which != 1) {
     const S* src = static_cast<const S*>(a.src);
     RT* rec = reinterpret_cast<RT*>(a.rec);
-    // the boundary kernel (a few warps, latency-bound) and the moments of
-    // the interface nodes run on the side stream while the bulk moments run
+    // chem_lanes > 1: the bulk nodes' moments and reaction sub-steps in one
+    // kernel with chem_lanes lanes per node (k_mchem); the boundary warps
+    // write their nodes' records and the interface nodes' sub-steps follow
+    // in k_chem.  chem_lanes = 1: k_moments with the sub-steps inline, the
+    // interface nodes' moments after the boundary kernel.
+    auto mchem = [&](cudaStream_t st, int node_set) {
+      const unsigned nbm = blocks_for(a.g.N, 128 / lc.chem_lanes);
+      if (lc.chem_lanes == 4)
+        k_mchem<D, M, S, RT, 4><<<nbm, 128, 0, st>>>(src, rec, a.Tfield, a.status, a.g, a.un,
+                                                     a.bc, mech, a.mech_dev, node_set);
+      else
+        k_mchem<D, M, S, RT, 8><<<nbm, 128, 0, st>>>(src, rec, a.Tfield, a.status, a.g, a.un,
+                                                     a.bc, mech, a.mech_dev, node_set);
+    };
+    // the boundary kernel (a few warps, latency-bound) and what follows it
+    // for the interface nodes run on a side stream beside the bulk work
     const bool fork = a.bc.n_if > 0 && a.side && a.ev_fork && a.ev_join;
     if (fork) {
       cudaError_t e = cudaEventRecord(a.ev_fork, s);
       if (e == cudaSuccess) e = cudaStreamWaitEvent(a.side, a.ev_fork, 0);
       if (e != cudaSuccess) return e;
-      // with the reaction sub-steps in k_chem the boundary warps also write
-      // their nodes' records; else the interface moments follow them
-      // and the interface nodes' reaction sub-steps after them; the bulk
-      // nodes' sub-steps follow the bulk moments on the main stream
       k_boundary<D, M, S><<<(a.bc.n_if + 3) / 4, 128, 0, a.side>>>(
           src, a.bc, a.Tfield, a.status, a.g, a.un, mech, chem_sep ? rec : nullptr, a.mech_dev);
       if (!chem_sep)
@@ -2134,11 +2380,11 @@ static cudaError_t step_impl(const DevMech& mech, const StepArgs& a, cudaStream_
                               a.mech_dev, NODES_INTERFACE);
       e = cudaEventRecord(a.ev_join, a.side);
       if (e != cudaSuccess) return e;
-      k_moments<D, M, S, RT><<<nb, bs, 0, s>>>(src, rec, a.Tfield, a.status, a.g, a.un, a.bc,
-                                               mech, !chem_sep, NODES_BULK);
       if (chem_sep)
-        launch_chem<D, M, RT>(lc, s, rec, a.Tfield, a.status, a.g.N, a.bc, a.un, a.mech_dev,
-                              NODES_BULK);
+        mchem(s, NODES_BULK);
+      else
+        k_moments<D, M, S, RT><<<nb, bs, 0, s>>>(src, rec, a.Tfield, a.status, a.g, a.un, a.bc,
+                                                 mech, 1, NODES_BULK);
       e = cudaStreamWaitEvent(s, a.ev_join, 0);
       if (e != cudaSuccess) return e;
     } else {
@@ -2147,12 +2393,15 @@ static cudaError_t step_impl(const DevMech& mech, const StepArgs& a, cudaStream_
         k_boundary<D, M, S><<<(a.bc.n_if + 3) / 4, 128, 0, s>>>(
             src, a.bc, a.Tfield, a.status, a.g, a.un, mech, bnd_rec ? rec : nullptr,
             a.mech_dev);
-      k_moments<D, M, S, RT><<<nb, bs, 0, s>>>(src, rec, a.Tfield, a.status, a.g, a.un, a.bc,
-                                               mech, !chem_sep,
-                                               bnd_rec ? NODES_BULK : NODES_ALL);
-      if (chem_sep)
-        launch_chem<D, M, RT>(lc, s, rec, a.Tfield, a.status, a.g.N, a.bc, a.un, a.mech_dev,
-                              NODES_ALL);
+      if (chem_sep) {
+        mchem(s, bnd_rec ? NODES_BULK : NODES_ALL);
+        if (bnd_rec)
+          launch_chem<D, M, RT>(lc, s, rec, a.Tfield, a.status, a.g.N, a.bc, a.un, a.mech_dev,
+                                NODES_INTERFACE);
+      } else {
+        k_moments<D, M, S, RT><<<nb, bs, 0, s>>>(src, rec, a.Tfield, a.status, a.g, a.un, a.bc,
+                                                 mech, 1, NODES_ALL);
+      }
     }
   }
   if (which != 0) {
@@ -2240,6 +2489,20 @@ static cudaError_t batch_impl(const DomainDev* doms, int ndom, const BatchGrids&
       k<<<batch_grid(k, nb, 128, 0, ps), 128, 0, st>>>(doms, ndom, node_set, nb);
     }
   };
+  // chem_lanes > 1: moments and sub-steps of the nodes in one kernel with
+  // chem_lanes lanes per node, on the chemistry grid
+  auto mchem = [&](int node_set) {
+    if (gr.ncblocks == 0) return;
+    if (lc.chem_lanes == 4) {
+      auto k = k_mchem_batch<D, M, S, RT, 4>;
+      k<<<batch_grid(k, gr.ncblocks, 128, 0, ps), 128, 0, s>>>(doms, ndom, parity, node_set,
+                                                               gr.ncblocks);
+    } else {
+      auto k = k_mchem_batch<D, M, S, RT, 8>;
+      k<<<batch_grid(k, gr.ncblocks, 128, 0, ps), 128, 0, s>>>(doms, ndom, parity, node_set,
+                                                               gr.ncblocks);
+    }
+  };
   if (gr.nbblocks > 0 && side.stream && side.fork && side.join) {
     // on the side stream, concurrent with the bulk moments: the boundary
     // kernel, then the interface nodes' moments (reaction sub-steps inline)
@@ -2256,9 +2519,11 @@ static cudaError_t batch_impl(const DomainDev* doms, int ndom, const BatchGrids&
       chem(NODES_INTERFACE, side.stream);
     e = cudaEventRecord(side.join, side.stream);
     if (e != cudaSuccess) return e;
-    kmom<<<batch_grid(kmom, gr.nblocks, bs, 0, ps), bs, 0, s>>>(doms, ndom, parity, chem_inline,
-                                                                NODES_BULK, gr.nblocks);
-    if (!chem_inline) chem(NODES_BULK, s);
+    if (chem_inline)
+      kmom<<<batch_grid(kmom, gr.nblocks, bs, 0, ps), bs, 0, s>>>(doms, ndom, parity, 1,
+                                                                  NODES_BULK, gr.nblocks);
+    else
+      mchem(NODES_BULK);
     e = cudaStreamWaitEvent(s, side.join, 0);
     if (e != cudaSuccess) return e;
   } else {
@@ -2266,9 +2531,13 @@ static cudaError_t batch_impl(const DomainDev* doms, int ndom, const BatchGrids&
     if (gr.nbblocks > 0)
       kbnd<<<batch_grid(kbnd, gr.nbblocks, bs, 0, ps), bs, 0, s>>>(doms, ndom, parity,
                                                                    !chem_inline, gr.nbblocks);
-    kmom<<<batch_grid(kmom, gr.nblocks, bs, 0, ps), bs, 0, s>>>(
-        doms, ndom, parity, chem_inline, bnd_rec ? NODES_BULK : NODES_ALL, gr.nblocks);
-    if (!chem_inline) chem(NODES_ALL, s);
+    if (chem_inline) {
+      kmom<<<batch_grid(kmom, gr.nblocks, bs, 0, ps), bs, 0, s>>>(doms, ndom, parity, 1,
+                                                                  NODES_ALL, gr.nblocks);
+    } else {
+      mchem(bnd_rec ? NODES_BULK : NODES_ALL);
+      if (bnd_rec) chem(NODES_INTERFACE, s);
+    }
   }
   if (lc.coll_split) {
     auto kp = k_prep_batch<D, M, RT>;
