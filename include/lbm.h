@@ -329,6 +329,20 @@ lbm_status lbm_get_info(lbm_t h, lbm_info* info);
 /* Release the handle and its device memory.  Returns the sticky status. */
 lbm_status lbm_destroy(lbm_t h);
 
+/* Test hook with no counterpart in the paper: the library's float-float exp
+ * and log (the functions of the mixed-precision path's Arrhenius rates and
+ * temperature) evaluated on the current device at the host values x[0..n),
+ * each first split into float-float (hi = x rounded to FP32, lo = x - hi
+ * rounded to FP32).  exp_out and log_out (host, n doubles each) receive
+ * hi + lo of the results; log of a value whose hi is not positive is NaN.
+ * exp returns +inf above 88.7 and 0 below -103; results below 2^-102 keep
+ * only the spacing of FP32's denormals in their low part (float-float has
+ * FP32's exponent range).  Allocates and frees its own
+ * device scratch; synchronous.  LBM_ERR_INVALID for NULL buffers or n < 0,
+ * LBM_ERR_RANGE for n > 2^24, LBM_ERR_CUDA on a device error (message in
+ * lbm_last_error(NULL)). */
+lbm_status lbm_ff_check(const double* x, long long n, double* exp_out, double* log_out);
+
 /* Allocation-free single step.  The paper has no counterpart: this entry
  * point exists for callers that cannot allocate device memory themselves -
  * a solver embedded in an application that owns every device allocation

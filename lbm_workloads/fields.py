@@ -131,9 +131,9 @@ def wall_ramp(x, nx, T_cold=300.0, T_hot=1500.0, frac=0.25):
 
 
 def channel_2d(seed=0, nx=2000, ny=40, phi=0.5, T_in=300.0, dx=25e-6, steps=50000,
-               mech=None):
+               mech=None, T_wall_hot=1500.0):
     """2-D microchannel: D2Q9 nx x ny, Tamm-Mott-Smith walls beyond y = 0 and
-    y = ny-1 carrying the wall_ramp temperature, parabolic inlet
+    y = ny-1 carrying the wall_ramp temperature (300 K to T_wall_hot), parabolic inlet
     u = u_max 4 s (1 - s) (s = (y + 1/2)/ny, u_max drawn from the seed in
     [0.2, 3] m/s) of fresh mixture at x = 0, pressure outlet at x = nx-1.
     Initial state: T = wall temperature of the column, fresh mixture, the
@@ -145,7 +145,7 @@ def channel_2d(seed=0, nx=2000, ny=40, phi=0.5, T_in=300.0, dx=25e-6, steps=5000
     x = np.arange(nx, dtype=float)
     s = (np.arange(ny) + 0.5) / ny
     prof = u_max * 4.0 * s * (1.0 - s)
-    Tw = wall_ramp(x, nx)
+    Tw = wall_ramp(x, nx, T_hot=T_wall_hot)
     w["T"] = np.broadcast_to(Tw[None, None, :], (1, ny, nx)).copy()
     w["u"][0] = np.broadcast_to(prof[None, :, None], (1, ny, nx))
     w.update(lattice="D2Q9", shape=(nx, ny, 1), dx=dx, T_max=3000.0, substeps=2,
@@ -223,13 +223,12 @@ def serving_mix(seed=0, n_requests=64, mean_interarrival=0.05, steps=(1000, 1000
             ny = int(rng.choice([20, 40]))
             # 12.5 um as for the reactors (the channel's own 25 um loses the
             # explicit sub-steps near the hot walls within 10k steps)
-            w = channel_2d(seed=seed * 1000 + k, nx=nx, ny=ny, phi=phi, dx=12.5e-6, mech=mech)
-            # cold start: the channel filled with the fresh mixture at the
-            # inlet temperature, the walls at their ramp.  (Started at the
-            # wall temperature the mixture autoignites within ~5k steps, and
-            # a reaction zone that reaches the outlet corner makes the LODI
-            # outlet fail within 10k steps in both precisions.)
-            w["T"] = np.full_like(w["T"], w["inlet"]["T"])
+            # walls ramping to 1000 K, below the chain-branching crossover of
+            # H2/air at 1 atm: with 1500 K walls the preheated mixture
+            # autoignites within ~5k steps and a reaction zone that reaches
+            # the outlet corner makes the LODI outlet fail (both precisions)
+            w = channel_2d(seed=seed * 1000 + k, nx=nx, ny=ny, phi=phi, dx=12.5e-6, mech=mech,
+                           T_wall_hot=1000.0)
             s = (np.arange(ny) + 0.5) / ny
             prof = u_in * 4.0 * s * (1.0 - s)
             w["u"][0] = np.broadcast_to(prof[None, :, None], w["u"][0].shape)

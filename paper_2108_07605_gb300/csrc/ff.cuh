@@ -12,9 +12,8 @@
 //   two_prod      with a fused multiply-add: p + e = a * b exactly.
 // exp: Tang's table-driven reduction to |r| <= ln2/128 with a 64-entry
 // float-float table of 2^(j/64) and a degree-6 polynomial for e^r.
-// log: one Newton step
-// y <- y + x e^(-y) - 1 from the FP32 logarithm (quadratic convergence takes
-// the 1e-7 start to the float-float precision).
+// log: from the FP32 logarithm y, log x = y + log(1 + t) with
+// t = x e^(-y) - 1, log(1 + t) to second order (|t| ~ 1e-7).
 // Intrinsics with explicit rounding keep the compiler from contracting or
 // reassociating the transformations.
 #pragma once
@@ -126,27 +125,38 @@ __device__ __forceinline__ ff ff_exp(ff x) {
   const float L1 = 0.010833740234375f, L2 = -3.3155381515825866e-06f,
               L3 = 2.572804640231345e-14f;
   const float k = rintf(__fmul_rn(x.hi, 92.33248138427734f));   // 64 / ln2
-  ff r = two_sum(__fsub_rn(x.hi, __fmul_rn(k, L1)), x.lo);
-  r = r - two_prod(k, L2);
-  r.lo = __fmaf_rn(-k, L3, r.lo);
-  // e^r - 1 = r + r^2 (1/2 + c), c = r/6 + r^2/24 + r^3/120 + r^4/720: c is
+  // r = x - k ln2/64 = (x.hi - k L1) - hi(k L2) + x.lo - lo(k L2) - k L3:
+  // the first difference is exact, the next two terms join it by exact
+  // two-sums (x.lo is as large as r's own rounding scale), and the last two
+  // (below 1e-9) with the two-sums' errors in FP32.
+  const float t = __fsub_rn(x.hi, __fmul_rn(k, L1));
+  const ff kL2 = two_prod(k, L2);
+  const ff s1 = two_sum(t, -kL2.hi);
+  const ff s2 = two_sum(s1.hi, x.lo);
+  ff r = two_sum(s2.hi, __fadd_rn(__fadd_rn(s1.lo, s2.lo), -__fmaf_rn(k, L3, kL2.lo)));
+  // e^r - 1 = r + r^2/2 + r^2 c, c = r/6 + r^2/24 + r^3/120 + r^4/720: c is
   // below 1e-3 and needs only FP32 (its rounding is below 1e-15 of e^r);
-  // the Taylor remainder r^7/5040 is below 1e-19.  r^2 (~3e-5 at most)
-  // in float-float from an exact product; its product with c (below 3e-8)
-  // in FP32.
+  // the Taylor remainder r^7/5040 is below 1e-19.  |r| <= ln2/128, so
+  // r^2/2 < |r|/256: the head sum needs no magnitude test, and the terms
+  // below ulp(r.hi) (r.lo, the low part of r^2/2, r^2 c) go in FP32.
   const float rh = r.hi;
   const float c = __fmul_rn(rh, __fmaf_rn(rh, __fmaf_rn(rh, __fmaf_rn(rh, 1.3888889225e-3f,
                                                                            8.3333337680e-3f),
                                                        4.1666667908e-2f),
                                           1.6666667163e-1f));
-  ff r2 = two_prod(rh, rh);
-  r2.lo = __fmaf_rn(__fmul_rn(2.f, rh), r.lo, r2.lo);
-  ff em1 = r + ff(__fmul_rn(0.5f, r2.hi), __fmul_rn(0.5f, r2.lo));
-  em1 = fast_two_sum(em1.hi, __fmaf_rn(r2.hi, c, em1.lo));
+  const ff r2 = two_prod(rh, rh);                       // r.hi^2 exactly
+  const float h2 = __fmul_rn(0.5f, r2.hi);
+  ff em1 = fast_two_sum(rh, h2);
+  float tail = __fmaf_rn(r2.hi, c, __fmaf_rn(0.5f, r2.lo, r.lo));
+  tail = __fmaf_rn(rh, r.lo, tail);                     // the cross term r.hi r.lo
+  em1 = fast_two_sum(em1.hi, __fadd_rn(em1.lo, tail));
   const int ki = (int)k;
-  const float2 t = __ldg(&kExp2Tab64[ki & 63]);
-  const ff tj(t.x, t.y);
-  const ff y = tj + tj * em1;
+  const float2 t64 = __ldg(&kExp2Tab64[ki & 63]);
+  // y = 2^(j/64) (1 + em1): the head product exactly, the rest in FP32
+  const ff p = two_prod(t64.x, em1.hi);
+  ff y = fast_two_sum(t64.x, p.hi);
+  const float lo = __fmaf_rn(t64.x, em1.lo, __fmaf_rn(t64.y, em1.hi, __fadd_rn(p.lo, t64.y)));
+  y = fast_two_sum(y.hi, __fadd_rn(y.lo, lo));
   // scale by 2^e: an exact multiply while 2^e is a normal float
   const int e = ki >> 6;
   if (e >= -126) {
@@ -157,8 +167,13 @@ __device__ __forceinline__ ff ff_exp(ff x) {
 }
 
 __device__ __forceinline__ ff ff_log(ff x) {
+  // y0 = log(x.hi) in FP32 (error d below a few 1e-7 relative), then
+  // log x = y0 + log(1 + t), t = x e^(-y0) - 1 (|t| ~ |d|): log(1 + t) =
+  // t - t^2/2 + O(t^3), the t^2 term in FP32 (a plain Newton step y0 + t
+  // would leave t^2/2, up to 1e-11 for large |log x|)
   const ff y0(logf(x.hi));
-  const ff t = x * ff_exp(-y0) - ff(1.f);
+  ff t = x * ff_exp(-y0) - ff(1.f);
+  t = fast_two_sum(t.hi, __fmaf_rn(-0.5f * t.hi, t.hi, t.lo));
   return y0 + t;
 }
 

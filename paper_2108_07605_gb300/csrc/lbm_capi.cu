@@ -7,6 +7,7 @@
 #include <string>
 #include <vector>
 
+#include "ff.cuh"
 #include "lbm_internal.h"
 
 using namespace lbm;
@@ -1434,3 +1435,34 @@ const char* lbm_last_error(lbm_t h) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Float-float exp and log at given points (a test hook for their accuracy).
+__global__ void k_ff_check(const double* __restrict__ x, long long n, double* __restrict__ e,
+                           double* __restrict__ l) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const ff v = ff_from_double(x[i]);
+  e[i] = ff_to_double(ff_exp(v));
+  l[i] = v.hi > 0.f ? ff_to_double(ff_log(v)) : __longlong_as_double(0x7ff8000000000000LL);
+}
+
+lbm_status lbm_ff_check(const double* x, long long n, double* exp_out, double* log_out) {
+  if (!x || !exp_out || !log_out || n < 0)
+    return fail(nullptr, LBM_ERR_INVALID, "lbm_ff_check: NULL buffer or negative n");
+  if (n > (1LL << 24)) return fail(nullptr, LBM_ERR_RANGE, "lbm_ff_check: n above 2^24");
+  if (n == 0) return LBM_OK;
+  double* d = nullptr;
+  const size_t b = (size_t)n * sizeof(double);
+  cudaError_t e = cudaMalloc(&d, 3 * b);
+  if (e != cudaSuccess) return cuda_fail(nullptr, e, "lbm_ff_check allocation");
+  e = cudaMemcpy(d, x, b, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) {
+    k_ff_check<<<(unsigned)((n + 255) / 256), 256>>>(d, n, d + n, d + 2 * n);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpy(exp_out, d + n, b, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(log_out, d + 2 * n, b, cudaMemcpyDeviceToHost);
+  cudaFree(d);
+  return e == cudaSuccess ? LBM_OK : cuda_fail(nullptr, e, "lbm_ff_check");
+}

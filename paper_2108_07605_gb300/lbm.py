@@ -103,6 +103,7 @@ EXPORTS = {
     "lbm_batch_run": (C.c_int, [C.c_void_p, C.c_int]),
     "lbm_batch_destroy": (C.c_int, [C.c_void_p]),
     "lbm_batch_autotune": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(lbm_launch)]),
+    "lbm_ff_check": (C.c_int, [C.c_void_p, C.c_longlong, C.c_void_p, C.c_void_p]),
     "lbm_batch_set_launch": (C.c_int, [C.c_void_p, C.POINTER(lbm_launch)]),
     "lbm_batch_get_launch": (C.c_int, [C.c_void_p, C.POINTER(lbm_launch)]),
     "lbm_set_launch": (C.c_int, [C.c_void_p, C.POINTER(lbm_launch)]),
@@ -296,6 +297,17 @@ def lbm_batch_autotune(plan, trial_steps=3):
     _check(load_library().lbm_batch_autotune(plan, int(trial_steps), C.byref(out)),
            plan.handles[0])
     return _launch_dict(out)
+
+
+def lbm_ff_check(x):
+    """Float-float exp and log of the library at the points x (1-D float64):
+    returns (exp, log) as float64 arrays (hi + lo of each result)."""
+    import numpy as np
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    e = np.empty_like(x)
+    lg = np.empty_like(x)
+    _check(load_library().lbm_ff_check(x.ctypes.data, x.size, e.ctypes.data, lg.ctypes.data))
+    return e, lg
 
 
 def lbm_batch_set_launch(plan, chem_lanes=-1, collide_split=-1, persistent=-1):

@@ -78,10 +78,14 @@ def placement():
     import bench
     from paper_2108_07605_gb300 import lbm
     from lbm_workloads.mechanism import h2_air_synthetic
+    from lbm_workloads import fields
     mech = h2_air_synthetic()
     for prec in ("fp32", "fp64"):
-        for wl in ("flame", "box"):
-            w = bench._workload(wl, seed=0)
+        for wl in ("flame", "flame256x32x32", "box"):
+            # the largest flame of the serving mix (262 144 nodes) between the
+            # 16 384-node flame and the 524 288-node box
+            w = fields.flame_1d(seed=0, nx=256, ny=32, nz=32, x_ign=64, mech=mech) \
+                if wl == "flame256x32x32" else bench._workload(wl, seed=0)
             s = lbm.Solver(mech, lattice=w["lattice"], shape=w["shape"], dx=w["dx"],
                            precision=prec, substeps=w["substeps"], T_max=w["T_max"],
                            **(bench.boundary_spec(w) or {}))
