@@ -14,7 +14,11 @@ rebuilt only when the batch's membership changes and replayed for a chunk of
 steps no longer than the shortest remaining request, so no request runs past
 its step count.  A request that has completed its steps is read back
 (lbm_moments), its handle destroyed and its memory returned, and waiting
-requests are admitted at the next tick.  A request whose solve fails (a
+requests are admitted at the next tick.  An optional cap on the resident
+nodes (max_nodes) admits in arrival order only while the resident requests'
+nodes stay below it (a request larger than the cap runs alone): enough
+resident work to fill the GPU, but not so much that every request advances
+at the pace of all of them and finishes near the end.  A request whose solve fails (a
 sticky device error such as a temperature Newton failure) is reported as
 failed with the library's message; the others are unaffected.  Reported:
 time-to-result (completion minus arrival) p50/p99 over the completed requests
@@ -59,9 +63,11 @@ class Request:
 class Server:
     """Admission by device memory, continuous batching by lattice/precision."""
 
-    def __init__(self, mech, budget_bytes, chunk=100, precision="fp32", device=0):
+    def __init__(self, mech, budget_bytes, chunk=100, precision="fp32", device=0,
+                 max_nodes=0):
         self.mech = mech
         self.budget = int(budget_bytes)
+        self.max_nodes = int(max_nodes)   # 0: no cap on resident nodes
         self.used = 0
         self.chunk = int(chunk)
         self.precision = precision
@@ -100,7 +106,9 @@ class Server:
         while pending or active:
             now = clock() - t0
             while pending and pending[0].arrival <= now and \
-                    self.used + pending[0].bytes <= self.budget:
+                    self.used + pending[0].bytes <= self.budget and \
+                    (self.max_nodes <= 0 or not active or
+                     sum(r.nodes for r in active) + pending[0].nodes <= self.max_nodes):
                 r = pending.pop(0)
                 self._admit(r, now)
                 active.append(r)
@@ -185,6 +193,8 @@ def main():
                    help="multiply every request's step count (1.0 = the stated 1k-10k)")
     p.add_argument("--serial", action="store_true",
                    help="one request at a time (no batching), for comparison")
+    p.add_argument("--max-nodes", type=int, default=0,
+                   help="cap on the resident requests' nodes (0: admit by memory only)")
     args = p.parse_args()
     from . import build
     build.build()
@@ -215,12 +225,13 @@ def main():
             done.append(r)
         out = summarize(done, time.perf_counter() - t0, node_updates)
     else:
-        srv = Server(mech, budget, chunk=args.chunk, precision=args.precision)
+        srv = Server(mech, budget, chunk=args.chunk, precision=args.precision,
+                     max_nodes=args.max_nodes)
         done = srv.run(stream)
         out = summarize(done, srv.elapsed, srv.node_updates)
     out.update(mode="serial" if args.serial else "continuous batching",
                precision=args.precision, step_scale=args.step_scale, seed=args.seed,
-               chunk=args.chunk, budget_gb=args.budget_gb)
+               chunk=args.chunk, budget_gb=args.budget_gb, max_nodes=args.max_nodes)
     print(json.dumps(out), flush=True)
 
 

@@ -75,3 +75,20 @@ def test_admission_waits_for_memory():
     assert all(r.error is None for r in done)
     assert max(resident) <= 1 + 0        # one at a time fits
     assert srv.used == 0
+
+
+def test_node_cap_admits_in_order_below_the_cap():
+    """With a cap on resident nodes, the resident requests' nodes stay below
+    it (one request at a time when a single one exceeds it) and every request
+    still finishes."""
+    from paper_2108_07605_gb300 import serve
+    mech = h2_air_synthetic()
+    stream = _small_mix(mech, n=6)
+    cap = max(int(w["P"].size) for _a, w in stream)
+    srv = serve.Server(mech, budget_bytes=int(2e9), chunk=10, precision="fp32", max_nodes=cap)
+    resident = []
+    done = srv.run(stream, on_tick=lambda now, act, pend, fin:
+                   resident.append((len(act), sum(r.nodes for r in act))))
+    assert len(done) == 6 and all(r.error is None for r in done)
+    assert all(nodes <= cap or n == 1 for n, nodes in resident)
+
