@@ -173,6 +173,14 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def launch_groups(launch, has_bnd):
+    """Names of the two timed launch groups of a step (lbm_step_timed): the
+    kernels before the collision, and the collision."""
+    g0 = (["k_boundary", "k_chem"] if has_bnd else []) + \
+        ["k_mchem" if launch["chem_lanes"] > 1 else "k_moments"]
+    return ["+".join(g0), "k_prep+k_coll" if launch["collide_split"] else "k_collide"]
+
+
 def group_counters(group, workload, precision):
     """Per-node counters of a launch group from the committed ncu summary
     (profiles/group_counters.txt): {"fp32_flop", "fp64_flop", "dram_bytes"},
@@ -325,9 +333,8 @@ def main():
     # one thread per node, or k_mchem, chem_lanes lanes per node), the
     # collision (one kernel, or two when split); with interface nodes also
     # the boundary kernel and, after it on the side stream, the interface
-    # nodes' moments (k_moments) or sub-steps (k_chem)
+    # nodes' sub-steps (k_chem)
     has_bnd = boundary_spec(w) is not None
-    lanes = launch["chem_lanes"] > 1
     launches_per_step = 1 + (2 if has_bnd else 0) + (2 if launch["collide_split"] else 1)
     value = node_updates_per_s(N, args.steps, world, M, total_ms * 1e-3)
 
@@ -337,10 +344,7 @@ def main():
     # 4.3 kB of populations, far above the machine balance (80.6 TFLOP/s FP32
     # or 1.25 FP64 against ~6.7 TB/s).  The ALU roof is the bound; the HBM
     # figures of the same group are reported beside it.
-    group0 = (["k_boundary", "k_chem" if lanes else "k_moments"] if has_bnd else []) + \
-        ["k_mchem" if lanes else "k_moments"]
-    names = ["+".join(dict.fromkeys(group0)),
-             "k_prep+k_coll" if launch["collide_split"] else "k_collide"]
+    names = launch_groups(launch, has_bnd)
     dom = int(np.argmax(kms))
     dom_ms = kms[dom] / args.steps
     alg_bytes = 2 * info.L * info.Q * info.bytes_per_population   # per node-step

@@ -230,11 +230,13 @@ lbm_status lbm_batch_destroy(lbm_batch_t b);
 
 /* Kernel placement of a step.  A performance choice only: every placement
  * evaluates the same formulas; they agree to rounding.
- *   chem_lanes     threads per node of the reaction sub-steps (Sec. 2.4,
- *                  Eq. R3): 1 = inside the moments kernel; 4 or 8 = in their
- *                  own kernel, the node's reactions dealt out over that many
- *                  lanes (for grids too small to fill the GPU at one thread
- *                  per node); -1 = by grid size.
+ *   chem_lanes     threads per node of the moments and reaction sub-steps
+ *                  (Sec. 2.4, Eq. R3): 1 = one thread per node; 4 or 8 = a
+ *                  group of that many lanes per node shares the pull, the
+ *                  temperature solve and the node's reactions (for grids too
+ *                  small to fill the GPU at one thread per node); -1 = by
+ *                  grid size.  Interface nodes (boundary reconstruction) take
+ *                  their sub-steps with eight lanes each in every placement.
  *   collide_split  0 = one thread per node does the whole collision; 1 = a
  *                  per-node kernel stores the collision parameters and a
  *                  second kernel updates the directions with nine threads

@@ -246,9 +246,9 @@ __device__ __forceinline__ void moments_finish(RT* __restrict__ rec, double* __r
 // ---------------------------------------------------------------------------
 // Moments of the post-stream state + temperature (Sec. 2.1, Sec. 3.1-3.2,
 // Sec. 3.7 slaving, Sec. 4.1 pull streaming).
-// chem_inline = 0: the reaction sub-steps run in k_chem (one warp per node);
-// this kernel then leaves the post-stream species densities rho_a (a < M) in
-// the record's increment slots for it.
+// chem_inline = 0: the reaction sub-steps run in a lane-group kernel
+// (k_chem); this kernel then leaves the post-stream species densities rho_a
+// (a < M) in the record's increment slots for it.
 template <int D, int M, typename S, typename RT>
 __device__ __forceinline__ void moments_body(const S* __restrict__ src, RT* __restrict__ rec,
                                              double* __restrict__ Tf, int* __restrict__ status,
@@ -2366,13 +2366,16 @@ static cudaError_t step_impl(const DevMech& mech, const StepArgs& a, cudaStream_
     // the boundary kernel (a few warps, latency-bound) and what follows it
     // for the interface nodes run on a side stream beside the bulk work
     const bool fork = a.bc.n_if > 0 && a.side && a.ev_fork && a.ev_join;
+    const bool if_rec = a.mech_dev != nullptr;     // interface records by the boundary warps
     if (fork) {
       cudaError_t e = cudaEventRecord(a.ev_fork, s);
       if (e == cudaSuccess) e = cudaStreamWaitEvent(a.side, a.ev_fork, 0);
       if (e != cudaSuccess) return e;
+      // the interface nodes: records by the boundary warps, sub-steps with
+      // eight lanes per node (k_chem), whatever the bulk placement
       k_boundary<D, M, S><<<(a.bc.n_if + 3) / 4, 128, 0, a.side>>>(
-          src, a.bc, a.Tfield, a.status, a.g, a.un, mech, chem_sep ? rec : nullptr, a.mech_dev);
-      if (!chem_sep)
+          src, a.bc, a.Tfield, a.status, a.g, a.un, mech, if_rec ? rec : nullptr, a.mech_dev);
+      if (!if_rec)
         k_moments<D, M, S, RT><<<blocks_for(a.bc.n_if, bs), bs, 0, a.side>>>(
             src, rec, a.Tfield, a.status, a.g, a.un, a.bc, mech, 1, NODES_INTERFACE);
       else
@@ -2388,20 +2391,19 @@ static cudaError_t step_impl(const DevMech& mech, const StepArgs& a, cudaStream_
       e = cudaStreamWaitEvent(s, a.ev_join, 0);
       if (e != cudaSuccess) return e;
     } else {
-      const bool bnd_rec = a.bc.n_if > 0 && chem_sep;
+      const bool bnd_rec = a.bc.n_if > 0 && if_rec;
       if (a.bc.n_if > 0)
         k_boundary<D, M, S><<<(a.bc.n_if + 3) / 4, 128, 0, s>>>(
             src, a.bc, a.Tfield, a.status, a.g, a.un, mech, bnd_rec ? rec : nullptr,
             a.mech_dev);
-      if (chem_sep) {
+      if (chem_sep)
         mchem(s, bnd_rec ? NODES_BULK : NODES_ALL);
-        if (bnd_rec)
-          launch_chem<D, M, RT>(lc, s, rec, a.Tfield, a.status, a.g.N, a.bc, a.un, a.mech_dev,
-                                NODES_INTERFACE);
-      } else {
+      else
         k_moments<D, M, S, RT><<<nb, bs, 0, s>>>(src, rec, a.Tfield, a.status, a.g, a.un, a.bc,
-                                                 mech, 1, NODES_ALL);
-      }
+                                                 mech, 1, bnd_rec ? NODES_BULK : NODES_ALL);
+      if (bnd_rec)
+        launch_chem<D, M, RT>(lc, s, rec, a.Tfield, a.status, a.g.N, a.bc, a.un, a.mech_dev,
+                              NODES_INTERFACE);
     }
   }
   if (which != 0) {
@@ -2510,13 +2512,11 @@ static cudaError_t batch_impl(const DomainDev* doms, int ndom, const BatchGrids&
     cudaError_t e = cudaEventRecord(side.fork, s);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(side.stream, side.fork, 0);
     if (e != cudaSuccess) return e;
-    kbnd<<<batch_grid(kbnd, gr.nbblocks, bs, 0, ps), bs, 0, side.stream>>>(
-        doms, ndom, parity, !chem_inline, gr.nbblocks);
-    if (chem_inline)
-      kmom<<<batch_grid(kmom, gr.nbblocks, bs, 0, ps), bs, 0, side.stream>>>(
-          doms, ndom, parity, chem_inline, NODES_INTERFACE, gr.nbblocks);
-    else
-      chem(NODES_INTERFACE, side.stream);
+    // (the interface nodes: records by the boundary warps, sub-steps with
+    // eight lanes per node, whatever the bulk placement)
+    kbnd<<<batch_grid(kbnd, gr.nbblocks, bs, 0, ps), bs, 0, side.stream>>>(doms, ndom, parity, 1,
+                                                                          gr.nbblocks);
+    chem(NODES_INTERFACE, side.stream);
     e = cudaEventRecord(side.join, side.stream);
     if (e != cudaSuccess) return e;
     if (chem_inline)
@@ -2527,17 +2527,16 @@ static cudaError_t batch_impl(const DomainDev* doms, int ndom, const BatchGrids&
     e = cudaStreamWaitEvent(s, side.join, 0);
     if (e != cudaSuccess) return e;
   } else {
-    const bool bnd_rec = gr.nbblocks > 0 && !chem_inline;
+    const bool bnd_rec = gr.nbblocks > 0;
     if (gr.nbblocks > 0)
-      kbnd<<<batch_grid(kbnd, gr.nbblocks, bs, 0, ps), bs, 0, s>>>(doms, ndom, parity,
-                                                                   !chem_inline, gr.nbblocks);
-    if (chem_inline) {
-      kmom<<<batch_grid(kmom, gr.nblocks, bs, 0, ps), bs, 0, s>>>(doms, ndom, parity, 1,
-                                                                  NODES_ALL, gr.nblocks);
-    } else {
+      kbnd<<<batch_grid(kbnd, gr.nbblocks, bs, 0, ps), bs, 0, s>>>(doms, ndom, parity, 1,
+                                                                   gr.nbblocks);
+    if (chem_inline)
+      kmom<<<batch_grid(kmom, gr.nblocks, bs, 0, ps), bs, 0, s>>>(
+          doms, ndom, parity, 1, bnd_rec ? NODES_BULK : NODES_ALL, gr.nblocks);
+    else
       mchem(bnd_rec ? NODES_BULK : NODES_ALL);
-      if (bnd_rec) chem(NODES_INTERFACE, s);
-    }
+    if (bnd_rec) chem(NODES_INTERFACE, s);
   }
   if (lc.coll_split) {
     auto kp = k_prep_batch<D, M, RT>;

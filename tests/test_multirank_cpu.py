@@ -51,3 +51,17 @@ def test_reference_arm_runs_on_rank_zero_only(capsys):
     # touching the oracle
     assert bench.run_reference(None, 1) is None
     assert capsys.readouterr().out == ""
+
+
+def test_group_counters_cover_the_default_bench_groups():
+    """Every launch group the default placements of the bench workloads time
+    has a line in profiles/group_counters.txt (the roofline's FLOP counts)."""
+    import bench
+    cases = [("flame", "fp32", 4, True), ("flame", "fp64", 1, True),
+             ("box", "fp32", 1, False), ("box", "fp64", 1, False)]
+    for workload, precision, lanes, has_bnd in cases:
+        for group in bench.launch_groups({"chem_lanes": lanes, "collide_split": 1}, has_bnd):
+            c = bench.group_counters(group, workload, precision)
+            assert c is not None, (group, workload, precision)
+            key = "fp64_flop" if precision == "fp64" else "fp32_flop"
+            assert c[key] > 1000 and c["dram_bytes"] > 0
