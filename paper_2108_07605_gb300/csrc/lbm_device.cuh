@@ -296,33 +296,6 @@ template <int D, int M, typename R = double> struct EqSet {
   double T_full;  // T of a solved state to the solve's precision (float-float in FP32)
 };
 
-// theta_a, theta and U/c^2 of the state.  FP32 (mixed path): the
-// mixture energy, a sum of formation-energy-sized terms, in float-float.
-template <int D, int M, typename R>
-__device__ void eq_prepare(EqSet<D, M, R>& s, const DevMech& m, const Units& un) {
-  if constexpr (sizeof(R) == 8) {
-    double Rm = 0.0, U = 0.0;
-    for (int a = 0; a < M; ++a) {
-      Rm += s.Y[a] * m.inv_mm[a];
-      U += s.Y[a] * species_U(m, a, s.T);
-      s.th_a[a] = m.Ra[a] * s.T * un.inv_c2;
-    }
-    s.th = R_U * Rm * s.T * un.inv_c2;
-    s.U = U * un.inv_c2;
-  } else {
-    float Rm = 0.f;
-    ff U;
-    const ff T(s.T);
-    for (int a = 0; a < M; ++a) {
-      Rm += s.Y[a] * m.inv_mm_s[a];
-      U += ff(s.Y[a]) * species_U_ff(m, a, T);
-      s.th_a[a] = m.Ra_s[a] * s.T * un.inv_c2_s;
-    }
-    s.th = float(R_U) * Rm * s.T * un.inv_c2_s;
-    s.U = (U * un.inv_c2_f).hi;
-  }
-}
-
 // Population l (0..M-2 species, M-1 momentum, M energy) in direction i.
 template <int D, int M, typename R>
 __device__ R eq_pop(const EqSet<D, M, R>& s, int l, int i) {

@@ -360,15 +360,6 @@ template <> struct Chem<double> {
   }
   __device__ static double mag(double x) { return fabs(x); }
   __device__ static double rtol(const Units& u) { return u.newton_rtol; }
-  template <int M>
-  __device__ static double newton(const DevMech& m, const double (&r)[M], double rho, double U,
-                                  double T, const Units& un, bool& ok) {
-    double Ys[M];
-    const double ir = 1.0 / rho;
-#pragma unroll
-    for (int a = 0; a < M; ++a) Ys[a] = r[a] * ir;
-    return newton_T<M>(m, Ys, U, T, un.newton_max_iter, un.newton_rtol, ok);
-  }
 };
 template <> struct Chem<ff> {
   __device__ static ff ex(ff x) { return ff_exp(x); }
@@ -395,14 +386,6 @@ template <> struct Chem<ff> {
   }
   __device__ static float mag(ff x) { return fabsf(x.hi); }
   __device__ static float rtol(const Units& u) { return u.newton_rtol_f; }
-  template <int M>
-  __device__ static ff newton(const DevMech& m, const ff (&r)[M], ff rho, ff U, ff T,
-                              const Units& un, bool& ok) {
-    ff Ys[M];
-#pragma unroll
-    for (int a = 0; a < M; ++a) Ys[a] = r[a] / rho;
-    return newton_T_ff<M>(m, Ys, U, T, un.newton_max_iter, un.newton_rtol_f, ok);
-  }
 };
 
 template <typename RT> struct ChemType { using type = double; };
@@ -1437,10 +1420,11 @@ __device__ __forceinline__ T species_sum(T v) {
   return shfl_ct(0xffffffffu, v, 0);
 }
 
-// theta_a, theta and U/c^2 of an equilibrium state (eq_prepare) by a warp:
-// lane a < M evaluates species a's energy, the warp sums.  m: the mechanism
-// for compile-time species indices; mp: the same at an address the lanes
-// may index by species.
+// theta_a, theta and U/c^2 of an equilibrium state by a warp: lane a < M
+// evaluates species a's energy (float-float in the mixed path: the mixture
+// energy is a sum of formation-energy-sized terms), the warp sums.  m: the
+// mechanism for compile-time species indices; mp: the same at an address
+// the lanes may index by species.
 template <int D, int M, typename R>
 __device__ __forceinline__ void eq_prepare_warp(EqSet<D, M, R>& s, const DevMech& m,
                                                 const DevMech& mp, const Units& un, int lane) {
@@ -1646,13 +1630,13 @@ __device__ __forceinline__ void boundary_body(const S* __restrict__ src, const B
     A.Y[M - 1] = R(1) - ysum;
     for (int d = 0; d < D; ++d) A.u[d] = R(0);     // u^tgt = u_a^tgt = 0
     A.T = R(bc.if_wallT[k]);
-    eq_prepare_warp(A, mech, mp, un, lane);                         // step 2: target (Eqs. tgtf-tgtfa)
+    eq_prepare_warp(A, mech, mp, un, lane);  // step 2: target (Eqs. tgtf-tgtfa)
   } else if (kind == BK_INLET) {
     A.rho = R(bc.rho_in);
     for (int a = 0; a < M; ++a) A.Y[a] = R(bc.Y_in[a]);
     for (int d = 0; d < D; ++d) A.u[d] = R(bc.if_uin[(long long)d * st + k]);
     A.T = R(bc.T_in);
-    eq_prepare_warp(A, mech, mp, un, lane);                         // step 1 (Eqs. in_f-in_fa)
+    eq_prepare_warp(A, mech, mp, un, lane);  // step 1 (Eqs. in_f-in_fa)
   } else {
     // LODI data from the stored state at x and x - n (Eq. convectiveBC)
     const int ax = (info >> 4) & 3;
@@ -1705,7 +1689,7 @@ __device__ __forceinline__ void boundary_body(const S* __restrict__ src, const B
       Ro += Ya * mech.inv_mm[a];
     }
     A.T = R(p_o * un.c * un.c / (rho_o * R_U * Ro));
-    eq_prepare_warp(A, mech, mp, un, lane);                         // step 1 (Eqs. out_f-out_fa)
+    eq_prepare_warp(A, mech, mp, un, lane);  // step 1 (Eqs. out_f-out_fa)
   }
   // incoming links at A, then the local state (Eqs. locRho-locT and analogues)
   if (in_i) {
