@@ -187,30 +187,42 @@ __device__ ff newton_T_ff(const DevMech& m, const ff* Y, ff U, ff T, int max_ite
   return T;
 }
 
+// The arrays the reaction loop indexes by species (concentrations, Gibbs
+// functions, rates) live in a per-thread slice of shared memory: a runtime
+// index into a register array would put it in local memory.  Every kernel
+// that runs the float-float rates has kChemThreads threads per block.
+constexpr int kChemThreads = 128;
+
 template <int M>
 __device__ void production_rates_ff(const DevMech& m, ff T, const ff* r, ff* rdot) {
+  __shared__ __align__(8) unsigned char chem_raw[3 * M * kChemThreads * sizeof(ff)];
+  ff* const Cs = reinterpret_cast<ff*>(chem_raw) + threadIdx.x;   // entry a at [a kChemThreads]
+  ff* const Gs = Cs + M * kChemThreads;
+  ff* const Ws = Gs + M * kChemThreads;
   const ff lnT = ff_log(T);
   const ff invT = ff(1.f) / T;
-  ff C[M], G[M], w[M];
+  ff C[M];
 #pragma unroll
   for (int a = 0; a < M; ++a) {
     C[a] = r[a] * m.inv_mm_f[a];
-    G[a] = m.g_inv_f[a] * invT + m.g0_f[a] + T * (m.g1_f[a] + T * m.g2_f[a]) - m.a0_f[a] * lnT;
-    w[a] = ff();
+    Cs[a * kChemThreads] = C[a];
+    Gs[a * kChemThreads] =
+        m.g_inv_f[a] * invT + m.g0_f[a] + T * (m.g1_f[a] + T * m.g2_f[a]) - m.a0_f[a] * lnT;
+    Ws[a * kChemThreads] = ff();
   }
   const ff ln_p0_rut = m.ln_p0_over_ru_f - lnT;
   for (int k = 0; k < m.R; ++k) {
     const DevReaction& rx = m.rx[k];
     const ff lnkf = rx.lnA_f + rx.b_f * lnT - rx.EaR_f * invT;
     ff fwd = ff_exp(lnkf);
-    for (int j = 0; j < rx.nr; ++j) fwd *= C[rx.reac[j]];
+    for (int j = 0; j < rx.nr; ++j) fwd *= Cs[rx.reac[j] * kChemThreads];
     ff rev;
     if (rx.reversible) {
       ff dG;
-      for (int j = 0; j < rx.np; ++j) dG += G[rx.prod[j]];
-      for (int j = 0; j < rx.nr; ++j) dG -= G[rx.reac[j]];
+      for (int j = 0; j < rx.np; ++j) dG += Gs[rx.prod[j] * kChemThreads];
+      for (int j = 0; j < rx.nr; ++j) dG -= Gs[rx.reac[j] * kChemThreads];
       rev = ff_exp(lnkf + dG - ff((float)rx.dn) * ln_p0_rut);
-      for (int j = 0; j < rx.np; ++j) rev *= C[rx.prod[j]];
+      for (int j = 0; j < rx.np; ++j) rev *= Cs[rx.prod[j] * kChemThreads];
     }
     ff q = fwd - rev;
     if (rx.third_body) {
@@ -219,11 +231,11 @@ __device__ void production_rates_ff(const DevMech& m, ff T, const ff* r, ff* rdo
       for (int a = 0; a < M; ++a) cm += m.eff_f[k][a] * C[a];
       q *= cm;
     }
-    for (int j = 0; j < rx.nr; ++j) w[rx.reac[j]] -= q;
-    for (int j = 0; j < rx.np; ++j) w[rx.prod[j]] += q;
+    for (int j = 0; j < rx.nr; ++j) Ws[rx.reac[j] * kChemThreads] -= q;
+    for (int j = 0; j < rx.np; ++j) Ws[rx.prod[j] * kChemThreads] += q;
   }
 #pragma unroll
-  for (int a = 0; a < M; ++a) rdot[a] = w[a] * m.mm_f[a];
+  for (int a = 0; a < M; ++a) rdot[a] = Ws[a * kChemThreads] * m.mm_f[a];
 }
 
 // ------------------------------------------------------------------------

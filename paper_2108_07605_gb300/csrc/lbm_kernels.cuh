@@ -87,6 +87,7 @@ template <> __device__ __forceinline__ float kcoef<float>(const DevMech& m, int 
 
 // threads per block of the node kernels (the shared-memory columns use it)
 constexpr int kBS = 128;
+static_assert(kBS == kChemThreads, "the chemistry's shared-memory slices assume kBS threads");
 
 // shared memory of the collision kernel per thread: the diffusion-velocity
 // matrix, then the axis-factor tables
@@ -456,6 +457,12 @@ __device__ __forceinline__ void chem_group_substeps(CT (&r)[M], const CT irho, c
                                                     int* __restrict__ status) {
   using X = Chem<CT>;
   const int base = (int)(threadIdx.x & 31) - sub;      // the group's first lane
+  // the arrays the reaction loop indexes by species: a per-thread slice of
+  // shared memory (as in production_rates_ff; 128-thread blocks)
+  __shared__ __align__(8) unsigned char chem_raw[3 * M * kChemThreads * sizeof(CT)];
+  CT* const Cs = reinterpret_cast<CT*>(chem_raw) + threadIdx.x;
+  CT* const Gs = Cs + M * kChemThreads;
+  CT* const Ws = Gs + M * kChemThreads;
   for (int s = 0; s < un.substeps; ++s) {
     if (s > 0) {
       bool ok;
@@ -472,26 +479,29 @@ __device__ __forceinline__ void chem_group_substeps(CT (&r)[M], const CT irho, c
       const int a = sub + j * L;
       Gown[j] = a < M ? X::gibbs(m, a, Ts, invT, lnT) : CT();
     }
-    CT C[M], G[M], w[M];
+    // species-indexed arrays in the thread's shared-memory slice (the
+    // register copy of C serves the unrolled third-body sums)
+    CT C[M];
 #pragma unroll
     for (int a = 0; a < M; ++a) {
       C[a] = r[a] * X::inv_mm(m, a);
-      G[a] = shfl_ct(gmask, Gown[a / L], base + a % L);
-      w[a] = CT();
+      Cs[a * kChemThreads] = C[a];
+      Gs[a * kChemThreads] = shfl_ct(gmask, Gown[a / L], base + a % L);
+      Ws[a * kChemThreads] = CT();
     }
     const CT lp = X::ln_p0(m) - lnT;   // ln(P0 / (R_U T))
     for (int k = sub; k < m.R; k += L) {
       const DevReaction& rx = m.rx[k];
       const CT lk = X::lnkf(rx, lnT, invT);
       CT fwd = X::ex(lk);
-      for (int j = 0; j < rx.nr; ++j) fwd *= C[rx.reac[j]];
+      for (int j = 0; j < rx.nr; ++j) fwd *= Cs[rx.reac[j] * kChemThreads];
       CT rev = CT();
       if (rx.reversible) {
         CT dG = CT();
-        for (int j = 0; j < rx.np; ++j) dG += G[rx.prod[j]];
-        for (int j = 0; j < rx.nr; ++j) dG -= G[rx.reac[j]];
+        for (int j = 0; j < rx.np; ++j) dG += Gs[rx.prod[j] * kChemThreads];
+        for (int j = 0; j < rx.nr; ++j) dG -= Gs[rx.reac[j] * kChemThreads];
         rev = X::ex(X::rev_arg(rx, lk, dG, lp));
-        for (int j = 0; j < rx.np; ++j) rev *= C[rx.prod[j]];
+        for (int j = 0; j < rx.np; ++j) rev *= Cs[rx.prod[j] * kChemThreads];
       }
       CT q = fwd - rev;
       if (rx.third_body) {
@@ -500,9 +510,12 @@ __device__ __forceinline__ void chem_group_substeps(CT (&r)[M], const CT irho, c
         for (int a = 0; a < M; ++a) cm += X::eff(m, k, a) * C[a];
         q *= cm;
       }
-      for (int j = 0; j < rx.nr; ++j) w[rx.reac[j]] -= q;
-      for (int j = 0; j < rx.np; ++j) w[rx.prod[j]] += q;
+      for (int j = 0; j < rx.nr; ++j) Ws[rx.reac[j] * kChemThreads] -= q;
+      for (int j = 0; j < rx.np; ++j) Ws[rx.prod[j] * kChemThreads] += q;
     }
+    CT w[M];
+#pragma unroll
+    for (int a = 0; a < M; ++a) w[a] = Ws[a * kChemThreads];
     // butterfly sums over the group: every lane ends with the same total
 #pragma unroll
     for (int o = 1; o < L; o <<= 1)
@@ -1819,7 +1832,7 @@ __device__ __forceinline__ void boundary_record(const BCDev& bc, R* __restrict__
 enum { NODES_ALL = 0, NODES_BULK = 1, NODES_INTERFACE = 2 };
 
 template <int D, int M, typename S, typename RT>
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(128, sizeof(RT) == 4 ? 4 : 1)
 k_moments(const S* __restrict__ src, RT* __restrict__ rec, double* __restrict__ Tf,
           int* __restrict__ status, const __grid_constant__ Geom g,
           const __grid_constant__ Units un, const __grid_constant__ BCDev bc,
@@ -1957,7 +1970,7 @@ __device__ __forceinline__ int domain_of_block(const DomainDev* __restrict__ d, 
 // launched persistent (a grid sized to the blocks resident on the GPU) each
 // block processes several tiles in turn.
 template <int D, int M, typename S, typename RT>
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(128, sizeof(RT) == 4 ? 4 : 1)
 k_moments_batch(const DomainDev* __restrict__ doms, int ndom, int parity, int chem_inline,
                 int node_set, int nblk) {
   for (int b = blockIdx.x; b < nblk; b += gridDim.x) {
