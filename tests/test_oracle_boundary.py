@@ -9,8 +9,8 @@ states they achieve, checked on the moments of the reconstructed nodes:
   the equilibria of the node's own local state.
 * Outlet (Sec. 4.4, remark after Eq. fa_outlet): the node takes the outlet
   data; a uniform state at rest at the outlet pressure is a fixed point.
-* Bounce-back (Eq. bb) and TMS both conserve mass in a closed box (Sec. 4.2:
-  the bounce-back density is used "to satisfy mass conservation").
+* Bounce-back (Eq. bb) and TMS both conserve mass in a closed box (Sec. 4.2
+  takes the bounce-back density so that the wall conserves mass).
 * LODI outlet (Sec. 4.4, reading R13): an acoustic pulse leaves through it
   with little reflection, while the same outlet clamped to its pressure
   (a large relaxation coefficient) reflects it; the wave amplitudes' signs
