@@ -1919,8 +1919,10 @@ k_prep(const RT* __restrict__ rec, const double* __restrict__ Tf, RT* __restrict
                       blockIdx.x * (long long)blockDim.x + threadIdx.x);
 }
 
+// FP32: four 288-thread blocks per SM (at most 56 registers), so a grid of
+// the 16k-node flame fits the GPU in one wave; FP64 would spill
 template <int D, int M, typename S, typename RT>
-__global__ void __launch_bounds__(32 * kCollTPN)
+__global__ void __launch_bounds__(32 * kCollTPN, sizeof(RT) == 4 ? 4 : 1)
 k_coll(const S* __restrict__ src, S* __restrict__ dst, const RT* __restrict__ cp,
        const __grid_constant__ Geom g, const __grid_constant__ BCDev bc,
        const __grid_constant__ DevMech mech) {
@@ -2061,7 +2063,7 @@ k_prep_batch(const DomainDev* __restrict__ doms, int ndom, int nblk) {
 }
 
 template <int D, int M, typename S, typename RT>
-__global__ void __launch_bounds__(32 * kCollTPN)
+__global__ void __launch_bounds__(32 * kCollTPN, sizeof(RT) == 4 ? 4 : 1)
 k_coll_batch(const DomainDev* __restrict__ doms, int ndom, int parity, int nblk) {
   extern __shared__ __align__(16) unsigned char coll_raw[];
   for (int b = blockIdx.x; b < nblk; b += gridDim.x) {
