@@ -158,7 +158,7 @@ std::string validate(const lbm_config* c) {
   if (c->c_ref == 0.0 && !(c->T_max > 0.0)) return "T_max must be positive when c_ref = 0";
   const lbm_mechanism& m = c->mech;
   if (m.n_species != 2 && m.n_species != 9)
-    return "n_species must be 2 or 9 in this build";
+    return "n_species must be 2 or 9 (the species counts the library is compiled for)";
   if (m.n_reactions < 0 || m.n_reactions > LBM_MAX_REACTIONS) return "n_reactions out of range";
   for (int a = 0; a < m.n_species; ++a) {
     if (!(m.molar_mass[a] > 0.0)) return "molar masses must be positive";
