@@ -51,6 +51,10 @@ PRECEDENCE = {1: 3, 2: 3, 3: 2, 4: 1}        # walls > inlet > outlet
 
 
 class Boundaries:
+    """Boundary reconstruction of Sec. 4 for one OracleLBM: face kinds, solid
+    nodes, interface-node classification and the procedures of Eq. bb and
+    Secs. 4.2.2 (TMS wall), 4.3 (inlet) and 4.4 (LODI outlet)."""
+
     def __init__(self, lbm, spec):
         self.lbm = lbm
         vs = lbm.vs
@@ -164,7 +168,8 @@ class Boundaries:
         return rho, u, Y, us, T
 
     def apply(self, post, pops):
-        """Replace the incoming populations of every interface node."""
+        """Replace the incoming populations of every interface node (Sec. 4:
+        Eq. bb, Secs. 4.2.2, 4.3, 4.4; walls before inlet before outlet)."""
         lbm = self.lbm
         out = pops.copy()
         flat = out.reshape(lbm.L, lbm.vs.Q, -1)
@@ -232,14 +237,16 @@ class Boundaries:
 
     def stored_fields(self, post, nodes):
         """rho, u, T, Y of the stored post-collision state `post` at flat node
-        indices (the fields at time t - dt); Newton starts from the T field."""
+        indices (the fields at time t - dt that Eq. convectiveBC and the LODI
+        data take); Newton starts from the T field."""
         lbm = self.lbm
         p = post.reshape(lbm.L, lbm.vs.Q, -1)[:, :, nodes]
         rho, u, Y, _, T = self._local_state(p, lbm.T.ravel()[nodes])
         return rho, u, T, Y
 
     def lodi_state(self, idx, post):
-        """LODI outlet data (rho, u, T, Y) at outlet nodes idx (flat), from the
+        """LODI outlet data (Sec. 4.4, Eq. convectiveBC; reading R13) (rho, u, T,
+        Y) at outlet nodes idx (flat), from the
         stored state of the previous step at x and x - n."""
         lbm = self.lbm
         mech = lbm.mech
@@ -295,8 +302,8 @@ class Boundaries:
 
     # ------------------------------------------------------------------ #
     def gradient(self, lbm, phi, kind):
-        """Isotropic gradient with ghost values outside the fluid (see the
-        module docstring).  phi: [K, z, y, x]; kind: "Phi" or "Y"."""
+        """Isotropic gradient (Sec. 3.4, readings R7, R8) with ghost values
+        outside the fluid (see the module docstring).  phi: [K, z, y, x]; kind: "Phi" or "Y"."""
         vs = lbm.vs
         D = vs.dim
         nz, ny, nx = lbm.shape

@@ -22,7 +22,8 @@ from . import thermo
 
 
 def forward_rate_constants(mech, T):
-    """k_f per reaction, shape [R, ...]."""
+    """k_f per reaction, shape [R, ...] (the Arrhenius form that stands in
+    for Cantera's rates, Sec. 3.6; readings R17)."""
     T = np.asarray(T, dtype=float)
     A = mech.arrhenius[:, 0].reshape((-1,) + (1,) * T.ndim)
     b = mech.arrhenius[:, 1].reshape((-1,) + (1,) * T.ndim)
@@ -31,7 +32,9 @@ def forward_rate_constants(mech, T):
 
 
 def equilibrium_constants(mech, T):
-    """K_c per reaction (concentration units), shape [R, ...]."""
+    """K_c per reaction (concentration units), shape [R, ...]: the table's own
+    equilibrium constants, which make the reverse rates consistent with the
+    thermodynamics of Sec. 3.1."""
     T = np.asarray(T, dtype=float)
     g = thermo.h_molar(mech, T) - T * thermo.s_molar(mech, T)      # [M, ...]
     nu = mech.nu_r - mech.nu_f                                      # [R, M]
@@ -41,7 +44,8 @@ def equilibrium_constants(mech, T):
 
 
 def rates_of_progress(mech, T, rho_species):
-    """q_r (mol/(m^3 s)), shape [R, ...].  rho_species: [M, ...] (kg/m^3)."""
+    """q_r (mol/(m^3 s)), shape [R, ...] (rates of progress for Sec. 2.4; third
+    bodies and reverse rates as in the module docstring).  rho_species: [M, ...] (kg/m^3)."""
     T = np.asarray(T, dtype=float)
     shape = T.shape
     C = rho_species / mech.molar_mass.reshape((-1,) + (1,) * T.ndim)  # [M, ...]
@@ -68,7 +72,8 @@ def rates_of_progress(mech, T, rho_species):
 
 
 def production_rates(mech, T, rho_species):
-    """rho_dot_a (kg/(m^3 s)), shape [M, ...]."""
+    """rho_dot_a (kg/(m^3 s)), shape [M, ...]: the mass production rates of
+    Sec. 2.4 (their sum vanishes, Eq. sumRhoDot)."""
     q = rates_of_progress(mech, T, rho_species)
     nu = mech.nu_r - mech.nu_f                                       # [R, M]
     wdot = np.tensordot(nu, q, axes=(0, 0))                          # [M, ...]

@@ -22,7 +22,8 @@ from . import chemistry, thermo
 
 
 def heat_release_rate(mech, T, rho_species):
-    """q (W/m^3) at each node; T: [...], rho_species: [M, ...]."""
+    """q (W/m^3) at each node (Sec. 5.3 follows it; q = -sum_a H_a rho_dot_a
+    with H_a of Sec. 3.1); T: [...], rho_species: [M, ...]."""
     wdot = chemistry.production_rates(mech, T, rho_species)
     return -np.sum(thermo.H_species(mech, T) * wdot, axis=0)
 

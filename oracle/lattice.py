@@ -17,6 +17,9 @@ import numpy as np
 
 
 class VelocitySet:
+    """D3Q27 / D2Q9 velocities and the index map of the module docstring
+    (Sec. 2.2, Eq. d3q27vel; reading R1)."""
+
     def __init__(self, dim: int):
         if dim not in (2, 3):
             raise ValueError("dim must be 2 or 3")

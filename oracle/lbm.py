@@ -48,7 +48,7 @@ def species_velocity_undefined(rho_a, j_a):
 
 
 class Units:
-    """Acoustic scaling: dt = dx / c."""
+    """Acoustic scaling: dt = dx / c (reading R10)."""
 
     def __init__(self, dx, c):
         self.dx = float(dx)
@@ -64,6 +64,9 @@ def default_reference_speed(mech, T_max):
 
 
 class OracleLBM:
+    """The reactive-mixture LBM of Secs. 2-4 on a box of nodes, in plain FP64
+    (test infrastructure)."""
+
     def __init__(self, mech, lattice="D3Q27", shape=(16, 16, 16), dx=1e-3,
                  c_ref=0.0, T_max=3000.0, substeps=2, newton_rtol=1e-13,
                  newton_max_iter=50, boundaries=None):
@@ -97,7 +100,8 @@ class OracleLBM:
         return Ra.reshape((-1,) + (1,) * np.ndim(T)) * T / self.units.c ** 2
 
     def _shift(self, field, c):
-        """field(x - c) on the periodic grid: np.roll moves a[x] to x + c."""
+        """field(x - c) on the periodic grid: np.roll moves a[x] to x + c (the pull
+        streaming of Sec. 4.1)."""
         axes = (-1, -2, -3)                          # x, y, z axes of [..., z, y, x]
         out = field
         for a in range(self.vs.dim):
@@ -178,6 +182,9 @@ class OracleLBM:
 
     # ------------------------------------------------------------------ #
     def step(self, nsteps=1):
+        """nsteps time steps of the path (streaming Sec. 4.1, boundaries Sec. 4,
+        moments and T Sec. 3.1, sub-steps Sec. 2.4 Eq. R3, collisions Sec. 2.3
+        and Secs. 3.2-3.4)."""
         for _ in range(nsteps):
             self._one_step()
 

@@ -19,11 +19,12 @@ from lbm_workloads.mechanism import R_UNIVERSAL, T_STANDARD, P_STANDARD
 
 
 class NewtonError(RuntimeError):
-    pass
+    """The temperature Newton of Eq. temperature did not converge (reading R11)."""
 
 
 def cp_molar(mech, T):
-    """c_p (J/(mol K)) per species, shape [M, ...]."""
+    """c_p (J/(mol K)) per species, shape [M, ...] (Sec. 3.1, the table's
+    polynomial, reading R17)."""
     T = np.asarray(T, dtype=float)
     a = mech.cp_coeffs
     return R_UNIVERSAL * (a[:, 0, None] + a[:, 1, None] * T.ravel()[None]
@@ -31,7 +32,8 @@ def cp_molar(mech, T):
 
 
 def h_molar(mech, T):
-    """Molar enthalpy incl. formation, h = h_f + int_T0^T c_p dT' (J/mol)."""
+    """Molar enthalpy incl. formation, h = h_f + int_T0^T c_p dT' (J/mol)
+    (Sec. 3.1, Eq. specHa per mole)."""
     T = np.asarray(T, dtype=float)
     a = mech.cp_coeffs
     t, t0 = T.ravel()[None], T_STANDARD
@@ -41,7 +43,8 @@ def h_molar(mech, T):
 
 
 def s_molar(mech, T):
-    """Standard-state molar entropy s = s0 + int_T0^T c_p/T' dT' (J/(mol K))."""
+    """Standard-state molar entropy s = s0 + int_T0^T c_p/T' dT' (J/(mol K));
+    enters the equilibrium constants of the reverse rates (Sec. 2.4)."""
     T = np.asarray(T, dtype=float)
     a = mech.cp_coeffs
     t, t0 = T.ravel()[None], T_STANDARD
@@ -51,43 +54,48 @@ def s_molar(mech, T):
 
 
 def species_gas_constant(mech):
+    """R_a = R_U / m_a (Sec. 2.1)."""
     return R_UNIVERSAL / mech.molar_mass                       # R_a, J/(kg K)
 
 
 def H_species(mech, T):
-    """Mass-specific enthalpy H_a (J/kg), shape [M, ...]."""
+    """Mass-specific enthalpy H_a (J/kg), shape [M, ...] (Sec. 3.1, Eq. specHa)."""
     mm = mech.molar_mass.reshape((-1,) + (1,) * np.ndim(T))
     return h_molar(mech, T) / mm
 
 
 def U_species(mech, T):
-    """Mass-specific internal energy U_a = H_a - R_a T (J/kg)."""
+    """Mass-specific internal energy U_a = H_a - R_a T (J/kg) (Sec. 3.1,
+    Eq. specUa)."""
     Ra = species_gas_constant(mech).reshape((-1,) + (1,) * np.ndim(T))
     return H_species(mech, T) - Ra * np.asarray(T)
 
 
 def Cv_species(mech, T):
-    """Mass-specific C_av = C_ap - R_a (Mayer relation), J/(kg K)."""
+    """Mass-specific C_av = C_ap - R_a (Mayer relation), J/(kg K) (Sec. 3.1)."""
     mm = mech.molar_mass.reshape((-1,) + (1,) * np.ndim(T))
     Ra = species_gas_constant(mech).reshape((-1,) + (1,) * np.ndim(T))
     return cp_molar(mech, T) / mm - Ra
 
 
 def mixture_gas_constant(mech, Y):
-    """R = R_U / m with 1/m = sum_a Y_a/m_a.  Y: [M, ...]."""
+    """R = R_U / m with 1/m = sum_a Y_a/m_a (Sec. 2.1).  Y: [M, ...]."""
     mm = mech.molar_mass.reshape((-1,) + (1,) * (np.ndim(Y) - 1))
     return R_UNIVERSAL * np.sum(Y / mm, axis=0)
 
 
 def mixture_U(mech, Y, T):
+    """U = sum_a Y_a U_a (Sec. 3.1, Eq. U)."""
     return np.sum(Y * U_species(mech, T), axis=0)
 
 
 def mixture_H(mech, Y, T):
+    """H = sum_a Y_a H_a (Sec. 3.1, Eq. H)."""
     return np.sum(Y * H_species(mech, T), axis=0)
 
 
 def mixture_Cv(mech, Y, T):
+    """C_v = sum_a Y_a C_av (Sec. 3.1), the Newton derivative of Eq. temperature."""
     return np.sum(Y * Cv_species(mech, T), axis=0)
 
 

@@ -27,14 +27,15 @@ from lbm_workloads.mechanism import R_UNIVERSAL, T_STANDARD, P_STANDARD
 
 
 def diffusion_coefficients(mech, T, P):
-    """D_ab (m^2/s), shape [M, M, ...]."""
+    """D_ab (m^2/s), shape [M, M, ...] (the power law of reading R9, standing in
+    for Cantera's binary coefficients, Sec. 3.6)."""
     T = np.asarray(T, dtype=float)
     s = (T / T_STANDARD) ** mech.D_T_exponent * (P_STANDARD / P)
     return mech.D0.reshape(mech.D0.shape + (1,) * T.ndim) * s
 
 
 def viscosity(mech, T, Y=None):
-    """Mixture viscosity (Pa s).  "mixture" model: mu0 (T/T0)^e.  "wilke"
+    """Mixture viscosity (Pa s), reading R9 (Sec. 3.5 takes it from Cantera).  "mixture" model: mu0 (T/T0)^e.  "wilke"
     model (Wilke's mixing rule, J. Chem. Phys. 18, 1950) over the species
     viscosities mu_a = mu0_a (T/T0)^e:
       mu = sum_a X_a mu_a / sum_b X_b Phi_ab,
@@ -62,7 +63,8 @@ def viscosity(mech, T, Y=None):
 
 
 def relaxation(mech, units, rho, Y, T):
-    """Per-node relaxation data.
+    """Per-node relaxation data (Sec. 2.3 Eqs. betaa, taua; Sec. 3.5 Eqs. mu,
+    lambda; reading R3).
 
     Returns dict with inv_tau_ab [M, M, ...] (zero diagonal), inv_tau_a [M, ...],
     beta [M, ...], omega [...], omega1 [...].
