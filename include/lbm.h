@@ -272,9 +272,13 @@ lbm_status lbm_autotune(lbm_t h, int trial_steps, lbm_launch* chosen);
 lbm_status lbm_batch_autotune(lbm_batch_t b, int trial_steps, lbm_launch* chosen);
 
 /* Set a plan's placement (-1 fields: the default for the batch's total node
- * count) and capture its graphs again; read the placement in use.  The
- * handles' own lbm_set_launch values do not apply to plans.  LBM_ERR_INVALID
- * for values out of range. */
+ * count) and capture its graphs again; read the placement in use.  A
+ * performance choice with no counterpart in the paper: every placement
+ * computes the step of Secs. 2-4.  The handles' own lbm_set_launch values do
+ * not apply to plans.  l is the caller's; the plan keeps a copy.
+ * LBM_ERR_INVALID for a NULL plan or l, or values out of range (the plan is
+ * unchanged); LBM_ERR_CUDA if the new graphs cannot be captured (destroy
+ * the plan then). */
 lbm_status lbm_batch_set_launch(lbm_batch_t b, const lbm_launch* l);
 lbm_status lbm_batch_get_launch(lbm_batch_t b, lbm_launch* l);
 
