@@ -1,6 +1,7 @@
 """Accuracy of the float-float exp and log the mixed-precision path uses for
-its Arrhenius rates and temperature (Tang's table-driven exp; log by one
-Newton step from the FP32 logarithm), against numpy's FP64 functions.
+its Arrhenius rates and temperature (Tang's table-driven exp; log from the
+FP32 logarithm y as y + log(1 + t), t = x e^(-y) - 1, to second order in t),
+against numpy's FP64 functions.
 
 Inputs carry at most 48 significant bits, so their float-float split is
 exact and the FP64 reference sees the same argument.  Float-float keeps

@@ -1,10 +1,11 @@
-"""Kernel placement (reaction sub-steps inside the moments kernel or with
-4 / 8 lanes per node in their own kernel; collision fused or split into a
+"""Kernel placement (moments and reaction sub-steps with one thread per node,
+or with groups of 4 / 8 lanes per node; collision fused or split into a
 per-node parameter kernel and a nine-threads-per-node direction kernel) and
 the autotuner that chooses among them.
 
 The placements evaluate the same formulas; only the species production rates
-are summed in another order when the reactions are dealt out over lanes, and
+and the Newton polynomial's terms are summed in another order when the work
+is dealt out over lanes, and
 the compiler may fuse multiply-adds differently in the two collision
 kernels, so they agree to rounding: 1e-13 relative per lattice in FP64.  In
 FP32 storage the rounding differences of the first step grow through the
