@@ -74,6 +74,8 @@ def _workload(name, seed):
     from lbm_workloads import fields
     return {"reactor": lambda: fields.reactor(seed=seed),
             "flame": lambda: fields.flame_1d(seed=seed),
+            "channel": lambda: fields.channel_2d(seed=seed),
+            "tube": lambda: fields.microtube(seed=seed),
             "box": lambda: fields.perturbed_box((128, 64, 64), "D3Q27", seed=seed,
                                                 dx=12.5e-6, amp_u=1.0)}[name]()
 
@@ -82,6 +84,10 @@ WORKLOADS = {"reactor": "homogeneous reactor 16^3 periodic D3Q27, M=9, 21 reacti
                         "phi=0.5, 1200 K (+1e-3 seeded perturbation), 1 atm",
              "flame": "quasi-1D premixed flame 1024x4x4 D3Q27, inlet/outlet, M=9, "
                       "21 reactions, phi=0.5, tanh ignition kernel at x=256",
+             "channel": "2D microchannel 2000x40 D2Q9, TMS walls 300->1500 K ramp, parabolic "
+                        "inlet, LODI outlet, M=9, 21 reactions, phi=0.5",
+             "tube": "3D microtube 600x40x40 D3Q27, circular staircase wall r=19 (TMS, "
+                     "300->1500 K ramp), inlet 1 m/s, LODI outlet, M=9, 21 reactions, phi=0.5",
              "box": "perturbed periodic box 128x64x64 D3Q27, M=9, 21 reactions, "
                     "1400 K +-2%, |u| <= 1 m/s (profiling case larger than L2)"}
 

@@ -369,12 +369,21 @@ lbm_status lbm_ff_check(const double* x, long long n, double* exp_out, double* l
  *  error    optional; set to a message on failure (valid until the next
  *           call on the same thread).
  * The per-node scratch lives in a fixed array inside the library sized for
- * LBM_NOALLOC_MAX_NODES nodes (about 8 MB, held by every GPU that loads
- * the library until the process exits); larger grids return LBM_ERR_RANGE.
+ * LBM_NOALLOC_MAX_NODES nodes: 16 384 x 61 + 32 doubles = 7 995 648 bytes,
+ * held by every GPU that loads the library until the process exits, whether
+ * or not this function is called; larger grids return LBM_ERR_RANGE.
  * Every call shares that array, so calls that overlap on the GPU race.  The
  * first call on a device looks up the array's device address; make it
- * before any stream capture.  The call waits for its stream and returns the
- * step's device status (LBM_ERR_NEWTON, LBM_ERR_NONFINITE). */
+ * before any stream capture.  The address is kept for the life of the
+ * process: after a cudaDeviceReset of that device do not call this again.
+ * The step always runs in the library's fixed placement (one thread per
+ * node for the moments with the reaction sub-steps inline, the fused
+ * collision kernel), which lbm_step uses after
+ * lbm_set_launch({chem_lanes = 1, collide_split = 0}); with that placement
+ * the two agree bit for bit, with another to the rounding of the changed
+ * summation order.  cfg->device must name a present GPU (LBM_ERR_RANGE).
+ * The call waits for its stream and returns the step's device status
+ * (LBM_ERR_NEWTON, LBM_ERR_NONFINITE). */
 #define LBM_NOALLOC_MAX_NODES 16384
 lbm_status lbm_step_noalloc(const lbm_config* cfg, const void* pops_in, void* pops_out,
                             double* T_guess, const char** error);

@@ -232,17 +232,20 @@ def h2_air_synthetic() -> Mechanism:
 
 
 def binary_inert(molar_mass=28.0e-3, D0=2.0e-5, cp_over_R=3.5,
-                 mu0=1.8e-5) -> Mechanism:
-    """Two chemically identical, non-reacting species "A" and "B" of equal
-    molar mass and constant heat capacity: the binary-diffusion and
-    single-fluid test cases (Sec. 2.1 limit of the Stefan-Maxwell model)."""
+                 mu0=1.8e-5, h_formation=(0.0, 0.0)) -> Mechanism:
+    """Two non-reacting species "A" and "B" of equal molar mass and constant
+    heat capacity: the binary-diffusion and single-fluid test cases (Sec. 2.1
+    limit of the Stefan-Maxwell model).  By default chemically identical;
+    h_formation (J/mol) gives them different formation enthalpies, so that
+    interdiffusion carries enthalpy."""
     sp = ["A", "B"]
     comp = np.array([[1.0], [1.0]])
     return Mechanism(
         species=sp, elements=["X"], composition=comp,
         molar_mass=np.array([molar_mass, molar_mass]),
         cp_coeffs=np.array([[cp_over_R, 0.0, 0.0], [cp_over_R, 0.0, 0.0]]),
-        h_formation=np.zeros(2), s_standard=np.array([150.0, 150.0]),
+        h_formation=np.array([float(h) for h in h_formation]),
+        s_standard=np.array([150.0, 150.0]),
         nu_f=np.zeros((0, 2)), nu_r=np.zeros((0, 2)), arrhenius=np.zeros((0, 3)),
         third_body=np.zeros(0, dtype=np.int32), efficiency=np.ones((0, 2)),
         reversible=np.zeros(0, dtype=np.int32),

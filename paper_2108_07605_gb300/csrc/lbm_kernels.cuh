@@ -1,17 +1,27 @@
 // Kernels of the reactive-mixture LBM step (templates; instantiated per
 // lattice, species count and precision by lbm_inst.cu).
 //
-//   k_moments   pull-stream all lattices, moments, temperature Newton,
-//               write the per-node moment record (scratch) and T guess.
+//   k_boundary  one warp per interface node: gather, bounce-back / TMS /
+//               inlet / LODI outlet reconstruction, the node's moment record.
+//   k_chem      the interface nodes' reaction sub-steps (lane groups).
+//   k_moments   one thread per bulk node: pull-stream all lattices, moments,
+//               temperature Newton, the reaction sub-steps, the moment
+//               record (scratch) and the T guess.
+//   k_mchem     the same with a group of lanes per node (small grids).
 //   k_collide   gradients from neighbour records, relaxation parameters,
-//               diffusion velocities, reaction sub-steps, collision of all
-//               lattices on a second pull gather, store to the other buffer.
+//               diffusion velocities, collision of all lattices on a second
+//               pull gather, store to the other buffer (fused collision).
+//   k_prep, k_coll  the same collision split into a per-node parameter
+//               kernel and a nine-threads-per-node direction kernel.
 //   k_init      populations at the equilibria of given fields.
 //   k_out       fields of the stored state (SI units).
+//   k_diag      per-node heat release and flame diagnostics.
 //
 // Template parameters: D (2 or 3), M (species), S (storage type), RT (type
-// of the lattice arithmetic: moments, equilibria, collision).  Temperature,
-// transport, diffusion velocities and chemistry always run in FP64.
+// of the lattice arithmetic: moments, equilibria, collision).  FP64 storage
+// computes everything in FP64.  FP32 and FP16 storage compute the lattice
+// arithmetic and transport in FP32 and the temperature Newton solve and the
+// chemistry in float-float (ff.cuh).
 #include <atomic>
 #include <climits>
 #include <cmath>

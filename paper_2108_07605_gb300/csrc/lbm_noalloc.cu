@@ -11,14 +11,15 @@
 //
 // Limits and behaviour:
 //  - the scratch holds the moment records of at most
-//    LBM_NOALLOC_MAX_NODES nodes (16 384 nodes, about 8 MB, plus the status
-//    word); every GPU that loads this library holds the array until the
-//    process exits;
+//    LBM_NOALLOC_MAX_NODES nodes (16 384 nodes x 61 fields + 32 doubles =
+//    7 995 648 bytes); every GPU that loads this library holds the array
+//    until the process exits;
 //  - every call shares the one array, so calls whose work overlaps on the
 //    GPU (other streams, other host threads) race on it;
 //  - the first call on a device looks up the array's device address with
 //    cudaGetSymbolAddress while that device is current; make that first call
-//    before any stream capture;
+//    before any stream capture.  The address is kept for the life of the
+//    process, so a cudaDeviceReset of that device ends its use here;
 //  - the status word is cleared at each call; the call waits for its stream
 //    to read it back.
 #include <cstring>
@@ -79,9 +80,16 @@ extern "C" lbm_status lbm_step_noalloc(const lbm_config* cfg, const void* pops_i
                       "FP16 offset storage needs the codec a handle keeps (use lbm_create)");
   else if (!pops_in || !pops_out || !T_guess || pops_in == pops_out)
     st = noalloc_fail(LBM_ERR_INVALID, "need distinct device buffers pops_in, pops_out and T_guess");
-  else if (cfg->device >= kMaxDevices)
-    st = noalloc_fail(LBM_ERR_RANGE, "device ordinal beyond the supported 64 devices");
+  else if (cfg->device < 0 || cfg->device >= kMaxDevices)
+    st = noalloc_fail(LBM_ERR_RANGE, "device ordinal outside 0..63");
   else {
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || cfg->device >= ndev)
+      st = noalloc_fail(LBM_ERR_RANGE, "device " + std::to_string(cfg->device) +
+                                           " is not present (" + std::to_string(ndev) +
+                                           " devices)");
+  }
+  if (st == LBM_OK) {
     const long long N = (long long)cfg->nx * cfg->ny * cfg->nz;
     const int D = cfg->lattice == LBM_D3Q27 ? 3 : 2;
     const int NF = record_fields(D, cfg->mech.n_species);
@@ -93,11 +101,11 @@ extern "C" lbm_status lbm_step_noalloc(const lbm_config* cfg, const void* pops_i
     else {
       int prev = -1;
       cudaGetDevice(&prev);
-      if (prev != cfg->device) cudaSetDevice(cfg->device);
+      cudaError_t e = prev != cfg->device ? cudaSetDevice(cfg->device) : cudaSuccess;
       double* scratch = nullptr;
-      cudaError_t e = scratch_on(cfg->device, &scratch);
+      if (e == cudaSuccess) e = scratch_on(cfg->device, &scratch);
       cudaStream_t stream = static_cast<cudaStream_t>(cfg->stream);
-      int* status = reinterpret_cast<int*>(scratch + kRecordDoubles);
+      int* status = scratch ? reinterpret_cast<int*>(scratch + kRecordDoubles) : nullptr;
       if (e == cudaSuccess) e = cudaMemsetAsync(status, 0, sizeof(int), stream);
       if (e == cudaSuccess) {
         DevMech mech;

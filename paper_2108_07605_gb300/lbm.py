@@ -30,6 +30,10 @@ STATUS_NAMES = {0: "LBM_OK", 1: "LBM_ERR_INVALID", 2: "LBM_ERR_OOM", 3: "LBM_ERR
 FACE_KINDS = {"periodic": LBM_PERIODIC, "bounce_back": LBM_BOUNCE_BACK,
               "tms": LBM_TMS_WALL, "inlet": LBM_INLET, "outlet": LBM_OUTLET}
 PRECISIONS = {"fp64": LBM_FP64, "fp32": LBM_FP32_STORE, "fp16": LBM_FP16_OFFSET}
+# the fixed scratch array of lbm_step_noalloc (LBM_NOALLOC_MAX_NODES x 61
+# fields + 32 doubles), resident on every GPU that loads the library
+NOALLOC_MAX_NODES = 16384
+NOALLOC_SCRATCH_BYTES = (NOALLOC_MAX_NODES * 61 + 32) * 8
 
 
 class lbm_mechanism(C.Structure):
@@ -392,9 +396,38 @@ def lbm_destroy(h):
     _check(load_library().lbm_destroy(h), None)
 
 
+def _noalloc_buffer(name, t, dtype, count, device):
+    """The C function cannot see its buffers' sizes, so they are checked
+    here: a contiguous CUDA tensor on `device` of `dtype` with at least
+    `count` elements."""
+    import torch
+    if not (isinstance(t, torch.Tensor) and t.is_cuda):
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if t.device.index != device:
+        raise ValueError(f"{name} is on cuda:{t.device.index}, the config names cuda:{device}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if t.dtype != dtype:
+        raise ValueError(f"{name} must be {dtype}, got {t.dtype}")
+    if t.numel() < count:
+        raise ValueError(f"{name} holds {t.numel()} elements, the grid needs {count}")
+
+
 def lbm_step_noalloc(cfg, pops_in, pops_out, T_guess):
     """One step on caller-owned device buffers with no device allocation
     (for callers that cannot allocate; see include/lbm.h)."""
+    import torch
+    D = 3 if cfg.lattice == LBM_D3Q27 else 2
+    Q = 27 if D == 3 else 9
+    N = int(cfg.nx) * int(cfg.ny) * int(cfg.nz)
+    L = int(cfg.mech.n_species) + 1
+    store = {LBM_FP64: torch.float64, LBM_FP32_STORE: torch.float32,
+             LBM_FP16_OFFSET: torch.float16}.get(int(cfg.precision))
+    if store is None:
+        raise ValueError(f"unknown precision {cfg.precision}")
+    _noalloc_buffer("pops_in", pops_in, store, L * Q * N, int(cfg.device))
+    _noalloc_buffer("pops_out", pops_out, store, L * Q * N, int(cfg.device))
+    _noalloc_buffer("T_guess", T_guess, torch.float64, N, int(cfg.device))
     err = C.c_char_p()
     st = load_library().lbm_step_noalloc(C.byref(cfg), _ptr(pops_in)[0], _ptr(pops_out)[0],
                                          _ptr(T_guess)[0], C.byref(err))

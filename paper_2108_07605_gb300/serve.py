@@ -66,7 +66,9 @@ class Server:
     def __init__(self, mech, budget_bytes, chunk=100, precision="fp32", device=0,
                  max_nodes=0):
         self.mech = mech
-        self.budget = int(budget_bytes)
+        # the library's fixed lbm_step_noalloc scratch is resident on the
+        # device as soon as the library is loaded: it counts against the budget
+        self.budget = int(budget_bytes) - lbm.NOALLOC_SCRATCH_BYTES
         self.max_nodes = int(max_nodes)   # 0: no cap on resident nodes
         self.used = 0
         self.chunk = int(chunk)
