@@ -159,6 +159,14 @@ typedef struct lbm_config {
                                  local equilibria (u and T take local values,
                                  not the targets); 0 (default): the full
                                  four-step inlet                              */
+  int chem_fp64;              /* with LBM_FP32_STORE: 1 runs the temperature
+                                 Newton solves (Sec. 3.1 Eq. temperature) and
+                                 the reaction sub-steps (Sec. 2.4 Eq. R3) in
+                                 native FP64 instead of float-float; the
+                                 populations, moments, transport and
+                                 collision stay FP32.  Ignored for LBM_FP64;
+                                 LBM_ERR_INVALID with LBM_FP16_OFFSET.
+                                 Default 0.                                   */
 } lbm_config;
 
 /* Derived lattice-unit data of a handle. */
@@ -348,6 +356,15 @@ lbm_status lbm_destroy(lbm_t h);
  * LBM_ERR_RANGE for n > 2^24, LBM_ERR_CUDA on a device error (message in
  * lbm_last_error(NULL)). */
 lbm_status lbm_ff_check(const double* x, long long n, double* exp_out, double* log_out);
+
+/* Measured fused-multiply-add throughput of the current device in TFLOP/s
+ * (2 FLOP per FMA), FP64 when fp64 != 0, else FP32.  No counterpart in the
+ * paper: the ALU roof against which the step's executed operation counts
+ * are reported.  Eight independent FMA chains per thread, eight 256-thread
+ * blocks per SM, best of three timed launches.  Synchronous; allocates and
+ * frees one element of device memory.  LBM_ERR_INVALID for a NULL tflops,
+ * LBM_ERR_CUDA on a device error. */
+lbm_status lbm_fma_peak(int fp64, double* tflops);
 
 /* Allocation-free single step.  The paper has no counterpart: this entry
  * point exists for callers that cannot allocate device memory themselves -

@@ -24,11 +24,13 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # longest compile is one instantiation, not all of them
 UNITS = [("lbm_capi.cu", "lbm_capi.o", []),
          ("lbm_noalloc.cu", "lbm_noalloc.o", []),
+         ("lbm_probe.cu", "lbm_probe.o", []),
          ("lbm_dispatch.cu", "lbm_dispatch.o", [])]
 for _d, _m in ((3, 9), (3, 2), (2, 9), (2, 2)):
-    for _prec, _tag in ((0, "f64"), (1, "f32"), (2, "f16")):
+    for _prec, _tag in ((0, "f64"), (1, "f32"), (2, "f16"), (3, "c64")):
         UNITS.append(("lbm_inst.cu", f"lbm_inst_{_d}_{_m}_{_tag}.o",
                       [f"-DLBM_D={_d}", f"-DLBM_M={_m}", f"-DLBM_PREC={_prec}",
+                       f"-DLBM_CHEM64={1 if _prec == 3 else 0}",
                        f"-DLBM_KSET=kernel_set_{_d}_{_m}_{_tag}"]))
 
 

@@ -99,10 +99,12 @@ void fill_domains(lbm_ctx* const* hs, int n, const Launch& lc, std::vector<Domai
     d.mech = h->mech_dev;
     d.block_begin = gr.nblocks;
     d.bblock_begin = gr.nbblocks;
+    d.tblock_begin = gr.ntblocks;
     d.cblock_begin = gr.ncblocks;
     d.kblock_begin = gr.nkblocks;
     gr.nblocks += (int)((h->g.N + 127) / 128);
     gr.nbblocks += (h->bc.n_if + 3) / 4;
+    gr.ntblocks += (h->bc.n_if + kBndNodesPerBlock - 1) / kBndNodesPerBlock;
     if (lc.chem_lanes > 1) {
       const int per = 128 / lc.chem_lanes;
       gr.ncblocks += (int)((h->g.N + per - 1) / per);
@@ -152,6 +154,9 @@ std::string validate(const lbm_config* c) {
   if (c->precision != LBM_FP64 && c->precision != LBM_FP32_STORE &&
       c->precision != LBM_FP16_OFFSET)
     return "precision must be LBM_FP64, LBM_FP32_STORE or LBM_FP16_OFFSET";
+  if (c->chem_fp64 != 0 && c->chem_fp64 != 1) return "chem_fp64 must be 0 or 1";
+  if (c->chem_fp64 && c->precision == LBM_FP16_OFFSET)
+    return "chem_fp64 is supported with LBM_FP32_STORE (and implied by LBM_FP64)";
   if (c->substeps < 1 || c->substeps > 64) return "substeps must be in 1..64";
   if (!(c->dx > 0.0) || !std::isfinite(c->dx)) return "dx must be positive";
   if (c->c_ref < 0.0 || !std::isfinite(c->c_ref)) return "c_ref must be >= 0";
@@ -562,7 +567,7 @@ lbm_status init_common(lbm_ctx* h, const double* rho_or_P, int is_pressure, cons
     const lbm_status st = init_fp16(h, drho, is_pressure, du, dT, dY);
     if (st != LBM_OK) return st;
   } else {
-    e = launch_init(h->D, M, h->cfg.precision, h->mech, h->g, h->un, drho, is_pressure, du, dT,
+    e = launch_init(h->D, M, kernel_precision(h->cfg), h->mech, h->g, h->un, drho, is_pressure, du, dT,
                     dY, h->pops[h->cur], h->Tf, h->status, h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "init kernel");
   }
@@ -802,7 +807,7 @@ lbm_status lbm_step(lbm_t h, int nsteps) {
   for (int k = 0; k < nsteps; ++k) {
     a.src = h->pops[h->cur];
     a.dst = h->pops[1 - h->cur];
-    cudaError_t e = launch_step(h->D, h->M, h->cfg.precision, h->mech, a, h->stream);
+    cudaError_t e = launch_step(h->D, h->M, kernel_precision(h->cfg), h->mech, a, h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "step launch");
     h->cur = 1 - h->cur;
     ++h->steps;
@@ -837,10 +842,10 @@ lbm_status lbm_step_timed(lbm_t h, int nsteps, double* kernel_ms, int n_kernels)
     a.src = h->pops[h->cur];
     a.dst = h->pops[1 - h->cur];
     cudaEventRecord(ev[3 * k], h->stream);
-    err = launch_step(h->D, h->M, h->cfg.precision, h->mech, a, h->stream, 0);
+    err = launch_step(h->D, h->M, kernel_precision(h->cfg), h->mech, a, h->stream, 0);
     cudaEventRecord(ev[3 * k + 1], h->stream);
     if (err == cudaSuccess)
-      err = launch_step(h->D, h->M, h->cfg.precision, h->mech, a, h->stream, 1);
+      err = launch_step(h->D, h->M, kernel_precision(h->cfg), h->mech, a, h->stream, 1);
     cudaEventRecord(ev[3 * k + 2], h->stream);
     h->cur = 1 - h->cur;
     ++h->steps;
@@ -915,10 +920,10 @@ lbm_status lbm_autotune(lbm_t h, int trial_steps, lbm_launch* chosen) {
   for (const Launch& cand : kCandidates) {
     if (e != cudaSuccess) break;
     a.lc = cand;
-    e = launch_step(h->D, h->M, h->cfg.precision, h->mech, a, h->stream);   // warm-up
+    e = launch_step(h->D, h->M, kernel_precision(h->cfg), h->mech, a, h->stream);   // warm-up
     if (e == cudaSuccess) e = cudaEventRecord(e0, h->stream);
     for (int t = 0; t < trial_steps && e == cudaSuccess; ++t)
-      e = launch_step(h->D, h->M, h->cfg.precision, h->mech, a, h->stream);
+      e = launch_step(h->D, h->M, kernel_precision(h->cfg), h->mech, a, h->stream);
     if (e == cudaSuccess) e = cudaEventRecord(e1, h->stream);
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(h->Tf, Tsave, tbytes, cudaMemcpyDeviceToDevice, h->stream);
@@ -955,6 +960,7 @@ lbm_status lbm_batch_step(lbm_t* hs, int n, int nsteps) {
     lbm_ctx* h = hs[k];
     if (!h->initialized) return fail(h0, LBM_ERR_STATE, "lbm_batch_step before lbm_init_fields");
     if (h->D != h0->D || h->M != h0->M || h->cfg.precision != h0->cfg.precision ||
+        kernel_precision(h->cfg) != kernel_precision(h0->cfg) ||
         h->cfg.device != h0->cfg.device)
       return fail(h0, LBM_ERR_INVALID,
                   "batched handles must share lattice, species count, precision and device");
@@ -982,7 +988,7 @@ lbm_status lbm_batch_step(lbm_t* hs, int n, int nsteps) {
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(ddev, doms.data(), n * sizeof(DomainDev), cudaMemcpyHostToDevice, s0);
   for (int step = 0; step < nsteps && e == cudaSuccess; ++step)
-    e = launch_batch_step(h0->D, h0->M, h0->cfg.precision, ddev, n, gr, lc, step & 1, s0);
+    e = launch_batch_step(h0->D, h0->M, kernel_precision(h0->cfg), ddev, n, gr, lc, step & 1, s0);
   if (e == cudaSuccess) e = cudaEventRecord(ev, s0);
   for (int k = 1; k < n && e == cudaSuccess; ++k)
     if (hs[k]->stream != s0) e = cudaStreamWaitEvent(hs[k]->stream, ev, 0);
@@ -1031,7 +1037,7 @@ cudaError_t batch_capture(lbm_batch_ctx* b, int first_parity, int nsteps, cudaGr
   cudaGraph_t graph = nullptr;
   cudaError_t e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
   for (int k = 0; k < nsteps && e == cudaSuccess; ++k)
-    e = launch_batch_step(h0->D, h0->M, h0->cfg.precision, b->ddev, (int)b->hs.size(), b->gr,
+    e = launch_batch_step(h0->D, h0->M, kernel_precision(h0->cfg), b->ddev, (int)b->hs.size(), b->gr,
                           b->lc, (first_parity + k) & 1, b->stream, b->side);
   const cudaError_t e2 = cudaStreamEndCapture(b->stream, &graph);
   if (e == cudaSuccess) e = e2;
@@ -1096,7 +1102,7 @@ lbm_status lbm_batch_create(lbm_t* hs, int n, lbm_batch_t* out) {
   }
   b->lc = resolve_launch(lbm_launch{-1, -1, -1}, total_nodes(hs, n), hs[0]->cfg.precision);
   if (e == cudaSuccess) e = batch_upload(b);
-  if (e == cudaSuccess) e = prepare_batch_step(h0->D, h0->M, h0->cfg.precision);
+  if (e == cudaSuccess) e = prepare_batch_step(h0->D, h0->M, kernel_precision(h0->cfg));
   if (e == cudaSuccess) e = batch_capture_all(b);
   if (e != cudaSuccess) {
     lbm_batch_destroy(b);
@@ -1207,11 +1213,11 @@ lbm_status lbm_batch_autotune(lbm_batch_t b, int trial_steps, lbm_launch* chosen
     // parity 0 every time: each trial step recomputes the next state of every
     // handle from its current buffer, advancing none of them
     if (e == cudaSuccess)
-      e = launch_batch_step(h0->D, h0->M, h0->cfg.precision, b->ddev, n, b->gr, b->lc, 0,
+      e = launch_batch_step(h0->D, h0->M, kernel_precision(h0->cfg), b->ddev, n, b->gr, b->lc, 0,
                             b->stream, b->side);
     if (e == cudaSuccess) e = cudaEventRecord(e0, b->stream);
     for (int t = 0; t < trial_steps && e == cudaSuccess; ++t)
-      e = launch_batch_step(h0->D, h0->M, h0->cfg.precision, b->ddev, n, b->gr, b->lc, 0,
+      e = launch_batch_step(h0->D, h0->M, kernel_precision(h0->cfg), b->ddev, n, b->gr, b->lc, 0,
                             b->stream, b->side);
     if (e == cudaSuccess) e = cudaEventRecord(e1, b->stream);
     for (int k = 0; k < n && e == cudaSuccess; ++k)
@@ -1252,7 +1258,7 @@ lbm_status lbm_moments(lbm_t h, double* rho, double* u, double* T, double* Y, do
   const long long N = h->g.N;
   const int M = h->M;
   if (on_device) {
-    cudaError_t e = launch_moments_out(h->D, M, h->cfg.precision, h->mech, h->g, h->un,
+    cudaError_t e = launch_moments_out(h->D, M, kernel_precision(h->cfg), h->mech, h->g, h->un,
                                        h->pops[h->cur], h->Tf, rho, u, T, Y, E, h->status,
                                        h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "moments kernel");
@@ -1263,7 +1269,7 @@ lbm_status lbm_moments(lbm_t h, double* rho, double* u, double* T, double* Y, do
   if (st != LBM_OK) return st;
   double* p = h->io;
   double *drho = p, *du = p + N, *dT = p + 4 * N, *dY = p + 5 * N, *dE = p + (5 + M) * N;
-  cudaError_t e = launch_moments_out(h->D, M, h->cfg.precision, h->mech, h->g, h->un,
+  cudaError_t e = launch_moments_out(h->D, M, kernel_precision(h->cfg), h->mech, h->g, h->un,
                                      h->pops[h->cur], h->Tf, rho ? drho : nullptr,
                                      u ? du : nullptr, T ? dT : nullptr, Y ? dY : nullptr,
                                      E ? dE : nullptr, h->status, h->stream);
@@ -1287,7 +1293,7 @@ lbm_status lbm_diagnostics(lbm_t h, lbm_diag* out) {
   if (st != LBM_OK) return st;
   DiagPart* part = reinterpret_cast<DiagPart*>(h->io);
   DiagPart* dout = part + nb;
-  cudaError_t e = launch_diagnostics(h->D, h->M, h->cfg.precision, h->mech, h->g, h->un,
+  cudaError_t e = launch_diagnostics(h->D, h->M, kernel_precision(h->cfg), h->mech, h->g, h->un,
                                      h->pops[h->cur], h->Tf, h->bc.tag, part, dout, h->status,
                                      h->stream);
   DiagPart r;

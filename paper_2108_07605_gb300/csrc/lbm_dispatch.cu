@@ -10,6 +10,7 @@ namespace lbm {
 #define LBM_DECLARE_SETS(D_, M_)                 \
   const KernelSet* kernel_set_##D_##_##M_##_f64(); \
   const KernelSet* kernel_set_##D_##_##M_##_f32(); \
+  const KernelSet* kernel_set_##D_##_##M_##_c64(); \
   const KernelSet* kernel_set_##D_##_##M_##_f16();
 LBM_DECLARE_SETS(3, 9)
 LBM_DECLARE_SETS(3, 2)
@@ -22,6 +23,7 @@ const KernelSet* kernel_set(int D, int M, lbm_precision prec) {
   if (D == D_ && M == M_) {                                                   \
     if (prec == LBM_FP64) return kernel_set_##D_##_##M_##_f64();              \
     if (prec == LBM_FP32_STORE) return kernel_set_##D_##_##M_##_f32();        \
+    if ((int)prec == LBM_KPREC_FP32_CHEM64) return kernel_set_##D_##_##M_##_c64(); \
     if (prec == LBM_FP16_OFFSET) return kernel_set_##D_##_##M_##_f16();       \
     return nullptr;                                                           \
   }

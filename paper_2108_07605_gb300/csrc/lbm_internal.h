@@ -156,6 +156,7 @@ struct DomainDev {
   void* cpar = nullptr;        // per-node collision parameters (split collision)
   int block_begin = 0;         // first block of this domain in the node grids
   int bblock_begin = 0;        // first block in the boundary grid
+  int tblock_begin = 0;        // first block in the thread-per-interface-node grid (k_bnode)
   int cblock_begin = 0;        // first block in the chemistry grid (k_chem)
   int kblock_begin = 0;        // first block in the split-collision grid (k_coll)
 };
@@ -170,10 +171,14 @@ struct SideStream {
 // Block totals of the batched grids.
 struct BatchGrids {
   int nblocks = 0;    // node kernels, 128 nodes per block
-  int nbblocks = 0;   // boundary kernel, 4 interface nodes per block
+  int nbblocks = 0;   // boundary grid, 4 interface nodes per block (k_chem, k_moments)
+  int ntblocks = 0;   // k_bnode, kBndNodesPerBlock interface nodes per block
   int ncblocks = 0;   // k_chem, 128 / chem_lanes nodes per block (0 without it)
   int nkblocks = 0;   // k_coll, 32 nodes per block (0 without it)
 };
+
+// interface nodes per block of the boundary kernel (one thread each)
+constexpr int kBndNodesPerBlock = 64;
 
 // Batched step: doms is a device array of ndom domains sharing (D, M, prec)
 // and laid out for the placement lc.
@@ -216,8 +221,16 @@ struct KernelSet {
   int record_fields;   // moment-record fields
   int param_fields;    // collision-parameter fields
 };
-// nullptr for an unsupported combination
+// nullptr for an unsupported combination.  Besides the lbm_precision values,
+// prec may be LBM_KPREC_FP32_CHEM64: FP32 storage and lattice arithmetic with
+// the temperature solve and the chemistry in native FP64 (cfg->chem_fp64).
+constexpr int LBM_KPREC_FP32_CHEM64 = 16;
 const KernelSet* kernel_set(int D, int M, lbm_precision prec);
+// the kernel-set precision of a configuration
+inline lbm_precision kernel_precision(const lbm_config& c) {
+  return (c.precision == LBM_FP32_STORE && c.chem_fp64) ? (lbm_precision)LBM_KPREC_FP32_CHEM64
+                                                         : c.precision;
+}
 
 // which: 0 = moments kernel only, 1 = collision kernel only, -1 = both.
 cudaError_t launch_step(int D, int M, lbm_precision prec, const DevMech& mech,

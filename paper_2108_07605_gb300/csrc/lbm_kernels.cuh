@@ -25,12 +25,35 @@
 #include <atomic>
 #include <climits>
 #include <cmath>
+#include <type_traits>
 
 #pragma once
 
 #include "lbm_device.cuh"
 
+// Chemistry mode of the mixed path in this translation unit: with FP32
+// lattice arithmetic, the temperature Newton solve and the reaction
+// chemistry run in float-float (LBM_CHEM64 = 0) or in native FP64
+// (LBM_CHEM64 = 1).  The two modes' templates live in distinct inline
+// namespaces, so both can be instantiated in one library.
+#ifndef LBM_CHEM64
+#define LBM_CHEM64 0
+#endif
+
 namespace lbm {
+#if LBM_CHEM64
+inline namespace chem64 {
+#else
+inline namespace chemff {
+#endif
+
+// float-float Newton and chemistry: FP32 lattice arithmetic, float-float mode
+template <typename RT> constexpr bool kFF = sizeof(RT) == 4 && !LBM_CHEM64;
+// resident blocks per SM the moments kernels are compiled for (register cap):
+// four for the float-float chemistry, two with FP64 chemistry beside FP32
+// lattice arithmetic, one in the FP64 path
+template <typename RT>
+constexpr int kMomentsMinBlocks = kFF<RT> ? 4 : (sizeof(RT) == 4 ? 2 : 1);
 
 // Arithmetic type of a storage type: FP16 storage computes in FP32.
 template <typename S> struct ComputeType { using type = S; };
@@ -148,7 +171,7 @@ __device__ __forceinline__ void moments_finish(RT* __restrict__ rec, double* __r
   bool ok;
   double T;
   RT thR;
-  if constexpr (sizeof(RT) == 4) {
+  if constexpr (kFF<RT>) {
     // mixed path: the temperature solve in float-float
     ff Yf[M];
     float Rm = 0.f;
@@ -184,7 +207,7 @@ __device__ __forceinline__ void moments_finish(RT* __restrict__ rec, double* __r
   if (!chem_inline) {
 #pragma unroll
     for (int a = 0; a < M - 1; ++a) rec[(RC::DRHO + a) * N + n] = rs[a];
-  } else if constexpr (sizeof(RT) == 4) {
+  } else if constexpr (kFF<RT>) {
     const ff Uphys = (ff(ER) + ff(-0.5f * usqR)) * un.c2_f;
     ff r[M], rdot[M];
 #pragma unroll
@@ -400,7 +423,7 @@ template <> struct Chem<ff> {
 };
 
 template <typename RT> struct ChemType { using type = double; };
-template <> struct ChemType<float> { using type = ff; };
+template <> struct ChemType<float> { using type = std::conditional_t<LBM_CHEM64 != 0, double, ff>; };
 
 __device__ __forceinline__ double shfl_ct(unsigned mask, double v, int src) {
   return __shfl_sync(mask, v, src);
@@ -560,7 +583,7 @@ __device__ __forceinline__ void chem_lanes_body(RT* __restrict__ rec,
   }
   const RT ER = rec[RC::E * N + n];
   CT U;
-  if constexpr (sizeof(RT) == 4) U = (ff(ER) + ff(-0.5f * usq)) * un.c2_f;
+  if constexpr (kFF<RT>) U = (ff(ER) + ff(-0.5f * usq)) * un.c2_f;
   else U = (double(ER) - 0.5 * double(usq)) * un.c * un.c;
   // the post-stream species densities the moments kernel left in the
   // increment slots; the slaved species from the mixture density
@@ -579,7 +602,7 @@ __device__ __forceinline__ void chem_lanes_body(RT* __restrict__ rec,
 #pragma unroll
   for (int a = 0; a < M - 1; ++a) {
     if (a % L != sub) continue;
-    if constexpr (sizeof(RT) == 4) rec[(RC::DRHO + a) * N + n] = (r[a] - r0[a]).hi;
+    if constexpr (kFF<RT>) rec[(RC::DRHO + a) * N + n] = (r[a] - r0[a]).hi;
     else rec[(RC::DRHO + a) * N + n] = RT(r[a] - r0[a]);
   }
 }
@@ -683,7 +706,7 @@ __device__ __forceinline__ void mchem_body(const S* __restrict__ src, RT* __rest
   const RT ER = rhoE * inv_rho;
   // temperature (Eq. temperature) from the node's previous T, shared solve
   CT U, r[M];
-  if constexpr (sizeof(RT) == 4) U = (ff(ER) + ff(-0.5f * usqR)) * un.c2_f;
+  if constexpr (kFF<RT>) U = (ff(ER) + ff(-0.5f * usqR)) * un.c2_f;
   else U = (double(ER) - 0.5 * double(usqR)) * un.c * un.c;
 #pragma unroll
   for (int a = 0; a < M; ++a) r[a] = X::of(rs[a]);
@@ -692,7 +715,7 @@ __device__ __forceinline__ void mchem_body(const S* __restrict__ src, RT* __rest
   const CT Tx = group_newton<M, L, CT>(mg, r, irho, U, X::of_T(Tf[n]), un, sub, gmask, ok);
   double T;
   RT thR;
-  if constexpr (sizeof(RT) == 4) {
+  if constexpr (kFF<RT>) {
     float Rm = 0.f;
 #pragma unroll
     for (int a = 0; a < M; ++a) Rm += YR[a] * m.inv_mm_s[a];
@@ -738,7 +761,7 @@ __device__ __forceinline__ void mchem_body(const S* __restrict__ src, RT* __rest
   chem_group_substeps<M, CT, L>(r, irho, U, X::of_T(T), un, mg, sub, gmask, status);
 #pragma unroll
   for (int a = 0; a < M - 1; ++a) {
-    if constexpr (sizeof(RT) == 4) put(RC::DRHO + a, (r[a] - r0[a]).hi);
+    if constexpr (kFF<RT>) put(RC::DRHO + a, (r[a] - r0[a]).hi);
     else put(RC::DRHO + a, RT(r[a] - r0[a]));
   }
 }
@@ -993,7 +1016,7 @@ __device__ __forceinline__ void node_params(const RT* __restrict__ rec,
 #pragma unroll
     for (int a = 0; a < M; ++a) {
       RT Ha;
-      if constexpr (sizeof(RT) == 4) {
+      if constexpr (kFF<RT>) {
         const ff Tf_(T);
         Ha = ((species_U_ff(mech, a, Tf_) + ff(mech.Ra_s[a]) * Tf_) * un.inv_c2_f).hi;
       } else {
@@ -1453,7 +1476,7 @@ __device__ __forceinline__ void eq_prepare_warp(EqSet<D, M, R>& s, const DevMech
                                                 const DevMech& mp, const Units& un, int lane) {
   const bool own = lane < M;
   const int a = own ? lane : 0;
-  if constexpr (sizeof(R) == 8) {
+  if constexpr (!kFF<R>) {
     double Rm = 0.0;
 #pragma unroll
     for (int b = 0; b < M; ++b) {
@@ -1557,7 +1580,7 @@ __device__ __noinline__ void warp_state_of(const R (&v)[M + 1], EqSet<D, M, R>& 
   // the species lanes, then the Newton iterates of newton_T / newton_T_ff
   // (same formulas and stopping rule) on every lane
   bool ok = false;
-  if constexpr (sizeof(R) == 8) {
+  if constexpr (!kFF<R>) {
     using X = Chem<double>;
     const double U = (rhoE / rho - 0.5 * usq) * un.c * un.c;
     double c[4];
@@ -1833,16 +1856,18 @@ __device__ __forceinline__ void boundary_record(const BCDev& bc, R* __restrict__
   }
 }
 
+#include "lbm_bnode.cuh"
+
 // ---------------------------------------------------------------------------
-// Single-domain kernels: one thread per node (moments, collision), one warp
-// per interface node (boundary).
+// Single-domain kernels: one thread per node (moments, collision), one thread
+// (k_bnode) or one warp (k_boundary) per interface node (boundary).
 // node sets of the moments kernel: every node, the nodes without boundary
 // reconstruction, or the interface nodes (after the boundary kernel, which a
 // side stream runs concurrently with the bulk)
 enum { NODES_ALL = 0, NODES_BULK = 1, NODES_INTERFACE = 2 };
 
 template <int D, int M, typename S, typename RT>
-__global__ void __launch_bounds__(128, sizeof(RT) == 4 ? 4 : 1)
+__global__ void __launch_bounds__(128, kMomentsMinBlocks<RT>)
 k_moments(const S* __restrict__ src, RT* __restrict__ rec, double* __restrict__ Tf,
           int* __restrict__ status, const __grid_constant__ Geom g,
           const __grid_constant__ Units un, const __grid_constant__ BCDev bc,
@@ -1959,10 +1984,26 @@ k_boundary(const S* __restrict__ src, const __grid_constant__ BCDev bc,
                              lane);
 }
 
+// One thread per interface node: reconstruction and record (lbm_bnode.cuh);
+// the interface nodes' reaction sub-steps follow in k_chem.
+template <int D, int M, typename S>
+__global__ void __launch_bounds__(kBnd)
+k_bnode(const S* __restrict__ src, const __grid_constant__ BCDev bc, double* __restrict__ Tf,
+        int* __restrict__ status, const __grid_constant__ Geom g,
+        const __grid_constant__ Units un, const __grid_constant__ DevMech mech,
+        typename ComputeType<S>::type* __restrict__ rec) {
+  using R = typename ComputeType<S>::type;
+  extern __shared__ __align__(16) unsigned char bnd_raw[];
+  const int k = blockIdx.x * kBnd + threadIdx.x;
+  if (k >= bc.n_if) return;
+  bnode_body<D, M, S, R>(src, bc, rec, Tf, status, g, un, mech, k,
+                         reinterpret_cast<R*>(bnd_raw) + threadIdx.x);
+}
+
 // ---------------------------------------------------------------------------
 // Batched kernels: the grid is the concatenation of every domain's tiles; a
 // block finds its domain by binary search over the domains' first blocks.
-enum { GRID_NODE = 0, GRID_BOUNDARY = 1, GRID_CHEM = 2, GRID_COLL = 3 };
+enum { GRID_NODE = 0, GRID_BOUNDARY = 1, GRID_CHEM = 2, GRID_COLL = 3, GRID_BNODE = 4 };
 __device__ __forceinline__ int domain_of_block(const DomainDev* __restrict__ d, int ndom,
                                                int b, int grid) {
   int lo = 0, hi = ndom - 1;
@@ -1971,6 +2012,7 @@ __device__ __forceinline__ int domain_of_block(const DomainDev* __restrict__ d, 
     const int first = grid == GRID_BOUNDARY ? d[mid].bblock_begin
                       : grid == GRID_CHEM   ? d[mid].cblock_begin
                       : grid == GRID_COLL   ? d[mid].kblock_begin
+                      : grid == GRID_BNODE  ? d[mid].tblock_begin
                                             : d[mid].block_begin;
     if (first <= b) lo = mid; else hi = mid - 1;
   }
@@ -1982,7 +2024,7 @@ __device__ __forceinline__ int domain_of_block(const DomainDev* __restrict__ d, 
 // launched persistent (a grid sized to the blocks resident on the GPU) each
 // block processes several tiles in turn.
 template <int D, int M, typename S, typename RT>
-__global__ void __launch_bounds__(128, sizeof(RT) == 4 ? 4 : 1)
+__global__ void __launch_bounds__(128, kMomentsMinBlocks<RT>)
 k_moments_batch(const DomainDev* __restrict__ doms, int ndom, int parity, int chem_inline,
                 int node_set, int nblk) {
   for (int b = blockIdx.x; b < nblk; b += gridDim.x) {
@@ -2086,6 +2128,22 @@ k_coll_batch(const DomainDev* __restrict__ doms, int ndom, int parity, int nblk)
                             static_cast<const RT*>(d.cpar), d.g, d.bc, *d.mech,
                             (b - d.kblock_begin) * (long long)kCollNodes,
                             reinterpret_cast<RT*>(coll_raw));
+  }
+}
+
+// One thread per interface node over every domain (the batched k_bnode).
+template <int D, int M, typename S>
+__global__ void __launch_bounds__(kBnd)
+k_bnode_batch(const DomainDev* __restrict__ doms, int ndom, int parity, int nblk) {
+  using R = typename ComputeType<S>::type;
+  extern __shared__ __align__(16) unsigned char bnd_raw[];
+  R* col = reinterpret_cast<R*>(bnd_raw) + threadIdx.x;
+  for (int b = blockIdx.x; b < nblk; b += gridDim.x) {
+    const DomainDev& d = doms[domain_of_block(doms, ndom, b, GRID_BNODE)];
+    const int k = (b - d.tblock_begin) * kBnd + threadIdx.x;
+    if (k >= d.bc.n_if) continue;
+    bnode_body<D, M, S, R>(static_cast<const S*>(d.pops[d.cur0 ^ parity]), d.bc,
+                           static_cast<R*>(d.rec), d.Tf, d.status, d.g, d.un, *d.mech, k, col);
   }
 }
 
@@ -2382,8 +2440,12 @@ static cudaError_t step_impl(const DevMech& mech, const StepArgs& a, cudaStream_
       if (e != cudaSuccess) return e;
       // the interface nodes: records by the boundary warps, sub-steps with
       // eight lanes per node (k_chem), whatever the bulk placement
-      k_boundary<D, M, S><<<(a.bc.n_if + 3) / 4, 128, 0, a.side>>>(
-          src, a.bc, a.Tfield, a.status, a.g, a.un, mech, if_rec ? rec : nullptr, a.mech_dev);
+      if (if_rec)
+        k_bnode<D, M, S><<<blocks_for(a.bc.n_if, kBnd), kBnd, bnode_smem<D, M, RT>(), a.side>>>(
+            src, a.bc, a.Tfield, a.status, a.g, a.un, mech, rec);
+      else
+        k_boundary<D, M, S><<<(a.bc.n_if + 3) / 4, 128, 0, a.side>>>(
+            src, a.bc, a.Tfield, a.status, a.g, a.un, mech, nullptr, a.mech_dev);
       if (!if_rec)
         k_moments<D, M, S, RT><<<blocks_for(a.bc.n_if, bs), bs, 0, a.side>>>(
             src, rec, a.Tfield, a.status, a.g, a.un, a.bc, mech, 1, NODES_INTERFACE);
@@ -2401,10 +2463,12 @@ static cudaError_t step_impl(const DevMech& mech, const StepArgs& a, cudaStream_
       if (e != cudaSuccess) return e;
     } else {
       const bool bnd_rec = a.bc.n_if > 0 && if_rec;
-      if (a.bc.n_if > 0)
+      if (bnd_rec)
+        k_bnode<D, M, S><<<blocks_for(a.bc.n_if, kBnd), kBnd, bnode_smem<D, M, RT>(), s>>>(
+            src, a.bc, a.Tfield, a.status, a.g, a.un, mech, rec);
+      else if (a.bc.n_if > 0)
         k_boundary<D, M, S><<<(a.bc.n_if + 3) / 4, 128, 0, s>>>(
-            src, a.bc, a.Tfield, a.status, a.g, a.un, mech, bnd_rec ? rec : nullptr,
-            a.mech_dev);
+            src, a.bc, a.Tfield, a.status, a.g, a.un, mech, nullptr, a.mech_dev);
       if (chem_sep)
         mchem(s, bnd_rec ? NODES_BULK : NODES_ALL);
       else
@@ -2486,7 +2550,8 @@ static cudaError_t batch_impl(const DomainDev* doms, int ndom, const BatchGrids&
   const int chem_inline = lc.chem_lanes <= 1;
   const bool ps = lc.persistent != 0;
   auto kmom = k_moments_batch<D, M, S, RT>;
-  auto kbnd = k_boundary_batch<D, M, S>;
+  auto kbnd = k_bnode_batch<D, M, S>;
+  const size_t sbnd = bnode_smem<D, M, RT>();
   // the reaction sub-steps in k_chem over a node set (the grid of the set)
   auto chem = [&](int node_set, cudaStream_t st) {
     const int nb = node_set == NODES_INTERFACE ? gr.nbblocks : gr.ncblocks;
@@ -2523,8 +2588,8 @@ static cudaError_t batch_impl(const DomainDev* doms, int ndom, const BatchGrids&
     if (e != cudaSuccess) return e;
     // (the interface nodes: records by the boundary warps, sub-steps with
     // eight lanes per node, whatever the bulk placement)
-    kbnd<<<batch_grid(kbnd, gr.nbblocks, bs, 0, ps), bs, 0, side.stream>>>(doms, ndom, parity, 1,
-                                                                          gr.nbblocks);
+    kbnd<<<batch_grid(kbnd, gr.ntblocks, kBnd, sbnd, ps), kBnd, sbnd, side.stream>>>(
+        doms, ndom, parity, gr.ntblocks);
     chem(NODES_INTERFACE, side.stream);
     e = cudaEventRecord(side.join, side.stream);
     if (e != cudaSuccess) return e;
@@ -2538,8 +2603,8 @@ static cudaError_t batch_impl(const DomainDev* doms, int ndom, const BatchGrids&
   } else {
     const bool bnd_rec = gr.nbblocks > 0;
     if (gr.nbblocks > 0)
-      kbnd<<<batch_grid(kbnd, gr.nbblocks, bs, 0, ps), bs, 0, s>>>(doms, ndom, parity, 1,
-                                                                   gr.nbblocks);
+      kbnd<<<batch_grid(kbnd, gr.ntblocks, kBnd, sbnd, ps), kBnd, sbnd, s>>>(doms, ndom, parity,
+                                                                          gr.ntblocks);
     if (chem_inline)
       kmom<<<batch_grid(kmom, gr.nblocks, bs, 0, ps), bs, 0, s>>>(
           doms, ndom, parity, 1, bnd_rec ? NODES_BULK : NODES_ALL, gr.nblocks);
@@ -2572,4 +2637,5 @@ const KernelSet* make_kernel_set() {
   return &ks;
 }
 
+}  // inline namespace
 }  // namespace lbm

@@ -121,7 +121,7 @@ extern "C" lbm_status lbm_step_noalloc(const lbm_config* cfg, const void* pops_i
         a.g.nz = cfg->nz;
         a.g.N = N;
         fill_units(*cfg, a.un);
-        e = launch_step(D, cfg->mech.n_species, cfg->precision, mech, a, stream);
+        e = launch_step(D, cfg->mech.n_species, kernel_precision(*cfg), mech, a, stream);
       }
       int bits = 0;
       if (e == cudaSuccess)

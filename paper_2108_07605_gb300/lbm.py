@@ -74,6 +74,7 @@ class lbm_config(C.Structure):
         ("newton_max_iter", C.c_int), ("newton_rtol", C.c_double),
         ("dev_alloc", ALLOC_FN), ("dev_free", FREE_FN), ("alloc_user", C.c_void_p),
         ("stream", C.c_void_p), ("device", C.c_int), ("inlet_simplified", C.c_int),
+        ("chem_fp64", C.c_int),
     ]
 
 
@@ -122,6 +123,7 @@ EXPORTS = {
     "lbm_get_info": (C.c_int, [C.c_void_p, C.POINTER(lbm_info)]),
     "lbm_destroy": (C.c_int, [C.c_void_p]),
     "lbm_last_error": (C.c_char_p, [C.c_void_p]),
+    "lbm_fma_peak": (C.c_int, [C.c_int, C.POINTER(C.c_double)]),
     "lbm_step_noalloc": (C.c_int, [C.POINTER(lbm_config), C.c_void_p, C.c_void_p,
                                    C.c_void_p, C.POINTER(C.c_char_p)]),
 }
@@ -435,6 +437,13 @@ def lbm_step_noalloc(cfg, pops_in, pops_out, T_guess):
         raise LBMError(st, err.value.decode() if err.value else "")
 
 
+def lbm_fma_peak(fp64):
+    """Measured FMA throughput (TFLOP/s) of the current device, FP64 or FP32."""
+    out = C.c_double(0.0)
+    _check(load_library().lbm_fma_peak(1 if fp64 else 0, C.byref(out)))
+    return out.value
+
+
 def lbm_last_error(h=None):
     msg = load_library().lbm_last_error(h)
     return msg.decode() if msg else ""
@@ -467,16 +476,20 @@ class _TorchAllocator:
 def make_config(mech, lattice="D3Q27", shape=(16, 16, 16), dx=1e-3, precision="fp64",
                 substeps=2, c_ref=0.0, T_max=3000.0, faces=None, newton_max_iter=50,
                 newton_rtol=1e-13, device=0, stream=None, use_torch_allocator=True,
-                wall_T=None, solid=None, solid_kind="tms", inlet=None, outlet=None):
+                wall_T=None, solid=None, solid_kind="tms", inlet=None, outlet=None,
+                chem_fp64=0):
     """Build an lbm_config from Python values.  Returns (cfg, keepalive).
 
     wall_T: scalar (every TMS face) or a grid array [nz, ny, nx] (per node);
     solid: optional grid array of solid nodes; inlet: dict(u, T, Y, P) with u
-    a 3-vector or a [3, nz, ny, nx] array (m/s); outlet: dict(P, sigma)."""
+    a 3-vector or a [3, nz, ny, nx] array (m/s); outlet: dict(P, sigma);
+    chem_fp64: with precision "fp32", the temperature solve and chemistry in
+    native FP64 instead of float-float."""
     cfg = lbm_config_defaults()
     cfg.lattice = LBM_D3Q27 if lattice == "D3Q27" else LBM_D2Q9
     cfg.nx, cfg.ny, cfg.nz = (int(v) for v in shape)
     cfg.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    cfg.chem_fp64 = int(chem_fp64)
     cfg.substeps = int(substeps)
     cfg.dx = float(dx)
     cfg.c_ref = float(c_ref)

@@ -27,11 +27,14 @@ def make_oracle(mech, w, c_ref=0.0):
 
 
 def make_gpu(mech, w, precision="fp64", c_ref=0.0):
+    """precision: "fp64", "fp32" (float-float chemistry), "fp32c64" (FP32
+    storage with the temperature solve and chemistry in FP64) or "fp16"."""
     from paper_2108_07605_gb300 import lbm
     bc = boundary_spec(w) or {}
+    chem64 = precision == "fp32c64"
     s = lbm.Solver(mech, lattice=w["lattice"], shape=w["shape"], dx=w["dx"],
-                   precision=precision, substeps=w["substeps"], c_ref=c_ref,
-                   T_max=w["T_max"], **bc)
+                   precision="fp32" if chem64 else precision, chem_fp64=int(chem64),
+                   substeps=w["substeps"], c_ref=c_ref, T_max=w["T_max"], **bc)
     s.init_fields_pressure(w["P"], w["u"], w["T"], w["Y"])
     return s
 

@@ -53,15 +53,13 @@ def test_reference_arm_runs_on_rank_zero_only(capsys):
     assert capsys.readouterr().out == ""
 
 
-def test_group_counters_cover_the_default_bench_groups():
-    """Every launch group the default placements of the bench workloads time
-    has a line in profiles/group_counters.txt (the roofline's FLOP counts)."""
+def test_step_counters_cover_the_default_bench_modes():
+    """The default bench workload's headline mode and its float-float
+    variant have a line in profiles/step_counters.txt (the ALU roof's
+    executed FLOP and the measured DRAM traffic)."""
     import bench
-    cases = [("flame", "fp32", 4, True), ("flame", "fp64", 1, True),
-             ("box", "fp32", 1, False), ("box", "fp64", 1, False)]
-    for workload, precision, lanes, has_bnd in cases:
-        for group in bench.launch_groups({"chem_lanes": lanes, "collide_split": 1}, has_bnd):
-            c = bench.group_counters(group, workload, precision)
-            assert c is not None, (group, workload, precision)
-            key = "fp64_flop" if precision == "fp64" else "fp32_flop"
-            assert c[key] > 1000 and c["dram_bytes"] > 0
+    for mode in ("fp64", "fp32"):
+        c = bench.step_counters("tube", mode)
+        assert c is not None, mode
+        key = "fp64_flop" if mode == "fp64" else "fp32_flop"
+        assert c[key] > 1000 and c["dram_bytes"] > 0
