@@ -6,26 +6,32 @@
 // its namespace.
 //
 // Why a thread per node.  A node's procedure is a chain of scalar steps
-// (moment sums over 27 directions x 10 lattices, up to four temperature
-// Newton solves, equilibrium parameters) around three passes over its 270
-// populations.  Spread over a warp (lane = direction), every scalar step and
-// every cross-lane reduction is a full-warp instruction: on GB300, whose
-// FP64 pipes run two lanes per clock per SM, that made the FP64 boundary
-// kernel execute ~63k FP64 FLOP per interface node.  With a thread per node
-// the sums are sequential adds and the scalar steps run once per node; the
-// direction loop index is the same for every thread of a warp, so its
-// branches on c_i are uniform.  Threads are consecutive interface nodes
-// (the list is in node order), so the pull loads of a wall row coalesce.
+// (moment sums over the 270 populations, up to four temperature Newton
+// solves, equilibrium parameters) around three passes over its populations.
+// Spread over a warp (lane = direction), every scalar step and every
+// cross-lane reduction is a full-warp instruction: on GB300, whose FP64
+// pipes run two lanes per clock per SM, that made the FP64 boundary kernel
+// execute ~63k FP64 FLOP per interface node.  With a thread per node the
+// sums are sequential adds and the scalar steps run once per node.  The
+// passes run lattice by lattice (compile-time l) and, inside, direction by
+// direction: the direction index is the same for every thread of a warp,
+// so the branches on c_i are uniform, and each equilibrium population is a
+// product of three entries of per-lattice axis-factor tables (Eq. prod)
+// built once per lattice and state.  Threads are consecutive interface
+// nodes (the list is in node order), so the pull loads of a wall row
+// coalesce.
 //
-// Per-thread arrays (species mass fractions and the TMS local species
-// velocities) live in this thread's shared-memory column, stride kBnd.
+// Per-thread arrays (species mass fractions, the TMS local species
+// velocities, the pull-source node of every direction) live in this
+// thread's shared-memory column, stride kBnd.
 
 constexpr int kBnd = kBndNodesPerBlock;   // threads per block of the boundary kernel
 
-// shared-memory entries per thread: target Y, local Y, local u_a, a spare Y
-template <int D, int M> constexpr int bnode_smem_entries() { return 3 * M + M * D; }
+// shared memory per thread: target Y, local Y, a spare Y and the local u_a
+// (R entries), then the Q pull sources (long long)
+template <int D, int M> constexpr int bnode_col_entries() { return 3 * M + M * D; }
 template <int D, int M, typename R> constexpr size_t bnode_smem() {
-  return sizeof(R) * kBnd * bnode_smem_entries<D, M>();
+  return (sizeof(R) * bnode_col_entries<D, M>() + sizeof(long long) * Lat<D>::Q) * kBnd;
 }
 
 // An equilibrium state of the boundary procedures (Eqs. faEqGeneral,
@@ -34,13 +40,13 @@ template <int D, int M, typename R> constexpr size_t bnode_smem() {
 template <int D, int M, typename R> struct BState {
   R rho, T, th, U;
   R u[D];
-  R* Y;          // [M], stride kBnd
-  R* us;         // [M D] species velocities, stride kBnd (nullptr: u for every species)
+  R* Y;           // [M], stride kBnd
+  R* us;          // [M D] species velocities, stride kBnd (nullptr: u for every species)
   double T_full;  // T to the solve's precision
 };
 
-// theta, U/c^2 of a state from its T and Y (the formulas of eq_prepare_warp:
-// the mixture energy as a sum over species, float-float in the mixed path)
+// theta, U/c^2 of a state from its T and Y (the mixture energy as a sum over
+// species, float-float in the mixed path)
 template <int D, int M, typename R>
 __device__ __forceinline__ void bstate_prepare(BState<D, M, R>& s, const DevMech& m,
                                                const Units& un) {
@@ -68,39 +74,54 @@ __device__ __forceinline__ void bstate_prepare(BState<D, M, R>& s, const DevMech
   }
 }
 
+// Population sums of a node (every lattice): rho, j, the momentum flux
+// tensor P of the f lattice, rho E and q of the g lattice, rho_a and j_a of
+// the stored species.
+template <int D, int M, typename R> struct BSums {
+  R rho, rhoE, j[D], q[D], P[Lat<D>::NP], rs[M], js[M][D];
+};
+
 // The macroscopic state of population sums (Eqs. density1, momentum1,
 // fdensity, f1momMomentum, g0momTotalEnergy, slaving Eq. strongest): rho,
-// u, Y, u_a (reading R5) and T by Newton on Eq. temperature from T_guess
-// (the formulas of warp_state_of), then theta and U/c^2 as bstate_prepare.
+// u, Y, u_a (reading R5) and T by Newton on Eq. temperature from T_guess,
+// then theta and U/c^2 as bstate_prepare.
 template <int D, int M, typename R>
-__device__ __forceinline__ void bstate_of(BState<D, M, R>& s, R rho, R rhoE, const R (&j)[D],
-                                          const R (&rs)[M], const R (&js)[M][D],
+__device__ __forceinline__ void bstate_of(BState<D, M, R>& s, const BSums<D, M, R>& z,
                                           double T_guess, const DevMech& m, const Units& un,
                                           int* status) {
-  s.rho = rho;
+  s.rho = z.rho;
+  const R irho = R(1) / z.rho;
   R usq = R(0);
 #pragma unroll
-  for (int d = 0; d < D; ++d) { s.u[d] = j[d] / rho; usq += s.u[d] * s.u[d]; }
-  R rM = rho, jM[D];
+  for (int d = 0; d < D; ++d) { s.u[d] = z.j[d] * irho; usq += s.u[d] * s.u[d]; }
+  R rM = z.rho, jM[D];
 #pragma unroll
-  for (int d = 0; d < D; ++d) jM[d] = j[d];
+  for (int d = 0; d < D; ++d) jM[d] = z.j[d];
 #pragma unroll
   for (int a = 0; a < M - 1; ++a) {
-    rM -= rs[a];
+    rM -= z.rs[a];
 #pragma unroll
-    for (int d = 0; d < D; ++d) jM[d] -= js[a][d];
+    for (int d = 0; d < D; ++d) jM[d] -= z.js[a][d];
   }
 #pragma unroll
   for (int a = 0; a < M; ++a) {
-    const R ra = a < M - 1 ? rs[a] : rM;
-    s.Y[a * kBnd] = ra / rho;
+    const R ra = a < M - 1 ? z.rs[a] : rM;
+    s.Y[a * kBnd] = ra * irho;
     if (s.us) {
       R ja[D];
 #pragma unroll
-      for (int d = 0; d < D; ++d) ja[d] = a < M - 1 ? js[a][d] : jM[d];
+      for (int d = 0; d < D; ++d) ja[d] = a < M - 1 ? z.js[a][d] : jM[d];
       const bool tiny = species_velocity_undefined<D, R>(ra, ja);
+      if constexpr (sizeof(R) == 8) {
+        // rho_a > 1e-300 when not tiny: 1/rho_a is finite
+        const R ira = tiny ? R(0) : R(1) / ra;
 #pragma unroll
-      for (int d = 0; d < D; ++d) s.us[(a * D + d) * kBnd] = tiny ? s.u[d] : ja[d] / ra;
+        for (int d = 0; d < D; ++d) s.us[(a * D + d) * kBnd] = tiny ? s.u[d] : ja[d] * ira;
+      } else {
+        // FP32: a positive rho_a below ~3e-39 has no finite reciprocal
+#pragma unroll
+        for (int d = 0; d < D; ++d) s.us[(a * D + d) * kBnd] = tiny ? s.u[d] : ja[d] / ra;
+      }
     }
   }
   bool ok;
@@ -108,7 +129,7 @@ __device__ __forceinline__ void bstate_of(BState<D, M, R>& s, R rho, R rhoE, con
     double Y[M];
 #pragma unroll
     for (int a = 0; a < M; ++a) Y[a] = double(s.Y[a * kBnd]);
-    const double U = (double(rhoE / rho) - 0.5 * double(usq)) * un.c * un.c;
+    const double U = (double(z.rhoE * irho) - 0.5 * double(usq)) * un.c * un.c;
     const double T = newton_T<M>(m, Y, U, T_guess, un.newton_max_iter, un.newton_rtol, ok);
     s.T = R(T);
     s.T_full = T;
@@ -116,7 +137,7 @@ __device__ __forceinline__ void bstate_of(BState<D, M, R>& s, R rho, R rhoE, con
     ff Yf[M];
 #pragma unroll
     for (int a = 0; a < M; ++a) Yf[a] = ff(s.Y[a * kBnd]);
-    const ff U = (ff(rhoE / rho) + ff(-0.5f * usq)) * un.c2_f;
+    const ff U = (ff(z.rhoE * irho) + ff(-0.5f * usq)) * un.c2_f;
     const ff T = newton_T_ff<M>(m, Yf, U, ff_from_double(T_guess), un.newton_max_iter,
                                 un.newton_rtol_f, ok);
     s.T = T.hi;
@@ -126,56 +147,103 @@ __device__ __forceinline__ void bstate_of(BState<D, M, R>& s, R rho, R rhoE, con
   bstate_prepare<D, M, R>(s, m, un);
 }
 
-// Per-axis factor Psi_c (Eqs. phi0, phiPlus, phis) for a warp-uniform c.
-template <typename R> __device__ __forceinline__ R bpsi(int c, R xi, R P) {
-  return c == 0 ? R(1) - P : R(0.5) * (c > 0 ? P + xi : P - xi);
+// Per-lattice axis-factor tables of a state (Eqs. phi0, phiPlus, phis,
+// prod): entry k of an axis is the factor for c = k - 1.  PTab: a species
+// or the f lattice, population = pref * prod_d t[d][c_d + 1].  GTab: the g
+// lattice by the closed form of Eq. geq_i, A = Psi_c(u_d, theta + u_d^2),
+// B = Psi_c applied to u_d^2 / 2.
+template <int D, typename R> struct PTab { R pref, t[D][3]; };
+template <int D, typename R> struct GTab { R rho, U, A[D][3], B[D][3]; };
+
+template <typename R> __device__ __forceinline__ R sel3(int c, const R (&t)[3]) {
+  return c < 0 ? t[0] : (c == 0 ? t[1] : t[2]);
 }
 
-// Equilibrium population of lattice l (compile-time) in direction with
-// velocity c (warp-uniform) of state s (Eqs. faEqGeneral, fEqGeneral,
-// gEqGeneral; the energy lattice by the closed form of Eq. geq_i).
 template <int D, int M, int l, typename R>
-__device__ __forceinline__ R beq(const BState<D, M, R>& s, const int (&c)[3], const DevMech& m,
-                                 const Units& un) {
+__device__ __forceinline__ void ptab(const BState<D, M, R>& s, PTab<D, R>& e, const DevMech& m,
+                                     const Units& un) {
+  R th;
   if constexpr (l < M - 1) {
-    R th_l;
-    if constexpr (sizeof(R) == 8) th_l = R(m.Ra[l] * double(s.T) * un.inv_c2);
-    else th_l = m.Ra_s[l] * s.T * un.inv_c2_s;
-    R p = s.rho * s.Y[l * kBnd];
-#pragma unroll
-    for (int d = 0; d < D; ++d) {
-      const R xi = s.us ? s.us[(l * D + d) * kBnd] : s.u[d];
-      p *= bpsi<R>(c[d], xi, th_l + xi * xi);
-    }
-    return p;
-  } else if constexpr (l == M - 1) {
-    R p = s.rho;
-#pragma unroll
-    for (int d = 0; d < D; ++d) p *= bpsi<R>(c[d], s.u[d], s.th + s.u[d] * s.u[d]);
-    return p;
+    if constexpr (sizeof(R) == 8) th = R(m.Ra[l] * double(s.T) * un.inv_c2);
+    else th = m.Ra_s[l] * s.T * un.inv_c2_s;
+    e.pref = s.rho * s.Y[l * kBnd];
   } else {
-    R A[3], B[3], prodA = R(1);
+    th = s.th;
+    e.pref = s.rho;
+  }
 #pragma unroll
-    for (int d = 0; d < D; ++d) {
-      const R ua = s.u[d];
-      const R O1 = s.th * ua + R(0.5) * ua * ua * ua;
-      const R O2 = s.th * s.th + R(2.5) * s.th * ua * ua + R(0.5) * ua * ua * ua * ua;
-      A[d] = bpsi<R>(c[d], ua, s.th + ua * ua);
-      B[d] = c[d] == 0 ? R(0.5) * ua * ua - O2 : R(0.5) * (c[d] > 0 ? O2 + O1 : O2 - O1);
-      prodA *= A[d];
-    }
-    R sumB = R(0);
-#pragma unroll
-    for (int d = 0; d < D; ++d) {
-      R t = B[d];
-#pragma unroll
-      for (int e = 0; e < D; ++e)
-        if (e != d) t *= A[e];
-      sumB += t;
-    }
-    return s.rho * (s.U * prodA + sumB);
+  for (int d = 0; d < D; ++d) {
+    const R xi = (l < M - 1 && s.us) ? s.us[(l * D + d) * kBnd] : s.u[d];
+    const R P = th + xi * xi;
+    e.t[d][0] = R(0.5) * (P - xi);
+    e.t[d][1] = R(1) - P;
+    e.t[d][2] = R(0.5) * (P + xi);
   }
 }
+
+template <int D, int M, typename R>
+__device__ __forceinline__ void gtab(const BState<D, M, R>& s, GTab<D, R>& g) {
+  g.rho = s.rho;
+  g.U = s.U;
+#pragma unroll
+  for (int d = 0; d < D; ++d) {
+    const R ua = s.u[d];
+    const R O1 = s.th * ua + R(0.5) * ua * ua * ua;
+    const R O2 = s.th * s.th + R(2.5) * s.th * ua * ua + R(0.5) * ua * ua * ua * ua;
+    const R P = s.th + ua * ua;
+    g.A[d][0] = R(0.5) * (P - ua);
+    g.A[d][1] = R(1) - P;
+    g.A[d][2] = R(0.5) * (P + ua);
+    g.B[d][0] = R(0.5) * (O2 - O1);
+    g.B[d][1] = R(0.5) * ua * ua - O2;
+    g.B[d][2] = R(0.5) * (O2 + O1);
+  }
+}
+
+template <int D, typename R>
+__device__ __forceinline__ R peval(const PTab<D, R>& e, const int (&c)[3]) {
+  R p = e.pref;
+#pragma unroll
+  for (int d = 0; d < D; ++d) p *= sel3(c[d], e.t[d]);
+  return p;
+}
+
+template <int D, typename R>
+__device__ __forceinline__ R geval(const GTab<D, R>& g, const int (&c)[3]) {
+  R A[D], B[D], prodA = R(1);
+#pragma unroll
+  for (int d = 0; d < D; ++d) {
+    A[d] = sel3(c[d], g.A[d]);
+    B[d] = sel3(c[d], g.B[d]);
+    prodA *= A[d];
+  }
+  R sumB = R(0);
+#pragma unroll
+  for (int d = 0; d < D; ++d) {
+    R t = B[d];
+#pragma unroll
+    for (int e = 0; e < D; ++e)
+      if (e != d) t *= A[e];
+    sumB += t;
+  }
+  return g.rho * (g.U * prodA + sumB);
+}
+
+// Tables of one state for the lattice of the current pass.
+template <int D, int M, typename R> struct ETab {
+  PTab<D, R> p;
+  GTab<D, R> g;
+  template <int l>
+  __device__ __forceinline__ void build(const BState<D, M, R>& s, const DevMech& m,
+                                        const Units& un) {
+    if constexpr (l == M) gtab<D, M, R>(s, g);
+    else ptab<D, M, l, R>(s, p, m, un);
+  }
+  template <int l> __device__ __forceinline__ R eval(const int (&c)[3]) const {
+    if constexpr (l == M) return geval<D, R>(g, c);
+    else return peval<D, R>(p, c);
+  }
+};
 
 // Compile-time loop l = B .. E-1: f(std::integral_constant<int, l>{}).
 template <int B, int E> struct ForL {
@@ -188,63 +256,89 @@ template <int E> struct ForL<E, E> {
   template <typename Fn> __device__ __forceinline__ static void run(Fn&&) {}
 };
 
-// Population sums sum_i v(l, i) and sum_i c_i v(l, i) of every lattice; the
-// functor gives v through fn.begin(i, c) (once per direction) and
-// fn.template get<l>(i, c) (compile-time l).
+// Population sums of a pass, lattice by lattice: fn.template setup<l>()
+// once per lattice, then fn.template get<l>(i, c) for every direction.
 template <int D, int M, typename R, typename F>
-__device__ __forceinline__ void bsums(F& fn, R& rho, R& rhoE, R (&j)[D], R (&rs)[M],
-                                      R (&js)[M][D]) {
-  constexpr int Q = Lat<D>::Q;
-  rho = rhoE = R(0);
+__device__ __forceinline__ void bsums(F& fn, BSums<D, M, R>& z) {
+  constexpr int Q = Lat<D>::Q, NP = Lat<D>::NP;
+  ForL<0, M + 1>::run([&](auto lc) {
+    constexpr int l = decltype(lc)::value;
+    fn.template setup<l>();
+    R sum = R(0), sj[D], sP[NP];
 #pragma unroll
-  for (int d = 0; d < D; ++d) j[d] = R(0);
+    for (int d = 0; d < D; ++d) sj[d] = R(0);
 #pragma unroll
-  for (int a = 0; a < M; ++a) {
-    rs[a] = R(0);
-#pragma unroll
-    for (int d = 0; d < D; ++d) js[a][d] = R(0);
-  }
+    for (int p = 0; p < NP; ++p) sP[p] = R(0);
 #pragma unroll 1
-  for (int i = 0; i < Q; ++i) {
-    const int c[3] = {cvel(i, 0), cvel(i, 1), D == 3 ? cvel(i, 2) : 0};
-    fn.begin(i, c);
-    auto acc = [&](R v, R& sum, R (&sj)[D]) {
+    for (int i = 0; i < Q; ++i) {
+      const int c[3] = {cvel(i, 0), cvel(i, 1), D == 3 ? cvel(i, 2) : 0};
+      const R v = fn.template get<l>(i, c);
       sum += v;
 #pragma unroll
-      for (int d = 0; d < D; ++d)
-        if (c[d] != 0) sj[d] += c[d] > 0 ? v : -v;
-    };
-    ForL<0, M - 1>::run([&](auto lc) {
-      constexpr int l = decltype(lc)::value;
-      acc(fn.template get<l>(i, c), rs[l], js[l]);
-    });
-    acc(fn.template get<M - 1>(i, c), rho, j);
-    rhoE += fn.template get<M>(i, c);
-  }
+      for (int d = 0; d < D; ++d) {
+        if (c[d] == 0) continue;
+        sj[d] += c[d] > 0 ? v : -v;
+        if constexpr (l == M - 1) {
+#pragma unroll
+          for (int e = d; e < D; ++e)
+            if (c[e] != 0) sP[pidx<D>(d, e)] += (c[d] == c[e]) ? v : -v;
+        }
+      }
+    }
+    if constexpr (l < M - 1) {
+      z.rs[l] = sum;
+#pragma unroll
+      for (int d = 0; d < D; ++d) z.js[l][d] = sj[d];
+    } else if constexpr (l == M - 1) {
+      z.rho = sum;
+#pragma unroll
+      for (int d = 0; d < D; ++d) z.j[d] = sj[d];
+#pragma unroll
+      for (int p = 0; p < NP; ++p) z.P[p] = sP[p];
+    } else {
+      z.rhoE = sum;
+#pragma unroll
+      for (int d = 0; d < D; ++d) z.q[d] = sj[d];
+    }
+  });
 }
 
-// Value functors of bsums.  BPull: the pulled population (wrapped source
-// address) or, with bbk and an incoming link, the node's own opposite
-// post-collision population (Eq. bb).
+// Value functors of bsums.  BPull: the pulled population (source node from
+// this thread's column) or, with bbk and an incoming link, the node's own
+// opposite post-collision population (Eq. bb).
 template <int D, int M, typename S, typename R> struct BPull {
   static constexpr int Q = Lat<D>::Q;
   const S* src;
   const float4* codec;
-  long long N, n, sn;
-  int x, y, z;
-  const Geom* g;
+  long long N, n;
+  const long long* sn;      // pull source of direction i at sn[i kBnd]
   unsigned inc;
-  bool in_i, bbk;
-  __device__ __forceinline__ void begin(int i, const int (&)[3]) {
-    in_i = inc >> i & 1u;
-    sn = node_shift<D>(x, y, z, i, -1, *g);
-  }
-  template <int l> __device__ __forceinline__ R get(int i, const int (&)[3]) const {
-    const bool bb = bbk && in_i;
-    const long long mm = bb ? n : sn;
+  bool bbk;
+  __device__ __forceinline__ bool incoming(int i) const { return inc >> i & 1u; }
+  template <int l> __device__ __forceinline__ void setup() {}
+  template <int l> __device__ __forceinline__ R pull(int i) const {
+    const bool bb = bbk && incoming(i);
+    const long long mm = bb ? n : sn[i * kBnd];
     const int ii = bb ? Q - 1 - i : i;
     return Codec<S>::template dec<R>(__ldg(src + (long long)(l * Q + ii) * N + mm), codec,
                                      l * Q + ii);
+  }
+  template <int l> __device__ __forceinline__ R get(int i, const int (&)[3]) const {
+    return pull<l>(i);
+  }
+};
+
+// BPull whose values are also stored as the node's reconstructed populations.
+template <int D, int M, typename S, typename R> struct BStorePull {
+  static constexpr int Q = Lat<D>::Q;
+  BPull<D, M, S, R> p;
+  double* P;
+  long long st;
+  template <int l> __device__ __forceinline__ void setup() {}
+  template <int l> __device__ __forceinline__ R get(int i, const int (&)[3]) const {
+    const R v = p.template pull<l>(i);
+    P[(long long)(l * Q + i) * st] = double(v);
+    return v;
   }
 };
 
@@ -254,24 +348,10 @@ template <int D, int M, typename S, typename R> struct BNode {
   const S* src;
   const float4* codec;
   long long N, node;
-  __device__ __forceinline__ void begin(int, const int (&)[3]) {}
+  template <int l> __device__ __forceinline__ void setup() {}
   template <int l> __device__ __forceinline__ R get(int i, const int (&)[3]) const {
     return Codec<S>::template dec<R>(__ldg(src + (long long)(l * Q + i) * N + node), codec,
                                      l * Q + i);
-  }
-};
-
-// Values written to the node's reconstructed populations as they are summed.
-template <int D, int M, typename R, typename F> struct BStore {
-  static constexpr int Q = Lat<D>::Q;
-  F& f;
-  double* P;
-  long long st;
-  __device__ __forceinline__ void begin(int i, const int (&c)[3]) { f.begin(i, c); }
-  template <int l> __device__ __forceinline__ R get(int i, const int (&c)[3]) const {
-    const R v = f.template get<l>(i, c);
-    P[(long long)(l * Q + i) * st] = double(v);
-    return v;
   }
 };
 
@@ -281,71 +361,99 @@ template <int D, int M, typename S, typename R> struct BLocal {
   const BState<D, M, R>* A;
   const DevMech* m;
   const Units* un;
-  __device__ __forceinline__ void begin(int i, const int (&c)[3]) { p.begin(i, c); }
+  ETab<D, M, R> ta;
+  template <int l> __device__ __forceinline__ void setup() {
+    ta.template build<l>(*A, *m, *un);
+  }
   template <int l> __device__ __forceinline__ R get(int i, const int (&c)[3]) const {
-    return p.in_i ? beq<D, M, l, R>(*A, c, *m, *un) : p.template get<l>(i, c);
+    return p.incoming(i) ? ta.template eval<l>(c) : p.template pull<l>(i);
   }
 };
 
-// Step 4: target + local populations - local equilibria; the simplified
-// inlet takes the local equilibria.
+// Step 4: the target Bt + the local populations - the local equilibria L;
+// the simplified inlet takes the local equilibria.  Stored as the node's
+// reconstructed populations.
 template <int D, int M, typename S, typename R> struct BFinal {
-  BLocal<D, M, S, R>* lo;
+  static constexpr int Q = Lat<D>::Q;
+  BLocal<D, M, S, R> lo;
   const BState<D, M, R>* Bt;
   const BState<D, M, R>* L;
-  bool simple;
-  __device__ __forceinline__ void begin(int i, const int (&c)[3]) { lo->begin(i, c); }
+  bool simple, same;        // same: Bt is the state A of the incoming links
+  double* P;
+  long long st;
+  ETab<D, M, R> tb, tl;
+  template <int l> __device__ __forceinline__ void setup() {
+    lo.template setup<l>();
+    if (!same) tb.template build<l>(*Bt, *lo.m, *lo.un);
+    tl.template build<l>(*L, *lo.m, *lo.un);
+  }
   template <int l> __device__ __forceinline__ R get(int i, const int (&c)[3]) const {
-    const R loc = beq<D, M, l, R>(*L, c, *lo->m, *lo->un);
-    if (simple) return loc;
-    return beq<D, M, l, R>(*Bt, c, *lo->m, *lo->un) + lo->template get<l>(i, c) - loc;
+    const R loc = tl.template eval<l>(c);
+    R v;
+    if (simple) {
+      v = loc;
+    } else if (lo.p.incoming(i)) {
+      const R a = lo.ta.template eval<l>(c);
+      v = (same ? a : tb.template eval<l>(c)) + a - loc;
+    } else {
+      v = (same ? lo.ta.template eval<l>(c) : tb.template eval<l>(c)) +
+          lo.p.template pull<l>(i) - loc;
+    }
+    P[(long long)(l * Q + i) * st] = double(v);
+    return v;
   }
 };
 
 // The boundary procedure of interface node k and its moment record.
+// col: this thread's shared-memory column of R entries, sncol: its column of
+// pull sources (both stride kBnd).
 template <int D, int M, typename S, typename R>
 __device__ __forceinline__ void bnode_body(const S* __restrict__ src, const BCDev& bc,
                                            R* __restrict__ rec, double* __restrict__ Tf,
                                            int* __restrict__ status, const Geom& g,
                                            const Units& un, const DevMech& m, int k,
-                                           R* col) {
+                                           R* col, long long* sncol) {
   constexpr int Q = Lat<D>::Q, NP = Lat<D>::NP;
   using RC = Rec<D, M>;
+  using Pull = BPull<D, M, S, R>;
   const long long N = g.N;
   const long long n = bc.if_node[k];
   const int info = bc.if_info[k];
   const int kind = info & 15;
   const unsigned inc = bc.if_inc[k];
-  const int x = (int)(n % g.nx);
-  const int y = (int)((n / g.nx) % g.ny);
-  const int z = (int)(n / ((long long)g.nx * g.ny));
+  {
+    const int x = (int)(n % g.nx);
+    const int y = (int)((n / g.nx) % g.ny);
+    const int z = (int)(n / ((long long)g.nx * g.ny));
+#pragma unroll 1
+    for (int i = 0; i < Q; ++i) sncol[i * kBnd] = node_shift<D>(x, y, z, i, -1, g);
+  }
   const long long st = bc.n_if;
   const float4* codec = g.codec;
   BState<D, M, R> A, B, L;
   A.Y = col;
   L.Y = col + M * kBnd;
-  L.us = col + 2 * M * kBnd;
-  B.Y = col + (2 * M + M * D) * kBnd;      // spare column (outlet upstream state)
+  B.Y = col + 2 * M * kBnd;                // spare column (outlet upstream state)
+  L.us = col + 3 * M * kBnd;
   A.us = B.us = nullptr;
-  R rho, rhoE, j[D], rs[M], js[M][D];
+  BSums<D, M, R> z;
 
-  using Pull = BPull<D, M, S, R>;
   if (kind == BK_BB) {
     // Eq. bb: incoming links take the node's own opposite post-collision
-    // populations; the record from the result
-    Pull pull{src, codec, N, n, 0, x, y, z, &g, inc, false, true};
-    BStore<D, M, R, Pull> out{pull, bc.pops + k, st};
-    bsums<D, M, R>(out, rho, rhoE, j, rs, js);
+    // populations
+    BStorePull<D, M, S, R> out{Pull{src, codec, N, n, sncol, inc, true}, bc.pops + k, st};
+    bsums<D, M, R>(out, z);
   } else {
     if (kind == BK_TMS) {
       // step 1, Eqs. BBrho and BBY: bounce-back density and mass fractions
-      Pull pull{src, codec, N, n, 0, x, y, z, &g, inc, false, true};
-      bsums<D, M, R>(pull, rho, rhoE, j, rs, js);
-      A.rho = rho;
+      Pull pull{src, codec, N, n, sncol, inc, true};
+      bsums<D, M, R>(pull, z);
+      A.rho = z.rho;
+      const R irho = R(1) / z.rho;
       R ysum = R(0);
 #pragma unroll
       for (int a = 0; a < M - 1; ++a) {
-        const R Ya = rs[a] / rho;
+        const R Ya = z.rs[a] * irho;
         A.Y[a * kBnd] = Ya;
         ysum += Ya;
       }
@@ -371,16 +479,14 @@ __device__ __forceinline__ void bnode_body(const S* __restrict__ src, const BCDe
       const long long stride =
           ax == 0 ? 1 : (ax == 1 ? (long long)g.nx : (long long)g.nx * g.ny);
       const long long up = n - sg * stride;
-      using Node = BNode<D, M, S, R>;
-      BState<D, M, R>& s0 = L;           // columns reused before the local state
-      BState<D, M, R>& s1 = B;
-      L.us = nullptr;
-      Node n0{src, codec, N, n};
-      bsums<D, M, R>(n0, rho, rhoE, j, rs, js);
-      bstate_of<D, M, R>(s0, rho, rhoE, j, rs, js, Tf[n], m, un, status);
-      Node n1{src, codec, N, up};
-      bsums<D, M, R>(n1, rho, rhoE, j, rs, js);
-      bstate_of<D, M, R>(s1, rho, rhoE, j, rs, js, Tf[n], m, un, status);
+      BState<D, M, R> s0 = L, s1 = B;      // the local and spare columns, free until later
+      s0.us = s1.us = nullptr;
+      BNode<D, M, S, R> n0{src, codec, N, n};
+      bsums<D, M, R>(n0, z);
+      bstate_of<D, M, R>(s0, z, Tf[n], m, un, status);
+      BNode<D, M, S, R> n1{src, codec, N, up};
+      bsums<D, M, R>(n1, z);
+      bstate_of<D, M, R>(s1, z, Tf[n], m, un, status);
       double R0 = 0.0, R1 = 0.0, Cv = 0.0;
       const double T0 = s0.T, T1 = s1.T;
 #pragma unroll
@@ -422,16 +528,13 @@ __device__ __forceinline__ void bnode_body(const S* __restrict__ src, const BCDe
       }
       A.T = R(p_o * un.c * un.c / (rho_o * R_U * Ro));
       bstate_prepare<D, M, R>(A, m, un);              // step 1 (Eqs. out_f-out_fa)
-      L.us = col + 2 * M * kBnd;
     }
-    // the local state: incoming links at A, the others as streamed (Eqs.
+    // the local state: incoming links at A, the others pulled (Eqs.
     // locRho-locT and their inlet / outlet analogues)
-    BLocal<D, M, S, R> local{Pull{src, codec, N, n, 0, x, y, z, &g, inc, false, false}, &A,
-                             &m, &un};
-    bsums<D, M, R>(local, rho, rhoE, j, rs, js);
+    BLocal<D, M, S, R> local{Pull{src, codec, N, n, sncol, inc, false}, &A, &m, &un, {}};
+    bsums<D, M, R>(local, z);
     if (kind != BK_TMS) L.us = nullptr;               // TMS local species use u_a^loc
-    bstate_of<D, M, R>(L, rho, rhoE, j, rs, js, Tf[n], m, un, status);
-    const bool simple = kind == BK_INLET && bc.inlet_simplified;
+    bstate_of<D, M, R>(L, z, Tf[n], m, un, status);
     if (kind == BK_INLET) {                           // target (Eqs. in_tgt_*)
       B.rho = L.rho;
       B.Y = L.Y;
@@ -440,43 +543,19 @@ __device__ __forceinline__ void bnode_body(const S* __restrict__ src, const BCDe
       B.T = R(bc.T_in);
       bstate_prepare<D, M, R>(B, m, un);
     }
-    // step 4 (Eqs. ftms-fatms, f_inlet-fa_inlet, f_outlet-fa_outlet):
-    // target + (incoming ? A : streamed) - local; the simplified inlet takes
-    // the local equilibria
-    BFinal<D, M, S, R> fin{&local, kind == BK_INLET ? &B : &A, &L, simple};
-    BStore<D, M, R, BFinal<D, M, S, R>> out{fin, bc.pops + k, st};
-    bsums<D, M, R>(out, rho, rhoE, j, rs, js);
+    // step 4 (Eqs. ftms-fatms, f_inlet-fa_inlet, f_outlet-fa_outlet)
+    BFinal<D, M, S, R> fin{local, &B, &L, kind == BK_INLET && bc.inlet_simplified != 0,
+                           kind != BK_INLET, bc.pops + k, st, {}, {}};
+    bsums<D, M, R>(fin, z);
   }
 
-  // the record from the reconstructed populations (as boundary_record): the
-  // state (Newton from the node's previous T), the energy flux and the
-  // momentum flux tensor; the reaction sub-steps are left to k_chem
-  R q[D], Pt[NP];
-  {
-    const double* P = bc.pops + k;
-#pragma unroll
-    for (int d = 0; d < D; ++d) q[d] = R(0);
-#pragma unroll
-    for (int p = 0; p < NP; ++p) Pt[p] = R(0);
-#pragma unroll 1
-    for (int i = 0; i < Q; ++i) {
-      const int c[3] = {cvel(i, 0), cvel(i, 1), D == 3 ? cvel(i, 2) : 0};
-      const R vf = R(P[(long long)((M - 1) * Q + i) * st]);
-      const R vg = R(P[(long long)(M * Q + i) * st]);
-#pragma unroll
-      for (int d = 0; d < D; ++d) {
-        if (c[d] == 0) continue;
-        q[d] += c[d] > 0 ? vg : -vg;
-#pragma unroll
-        for (int e = d; e < D; ++e)
-          if (c[e] != 0) Pt[pidx<D>(d, e)] += (c[d] * c[e] > 0) ? vf : -vf;
-      }
-    }
-  }
+  // the record from the reconstructed populations (the fields the moments
+  // kernel records: state with Newton from the node's previous T, energy
+  // flux, momentum flux tensor); the reaction sub-steps are left to k_chem
   BState<D, M, R> s;
   s.Y = A.Y;                                    // the target columns are free now
-  s.us = L.us ? L.us : col + 2 * M * kBnd;
-  bstate_of<D, M, R>(s, rho, rhoE, j, rs, js, Tf[n], m, un, status);
+  s.us = col + 3 * M * kBnd;
+  bstate_of<D, M, R>(s, z, Tf[n], m, un, status);
   if (!(s.rho > R(0)) || !isfinite(double(s.rho)) || !isfinite(s.T_full))
     atomicOr(status, ST_NONFINITE);
   Tf[n] = s.T_full;
@@ -499,13 +578,13 @@ __device__ __forceinline__ void bnode_body(const S* __restrict__ src, const BCDe
 #pragma unroll
   for (int d = 0; d < D; ++d) {
     rec[(RC::U + d) * N + n] = s.u[d];
-    rec[(RC::QF + d) * N + n] = q[d];
+    rec[(RC::QF + d) * N + n] = z.q[d];
     rec[(RC::PHI + d) * N + n] =
         rr * s.u[d] * (R(1) - R(3) * thR) - rr * s.u[d] * s.u[d] * s.u[d];
   }
 #pragma unroll
-  for (int p = 0; p < NP; ++p) rec[(RC::P + p) * N + n] = Pt[p];
-  rec[RC::E * N + n] = rhoE * (R(1) / rr);
+  for (int p = 0; p < NP; ++p) rec[(RC::P + p) * N + n] = z.P[p];
+  rec[RC::E * N + n] = z.rhoE * (R(1) / rr);
 #pragma unroll
   for (int a = 0; a < M; ++a) {
     rec[(RC::Y + a) * N + n] = s.Y[a * kBnd];

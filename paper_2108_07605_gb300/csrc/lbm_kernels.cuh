@@ -1997,7 +1997,10 @@ k_bnode(const S* __restrict__ src, const __grid_constant__ BCDev bc, double* __r
   const int k = blockIdx.x * kBnd + threadIdx.x;
   if (k >= bc.n_if) return;
   bnode_body<D, M, S, R>(src, bc, rec, Tf, status, g, un, mech, k,
-                         reinterpret_cast<R*>(bnd_raw) + threadIdx.x);
+                         reinterpret_cast<R*>(bnd_raw) + threadIdx.x,
+                         reinterpret_cast<long long*>(
+                             bnd_raw + sizeof(R) * bnode_col_entries<D, M>() * kBnd) +
+                             threadIdx.x);
 }
 
 // ---------------------------------------------------------------------------
@@ -2138,12 +2141,16 @@ k_bnode_batch(const DomainDev* __restrict__ doms, int ndom, int parity, int nblk
   using R = typename ComputeType<S>::type;
   extern __shared__ __align__(16) unsigned char bnd_raw[];
   R* col = reinterpret_cast<R*>(bnd_raw) + threadIdx.x;
+  long long* sncol =
+      reinterpret_cast<long long*>(bnd_raw + sizeof(R) * bnode_col_entries<D, M>() * kBnd) +
+      threadIdx.x;
   for (int b = blockIdx.x; b < nblk; b += gridDim.x) {
     const DomainDev& d = doms[domain_of_block(doms, ndom, b, GRID_BNODE)];
     const int k = (b - d.tblock_begin) * kBnd + threadIdx.x;
     if (k >= d.bc.n_if) continue;
     bnode_body<D, M, S, R>(static_cast<const S*>(d.pops[d.cur0 ^ parity]), d.bc,
-                           static_cast<R*>(d.rec), d.Tf, d.status, d.g, d.un, *d.mech, k, col);
+                           static_cast<R*>(d.rec), d.Tf, d.status, d.g, d.un, *d.mech, k, col,
+                           sncol);
   }
 }
 
