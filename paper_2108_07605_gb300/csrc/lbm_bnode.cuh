@@ -269,19 +269,32 @@ __device__ __forceinline__ void bsums(F& fn, BSums<D, M, R>& z) {
     for (int d = 0; d < D; ++d) sj[d] = R(0);
 #pragma unroll
     for (int p = 0; p < NP; ++p) sP[p] = R(0);
-#pragma unroll 1
-    for (int i = 0; i < Q; ++i) {
-      const int c[3] = {cvel(i, 0), cvel(i, 1), D == 3 ? cvel(i, 2) : 0};
-      const R v = fn.template get<l>(i, c);
-      sum += v;
+    // directions in rows of three (c_x = -1, 0, 1 at compile time), so that
+    // a row's loads are in flight together; in FP32, where the pass waits
+    // on memory rather than on the FP64 pipe, three rows at a time
+    constexpr int kRows = 1;
+#pragma unroll kRows
+    for (int yz = 0; yz < Q / 3; ++yz) {
+      const int cy = yz % 3 - 1, cz = D == 3 ? yz / 3 - 1 : 0;
+      R v[3];
 #pragma unroll
-      for (int d = 0; d < D; ++d) {
-        if (c[d] == 0) continue;
-        sj[d] += c[d] > 0 ? v : -v;
-        if constexpr (l == M - 1) {
+      for (int k = 0; k < 3; ++k) {
+        const int c[3] = {k - 1, cy, cz};
+        v[k] = fn.template get<l>(3 * yz + k, c);
+      }
 #pragma unroll
-          for (int e = d; e < D; ++e)
-            if (c[e] != 0) sP[pidx<D>(d, e)] += (c[d] == c[e]) ? v : -v;
+      for (int k = 0; k < 3; ++k) {
+        const int c[3] = {k - 1, cy, cz};
+        sum += v[k];
+#pragma unroll
+        for (int d = 0; d < D; ++d) {
+          if (c[d] == 0) continue;
+          sj[d] += c[d] > 0 ? v[k] : -v[k];
+          if constexpr (l == M - 1) {
+#pragma unroll
+            for (int e = d; e < D; ++e)
+              if (c[e] != 0) sP[pidx<D>(d, e)] += (c[d] == c[e]) ? v[k] : -v[k];
+          }
         }
       }
     }
