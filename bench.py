@@ -139,7 +139,8 @@ def fluid_nodes(w):
 def boundary_spec(w):
     """Boundary description of a workload (faces, inlet, outlet, walls,
     solid nodes), or None for a periodic box."""
-    keys = ("faces", "inlet", "outlet", "wall_T", "solid", "solid_kind")
+    keys = ("faces", "inlet", "outlet", "wall_T", "solid", "solid_kind", "wall_dist",
+            "wall_normal")
     if all(f == "periodic" for f in w.get("faces", ("periodic",) * 6)) and w.get("solid") is None:
         return None
     return {k: w[k] for k in keys if k in w}

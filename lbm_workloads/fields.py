@@ -157,13 +157,29 @@ def channel_2d(seed=0, nx=2000, ny=40, phi=0.5, T_in=300.0, dx=25e-6, steps=5000
     return w
 
 
+def pipe_wall_geometry(ny, nz, radius):
+    """The circular wall (y - c)^2 + (z - c)^2 = radius^2, c = (n-1)/2, as
+    grid data: the solid mask of the cross-section, and for every node its
+    normal distance to the wall (radius - r) and inward unit normal
+    (0, -(y - c)/r, -(z - c)/r).  Returns (solid [nz, ny], dist [nz, ny],
+    normal [3, nz, ny])."""
+    cy, cz = (ny - 1) / 2.0, (nz - 1) / 2.0
+    zz, yy = np.meshgrid(np.arange(nz), np.arange(ny), indexing="ij")
+    r = np.sqrt((yy - cy) ** 2 + (zz - cz) ** 2)
+    rs = np.where(r > 0, r, 1.0)
+    normal = np.stack([np.zeros_like(r), -(yy - cy) / rs, -(zz - cz) / rs])
+    return r >= radius, radius - r, normal
+
+
 def microtube(seed=0, nx=600, ny=40, nz=40, radius=19.0, phi=0.5, T_in=300.0,
-              u_in=1.0, dx=25e-6, steps=20000, mech=None):
+              u_in=1.0, dx=25e-6, steps=20000, mech=None, offgrid=False):
     """3-D microtube: D3Q27 nx x ny x nz, fluid where
     (y - c)^2 + (z - c)^2 < radius^2 (c = (ny-1)/2), staircase solid elsewhere
     with Tamm-Mott-Smith walls at the wall_ramp temperature; inlet of fresh
     mixture at u_in at x = 0, pressure outlet at x = nx-1; initial velocity
-    u_in (1 + 0.01 N(0,1)) seeded, T = wall temperature of the column."""
+    u_in (1 + 0.01 N(0,1)) seeded, T = wall temperature of the column.
+    offgrid: also give the wall's normal distance and inward normal per node
+    (wall_dist, wall_normal), for targets interpolated off the grid."""
     mech = mech or h2_air_synthetic()
     rng = philox(seed)
     Y = mole_to_mass_fractions(mech, air_mole_fractions(mech, phi))
@@ -182,6 +198,10 @@ def microtube(seed=0, nx=600, ny=40, nz=40, radius=19.0, phi=0.5, T_in=300.0,
              inlet=dict(u=np.array([u_in, 0.0, 0.0]), T=T_in, Y=Y, P=P_STANDARD),
              outlet=dict(P=P_STANDARD), steps=steps, seed=seed,
              name=f"microtube {nx}x{ny}x{nz} D3Q27 r={radius} phi={phi}")
+    if offgrid:
+        _, dist, normal = pipe_wall_geometry(ny, nz, radius)
+        w["wall_dist"] = np.broadcast_to(dist[:, :, None], (nz, ny, nx)).copy()
+        w["wall_normal"] = np.broadcast_to(normal[:, :, :, None], (3, nz, ny, nx)).copy()
     return w
 
 

@@ -123,6 +123,57 @@ class Boundaries:
         if np.any((self.node_kind == 2) & (self.wall_T is None)):
             raise ValueError("TMS walls need wall_T")
         self.ext = ext
+        self._offgrid_targets(spec)
+
+    def _offgrid_targets(self, spec):
+        """Off-grid TMS targets (Sec. 4.2.2, last paragraph; reading R20).
+        With spec["wall_dist"] (normal distance delta >= 0 from each node to
+        the wall, lattice units) and spec["wall_normal"] ([3, ...] inward
+        unit normal n), a TMS node x interpolates its targets linearly along
+        the normal between the wall (at -delta) and the fluid node
+        x_f = x + c_k (at h = c_k . n), c_k the lattice vector most aligned
+        with n:  phi^tgt = (h phi^wall + delta phi(x_f)) / (h + delta), for
+        u, u_a (wall values 0) and T.  phi(x_f) are the fields of the stored
+        post-collision state of x_f.  Nodes whose x_f is solid or beyond a
+        non-periodic face keep the wall values (reading R12)."""
+        self.og_nodes = None
+        wd, wn = spec.get("wall_dist"), spec.get("wall_normal")
+        if wd is None or wn is None:
+            return
+        lbm = self.lbm
+        vs = lbm.vs
+        D = vs.dim
+        nz, ny, nx = lbm.shape
+        ext = (nx, ny, nz)
+        wd = np.broadcast_to(np.asarray(wd, dtype=float), lbm.shape).ravel()
+        wn = np.asarray(wn, dtype=float).reshape(3, -1)[:D]
+        c = vs.c.astype(float)
+        nonzero = np.array([i for i in range(vs.Q) if np.any(vs.c[i])])
+        cn = c[nonzero] / np.linalg.norm(c[nonzero], axis=1)[:, None]
+        nodes, nbr, h, delta = [], [], [], []
+        for node in np.nonzero((self.node_kind == 2).ravel())[0]:
+            n_hat = wn[:, node]
+            k = nonzero[int(np.argmax(cn @ n_hat))]
+            xyz = [node % nx, (node // nx) % ny, node // (nx * ny)]
+            ok = True
+            for a in range(D):
+                s_a = xyz[a] + int(vs.c[k][a])
+                if s_a < 0 or s_a >= ext[a]:
+                    if self.faces[2 * a + (1 if s_a >= ext[a] else 0)] != 0:
+                        ok = False
+                    s_a %= ext[a]
+                xyz[a] = s_a
+            f = xyz[0] + nx * (xyz[1] + ny * xyz[2])
+            if not ok or self.solid.ravel()[f]:
+                continue
+            nodes.append(node)
+            nbr.append(f)
+            h.append(float(c[k] @ n_hat))
+            delta.append(float(wd[node]))
+        self.og_nodes = np.array(nodes, dtype=int)
+        self.og_nbr = np.array(nbr, dtype=int)
+        self.og_h = np.array(h)
+        self.og_delta = np.array(delta)
 
     # ------------------------------------------------------------------ #
     def _equilibria(self, rho, Y, u, T, u_species=None):
@@ -188,14 +239,15 @@ class Boundaries:
                 bb = post_flat[:, opp][:, :, idx]
                 flat[:, :, idx] = np.where(D, bb, p)
             elif k == 2:
-                flat[:, :, idx] = self._tms(p, post_flat[:, opp][:, :, idx], D, idx, Tguess[idx])
+                flat[:, :, idx] = self._tms(p, post_flat[:, opp][:, :, idx], D, idx, Tguess[idx],
+                                            post_flat)
             elif k == 3:
                 flat[:, :, idx] = self._inlet(p, D, idx, Tguess[idx])
             else:
                 flat[:, :, idx] = self._outlet(p, D, idx, Tguess[idx], post)
         return out
 
-    def _tms(self, p, bb, D, idx, Tg):
+    def _tms(self, p, bb, D, idx, Tg, post_flat=None):
         """Sec. 4.2.2, steps 1-4."""
         lbm = self.lbm
         M, dim = lbm.M, lbm.vs.dim
@@ -207,10 +259,27 @@ class Boundaries:
         for a in range(M - 1):
             Y_bb[a] = pb[a].sum(axis=0) / rho_bb
         Y_bb[M - 1] = 1.0 - Y_bb[: M - 1].sum(axis=0)
-        # step 2: target equilibria at (rho_bb, Y_bb, u_wall = 0, T_wall)
+        # step 2: target equilibria at (rho_bb, Y_bb, u_wall = 0, T_wall), or
+        # at the off-grid targets interpolated towards the fluid
         u_t = np.zeros((dim, n))
-        T_t = self.wall_T.ravel()[idx]
-        tgt = self._equilibria(rho_bb, Y_bb, u_t, T_t)
+        T_t = self.wall_T.ravel()[idx].copy()
+        us_t = None
+        if self.og_nodes is not None and self.og_nodes.size:
+            pos = np.searchsorted(self.og_nodes, idx)
+            pos = np.minimum(pos, self.og_nodes.size - 1)
+            has = self.og_nodes[pos] == idx
+            if np.any(has):
+                sel = np.nonzero(has)[0]
+                j = pos[sel]
+                pf = post_flat[:, :, self.og_nbr[j]]
+                _, u_f, _, us_f, T_f = self._local_state(pf, Tg[sel])
+                h, dl = self.og_h[j], self.og_delta[j]
+                w = dl / (h + dl)
+                us_t = np.zeros((M, dim, n))
+                u_t[:, sel] = w * u_f
+                us_t[:, :, sel] = w * us_f
+                T_t[sel] = (h * T_t[sel] + dl * T_f) / (h + dl)
+        tgt = self._equilibria(rho_bb, Y_bb, u_t, T_t, u_species=us_t)
         # step 3: local state with the incoming populations at the target
         pl = np.where(D, tgt, p)
         rho_l, u_l, Y_l, us_l, T_l = self._local_state(pl, Tg)

@@ -7,7 +7,8 @@ from lbm_workloads.fields import perturbed_box  # noqa: F401
 from oracle import OracleLBM, thermo
 
 
-BC_KEYS = ("faces", "inlet", "outlet", "wall_T", "solid", "solid_kind")
+BC_KEYS = ("faces", "inlet", "outlet", "wall_T", "solid", "solid_kind", "wall_dist",
+           "wall_normal")
 
 
 def boundary_spec(w):
