@@ -159,6 +159,22 @@ typedef struct lbm_config {
                                  local equilibria (u and T take local values,
                                  not the targets); 0 (default): the full
                                  four-step inlet                              */
+  const double* wall_dist;    /* optional, host [N]: normal distance from each
+                                 node to the wall (lattice units, >= 0 at
+                                 fluid nodes), with wall_normal; NULL: the
+                                 TMS targets apply at the interface node
+                                 itself (walls on the grid or staircase)      */
+  const double* wall_normal;  /* optional, host [3][N]: inward unit normal of
+                                 the wall at each node.  With both arrays a
+                                 TMS interface node takes its targets (Sec.
+                                 4.2.2, last paragraph) by linear
+                                 interpolation along the normal between the
+                                 wall (u = u_a = 0, T = its wall temperature)
+                                 and the fluid node x + c_k most aligned with
+                                 the normal, from that node's stored
+                                 post-collision fields; a node whose x + c_k
+                                 is solid or beyond a non-periodic face keeps
+                                 the wall values.  Copied at lbm_create.      */
   int chem_fp64;              /* with LBM_FP32_STORE: 1 runs the temperature
                                  Newton solves (Sec. 3.1 Eq. temperature) and
                                  the reaction sub-steps (Sec. 2.4 Eq. R3) in

@@ -27,9 +27,10 @@
 
 constexpr int kBnd = kBndNodesPerBlock;   // threads per block of the boundary kernel
 
-// shared memory per thread: target Y, local Y, a spare Y and the local u_a
-// (R entries), then the Q pull sources (long long)
-template <int D, int M> constexpr int bnode_col_entries() { return 3 * M + M * D; }
+// shared memory per thread: target Y, local Y, a spare Y, the local u_a and
+// the target u_a (off-grid TMS targets) (R entries), then the Q pull sources
+// (long long)
+template <int D, int M> constexpr int bnode_col_entries() { return 3 * M + 2 * M * D; }
 template <int D, int M, typename R> constexpr size_t bnode_smem() {
   return (sizeof(R) * bnode_col_entries<D, M>() + sizeof(long long) * Lat<D>::Q) * kBnd;
 }
@@ -474,6 +475,25 @@ __device__ __forceinline__ void bnode_body(const S* __restrict__ src, const BCDe
 #pragma unroll
       for (int d = 0; d < D; ++d) A.u[d] = R(0);     // u^tgt = u_a^tgt = 0
       A.T = R(bc.if_wallT[k]);
+      if (bc.if_nbr && bc.if_nbr[k] >= 0) {
+        // off-grid targets (last paragraph of Sec. 4.2.2; reading R20): the
+        // stored state of the fluid node x_f (Newton from this node's own T
+        // guess, as for the outlet), interpolated along the wall normal
+        // between the wall (at -delta) and x_f (at h)
+        BState<D, M, R> sf = B;            // the spare and local-u_a columns, free now
+        sf.us = L.us;
+        BNode<D, M, S, R> nf{src, codec, N, (long long)bc.if_nbr[k]};
+        bsums<D, M, R>(nf, z);
+        bstate_of<D, M, R>(sf, z, Tf[n], m, un, status);
+        const double h = bc.if_wh[k], dl = bc.if_wd[k];
+        const R w = R(dl / (h + dl));
+#pragma unroll
+        for (int d = 0; d < D; ++d) A.u[d] = w * sf.u[d];
+        A.us = col + (3 * M + M * D) * kBnd;
+#pragma unroll
+        for (int e = 0; e < M * D; ++e) A.us[e * kBnd] = w * sf.us[e * kBnd];
+        A.T = R((h * bc.if_wallT[k] + dl * sf.T_full) / (h + dl));
+      }
       bstate_prepare<D, M, R>(A, m, un);              // step 2: target (Eqs. tgtf-tgtfa)
     } else if (kind == BK_INLET) {
       A.rho = R(bc.rho_in);

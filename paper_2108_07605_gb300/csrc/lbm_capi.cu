@@ -155,6 +155,8 @@ std::string validate(const lbm_config* c) {
       c->precision != LBM_FP16_OFFSET)
     return "precision must be LBM_FP64, LBM_FP32_STORE or LBM_FP16_OFFSET";
   if (c->chem_fp64 != 0 && c->chem_fp64 != 1) return "chem_fp64 must be 0 or 1";
+  if ((c->wall_dist == nullptr) != (c->wall_normal == nullptr))
+    return "wall_dist and wall_normal go together";
   if (c->chem_fp64 && c->precision == LBM_FP16_OFFSET)
     return "chem_fp64 is supported with LBM_FP32_STORE (and implied by LBM_FP64)";
   if (c->substeps < 1 || c->substeps > 64) return "substeps must be in 1..64";
@@ -322,6 +324,9 @@ struct HostBC {
   std::vector<int> tag, if_node, if_info;
   std::vector<unsigned> if_inc;
   std::vector<double> wallT, uin;   // uin [3][n_if], lattice units
+  bool offgrid = false;             // off-grid TMS targets (wall_dist, wall_normal)
+  std::vector<int> og_nbr;          // [n_if] fluid node x_f, -1: none
+  std::vector<double> og_h, og_d;   // [n_if] normal projection of c_k, wall distance
 };
 
 int precedence(int k) {
@@ -379,6 +384,51 @@ HostBC classify(const lbm_config& c, double c_ref) {
     for (int d = 0; d < 3; ++d)
       h.uin[(size_t)d * h.n_if + k] =
           (c.inlet_u ? c.inlet_u[(long long)d * N + h.if_node[k]] : c.inlet_u_uniform[d]) / c_ref;
+  // off-grid TMS targets (Sec. 4.2.2, last paragraph): per TMS node the
+  // fluid node x + c_k whose direction is most aligned with the inward
+  // normal (first such direction in index order), its projection on the
+  // normal and the node's wall distance
+  h.offgrid = c.wall_dist && c.wall_normal;
+  if (h.offgrid) {
+    h.og_nbr.assign(h.n_if, -1);
+    h.og_h.assign(h.n_if, 0.0);
+    h.og_d.assign(h.n_if, 0.0);
+    for (int k = 0; k < h.n_if; ++k) {
+      if ((h.if_info[k] & 15) != BK_TMS) continue;
+      const long long n = h.if_node[k];
+      double nrm[3] = {0.0, 0.0, 0.0};
+      for (int d = 0; d < D; ++d) nrm[d] = c.wall_normal[(long long)d * N + n];
+      int best = -1;
+      double bval = 0.0;
+      for (int i = 0; i < Q; ++i) {
+        double cc = 0.0, dot = 0.0;
+        for (int d = 0; d < D; ++d) cc += cvel_host(i, d) * cvel_host(i, d);
+        if (cc == 0.0) continue;
+        const double inv = 1.0 / std::sqrt(cc);
+        for (int d = 0; d < D; ++d) dot += (cvel_host(i, d) * inv) * nrm[d];
+        if (best < 0 || dot > bval) { best = i; bval = dot; }
+      }
+      const int co[3] = {(int)(n % c.nx), (int)((n / c.nx) % c.ny),
+                         (int)(n / ((long long)c.nx * c.ny))};
+      int xf[3] = {co[0], co[1], co[2]};
+      bool ok = true;
+      double hproj = 0.0;
+      for (int d = 0; d < D; ++d) {
+        int v = co[d] + cvel_host(best, d);
+        if (v < 0 || v >= ext[d]) {
+          if (c.face_bc[2 * d + (v >= ext[d] ? 1 : 0)] != LBM_PERIODIC) ok = false;
+          v = (v + ext[d]) % ext[d];
+        }
+        xf[d] = v;
+        hproj += cvel_host(best, d) * nrm[d];
+      }
+      const long long nf = xf[0] + (long long)c.nx * (xf[1] + (long long)c.ny * xf[2]);
+      if (!ok || (h.has_solid && c.solid_mask[nf])) continue;
+      h.og_nbr[k] = (int)nf;
+      h.og_h[k] = hproj;
+      h.og_d[k] = c.wall_dist[n];
+    }
+  }
   return h;
 }
 
@@ -406,6 +456,7 @@ Sizes sizes_for(const lbm_config& c, const HostBC& hb) {
     const size_t nif = (size_t)hb.n_if;
     s.bc = align256(N * sizeof(int)) + 3 * align256(nif * sizeof(int)) +
            4 * align256(nif * sizeof(double)) + align256((size_t)(M + 1) * Q * nif * sizeof(double));
+    if (hb.offgrid) s.bc += align256(nif * sizeof(int)) + 2 * align256(nif * sizeof(double));
   }
   s.total = 2 * s.pops + s.rec + s.cpar + s.codec + s.tf + s.status + s.bc;
   return s;
@@ -725,6 +776,20 @@ lbm_status lbm_create(const lbm_config* cfg, lbm_t* out) {
     double* uin = reinterpret_cast<double*>(take(3 * nif * sizeof(double)));
     b.pops = reinterpret_cast<double*>(take((size_t)h->L * h->Q * nif * sizeof(double)));
     cudaError_t e = cudaMemcpy(tag, hb.tag.data(), N * sizeof(int), cudaMemcpyHostToDevice);
+    if (hb.offgrid) {
+      int* nbr = reinterpret_cast<int*>(take(nif * sizeof(int)));
+      double* wh = reinterpret_cast<double*>(take(nif * sizeof(double)));
+      double* wd = reinterpret_cast<double*>(take(nif * sizeof(double)));
+      if (nif && e == cudaSuccess)
+        e = cudaMemcpy(nbr, hb.og_nbr.data(), nif * sizeof(int), cudaMemcpyHostToDevice);
+      if (nif && e == cudaSuccess)
+        e = cudaMemcpy(wh, hb.og_h.data(), nif * sizeof(double), cudaMemcpyHostToDevice);
+      if (nif && e == cudaSuccess)
+        e = cudaMemcpy(wd, hb.og_d.data(), nif * sizeof(double), cudaMemcpyHostToDevice);
+      b.if_nbr = nbr;
+      b.if_wh = wh;
+      b.if_wd = wd;
+    }
     if (nif && e == cudaSuccess)
       e = cudaMemcpy(if_node, hb.if_node.data(), nif * sizeof(int), cudaMemcpyHostToDevice);
     if (nif && e == cudaSuccess)

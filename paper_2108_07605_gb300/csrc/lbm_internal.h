@@ -105,6 +105,12 @@ struct BCDev {
   const double* if_wallT = nullptr;  // [n_if] TMS target temperature (K)
   const double* if_uin = nullptr;    // [3][n_if] inlet velocity, lattice units
   double* pops = nullptr;            // [L][Q][n_if] reconstructed populations
+  // off-grid TMS targets (nullptr: targets at the node): the fluid node x_f
+  // of each interface node (-1: none), its normal projection h and the
+  // node's normal wall distance delta (lattice units)
+  const int* if_nbr = nullptr;
+  const double* if_wh = nullptr;
+  const double* if_wd = nullptr;
   int n_if = 0;
   int face[6] = {0, 0, 0, 0, 0, 0};
   int has_solid = 0;

@@ -2376,6 +2376,8 @@ static cudaError_t prepare_impl() {
   big((const void*)k_prep_batch<D, M, RT>, prep_smem<D, M, RT>());
   big((const void*)k_coll<D, M, S, RT>, coll_smem<D, M, RT>());
   big((const void*)k_coll_batch<D, M, S, RT>, coll_smem<D, M, RT>());
+  big((const void*)k_bnode<D, M, S>, bnode_smem<D, M, RT>());
+  big((const void*)k_bnode_batch<D, M, S>, bnode_smem<D, M, RT>());
   return e;
 }
 

@@ -74,6 +74,7 @@ class lbm_config(C.Structure):
         ("newton_max_iter", C.c_int), ("newton_rtol", C.c_double),
         ("dev_alloc", ALLOC_FN), ("dev_free", FREE_FN), ("alloc_user", C.c_void_p),
         ("stream", C.c_void_p), ("device", C.c_int), ("inlet_simplified", C.c_int),
+        ("wall_dist", C.POINTER(C.c_double)), ("wall_normal", C.POINTER(C.c_double)),
         ("chem_fp64", C.c_int),
     ]
 
@@ -477,14 +478,15 @@ def make_config(mech, lattice="D3Q27", shape=(16, 16, 16), dx=1e-3, precision="f
                 substeps=2, c_ref=0.0, T_max=3000.0, faces=None, newton_max_iter=50,
                 newton_rtol=1e-13, device=0, stream=None, use_torch_allocator=True,
                 wall_T=None, solid=None, solid_kind="tms", inlet=None, outlet=None,
-                chem_fp64=0):
+                chem_fp64=0, wall_dist=None, wall_normal=None):
     """Build an lbm_config from Python values.  Returns (cfg, keepalive).
 
     wall_T: scalar (every TMS face) or a grid array [nz, ny, nx] (per node);
     solid: optional grid array of solid nodes; inlet: dict(u, T, Y, P) with u
     a 3-vector or a [3, nz, ny, nx] array (m/s); outlet: dict(P, sigma);
     chem_fp64: with precision "fp32", the temperature solve and chemistry in
-    native FP64 instead of float-float."""
+    native FP64 instead of float-float; wall_dist [nz, ny, nx] and
+    wall_normal [3, nz, ny, nx] (together): off-grid TMS targets."""
     cfg = lbm_config_defaults()
     cfg.lattice = LBM_D3Q27 if lattice == "D3Q27" else LBM_D2Q9
     cfg.nx, cfg.ny, cfg.nz = (int(v) for v in shape)
@@ -510,6 +512,16 @@ def make_config(mech, lattice="D3Q27", shape=(16, 16, 16), dx=1e-3, precision="f
             wt = np.ascontiguousarray(wt.reshape(-1))
             keep.append(wt)
             cfg.wall_T_nodes = wt.ctypes.data_as(C.POINTER(C.c_double))
+    if (wall_dist is None) != (wall_normal is None):
+        raise ValueError("wall_dist and wall_normal go together")
+    if wall_dist is not None:
+        wd = np.ascontiguousarray(np.asarray(wall_dist, dtype=np.float64).reshape(-1))
+        wn = np.ascontiguousarray(np.asarray(wall_normal, dtype=np.float64).reshape(-1))
+        if wd.size != cfg.nx * cfg.ny * cfg.nz or wn.size != 3 * wd.size:
+            raise ValueError("wall_dist needs one value per node and wall_normal three")
+        keep += [wd, wn]
+        cfg.wall_dist = wd.ctypes.data_as(C.POINTER(C.c_double))
+        cfg.wall_normal = wn.ctypes.data_as(C.POINTER(C.c_double))
     if solid is not None:
         sm = np.ascontiguousarray(np.asarray(solid, dtype=np.uint8).reshape(-1))
         keep.append(sm)

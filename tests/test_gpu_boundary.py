@@ -1,8 +1,9 @@
 """GPU parity of the boundary conditions (Sec. 4) against the oracle:
 bounce-back box, flux inlet + LODI outlet (flame layout), Tamm-Mott-Smith
 walls with a temperature ramp and a parabolic inlet (channel layout, D2Q9),
-staircase solid walls (microtube layout), and the full-size 1024x4x4 flame
-in the launch configuration the benchmark times.  FP64 tolerance: 1e-10
+staircase solid walls (microtube layout) with targets at the interface node
+or interpolated off the grid along the wall normal, and the full-size
+1024x4x4 flame in the launch configuration the benchmark times.  FP64 tolerance: 1e-10
 relative per lattice, as for the periodic tests; solid nodes are excluded
 (their populations are not defined)."""
 import numpy as np
@@ -73,4 +74,15 @@ def test_flame_layout_simplified_inlet(mech):
     w = fields.flame_1d(nx=40, ny=3, nz=2, x_ign=10)
     w["inlet"] = dict(w["inlet"], simplified=True)
     err = _compare(mech, w, 12)
+    assert np.all(err < RTOL_FP64), err
+
+
+@pytest.mark.parametrize("shape,radius,nsteps", [((10, 9, 9), 3.6, 6), ((20, 40, 40), 19.0, 5)])
+def test_tube_offgrid_targets(mech, shape, radius, nsteps):
+    """Off-grid TMS targets (Sec. 4.2.2, last paragraph): the circular wall
+    given by its normal distance and normal per node, targets interpolated
+    towards the fluid, against the oracle with the same geometry."""
+    nx, ny, nz = shape
+    w = fields.microtube(nx=nx, ny=ny, nz=nz, radius=radius, dx=25e-6, offgrid=True)
+    err = _compare(mech, w, nsteps)
     assert np.all(err < RTOL_FP64), err

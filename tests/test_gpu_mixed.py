@@ -44,6 +44,8 @@ CASES = {
     "flame layout": (lambda m: fields.flame_1d(nx=40, ny=3, nz=2, x_ign=10), 50),
     "channel layout": (lambda m: fields.channel_2d(nx=30, ny=9), 50),
     "tube layout": (lambda m: fields.microtube(nx=10, ny=9, nz=9, radius=3.6), 30),
+    "tube layout, off-grid targets": (
+        lambda m: fields.microtube(nx=10, ny=9, nz=9, radius=3.6, offgrid=True), 30),
     "flame 1024x4x4": (lambda m: fields.flame_1d(), 20),
 }
 
