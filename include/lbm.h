@@ -175,6 +175,11 @@ typedef struct lbm_config {
                                  post-collision fields; a node whose x + c_k
                                  is solid or beyond a non-periodic face keeps
                                  the wall values.  Copied at lbm_create.      */
+  double outlet_length;       /* LODI length L (lattice units) in the incoming
+                                 wave's relaxation K = sigma (1 - Ma^2) c / L;
+                                 0 (default): the domain's extent along the
+                                 outlet normal.  A slab of a longer domain
+                                 gives the whole domain's length.             */
   int chem_fp64;              /* with LBM_FP32_STORE: 1 runs the temperature
                                  Newton solves (Sec. 3.1 Eq. temperature) and
                                  the reaction sub-steps (Sec. 2.4 Eq. R3) in
@@ -420,6 +425,24 @@ lbm_status lbm_fma_peak(int fp64, double* tflops);
 #define LBM_NOALLOC_MAX_NODES 16384
 lbm_status lbm_step_noalloc(const lbm_config* cfg, const void* pops_in, void* pops_out,
                             double* T_guess, const char** error);
+
+/* Halo planes for an x-slab domain decomposition (the paper runs on one
+ * domain; the slab split keeps every step of Sec. 2-4 local to
+ * a node and its neighbours up to two planes away, so a slab that receives
+ * its neighbours' two nearest planes before each step advances its own
+ * planes exactly as the undivided domain would).
+ * lbm_get_planes copies planes x0 .. x0+nplanes-1 of the current state out
+ * to buf, lbm_set_planes copies buf into them: the populations
+ * [L][Q][nz][ny][nplanes] in the storage precision (8 bytes FP64, 4 bytes
+ * FP32), then the temperature guesses [nz][ny][nplanes] as doubles; total
+ * nplanes*ny*nz*(L*Q*elem + 8) bytes.  buf is host memory, or device memory
+ * on the handle's device when on_device != 0; owned by the caller.
+ * Synchronous (the handle's stream is drained).  LBM_ERR_RANGE for planes
+ * outside 0..nx-1, LBM_ERR_INVALID for FP16 offset storage (its codec is a
+ * property of each handle) or a NULL buffer, LBM_ERR_STATE before
+ * lbm_init_fields. */
+lbm_status lbm_get_planes(lbm_t h, int x0, int nplanes, void* buf, int on_device);
+lbm_status lbm_set_planes(lbm_t h, int x0, int nplanes, const void* buf, int on_device);
 
 /* Text of the last error on h (or of the last lbm_create failure if h is
  * NULL).  Valid until the next call on h. */

@@ -74,6 +74,10 @@ class Boundaries:
         mech = lbm.mech
         self.outlet_P = float(outlet.get("P", 101325.0))
         self.outlet_sigma = float(outlet.get("sigma", 0.25))
+        # LODI length L of K = sigma (1 - Ma^2) c / L: the domain's extent
+        # along the outlet normal unless given (a slab of a longer domain
+        # keeps the whole domain's length)
+        self.outlet_length = outlet.get("length")
         if inlet is not None:
             u_in = np.asarray(inlet["u"], dtype=float)
             if u_in.ndim == 1:                       # uniform, else one vector per node
@@ -339,7 +343,8 @@ class Boundaries:
         gamma = (Cv + R0) / Cv
         cs = np.sqrt(gamma * R0 * T0 / c2)
         Ma = un0 / cs
-        Ln = np.array([nx, ny, nz])[ax]
+        Ln = np.array([nx, ny, nz])[ax] if self.outlet_length is None else \
+            np.full(idx.size, float(self.outlet_length))
         K = self.outlet_sigma * (1.0 - Ma ** 2) * cs / Ln
         P_t = self.outlet_P / c2
         dn_rho = rho0 - rho1

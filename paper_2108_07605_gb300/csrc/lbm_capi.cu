@@ -155,6 +155,8 @@ std::string validate(const lbm_config* c) {
       c->precision != LBM_FP16_OFFSET)
     return "precision must be LBM_FP64, LBM_FP32_STORE or LBM_FP16_OFFSET";
   if (c->chem_fp64 != 0 && c->chem_fp64 != 1) return "chem_fp64 must be 0 or 1";
+  if (!(c->outlet_length >= 0.0) || !std::isfinite(c->outlet_length))
+    return "outlet_length must be >= 0";
   if ((c->wall_dist == nullptr) != (c->wall_normal == nullptr))
     return "wall_dist and wall_normal go together";
   if (c->chem_fp64 && c->precision == LBM_FP16_OFFSET)
@@ -815,6 +817,7 @@ lbm_status lbm_create(const lbm_config* cfg, lbm_t* out) {
     b.has_solid = hb.has_solid ? 1 : 0;
     b.solid_kind = cfg->solid_bc;
     b.sigma = cfg->outlet_sigma;
+    b.outlet_L = cfg->outlet_length;
     b.inlet_simplified = cfg->inlet_simplified ? 1 : 0;
     b.p_out_lat = cfg->outlet_P * h->un.inv_c2;
     double Rin = 0.0;
@@ -1395,6 +1398,55 @@ lbm_status lbm_get_populations(lbm_t h, double* out, int on_device) {
                         h->stream);
   if (e != cudaSuccess) return cuda_fail(h, e, "population download");
   return check_status(h);
+}
+
+// Planes x0 .. x0+nplanes-1 of the stored state: populations [L][Q][nz][ny]
+// [nplanes] in the storage precision, then the temperature guesses
+// [nz][ny][nplanes] (FP64).  One strided copy each (rows of nplanes values
+// at pitch nx), synchronous.
+static lbm_status planes_io(lbm_t h, int x0, int nplanes, void* buf, int on_device, bool out) {
+  if (!h) return fail(nullptr, LBM_ERR_INVALID, "handle is NULL");
+  if (!buf) return fail(h, LBM_ERR_INVALID, "buffer is NULL");
+  if (h->cfg.precision == LBM_FP16_OFFSET)
+    return fail(h, LBM_ERR_INVALID, "plane copies need FP64 or FP32 storage (FP16 offsets "
+                                    "depend on each handle's codec)");
+  if (nplanes < 1 || x0 < 0 || x0 + nplanes > h->g.nx)
+    return fail(h, LBM_ERR_RANGE, "planes outside 0 .. nx-1");
+  if (!h->initialized) return fail(h, LBM_ERR_STATE, "no state before lbm_init_fields");
+  DeviceGuard dg(h->cfg.device);
+  const size_t rows = (size_t)h->L * h->Q * h->g.nz * h->g.ny;
+  const size_t trows = (size_t)h->g.nz * h->g.ny;
+  const size_t e1 = h->elem, w = (size_t)nplanes;
+  char* pops = static_cast<char*>(h->pops[h->cur]) + (size_t)x0 * e1;
+  char* tf = reinterpret_cast<char*>(h->Tf + x0);
+  char* b = static_cast<char*>(buf);
+  char* bt = b + rows * w * e1;
+  const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice
+                                     : (out ? cudaMemcpyDeviceToHost : cudaMemcpyHostToDevice);
+  const size_t pitch = (size_t)h->g.nx * e1, tpitch = (size_t)h->g.nx * sizeof(double);
+  cudaError_t e;
+  if (out) {
+    e = cudaMemcpy2DAsync(b, w * e1, pops, pitch, w * e1, rows, k, h->stream);
+    if (e == cudaSuccess)
+      e = cudaMemcpy2DAsync(bt, w * sizeof(double), tf, tpitch, w * sizeof(double), trows, k,
+                            h->stream);
+  } else {
+    e = cudaMemcpy2DAsync(pops, pitch, b, w * e1, w * e1, rows, k, h->stream);
+    if (e == cudaSuccess)
+      e = cudaMemcpy2DAsync(tf, tpitch, bt, w * sizeof(double), w * sizeof(double), trows, k,
+                            h->stream);
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "plane copy");
+  return LBM_OK;
+}
+
+lbm_status lbm_get_planes(lbm_t h, int x0, int nplanes, void* buf, int on_device) {
+  return planes_io(h, x0, nplanes, buf, on_device, true);
+}
+
+lbm_status lbm_set_planes(lbm_t h, int x0, int nplanes, const void* buf, int on_device) {
+  return planes_io(h, x0, nplanes, const_cast<void*>(buf), on_device, false);
 }
 
 lbm_status lbm_synchronize(lbm_t h) {

@@ -118,6 +118,7 @@ struct BCDev {
   double rho_in = 0.0, T_in = 0.0, theta_in = 0.0;
   double Y_in[LBM_MAX_SPECIES] = {0};
   double p_out_lat = 0.0, sigma = 0.25;
+  double outlet_L = 0.0;          // LODI length (lattice units); 0: the extent
   int inlet_simplified = 0;       // simplified flux inlet (Sec. 4.3)
 };
 

@@ -1717,7 +1717,7 @@ __device__ __forceinline__ void boundary_body(const S* __restrict__ src, const B
     const double gamma = (Cv + R0) / Cv;
     const double cs = sqrt(gamma * R0 * T0 * un.inv_c2);
     const double Ma = un0 / cs;
-    const double Ln = ax == 0 ? g.nx : (ax == 1 ? g.ny : g.nz);
+    const double Ln = bc.outlet_L > 0.0 ? bc.outlet_L : (ax == 0 ? g.nx : (ax == 1 ? g.ny : g.nz));
     const double K = bc.sigma * (1.0 - Ma * Ma) * cs / Ln;
     const double L1 = K * (p0 - bc.p_out_lat);
     const double L2 = un0 * (cs * cs * (r0 - r1) - (p0 - p1));

@@ -75,7 +75,7 @@ class lbm_config(C.Structure):
         ("dev_alloc", ALLOC_FN), ("dev_free", FREE_FN), ("alloc_user", C.c_void_p),
         ("stream", C.c_void_p), ("device", C.c_int), ("inlet_simplified", C.c_int),
         ("wall_dist", C.POINTER(C.c_double)), ("wall_normal", C.POINTER(C.c_double)),
-        ("chem_fp64", C.c_int),
+        ("outlet_length", C.c_double), ("chem_fp64", C.c_int),
     ]
 
 
@@ -125,6 +125,8 @@ EXPORTS = {
     "lbm_destroy": (C.c_int, [C.c_void_p]),
     "lbm_last_error": (C.c_char_p, [C.c_void_p]),
     "lbm_fma_peak": (C.c_int, [C.c_int, C.POINTER(C.c_double)]),
+    "lbm_get_planes": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_int]),
+    "lbm_set_planes": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_int]),
     "lbm_step_noalloc": (C.c_int, [C.POINTER(lbm_config), C.c_void_p, C.c_void_p,
                                    C.c_void_p, C.POINTER(C.c_char_p)]),
 }
@@ -438,6 +440,20 @@ def lbm_step_noalloc(cfg, pops_in, pops_out, T_guess):
         raise LBMError(st, err.value.decode() if err.value else "")
 
 
+def lbm_get_planes(h, x0, nplanes, buf):
+    """Copy planes x0 .. x0+nplanes-1 (populations in the storage precision,
+    then the temperature guesses) into buf (a numpy array or a CUDA tensor
+    of at least the plane bytes, any dtype)."""
+    p, on = _ptr(buf)
+    _check(load_library().lbm_get_planes(h, int(x0), int(nplanes), p, on), h)
+
+
+def lbm_set_planes(h, x0, nplanes, buf):
+    """Copy buf (as written by lbm_get_planes) into planes x0 .. x0+nplanes-1."""
+    p, on = _ptr(buf)
+    _check(load_library().lbm_set_planes(h, int(x0), int(nplanes), p, on), h)
+
+
 def lbm_fma_peak(fp64):
     """Measured FMA throughput (TFLOP/s) of the current device, FP64 or FP32."""
     out = C.c_double(0.0)
@@ -544,6 +560,7 @@ def make_config(mech, lattice="D3Q27", shape=(16, 16, 16), dx=1e-3, precision="f
     if outlet is not None:
         cfg.outlet_P = float(outlet.get("P", 101325.0))
         cfg.outlet_sigma = float(outlet.get("sigma", 0.25))
+        cfg.outlet_length = float(outlet.get("length") or 0.0)
     if stream is None:
         try:
             import torch
