@@ -103,6 +103,8 @@ def parse():
                    help="reaction sub-steps l (Eq. R3); 0 keeps the workload's value")
     p.add_argument("--nx", type=int, default=0,
                    help="length of the flame, channel or tube (0: the workload's own)")
+    p.add_argument("--serve-scale", type=float, default=0.02,
+                   help="step scale of the serving mix timed beside the headline (0: skip)")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
     return p.parse_args()
@@ -420,6 +422,39 @@ def roofline(workload, mode, info, Nf, ms_per_step, peaks, fma):
     return roof
 
 
+def served_mix(mech, step_scale, device):
+    """The serving mix (64 seeded requests, Poisson arrivals with mean 50 ms,
+    reactor / flame / channel solves of 4k to 262k nodes) with every
+    request's 1k-10k steps scaled by step_scale: the continuous-batching
+    server in FP32 storage (least remaining work first) and, as the
+    baseline, the plain FP64 path one request at a time.  Time-to-result =
+    completion minus arrival on the host clock."""
+    from lbm_workloads.fields import serving_mix
+    from paper_2108_07605_gb300 import serve
+
+    def stream():
+        st = serving_mix(seed=0, mech=mech)
+        for _, w in st:
+            w["steps"] = max(1, int(round(w["steps"] * step_scale)))
+        return st
+    budget = int(40e9)
+    srv = serve.Server(mech, budget, chunk=100, precision="fp32", device=device)
+    done = srv.run(stream())
+    ours = serve.summarize(done, srv.elapsed, srv.node_updates)
+    base = serve.run_serial(mech, stream(), budget, "fp64", device=device)
+    keys = ("p50_time_to_result_s", "p99_time_to_result_s", "node_updates_per_s",
+            "makespan_s", "requests")
+    return {"mix": f"64 seeded requests (Poisson arrivals, mean 50 ms; reactor, flame and "
+                   f"channel solves of 4k-262k nodes), the stated 1k-10k steps scaled by "
+                   f"{step_scale}",
+            "batched_fp32_srpt": {k: ours[k] for k in keys},
+            "serial_fp64": {k: base[k] for k in keys},
+            "failed": len(ours["failed"]) + len(base["failed"]),
+            "throughput_vs_serial_fp64": ours["node_updates_per_s"] / base["node_updates_per_s"],
+            "p99_vs_serial_fp64": ours["p99_time_to_result_s"] / base["p99_time_to_result_s"],
+            "p50_vs_serial_fp64": ours["p50_time_to_result_s"] / base["p50_time_to_result_s"]}
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
@@ -537,6 +572,8 @@ def main():
                           "roofline": roofline(args.workload, mode, vinfo, Nf, vms_step, peaks,
                                                fma)}
 
+    served = served_mix(mech, args.serve_scale, local) if args.serve_scale > 0 else None
+
     if rank != 0:
         return
     cpu = None
@@ -559,6 +596,7 @@ def main():
         "kernel_ms_per_step": {names[0]: kms[0] / args.steps, names[1]: kms[1] / args.steps},
         "fma_peak_tflops": fma,
         "variants": variants,
+        "served": served,
         "clocks": clk.summary(),
     }
     print(json.dumps(line), flush=True)

@@ -6,13 +6,16 @@
 Requests (reactor, flame or channel solves of different grid sizes) arrive
 over time.  The loop admits a request as soon as it has arrived and its
 device memory (lbm_bytes_required) fits the remaining budget, initialises
-its populations on the GPU and keeps them resident.  Every tick advances all
-resident requests together: the requests that share a lattice and precision
-form a batch plan (lbm_batch_create: the batched kernels - one launch per
-kernel per step over the tiles of every request - captured as CUDA graphs),
-rebuilt only when the batch's membership changes and replayed for a chunk of
-steps no longer than the shortest remaining request, so no request runs past
-its step count.  A request that has completed its steps is read back
+its populations on the GPU and keeps them resident.  Every tick advances a
+set of resident requests together (policy "srpt", the default: those with
+the least remaining work, up to a node count that fills the GPU; policy
+"fifo": all of them): the advanced requests that share a lattice form a
+batch plan (lbm_batch_create: the batched kernels - one launch per kernel
+per step over the tiles of every request - captured as CUDA graphs), kept
+while the set does not change and replayed for a chunk of steps no longer
+than the shortest remaining request, so no request runs past its step
+count.  The host waits only for the previous tick's event, never for the
+whole device, so the next tick's launches are queued while one runs.  A request that has completed its steps is read back
 (lbm_moments), its handle destroyed and its memory returned, and waiting
 requests are admitted at the next tick.  An optional cap on the resident
 nodes (max_nodes) admits in arrival order only while the resident requests'
@@ -60,20 +63,56 @@ class Request:
         return int(self.w["P"].size)
 
 
+class _TickFence:
+    """Keeps the host at most one tick ahead of the GPU: an event is
+    recorded on the current stream after each tick's launches, and the host
+    waits for the previous tick's event (not for the whole device)."""
+
+    def __init__(self, device):
+        import torch
+        self.torch, self.device = torch, device
+        self.prev = None
+
+    def mark(self):
+        ev = self.torch.cuda.Event()
+        ev.record(self.torch.cuda.current_stream(self.device))
+        if self.prev is not None:
+            self.prev.synchronize()
+        self.prev = ev
+
+    def drain(self):
+        if self.prev is not None:
+            self.prev.synchronize()
+        self.prev = None
+
+
 class Server:
-    """Admission by device memory, continuous batching by lattice/precision."""
+    """Admission by device memory, continuous batching by lattice/precision.
+
+    policy "srpt" (default): every arrived request that fits the memory
+    budget is admitted and initialised at once (its populations stay
+    resident); each tick advances the resident requests with the least
+    remaining work (nodes x remaining steps) first, as many as keep the
+    advanced nodes within active_nodes (at least one request): short
+    requests do not wait behind long ones, and the GPU stays full.
+    policy "fifo": every resident request advances every tick; admission in
+    arrival order, optionally capped at max_nodes resident nodes."""
 
     def __init__(self, mech, budget_bytes, chunk=100, precision="fp32", device=0,
-                 max_nodes=0):
+                 max_nodes=0, policy="srpt", active_nodes=600_000):
+        if policy not in ("srpt", "fifo"):
+            raise ValueError(policy)
         self.mech = mech
         # the library's fixed lbm_step_noalloc scratch is resident on the
         # device as soon as the library is loaded: it counts against the budget
         self.budget = int(budget_bytes) - lbm.NOALLOC_SCRATCH_BYTES
-        self.max_nodes = int(max_nodes)   # 0: no cap on resident nodes
+        self.max_nodes = int(max_nodes)   # 0: no cap on resident nodes (fifo)
         self.used = 0
         self.chunk = int(chunk)
         self.precision = precision
         self.device = device
+        self.policy = policy
+        self.active_nodes = int(active_nodes)
 
     def _config_bytes(self, req):
         cfg, _keep = lbm.make_config(self.mech, lattice=req.w["lattice"], shape=req.w["shape"],
@@ -92,63 +131,77 @@ class Server:
         req.admitted = now
         self.used += req.bytes
 
+    def _advanced(self, resident):
+        """The requests this tick advances."""
+        if self.policy == "fifo":
+            return list(resident)
+        order = sorted(resident, key=lambda r: (r.nodes * r.remaining, r.arrival, r.rid))
+        chosen, nodes = [], 0
+        for r in order:
+            if chosen and nodes + r.nodes > self.active_nodes:
+                continue
+            chosen.append(r)
+            nodes += r.nodes
+        return chosen
+
     def run(self, stream, clock=time.perf_counter, on_tick=None):
         """stream: [(arrival_s, workload), ...] sorted by arrival.  Returns the
         finished requests (with .result = moments) in completion order."""
-        import torch
         pending = [Request(k, a, w) for k, (a, w) in enumerate(stream)]
         for r in pending:
             r.bytes = self._config_bytes(r)
             if r.bytes > self.budget:
                 raise ValueError(f"request {r.rid} needs {r.bytes} B, above the budget")
-        active, done = [], []
-        plans = {}          # batch key -> (handles of the plan, plan)
+        resident, done = [], []
+        plans = {}          # (lattice, member ids) -> plan
+        fence = _TickFence(self.device)
         t0 = clock()
         node_updates = 0
-        while pending or active:
+        while pending or resident:
             now = clock() - t0
             while pending and pending[0].arrival <= now and \
                     self.used + pending[0].bytes <= self.budget and \
-                    (self.max_nodes <= 0 or not active or
-                     sum(r.nodes for r in active) + pending[0].nodes <= self.max_nodes):
+                    (self.policy != "fifo" or self.max_nodes <= 0 or not resident or
+                     sum(r.nodes for r in resident) + pending[0].nodes <= self.max_nodes):
                 r = pending.pop(0)
                 self._admit(r, now)
-                active.append(r)
-            if not active:
+                resident.append(r)
+            if not resident:
                 if pending:
                     time.sleep(max(0.0, min(0.005, pending[0].arrival - now)))
                 continue
+            adv = self._advanced(resident)
+            n = min(self.chunk, min(r.remaining for r in adv))
             groups = {}
-            for r in active:
-                groups.setdefault((r.w["lattice"], self.precision), []).append(r)
-            for key, grp in groups.items():
-                n = min(self.chunk, min(r.remaining for r in grp))
-                ids = tuple(r.rid for r in grp)
-                if key not in plans or plans[key][0] != ids:
-                    if key in plans:
-                        lbm.lbm_batch_destroy(plans[key][1])
-                    plans[key] = (ids, lbm.lbm_batch_create([r.solver.h for r in grp]))
-                lbm.lbm_batch_run(plans[key][1], n)
+            for r in adv:
+                groups.setdefault(r.w["lattice"], []).append(r)
+            for lat, grp in groups.items():
+                key = (lat, tuple(r.rid for r in grp))
+                if key not in plans:
+                    plans[key] = lbm.lbm_batch_create([r.solver.h for r in grp])
+                lbm.lbm_batch_run(plans[key], n)
                 for r in grp:
                     r.remaining -= n
                     node_updates += n * r.nodes * (self.mech.n_species + 2)
-            torch.cuda.synchronize(self.device)
-            now = clock() - t0
-            still = []
-            for r in active:
-                if r.remaining == 0:
-                    still_planned = [k for k, (ids, _p) in plans.items() if r.rid in ids]
-                    for k in still_planned:   # a plan must not outlive its handles
-                        lbm.lbm_batch_destroy(plans.pop(k)[1])
+            fence.mark()
+            finished = [r for r in adv if r.remaining == 0]
+            if finished:
+                gone = {r.rid for r in finished}
+                for key in [k for k in plans if gone & set(k[1])]:
+                    lbm.lbm_batch_destroy(plans.pop(key))   # a plan must not outlive its handles
+                for r in finished:
                     self._finish(r, clock, t0)
                     self.used -= r.bytes
                     done.append(r)
-                else:
-                    still.append(r)
-            active = still
+                resident = [r for r in resident if r.rid not in gone]
+            # plans of member sets that no longer run are dropped
+            live = {(lat, tuple(r.rid for r in grp)) for lat, grp in groups.items()}
+            for key in [k for k in plans if k not in live]:
+                lbm.lbm_batch_destroy(plans.pop(key))
             if on_tick:
-                on_tick(now, active, pending, done)
-        for _ids, plan in plans.values():
+                on_tick(clock() - t0, resident, pending, done)
+        fence.drain()
+        for plan in plans.values():
             lbm.lbm_batch_destroy(plan)
         self.elapsed = clock() - t0
         self.node_updates = node_updates
@@ -166,6 +219,29 @@ class Server:
         except lbm.LBMError:
             pass
         r.solver = None
+
+
+def run_serial(mech, stream, budget, precision, device=0):
+    """The baseline of the serving loop: the same requests one after another
+    in arrival order, each advanced alone with lbm_step for its whole step
+    count.  Returns summarize()'s dict."""
+    import torch
+    t0 = time.perf_counter()
+    srv = Server(mech, budget, precision=precision, device=device)
+    done = []
+    node_updates = 0
+    for k, (arr, w) in enumerate(stream):
+        r = Request(k, arr, w)
+        now = time.perf_counter() - t0
+        if now < arr:
+            time.sleep(arr - now)
+        srv._admit(r, time.perf_counter() - t0)
+        r.solver.step(r.remaining)
+        torch.cuda.synchronize(device)
+        node_updates += r.remaining * r.nodes * (mech.n_species + 2)
+        Server._finish(r, time.perf_counter, t0)
+        done.append(r)
+    return summarize(done, time.perf_counter() - t0, node_updates)
 
 
 def summarize(done, elapsed, node_updates):
@@ -196,7 +272,10 @@ def main():
     p.add_argument("--serial", action="store_true",
                    help="one request at a time (no batching), for comparison")
     p.add_argument("--max-nodes", type=int, default=0,
-                   help="cap on the resident requests' nodes (0: admit by memory only)")
+                   help="fifo: cap on the resident requests' nodes (0: admit by memory only)")
+    p.add_argument("--policy", default="srpt", choices=["srpt", "fifo"])
+    p.add_argument("--active-nodes", type=int, default=600_000,
+                   help="srpt: nodes advanced per tick (least remaining work first)")
     args = p.parse_args()
     from . import build
     build.build()
@@ -208,32 +287,17 @@ def main():
         w["steps"] = max(1, int(round(w["steps"] * args.step_scale)))
     budget = int(args.budget_gb * 1e9)
     if args.serial:
-        # serial baseline: the same requests, one after another, unbatched
-        t0 = time.perf_counter()
-        srv = Server(mech, budget, chunk=args.chunk, precision=args.precision)
-        done = []
-        node_updates = 0
-        import torch
-        for k, (arr, w) in enumerate(stream):
-            r = Request(k, arr, w)
-            now = time.perf_counter() - t0
-            if now < arr:
-                time.sleep(arr - now)
-            srv._admit(r, time.perf_counter() - t0)
-            r.solver.step(r.remaining)
-            torch.cuda.synchronize()
-            node_updates += r.remaining * r.nodes * (mech.n_species + 2)
-            Server._finish(r, time.perf_counter, t0)
-            done.append(r)
-        out = summarize(done, time.perf_counter() - t0, node_updates)
+        out = run_serial(mech, stream, budget, args.precision)
     else:
         srv = Server(mech, budget, chunk=args.chunk, precision=args.precision,
-                     max_nodes=args.max_nodes)
+                     max_nodes=args.max_nodes, policy=args.policy,
+                     active_nodes=args.active_nodes)
         done = srv.run(stream)
         out = summarize(done, srv.elapsed, srv.node_updates)
-    out.update(mode="serial" if args.serial else "continuous batching",
+    out.update(mode="serial" if args.serial else f"continuous batching ({args.policy})",
                precision=args.precision, step_scale=args.step_scale, seed=args.seed,
-               chunk=args.chunk, budget_gb=args.budget_gb, max_nodes=args.max_nodes)
+               chunk=args.chunk, budget_gb=args.budget_gb, max_nodes=args.max_nodes,
+               active_nodes=args.active_nodes)
     print(json.dumps(out), flush=True)
 
 

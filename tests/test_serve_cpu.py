@@ -1,8 +1,9 @@
 """The serving loop's scheduling on the CPU, with the library calls replaced
-by fakes (no GPU): admission by memory budget and by the resident-node cap
-in arrival order, chunks that never run a request past its step count,
-every request finishing once, and a failing request reported without
-stopping the others."""
+by fakes (no GPU): admission by memory budget and (fifo policy) by the
+resident-node cap in arrival order, the srpt policy advancing the least
+remaining work first within the active-node cap, chunks that never run a
+request past its step count, every request finishing once, and a failing
+request reported without stopping the others."""
 import numpy as np
 import pytest
 
@@ -55,6 +56,17 @@ def fakes(monkeypatch):
     monkeypatch.setattr(lbm, "lbm_batch_run", run)
     monkeypatch.setattr(lbm, "lbm_batch_destroy", destroy)
     monkeypatch.setattr(torch.cuda, "synchronize", lambda *a, **k: None)
+
+    class NoFence:
+        def __init__(self, device):
+            pass
+
+        def mark(self):
+            pass
+
+        def drain(self):
+            pass
+    monkeypatch.setattr(serve, "_TickFence", NoFence)
     monkeypatch.setattr(serve.Server, "_config_bytes", lambda self, r: r.w["bytes"])
 
     def admit(self, r, now):
@@ -97,7 +109,7 @@ def test_every_request_finishes_once_within_the_budget(fakes):
 def test_node_cap_admits_in_arrival_order(fakes):
     stream = _stream(12, seed=1)
     cap = 5000
-    srv = serve.Server(None, 10 ** 12, chunk=5, max_nodes=cap)
+    srv = serve.Server(None, 10 ** 12, chunk=5, max_nodes=cap, policy="fifo")
     srv.mech = type("M", (), {"n_species": 9})()
     done = _run(srv, stream, fakes)
     assert len(done) == 12
@@ -117,3 +129,31 @@ def test_a_failing_request_is_reported_and_the_others_finish(fakes):
     assert [f["request"] for f in out["failed"]] == [3]
     assert "Newton" in out["failed"][0]["error"]
     assert all(r.error is None for r in done if r.rid != 3)
+
+
+def test_srpt_advances_least_remaining_work_first(fakes):
+    """A long request that arrived first and a short one that arrived later,
+    both resident, with room to advance only one at a time: the short one
+    runs first and finishes first; the long one then runs to its end."""
+    stream = [(0.0, {"P": np.zeros(4096), "steps": 40, "lattice": "D3Q27", "bytes": 10}),
+              (0.0, {"P": np.zeros(4096), "steps": 5, "lattice": "D3Q27", "bytes": 10})]
+    srv = serve.Server(None, 10 ** 12, chunk=10, policy="srpt", active_nodes=5000)
+    srv.mech = type("M", (), {"n_species": 9})()
+    done = _run(srv, stream, fakes)
+    assert [r.rid for r in done] == [1, 0]
+    assert all(len(members) == 1 for members, _n in fakes["runs"])
+    assert fakes["runs"][0] == ((1,), 5)
+    assert sum(n for members, n in fakes["runs"] if members == (0,)) == 40
+
+
+def test_srpt_keeps_the_advanced_nodes_within_the_cap(fakes):
+    stream = _stream(12, seed=4)
+    cap = 5000
+    srv = serve.Server(None, 10 ** 12, chunk=6, policy="srpt", active_nodes=cap)
+    srv.mech = type("M", (), {"n_species": 9})()
+    done = _run(srv, stream, fakes)
+    assert sorted(r.rid for r in done) == list(range(12))
+    nodes = {k: int(w["P"].size) for k, (_a, w) in enumerate(stream)}
+    for members, n in fakes["runs"]:
+        assert sum(nodes[m] for m in members) <= cap or len(members) == 1
+        assert 1 <= n <= 6
