@@ -808,7 +808,7 @@ template <int D, int M, typename RT> struct NodePar {
   RT rho, om, U, theta;          // density, omega, internal energy, R T (lattice)
   RT u[D], Pex[D], W[D];         // velocity, extended diagonal pressure, energy-flux term
   RT th[M], V[M][D], rs[M];      // theta_b, diffusion velocities, rho_b
-  RT cF[M - 1], tb[M - 1], dr[M - 1];   // (beta_a - 1) Y_a s, 2 beta_a, reaction increments
+  RT cF[M - 1], om1[M - 1], hh[M - 1];  // (beta_a - 1) Y_a s, 1 - 2 beta_a, 2 beta_a rho_a + drho_a
 };
 
 // Field offsets of NodePar stored field-major [field][N] (split collision).
@@ -817,9 +817,9 @@ template <int D, int M> struct CPar {
   static constexpr int V = TH + M;
   static constexpr int RS = V + M * D;
   static constexpr int CF = RS + M;
-  static constexpr int TB = CF + M - 1;
-  static constexpr int DR = TB + M - 1;
-  static constexpr int U = DR + M - 1;
+  static constexpr int OM1 = CF + M - 1;
+  static constexpr int HH = OM1 + M - 1;
+  static constexpr int U = HH + M - 1;
   static constexpr int PEX = U + D;
   static constexpr int W = PEX + D;
   static constexpr int RHO = W + D;
@@ -1066,15 +1066,17 @@ __device__ __forceinline__ void node_params(const RT* __restrict__ rec,
   p.om = RT(omega);
   p.U = RT(U_lat);
   p.theta = RT(theta);
-  // species coefficients of the update:
-  // f_a += 2 beta_a (rho_a psi_a - f_a) + cF_a sum_b K_ab d_b + drho_a psi_a
-  // with cF_a = (beta_a - 1) Y_a s (1/tau_ab = s K_ab)
+  // species coefficients of the update
+  //   f_a + 2 beta_a (rho_a psi_a - f_a) + cF_a sum_b K_ab d_b + drho_a psi_a
+  //     = f_a om1_a + psi_a hh_a + cF_a sum_b K_ab d_b,
+  // cF_a = (beta_a - 1) Y_a s (1/tau_ab = s K_ab), om1_a = 1 - 2 beta_a,
+  // hh_a = 2 beta_a rho_a + drho_a
 #pragma unroll
   for (int a = 0; a < M - 1; ++a) {
-    const RT beta = RT(inv_tau_a[a] / (PT(2) + inv_tau_a[a]));
-    p.cF[a] = RT((inv_tau_a[a] / (PT(2) + inv_tau_a[a]) - PT(1)) * Y[a] * s_tau);
-    p.dr[a] = rec[(RC::DRHO + a) * N + n];
-    p.tb[a] = RT(2) * beta;
+    const PT beta = inv_tau_a[a] / (PT(2) + inv_tau_a[a]);
+    p.cF[a] = RT((beta - PT(1)) * Y[a] * s_tau);
+    p.om1[a] = RT(PT(1) - PT(2) * beta);
+    p.hh[a] = RT(PT(2) * beta * rs[a] + PT(rec[(RC::DRHO + a) * N + n]));
   }
 }
 
@@ -1111,10 +1113,6 @@ __device__ __forceinline__ RT axis_factor(int e, const RT* th, const RT* u, cons
   return c == 0 ? RT(1) - Ps : (c > 0 ? RT(0.5) * (Ps + xs) : RT(0.5) * (Ps - xs));
 }
 
-// Collision of every lattice in direction i of node n (Sec. 2.3 Eq.
-// finalNumericalEquationsReactive; Sec. 3.2 Eqs. f, g; Sec. 3.3 Eq. feqmix):
-// PS supplies the node's parameters (registers, or the block's shared memory
-// in the split placement).
 // The M + 1 populations of direction i entering node n's collision (pulled
 // from node sn, or the boundary-reconstructed ones).
 template <int D, int M, typename S, typename RT>
@@ -1126,15 +1124,56 @@ __device__ __forceinline__ void load_direction(const S* __restrict__ src, const 
   for (int l = 0; l <= M; ++l) fin[l] = pop_in<RT>(src, bc, tag, N, sn, l * Q + i, codec);
 }
 
+// The part of the equilibria of direction (c_x, c_y, c_z) that depends on
+// (c_x, c_y) only, shared by the directions that differ in c_z (the product
+// form, Sec. 3.3 Eqs. prod, feqmix; Sec. 3.4 Eq. geq_i):
+//   species  e_b = psi_x psi_y of psi(u, theta_b), s_b the same of psi(u + V_b, theta_b);
+//   momentum rho psi_x psi_y of the extended equilibrium;
+//   energy   g^eq = rho [A_z (U A_x A_y + B_x A_y + A_x B_y) + A_x A_y B_z].
+template <int D, int M, typename RT> struct XYPart {
+  RT e[M], s[M];
+  RT fxy, gP, gQ;
+};
+
+template <int D, int M, typename RT, typename PS>
+__device__ __forceinline__ void xy_part(const PS& ps, int cx, int cy, XYPart<D, M, RT>& h) {
+#pragma unroll
+  for (int b = 0; b < M; ++b) {
+    h.e[b] = ps.sp(0, b, 0, cx) * ps.sp(0, b, 1, cy);
+    h.s[b] = ps.sp(1, b, 0, cx) * ps.sp(1, b, 1, cy);
+  }
+  h.fxy = ps.rho() * psi1<RT>(cx, ps.u(0), ps.Pex(0)) * psi1<RT>(cy, ps.u(1), ps.Pex(1));
+  const RT ax = ps.Af(0, cx), ay = ps.Af(1, cy);
+  h.gP = ax * ay;
+  h.gQ = ps.U() * h.gP + ps.Bf(0, cx) * ay + ax * ps.Bf(1, cy);
+}
+
+// Collision of every lattice in direction i = (c_x, c_y, cz) of node n
+// (Sec. 2.3 Eq. finalNumericalEquationsReactive; Sec. 3.2 Eqs. f, g; Sec.
+// 3.3 Eq. feqmix), from the shared (c_x, c_y) part h.  PS supplies the
+// node's parameters (registers, or the block's shared memory in the split
+// placement).  The species update
+//   f_a + 2 beta_a (rho_a psi_a - f_a) + cF_a sum_b K_ab d_b + drho_a psi_a
+// is evaluated as f_a om1_a + psi_a hh_a + cF_a F_a with the per-node
+// om1_a = 1 - 2 beta_a and hh_a = 2 beta_a rho_a + drho_a.
 template <int D, int M, typename S, typename RT, typename PS>
-__device__ __forceinline__ void collide_direction(const PS& ps, int i, const RT (&fin)[M + 1],
+__device__ __forceinline__ void collide_direction(const PS& ps, const XYPart<D, M, RT>& h,
+                                                  int i, const RT (&fin)[M + 1],
                                                   S* __restrict__ dst, long long N, long long n,
                                                   const DevMech& mech, const float4* codec) {
   constexpr int Q = Lat<D>::Q;
-  int c[3];
-  c[0] = cvel(i, 0); c[1] = cvel(i, 1); c[2] = D == 3 ? cvel(i, 2) : 0;
+  const int cz = D == 3 ? cvel(i, 2) : 0;
   RT pe[M], dd[M];
-  ps.factors(c, pe, dd);
+#pragma unroll
+  for (int b = 0; b < M; ++b) {
+    RT e = h.e[b], st = h.s[b];
+    if constexpr (D == 3) {
+      e *= ps.sp(0, b, 2, cz);
+      st *= ps.sp(1, b, 2, cz);
+    }
+    pe[b] = e;
+    dd[b] = ps.rs(b) * (e - st);
+  }
 #pragma unroll
   for (int a = 0; a < M - 1; ++a) {
     RT F = RT(0);
@@ -1142,31 +1181,19 @@ __device__ __forceinline__ void collide_direction(const PS& ps, int i, const RT 
     for (int b = 0; b < M; ++b)
       if (b != a) F += kcoef<RT>(mech, a, b) * dd[b];
     const long long off = (long long)(a * Q + i) * N;
-    const RT f = fin[a];
-    const RT fn = f + ps.tb(a) * (ps.rs(a) * pe[a] - f) + ps.cF(a) * F + ps.dr(a) * pe[a];
+    const RT fn = fin[a] * ps.om1(a) + pe[a] * ps.hh(a) + ps.cF(a) * F;
     dst[off + n] = Codec<S>::enc(fn, codec, a * Q + i);
   }
   {
-    RT fex = ps.rho();
-#pragma unroll
-    for (int d = 0; d < D; ++d) fex *= psi1<RT>(c[d], ps.u(d), ps.Pex(d));
+    RT fex = h.fxy;
+    if constexpr (D == 3) fex *= psi1<RT>(cz, ps.u(2), ps.Pex(2));
     const long long off = (long long)((M - 1) * Q + i) * N;
     const RT f = fin[M - 1];
     dst[off + n] = Codec<S>::enc(f + ps.om() * (fex - f), codec, (M - 1) * Q + i);
   }
   {
-    RT prodA = RT(1);
-#pragma unroll
-    for (int d = 0; d < D; ++d) prodA *= ps.Af(d, c[d]);
-    RT geq = ps.U() * prodA;
-#pragma unroll
-    for (int d = 0; d < D; ++d) {
-      RT t = ps.Bf(d, c[d]);
-#pragma unroll
-      for (int e = 0; e < D; ++e)
-        if (e != d) t *= ps.Af(e, c[e]);
-      geq += t;
-    }
+    RT geq = h.gQ;
+    if constexpr (D == 3) geq = ps.Af(2, cz) * h.gQ + h.gP * ps.Bf(2, cz);
     geq *= ps.rho();
     const long long off = (long long)(M * Q + i) * N;
     const RT gv = fin[M];
@@ -1174,7 +1201,7 @@ __device__ __forceinline__ void collide_direction(const PS& ps, int i, const RT 
     if (csq(i, D) == 1) {
 #pragma unroll
       for (int d = 0; d < D; ++d)
-        if (c[d] != 0) gn += (c[d] > 0 ? RT(0.5) : RT(-0.5)) * ps.W(d);
+        if (cvel(i, d) != 0) gn += (cvel(i, d) > 0 ? RT(0.5) : RT(-0.5)) * ps.W(d);
     }
     dst[off + n] = Codec<S>::enc(gn, codec, M * Q + i);
   }
@@ -1199,42 +1226,15 @@ template <int D, int M, typename RT> struct RegPar {
   __device__ RT W(int d) const { return p.W[d]; }
   __device__ RT rs(int a) const { return p.rs[a]; }
   __device__ RT cF(int a) const { return p.cF[a]; }
-  __device__ RT tb(int a) const { return p.tb[a]; }
-  __device__ RT dr(int a) const { return p.dr[a]; }
+  __device__ RT om1(int a) const { return p.om1[a]; }
+  __device__ RT hh(int a) const { return p.hh[a]; }
   __device__ RT Af(int d, int c) const { return c == 0 ? Afv[d][1] : (c > 0 ? Afv[d][2] : Afv[d][0]); }
   __device__ RT Bf(int d, int c) const { return c == 0 ? Bfv[d][1] : (c > 0 ? Bfv[d][2] : Bfv[d][0]); }
-  __device__ void factors(const int (&c)[3], RT (&pe)[M], RT (&dd)[M]) const {
-    if (tab) {
-      int off[3];
-#pragma unroll
-      for (int d = 0; d < D; ++d) off[d] = (d * 3 + c[d] + 1) * kBS;
-#pragma unroll
-      for (int b = 0; b < M; ++b) {
-        const RT* te = tab + b * D * 3 * kBS;
-        const RT* ts = tab + (M + b) * D * 3 * kBS;
-        RT e = te[off[0]], st = ts[off[0]];
-#pragma unroll
-        for (int d = 1; d < D; ++d) {
-          e *= te[off[d]];
-          st *= ts[off[d]];
-        }
-        pe[b] = e;
-        dd[b] = p.rs[b] * (e - st);
-      }
-    } else {
-#pragma unroll
-      for (int b = 0; b < M; ++b) {
-        RT e = RT(1), st = RT(1);
-#pragma unroll
-        for (int d = 0; d < D; ++d) {
-          e *= psi1<RT>(c[d], p.u[d], p.th[b] + p.u[d] * p.u[d]);
-          const RT xs = p.u[d] + p.V[b][d];
-          st *= psi1<RT>(c[d], xs, p.th[b] + xs * xs);
-        }
-        pe[b] = e;
-        dd[b] = p.rs[b] * (e - st);
-      }
-    }
+  // species axis factor (set 0: psi(u, theta_b); set 1: psi(u + V_b, theta_b))
+  __device__ RT sp(int set, int b, int d, int c) const {
+    if (tab) return tab[(((set * M + b) * D + d) * 3 + c + 1) * kBS];
+    const RT xs = set ? p.u[d] + p.V[b][d] : p.u[d];
+    return psi1<RT>(c, xs, p.th[b] + xs * xs);
   }
 };
 
@@ -1269,12 +1269,18 @@ __device__ __forceinline__ void collide_body(const S* __restrict__ src, S* __res
       tab[e * kBS] = axis_factor<D, M, RT>(e, p.th, p.u, &p.V[0][0]);
   }
   const RegPar<D, M, RT> ps(p, tab);
+  // directions i = j + 9 k share (c_x, c_y) = direction j's
 #pragma unroll 1
-  for (int i = 0; i < Q; ++i) {
-    RT fin[M + 1];
-    load_direction<D, M, S, RT>(src, bc, tag, N, node_shift<D>(x, y, z, i, -1, g), i, g.codec,
-                                fin);
-    collide_direction<D, M, S, RT>(ps, i, fin, dst, N, n, mech, g.codec);
+  for (int j = 0; j < 9; ++j) {
+    XYPart<D, M, RT> h;
+    xy_part<D, M, RT>(ps, cvel(j, 0), cvel(j, 1), h);
+#pragma unroll 1
+    for (int i = j; i < Q; i += 9) {
+      RT fin[M + 1];
+      load_direction<D, M, S, RT>(src, bc, tag, N, node_shift<D>(x, y, z, i, -1, g), i,
+                                  g.codec, fin);
+      collide_direction<D, M, S, RT>(ps, h, i, fin, dst, N, n, mech, g.codec);
+    }
   }
 }
 
@@ -1307,8 +1313,8 @@ __device__ __forceinline__ void prep_body(const RT* __restrict__ rec,
 #pragma unroll
   for (int a = 0; a < M - 1; ++a) {
     cp[(CP::CF + a) * N + n] = p.cF[a];
-    cp[(CP::TB + a) * N + n] = p.tb[a];
-    cp[(CP::DR + a) * N + n] = p.dr[a];
+    cp[(CP::OM1 + a) * N + n] = p.om1[a];
+    cp[(CP::HH + a) * N + n] = p.hh[a];
   }
 #pragma unroll
   for (int d = 0; d < D; ++d) {
@@ -1346,23 +1352,12 @@ template <int D, int M, typename RT> struct SmemPar {
   __device__ RT W(int d) const { return get(CP::W + d); }
   __device__ RT rs(int a) const { return get(CP::RS + a); }
   __device__ RT cF(int a) const { return get(CP::CF + a); }
-  __device__ RT tb(int a) const { return get(CP::TB + a); }
-  __device__ RT dr(int a) const { return get(CP::DR + a); }
+  __device__ RT om1(int a) const { return get(CP::OM1 + a); }
+  __device__ RT hh(int a) const { return get(CP::HH + a); }
   __device__ RT Af(int d, int c) const { return get(AF + d * 3 + c + 1); }
   __device__ RT Bf(int d, int c) const { return get(BF + d * 3 + c + 1); }
-  __device__ void factors(const int (&c)[3], RT (&pe)[M], RT (&dd)[M]) const {
-#pragma unroll
-    for (int b = 0; b < M; ++b) {
-      RT e = get(TAB + (b * D) * 3 + c[0] + 1);
-      RT st = get(TAB + ((M + b) * D) * 3 + c[0] + 1);
-#pragma unroll
-      for (int d = 1; d < D; ++d) {
-        e *= get(TAB + (b * D + d) * 3 + c[d] + 1);
-        st *= get(TAB + ((M + b) * D + d) * 3 + c[d] + 1);
-      }
-      pe[b] = e;
-      dd[b] = rs(b) * (e - st);
-    }
+  __device__ RT sp(int set, int b, int d, int c) const {
+    return get(TAB + ((set * M + b) * D + d) * 3 + c + 1);
   }
 };
 
@@ -1416,19 +1411,25 @@ __device__ __forceinline__ void coll_block(const S* __restrict__ src, S* __restr
   const int x = (int)(n % g.nx);
   const int y = (int)((n / g.nx) % g.ny);
   const int z = (int)(n / ((long long)g.nx * g.ny));
-  // software pipeline: the next direction's populations are in flight while
-  // this one collides (each thread has Q / kCollTPN directions)
+  // warp w takes the directions i = w + 9 k, which share (c_x, c_y); software
+  // pipeline: the next direction's populations are in flight while this one
+  // collides
+  // (FP64: the pair part is formed once and kept in registers; FP32 forms it
+  // per direction, which keeps k_coll within its 56-register budget)
+  static_assert(kCollTPN == 9, "one warp per (c_x, c_y) pair");
+  XYPart<D, M, RT> h;
+  if constexpr (sizeof(RT) == 8) xy_part<D, M, RT>(ps, cvel(w, 0), cvel(w, 1), h);
   RT fa[M + 1], fb[M + 1];
-  if (w < Q)
-    load_direction<D, M, S, RT>(src, bc, tag, N, node_shift<D>(x, y, z, w, -1, g), w, g.codec,
-                                fa);
+  load_direction<D, M, S, RT>(src, bc, tag, N, node_shift<D>(x, y, z, w, -1, g), w, g.codec,
+                              fa);
 #pragma unroll 1
   for (int i = w; i < Q; i += kCollTPN) {
     const int inext = i + kCollTPN;
     if (inext < Q)
       load_direction<D, M, S, RT>(src, bc, tag, N, node_shift<D>(x, y, z, inext, -1, g), inext,
                                   g.codec, fb);
-    collide_direction<D, M, S, RT>(ps, i, fa, dst, N, n, mech, g.codec);
+    if constexpr (sizeof(RT) == 4) xy_part<D, M, RT>(ps, cvel(w, 0), cvel(w, 1), h);
+    collide_direction<D, M, S, RT>(ps, h, i, fa, dst, N, n, mech, g.codec);
 #pragma unroll
     for (int l = 0; l <= M; ++l) fa[l] = fb[l];
   }
