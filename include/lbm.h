@@ -278,8 +278,21 @@ typedef struct {
   int collide_split;
   int persistent;     /* batch plans only: 1 = every batched kernel runs a grid
                          of the blocks the GPU holds at once, each block
-                         looping over tiles of the work-list; 0 / -1 (the
-                         default) = one block per tile */
+                         looping over tiles of the work-list; 2 = the whole
+                         step as ONE launch: a grid of the resident blocks
+                         claims the items of a work-list in stage order
+                         (boundary + sub-steps of 128 interface nodes,
+                         moments + sub-steps of a node tile; collision
+                         parameters of a node tile once its domain's first
+                         stage is done; the collision of 32 nodes once their
+                         parameters are), with chem_lanes 1 and split
+                         collision; a dependency wait that outlasts 4 s
+                         ends the launch and the handles report
+                         LBM_ERR_TIMEOUT; 0 = one block per tile; -1 = the
+                         default: 2 for plans of FP64 storage, else 0 */
+  int nodes_per_thread;  /* persistent = 2: nodes per thread of the node
+                         tiles, 1, 2 or 4 (tiles of 128, 256, 512 nodes);
+                         -1 = 1 */
 } lbm_launch;
 
 /* Set / read the handle's placement (lbm_get_launch reports the resolved
@@ -295,13 +308,17 @@ lbm_status lbm_get_launch(lbm_t h, lbm_launch* l);
  * exactly as without the call.  Synchronises. */
 lbm_status lbm_autotune(lbm_t h, int trial_steps, lbm_launch* chosen);
 
-/* The same for a batch plan: times each placement over the whole batch, keeps
- * the fastest and captures the plan's graphs again with it.  A new plan
- * starts with the placement chosen by the batch's total node count. */
+/* The same for a batch plan: times trial_steps replays of each placement's
+ * captured one-step graph over the whole batch (the six placements above,
+ * the best of them with persistent grids, and the single launch with 1, 2
+ * and 4 nodes per thread), keeps the fastest and captures the plan's graphs
+ * again with it.  A new plan starts with the default placement (see
+ * lbm_batch_set_launch). */
 lbm_status lbm_batch_autotune(lbm_batch_t b, int trial_steps, lbm_launch* chosen);
 
-/* Set a plan's placement (-1 fields: the default for the batch's total node
- * count) and capture its graphs again; read the placement in use.  A
+/* Set a plan's placement (-1 fields: the default for the batch's precision
+ * and total node count) and capture its graphs again; read the placement in
+ * use.  A
  * performance choice with no counterpart in the paper: every placement
  * computes the step of Secs. 2-4.  The handles' own lbm_set_launch values do
  * not apply to plans.  l is the caller's; the plan keeps a copy.
@@ -386,6 +403,16 @@ lbm_status lbm_ff_check(const double* x, long long n, double* exp_out, double* l
  * frees one element of device memory.  LBM_ERR_INVALID for a NULL tflops,
  * LBM_ERR_CUDA on a device error. */
 lbm_status lbm_fma_peak(int fp64, double* tflops);
+
+/* Check of the bounded device wait the single-launch batched step uses for
+ * its dependencies (no counterpart in the paper): one thread waits for a
+ * device word that is already 1 (set_word = 1) or that nothing sets
+ * (set_word = 0), giving up after timeout_ns.  result[0] = 1 if the wait saw
+ * the word set, result[1] = the abort word afterwards (1 after a timeout),
+ * result[2] = the wait's length in microseconds.  Synchronous; on the current
+ * device.  LBM_ERR_INVALID for a NULL result or a negative timeout,
+ * LBM_ERR_RANGE for timeout_ns > 1e8, LBM_ERR_CUDA on a device error. */
+lbm_status lbm_wait_probe(int set_word, long long timeout_ns, long long* result);
 
 /* Allocation-free single step.  The paper has no counterpart: this entry
  * point exists for callers that cannot allocate device memory themselves -

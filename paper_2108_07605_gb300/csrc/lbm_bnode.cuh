@@ -484,7 +484,7 @@ __device__ __forceinline__ void bnode_body(const S* __restrict__ src, const BCDe
         sf.us = L.us;
         BNode<D, M, S, R> nf{src, codec, N, (long long)bc.if_nbr[k]};
         bsums<D, M, R>(nf, z);
-        bstate_of<D, M, R>(sf, z, Tf[n], m, un, status);
+        bstate_of<D, M, R>(sf, z, __ldcg(Tf + n), m, un, status);
         const double h = bc.if_wh[k], dl = bc.if_wd[k];
         const R w = R(dl / (h + dl));
 #pragma unroll
@@ -516,10 +516,10 @@ __device__ __forceinline__ void bnode_body(const S* __restrict__ src, const BCDe
       s0.us = s1.us = nullptr;
       BNode<D, M, S, R> n0{src, codec, N, n};
       bsums<D, M, R>(n0, z);
-      bstate_of<D, M, R>(s0, z, Tf[n], m, un, status);
+      bstate_of<D, M, R>(s0, z, __ldcg(Tf + n), m, un, status);
       BNode<D, M, S, R> n1{src, codec, N, up};
       bsums<D, M, R>(n1, z);
-      bstate_of<D, M, R>(s1, z, Tf[n], m, un, status);
+      bstate_of<D, M, R>(s1, z, __ldcg(Tf + n), m, un, status);
       double R0 = 0.0, R1 = 0.0, Cv = 0.0;
       const double T0 = s0.T, T1 = s1.T;
 #pragma unroll
@@ -567,7 +567,7 @@ __device__ __forceinline__ void bnode_body(const S* __restrict__ src, const BCDe
     BLocal<D, M, S, R> local{Pull{src, codec, N, n, sncol, inc, false}, &A, &m, &un, {}};
     bsums<D, M, R>(local, z);
     if (kind != BK_TMS) L.us = nullptr;               // TMS local species use u_a^loc
-    bstate_of<D, M, R>(L, z, Tf[n], m, un, status);
+    bstate_of<D, M, R>(L, z, __ldcg(Tf + n), m, un, status);
     if (kind == BK_INLET) {                           // target (Eqs. in_tgt_*)
       B.rho = L.rho;
       B.Y = L.Y;
@@ -588,7 +588,7 @@ __device__ __forceinline__ void bnode_body(const S* __restrict__ src, const BCDe
   BState<D, M, R> s;
   s.Y = A.Y;                                    // the target columns are free now
   s.us = col + 3 * M * kBnd;
-  bstate_of<D, M, R>(s, z, Tf[n], m, un, status);
+  bstate_of<D, M, R>(s, z, __ldcg(Tf + n), m, un, status);
   if (!(s.rho > R(0)) || !isfinite(double(s.rho)) || !isfinite(s.T_full))
     atomicOr(status, ST_NONFINITE);
   Tf[n] = s.T_full;

@@ -62,13 +62,19 @@ lbm_status cuda_fail(lbm_ctx* h, cudaError_t e, const char* where) {
 // the extra redundant work of the lanes costs more than it hides.
 constexpr long long kSmallGrid = 152LL * 4 * 128;
 
-Launch resolve_launch(const lbm_launch& opt, long long nodes, lbm_precision prec) {
+// plan: a batch plan's placement, whose default for FP64 storage is the
+// single launch over the work-list (measured faster there; FP32 and FP16
+// keep one launch per kernel, whose kernels hold fewer registers)
+Launch resolve_launch(const lbm_launch& opt, long long nodes, lbm_precision prec,
+                      bool plan = false) {
   Launch lc;
   const bool small = nodes < kSmallGrid;
   lc.chem_lanes = opt.chem_lanes > 0 ? opt.chem_lanes
                                      : (small && prec == LBM_FP32_STORE ? 4 : 1);
   lc.coll_split = opt.collide_split >= 0 ? opt.collide_split : 1;
-  lc.persistent = opt.persistent > 0 ? 1 : 0;
+  lc.persistent = opt.persistent >= 0 ? opt.persistent
+                                     : (plan && prec == LBM_FP64 ? 2 : 0);
+  lc.npt = opt.nodes_per_thread > 0 ? opt.nodes_per_thread : 1;
   return lc;
 }
 
@@ -472,6 +478,7 @@ lbm_status check_status(lbm_ctx* h) {
   if (st & ST_NEWTON) return fail(h, LBM_ERR_NEWTON, "temperature Newton did not converge");
   if (st & ST_NONFINITE) return fail(h, LBM_ERR_NONFINITE, "non-finite or non-positive density or temperature");
   if (st & ST_RANGE) return fail(h, LBM_ERR_RANGE, "value out of range");
+  if (st & ST_TIMEOUT) return fail(h, LBM_ERR_TIMEOUT, "a bounded device wait gave up");
   return LBM_OK;
 }
 
@@ -938,7 +945,10 @@ lbm_status lbm_set_launch(lbm_t h, const lbm_launch* l) {
   if (l->collide_split < -1 || l->collide_split > 1)
     return fail(h, LBM_ERR_INVALID, "collide_split must be -1, 0 or 1");
   if (l->persistent < -1 || l->persistent > 1)
-    return fail(h, LBM_ERR_INVALID, "persistent must be -1, 0 or 1");
+    return fail(h, LBM_ERR_INVALID, "persistent must be -1, 0 or 1 (2: batch plans only)");
+  if (l->nodes_per_thread != -1 && l->nodes_per_thread != 1 && l->nodes_per_thread != 2 &&
+      l->nodes_per_thread != 4)
+    return fail(h, LBM_ERR_INVALID, "nodes_per_thread must be -1, 1, 2 or 4");
   h->opt = *l;
   return LBM_OK;
 }
@@ -949,6 +959,7 @@ lbm_status lbm_get_launch(lbm_t h, lbm_launch* l) {
   l->chem_lanes = lc.chem_lanes;
   l->collide_split = lc.coll_split;
   l->persistent = lc.persistent;
+  l->nodes_per_thread = lc.npt;
   return LBM_OK;
 }
 
@@ -1013,7 +1024,9 @@ lbm_status lbm_autotune(lbm_t h, int trial_steps, lbm_launch* chosen) {
   h->opt.collide_split = best.coll_split;
   if (chosen) {
     *chosen = h->opt;
-    chosen->persistent = resolve_launch(h->opt, h->g.N, h->cfg.precision).persistent;
+    const Launch r = resolve_launch(h->opt, h->g.N, h->cfg.precision);
+    chosen->persistent = r.persistent;
+    chosen->nodes_per_thread = r.npt;
   }
   return LBM_OK;
 }
@@ -1039,7 +1052,7 @@ lbm_status lbm_batch_step(lbm_t* hs, int n, int nsteps) {
   DeviceGuard dg(h0->cfg.device);
   std::vector<DomainDev> doms;
   BatchGrids gr;
-  const Launch lc = resolve_launch(lbm_launch{-1, -1, -1}, total_nodes(hs, n), hs[0]->cfg.precision);
+  const Launch lc = resolve_launch(lbm_launch{-1, -1, -1, -1}, total_nodes(hs, n), hs[0]->cfg.precision);
   fill_domains(hs, n, lc, doms, gr);
   // every handle's earlier work precedes the batch; the batch runs on the
   // first handle's stream and each handle's stream waits for it afterwards
@@ -1085,17 +1098,76 @@ struct lbm_batch_ctx {
   int parity = 0;
   cudaStream_t stream = nullptr;
   cudaGraphExec_t one[2] = {nullptr, nullptr}, two[2] = {nullptr, nullptr};
+  // persistent == 2: the work-list and its sync words on the device
+  PItem* items = nullptr;
+  int items_cap = 0;
+  int* sync = nullptr;
+  int sync_cap = 0;
 };
 
 namespace {
 
+// The work-list of the single-launch step (PItem): stage 1 (the boundary
+// items of every domain, then the moments items), stage 2 (parameter items),
+// stage 3 (collision items), each stage domain by domain.  nsync: the sync
+// words the launch needs.
+void build_worklist(lbm_ctx* const* hs, int n, int npt, std::vector<PItem>& items, int& nsync) {
+  items.clear();
+  const long long tile = (long long)kPersistThreads * npt;
+  std::vector<int> n1(n, 0), pbase(n, 0);
+  for (int k = 0; k < n; ++k)
+    for (long long f = 0; f < hs[k]->bc.n_if; f += kPersistBndNodes, ++n1[k])
+      items.push_back(PItem{PI_BND, k, f, 0, 0});
+  for (int k = 0; k < n; ++k)
+    for (long long f = 0; f < hs[k]->g.N; f += tile, ++n1[k])
+      items.push_back(PItem{PI_MOM, k, f, 0, 0});
+  int nflag = 0;
+  for (int k = 0; k < n; ++k) {
+    pbase[k] = nflag;
+    for (long long f = 0; f < hs[k]->g.N; f += tile)
+      items.push_back(PItem{PI_PREP, k, f, n1[k], nflag++});
+  }
+  for (int k = 0; k < n; ++k)
+    for (long long f = 0; f < hs[k]->g.N; f += kCollNodesPerBlock)
+      items.push_back(PItem{PI_COLL, k, f, pbase[k] + (int)(f / tile), 0});
+  nsync = kSyncHead + n + nflag;
+}
+
 cudaError_t batch_upload(lbm_batch_ctx* b) {
   std::vector<DomainDev> doms;
-  fill_domains(b->hs.data(), (int)b->hs.size(), b->lc, doms, b->gr);
-  for (size_t k = 0; k < b->hs.size(); ++k) b->cur[k] = b->hs[k]->cur;
+  const int n = (int)b->hs.size();
+  fill_domains(b->hs.data(), n, b->lc, doms, b->gr);
+  for (int k = 0; k < n; ++k) b->cur[k] = b->hs[k]->cur;
   b->parity = 0;
   cudaError_t e = cudaMemcpyAsync(b->ddev, doms.data(), doms.size() * sizeof(DomainDev),
                                   cudaMemcpyHostToDevice, b->stream);
+  if (e == cudaSuccess && b->lc.persistent == 2) {
+    std::vector<PItem> items;
+    int nsync = 0;
+    build_worklist(b->hs.data(), n, b->lc.npt, items, nsync);
+    const lbm_config& cfg = b->hs[0]->cfg;
+    if ((int)items.size() > b->items_cap) {
+      e = cudaStreamSynchronize(b->stream);
+      dfree(cfg, b->items);
+      b->items = static_cast<PItem*>(dalloc(cfg, items.size() * sizeof(PItem)));
+      b->items_cap = b->items ? (int)items.size() : 0;
+      if (!b->items) e = cudaErrorMemoryAllocation;
+    }
+    if (e == cudaSuccess && nsync > b->sync_cap) {
+      e = cudaStreamSynchronize(b->stream);
+      dfree(cfg, b->sync);
+      b->sync = static_cast<int*>(dalloc(cfg, (size_t)nsync * sizeof(int)));
+      b->sync_cap = b->sync ? nsync : 0;
+      if (!b->sync) e = cudaErrorMemoryAllocation;
+    }
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(b->items, items.data(), items.size() * sizeof(PItem),
+                          cudaMemcpyHostToDevice, b->stream);
+    b->gr.items = b->items;
+    b->gr.nitems = (int)items.size();
+    b->gr.sync = b->sync;
+    b->gr.nsync = nsync;
+  }
   if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
   return e;
 }
@@ -1145,6 +1217,8 @@ lbm_status lbm_batch_destroy(lbm_batch_t b) {
   if (b->side.join) cudaEventDestroy(b->side.join);
   if (b->side.stream) cudaStreamDestroy(b->side.stream);
   if (b->ddev && !b->hs.empty()) dfree(b->hs[0]->cfg, b->ddev);
+  if (b->items && !b->hs.empty()) dfree(b->hs[0]->cfg, b->items);
+  if (b->sync && !b->hs.empty()) dfree(b->hs[0]->cfg, b->sync);
   if (b->stream) cudaStreamDestroy(b->stream);
   delete b;
   return LBM_OK;
@@ -1168,7 +1242,8 @@ lbm_status lbm_batch_create(lbm_t* hs, int n, lbm_batch_t* out) {
     b->ddev = static_cast<DomainDev*>(dalloc(h0->cfg, n * sizeof(DomainDev)));
     if (!b->ddev) e = cudaErrorMemoryAllocation;
   }
-  b->lc = resolve_launch(lbm_launch{-1, -1, -1}, total_nodes(hs, n), hs[0]->cfg.precision);
+  b->lc = resolve_launch(lbm_launch{-1, -1, -1, -1}, total_nodes(hs, n), hs[0]->cfg.precision,
+                         true);
   if (e == cudaSuccess) e = batch_upload(b);
   if (e == cudaSuccess) e = prepare_batch_step(h0->D, h0->M, kernel_precision(h0->cfg));
   if (e == cudaSuccess) e = batch_capture_all(b);
@@ -1223,11 +1298,14 @@ lbm_status lbm_batch_set_launch(lbm_batch_t b, const lbm_launch* l) {
   if (!b || !l) return fail(nullptr, LBM_ERR_INVALID, "plan or launch is NULL");
   lbm_ctx* h0 = b->hs[0];
   if ((l->chem_lanes != -1 && l->chem_lanes != 1 && l->chem_lanes != 4 && l->chem_lanes != 8) ||
-      l->collide_split < -1 || l->collide_split > 1 || l->persistent < -1 || l->persistent > 1)
+      l->collide_split < -1 || l->collide_split > 1 || l->persistent < -1 || l->persistent > 2 ||
+      (l->nodes_per_thread != -1 && l->nodes_per_thread != 1 && l->nodes_per_thread != 2 &&
+       l->nodes_per_thread != 4))
     return fail(h0, LBM_ERR_INVALID, "placement out of range");
   DeviceGuard dg(h0->cfg.device);
   cudaError_t e = cudaStreamSynchronize(b->stream);
-  b->lc = resolve_launch(*l, total_nodes(b->hs.data(), (int)b->hs.size()), h0->cfg.precision);
+  b->lc = resolve_launch(*l, total_nodes(b->hs.data(), (int)b->hs.size()), h0->cfg.precision,
+                         true);
   if (e == cudaSuccess) e = batch_upload(b);
   if (e == cudaSuccess) e = batch_capture_all(b);
   return e == cudaSuccess ? LBM_OK : cuda_fail(h0, e, "batch placement");
@@ -1238,6 +1316,7 @@ lbm_status lbm_batch_get_launch(lbm_batch_t b, lbm_launch* l) {
   l->chem_lanes = b->lc.chem_lanes;
   l->collide_split = b->lc.coll_split;
   l->persistent = b->lc.persistent;
+  l->nodes_per_thread = b->lc.npt;
   return LBM_OK;
 }
 
@@ -1265,28 +1344,36 @@ lbm_status lbm_batch_autotune(lbm_batch_t b, int trial_steps, lbm_launch* chosen
   Launch best = b->lc;
   bool first = true;
   // stage 1: the six placements with one block per tile; stage 2: the best
-  // of them with persistent grids
+  // of them with persistent grids; stage 3: the whole step as one launch over
+  // the work-list with 1, 2 and 4 nodes per thread (tiles of 128, 256, 512
+  // nodes)
   const size_t nc = sizeof(kCandidates) / sizeof(kCandidates[0]);
-  for (size_t ci = 0; ci <= nc; ++ci) {
+  const int npts[3] = {1, 2, 4};
+  for (size_t ci = 0; ci <= nc + 3; ++ci) {
     if (e != cudaSuccess) break;
     Launch cand;
     if (ci < nc) {
       cand = kCandidates[ci];
-    } else {
+    } else if (ci == nc) {
       cand = best;
       cand.persistent = 1;
+    } else {
+      cand = Launch();
+      cand.chem_lanes = 1;
+      cand.coll_split = 1;
+      cand.persistent = 2;
+      cand.npt = npts[ci - nc - 1];
     }
     b->lc = cand;
     e = batch_upload(b);
-    // parity 0 every time: each trial step recomputes the next state of every
-    // handle from its current buffer, advancing none of them
-    if (e == cudaSuccess)
-      e = launch_batch_step(h0->D, h0->M, kernel_precision(h0->cfg), b->ddev, n, b->gr, b->lc, 0,
-                            b->stream, b->side);
+    // the candidate as the plan would run it: its captured one-step graph
+    // from parity 0, replayed; every trial step recomputes the next state of
+    // every handle from its current buffer, advancing none of them
+    if (e == cudaSuccess) e = batch_capture_all(b);
+    if (e == cudaSuccess) e = cudaGraphLaunch(b->one[0], b->stream);
     if (e == cudaSuccess) e = cudaEventRecord(e0, b->stream);
     for (int t = 0; t < trial_steps && e == cudaSuccess; ++t)
-      e = launch_batch_step(h0->D, h0->M, kernel_precision(h0->cfg), b->ddev, n, b->gr, b->lc, 0,
-                            b->stream, b->side);
+      e = cudaGraphLaunch(b->one[0], b->stream);
     if (e == cudaSuccess) e = cudaEventRecord(e1, b->stream);
     for (int k = 0; k < n && e == cudaSuccess; ++k)
       e = cudaMemcpyAsync(b->hs[k]->Tf, Tsave[k], (size_t)b->hs[k]->g.N * sizeof(double),
@@ -1314,6 +1401,7 @@ lbm_status lbm_batch_autotune(lbm_batch_t b, int trial_steps, lbm_launch* chosen
     chosen->chem_lanes = best.chem_lanes;
     chosen->collide_split = best.coll_split;
     chosen->persistent = best.persistent;
+    chosen->nodes_per_thread = best.npt;
   }
   return LBM_OK;
 }

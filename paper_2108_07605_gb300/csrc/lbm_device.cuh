@@ -193,10 +193,15 @@ __device__ ff newton_T_ff(const DevMech& m, const ff* Y, ff U, ff T, int max_ite
 // that runs the float-float rates has kChemThreads threads per block.
 constexpr int kChemThreads = 128;
 
+// bytes of one block's slices (kChemThreads threads, C, G and W per species)
+template <int M, typename CT> constexpr size_t chem_slice_bytes() {
+  return (size_t)3 * M * kChemThreads * sizeof(CT);
+}
+
+// Cs: this thread's slice (entry a of C at Cs[a kChemThreads], then G and W)
 template <int M>
-__device__ void production_rates_ff(const DevMech& m, ff T, const ff* r, ff* rdot) {
-  __shared__ __align__(8) unsigned char chem_raw[3 * M * kChemThreads * sizeof(ff)];
-  ff* const Cs = reinterpret_cast<ff*>(chem_raw) + threadIdx.x;   // entry a at [a kChemThreads]
+__device__ void production_rates_ff(const DevMech& m, ff T, const ff* r, ff* rdot,
+                                    ff* const Cs) {
   ff* const Gs = Cs + M * kChemThreads;
   ff* const Ws = Gs + M * kChemThreads;
   const ff lnT = ff_log(T);

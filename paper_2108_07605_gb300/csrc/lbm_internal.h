@@ -23,6 +23,7 @@ constexpr double RHO_TINY = 1e-300;       // u_a := u below this species density
 constexpr int ST_NEWTON = 1;
 constexpr int ST_NONFINITE = 2;
 constexpr int ST_RANGE = 4;
+constexpr int ST_TIMEOUT = 8;   // a bounded device wait gave up
 
 struct DevReaction {
   int nr, np;            // number of reactant / product molecules (<= 3)
@@ -126,7 +127,9 @@ struct BCDev {
 struct Launch {
   int chem_lanes = 1;    // 1: chemistry inside the moments kernel; 4 or 8: k_chem lanes per node
   int coll_split = 0;    // 0: fused collision; 1: k_prep + k_coll
-  int persistent = 0;    // batched kernels: 1 = grids of the resident blocks, looping over tiles
+  int persistent = 0;    // batched kernels: 1 = grids of the resident blocks, looping over
+                         // tiles; 2 = the whole step as one launch over a work-list
+  int npt = 1;           // persistent == 2: nodes per thread of the node items (1, 2, 4)
 };
 
 struct StepArgs {
@@ -175,6 +178,32 @@ struct SideStream {
   cudaEvent_t fork = nullptr, join = nullptr;
 };
 
+// The whole batched step as one launch (Launch::persistent == 2): a
+// work-list of items in stage order, claimed by the blocks of a persistent
+// grid through an atomic counter.  Stage 1: PI_BND (kPersistBndNodes
+// interface nodes: boundary reconstruction, record, reaction sub-steps) and
+// PI_MOM (kPersistThreads * npt nodes: moments, sub-steps); stage 2: PI_PREP
+// (collision parameters of kPersistThreads * npt nodes), after every stage-1
+// item of its domain; stage 3: PI_COLL (kCollNodesPerBlock nodes), after the
+// PI_PREP item holding its nodes.  An item waits only on items earlier in
+// the list, which blocks already running hold, so every wait ends without
+// any assumption on how many blocks are resident.
+enum PItemKind : int { PI_BND = 0, PI_MOM = 1, PI_PREP = 2, PI_COLL = 3 };
+struct PItem {
+  int kind;     // PItemKind
+  int dom;      // domain index
+  long long first;   // first interface index (PI_BND) or first node
+  int dep;      // PI_PREP: the domain's stage-1 item count; PI_COLL: the flag to wait for
+  int flag;     // PI_PREP: the flag it sets
+};
+constexpr int kPersistThreads = 128;
+constexpr int kPersistBndNodes = 128;
+// sync words of the work-list: [0] next item, [1] abort, then one stage-1
+// completion count per domain, then one flag per PI_PREP item
+constexpr int kSyncHead = 2;
+// a wait of the persistent step gives up after this long (it sets ST_TIMEOUT)
+constexpr long long kPersistTimeoutNs = 4000000000LL;
+
 // Block totals of the batched grids.
 struct BatchGrids {
   int nblocks = 0;    // node kernels, 128 nodes per block
@@ -182,6 +211,14 @@ struct BatchGrids {
   int ntblocks = 0;   // k_bnode, kBndNodesPerBlock interface nodes per block
   int ncblocks = 0;   // k_chem, 128 / chem_lanes nodes per block (0 without it)
   int nkblocks = 0;   // k_coll, 32 nodes per block (0 without it)
+  // persistent == 2: the device work-list and its sync words (zeroed before
+  // every launch), the domains' interface-node presence
+  const PItem* items = nullptr;
+  int nitems = 0;
+  int* sync = nullptr;
+  int nsync = 0;
+  int any_if = 0;
+  long long timeout_ns = kPersistTimeoutNs;
 };
 
 // interface nodes per block of the boundary kernel (one thread each)

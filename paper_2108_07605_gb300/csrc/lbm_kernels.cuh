@@ -30,6 +30,7 @@
 #pragma once
 
 #include "lbm_device.cuh"
+#include "lbm_sync.cuh"
 
 // Chemistry mode of the mixed path in this translation unit: with FP32
 // lattice arithmetic, the temperature Newton solve and the reaction
@@ -135,19 +136,91 @@ __device__ __forceinline__ constexpr int pidx(int a, int b) {
 }
 
 // ---------------------------------------------------------------------------
+// Reaction sub-steps of one node by one thread at frozen internal energy
+// (Sec. 2.4 Eq. R3): rs the post-stream species densities (the slaved one
+// included), rho, ER = E / rho and usqR = |u|^2 of the moments, T_0 = T
+// their temperature; dr receives the increments drho_a (a < M - 1).  The
+// mixed path runs it in float-float, whose rate arrays live in the thread's
+// shared-memory slice (kDynChem: chem_slice, the block's slices of
+// chem_slice_bytes in dynamic shared memory; else a static array of the
+// calling kernel); FP64 chemistry otherwise.  Blocks of kChemThreads threads.
+template <int M>
+__device__ __forceinline__ ff* chem_static_slice() {
+  __shared__ __align__(8) unsigned char chem_raw[chem_slice_bytes<M, ff>()];
+  return reinterpret_cast<ff*>(chem_raw);
+}
+
+template <int M, typename RT, bool kDynChem>
+__device__ __forceinline__ void node_substeps(const RT (&rs)[M], RT rho, RT ER, RT usqR,
+                                              double T, const Units& un, const DevMech& mech,
+                                              int* __restrict__ status, void* chem_slice,
+                                              RT (&dr)[M - 1]) {
+  if constexpr (kFF<RT>) {
+    ff* Cs;
+    if constexpr (kDynChem) Cs = static_cast<ff*>(chem_slice) + threadIdx.x;
+    else Cs = chem_static_slice<M>() + threadIdx.x;
+    const ff Uphys = (ff(ER) + ff(-0.5f * usqR)) * un.c2_f;
+    ff r[M], rdot[M];
+#pragma unroll
+    for (int a = 0; a < M; ++a) r[a] = ff(rs[a]);
+    ff Ts = ff_from_double(T);
+    const ff rho_f(rho);
+    for (int s = 0; s < un.substeps; ++s) {
+      if (s > 0) {
+        ff Ys[M];
+#pragma unroll
+        for (int a = 0; a < M; ++a) Ys[a] = r[a] / rho_f;
+        bool oks;
+        Ts = newton_T_ff<M>(mech, Ys, Uphys, Ts, un.newton_max_iter, un.newton_rtol_f, oks);
+        if (!oks) atomicOr(status, ST_NEWTON);
+      }
+      production_rates_ff<M>(mech, Ts, r, rdot, Cs);
+#pragma unroll
+      for (int a = 0; a < M; ++a) r[a] += un.dt_sub_f * rdot[a];
+    }
+#pragma unroll
+    for (int a = 0; a < M - 1; ++a) dr[a] = (r[a] - ff(rs[a])).hi;
+  } else {
+    const double Uphys = (double(ER) - 0.5 * double(usqR)) * un.c * un.c;
+    const double dtr = un.dt / un.substeps;
+    const double rho_d = double(rho);
+    double r[M], rdot[M];
+#pragma unroll
+    for (int a = 0; a < M; ++a) r[a] = double(rs[a]);
+    double Ts = T;
+    for (int s = 0; s < un.substeps; ++s) {
+      if (s > 0) {
+        double Ys[M];
+        const double ir = 1.0 / rho_d;
+#pragma unroll
+        for (int a = 0; a < M; ++a) Ys[a] = r[a] * ir;
+        bool oks;
+        Ts = newton_T<M>(mech, Ys, Uphys, Ts, un.newton_max_iter, un.newton_rtol, oks);
+        if (!oks) atomicOr(status, ST_NEWTON);
+      }
+      production_rates<M>(mech, Ts, r, rdot);
+#pragma unroll
+      for (int a = 0; a < M; ++a) r[a] += dtr * rdot[a];
+    }
+#pragma unroll
+    for (int a = 0; a < M - 1; ++a) dr[a] = RT(r[a] - double(rs[a]));
+  }
+}
+
+// ---------------------------------------------------------------------------
 // The node's record from its population sums (Sec. 2.1, Sec. 3.1-3.2, Sec.
 // 3.7 slaving): fields, temperature by Newton from the node's previous T,
 // and the reaction sub-steps when chem_inline (else the species densities go
 // to the increment slots for k_chem).  Shared by the moments kernel (one
 // thread per node) and the boundary kernel (interface nodes, one warp each).
-template <int D, int M, typename RT>
+template <int D, int M, typename RT, bool kDynChem = false>
 __device__ __forceinline__ void moments_finish(RT* __restrict__ rec, double* __restrict__ Tf,
                                                int* __restrict__ status, long long N,
                                                const Units& un, const DevMech& mech,
                                                long long n, int chem_inline, RT rho, RT rhoE,
                                                const RT (&j)[D], const RT (&q)[D],
                                                const RT (&P)[Lat<D>::NP], RT (&rs)[M],
-                                               RT (&js)[M][D]) {
+                                               RT (&js)[M][D], void* chem_slice) {
   constexpr int NP = Lat<D>::NP;
   using RC = Rec<D, M>;
   // slaved species M (Eq. strongest)
@@ -181,7 +254,7 @@ __device__ __forceinline__ void moments_finish(RT* __restrict__ rec, double* __r
       Rm += YR[a] * mech.inv_mm_s[a];
     }
     const ff U = (ff(ER) + ff(-0.5f * usqR)) * un.c2_f;
-    const ff Tx = newton_T_ff<M>(mech, Yf, U, ff_from_double(Tf[n]), un.newton_max_iter,
+    const ff Tx = newton_T_ff<M>(mech, Yf, U, ff_from_double(__ldcg(Tf + n)), un.newton_max_iter,
                                  un.newton_rtol_f, ok);
     T = ff_to_double(Tx);
     thR = Rm * float(R_U) * Tx.hi * un.inv_c2_s;
@@ -190,7 +263,7 @@ __device__ __forceinline__ void moments_finish(RT* __restrict__ rec, double* __r
 #pragma unroll
     for (int a = 0; a < M; ++a) Y[a] = double(YR[a]);
     const double U = (double(ER) - 0.5 * double(usqR)) * un.c * un.c;
-    T = newton_T<M>(mech, Y, U, Tf[n], un.newton_max_iter, un.newton_rtol, ok);
+    T = newton_T<M>(mech, Y, U, __ldcg(Tf + n), un.newton_max_iter, un.newton_rtol, ok);
     double Rmix = 0.0;
 #pragma unroll
     for (int a = 0; a < M; ++a) Rmix += Y[a] * mech.inv_mm[a];
@@ -207,52 +280,11 @@ __device__ __forceinline__ void moments_finish(RT* __restrict__ rec, double* __r
   if (!chem_inline) {
 #pragma unroll
     for (int a = 0; a < M - 1; ++a) rec[(RC::DRHO + a) * N + n] = rs[a];
-  } else if constexpr (kFF<RT>) {
-    const ff Uphys = (ff(ER) + ff(-0.5f * usqR)) * un.c2_f;
-    ff r[M], rdot[M];
-#pragma unroll
-    for (int a = 0; a < M; ++a) r[a] = ff(rs[a]);
-    ff Ts = ff_from_double(T);
-    const ff rho_f(rho);
-    for (int s = 0; s < un.substeps; ++s) {
-      if (s > 0) {
-        ff Ys[M];
-#pragma unroll
-        for (int a = 0; a < M; ++a) Ys[a] = r[a] / rho_f;
-        bool oks;
-        Ts = newton_T_ff<M>(mech, Ys, Uphys, Ts, un.newton_max_iter, un.newton_rtol_f, oks);
-        if (!oks) atomicOr(status, ST_NEWTON);
-      }
-      production_rates_ff<M>(mech, Ts, r, rdot);
-#pragma unroll
-      for (int a = 0; a < M; ++a) r[a] += un.dt_sub_f * rdot[a];
-    }
-#pragma unroll
-    for (int a = 0; a < M - 1; ++a) rec[(RC::DRHO + a) * N + n] = (r[a] - ff(rs[a])).hi;
   } else {
-    const double Uphys = (double(ER) - 0.5 * double(usqR)) * un.c * un.c;
-    const double dtr = un.dt / un.substeps;
-    const double rho_d = double(rho);
-    double r[M], rdot[M];
+    RT dr[M - 1];
+    node_substeps<M, RT, kDynChem>(rs, rho, ER, usqR, T, un, mech, status, chem_slice, dr);
 #pragma unroll
-    for (int a = 0; a < M; ++a) r[a] = double(rs[a]);
-    double Ts = T;
-    for (int s = 0; s < un.substeps; ++s) {
-      if (s > 0) {
-        double Ys[M];
-        const double ir = 1.0 / rho_d;
-#pragma unroll
-        for (int a = 0; a < M; ++a) Ys[a] = r[a] * ir;
-        bool oks;
-        Ts = newton_T<M>(mech, Ys, Uphys, Ts, un.newton_max_iter, un.newton_rtol, oks);
-        if (!oks) atomicOr(status, ST_NEWTON);
-      }
-      production_rates<M>(mech, Ts, r, rdot);
-#pragma unroll
-      for (int a = 0; a < M; ++a) r[a] += dtr * rdot[a];
-    }
-#pragma unroll
-    for (int a = 0; a < M - 1; ++a) rec[(RC::DRHO + a) * N + n] = RT(r[a] - double(rs[a]));
+    for (int a = 0; a < M - 1; ++a) rec[(RC::DRHO + a) * N + n] = dr[a];
   }
 
   rec[RC::RHO * N + n] = rho;
@@ -283,12 +315,12 @@ __device__ __forceinline__ void moments_finish(RT* __restrict__ rec, double* __r
 // chem_inline = 0: the reaction sub-steps run in a lane-group kernel
 // (k_chem); this kernel then leaves the post-stream species densities rho_a
 // (a < M) in the record's increment slots for it.
-template <int D, int M, typename S, typename RT>
+template <int D, int M, typename S, typename RT, bool kDynChem = false>
 __device__ __forceinline__ void moments_body(const S* __restrict__ src, RT* __restrict__ rec,
                                              double* __restrict__ Tf, int* __restrict__ status,
                                              const Geom& g, const Units& un, const BCDev& bc,
                                              const DevMech& mech, long long n,
-                                             int chem_inline) {
+                                             int chem_inline, void* chem_slice = nullptr) {
   constexpr int Q = Lat<D>::Q, NP = Lat<D>::NP;
   using RC = Rec<D, M>;
   const long long N = g.N;
@@ -349,8 +381,8 @@ __device__ __forceinline__ void moments_body(const S* __restrict__ src, RT* __re
         if (d != 0 || ix != 1) q[d] += cv[d] * gv;
     }
   }
-  moments_finish<D, M, RT>(rec, Tf, status, N, un, mech, n, chem_inline, rho, rhoE, j, q, P, rs,
-                           js);
+  moments_finish<D, M, RT, kDynChem>(rec, Tf, status, N, un, mech, n, chem_inline, rho, rhoE, j,
+                                     q, P, rs, js, chem_slice);
 }
 
 // ---------------------------------------------------------------------------
@@ -852,7 +884,7 @@ __device__ __forceinline__ void node_params(const RT* __restrict__ rec,
   using PT = RT;
   using MP = MixParams<PT>;
   const PT rho = PT(rec[RC::RHO * N + n]);
-  const double T_d = Tf[n];
+  const double T_d = __ldcg(Tf + n);
   const PT T = PT(T_d);
   const PT E = PT(rec[RC::E * N + n]);
   PT u[D], Y[M];
@@ -1361,8 +1393,11 @@ template <int D, int M, typename RT> struct SmemPar {
   }
 };
 
-// One block: nodes n0 .. n0 + 31.  sm holds coll_smem_entries * kCollNodes.
-template <int D, int M, typename S, typename RT>
+// One block of TPN warps: nodes n0 .. n0 + 31.  sm holds coll_smem_entries *
+// kCollNodes.  The Q directions, taken in the order k = 0 .. Q - 1 with
+// direction (k / NZ) + 9 (k % NZ) (NZ = 3 in 3D: the directions of one
+// (c_x, c_y) pair in a row), are dealt to the warps in contiguous chunks.
+template <int D, int M, typename S, typename RT, int TPN = kCollTPN>
 __device__ __forceinline__ void coll_block(const S* __restrict__ src, S* __restrict__ dst,
                                            const RT* __restrict__ cp, const Geom& g,
                                            const BCDev& bc, const DevMech& mech, long long n0,
@@ -1376,8 +1411,8 @@ __device__ __forceinline__ void coll_block(const S* __restrict__ src, S* __restr
   const long long n = n0 + lane;
   const int tag = n < N ? (bc.tag ? bc.tag[n] : TAG_BULK) : TAG_SOLID;
   const bool valid = tag != TAG_SOLID;
-  for (int f = w; f < CP::NF; f += kCollTPN)
-    sm[f * kCollNodes + lane] = valid ? cp[f * N + n] : RT(0);
+  for (int f = w; f < CP::NF; f += TPN)
+    sm[f * kCollNodes + lane] = valid ? __ldcg(cp + f * N + n) : RT(0);
   __syncthreads();
   if (valid) {
     if (w == 0) {
@@ -1393,7 +1428,7 @@ __device__ __forceinline__ void coll_block(const S* __restrict__ src, S* __restr
           sm[(SP::BF + d * 3 + k) * kCollNodes + lane] = Bf[d][k];
         }
     }
-    for (int e = w; e < NT; e += kCollTPN) {
+    for (int e = w; e < NT; e += TPN) {
       const int c = e % 3 - 1;
       const int d = (e / 3) % D;
       const int b = (e / (3 * D)) % M;
@@ -1411,27 +1446,34 @@ __device__ __forceinline__ void coll_block(const S* __restrict__ src, S* __restr
   const int x = (int)(n % g.nx);
   const int y = (int)((n / g.nx) % g.ny);
   const int z = (int)(n / ((long long)g.nx * g.ny));
-  // warp w takes the directions i = w + 9 k, which share (c_x, c_y); software
-  // pipeline: the next direction's populations are in flight while this one
-  // collides
-  // (FP64: the pair part is formed once and kept in registers; FP32 forms it
-  // per direction, which keeps k_coll within its 56-register budget)
-  static_assert(kCollTPN == 9, "one warp per (c_x, c_y) pair");
+  // software pipeline: the next direction's populations are in flight while
+  // this one collides.  FP64 forms the (c_x, c_y) part once per pair and
+  // keeps it in registers; FP32 forms it per direction, which keeps k_coll
+  // within its 56-register budget.
+  constexpr int NZ = D == 3 ? 3 : 1;
+  constexpr int CH = (Q + TPN - 1) / TPN;
+  const int k0 = w * CH, k1 = min(k0 + CH, Q);
+  if (k0 >= k1) return;
   XYPart<D, M, RT> h;
-  if constexpr (sizeof(RT) == 8) xy_part<D, M, RT>(ps, cvel(w, 0), cvel(w, 1), h);
+  int jcur = -1;
   RT fa[M + 1], fb[M + 1];
-  load_direction<D, M, S, RT>(src, bc, tag, N, node_shift<D>(x, y, z, w, -1, g), w, g.codec,
-                              fa);
+  int i = k0 / NZ + 9 * (k0 % NZ);
+  load_direction<D, M, S, RT>(src, bc, tag, N, node_shift<D>(x, y, z, i, -1, g), i, g.codec, fa);
 #pragma unroll 1
-  for (int i = w; i < Q; i += kCollTPN) {
-    const int inext = i + kCollTPN;
-    if (inext < Q)
+  for (int k = k0; k < k1; ++k) {
+    const int inext = k + 1 < k1 ? (k + 1) / NZ + 9 * ((k + 1) % NZ) : -1;
+    if (inext >= 0)
       load_direction<D, M, S, RT>(src, bc, tag, N, node_shift<D>(x, y, z, inext, -1, g), inext,
                                   g.codec, fb);
-    if constexpr (sizeof(RT) == 4) xy_part<D, M, RT>(ps, cvel(w, 0), cvel(w, 1), h);
+    const int j = k / NZ;
+    if (sizeof(RT) == 4 || j != jcur) {
+      xy_part<D, M, RT>(ps, cvel(j, 0), cvel(j, 1), h);
+      jcur = j;
+    }
     collide_direction<D, M, S, RT>(ps, h, i, fa, dst, N, n, mech, g.codec);
 #pragma unroll
     for (int l = 0; l <= M; ++l) fa[l] = fb[l];
+    i = inext;
   }
 }
 
@@ -2155,6 +2197,139 @@ k_bnode_batch(const DomainDev* __restrict__ doms, int ndom, int parity, int nblk
   }
 }
 
+// ---------------------------------------------------------------------------
+// The whole batched step as one persistent launch over a work-list (PItem,
+// lbm_internal.h).  Dependencies go through sync words: a producer block
+// fences its stores and then releases a count or a flag; a consumer's first
+// thread acquires it (bounded by timeout_ns on the global timer, after which
+// it sets the abort word and ST_TIMEOUT in the item's domain) before the
+// block reads.  Data written earlier in the same launch is read only after
+// such an acquire, and the reads that could meet a line fetched before its
+// last write (the temperature guesses and the collision parameters) bypass
+// the L1 (ld.global.cg).
+// Reaction sub-steps of interface node n (Sec. 2.4 Eq. R3) by one thread,
+// from the record the boundary reconstruction left (post-stream species
+// densities in the increment slots), as chem_lanes_body does with lanes.
+template <int D, int M, typename RT>
+__device__ __forceinline__ void iface_substeps(RT* __restrict__ rec, const double* __restrict__ Tf,
+                                               int* __restrict__ status, long long N,
+                                               const Units& un, const DevMech& mech, long long n,
+                                               void* chem_slice) {
+  using RC = Rec<D, M>;
+  const RT rho = __ldcg(rec + RC::RHO * N + n);
+  RT usq = RT(0);
+#pragma unroll
+  for (int d = 0; d < D; ++d) {
+    const RT ud = __ldcg(rec + (RC::U + d) * N + n);
+    usq += ud * ud;
+  }
+  const RT ER = __ldcg(rec + RC::E * N + n);
+  RT rs[M];
+  RT last = rho;
+#pragma unroll
+  for (int a = 0; a < M - 1; ++a) {
+    rs[a] = __ldcg(rec + (RC::DRHO + a) * N + n);
+    last -= rs[a];
+  }
+  rs[M - 1] = last;
+  RT dr[M - 1];
+  node_substeps<M, RT, true>(rs, rho, ER, usq, __ldcg(Tf + n), un, mech, status, chem_slice, dr);
+#pragma unroll
+  for (int a = 0; a < M - 1; ++a) rec[(RC::DRHO + a) * N + n] = dr[a];
+}
+
+template <typename RT> constexpr int kPersistMinBlocks = sizeof(RT) == 8 ? 2 : 3;
+constexpr int kPersistCollWarps = kPersistThreads / 32;
+
+template <int D, int M, typename S, typename RT>
+__global__ void __launch_bounds__(kPersistThreads, kPersistMinBlocks<RT>)
+k_step_persist(const DomainDev* __restrict__ doms, int ndom, int parity,
+               const PItem* __restrict__ items, int nitems, int npt, int* __restrict__ sync,
+               long long timeout_ns) {
+  using R = typename ComputeType<S>::type;
+  constexpr int Q = Lat<D>::Q;
+  extern __shared__ __align__(16) unsigned char ps_raw[];
+  __shared__ int s_item, s_go;
+  int* const next = sync;
+  int* const abort_w = sync + 1;
+  int* const done1 = sync + kSyncHead;
+  int* const pflag = done1 + ndom;
+  for (;;) {
+    if (threadIdx.x == 0) {
+      const int it = atomicAdd(next, 1);
+      int go = it < nitems && !ld_acquire_gpu(abort_w);
+      if (go) {
+        const PItem w = items[it];
+        if (w.kind == PI_PREP) go = wait_at_least(done1 + w.dom, w.dep, abort_w, timeout_ns);
+        else if (w.kind == PI_COLL) go = wait_at_least(pflag + w.dep, 1, abort_w, timeout_ns);
+        if (!go) atomicOr(doms[w.dom].status, ST_TIMEOUT);
+      }
+      s_item = it;
+      s_go = go;
+    }
+    __syncthreads();
+    if (!s_go) break;
+    const PItem w = items[s_item];
+    const DomainDev& d = doms[w.dom];
+    const int c = d.cur0 ^ parity;
+    const S* src = static_cast<const S*>(d.pops[c]);
+    RT* rec = static_cast<RT*>(d.rec);
+    if (w.kind == PI_BND) {
+      // two groups of kBnd threads, each with its boundary columns
+      const int grp = threadIdx.x / kBnd, t = threadIdx.x % kBnd;
+      constexpr int E = bnode_col_entries<D, M>();
+      R* col = reinterpret_cast<R*>(ps_raw) + grp * E * kBnd + t;
+      long long* sncol =
+          reinterpret_cast<long long*>(ps_raw + sizeof(R) * E * kBnd * (kPersistThreads / kBnd)) +
+          grp * Q * kBnd + t;
+      const long long k = w.first + threadIdx.x;
+      if (k < d.bc.n_if)
+        bnode_body<D, M, S, R>(src, d.bc, static_cast<R*>(d.rec), d.Tf, d.status, d.g, d.un,
+                               *d.mech, (int)k, col, sncol);
+      __syncthreads();   // the columns become the sub-steps' shared-memory slices
+      if (k < d.bc.n_if)
+        iface_substeps<D, M, RT>(rec, d.Tf, d.status, d.g.N, d.un, *d.mech, d.bc.if_node[k],
+                                 ps_raw);
+    } else if (w.kind == PI_MOM) {
+      for (int j = 0; j < npt; ++j) {
+        const long long n = w.first + (long long)j * kPersistThreads + threadIdx.x;
+        if (n >= d.g.N) break;
+        if (d.bc.tag && d.bc.tag[n] >= 0) continue;   // interface node: PI_BND
+        moments_body<D, M, S, RT, true>(src, rec, d.Tf, d.status, d.g, d.un, d.bc, *d.mech, n, 1,
+                                        ps_raw);
+      }
+    } else if (w.kind == PI_PREP) {
+      for (int j = 0; j < npt; ++j)
+        prep_body<D, M, RT>(rec, d.Tf, static_cast<RT*>(d.cpar), d.g, d.un, d.bc, *d.mech,
+                            w.first + (long long)j * kPersistThreads + threadIdx.x);
+    } else {
+      coll_block<D, M, S, RT, kPersistCollWarps>(
+          src, static_cast<S*>(const_cast<void*>(d.pops[1 - c])),
+          static_cast<const RT*>(d.cpar), d.g, d.bc, *d.mech, w.first,
+          reinterpret_cast<RT*>(ps_raw));
+    }
+    // publish the item: every thread's stores, then the block's release
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      if (w.kind == PI_BND || w.kind == PI_MOM) add_release_gpu(done1 + w.dom, 1);
+      else if (w.kind == PI_PREP) st_release_gpu(pflag + w.flag, 1);
+    }
+  }
+}
+
+// dynamic shared memory of k_step_persist: the largest of its items' needs
+template <int D, int M, typename S, typename RT> constexpr size_t persist_smem() {
+  using R = typename ComputeType<S>::type;
+  const size_t bnd = bnode_smem<D, M, R>() * (kPersistThreads / kBnd);
+  const size_t prep = (size_t)M * M * kBS * sizeof(RT);
+  const size_t coll = (size_t)coll_smem_entries<D, M>() * kCollNodes * sizeof(RT);
+  const size_t chem = kFF<RT> ? chem_slice_bytes<M, ff>() : 0;
+  size_t m = bnd > prep ? bnd : prep;
+  m = m > coll ? m : coll;
+  return m > chem ? m : chem;
+}
+
 template <int D, int M, typename S>
 __global__ void __launch_bounds__(128)
 k_boundary_batch(const DomainDev* __restrict__ doms, int ndom, int parity, int with_rec,
@@ -2379,6 +2554,7 @@ static cudaError_t prepare_impl() {
   big((const void*)k_coll_batch<D, M, S, RT>, coll_smem<D, M, RT>());
   big((const void*)k_bnode<D, M, S>, bnode_smem<D, M, RT>());
   big((const void*)k_bnode_batch<D, M, S>, bnode_smem<D, M, RT>());
+  big((const void*)k_step_persist<D, M, S, RT>, persist_smem<D, M, S, RT>());
   return e;
 }
 
@@ -2557,6 +2733,18 @@ static cudaError_t batch_impl(const DomainDev* doms, int ndom, const BatchGrids&
   const int bs = kBS;
   const cudaError_t pe = prepare_once<D, M, S, RT>();
   if (pe != cudaSuccess) return pe;
+  if (lc.persistent == 2) {
+    // the whole step as one launch over the work-list (sync words zeroed
+    // first)
+    if (gr.nitems == 0) return cudaSuccess;
+    auto kp = k_step_persist<D, M, S, RT>;
+    const size_t sm = persist_smem<D, M, S, RT>();
+    cudaError_t e = cudaMemsetAsync(gr.sync, 0, (size_t)gr.nsync * sizeof(int), s);
+    if (e != cudaSuccess) return e;
+    kp<<<batch_grid(kp, gr.nitems, kPersistThreads, sm, true), kPersistThreads, sm, s>>>(
+        doms, ndom, parity, gr.items, gr.nitems, lc.npt, gr.sync, gr.timeout_ns);
+    return cudaGetLastError();
+  }
   const int chem_inline = lc.chem_lanes <= 1;
   const bool ps = lc.persistent != 0;
   auto kmom = k_moments_batch<D, M, S, RT>;

@@ -12,6 +12,7 @@
 #include <string>
 
 #include "lbm_internal.h"
+#include "lbm_sync.cuh"
 
 namespace {
 
@@ -63,7 +64,38 @@ cudaError_t time_fma(int iters, double* tflops) {
   return cudaSuccess;
 }
 
+// One thread waits on words[0] (abort word words[1]) with the persistent
+// step's bounded wait; out[0] = 1 if the wait saw the word set, out[1] = the
+// abort word afterwards, out[2] = the wait's length in microseconds.
+__global__ void k_wait_probe(int* words, long long timeout_ns, long long* out) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const unsigned long long t0 = lbm::global_ns();
+  const bool ok = lbm::wait_at_least(words, 1, words + 1, timeout_ns);
+  out[0] = ok ? 1 : 0;
+  out[1] = lbm::ld_acquire_gpu(words + 1);
+  out[2] = (long long)((lbm::global_ns() - t0) / 1000ull);
+}
+
 }  // namespace
+
+extern "C" lbm_status lbm_wait_probe(int set_word, long long timeout_ns, long long* result) {
+  if (!result || timeout_ns < 0) return LBM_ERR_INVALID;
+  if (timeout_ns > 100000000LL) return LBM_ERR_RANGE;
+  int* words = nullptr;
+  long long* out = nullptr;
+  cudaError_t e = cudaMalloc(&words, 2 * sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc(&out, 3 * sizeof(long long));
+  const int init[2] = {set_word ? 1 : 0, 0};
+  if (e == cudaSuccess) e = cudaMemcpy(words, init, sizeof(init), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) {
+    k_wait_probe<<<1, 32>>>(words, timeout_ns, out);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpy(result, out, 3 * sizeof(long long), cudaMemcpyDeviceToHost);
+  if (words) cudaFree(words);
+  if (out) cudaFree(out);
+  return e == cudaSuccess ? LBM_OK : LBM_ERR_CUDA;
+}
 
 extern "C" lbm_status lbm_fma_peak(int fp64, double* tflops) {
   if (!tflops) return LBM_ERR_INVALID;

@@ -80,7 +80,8 @@ class lbm_config(C.Structure):
 
 
 class lbm_launch(C.Structure):
-    _fields_ = [("chem_lanes", C.c_int), ("collide_split", C.c_int), ("persistent", C.c_int)]
+    _fields_ = [("chem_lanes", C.c_int), ("collide_split", C.c_int), ("persistent", C.c_int),
+                ("nodes_per_thread", C.c_int)]
 
 
 class lbm_diag(C.Structure):
@@ -125,6 +126,7 @@ EXPORTS = {
     "lbm_destroy": (C.c_int, [C.c_void_p]),
     "lbm_last_error": (C.c_char_p, [C.c_void_p]),
     "lbm_fma_peak": (C.c_int, [C.c_int, C.POINTER(C.c_double)]),
+    "lbm_wait_probe": (C.c_int, [C.c_int, C.c_longlong, C.POINTER(C.c_longlong)]),
     "lbm_get_planes": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_int]),
     "lbm_set_planes": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_int]),
     "lbm_step_noalloc": (C.c_int, [C.POINTER(lbm_config), C.c_void_p, C.c_void_p,
@@ -297,7 +299,7 @@ def lbm_batch_destroy(plan):
 
 def _launch_dict(l):
     return {"chem_lanes": l.chem_lanes, "collide_split": l.collide_split,
-            "persistent": l.persistent}
+            "persistent": l.persistent, "nodes_per_thread": l.nodes_per_thread}
 
 
 def lbm_batch_autotune(plan, trial_steps=3):
@@ -319,9 +321,10 @@ def lbm_ff_check(x):
     return e, lg
 
 
-def lbm_batch_set_launch(plan, chem_lanes=-1, collide_split=-1, persistent=-1):
+def lbm_batch_set_launch(plan, chem_lanes=-1, collide_split=-1, persistent=-1,
+                         nodes_per_thread=-1):
     l = lbm_launch(chem_lanes=int(chem_lanes), collide_split=int(collide_split),
-                   persistent=int(persistent))
+                   persistent=int(persistent), nodes_per_thread=int(nodes_per_thread))
     _check(load_library().lbm_batch_set_launch(plan, C.byref(l)), plan.handles[0])
 
 
@@ -331,9 +334,9 @@ def lbm_batch_get_launch(plan):
     return _launch_dict(out)
 
 
-def lbm_set_launch(h, chem_lanes=-1, collide_split=-1, persistent=-1):
+def lbm_set_launch(h, chem_lanes=-1, collide_split=-1, persistent=-1, nodes_per_thread=-1):
     l = lbm_launch(chem_lanes=int(chem_lanes), collide_split=int(collide_split),
-                   persistent=int(persistent))
+                   persistent=int(persistent), nodes_per_thread=int(nodes_per_thread))
     _check(load_library().lbm_set_launch(h, C.byref(l)), h)
 
 
@@ -459,6 +462,15 @@ def lbm_fma_peak(fp64):
     out = C.c_double(0.0)
     _check(load_library().lbm_fma_peak(1 if fp64 else 0, C.byref(out)))
     return out.value
+
+
+def lbm_wait_probe(set_word, timeout_ns):
+    """The bounded device wait of the single-launch batched step on a word
+    that is set (set_word) or that nothing sets: returns (saw_word, abort,
+    microseconds)."""
+    out = (C.c_longlong * 3)()
+    _check(load_library().lbm_wait_probe(1 if set_word else 0, int(timeout_ns), out))
+    return int(out[0]), int(out[1]), int(out[2])
 
 
 def lbm_last_error(h=None):
@@ -597,8 +609,8 @@ class Solver:
     def step(self, n=1):
         lbm_step(self.h, n)
 
-    def set_launch(self, chem_lanes=-1, collide_split=-1, persistent=-1):
-        lbm_set_launch(self.h, chem_lanes, collide_split, persistent)
+    def set_launch(self, chem_lanes=-1, collide_split=-1, persistent=-1, nodes_per_thread=-1):
+        lbm_set_launch(self.h, chem_lanes, collide_split, persistent, nodes_per_thread)
 
     def launch(self):
         return lbm_get_launch(self.h)

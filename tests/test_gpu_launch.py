@@ -32,7 +32,8 @@ PLACEMENTS = [(1, 0), (4, 0), (8, 0), (1, 1), (4, 1), (8, 1)]
 
 
 def _pl(cl, cs, persistent=0):
-    return {"chem_lanes": cl, "collide_split": cs, "persistent": persistent}
+    return {"chem_lanes": cl, "collide_split": cs, "persistent": persistent,
+            "nodes_per_thread": 1}
 
 
 @pytest.fixture(scope="module")
