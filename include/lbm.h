@@ -270,8 +270,10 @@ lbm_status lbm_batch_destroy(lbm_batch_t b);
  *                  per-node kernel stores the collision parameters and a
  *                  second kernel updates the directions with nine threads
  *                  per node; -1 = default.
- * Defaults: collide_split 1; chem_lanes 4 for FP32 storage below 77,824
- * nodes (four 128-thread blocks per SM of a 152-SM GPU), else 1.
+ * Defaults (below 77,824 nodes, four 128-thread blocks per SM of a 152-SM
+ * GPU, a grid is small): collide_split 0 for FP64 storage on grids that are
+ * not small (except the single launch of a plan, see persistent), else 1;
+ * chem_lanes 4 for small FP32-storage grids, else 1.
  * lbm_set_launch rejects other values with LBM_ERR_INVALID. */
 typedef struct {
   int chem_lanes;
@@ -284,9 +286,11 @@ typedef struct {
                          (boundary + sub-steps of 128 interface nodes,
                          moments + sub-steps of a node tile; collision
                          parameters of a node tile once its domain's first
-                         stage is done; the collision of 32 nodes once their
-                         parameters are), with chem_lanes 1 and split
-                         collision; a dependency wait that outlasts 4 s
+                         stage is done and the collision of 32 nodes once
+                         their parameters are, or with collide_split 0 the
+                         whole collision of a node tile once its domain's
+                         first stage is done), with chem_lanes 1; a
+                         dependency wait that outlasts 4 s
                          ends the launch and the handles report
                          LBM_ERR_TIMEOUT; 0 = one block per tile; -1 = the
                          default: 2 for plans of FP64 storage, else 0 */
@@ -310,8 +314,9 @@ lbm_status lbm_autotune(lbm_t h, int trial_steps, lbm_launch* chosen);
 
 /* The same for a batch plan: times trial_steps replays of each placement's
  * captured one-step graph over the whole batch (the six placements above,
- * the best of them with persistent grids, and the single launch with 1, 2
- * and 4 nodes per thread), keeps the fastest and captures the plan's graphs
+ * the best of them with persistent grids, and the single launch with split
+ * and fused collision, each with 1, 2 and 4 nodes per thread), keeps the
+ * fastest and captures the plan's graphs
  * again with it.  A new plan starts with the default placement (see
  * lbm_batch_set_launch). */
 lbm_status lbm_batch_autotune(lbm_batch_t b, int trial_steps, lbm_launch* chosen);

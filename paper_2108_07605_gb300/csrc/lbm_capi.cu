@@ -62,18 +62,25 @@ lbm_status cuda_fail(lbm_ctx* h, cudaError_t e, const char* where) {
 // the extra redundant work of the lanes costs more than it hides.
 constexpr long long kSmallGrid = 152LL * 4 * 128;
 
-// plan: a batch plan's placement, whose default for FP64 storage is the
-// single launch over the work-list (measured faster there; FP32 and FP16
-// keep one launch per kernel, whose kernels hold fewer registers)
+// Defaults, measured on one GB300.  plan: a batch plan's placement, whose
+// default for FP64 storage is the single launch over the work-list with
+// split collision (13 % faster than one launch per kernel on a mix of eight
+// small domains, within 1-2 % of the best on large ones); FP32 and FP16
+// plans keep one launch per kernel, whose kernels hold fewer registers than
+// the single launch.  One handle, FP64, a grid that fills the GPU at one
+// thread per node: the fused collision (3 % faster on the 600x40x40 tube);
+// else the split one.
 Launch resolve_launch(const lbm_launch& opt, long long nodes, lbm_precision prec,
                       bool plan = false) {
   Launch lc;
   const bool small = nodes < kSmallGrid;
   lc.chem_lanes = opt.chem_lanes > 0 ? opt.chem_lanes
                                      : (small && prec == LBM_FP32_STORE ? 4 : 1);
-  lc.coll_split = opt.collide_split >= 0 ? opt.collide_split : 1;
   lc.persistent = opt.persistent >= 0 ? opt.persistent
                                      : (plan && prec == LBM_FP64 ? 2 : 0);
+  lc.coll_split = opt.collide_split >= 0
+                      ? opt.collide_split
+                      : (prec == LBM_FP64 && !small && lc.persistent != 2 ? 0 : 1);
   lc.npt = opt.nodes_per_thread > 0 ? opt.nodes_per_thread : 1;
   return lc;
 }
@@ -82,9 +89,9 @@ Launch resolve_launch(const lbm_launch& opt, long long nodes, lbm_precision prec
 const Launch kCandidates[] = {{1, 0}, {4, 0}, {8, 0}, {1, 1}, {4, 1}, {8, 1}};
 
 // Domains of a batched step: each handle's tiles follow the previous
-// handle's in every grid (128 nodes per node-kernel block, 4 interface nodes
-// per boundary block, 128 / chem_lanes nodes per chemistry block, 32 nodes
-// per split-collision block).
+// handle's in every grid (128 nodes per node-kernel block, 16 interface nodes
+// per interface-chemistry block, 128 / chem_lanes nodes per chemistry block,
+// 32 nodes per split-collision block).
 void fill_domains(lbm_ctx* const* hs, int n, const Launch& lc, std::vector<DomainDev>& doms,
                   BatchGrids& gr) {
   doms.assign(n, DomainDev());
@@ -109,7 +116,7 @@ void fill_domains(lbm_ctx* const* hs, int n, const Launch& lc, std::vector<Domai
     d.cblock_begin = gr.ncblocks;
     d.kblock_begin = gr.nkblocks;
     gr.nblocks += (int)((h->g.N + 127) / 128);
-    gr.nbblocks += (h->bc.n_if + 3) / 4;
+    gr.nbblocks += (h->bc.n_if + kIfChemNodesPerBlock - 1) / kIfChemNodesPerBlock;
     gr.ntblocks += (h->bc.n_if + kBndNodesPerBlock - 1) / kBndNodesPerBlock;
     if (lc.chem_lanes > 1) {
       const int per = 128 / lc.chem_lanes;
@@ -1111,7 +1118,8 @@ namespace {
 // items of every domain, then the moments items), stage 2 (parameter items),
 // stage 3 (collision items), each stage domain by domain.  nsync: the sync
 // words the launch needs.
-void build_worklist(lbm_ctx* const* hs, int n, int npt, std::vector<PItem>& items, int& nsync) {
+void build_worklist(lbm_ctx* const* hs, int n, int npt, bool split, std::vector<PItem>& items,
+                    int& nsync) {
   items.clear();
   const long long tile = (long long)kPersistThreads * npt;
   std::vector<int> n1(n, 0), pbase(n, 0);
@@ -1122,6 +1130,13 @@ void build_worklist(lbm_ctx* const* hs, int n, int npt, std::vector<PItem>& item
     for (long long f = 0; f < hs[k]->g.N; f += tile, ++n1[k])
       items.push_back(PItem{PI_MOM, k, f, 0, 0});
   int nflag = 0;
+  if (!split) {
+    for (int k = 0; k < n; ++k)
+      for (long long f = 0; f < hs[k]->g.N; f += tile)
+        items.push_back(PItem{PI_COLLIDE, k, f, n1[k], 0});
+    nsync = kSyncHead + n;
+    return;
+  }
   for (int k = 0; k < n; ++k) {
     pbase[k] = nflag;
     for (long long f = 0; f < hs[k]->g.N; f += tile)
@@ -1144,7 +1159,7 @@ cudaError_t batch_upload(lbm_batch_ctx* b) {
   if (e == cudaSuccess && b->lc.persistent == 2) {
     std::vector<PItem> items;
     int nsync = 0;
-    build_worklist(b->hs.data(), n, b->lc.npt, items, nsync);
+    build_worklist(b->hs.data(), n, b->lc.npt, b->lc.coll_split != 0, items, nsync);
     const lbm_config& cfg = b->hs[0]->cfg;
     if ((int)items.size() > b->items_cap) {
       e = cudaStreamSynchronize(b->stream);
@@ -1345,11 +1360,11 @@ lbm_status lbm_batch_autotune(lbm_batch_t b, int trial_steps, lbm_launch* chosen
   bool first = true;
   // stage 1: the six placements with one block per tile; stage 2: the best
   // of them with persistent grids; stage 3: the whole step as one launch over
-  // the work-list with 1, 2 and 4 nodes per thread (tiles of 128, 256, 512
-  // nodes)
+  // the work-list, split and fused collision, each with 1, 2 and 4 nodes per
+  // thread (tiles of 128, 256, 512 nodes)
   const size_t nc = sizeof(kCandidates) / sizeof(kCandidates[0]);
   const int npts[3] = {1, 2, 4};
-  for (size_t ci = 0; ci <= nc + 3; ++ci) {
+  for (size_t ci = 0; ci <= nc + 6; ++ci) {
     if (e != cudaSuccess) break;
     Launch cand;
     if (ci < nc) {
@@ -1360,9 +1375,9 @@ lbm_status lbm_batch_autotune(lbm_batch_t b, int trial_steps, lbm_launch* chosen
     } else {
       cand = Launch();
       cand.chem_lanes = 1;
-      cand.coll_split = 1;
+      cand.coll_split = (ci - nc - 1) < 3 ? 1 : 0;
       cand.persistent = 2;
-      cand.npt = npts[ci - nc - 1];
+      cand.npt = npts[(ci - nc - 1) % 3];
     }
     b->lc = cand;
     e = batch_upload(b);

@@ -165,7 +165,7 @@ struct DomainDev {
   const DevMech* mech = nullptr;   // device copy of the handle's mechanism
   void* cpar = nullptr;        // per-node collision parameters (split collision)
   int block_begin = 0;         // first block of this domain in the node grids
-  int bblock_begin = 0;        // first block in the boundary grid
+  int bblock_begin = 0;        // first block in the interface-chemistry grid
   int tblock_begin = 0;        // first block in the thread-per-interface-node grid (k_bnode)
   int cblock_begin = 0;        // first block in the chemistry grid (k_chem)
   int kblock_begin = 0;        // first block in the split-collision grid (k_coll)
@@ -182,18 +182,21 @@ struct SideStream {
 // work-list of items in stage order, claimed by the blocks of a persistent
 // grid through an atomic counter.  Stage 1: PI_BND (kPersistBndNodes
 // interface nodes: boundary reconstruction, record, reaction sub-steps) and
-// PI_MOM (kPersistThreads * npt nodes: moments, sub-steps); stage 2: PI_PREP
-// (collision parameters of kPersistThreads * npt nodes), after every stage-1
-// item of its domain; stage 3: PI_COLL (kCollNodesPerBlock nodes), after the
-// PI_PREP item holding its nodes.  An item waits only on items earlier in
-// the list, which blocks already running hold, so every wait ends without
-// any assumption on how many blocks are resident.
-enum PItemKind : int { PI_BND = 0, PI_MOM = 1, PI_PREP = 2, PI_COLL = 3 };
+// PI_MOM (kPersistThreads * npt nodes: moments, sub-steps).  Split
+// collision: stage 2, PI_PREP (collision parameters of kPersistThreads * npt
+// nodes), after every stage-1 item of its domain; stage 3, PI_COLL
+// (kCollNodesPerBlock nodes), after the PI_PREP item holding its nodes.
+// Fused collision: stage 2, PI_COLLIDE (the whole collision of
+// kPersistThreads * npt nodes, one thread per node), after every stage-1
+// item of its domain.  An item waits only on items earlier in the list,
+// which blocks already running hold, so every wait ends without any
+// assumption on how many blocks are resident.
+enum PItemKind : int { PI_BND = 0, PI_MOM = 1, PI_PREP = 2, PI_COLL = 3, PI_COLLIDE = 4 };
 struct PItem {
   int kind;     // PItemKind
   int dom;      // domain index
   long long first;   // first interface index (PI_BND) or first node
-  int dep;      // PI_PREP: the domain's stage-1 item count; PI_COLL: the flag to wait for
+  int dep;      // PI_PREP, PI_COLLIDE: the domain's stage-1 item count; PI_COLL: the flag
   int flag;     // PI_PREP: the flag it sets
 };
 constexpr int kPersistThreads = 128;
@@ -207,7 +210,7 @@ constexpr long long kPersistTimeoutNs = 4000000000LL;
 // Block totals of the batched grids.
 struct BatchGrids {
   int nblocks = 0;    // node kernels, 128 nodes per block
-  int nbblocks = 0;   // boundary grid, 4 interface nodes per block (k_chem, k_moments)
+  int nbblocks = 0;   // interface-chemistry grid, kIfChemNodesPerBlock nodes per block
   int ntblocks = 0;   // k_bnode, kBndNodesPerBlock interface nodes per block
   int ncblocks = 0;   // k_chem, 128 / chem_lanes nodes per block (0 without it)
   int nkblocks = 0;   // k_coll, 32 nodes per block (0 without it)
@@ -223,6 +226,8 @@ struct BatchGrids {
 
 // interface nodes per block of the boundary kernel (one thread each)
 constexpr int kBndNodesPerBlock = 64;
+// interface nodes per block of the batched interface chemistry (8 lanes each)
+constexpr int kIfChemNodesPerBlock = 16;
 
 // Batched step: doms is a device array of ndom domains sharing (D, M, prec)
 // and laid out for the placement lc.

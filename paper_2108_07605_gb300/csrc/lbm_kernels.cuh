@@ -124,10 +124,11 @@ constexpr int kBS = 128;
 static_assert(kBS == kChemThreads, "the chemistry's shared-memory slices assume kBS threads");
 
 // shared memory of the collision kernel per thread: the diffusion-velocity
-// matrix, then the axis-factor tables
-// (tables only in the FP32 path: in FP64 they would halve the occupancy)
+// matrix, then the axis-factor tables (FP32: every axis; FP64 in 3D: the z
+// axis only, the whole table would halve the occupancy)
 template <int D, int M, typename RT> constexpr int collide_smem_entries() {
-  return (sizeof(RT) == 4 && 2 * M * D * 3 > M * M) ? 2 * M * D * 3 : M * M;
+  constexpr int tab = sizeof(RT) == 4 ? 2 * M * D * 3 : (D == 3 ? 2 * M * 3 : 0);
+  return tab > M * M ? tab : M * M;
 }
 
 template <int D>
@@ -1239,15 +1240,18 @@ __device__ __forceinline__ void collide_direction(const PS& ps, const XYPart<D, 
   }
 }
 
-// Parameters held in registers (fused placement).  The species factor
-// products come from a table in this thread's shared-memory column (FP32:
-// entry stride kBS) or are formed directly (FP64, where the table would
-// halve the occupancy).
+// Parameters held in registers (fused placement).  The species axis factors
+// come from a table in this thread's shared-memory column (FP32, entry stride
+// kBS) or are formed directly, except, in FP64 3D, those of the z axis,
+// tabulated in the column (ztab: entry ((set M + b) 3 + c + 1) kBS), which
+// every direction reads while the x and y factors serve a (c_x, c_y) pair.
 template <int D, int M, typename RT> struct RegPar {
   const NodePar<D, M, RT>& p;
   RT Afv[D][3], Bfv[D][3];
   const RT* tab;
-  __device__ RegPar(const NodePar<D, M, RT>& p_, const RT* tab_) : p(p_), tab(tab_) {
+  const RT* ztab;
+  __device__ RegPar(const NodePar<D, M, RT>& p_, const RT* tab_, const RT* ztab_ = nullptr)
+      : p(p_), tab(tab_), ztab(ztab_) {
     energy_factors<D, RT>(p.u, p.theta, Afv, Bfv);
   }
   __device__ RT rho() const { return p.rho; }
@@ -1265,6 +1269,7 @@ template <int D, int M, typename RT> struct RegPar {
   // species axis factor (set 0: psi(u, theta_b); set 1: psi(u + V_b, theta_b))
   __device__ RT sp(int set, int b, int d, int c) const {
     if (tab) return tab[(((set * M + b) * D + d) * 3 + c + 1) * kBS];
+    if (D == 3 && d == 2 && ztab) return ztab[((set * M + b) * 3 + c + 1) * kBS];
     const RT xs = set ? p.u[d] + p.V[b][d] : p.u[d];
     return psi1<RT>(c, xs, p.th[b] + xs * xs);
   }
@@ -1293,14 +1298,28 @@ __device__ __forceinline__ void collide_body(const S* __restrict__ src, S* __res
   // shared-memory column (the solve's space, now free)
   extern __shared__ unsigned char smem_raw[];
   RT* tab = nullptr;
+  RT* ztab = nullptr;
   if constexpr (sizeof(RT) == 4) {
     tab = reinterpret_cast<RT*>(smem_raw) + threadIdx.x;
     constexpr int NT = 2 * M * D * 3;
 #pragma unroll
     for (int e = 0; e < NT; ++e)
       tab[e * kBS] = axis_factor<D, M, RT>(e, p.th, p.u, &p.V[0][0]);
+  } else if constexpr (D == 3) {
+    // FP64: the z-axis factors, psi_c(x_s, theta_b + x_s^2) with x_s = u_z
+    // (set 0) or u_z + V_bz (set 1)
+    ztab = reinterpret_cast<RT*>(smem_raw) + threadIdx.x;
+#pragma unroll
+    for (int set = 0; set < 2; ++set)
+#pragma unroll
+      for (int b = 0; b < M; ++b) {
+        const RT xs = set ? p.u[2] + p.V[b][2] : p.u[2];
+        const RT Ps = p.th[b] + xs * xs;
+#pragma unroll
+        for (int c = -1; c <= 1; ++c) ztab[((set * M + b) * 3 + c + 1) * kBS] = psi1<RT>(c, xs, Ps);
+      }
   }
-  const RegPar<D, M, RT> ps(p, tab);
+  const RegPar<D, M, RT> ps(p, tab, ztab);
   // directions i = j + 9 k share (c_x, c_y) = direction j's
 #pragma unroll 1
   for (int j = 0; j < 9; ++j) {
@@ -2073,40 +2092,29 @@ template <int D, int M, typename S, typename RT>
 __global__ void __launch_bounds__(128, kMomentsMinBlocks<RT>)
 k_moments_batch(const DomainDev* __restrict__ doms, int ndom, int parity, int chem_inline,
                 int node_set, int nblk) {
+  // node_set: NODES_ALL or NODES_BULK (the interface nodes' records come from
+  // k_bnode_batch)
   for (int b = blockIdx.x; b < nblk; b += gridDim.x) {
-    // NODES_INTERFACE: the boundary grid (four interface nodes per block), one
-    // thread per interface node
-    const DomainDev& d = doms[domain_of_block(
-        doms, ndom, b, node_set == NODES_INTERFACE ? GRID_BOUNDARY : GRID_NODE)];
+    const DomainDev& d = doms[domain_of_block(doms, ndom, b, GRID_NODE)];
     const int c = d.cur0 ^ parity;
-    long long n;
-    if (node_set == NODES_INTERFACE) {
-      if (threadIdx.x & 31) continue;
-      const long long k = (b - d.bblock_begin) * 4LL + (threadIdx.x >> 5);
-      if (k >= d.bc.n_if) continue;
-      n = d.bc.if_node[k];
-    } else {
-      n = (b - d.block_begin) * (long long)blockDim.x + threadIdx.x;
-      if (node_set == NODES_BULK && d.bc.tag && n < d.g.N && d.bc.tag[n] >= 0) continue;
-    }
+    const long long n = (b - d.block_begin) * (long long)blockDim.x + threadIdx.x;
+    if (node_set == NODES_BULK && d.bc.tag && n < d.g.N && d.bc.tag[n] >= 0) continue;
     moments_body<D, M, S, RT>(static_cast<const S*>(d.pops[c]), static_cast<RT*>(d.rec), d.Tf,
                               d.status, d.g, d.un, d.bc, *d.mech, n, chem_inline);
   }
 }
 
-// NODES_INTERFACE: the boundary grid (four interface nodes per block), the
-// first L lanes of warp w on the block's interface node w
+// NODES_INTERFACE: the interface-chemistry grid (128 / L interface nodes
+// per block, L lanes each, as k_chem)
 template <int D, int M, typename RT, int L>
 __global__ void __launch_bounds__(128)
 k_chem_batch(const DomainDev* __restrict__ doms, int ndom, int node_set, int nblk) {
   for (int b = blockIdx.x; b < nblk; b += gridDim.x) {
     if (node_set == NODES_INTERFACE) {
       const DomainDev& d = doms[domain_of_block(doms, ndom, b, GRID_BOUNDARY)];
-      const int lane = threadIdx.x & 31;
-      const int k = (b - d.bblock_begin) * 4 + threadIdx.x / 32;
-      if (lane >= L || k >= d.bc.n_if) continue;
-      chem_lanes_body<D, M, RT, L>(static_cast<RT*>(d.rec), d.Tf, d.status, d.g.N, d.bc.tag,
-                                   d.un, *d.mech, d.bc.if_node[k], lane, (1u << L) - 1u);
+      chem_entry<D, M, RT, L>(static_cast<RT*>(d.rec), d.Tf, d.status, d.g.N, d.bc.tag, d.un,
+                              *d.mech, (b - d.bblock_begin) * (128LL / L), NODES_INTERFACE,
+                              d.bc.if_node, d.bc.n_if);
     } else {
       const DomainDev& d = doms[domain_of_block(doms, ndom, b, GRID_CHEM)];
       chem_entry<D, M, RT, L>(static_cast<RT*>(d.rec), d.Tf, d.status, d.g.N, d.bc.tag, d.un,
@@ -2260,7 +2268,8 @@ k_step_persist(const DomainDev* __restrict__ doms, int ndom, int parity,
       int go = it < nitems && !ld_acquire_gpu(abort_w);
       if (go) {
         const PItem w = items[it];
-        if (w.kind == PI_PREP) go = wait_at_least(done1 + w.dom, w.dep, abort_w, timeout_ns);
+        if (w.kind == PI_PREP || w.kind == PI_COLLIDE)
+          go = wait_at_least(done1 + w.dom, w.dep, abort_w, timeout_ns);
         else if (w.kind == PI_COLL) go = wait_at_least(pflag + w.dep, 1, abort_w, timeout_ns);
         if (!go) atomicOr(doms[w.dom].status, ST_TIMEOUT);
       }
@@ -2302,6 +2311,11 @@ k_step_persist(const DomainDev* __restrict__ doms, int ndom, int parity,
       for (int j = 0; j < npt; ++j)
         prep_body<D, M, RT>(rec, d.Tf, static_cast<RT*>(d.cpar), d.g, d.un, d.bc, *d.mech,
                             w.first + (long long)j * kPersistThreads + threadIdx.x);
+    } else if (w.kind == PI_COLLIDE) {
+      for (int j = 0; j < npt; ++j)
+        collide_body<D, M, S, RT>(src, static_cast<S*>(const_cast<void*>(d.pops[1 - c])), rec,
+                                  d.Tf, d.status, d.g, d.un, d.bc, *d.mech,
+                                  w.first + (long long)j * kPersistThreads + threadIdx.x);
     } else {
       coll_block<D, M, S, RT, kPersistCollWarps>(
           src, static_cast<S*>(const_cast<void*>(d.pops[1 - c])),
@@ -2319,32 +2333,22 @@ k_step_persist(const DomainDev* __restrict__ doms, int ndom, int parity,
 }
 
 // dynamic shared memory of k_step_persist: the largest of its items' needs
-template <int D, int M, typename S, typename RT> constexpr size_t persist_smem() {
+// (split: parameter and collision items; else fused collision items)
+template <int D, int M, typename S, typename RT> constexpr size_t persist_smem(bool split) {
   using R = typename ComputeType<S>::type;
   const size_t bnd = bnode_smem<D, M, R>() * (kPersistThreads / kBnd);
   const size_t prep = (size_t)M * M * kBS * sizeof(RT);
   const size_t coll = (size_t)coll_smem_entries<D, M>() * kCollNodes * sizeof(RT);
+  const size_t fused = (size_t)collide_smem_entries<D, M, RT>() * kBS * sizeof(RT);
   const size_t chem = kFF<RT> ? chem_slice_bytes<M, ff>() : 0;
-  size_t m = bnd > prep ? bnd : prep;
-  m = m > coll ? m : coll;
-  return m > chem ? m : chem;
-}
-
-template <int D, int M, typename S>
-__global__ void __launch_bounds__(128)
-k_boundary_batch(const DomainDev* __restrict__ doms, int ndom, int parity, int with_rec,
-                 int nblk) {
-  using R = typename ComputeType<S>::type;
-  for (int b = blockIdx.x; b < nblk; b += gridDim.x) {
-    const DomainDev& d = doms[domain_of_block(doms, ndom, b, GRID_BOUNDARY)];
-    const int c = d.cur0 ^ parity;
-    const int k = (b - d.bblock_begin) * 4 + threadIdx.x / 32, lane = threadIdx.x & 31;
-    boundary_body<D, M, S, R>(static_cast<const S*>(d.pops[c]), d.bc, d.Tf, d.status, d.g,
-                              d.un, *d.mech, *d.mech, k, lane);
-    if (with_rec)
-      boundary_record<D, M, R>(d.bc, static_cast<R*>(d.rec), d.Tf, d.status, d.g, d.un,
-                               *d.mech, *d.mech, k, lane);
+  size_t m = bnd > chem ? bnd : chem;
+  if (split) {
+    m = m > prep ? m : prep;
+    m = m > coll ? m : coll;
+  } else {
+    m = m > fused ? m : fused;
   }
+  return m;
 }
 
 // ---------------------------------------------------------------------------
@@ -2554,7 +2558,8 @@ static cudaError_t prepare_impl() {
   big((const void*)k_coll_batch<D, M, S, RT>, coll_smem<D, M, RT>());
   big((const void*)k_bnode<D, M, S>, bnode_smem<D, M, RT>());
   big((const void*)k_bnode_batch<D, M, S>, bnode_smem<D, M, RT>());
-  big((const void*)k_step_persist<D, M, S, RT>, persist_smem<D, M, S, RT>());
+  big((const void*)k_step_persist<D, M, S, RT>,
+      std::max(persist_smem<D, M, S, RT>(true), persist_smem<D, M, S, RT>(false)));
   return e;
 }
 
@@ -2738,7 +2743,7 @@ static cudaError_t batch_impl(const DomainDev* doms, int ndom, const BatchGrids&
     // first)
     if (gr.nitems == 0) return cudaSuccess;
     auto kp = k_step_persist<D, M, S, RT>;
-    const size_t sm = persist_smem<D, M, S, RT>();
+    const size_t sm = persist_smem<D, M, S, RT>(lc.coll_split != 0);
     cudaError_t e = cudaMemsetAsync(gr.sync, 0, (size_t)gr.nsync * sizeof(int), s);
     if (e != cudaSuccess) return e;
     kp<<<batch_grid(kp, gr.nitems, kPersistThreads, sm, true), kPersistThreads, sm, s>>>(
@@ -2751,6 +2756,7 @@ static cudaError_t batch_impl(const DomainDev* doms, int ndom, const BatchGrids&
   auto kbnd = k_bnode_batch<D, M, S>;
   const size_t sbnd = bnode_smem<D, M, RT>();
   // the reaction sub-steps in k_chem over a node set (the grid of the set)
+  static_assert(128 / 8 == kIfChemNodesPerBlock, "interface chemistry: 8 lanes per node");
   auto chem = [&](int node_set, cudaStream_t st) {
     const int nb = node_set == NODES_INTERFACE ? gr.nbblocks : gr.ncblocks;
     if (nb == 0) return;

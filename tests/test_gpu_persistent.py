@@ -5,7 +5,9 @@ item waiting (boundedly) only for the items it reads.
 
 * Uneven domains (flame with inlet and outlet, periodic box, staircase tube
   with off-grid wall targets, reactor; D2Q9 channel and box) advanced by a
-  single-launch plan equal the same handles stepped alone: 1e-12 relative
+  single-launch plan (split collision: parameter then collision items; fused:
+  one collision item per node tile) equal the same handles stepped alone
+  with the same placement: 1e-12 relative
   per lattice in FP64, 5e-5 in FP32 storage (float-float chemistry in the
   launch's dynamic shared memory), for 1, 2 and 4 nodes per thread, over odd
   and even step counts.
@@ -49,30 +51,32 @@ def _keep(a, w):
     return np.ones(a.N, bool) if w.get("solid") is None else ~np.asarray(w["solid"]).reshape(-1)
 
 
-def _run_pairs(mech, ws, precision, npt, runs):
+def _run_pairs(mech, ws, precision, npt, runs, split=1):
     from paper_2108_07605_gb300 import lbm
     pairs = [(make_gpu(mech, w, precision=precision), make_gpu(mech, w, precision=precision))
              for w in ws]
     plan = lbm.lbm_batch_create([a.h for a, _ in pairs])
-    lbm.lbm_batch_set_launch(plan, persistent=2, nodes_per_thread=npt)
+    lbm.lbm_batch_set_launch(plan, collide_split=split, persistent=2, nodes_per_thread=npt)
     got = lbm.lbm_batch_get_launch(plan)
     assert got["persistent"] == 2 and got["nodes_per_thread"] == npt
+    assert got["collide_split"] == split
     total = 0
     for r in runs:
         lbm.lbm_batch_run(plan, r)
         total += r
     lbm.lbm_batch_destroy(plan)
     for _, b in pairs:
-        b.set_launch(chem_lanes=1, collide_split=1)
+        b.set_launch(chem_lanes=1, collide_split=split)
         b.step(total)
     return pairs
 
 
-@pytest.mark.parametrize("precision,npt", [("fp64", 1), ("fp64", 2), ("fp64", 4),
-                                           ("fp32", 1), ("fp32", 4)])
-def test_single_launch_equals_separate_steps_d3q27(mech, precision, npt):
+@pytest.mark.parametrize("precision,npt,split", [
+    ("fp64", 1, 1), ("fp64", 2, 1), ("fp64", 4, 1), ("fp64", 1, 0), ("fp64", 2, 0),
+    ("fp32", 1, 1), ("fp32", 4, 1), ("fp32", 1, 0)])
+def test_single_launch_equals_separate_steps_d3q27(mech, precision, npt, split):
     ws = _mix3d(mech)
-    pairs = _run_pairs(mech, ws, precision, npt, [3, 4])
+    pairs = _run_pairs(mech, ws, precision, npt, [3, 4], split)
     for (a, b), w in zip(pairs, ws):
         err = max_rel_err_per_lattice(a.populations(), b.populations(), _keep(a, w))
         assert np.all(err <= TOL[precision]), (w.get("name"), err.max())
@@ -83,9 +87,10 @@ def test_single_launch_equals_separate_steps_d3q27(mech, precision, npt):
         b.close()
 
 
-def test_single_launch_equals_separate_steps_d2q9(mech):
+@pytest.mark.parametrize("split", [1, 0])
+def test_single_launch_equals_separate_steps_d2q9(mech, split):
     ws = [fields.channel_2d(nx=30, ny=9), fields.perturbed_box((17, 6, 1), "D2Q9", mech=mech)]
-    pairs = _run_pairs(mech, ws, "fp64", 2, [5, 4])
+    pairs = _run_pairs(mech, ws, "fp64", 2, [5, 4], split)
     for a, b in pairs:
         err = max_rel_err_per_lattice(a.populations(), b.populations())
         assert np.all(err <= TOL["fp64"]), err.max()
@@ -112,7 +117,8 @@ def test_single_launch_many_domains(mech):
         b.close()
 
 
-def test_single_launch_matches_the_oracle(mech):
+@pytest.mark.parametrize("split", [1, 0])
+def test_single_launch_matches_the_oracle(mech, split):
     """FP64, element by element against the oracle after 4 steps."""
     from paper_2108_07605_gb300 import lbm
     ws = [fields.flame_1d(nx=24, ny=2, nz=2, x_ign=6, mech=mech),
@@ -120,7 +126,7 @@ def test_single_launch_matches_the_oracle(mech):
           fields.perturbed_box((7, 5, 4), "D3Q27", mech=mech)]
     gs = [make_gpu(mech, w) for w in ws]
     plan = lbm.lbm_batch_create([g.h for g in gs])
-    lbm.lbm_batch_set_launch(plan, persistent=2, nodes_per_thread=1)
+    lbm.lbm_batch_set_launch(plan, collide_split=split, persistent=2, nodes_per_thread=1)
     lbm.lbm_batch_run(plan, 4)
     lbm.lbm_batch_destroy(plan)
     for g, w in zip(gs, ws):
