@@ -400,6 +400,14 @@ lbm_status lbm_destroy(lbm_t h);
  * lbm_last_error(NULL)). */
 lbm_status lbm_ff_check(const double* x, long long n, double* exp_out, double* log_out);
 
+/* The FP64 exp of the reaction rates (Sec. 3.6's Arrhenius form and the
+ * reverse rates from equilibrium constants: exp of ln k), Tang's
+ * table-driven method, at the n points x (host arrays; exp_out receives n
+ * values).  A test hook for its accuracy; synchronous.  LBM_ERR_INVALID for
+ * NULL buffers or n < 0, LBM_ERR_RANGE for n > 2^24, LBM_ERR_CUDA on a
+ * device error. */
+lbm_status lbm_exp64_check(const double* x, long long n, double* exp_out);
+
 /* Measured fused-multiply-add throughput of the current device in TFLOP/s
  * (2 FLOP per FMA), FP64 when fp64 != 0, else FP32.  No counterpart in the
  * paper: the ALU roof against which the step's executed operation counts

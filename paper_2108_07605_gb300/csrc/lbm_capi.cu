@@ -7,6 +7,7 @@
 #include <string>
 #include <vector>
 
+#include "exp64.cuh"
 #include "ff.cuh"
 #include "lbm_internal.h"
 
@@ -1661,6 +1662,33 @@ const char* lbm_last_error(lbm_t h) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// The FP64 table-driven exp at given points (a test hook for its accuracy).
+__global__ void k_exp64_check(const double* __restrict__ x, long long n,
+                              double* __restrict__ e) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i < n) e[i] = exp_tang(x[i]);
+}
+
+lbm_status lbm_exp64_check(const double* x, long long n, double* exp_out) {
+  if (!x || !exp_out || n < 0)
+    return fail(nullptr, LBM_ERR_INVALID, "lbm_exp64_check: NULL buffer or negative n");
+  if (n > (1LL << 24)) return fail(nullptr, LBM_ERR_RANGE, "lbm_exp64_check: n above 2^24");
+  if (n == 0) return LBM_OK;
+  double* d = nullptr;
+  const size_t b = (size_t)n * sizeof(double);
+  cudaError_t e = cudaMalloc(&d, 2 * b);
+  if (e != cudaSuccess) return cuda_fail(nullptr, e, "lbm_exp64_check allocation");
+  e = cudaMemcpy(d, x, b, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) {
+    k_exp64_check<<<(unsigned)((n + 255) / 256), 256>>>(d, n, d + n);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpy(exp_out, d + n, b, cudaMemcpyDeviceToHost);
+  cudaFree(d);
+  return e == cudaSuccess ? LBM_OK : cuda_fail(nullptr, e, "lbm_exp64_check");
+}
 
 // ---------------------------------------------------------------------------
 // Float-float exp and log at given points (a test hook for their accuracy).

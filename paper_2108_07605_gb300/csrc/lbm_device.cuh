@@ -9,6 +9,7 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "exp64.cuh"
 #include "lbm_internal.h"
 
 namespace lbm {
@@ -130,7 +131,7 @@ __device__ void production_rates(const DevMech& m, double T, const double* r,
   for (int k = 0; k < m.R; ++k) {
     const DevReaction& rx = m.rx[k];
     const double lnkf = rx.lnA + rx.b * lnT - rx.EaR * invT;
-    double fwd = exp(lnkf);
+    double fwd = exp_tang(lnkf);
     for (int j = 0; j < rx.nr; ++j) fwd *= C[rx.reac[j]];
     double rev = 0.0;
     if (rx.reversible) {
@@ -138,7 +139,7 @@ __device__ void production_rates(const DevMech& m, double T, const double* r,
       for (int j = 0; j < rx.np; ++j) dG += G[rx.prod[j]];
       for (int j = 0; j < rx.nr; ++j) dG -= G[rx.reac[j]];
       // k_r = k_f / K_c, ln K_c = -dG + dn ln(P0/(R_U T))
-      rev = exp(lnkf + dG - rx.dn * ln_p0_rut);
+      rev = exp_tang(lnkf + dG - rx.dn * ln_p0_rut);
       for (int j = 0; j < rx.np; ++j) rev *= C[rx.prod[j]];
     }
     double q = fwd - rev;

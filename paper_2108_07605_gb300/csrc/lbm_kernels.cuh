@@ -403,7 +403,7 @@ __device__ __forceinline__ ff shfl_xor_ct(unsigned mask, ff v, int o) {
 
 template <typename CT> struct Chem;
 template <> struct Chem<double> {
-  __device__ static double ex(double x) { return exp(x); }
+  __device__ static double ex(double x) { return exp_tang(x); }
   __device__ static double ln(double x) { return log(x); }
   __device__ static double inv(double x) { return 1.0 / x; }
   __device__ static double inv_mm(const DevMech& m, int a) { return m.inv_mm[a]; }

@@ -111,6 +111,7 @@ EXPORTS = {
     "lbm_batch_destroy": (C.c_int, [C.c_void_p]),
     "lbm_batch_autotune": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(lbm_launch)]),
     "lbm_ff_check": (C.c_int, [C.c_void_p, C.c_longlong, C.c_void_p, C.c_void_p]),
+    "lbm_exp64_check": (C.c_int, [C.c_void_p, C.c_longlong, C.c_void_p]),
     "lbm_batch_set_launch": (C.c_int, [C.c_void_p, C.POINTER(lbm_launch)]),
     "lbm_batch_get_launch": (C.c_int, [C.c_void_p, C.POINTER(lbm_launch)]),
     "lbm_set_launch": (C.c_int, [C.c_void_p, C.POINTER(lbm_launch)]),
@@ -308,6 +309,15 @@ def lbm_batch_autotune(plan, trial_steps=3):
     _check(load_library().lbm_batch_autotune(plan, int(trial_steps), C.byref(out)),
            plan.handles[0])
     return _launch_dict(out)
+
+
+def lbm_exp64_check(x):
+    """The library's FP64 exp (reaction rates) at the points x (1-D float64)."""
+    import numpy as np
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    e = np.empty_like(x)
+    _check(load_library().lbm_exp64_check(x.ctypes.data, x.size, e.ctypes.data))
+    return e
 
 
 def lbm_ff_check(x):

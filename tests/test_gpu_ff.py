@@ -66,3 +66,18 @@ def test_ff_check_rejects_bad_arguments():
     assert L.lbm_ff_check(None, 4, x.ctypes.data, x.ctypes.data) == 1  # LBM_ERR_INVALID
     assert L.lbm_ff_check(x.ctypes.data, -1, x.ctypes.data, x.ctypes.data) == 1  # LBM_ERR_INVALID
     assert L.lbm_ff_check(x.ctypes.data, 1 << 25, x.ctypes.data, x.ctypes.data) == 6  # LBM_ERR_RANGE
+
+
+def test_fp64_table_exp_error():
+    """The FP64 rates' exp (Tang's method): within 2 ulp of numpy's exp over
+    the range of ln k (and well beyond), exact at 0, the library's exp past
+    |x| = 700."""
+    rng = np.random.default_rng(13)
+    x = np.concatenate([rng.uniform(-700.0, 700.0, 200_000), rng.uniform(-1e-3, 1e-3, 20_000),
+                        np.arange(-640, 641, dtype=np.float64) * np.log(2.0) / 64,
+                        [0.0, 700.0, -700.0, 705.0, -720.0]])
+    e = lbm.lbm_exp64_check(x)
+    ref = np.exp(x)
+    ulp = np.spacing(ref)
+    assert np.max(np.abs(e - ref) / ulp) <= 2.0
+    assert e[x == 0.0][0] == 1.0
