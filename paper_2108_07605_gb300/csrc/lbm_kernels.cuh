@@ -345,41 +345,58 @@ __device__ __forceinline__ void moments_body(const S* __restrict__ src, RT* __re
 #pragma unroll
     for (int d = 0; d < D; ++d) js[a][d] = RT(0);
   }
-  // x-rows of three velocities unrolled (c_x a constant), rows rolled: the
-  // fully unrolled loop is ~27 copies of the body, whose instruction fetch
-  // dominates grids too small to keep many warps per SM
+  // rows of three velocities (c_x = -1, 0, 1 at fixed c_y, c_z), rows
+  // rolled: the fully unrolled loop is ~27 copies of the body, whose
+  // instruction fetch dominates grids too small to keep many warps per SM.
+  // A row's populations enter through their sum s and difference d = f_+ -
+  // f_- (and f_+ + f_- for P_xx): sum_i c_ix f_i = sum_rows d,
+  // sum_i c_iy f_i = sum_rows c_y s, and so on.
 #pragma unroll 1
   for (int r = 0; r < Q / 3; ++r) {
     const RT cy = RT(r % 3 - 1), cz = RT(D == 3 ? r / 3 - 1 : 0);
-    const RT cyc[3] = {RT(0), cy, cz};
+    const long long sn0 = node_shift<D>(x, y, z, 3 * r, -1, g);
+    const long long sn1 = node_shift<D>(x, y, z, 3 * r + 1, -1, g);
+    const long long sn2 = node_shift<D>(x, y, z, 3 * r + 2, -1, g);
 #pragma unroll
-    for (int ix = 0; ix < 3; ++ix) {
-      const int i = 3 * r + ix;
-      const RT cx = RT(ix - 1);
-      const RT cv[3] = {cx, cy, cz};
-      const long long sn = node_shift<D>(x, y, z, i, -1, g);
-#pragma unroll
-      for (int a = 0; a < M - 1; ++a) {
-        const RT v = pop_in<RT>(src, bc, tag, N, sn, a * Q + i, codec);
-        rs[a] += v;
-        if (ix != 1) js[a][0] += cx * v;
-#pragma unroll
-        for (int d = 1; d < D; ++d) js[a][d] += cyc[d] * v;
+    for (int a = 0; a < M - 1; ++a) {
+      const RT v0 = pop_in<RT>(src, bc, tag, N, sn0, a * Q + 3 * r, codec);
+      const RT v1 = pop_in<RT>(src, bc, tag, N, sn1, a * Q + 3 * r + 1, codec);
+      const RT v2 = pop_in<RT>(src, bc, tag, N, sn2, a * Q + 3 * r + 2, codec);
+      const RT sr = v0 + v1 + v2;
+      rs[a] += sr;
+      js[a][0] += v2 - v0;
+      js[a][1] += cy * sr;
+      if (D == 3) js[a][D - 1] += cz * sr;
+    }
+    {
+      const int l = M - 1;
+      const RT f0 = pop_in<RT>(src, bc, tag, N, sn0, l * Q + 3 * r, codec);
+      const RT f1 = pop_in<RT>(src, bc, tag, N, sn1, l * Q + 3 * r + 1, codec);
+      const RT f2 = pop_in<RT>(src, bc, tag, N, sn2, l * Q + 3 * r + 2, codec);
+      const RT sx = f0 + f2, sr = sx + f1, dx = f2 - f0;
+      rho += sr;
+      j[0] += dx;
+      j[1] += cy * sr;
+      P[pidx<D>(0, 0)] += sx;
+      P[pidx<D>(1, 1)] += (cy * cy) * sr;
+      P[pidx<D>(0, 1)] += cy * dx;
+      if constexpr (D == 3) {
+        j[2] += cz * sr;
+        P[pidx<D>(2, 2)] += (cz * cz) * sr;
+        P[pidx<D>(0, 2)] += cz * dx;
+        P[pidx<D>(1, 2)] += (cy * cz) * sr;
       }
-      const RT f = pop_in<RT>(src, bc, tag, N, sn, (M - 1) * Q + i, codec);
-      rho += f;
-#pragma unroll
-      for (int d = 0; d < D; ++d) {
-        if (d != 0 || ix != 1) j[d] += cv[d] * f;
-#pragma unroll
-        for (int e = d; e < D; ++e)
-          if (d != 0 || ix != 1) P[pidx<D>(d, e)] += cv[d] * cv[e] * f;
-      }
-      const RT gv = pop_in<RT>(src, bc, tag, N, sn, M * Q + i, codec);
-      rhoE += gv;
-#pragma unroll
-      for (int d = 0; d < D; ++d)
-        if (d != 0 || ix != 1) q[d] += cv[d] * gv;
+    }
+    {
+      const int l = M;
+      const RT g0 = pop_in<RT>(src, bc, tag, N, sn0, l * Q + 3 * r, codec);
+      const RT g1 = pop_in<RT>(src, bc, tag, N, sn1, l * Q + 3 * r + 1, codec);
+      const RT g2 = pop_in<RT>(src, bc, tag, N, sn2, l * Q + 3 * r + 2, codec);
+      const RT sr = g0 + g1 + g2;
+      rhoE += sr;
+      q[0] += g2 - g0;
+      q[1] += cy * sr;
+      if (D == 3) q[D - 1] += cz * sr;
     }
   }
   moments_finish<D, M, RT, kDynChem>(rec, Tf, status, N, un, mech, n, chem_inline, rho, rhoE, j,
