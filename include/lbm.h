@@ -293,7 +293,8 @@ typedef struct {
                          dependency wait that outlasts 4 s
                          ends the launch and the handles report
                          LBM_ERR_TIMEOUT; 0 = one block per tile; -1 = the
-                         default: 2 for plans of FP64 storage, else 0 */
+                         default: 2 for plans of FP64 storage below 311,296
+                         nodes in all, else 0 */
   int nodes_per_thread;  /* persistent = 2: nodes per thread of the node
                          tiles, 1, 2 or 4 (tiles of 128, 256, 512 nodes);
                          -1 = 1 */

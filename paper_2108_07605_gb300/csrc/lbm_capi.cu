@@ -64,21 +64,24 @@ lbm_status cuda_fail(lbm_ctx* h, cudaError_t e, const char* where) {
 constexpr long long kSmallGrid = 152LL * 4 * 128;
 
 // Defaults, measured on one GB300.  plan: a batch plan's placement, whose
-// default for FP64 storage is the single launch over the work-list with
-// split collision (13 % faster than one launch per kernel on a mix of eight
-// small domains, within 1-2 % of the best on large ones); FP32 and FP16
-// plans keep one launch per kernel, whose kernels hold fewer registers than
-// the single launch.  One handle, FP64, a grid that fills the GPU at one
+// default for FP64 storage below kPlanSingleLaunch nodes in total is the
+// single launch over the work-list with split collision (17 % faster than
+// one launch per kernel on a mix of eight domains of 92k nodes in all; on
+// batches of about a million nodes one launch per kernel is 2 % faster);
+// FP32 and FP16 plans keep one launch per kernel, whose kernels hold fewer
+// registers than the single launch.  FP64, a grid that fills the GPU at one
 // thread per node: the fused collision (3 % faster on the 600x40x40 tube);
 // else the split one.
+constexpr long long kPlanSingleLaunch = 4 * kSmallGrid;
 Launch resolve_launch(const lbm_launch& opt, long long nodes, lbm_precision prec,
                       bool plan = false) {
   Launch lc;
   const bool small = nodes < kSmallGrid;
   lc.chem_lanes = opt.chem_lanes > 0 ? opt.chem_lanes
                                      : (small && prec == LBM_FP32_STORE ? 4 : 1);
-  lc.persistent = opt.persistent >= 0 ? opt.persistent
-                                     : (plan && prec == LBM_FP64 ? 2 : 0);
+  lc.persistent = opt.persistent >= 0
+                      ? opt.persistent
+                      : (plan && prec == LBM_FP64 && nodes < kPlanSingleLaunch ? 2 : 0);
   lc.coll_split = opt.collide_split >= 0
                       ? opt.collide_split
                       : (prec == LBM_FP64 && !small && lc.persistent != 2 ? 0 : 1);

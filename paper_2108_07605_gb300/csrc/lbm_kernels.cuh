@@ -2105,14 +2105,40 @@ __device__ __forceinline__ int domain_of_block(const DomainDev* __restrict__ d, 
 // ... below nblk: launched with one block per tile it runs each tile once;
 // launched persistent (a grid sized to the blocks resident on the GPU) each
 // block processes several tiles in turn.
+//
+// The block's domain descriptor is copied to shared memory whenever the
+// block moves to another domain (k block-uniform, every thread calls it),
+// so the bodies read its fields from shared memory rather than reloading
+// them from global memory around every store.
+struct BlockDomain {
+  unsigned char* raw;   // __shared__ storage of sizeof(DomainDev) bytes
+  int cur = -1;
+  __device__ const DomainDev& get(const DomainDev* __restrict__ doms, int k) {
+    if (k != cur) {
+      __syncthreads();   // the previous domain's readers are done
+      const unsigned* src = reinterpret_cast<const unsigned*>(doms + k);
+      unsigned* dst = reinterpret_cast<unsigned*>(raw);
+      for (int i = threadIdx.x; i < (int)(sizeof(DomainDev) / 4); i += blockDim.x)
+        dst[i] = src[i];
+      __syncthreads();
+      cur = k;
+    }
+    return *reinterpret_cast<const DomainDev*>(raw);
+  }
+};
+static_assert(sizeof(DomainDev) % 4 == 0, "domain descriptor copied in 4-byte words");
+#define LBM_BLOCK_DOMAIN(name)                                          \
+  __shared__ __align__(16) unsigned char name##_raw[sizeof(DomainDev)]; \
+  BlockDomain name{name##_raw}
 template <int D, int M, typename S, typename RT>
 __global__ void __launch_bounds__(128, kMomentsMinBlocks<RT>)
 k_moments_batch(const DomainDev* __restrict__ doms, int ndom, int parity, int chem_inline,
                 int node_set, int nblk) {
+  LBM_BLOCK_DOMAIN(bd);
   // node_set: NODES_ALL or NODES_BULK (the interface nodes' records come from
   // k_bnode_batch)
   for (int b = blockIdx.x; b < nblk; b += gridDim.x) {
-    const DomainDev& d = doms[domain_of_block(doms, ndom, b, GRID_NODE)];
+    const DomainDev& d = bd.get(doms, domain_of_block(doms, ndom, b, GRID_NODE));
     const int c = d.cur0 ^ parity;
     const long long n = (b - d.block_begin) * (long long)blockDim.x + threadIdx.x;
     if (node_set == NODES_BULK && d.bc.tag && n < d.g.N && d.bc.tag[n] >= 0) continue;
@@ -2126,14 +2152,15 @@ k_moments_batch(const DomainDev* __restrict__ doms, int ndom, int parity, int ch
 template <int D, int M, typename RT, int L>
 __global__ void __launch_bounds__(128)
 k_chem_batch(const DomainDev* __restrict__ doms, int ndom, int node_set, int nblk) {
+  LBM_BLOCK_DOMAIN(bd);
   for (int b = blockIdx.x; b < nblk; b += gridDim.x) {
     if (node_set == NODES_INTERFACE) {
-      const DomainDev& d = doms[domain_of_block(doms, ndom, b, GRID_BOUNDARY)];
+      const DomainDev& d = bd.get(doms, domain_of_block(doms, ndom, b, GRID_BOUNDARY));
       chem_entry<D, M, RT, L>(static_cast<RT*>(d.rec), d.Tf, d.status, d.g.N, d.bc.tag, d.un,
                               *d.mech, (b - d.bblock_begin) * (128LL / L), NODES_INTERFACE,
                               d.bc.if_node, d.bc.n_if);
     } else {
-      const DomainDev& d = doms[domain_of_block(doms, ndom, b, GRID_CHEM)];
+      const DomainDev& d = bd.get(doms, domain_of_block(doms, ndom, b, GRID_CHEM));
       chem_entry<D, M, RT, L>(static_cast<RT*>(d.rec), d.Tf, d.status, d.g.N, d.bc.tag, d.un,
                               *d.mech, (b - d.cblock_begin) * (128LL / L), node_set, nullptr,
                               0);
@@ -2146,8 +2173,9 @@ template <int D, int M, typename S, typename RT, int L>
 __global__ void __launch_bounds__(128)
 k_mchem_batch(const DomainDev* __restrict__ doms, int ndom, int parity, int node_set,
               int nblk) {
+  LBM_BLOCK_DOMAIN(bd);
   for (int b = blockIdx.x; b < nblk; b += gridDim.x) {
-    const DomainDev& d = doms[domain_of_block(doms, ndom, b, GRID_CHEM)];
+    const DomainDev& d = bd.get(doms, domain_of_block(doms, ndom, b, GRID_CHEM));
     const int c = d.cur0 ^ parity;
     const int lane = threadIdx.x & 31;
     const long long n = (b - d.cblock_begin) * (128LL / L) + threadIdx.x / L;
@@ -2164,8 +2192,9 @@ k_mchem_batch(const DomainDev* __restrict__ doms, int ndom, int parity, int node
 template <int D, int M, typename S, typename RT>
 __global__ void __launch_bounds__(128)
 k_collide_batch(const DomainDev* __restrict__ doms, int ndom, int parity, int nblk) {
+  LBM_BLOCK_DOMAIN(bd);
   for (int b = blockIdx.x; b < nblk; b += gridDim.x) {
-    const DomainDev& d = doms[domain_of_block(doms, ndom, b, GRID_NODE)];
+    const DomainDev& d = bd.get(doms, domain_of_block(doms, ndom, b, GRID_NODE));
     const int c = d.cur0 ^ parity;
     collide_body<D, M, S, RT>(static_cast<const S*>(d.pops[c]),
                               static_cast<S*>(const_cast<void*>(d.pops[1 - c])),
@@ -2177,8 +2206,9 @@ k_collide_batch(const DomainDev* __restrict__ doms, int ndom, int parity, int nb
 template <int D, int M, typename RT>
 __global__ void __launch_bounds__(128)
 k_prep_batch(const DomainDev* __restrict__ doms, int ndom, int nblk) {
+  LBM_BLOCK_DOMAIN(bd);
   for (int b = blockIdx.x; b < nblk; b += gridDim.x) {
-    const DomainDev& d = doms[domain_of_block(doms, ndom, b, GRID_NODE)];
+    const DomainDev& d = bd.get(doms, domain_of_block(doms, ndom, b, GRID_NODE));
     prep_body<D, M, RT>(static_cast<const RT*>(d.rec), d.Tf, static_cast<RT*>(d.cpar), d.g,
                         d.un, d.bc, *d.mech,
                         (b - d.block_begin) * (long long)blockDim.x + threadIdx.x);
@@ -2188,9 +2218,10 @@ k_prep_batch(const DomainDev* __restrict__ doms, int ndom, int nblk) {
 template <int D, int M, typename S, typename RT>
 __global__ void __launch_bounds__(32 * kCollTPN, sizeof(RT) == 4 ? 4 : 1)
 k_coll_batch(const DomainDev* __restrict__ doms, int ndom, int parity, int nblk) {
+  LBM_BLOCK_DOMAIN(bd);
   extern __shared__ __align__(16) unsigned char coll_raw[];
   for (int b = blockIdx.x; b < nblk; b += gridDim.x) {
-    const DomainDev& d = doms[domain_of_block(doms, ndom, b, GRID_COLL)];
+    const DomainDev& d = bd.get(doms, domain_of_block(doms, ndom, b, GRID_COLL));
     const int c = d.cur0 ^ parity;
     // the previous tile's threads are done with the shared memory
     if (b != blockIdx.x) __syncthreads();
@@ -2206,6 +2237,7 @@ k_coll_batch(const DomainDev* __restrict__ doms, int ndom, int parity, int nblk)
 template <int D, int M, typename S>
 __global__ void __launch_bounds__(kBnd)
 k_bnode_batch(const DomainDev* __restrict__ doms, int ndom, int parity, int nblk) {
+  LBM_BLOCK_DOMAIN(bd);
   using R = typename ComputeType<S>::type;
   extern __shared__ __align__(16) unsigned char bnd_raw[];
   R* col = reinterpret_cast<R*>(bnd_raw) + threadIdx.x;
@@ -2213,7 +2245,7 @@ k_bnode_batch(const DomainDev* __restrict__ doms, int ndom, int parity, int nblk
       reinterpret_cast<long long*>(bnd_raw + sizeof(R) * bnode_col_entries<D, M>() * kBnd) +
       threadIdx.x;
   for (int b = blockIdx.x; b < nblk; b += gridDim.x) {
-    const DomainDev& d = doms[domain_of_block(doms, ndom, b, GRID_BNODE)];
+    const DomainDev& d = bd.get(doms, domain_of_block(doms, ndom, b, GRID_BNODE));
     const int k = (b - d.tblock_begin) * kBnd + threadIdx.x;
     if (k >= d.bc.n_if) continue;
     bnode_body<D, M, S, R>(static_cast<const S*>(d.pops[d.cur0 ^ parity]), d.bc,
@@ -2271,6 +2303,7 @@ __global__ void __launch_bounds__(kPersistThreads, kPersistMinBlocks<RT>)
 k_step_persist(const DomainDev* __restrict__ doms, int ndom, int parity,
                const PItem* __restrict__ items, int nitems, int npt, int* __restrict__ sync,
                long long timeout_ns) {
+  LBM_BLOCK_DOMAIN(bd);
   using R = typename ComputeType<S>::type;
   constexpr int Q = Lat<D>::Q;
   extern __shared__ __align__(16) unsigned char ps_raw[];
@@ -2296,7 +2329,7 @@ k_step_persist(const DomainDev* __restrict__ doms, int ndom, int parity,
     __syncthreads();
     if (!s_go) break;
     const PItem w = items[s_item];
-    const DomainDev& d = doms[w.dom];
+    const DomainDev& d = bd.get(doms, w.dom);
     const int c = d.cur0 ^ parity;
     const S* src = static_cast<const S*>(d.pops[c]);
     RT* rec = static_cast<RT*>(d.rec);
