@@ -332,6 +332,25 @@ lbm_status lbm_batch_autotune(lbm_batch_t b, int trial_steps, lbm_launch* chosen
  * unchanged); LBM_ERR_CUDA if the new graphs cannot be captured (destroy
  * the plan then). */
 lbm_status lbm_batch_set_launch(lbm_batch_t b, const lbm_launch* l);
+
+/* The work-list of the single-launch batched step (persistent = 2) for n
+ * domains of nodes[k] nodes, n_if[k] of them interface nodes: host only (no
+ * device, no handle), the list a plan of such handles uploads.  items
+ * receives five values per item, in list order: kind (0 boundary: 128
+ * interface nodes from `first`; 1 moments and 2 collision parameters: a
+ * tile of 128 x nodes_per_thread nodes; 3 collision: 32 nodes; 4 fused
+ * collision: a tile), domain, first (interface index or node), dep (kinds 2
+ * and 4: the count of the domain's kind-0 and kind-1 items they wait for;
+ * kind 3: the flag it waits for), flag (kind 2: the flag it sets).  Every
+ * dependency names items earlier in the list, the property that lets the
+ * launch's bounded waits end without a co-residency guarantee.  *nitems and
+ * *nsync receive the item and sync-word counts (cap = 0: counts only).
+ * LBM_ERR_INVALID for NULL pointers, n < 1, nodes_per_thread not 1, 2 or 4,
+ * or a domain with nodes < 1 or n_if outside 0..nodes; LBM_ERR_RANGE if cap
+ * (> 0) is below the item count. */
+lbm_status lbm_worklist(const long long* nodes, const long long* n_if, int n,
+                        int nodes_per_thread, int collide_split, long long* items, int cap,
+                        int* nitems, int* nsync);
 lbm_status lbm_batch_get_launch(lbm_batch_t b, lbm_launch* l);
 
 /* As lbm_step, and adds each kernel's device time in milliseconds, measured

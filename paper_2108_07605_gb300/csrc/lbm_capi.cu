@@ -1122,34 +1122,44 @@ namespace {
 // items of every domain, then the moments items), stage 2 (parameter items),
 // stage 3 (collision items), each stage domain by domain.  nsync: the sync
 // words the launch needs.
-void build_worklist(lbm_ctx* const* hs, int n, int npt, bool split, std::vector<PItem>& items,
-                    int& nsync) {
+void build_worklist(const long long* nodes, const long long* nif, int n, int npt, bool split,
+                    std::vector<PItem>& items, int& nsync) {
   items.clear();
   const long long tile = (long long)kPersistThreads * npt;
   std::vector<int> n1(n, 0), pbase(n, 0);
   for (int k = 0; k < n; ++k)
-    for (long long f = 0; f < hs[k]->bc.n_if; f += kPersistBndNodes, ++n1[k])
+    for (long long f = 0; f < nif[k]; f += kPersistBndNodes, ++n1[k])
       items.push_back(PItem{PI_BND, k, f, 0, 0});
   for (int k = 0; k < n; ++k)
-    for (long long f = 0; f < hs[k]->g.N; f += tile, ++n1[k])
+    for (long long f = 0; f < nodes[k]; f += tile, ++n1[k])
       items.push_back(PItem{PI_MOM, k, f, 0, 0});
   int nflag = 0;
   if (!split) {
     for (int k = 0; k < n; ++k)
-      for (long long f = 0; f < hs[k]->g.N; f += tile)
+      for (long long f = 0; f < nodes[k]; f += tile)
         items.push_back(PItem{PI_COLLIDE, k, f, n1[k], 0});
     nsync = kSyncHead + n;
     return;
   }
   for (int k = 0; k < n; ++k) {
     pbase[k] = nflag;
-    for (long long f = 0; f < hs[k]->g.N; f += tile)
+    for (long long f = 0; f < nodes[k]; f += tile)
       items.push_back(PItem{PI_PREP, k, f, n1[k], nflag++});
   }
   for (int k = 0; k < n; ++k)
-    for (long long f = 0; f < hs[k]->g.N; f += kCollNodesPerBlock)
+    for (long long f = 0; f < nodes[k]; f += kCollNodesPerBlock)
       items.push_back(PItem{PI_COLL, k, f, pbase[k] + (int)(f / tile), 0});
   nsync = kSyncHead + n + nflag;
+}
+
+void build_worklist(lbm_ctx* const* hs, int n, int npt, bool split, std::vector<PItem>& items,
+                    int& nsync) {
+  std::vector<long long> nodes(n), nif(n);
+  for (int k = 0; k < n; ++k) {
+    nodes[k] = hs[k]->g.N;
+    nif[k] = hs[k]->bc.n_if;
+  }
+  build_worklist(nodes.data(), nif.data(), n, npt, split, items, nsync);
 }
 
 cudaError_t batch_upload(lbm_batch_ctx* b) {
@@ -1336,6 +1346,33 @@ lbm_status lbm_batch_get_launch(lbm_batch_t b, lbm_launch* l) {
   l->collide_split = b->lc.coll_split;
   l->persistent = b->lc.persistent;
   l->nodes_per_thread = b->lc.npt;
+  return LBM_OK;
+}
+
+lbm_status lbm_worklist(const long long* nodes, const long long* n_if, int n,
+                        int nodes_per_thread, int collide_split, long long* items, int cap,
+                        int* nitems, int* nsync) {
+  if (!nodes || !n_if || !nitems || !nsync || n < 1 || (cap > 0 && !items))
+    return fail(nullptr, LBM_ERR_INVALID, "lbm_worklist: NULL argument or no domain");
+  if (nodes_per_thread != 1 && nodes_per_thread != 2 && nodes_per_thread != 4)
+    return fail(nullptr, LBM_ERR_INVALID, "lbm_worklist: nodes_per_thread must be 1, 2 or 4");
+  for (int k = 0; k < n; ++k)
+    if (nodes[k] < 1 || n_if[k] < 0 || n_if[k] > nodes[k])
+      return fail(nullptr, LBM_ERR_INVALID, "lbm_worklist: bad domain size");
+  std::vector<PItem> list;
+  int ns = 0;
+  build_worklist(nodes, n_if, n, nodes_per_thread, collide_split != 0, list, ns);
+  *nitems = (int)list.size();
+  *nsync = ns;
+  if ((int)list.size() > cap) return cap > 0 ? fail(nullptr, LBM_ERR_RANGE, "lbm_worklist: cap too small") : LBM_OK;
+  for (size_t i = 0; i < list.size(); ++i) {
+    long long* o = items + 5 * i;
+    o[0] = list[i].kind;
+    o[1] = list[i].dom;
+    o[2] = list[i].first;
+    o[3] = list[i].dep;
+    o[4] = list[i].flag;
+  }
   return LBM_OK;
 }
 

@@ -128,6 +128,8 @@ EXPORTS = {
     "lbm_last_error": (C.c_char_p, [C.c_void_p]),
     "lbm_fma_peak": (C.c_int, [C.c_int, C.POINTER(C.c_double)]),
     "lbm_wait_probe": (C.c_int, [C.c_int, C.c_longlong, C.POINTER(C.c_longlong)]),
+    "lbm_worklist": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_void_p,
+                               C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     "lbm_get_planes": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_int]),
     "lbm_set_planes": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_int]),
     "lbm_step_noalloc": (C.c_int, [C.POINTER(lbm_config), C.c_void_p, C.c_void_p,
@@ -472,6 +474,25 @@ def lbm_fma_peak(fp64):
     out = C.c_double(0.0)
     _check(load_library().lbm_fma_peak(1 if fp64 else 0, C.byref(out)))
     return out.value
+
+
+def lbm_worklist(nodes, n_if, nodes_per_thread=1, collide_split=1):
+    """The single-launch step's work-list for domains of the given node and
+    interface-node counts (host only): returns (items [n, 5] int64: kind,
+    domain, first, dep, flag; the number of sync words)."""
+    import numpy as np
+    nodes = np.ascontiguousarray(nodes, dtype=np.int64)
+    n_if = np.ascontiguousarray(n_if, dtype=np.int64)
+    lib = load_library()
+    cnt, ns = C.c_int(0), C.c_int(0)
+    _check(lib.lbm_worklist(nodes.ctypes.data, n_if.ctypes.data, nodes.size,
+                            int(nodes_per_thread), int(collide_split), None, 0,
+                            C.byref(cnt), C.byref(ns)))
+    items = np.zeros((max(cnt.value, 1), 5), dtype=np.int64)
+    _check(lib.lbm_worklist(nodes.ctypes.data, n_if.ctypes.data, nodes.size,
+                            int(nodes_per_thread), int(collide_split), items.ctypes.data,
+                            cnt.value, C.byref(cnt), C.byref(ns)))
+    return items[:cnt.value], ns.value
 
 
 def lbm_wait_probe(set_word, timeout_ns):

@@ -129,3 +129,51 @@ def test_mechanism_marshalling_round_trip(lbm):
     assert np.isclose(s.molar_mass[8], mech.molar_mass[8])
     assert s.nu_f[4][0] == 1 and s.nu_r[4][3] == 2          # H2 + M <=> 2 H + M
     assert s.third_body[4] == 1 and s.efficiency[4][2] == 12.0
+
+
+def _check_worklist(items, nsync, nodes, nif, npt, split):
+    """The single launch's list: stage order, coverage, and every dependency
+    on items earlier in the list (what lets its bounded waits end)."""
+    stage = {0: 1, 1: 1, 2: 2, 4: 2, 3: 3}
+    kinds = items[:, 0]
+    st = np.array([stage[int(k)] for k in kinds])
+    assert np.all(np.diff(st) >= 0)
+    tile = 128 * npt
+    n = len(nodes)
+    n1 = [int(np.sum((kinds <= 1) & (items[:, 1] == d))) for d in range(n)]
+    flag_at = {}
+    for i, (kind, dom, first, dep, flag) in enumerate(items):
+        if kind == 2:
+            flag_at[int(flag)] = (i, int(dom), int(first))
+    for d in range(n):
+        mine = items[items[:, 1] == d]
+        bnd = mine[mine[:, 0] == 0][:, 2]
+        assert list(bnd) == list(range(0, nif[d], 128))
+        for kind, step in ((1, tile), (2 if split else 4, tile), (3, 32)):
+            if kind == 3 and not split:
+                continue
+            firsts = mine[mine[:, 0] == kind][:, 2]
+            assert list(firsts) == list(range(0, nodes[d], step)), (d, kind)
+    for i, (kind, dom, first, dep, flag) in enumerate(items):
+        if kind in (2, 4):
+            assert dep == n1[dom]
+            before = items[:i]
+            assert np.sum((before[:, 0] <= 1) & (before[:, 1] == dom)) == n1[dom]
+        elif kind == 3:
+            j, pdom, pfirst = flag_at[int(dep)]
+            assert j < i and pdom == dom and pfirst <= first < pfirst + tile
+    nprep = int(np.sum(kinds == 2))
+    assert nsync == 2 + n + nprep
+    assert sorted(flag_at) == list(range(nprep))
+
+
+@pytest.mark.parametrize("npt,split", [(1, 1), (2, 1), (4, 1), (1, 0), (4, 0)])
+def test_single_launch_worklist_order(lbm, npt, split):
+    nodes = [4096, 130, 96000, 1, 300]
+    nif = [0, 40, 14400, 1, 300]
+    items, nsync = lbm.lbm_worklist(nodes, nif, npt, split)
+    _check_worklist(items, nsync, nodes, nif, npt, split)
+    with pytest.raises(lbm.LBMError):
+        lbm.lbm_worklist([10], [11], npt, split)          # more interface nodes than nodes
+    with pytest.raises(lbm.LBMError):
+        lbm.lbm_worklist([10], [0], 3, split)             # nodes per thread
