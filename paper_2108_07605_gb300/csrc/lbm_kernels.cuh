@@ -124,10 +124,10 @@ constexpr int kBS = 128;
 static_assert(kBS == kChemThreads, "the chemistry's shared-memory slices assume kBS threads");
 
 // shared memory of the collision kernel per thread: the diffusion-velocity
-// matrix, then the axis-factor tables (FP32: every axis; FP64 in 3D: the z
-// axis only, the whole table would halve the occupancy)
+// matrix, then the axis-factor tables (FP32: every axis; FP64 in 3D: the y
+// and z axes, the whole table would halve the occupancy)
 template <int D, int M, typename RT> constexpr int collide_smem_entries() {
-  constexpr int tab = sizeof(RT) == 4 ? 2 * M * D * 3 : (D == 3 ? 2 * M * 3 : 0);
+  constexpr int tab = sizeof(RT) == 4 ? 2 * M * D * 3 : (D == 3 ? 2 * M * 2 * 3 : 0);
   return tab > M * M ? tab : M * M;
 }
 
@@ -1259,16 +1259,16 @@ __device__ __forceinline__ void collide_direction(const PS& ps, const XYPart<D, 
 
 // Parameters held in registers (fused placement).  The species axis factors
 // come from a table in this thread's shared-memory column (FP32, entry stride
-// kBS) or are formed directly, except, in FP64 3D, those of the z axis,
-// tabulated in the column (ztab: entry ((set M + b) 3 + c + 1) kBS), which
-// every direction reads while the x and y factors serve a (c_x, c_y) pair.
+// kBS) or are formed directly, except, in FP64 3D, those of the y and z axes,
+// tabulated in the column (yztab: entry (((set M + b) 2 + d - 1) 3 + c + 1)
+// kBS, d = 1, 2).
 template <int D, int M, typename RT> struct RegPar {
   const NodePar<D, M, RT>& p;
   RT Afv[D][3], Bfv[D][3];
   const RT* tab;
-  const RT* ztab;
-  __device__ RegPar(const NodePar<D, M, RT>& p_, const RT* tab_, const RT* ztab_ = nullptr)
-      : p(p_), tab(tab_), ztab(ztab_) {
+  const RT* yztab;
+  __device__ RegPar(const NodePar<D, M, RT>& p_, const RT* tab_, const RT* yztab_ = nullptr)
+      : p(p_), tab(tab_), yztab(yztab_) {
     energy_factors<D, RT>(p.u, p.theta, Afv, Bfv);
   }
   __device__ RT rho() const { return p.rho; }
@@ -1286,7 +1286,7 @@ template <int D, int M, typename RT> struct RegPar {
   // species axis factor (set 0: psi(u, theta_b); set 1: psi(u + V_b, theta_b))
   __device__ RT sp(int set, int b, int d, int c) const {
     if (tab) return tab[(((set * M + b) * D + d) * 3 + c + 1) * kBS];
-    if (D == 3 && d == 2 && ztab) return ztab[((set * M + b) * 3 + c + 1) * kBS];
+    if (D == 3 && d > 0 && yztab) return yztab[(((set * M + b) * 2 + d - 1) * 3 + c + 1) * kBS];
     const RT xs = set ? p.u[d] + p.V[b][d] : p.u[d];
     return psi1<RT>(c, xs, p.th[b] + xs * xs);
   }
@@ -1315,7 +1315,7 @@ __device__ __forceinline__ void collide_body(const S* __restrict__ src, S* __res
   // shared-memory column (the solve's space, now free)
   extern __shared__ unsigned char smem_raw[];
   RT* tab = nullptr;
-  RT* ztab = nullptr;
+  RT* yztab = nullptr;
   if constexpr (sizeof(RT) == 4) {
     tab = reinterpret_cast<RT*>(smem_raw) + threadIdx.x;
     constexpr int NT = 2 * M * D * 3;
@@ -1323,20 +1323,23 @@ __device__ __forceinline__ void collide_body(const S* __restrict__ src, S* __res
     for (int e = 0; e < NT; ++e)
       tab[e * kBS] = axis_factor<D, M, RT>(e, p.th, p.u, &p.V[0][0]);
   } else if constexpr (D == 3) {
-    // FP64: the z-axis factors, psi_c(x_s, theta_b + x_s^2) with x_s = u_z
-    // (set 0) or u_z + V_bz (set 1)
-    ztab = reinterpret_cast<RT*>(smem_raw) + threadIdx.x;
+    // FP64: the y- and z-axis factors, psi_c(x_s, theta_b + x_s^2) with
+    // x_s = u_d (set 0) or u_d + V_bd (set 1)
+    yztab = reinterpret_cast<RT*>(smem_raw) + threadIdx.x;
 #pragma unroll
     for (int set = 0; set < 2; ++set)
 #pragma unroll
-      for (int b = 0; b < M; ++b) {
-        const RT xs = set ? p.u[2] + p.V[b][2] : p.u[2];
-        const RT Ps = p.th[b] + xs * xs;
+      for (int b = 0; b < M; ++b)
 #pragma unroll
-        for (int c = -1; c <= 1; ++c) ztab[((set * M + b) * 3 + c + 1) * kBS] = psi1<RT>(c, xs, Ps);
-      }
+        for (int d = 1; d < 3; ++d) {
+          const RT xs = set ? p.u[d] + p.V[b][d] : p.u[d];
+          const RT Ps = p.th[b] + xs * xs;
+#pragma unroll
+          for (int c = -1; c <= 1; ++c)
+            yztab[(((set * M + b) * 2 + d - 1) * 3 + c + 1) * kBS] = psi1<RT>(c, xs, Ps);
+        }
   }
-  const RegPar<D, M, RT> ps(p, tab, ztab);
+  const RegPar<D, M, RT> ps(p, tab, yztab);
   // directions i = j + 9 k share (c_x, c_y) = direction j's
 #pragma unroll 1
   for (int j = 0; j < 9; ++j) {
