@@ -131,3 +131,46 @@ def test_tube_segment_reduced_precision_fields(mech, tube_oracle, precision):
     assert dT <= tol["T"], dT
     assert du <= tol["u"], du
     assert drho <= tol["rho"], drho
+
+
+def test_substeps_converge_to_radau_on_the_gpu(mech):
+    """The GPU's reaction sub-steps (Sec. 2.4 Eq. R3, the discussion after
+    it): a uniform, still 4^3 periodic box is a constant-U reactor whose
+    species advance only by the l explicit sub-steps per step.  Against a
+    tight-tolerance Radau solution of the same reactor over the same time,
+    the OH density's error falls at first order in dt/l: l = 2 and l = 4
+    halve it and quarter it (within 1.6-2.5 per doubling), and stays small."""
+    scipy = pytest.importorskip("scipy.integrate")
+    from oracle import chemistry, thermo
+    w = fields.reactor(n=4, T0=1300.0, perturbation=0.0, dx=12.5e-6, mech=mech)
+    rho = thermo.density_from_pressure(mech, w["P"], w["T"], w["Y"]).reshape(-1)[0]
+    Y0 = np.asarray(w["Y"]).reshape(mech.n_species, -1)[:, 0]
+    T0 = 1300.0
+    U = float(thermo.mixture_U(mech, Y0[:, None], np.array([T0]))[0])
+    r0 = rho * Y0
+    iOH = mech.index("OH")
+    errs = []
+    for l in (1, 2, 4):
+        w["substeps"] = l
+        g = make_gpu(mech, w)
+        dt = g.info.dt
+        nsteps = int(round(1.0e-5 / dt))
+        g.step(nsteps)
+        m = g.moments()
+        g.close()
+        r_gpu = m["rho"][0] * m["Y"][:, 0]
+        t_end = nsteps * dt
+
+        def rhs(t, r):
+            T = thermo.temperature_from_energy(mech, (r / rho)[:, None], np.array([U]),
+                                               np.array([rhs.T]))
+            rhs.T = T[0]
+            return chemistry.production_rates(mech, T, r[:, None])[:, 0]
+        rhs.T = T0
+        ref = scipy.solve_ivp(rhs, (0.0, t_end), r0, method="Radau", rtol=1e-12,
+                              atol=1e-18).y[:, -1]
+        assert abs(ref[iOH] - r0[iOH]) > 10 * abs(r0[iOH]) + 1e-12   # OH has grown
+        errs.append(abs(r_gpu[iOH] - ref[iOH]) / abs(ref[iOH]))
+    assert errs[0] < 1e-2, errs
+    for a, b in zip(errs, errs[1:]):
+        assert 1.6 < a / b < 2.5, errs
