@@ -2298,6 +2298,24 @@ __device__ __forceinline__ void iface_substeps(RT* __restrict__ rec, const doubl
   for (int a = 0; a < M - 1; ++a) rec[(RC::DRHO + a) * N + n] = dr[a];
 }
 
+// The interface nodes' sub-steps with one thread per node (grids with at
+// least kIfChemThreadNodes interface nodes, which fill the GPU this way):
+// the same arithmetic as the lane groups of k_chem without their redundant
+// per-lane temperature and Gibbs evaluations.  Float-float rate arrays in
+// dynamic shared memory (chem_slice_bytes).
+constexpr long long kIfChemThreadNodes = 152LL * 128;
+
+template <int D, int M, typename RT>
+__global__ void __launch_bounds__(kChemThreads)
+k_iface_chem(RT* __restrict__ rec, const double* __restrict__ Tf, int* __restrict__ status,
+             long long N, const int* __restrict__ if_node, int n_if,
+             const __grid_constant__ Units un, const DevMech* __restrict__ mech) {
+  extern __shared__ __align__(16) unsigned char ic_raw[];
+  const long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (k >= n_if) return;
+  iface_substeps<D, M, RT>(rec, Tf, status, N, un, *mech, if_node[k], ic_raw);
+}
+
 template <typename RT> constexpr int kPersistMinBlocks = sizeof(RT) == 8 ? 2 : 3;
 constexpr int kPersistCollWarps = kPersistThreads / 32;
 
@@ -2620,7 +2638,13 @@ template <int D, int M, typename RT>
 static void launch_chem(const Launch& lc, cudaStream_t s, RT* rec, const double* Tf,
                         int* status, long long N, const BCDev& bc, const Units& un,
                         const DevMech* mech, int node_set) {
-  // the interface nodes are few and on the critical path: 8 lanes each
+  if (node_set == NODES_INTERFACE && bc.n_if >= kIfChemThreadNodes) {
+    const size_t sm = kFF<RT> ? chem_slice_bytes<M, ff>() : 0;
+    k_iface_chem<D, M, RT><<<blocks_for(bc.n_if, kChemThreads), kChemThreads, sm, s>>>(
+        rec, Tf, status, N, bc.if_node, bc.n_if, un, mech);
+    return;
+  }
+  // fewer interface nodes: on the critical path, 8 lanes each
   const int lanes = node_set == NODES_INTERFACE ? 8 : lc.chem_lanes;
   const long long n = node_set == NODES_INTERFACE ? bc.n_if : N;
   const unsigned nblk = blocks_for(n, 128 / lanes);
