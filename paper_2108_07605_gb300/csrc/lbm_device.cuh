@@ -303,51 +303,4 @@ __device__ __forceinline__ void solve_dd_strided(R* A, int st, R (&B)[M][D]) {
   }
 }
 
-// ------------------------------------------------------------------------
-// Equilibrium populations of a macroscopic state (Sec. 4.1, Eqs.
-// faEqGeneral, fEqGeneral, gEqGeneral), used by the boundary procedures.
-template <int D, int M, typename R = double> struct EqSet {
-  R rho, T, th, U;
-  R Y[M], th_a[M], u[D];
-  R us[M][D];   // species velocities, used when own_species_u
-  bool own_species_u;
-  double T_full;  // T of a solved state to the solve's precision (float-float in FP32)
-};
-
-// Population l (0..M-2 species, M-1 momentum, M energy) in direction i.
-template <int D, int M, typename R>
-__device__ R eq_pop(const EqSet<D, M, R>& s, int l, int i) {
-  int c[3] = {cvel(i, 0), cvel(i, 1), D == 3 ? cvel(i, 2) : 0};
-  if (l < M - 1) {
-    R p = s.rho * s.Y[l];
-    for (int d = 0; d < D; ++d) {
-      const R ud = s.own_species_u ? s.us[l][d] : s.u[d];
-      p *= psi1<R>(c[d], ud, s.th_a[l] + ud * ud);
-    }
-    return p;
-  }
-  if (l == M - 1) {
-    R p = s.rho;
-    for (int d = 0; d < D; ++d) p *= psi1<R>(c[d], s.u[d], s.th + s.u[d] * s.u[d]);
-    return p;
-  }
-  R A[3], B[3], prodA = R(1);
-  for (int d = 0; d < D; ++d) {
-    const R ua = s.u[d];
-    const R O1 = s.th * ua + R(0.5) * ua * ua * ua;
-    const R O2 = s.th * s.th + R(2.5) * s.th * ua * ua + R(0.5) * ua * ua * ua * ua;
-    A[d] = psi1<R>(c[d], ua, s.th + ua * ua);
-    B[d] = c[d] == 0 ? R(0.5) * ua * ua - O2 : R(0.5) * (O2 + R(c[d]) * O1);
-    prodA *= A[d];
-  }
-  R sumB = R(0);
-  for (int d = 0; d < D; ++d) {
-    R t = B[d];
-    for (int e = 0; e < D; ++e)
-      if (e != d) t *= A[e];
-    sumB += t;
-  }
-  return s.rho * (s.U * prodA + sumB);
-}
-
 }  // namespace lbm

@@ -1,9 +1,11 @@
 // Kernels of the reactive-mixture LBM step (templates; instantiated per
 // lattice, species count and precision by lbm_inst.cu).
 //
-//   k_boundary  one warp per interface node: gather, bounce-back / TMS /
-//               inlet / LODI outlet reconstruction, the node's moment record.
-//   k_chem      the interface nodes' reaction sub-steps (lane groups).
+//   k_bnode     one thread per interface node: gather, bounce-back / TMS /
+//               inlet / LODI outlet reconstruction, the node's moment record
+//               (lbm_bnode.cuh).
+//   k_iface_chem, k_chem  the interface nodes' reaction sub-steps (a thread
+//               or a lane group per node).
 //   k_moments   one thread per bulk node: pull-stream all lattices, moments,
 //               temperature Newton, the reaction sub-steps, the moment
 //               record (scratch) and the T guess.
@@ -13,6 +15,8 @@
 //               pull gather, store to the other buffer (fused collision).
 //   k_prep, k_coll  the same collision split into a per-node parameter
 //               kernel and a nine-threads-per-node direction kernel.
+//   k_*_batch   the same bodies over the tiles of several handles.
+//   k_step_persist  a whole batched step as one launch over a work-list.
 //   k_init      populations at the equilibria of given fields.
 //   k_out       fields of the stored state (SI units).
 //   k_diag      per-node heat release and flame diagnostics.
@@ -21,7 +25,7 @@
 // of the lattice arithmetic: moments, equilibria, collision).  FP64 storage
 // computes everything in FP64.  FP32 and FP16 storage compute the lattice
 // arithmetic and transport in FP32 and the temperature Newton solve and the
-// chemistry in float-float (ff.cuh).
+// chemistry in float-float (ff.cuh) or, with LBM_CHEM64, in FP64.
 #include <atomic>
 #include <climits>
 #include <cmath>
@@ -1517,435 +1521,14 @@ __device__ __forceinline__ void coll_block(const S* __restrict__ src, S* __restr
 }
 
 
-// ---------------------------------------------------------------------------
-// Boundary reconstruction at interface nodes (Sec. 4).  One warp per
-// interface node: lanes stride over the node's L*Q populations, moment sums
-// are reduced with warp shuffles, and the per-node scalars (local state,
-// Newton temperature, LODI data) are evaluated redundantly by every lane.
-// Writes the node's full post-boundary population set to bc.pops, which the
-// moments and collision kernels read for that node.
-//   bounce-back (Eq. bb): incoming f_i = f_{-i}^post of the node itself;
-//   TMS wall (Sec. 4.2.2), flux inlet (Sec. 4.3), outlet (Sec. 4.4): put
-//   the first equilibrium A on the incoming links, take the local state
-//   `loc` of the result, then every population becomes B + f - f^loc with
-//   B = A (wall: target; outlet: outlet data) or, for the inlet, the
-//   target equilibrium at (rho^loc, Y^loc, u^in, T^in).
-
-template <typename R>
-__device__ __forceinline__ R warp_sum(R v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
-
-// Sum over the species lanes 0..M-1 of a warp (the other lanes hold zero):
-// a butterfly over the lanes that can hold species, then lane 0's total to
-// every lane, so that every lane continues with the same value.
-template <int M, typename T>
-__device__ __forceinline__ T species_sum(T v) {
-#pragma unroll
-  for (int o = 1; o < (M > 16 ? 32 : 16); o <<= 1) v += shfl_xor_ct(0xffffffffu, v, o);
-  return shfl_ct(0xffffffffu, v, 0);
-}
-
-// theta_a, theta and U/c^2 of an equilibrium state by a warp: lane a < M
-// evaluates species a's energy (float-float in the mixed path: the mixture
-// energy is a sum of formation-energy-sized terms), the warp sums.  m: the
-// mechanism for compile-time species indices; mp: the same at an address
-// the lanes may index by species.
-template <int D, int M, typename R>
-__device__ __forceinline__ void eq_prepare_warp(EqSet<D, M, R>& s, const DevMech& m,
-                                                const DevMech& mp, const Units& un, int lane) {
-  const bool own = lane < M;
-  const int a = own ? lane : 0;
-  if constexpr (!kFF<R>) {
-    double Rm = 0.0;
-#pragma unroll
-    for (int b = 0; b < M; ++b) {
-      Rm += s.Y[b] * m.inv_mm[b];
-      s.th_a[b] = m.Ra[b] * s.T * un.inv_c2;
-    }
-    const double U = species_sum<M>(own ? s.Y[a] * species_U(mp, a, s.T) : 0.0);
-    s.th = R_U * Rm * s.T * un.inv_c2;
-    s.U = U * un.inv_c2;
-  } else {
-    float Rm = 0.f;
-    const ff T(s.T);
-#pragma unroll
-    for (int b = 0; b < M; ++b) {
-      Rm += s.Y[b] * m.inv_mm_s[b];
-      s.th_a[b] = m.Ra_s[b] * s.T * un.inv_c2_s;
-    }
-    const ff U = species_sum<M>(own ? ff(s.Y[a]) * species_U_ff(mp, a, T) : ff());
-    s.th = float(R_U) * Rm * s.T * un.inv_c2_s;
-    s.U = (U * un.inv_c2_f).hi;
-  }
-}
-
-// Warp-cooperative macroscopic state of a node: lane i < Q holds v[l], the
-// population of lattice l in direction i (lanes >= Q hold zeros).  rho, u,
-// Y, u_a (Eq. momentum1 with reading R5), T by Newton on Eq. temperature from
-// T_guess; every lane returns the same state.  R = float (mixed path): sums
-// in FP32, the Newton solve in float-float as in the moments kernel.  Not
-// inlined: the boundary kernel calls it up to three times, and one shared
-// copy keeps its instruction footprint small.
-template <int D, int M, typename R>
-__device__ __noinline__ void warp_state_of(const R (&v)[M + 1], EqSet<D, M, R>& s,
-                                           double T_guess, const DevMech& m,
-                                           const DevMech& mp, const Units& un, int* status,
-                                           int lane) {
-  constexpr int Q = Lat<D>::Q;
-  const bool act = lane < Q;
-  const int i = act ? lane : 0;
-  R c[D];
-#pragma unroll
-  for (int d = 0; d < D; ++d) c[d] = act ? R(cvel(i, d)) : R(0);
-  R rho, rhoE, j[D], rs[M], js[M][D];
-#pragma unroll
-  for (int l = 0; l < M - 1; ++l) {
-    rs[l] = v[l];
-#pragma unroll
-    for (int d = 0; d < D; ++d) js[l][d] = c[d] * v[l];
-  }
-  rho = v[M - 1];
-#pragma unroll
-  for (int d = 0; d < D; ++d) j[d] = c[d] * v[M - 1];
-  rhoE = v[M];
-  rho = warp_sum(rho);
-  rhoE = warp_sum(rhoE);
-#pragma unroll
-  for (int d = 0; d < D; ++d) j[d] = warp_sum(j[d]);
-#pragma unroll
-  for (int a = 0; a < M - 1; ++a) {
-    rs[a] = warp_sum(rs[a]);
-#pragma unroll
-    for (int d = 0; d < D; ++d) js[a][d] = warp_sum(js[a][d]);
-  }
-  rs[M - 1] = rho;
-#pragma unroll
-  for (int d = 0; d < D; ++d) js[M - 1][d] = j[d];
-#pragma unroll
-  for (int a = 0; a < M - 1; ++a) {
-    rs[M - 1] -= rs[a];
-#pragma unroll
-    for (int d = 0; d < D; ++d) js[M - 1][d] -= js[a][d];
-  }
-  s.rho = rho;
-  R usq = R(0);
-#pragma unroll
-  for (int d = 0; d < D; ++d) { s.u[d] = j[d] / rho; usq += s.u[d] * s.u[d]; }
-  // species a = lane: Y_a and u_a (reading R5), then shared by shuffles
-  const bool own = lane < M;
-  const int a = own ? lane : 0;
-  R ra = rs[0], ja[D];
-#pragma unroll
-  for (int d = 0; d < D; ++d) ja[d] = js[0][d];
-#pragma unroll
-  for (int b = 1; b < M; ++b)
-    if (b == a) {
-      ra = rs[b];
-#pragma unroll
-      for (int d = 0; d < D; ++d) ja[d] = js[b][d];
-    }
-  const R Ya = own ? ra / rho : R(0);
-  const bool tiny = species_velocity_undefined<D, R>(ra, ja);
-  R usa[D];
-#pragma unroll
-  for (int d = 0; d < D; ++d) usa[d] = tiny ? s.u[d] : ja[d] / ra;
-#pragma unroll
-  for (int b = 0; b < M; ++b) {
-    s.Y[b] = __shfl_sync(0xffffffffu, Ya, b);
-#pragma unroll
-    for (int d = 0; d < D; ++d) s.us[b][d] = __shfl_sync(0xffffffffu, usa[d], b);
-  }
-  // temperature: the mixture energy polynomial's coefficients summed over
-  // the species lanes, then the Newton iterates of newton_T / newton_T_ff
-  // (same formulas and stopping rule) on every lane
-  bool ok = false;
-  if constexpr (!kFF<R>) {
-    using X = Chem<double>;
-    const double U = (rhoE / rho - 0.5 * usq) * un.c * un.c;
-    double c[4];
-#pragma unroll
-    for (int k = 0; k < 4; ++k) c[k] = species_sum<M>(own ? Ya * X::ucoef(mp, k, a) : 0.0);
-    double T = T_guess;
-    for (int it = 0; it < un.newton_max_iter; ++it) {
-      const double F = c[0] + T * (c[1] + T * (c[2] + T * c[3])) - U;
-      const double dF = c[1] + T * (2.0 * c[2] + 3.0 * T * c[3]);
-      const double dT = -F / dF;
-      T += dT;
-      if (fabs(dT) <= un.newton_rtol * fabs(T)) { ok = true; break; }
-    }
-    s.T = T;
-    s.T_full = T;
-  } else {
-    using X = Chem<ff>;
-    const ff U = (ff(rhoE / rho) + ff(-0.5f * usq)) * un.c2_f;
-    ff c[4];
-#pragma unroll
-    for (int k = 0; k < 4; ++k) c[k] = species_sum<M>(own ? ff(Ya) * X::ucoef(mp, k, a) : ff());
-    const ff two(2.f), three(3.f);
-    ff T = ff_from_double(T_guess);
-    for (int it = 0; it < un.newton_max_iter; ++it) {
-      const ff F = c[0] + T * (c[1] + T * (c[2] + T * c[3])) - U;
-      const ff dF = c[1] + T * (two * c[2] + three * T * c[3]);
-      const ff dT = -(F / dF);
-      T += dT;
-      if (fabsf(dT.hi) <= un.newton_rtol_f * fabsf(T.hi)) { ok = true; break; }
-    }
-    s.T = T.hi;
-    s.T_full = ff_to_double(T);
-  }
-  if (!ok && lane == 0) atomicOr(status, ST_NEWTON);
-}
-
-// Boundary reconstruction of interface node k by one warp (Sec. 4).  R is
-// the lattice type of the path (FP64, or FP32 for FP32 storage); the
-// reconstructed populations are kept in FP64 scratch.
-template <int D, int M, typename S, typename R>
-__device__ __forceinline__ void boundary_body(const S* __restrict__ src, const BCDev& bc,
-                                              const double* Tf,
-                                              int* __restrict__ status, const Geom& g,
-                                              const Units& un, const DevMech& mech,
-                                              const DevMech& mp, int k, int lane) {
-  constexpr int Q = Lat<D>::Q, L = M + 1;
-  if (k >= bc.n_if) return;                                         // whole warp leaves
-  const long long N = g.N;
-  const long long n = bc.if_node[k];
-  const int info = bc.if_info[k];
-  const int kind = info & 15;
-  const unsigned inc = bc.if_inc[k];
-  const int x = (int)(n % g.nx);
-  const int y = (int)((n / g.nx) % g.ny);
-  const int z = (int)(n / ((long long)g.nx * g.ny));
-  const long long st = bc.n_if;
-  const float4* codec = g.codec;
-  // population (l, i) of node m, decoded
-  auto ld = [&](int l, int i, long long m) {
-    return Codec<S>::template dec<R>(__ldg(src + (long long)(l * Q + i) * N + m), codec,
-                                     l * Q + i);
-  };
-  double* P = bc.pops + k;                       // element (l, i) at P[(l Q + i) st]
-  // lane i < Q works on direction i, every lattice l (unrolled)
-  const bool act = lane < Q;
-  const int i = act ? lane : 0;
-  const bool in_i = act && (inc >> i & 1u);      // an incoming (unknown) link
-  if (act) {                                     // pull streaming (wrapped address)
-    const long long sn = node_shift<D>(x, y, z, i, -1, g);
-    const bool bb = in_i && kind == BK_BB;
-#pragma unroll
-    for (int l = 0; l < L; ++l)
-      P[(long long)(l * Q + i) * st] = bb ? double(ld(l, Q - 1 - i, n)) : double(ld(l, i, sn));
-  }
-  if (kind == BK_BB) return;
-  __syncwarp();
-  EqSet<D, M, R> A, B, loc;
-  A.own_species_u = B.own_species_u = false;
-  if (kind == BK_TMS) {
-    // step 1: bounce-back density and mass fractions (Eqs. BBrho, BBY)
-    R rho_bb, rs[M];
-#pragma unroll
-    for (int l = 0; l < M; ++l) {
-      const R v = !act ? R(0) : (in_i ? ld(l, Q - 1 - i, n) : R(P[(long long)(l * Q + i) * st]));
-      if (l < M - 1) rs[l] = v; else rho_bb = v;
-    }
-    rho_bb = warp_sum(rho_bb);
-#pragma unroll
-    for (int a = 0; a < M - 1; ++a) rs[a] = warp_sum(rs[a]);
-    A.rho = rho_bb;
-    R ysum = R(0);
-    for (int a = 0; a < M - 1; ++a) { A.Y[a] = rs[a] / rho_bb; ysum += A.Y[a]; }
-    A.Y[M - 1] = R(1) - ysum;
-    for (int d = 0; d < D; ++d) A.u[d] = R(0);     // u^tgt = u_a^tgt = 0
-    A.T = R(bc.if_wallT[k]);
-    eq_prepare_warp(A, mech, mp, un, lane);  // step 2: target (Eqs. tgtf-tgtfa)
-  } else if (kind == BK_INLET) {
-    A.rho = R(bc.rho_in);
-    for (int a = 0; a < M; ++a) A.Y[a] = R(bc.Y_in[a]);
-    for (int d = 0; d < D; ++d) A.u[d] = R(bc.if_uin[(long long)d * st + k]);
-    A.T = R(bc.T_in);
-    eq_prepare_warp(A, mech, mp, un, lane);  // step 1 (Eqs. in_f-in_fa)
-  } else {
-    // LODI data from the stored state at x and x - n (Eq. convectiveBC)
-    const int ax = (info >> 4) & 3;
-    const int sg = (info >> 6) & 1 ? 1 : -1;
-    const long long stride = ax == 0 ? 1 : (ax == 1 ? (long long)g.nx : (long long)g.nx * g.ny);
-    const long long up = n - sg * stride;
-    EqSet<D, M, R> s0, s1;
-    R v[L];
-#pragma unroll
-    for (int l = 0; l < L; ++l) v[l] = act ? ld(l, i, n) : R(0);
-    warp_state_of<D, M, R>(v, s0, Tf[n], mech, mp, un, status, lane);
-    // (the upstream node's Newton starts from this node's T guess: the bulk
-    // moments kernel may be rewriting the upstream one concurrently)
-#pragma unroll
-    for (int l = 0; l < L; ++l) v[l] = act ? ld(l, i, up) : R(0);
-    warp_state_of<D, M, R>(v, s1, Tf[n], mech, mp, un, status, lane);
-    // LODI wave amplitudes (reading R13) in FP64 from the two states: a few
-    // scalars per node
-    double R0 = 0.0, R1 = 0.0, Cv = 0.0;
-    const double T0 = s0.T, T1 = s1.T;
-    for (int a = 0; a < M; ++a) {
-      R0 += double(s0.Y[a]) * mech.inv_mm[a];
-      R1 += double(s1.Y[a]) * mech.inv_mm[a];
-      Cv += double(s0.Y[a]) * (mech.u1[a] + T0 * (2.0 * mech.u2[a] + 3.0 * T0 * mech.u3[a]));
-    }
-    R0 *= R_U;
-    R1 *= R_U;
-    const double r0 = s0.rho, r1 = s1.rho;
-    const double p0 = r0 * R0 * T0 * un.inv_c2;
-    const double p1 = r1 * R1 * T1 * un.inv_c2;
-    const double un0 = sg * double(s0.u[ax]), un1 = sg * double(s1.u[ax]);
-    const double gamma = (Cv + R0) / Cv;
-    const double cs = sqrt(gamma * R0 * T0 * un.inv_c2);
-    const double Ma = un0 / cs;
-    const double Ln = bc.outlet_L > 0.0 ? bc.outlet_L : (ax == 0 ? g.nx : (ax == 1 ? g.ny : g.nz));
-    const double K = bc.sigma * (1.0 - Ma * Ma) * cs / Ln;
-    const double L1 = K * (p0 - bc.p_out_lat);
-    const double L2 = un0 * (cs * cs * (r0 - r1) - (p0 - p1));
-    const double L5 = (un0 + cs) * ((p0 - p1) + r0 * cs * (un0 - un1));
-    const double rho_o = r0 - (L2 + 0.5 * (L5 + L1)) / (cs * cs);
-    A.rho = R(rho_o);
-    const double p_o = p0 - 0.5 * (L5 + L1);
-    const double un_o = un0 - (L5 - L1) / (2.0 * r0 * cs);
-    for (int d = 0; d < D; ++d) A.u[d] = R(double(s0.u[d]) - un0 * double(s0.u[d] - s1.u[d]));
-    A.u[ax] = R(sg * un_o);
-    double Ro = 0.0;
-    for (int a = 0; a < M; ++a) {
-      const double Ya = double(s0.Y[a]) - un0 * double(s0.Y[a] - s1.Y[a]);
-      A.Y[a] = R(Ya);
-      Ro += Ya * mech.inv_mm[a];
-    }
-    A.T = R(p_o * un.c * un.c / (rho_o * R_U * Ro));
-    eq_prepare_warp(A, mech, mp, un, lane);  // step 1 (Eqs. out_f-out_fa)
-  }
-  // incoming links at A, then the local state (Eqs. locRho-locT and analogues)
-  if (in_i) {
-#pragma unroll 1
-    for (int l = 0; l < L; ++l) P[(long long)(l * Q + i) * st] = double(eq_pop(A, l, i));
-  }
-  __syncwarp();
-  {
-    R v[L];
-#pragma unroll
-    for (int l = 0; l < L; ++l) v[l] = act ? R(P[(long long)(l * Q + i) * st]) : R(0);
-    warp_state_of<D, M, R>(v, loc, Tf[n], mech, mp, un, status, lane);
-  }
-  loc.own_species_u = kind == BK_TMS;             // TMS local species use u_a^loc
-  eq_prepare_warp(loc, mech, mp, un, lane);
-  if (kind == BK_INLET && bc.inlet_simplified) {  // simplified inlet: the local equilibria
-    __syncwarp();
-    if (act) {
-#pragma unroll 1
-      for (int l = 0; l < L; ++l) P[(long long)(l * Q + i) * st] = double(eq_pop(loc, l, i));
-    }
-    return;
-  }
-  if (kind == BK_INLET) {                         // target (Eqs. in_tgt_*)
-    B.rho = loc.rho;
-    for (int a = 0; a < M; ++a) B.Y[a] = loc.Y[a];
-    for (int d = 0; d < D; ++d) B.u[d] = A.u[d];
-    B.T = R(bc.T_in);
-    eq_prepare_warp(B, mech, mp, un, lane);
-  }
-  const EqSet<D, M, R>& Bref = kind == BK_INLET ? B : A;
-  __syncwarp();
-  if (act) {
-#pragma unroll 1
-    for (int l = 0; l < L; ++l) {
-      double& p = P[(long long)(l * Q + i) * st];
-      p = double(eq_pop(Bref, l, i) + R(p) - eq_pop(loc, l, i));
-    }
-  }
-}
-
-// The record of interface node k from its reconstructed populations, by the
-// warp that reconstructed them: lane i sums direction i, the sums are reduced
-// across the warp, and lane 0 completes the record as the moments kernel
-// does (moments_finish; the reaction sub-steps are left to k_chem).  Takes
-// the interface nodes' moments off the side stream's critical path.
-template <int D, int M, typename R>
-__device__ __forceinline__ void boundary_record(const BCDev& bc, R* __restrict__ rec,
-                                                double* __restrict__ Tf,
-                                                int* __restrict__ status, const Geom& g,
-                                                const Units& un, const DevMech& mech,
-                                                const DevMech& mp, int k, int lane) {
-  constexpr int Q = Lat<D>::Q, NP = Lat<D>::NP, L = M + 1;
-  using RC = Rec<D, M>;
-  if (k >= bc.n_if) return;                                         // whole warp leaves
-  __syncwarp();
-  const long long N = g.N;
-  const long long n = bc.if_node[k];
-  const double* P = bc.pops + k;
-  const long long st = bc.n_if;
-  const bool act = lane < Q;
-  const int i = act ? lane : 0;
-  // rho, u, Y, u_a and T (Newton from the node's previous T) by the shared
-  // warp routine; the energy flux and the momentum flux tensor beside it
-  R v[L];
-#pragma unroll
-  for (int l = 0; l < L; ++l) v[l] = act ? R(P[(long long)(l * Q + i) * st]) : R(0);
-  EqSet<D, M, R> s;
-  s.own_species_u = false;
-  warp_state_of<D, M, R>(v, s, Tf[n], mech, mp, un, status, lane);
-  R c[D];
-#pragma unroll
-  for (int d = 0; d < D; ++d) c[d] = act ? R(cvel(i, d)) : R(0);
-  R rhoE = v[M], q[D], Pt[NP];
-#pragma unroll
-  for (int d = 0; d < D; ++d) {
-    q[d] = warp_sum(c[d] * v[M]);
-#pragma unroll
-    for (int e = d; e < D; ++e) Pt[pidx<D>(d, e)] = warp_sum(c[d] * c[e] * v[M - 1]);
-  }
-  rhoE = warp_sum(rhoE);
-  if (lane != 0) return;
-  // the record as the moments kernel writes it (moments_finish), the
-  // reaction sub-steps left to k_chem
-  const R rho = s.rho;
-  if (!(rho > R(0)) || !isfinite(double(rho)) || !isfinite(s.T_full))
-    atomicOr(status, ST_NONFINITE);
-  Tf[n] = s.T_full;
-  R thR;
-  if constexpr (sizeof(R) == 4) {
-    float Rm = 0.f;
-#pragma unroll
-    for (int a = 0; a < M; ++a) Rm += s.Y[a] * mech.inv_mm_s[a];
-    thR = Rm * float(R_U) * s.T * un.inv_c2_s;
-  } else {
-    double Rmix = 0.0;
-#pragma unroll
-    for (int a = 0; a < M; ++a) Rmix += s.Y[a] * mech.inv_mm[a];
-    thR = R(Rmix * R_U * s.T * un.inv_c2);
-  }
-#pragma unroll
-  for (int a = 0; a < M - 1; ++a) rec[(RC::DRHO + a) * N + n] = s.Y[a] * rho;
-  rec[RC::RHO * N + n] = rho;
-#pragma unroll
-  for (int d = 0; d < D; ++d) {
-    rec[(RC::U + d) * N + n] = s.u[d];
-    rec[(RC::QF + d) * N + n] = q[d];
-    rec[(RC::PHI + d) * N + n] = rho * s.u[d] * (R(1) - R(3) * thR) - rho * s.u[d] * s.u[d] * s.u[d];
-  }
-#pragma unroll
-  for (int p = 0; p < NP; ++p) rec[(RC::P + p) * N + n] = Pt[p];
-  rec[RC::E * N + n] = rhoE * (R(1) / rho);
-#pragma unroll
-  for (int a = 0; a < M; ++a) {
-    rec[(RC::Y + a) * N + n] = s.Y[a];
-#pragma unroll
-    for (int d = 0; d < D; ++d) rec[(RC::US + a * D + d) * N + n] = s.us[a][d];
-  }
-}
-
 #include "lbm_bnode.cuh"
 
 // ---------------------------------------------------------------------------
 // Single-domain kernels: one thread per node (moments, collision), one thread
-// (k_bnode) or one warp (k_boundary) per interface node (boundary).
-// node sets of the moments kernel: every node, the nodes without boundary
-// reconstruction, or the interface nodes (after the boundary kernel, which a
-// side stream runs concurrently with the bulk)
+// per interface node (k_bnode: boundary reconstruction and record).
+// Node sets: every node, the nodes without boundary reconstruction (the
+// bulk), or the interface nodes (whose sub-steps follow k_bnode, on a side
+// stream concurrent with the bulk).
 enum { NODES_ALL = 0, NODES_BULK = 1, NODES_INTERFACE = 2 };
 
 template <int D, int M, typename S, typename RT>
@@ -1954,14 +1537,9 @@ k_moments(const S* __restrict__ src, RT* __restrict__ rec, double* __restrict__ 
           int* __restrict__ status, const __grid_constant__ Geom g,
           const __grid_constant__ Units un, const __grid_constant__ BCDev bc,
           const __grid_constant__ DevMech mech, int chem_inline, int node_set) {
-  const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  long long n = idx;
-  if (node_set == NODES_INTERFACE) {
-    if (idx >= bc.n_if) return;
-    n = bc.if_node[idx];
-  } else if (node_set == NODES_BULK && bc.tag && n < g.N && bc.tag[n] >= 0) {
-    return;
-  }
+  // node_set: NODES_ALL or NODES_BULK
+  const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (node_set == NODES_BULK && bc.tag && n < g.N && bc.tag[n] >= 0) return;
   moments_body<D, M, S, RT>(src, rec, Tf, status, g, un, bc, mech, n, chem_inline);
 }
 
@@ -2046,24 +1624,6 @@ k_coll(const S* __restrict__ src, S* __restrict__ dst, const RT* __restrict__ cp
   extern __shared__ __align__(16) unsigned char coll_raw[];
   coll_block<D, M, S, RT>(src, dst, cp, g, bc, mech, blockIdx.x * (long long)kCollNodes,
                           reinterpret_cast<RT*>(coll_raw));
-}
-
-// rec != nullptr: the warp also writes its interface node's record
-// (reaction sub-steps in k_chem); else the moments kernel does.
-template <int D, int M, typename S>
-__global__ void __launch_bounds__(128)
-k_boundary(const S* __restrict__ src, const __grid_constant__ BCDev bc,
-           double* __restrict__ Tf, int* __restrict__ status,
-           const __grid_constant__ Geom g, const __grid_constant__ Units un,
-           const __grid_constant__ DevMech mech, typename ComputeType<S>::type* rec,
-           const DevMech* __restrict__ mech_g) {
-  using R = typename ComputeType<S>::type;
-  const int k = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32, lane = threadIdx.x & 31;
-  // species-indexed reads by lane from the global copy where there is one
-  boundary_body<D, M, S, R>(src, bc, Tf, status, g, un, mech, mech_g ? *mech_g : mech, k, lane);
-  if (rec)
-    boundary_record<D, M, R>(bc, rec, Tf, status, g, un, mech, mech_g ? *mech_g : mech, k,
-                             lane);
 }
 
 // One thread per interface node: reconstruction and record (lbm_bnode.cuh);
@@ -2698,28 +2258,20 @@ static cudaError_t step_impl(const DevMech& mech, const StepArgs& a, cudaStream_
         k_mchem<D, M, S, RT, 8><<<nbm, 128, 0, st>>>(src, rec, a.Tfield, a.status, a.g, a.un,
                                                      a.bc, mech, a.mech_dev, node_set);
     };
-    // the boundary kernel (a few warps, latency-bound) and what follows it
-    // for the interface nodes run on a side stream beside the bulk work
+    // the boundary kernel and the interface nodes' sub-steps run on a side
+    // stream beside the bulk moments.  Interface nodes need the handle's
+    // device copy of the mechanism (every handle has one; the
+    // allocation-free step accepts no interface nodes).
+    if (a.bc.n_if > 0 && !a.mech_dev) return cudaErrorInvalidValue;
     const bool fork = a.bc.n_if > 0 && a.side && a.ev_fork && a.ev_join;
-    const bool if_rec = a.mech_dev != nullptr;     // interface records by the boundary warps
     if (fork) {
       cudaError_t e = cudaEventRecord(a.ev_fork, s);
       if (e == cudaSuccess) e = cudaStreamWaitEvent(a.side, a.ev_fork, 0);
       if (e != cudaSuccess) return e;
-      // the interface nodes: records by the boundary warps, sub-steps with
-      // eight lanes per node (k_chem), whatever the bulk placement
-      if (if_rec)
-        k_bnode<D, M, S><<<blocks_for(a.bc.n_if, kBnd), kBnd, bnode_smem<D, M, RT>(), a.side>>>(
-            src, a.bc, a.Tfield, a.status, a.g, a.un, mech, rec);
-      else
-        k_boundary<D, M, S><<<(a.bc.n_if + 3) / 4, 128, 0, a.side>>>(
-            src, a.bc, a.Tfield, a.status, a.g, a.un, mech, nullptr, a.mech_dev);
-      if (!if_rec)
-        k_moments<D, M, S, RT><<<blocks_for(a.bc.n_if, bs), bs, 0, a.side>>>(
-            src, rec, a.Tfield, a.status, a.g, a.un, a.bc, mech, 1, NODES_INTERFACE);
-      else
-        launch_chem<D, M, RT>(lc, a.side, rec, a.Tfield, a.status, a.g.N, a.bc, a.un,
-                              a.mech_dev, NODES_INTERFACE);
+      k_bnode<D, M, S><<<blocks_for(a.bc.n_if, kBnd), kBnd, bnode_smem<D, M, RT>(), a.side>>>(
+          src, a.bc, a.Tfield, a.status, a.g, a.un, mech, rec);
+      launch_chem<D, M, RT>(lc, a.side, rec, a.Tfield, a.status, a.g.N, a.bc, a.un,
+                            a.mech_dev, NODES_INTERFACE);
       e = cudaEventRecord(a.ev_join, a.side);
       if (e != cudaSuccess) return e;
       if (chem_sep)
@@ -2730,19 +2282,16 @@ static cudaError_t step_impl(const DevMech& mech, const StepArgs& a, cudaStream_
       e = cudaStreamWaitEvent(s, a.ev_join, 0);
       if (e != cudaSuccess) return e;
     } else {
-      const bool bnd_rec = a.bc.n_if > 0 && if_rec;
-      if (bnd_rec)
+      const bool bnd = a.bc.n_if > 0;
+      if (bnd)
         k_bnode<D, M, S><<<blocks_for(a.bc.n_if, kBnd), kBnd, bnode_smem<D, M, RT>(), s>>>(
             src, a.bc, a.Tfield, a.status, a.g, a.un, mech, rec);
-      else if (a.bc.n_if > 0)
-        k_boundary<D, M, S><<<(a.bc.n_if + 3) / 4, 128, 0, s>>>(
-            src, a.bc, a.Tfield, a.status, a.g, a.un, mech, nullptr, a.mech_dev);
       if (chem_sep)
-        mchem(s, bnd_rec ? NODES_BULK : NODES_ALL);
+        mchem(s, bnd ? NODES_BULK : NODES_ALL);
       else
         k_moments<D, M, S, RT><<<nb, bs, 0, s>>>(src, rec, a.Tfield, a.status, a.g, a.un, a.bc,
-                                                 mech, 1, bnd_rec ? NODES_BULK : NODES_ALL);
-      if (bnd_rec)
+                                                 mech, 1, bnd ? NODES_BULK : NODES_ALL);
+      if (bnd)
         launch_chem<D, M, RT>(lc, s, rec, a.Tfield, a.status, a.g.N, a.bc, a.un, a.mech_dev,
                               NODES_INTERFACE);
     }
