@@ -265,7 +265,10 @@ lbm_status lbm_batch_destroy(lbm_batch_t b);
  *                  temperature solve and the node's reactions (for grids too
  *                  small to fill the GPU at one thread per node); -1 = by
  *                  grid size.  Interface nodes (boundary reconstruction) take
- *                  their sub-steps with eight lanes each in every placement.
+ *                  their sub-steps, in every placement, with one thread each
+ *                  when a grid has at least 19,456 of them and with eight
+ *                  lanes each otherwise (the single launch of a plan: one
+ *                  thread each).
  *   collide_split  0 = one thread per node does the whole collision; 1 = a
  *                  per-node kernel stores the collision parameters and a
  *                  second kernel updates the directions with nine threads

@@ -584,7 +584,7 @@ __device__ __forceinline__ void bnode_body(const S* __restrict__ src, const BCDe
 
   // the record from the reconstructed populations (the fields the moments
   // kernel records: state with Newton from the node's previous T, energy
-  // flux, momentum flux tensor); the reaction sub-steps are left to k_chem
+  // flux, momentum flux tensor); the reaction sub-steps follow in their own kernel
   BState<D, M, R> s;
   s.Y = A.Y;                                    // the target columns are free now
   s.us = col + 3 * M * kBnd;

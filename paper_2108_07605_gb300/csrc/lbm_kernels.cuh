@@ -216,8 +216,8 @@ __device__ __forceinline__ void node_substeps(const RT (&rs)[M], RT rho, RT ER, 
 // The node's record from its population sums (Sec. 2.1, Sec. 3.1-3.2, Sec.
 // 3.7 slaving): fields, temperature by Newton from the node's previous T,
 // and the reaction sub-steps when chem_inline (else the species densities go
-// to the increment slots for k_chem).  Shared by the moments kernel (one
-// thread per node) and the boundary kernel (interface nodes, one warp each).
+// to the increment slots for a separate sub-step kernel).  Used by the
+// moments kernels (one thread per node).
 template <int D, int M, typename RT, bool kDynChem = false>
 __device__ __forceinline__ void moments_finish(RT* __restrict__ rec, double* __restrict__ Tf,
                                                int* __restrict__ status, long long N,
