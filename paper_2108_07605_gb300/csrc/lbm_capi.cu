@@ -122,6 +122,7 @@ void fill_domains(lbm_ctx* const* hs, int n, const Launch& lc, std::vector<Domai
     gr.nblocks += (int)((h->g.N + 127) / 128);
     gr.nbblocks += (h->bc.n_if + kIfChemNodesPerBlock - 1) / kIfChemNodesPerBlock;
     gr.ntblocks += (h->bc.n_if + kBndNodesPerBlock - 1) / kBndNodesPerBlock;
+    gr.n_if_total += h->bc.n_if;
     if (lc.chem_lanes > 1) {
       const int per = 128 / lc.chem_lanes;
       gr.ncblocks += (int)((h->g.N + per - 1) / per);

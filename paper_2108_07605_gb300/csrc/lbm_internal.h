@@ -214,6 +214,7 @@ struct BatchGrids {
   int ntblocks = 0;   // k_bnode, kBndNodesPerBlock interface nodes per block
   int ncblocks = 0;   // k_chem, 128 / chem_lanes nodes per block (0 without it)
   int nkblocks = 0;   // k_coll, 32 nodes per block (0 without it)
+  long long n_if_total = 0;   // interface nodes of every domain
   // persistent == 2: the device work-list and its sync words (zeroed before
   // every launch), the domains' interface-node presence
   const PItem* items = nullptr;

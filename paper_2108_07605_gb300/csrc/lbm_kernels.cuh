@@ -1876,6 +1876,23 @@ k_iface_chem(RT* __restrict__ rec, const double* __restrict__ Tf, int* __restric
   iface_substeps<D, M, RT>(rec, Tf, status, N, un, *mech, if_node[k], ic_raw);
 }
 
+// The same over the interface nodes of several handles (batch plans whose
+// handles hold at least kIfChemThreadNodes interface nodes in all), on the
+// thread-per-interface-node grid of k_bnode_batch.
+template <int D, int M, typename RT>
+__global__ void __launch_bounds__(kBnd)
+k_iface_chem_batch(const DomainDev* __restrict__ doms, int ndom, int nblk) {
+  LBM_BLOCK_DOMAIN(bd);
+  extern __shared__ __align__(16) unsigned char icb_raw[];
+  for (int b = blockIdx.x; b < nblk; b += gridDim.x) {
+    const DomainDev& d = bd.get(doms, domain_of_block(doms, ndom, b, GRID_BNODE));
+    const long long k = (b - d.tblock_begin) * (long long)kBnd + threadIdx.x;
+    if (k >= d.bc.n_if) continue;
+    iface_substeps<D, M, RT>(static_cast<RT*>(d.rec), d.Tf, d.status, d.g.N, d.un, *d.mech,
+                             d.bc.if_node[k], icb_raw);
+  }
+}
+
 template <typename RT> constexpr int kPersistMinBlocks = sizeof(RT) == 8 ? 2 : 3;
 constexpr int kPersistCollWarps = kPersistThreads / 32;
 
@@ -2384,6 +2401,13 @@ static cudaError_t batch_impl(const DomainDev* doms, int ndom, const BatchGrids&
   // the reaction sub-steps in k_chem over a node set (the grid of the set)
   static_assert(128 / 8 == kIfChemNodesPerBlock, "interface chemistry: 8 lanes per node");
   auto chem = [&](int node_set, cudaStream_t st) {
+    if (node_set == NODES_INTERFACE && gr.n_if_total >= kIfChemThreadNodes) {
+      // enough interface nodes to fill the GPU with one thread each
+      auto k = k_iface_chem_batch<D, M, RT>;
+      const size_t sm = kFF<RT> ? chem_slice_bytes<M, ff>() : 0;
+      k<<<batch_grid(k, gr.ntblocks, kBnd, sm, ps), kBnd, sm, st>>>(doms, ndom, gr.ntblocks);
+      return;
+    }
     const int nb = node_set == NODES_INTERFACE ? gr.nbblocks : gr.ncblocks;
     if (nb == 0) return;
     // the interface nodes are few and on the critical path: 8 lanes each
