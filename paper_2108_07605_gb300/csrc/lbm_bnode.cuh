@@ -259,7 +259,11 @@ template <int E> struct ForL<E, E> {
 
 // Population sums of a pass, lattice by lattice: fn.template setup<l>()
 // once per lattice, then fn.template get<l>(i, c) for every direction.
-template <int D, int M, typename R, typename F>
+// Directions in rows of three (c_x = -1, 0, 1 at compile time, a row's loads
+// in flight together); a row enters through its sum s and difference
+// d = f_+ - f_- (and f_+ + f_- for P_xx).  kDensOnly: the densities rho_a,
+// rho and rho E only (the bounce-back pass of a wall).
+template <int D, int M, typename R, bool kDensOnly = false, typename F>
 __device__ __forceinline__ void bsums(F& fn, BSums<D, M, R>& z) {
   constexpr int Q = Lat<D>::Q, NP = Lat<D>::NP;
   ForL<0, M + 1>::run([&](auto lc) {
@@ -270,11 +274,7 @@ __device__ __forceinline__ void bsums(F& fn, BSums<D, M, R>& z) {
     for (int d = 0; d < D; ++d) sj[d] = R(0);
 #pragma unroll
     for (int p = 0; p < NP; ++p) sP[p] = R(0);
-    // directions in rows of three (c_x = -1, 0, 1 at compile time), so that
-    // a row's loads are in flight together; in FP32, where the pass waits
-    // on memory rather than on the FP64 pipe, three rows at a time
-    constexpr int kRows = 1;
-#pragma unroll kRows
+#pragma unroll 1
     for (int yz = 0; yz < Q / 3; ++yz) {
       const int cy = yz % 3 - 1, cz = D == 3 ? yz / 3 - 1 : 0;
       R v[3];
@@ -283,18 +283,26 @@ __device__ __forceinline__ void bsums(F& fn, BSums<D, M, R>& z) {
         const int c[3] = {k - 1, cy, cz};
         v[k] = fn.template get<l>(3 * yz + k, c);
       }
-#pragma unroll
-      for (int k = 0; k < 3; ++k) {
-        const int c[3] = {k - 1, cy, cz};
-        sum += v[k];
-#pragma unroll
-        for (int d = 0; d < D; ++d) {
-          if (c[d] == 0) continue;
-          sj[d] += c[d] > 0 ? v[k] : -v[k];
-          if constexpr (l == M - 1) {
-#pragma unroll
-            for (int e = d; e < D; ++e)
-              if (c[e] != 0) sP[pidx<D>(d, e)] += (c[d] == c[e]) ? v[k] : -v[k];
+      const R sx = v[0] + v[2], sr = sx + v[1];
+      sum += sr;
+      if constexpr (!kDensOnly) {
+        const R dx = v[2] - v[0];
+        sj[0] += dx;
+        if (cy != 0) sj[1] += cy > 0 ? sr : -sr;
+        if constexpr (D == 3)
+          if (cz != 0) sj[2] += cz > 0 ? sr : -sr;
+        if constexpr (l == M - 1) {
+          sP[pidx<D>(0, 0)] += sx;
+          if (cy != 0) {
+            sP[pidx<D>(1, 1)] += sr;
+            sP[pidx<D>(0, 1)] += cy > 0 ? dx : -dx;
+          }
+          if constexpr (D == 3) {
+            if (cz != 0) {
+              sP[pidx<D>(2, 2)] += sr;
+              sP[pidx<D>(0, 2)] += cz > 0 ? dx : -dx;
+              if (cy != 0) sP[pidx<D>(1, 2)] += cy == cz ? sr : -sr;
+            }
           }
         }
       }
@@ -461,7 +469,7 @@ __device__ __forceinline__ void bnode_body(const S* __restrict__ src, const BCDe
     if (kind == BK_TMS) {
       // step 1, Eqs. BBrho and BBY: bounce-back density and mass fractions
       Pull pull{src, codec, N, n, sncol, inc, true};
-      bsums<D, M, R>(pull, z);
+      bsums<D, M, R, true>(pull, z);
       A.rho = z.rho;
       const R irho = R(1) / z.rho;
       R ysum = R(0);

@@ -306,11 +306,20 @@ __device__ __forceinline__ void moments_finish(RT* __restrict__ rec, double* __r
   for (int a = 0; a < M; ++a) {
     rec[(RC::Y + a) * N + n] = YR[a];
     // where defined, |j_a| < rho_a, so the quotient lies in (-1, 1) even when
-    // rho_a is denormal in FP32 (its reciprocal would overflow)
+    // rho_a is denormal in FP32 (its reciprocal would overflow: FP32 divides);
+    // in FP64 rho_a > 1e-300 where defined, so one reciprocal serves the D
+    // components
     const bool tiny = species_velocity_undefined<D, RT>(rs[a], js[a]);
+    if constexpr (sizeof(RT) == 8) {
+      const RT ira = tiny ? RT(0) : RT(1) / rs[a];
 #pragma unroll
-    for (int d = 0; d < D; ++d)
-      rec[(RC::US + a * D + d) * N + n] = tiny ? uR[d] : js[a][d] / rs[a];
+      for (int d = 0; d < D; ++d)
+        rec[(RC::US + a * D + d) * N + n] = tiny ? uR[d] : js[a][d] * ira;
+    } else {
+#pragma unroll
+      for (int d = 0; d < D; ++d)
+        rec[(RC::US + a * D + d) * N + n] = tiny ? uR[d] : js[a][d] / rs[a];
+    }
   }
 }
 
