@@ -201,48 +201,40 @@ __device__ __forceinline__ void gtab(const BState<D, M, R>& s, GTab<D, R>& g) {
   }
 }
 
-template <int D, typename R>
-__device__ __forceinline__ R peval(const PTab<D, R>& e, const int (&c)[3]) {
-  R p = e.pref;
-#pragma unroll
-  for (int d = 0; d < D; ++d) p *= sel3(c[d], e.t[d]);
-  return p;
-}
-
-template <int D, typename R>
-__device__ __forceinline__ R geval(const GTab<D, R>& g, const int (&c)[3]) {
-  R A[D], B[D], prodA = R(1);
-#pragma unroll
-  for (int d = 0; d < D; ++d) {
-    A[d] = sel3(c[d], g.A[d]);
-    B[d] = sel3(c[d], g.B[d]);
-    prodA *= A[d];
-  }
-  R sumB = R(0);
-#pragma unroll
-  for (int d = 0; d < D; ++d) {
-    R t = B[d];
-#pragma unroll
-    for (int e = 0; e < D; ++e)
-      if (e != d) t *= A[e];
-    sumB += t;
-  }
-  return g.rho * (g.U * prodA + sumB);
-}
-
-// Tables of one state for the lattice of the current pass.
+// Tables of one state for the lattice of the current pass.  row<l>(c_y,
+// c_z) forms the part shared by a row of three directions (the population's
+// pref t_y t_z; for g, A_y A_z and U A_y A_z + B_y A_z + A_y B_z, since
+// g^eq = rho [A_x (U A_y A_z + B_y A_z + A_y B_z) + B_x A_y A_z]); evalx<l>(c_x)
+// then finishes a direction of that row.
 template <int D, int M, typename R> struct ETab {
   PTab<D, R> p;
   GTab<D, R> g;
+  R rp, rP, rQ;
   template <int l>
   __device__ __forceinline__ void build(const BState<D, M, R>& s, const DevMech& m,
                                         const Units& un) {
     if constexpr (l == M) gtab<D, M, R>(s, g);
     else ptab<D, M, l, R>(s, p, m, un);
   }
-  template <int l> __device__ __forceinline__ R eval(const int (&c)[3]) const {
-    if constexpr (l == M) return geval<D, R>(g, c);
-    else return peval<D, R>(p, c);
+  template <int l> __device__ __forceinline__ void row(int cy, int cz) {
+    if constexpr (l == M) {
+      const R ay = sel3(cy, g.A[1]), by = sel3(cy, g.B[1]);
+      if constexpr (D == 3) {
+        const R az = sel3(cz, g.A[2]), bz = sel3(cz, g.B[2]);
+        rP = ay * az;
+        rQ = g.U * rP + by * az + ay * bz;
+      } else {
+        rP = ay;
+        rQ = g.U * ay + by;
+      }
+    } else {
+      rp = p.pref * sel3(cy, p.t[1]);
+      if constexpr (D == 3) rp *= sel3(cz, p.t[2]);
+    }
+  }
+  template <int l> __device__ __forceinline__ R evalx(int cx) const {
+    if constexpr (l == M) return g.rho * (sel3(cx, g.A[0]) * rQ + sel3(cx, g.B[0]) * rP);
+    else return rp * sel3(cx, p.t[0]);
   }
 };
 
@@ -258,7 +250,8 @@ template <int E> struct ForL<E, E> {
 };
 
 // Population sums of a pass, lattice by lattice: fn.template setup<l>()
-// once per lattice, then fn.template get<l>(i, c) for every direction.
+// once per lattice, then, row by row, fn.template row<l>(c_y, c_z) and
+// fn.template get<l>(i, c) for the row's three directions.
 // Directions in rows of three (c_x = -1, 0, 1 at compile time, a row's loads
 // in flight together); a row enters through its sum s and difference
 // d = f_+ - f_- (and f_+ + f_- for P_xx).  kDensOnly: the densities rho_a,
@@ -277,6 +270,7 @@ __device__ __forceinline__ void bsums(F& fn, BSums<D, M, R>& z) {
 #pragma unroll 1
     for (int yz = 0; yz < Q / 3; ++yz) {
       const int cy = yz % 3 - 1, cz = D == 3 ? yz / 3 - 1 : 0;
+      fn.template row<l>(cy, cz);
       R v[3];
 #pragma unroll
       for (int k = 0; k < 3; ++k) {
@@ -338,6 +332,7 @@ template <int D, int M, typename S, typename R> struct BPull {
   bool bbk;
   __device__ __forceinline__ bool incoming(int i) const { return inc >> i & 1u; }
   template <int l> __device__ __forceinline__ void setup() {}
+  template <int l> __device__ __forceinline__ void row(int, int) {}
   template <int l> __device__ __forceinline__ R pull(int i) const {
     const bool bb = bbk && incoming(i);
     const long long mm = bb ? n : sn[i * kBnd];
@@ -357,6 +352,7 @@ template <int D, int M, typename S, typename R> struct BStorePull {
   double* P;
   long long st;
   template <int l> __device__ __forceinline__ void setup() {}
+  template <int l> __device__ __forceinline__ void row(int, int) {}
   template <int l> __device__ __forceinline__ R get(int i, const int (&)[3]) const {
     const R v = p.template pull<l>(i);
     P[(long long)(l * Q + i) * st] = double(v);
@@ -371,6 +367,7 @@ template <int D, int M, typename S, typename R> struct BNode {
   const float4* codec;
   long long N, node;
   template <int l> __device__ __forceinline__ void setup() {}
+  template <int l> __device__ __forceinline__ void row(int, int) {}
   template <int l> __device__ __forceinline__ R get(int i, const int (&)[3]) const {
     return Codec<S>::template dec<R>(__ldg(src + (long long)(l * Q + i) * N + node), codec,
                                      l * Q + i);
@@ -387,8 +384,11 @@ template <int D, int M, typename S, typename R> struct BLocal {
   template <int l> __device__ __forceinline__ void setup() {
     ta.template build<l>(*A, *m, *un);
   }
+  template <int l> __device__ __forceinline__ void row(int cy, int cz) {
+    ta.template row<l>(cy, cz);
+  }
   template <int l> __device__ __forceinline__ R get(int i, const int (&c)[3]) const {
-    return p.incoming(i) ? ta.template eval<l>(c) : p.template pull<l>(i);
+    return p.incoming(i) ? ta.template evalx<l>(c[0]) : p.template pull<l>(i);
   }
 };
 
@@ -409,16 +409,21 @@ template <int D, int M, typename S, typename R> struct BFinal {
     if (!same) tb.template build<l>(*Bt, *lo.m, *lo.un);
     tl.template build<l>(*L, *lo.m, *lo.un);
   }
+  template <int l> __device__ __forceinline__ void row(int cy, int cz) {
+    lo.template row<l>(cy, cz);
+    if (!same) tb.template row<l>(cy, cz);
+    tl.template row<l>(cy, cz);
+  }
   template <int l> __device__ __forceinline__ R get(int i, const int (&c)[3]) const {
-    const R loc = tl.template eval<l>(c);
+    const R loc = tl.template evalx<l>(c[0]);
     R v;
     if (simple) {
       v = loc;
     } else if (lo.p.incoming(i)) {
-      const R a = lo.ta.template eval<l>(c);
-      v = (same ? a : tb.template eval<l>(c)) + a - loc;
+      const R a = lo.ta.template evalx<l>(c[0]);
+      v = (same ? a : tb.template evalx<l>(c[0])) + a - loc;
     } else {
-      v = (same ? lo.ta.template eval<l>(c) : tb.template eval<l>(c)) +
+      v = (same ? lo.ta.template evalx<l>(c[0]) : tb.template evalx<l>(c[0])) +
           lo.p.template pull<l>(i) - loc;
     }
     P[(long long)(l * Q + i) * st] = double(v);

@@ -33,6 +33,9 @@ pytestmark = pytest.mark.gpu
 # flame's steep front amplifies over seven steps to ~2e-5 of a lattice's
 # largest population
 TOL = {"fp64": 1e-12, "fp32": 5e-5}
+# temperature (K): FP64 to its Newton tolerance; FP32 storage to well inside
+# its stated 0.05 K against the oracle (FP32 moments summed in another order)
+TOL_T = {"fp64": 3e-6, "fp32": 1e-3}
 
 
 @pytest.fixture(scope="module")
@@ -82,7 +85,7 @@ def test_single_launch_equals_separate_steps_d3q27(mech, precision, npt, split):
         assert np.all(err <= TOL[precision]), (w.get("name"), err.max())
         ta, tb = a.moments()["T"], b.moments()["T"]
         k = _keep(a, w)
-        assert np.max(np.abs(ta.reshape(-1)[k] - tb.reshape(-1)[k])) <= 1e-9 * 3000
+        assert np.max(np.abs(ta.reshape(-1)[k] - tb.reshape(-1)[k])) <= TOL_T[precision]
         a.close()
         b.close()
 
