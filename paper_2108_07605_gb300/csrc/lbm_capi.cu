@@ -65,9 +65,9 @@ constexpr long long kSmallGrid = 152LL * 4 * 128;
 
 // Defaults, measured on one GB300.  plan: a batch plan's placement, whose
 // default for FP64 storage below kPlanSingleLaunch nodes in total is the
-// single launch over the work-list with split collision (17 % faster than
+// single launch over the work-list with split collision (14 % faster than
 // one launch per kernel on a mix of eight domains of 92k nodes in all; on
-// batches of about a million nodes one launch per kernel is 2 % faster);
+// batches of about a million nodes one launch per kernel is 2-6 % faster);
 // FP32 and FP16 plans keep one launch per kernel, whose kernels hold fewer
 // registers than the single launch.  FP64, a grid that fills the GPU at one
 // thread per node: the fused collision (3 % faster on the 600x40x40 tube);

@@ -2,6 +2,8 @@
 
     python -m paper_2108_07605_gb300.serve [--requests 64] [--seed 0]
         [--budget-gb 40] [--chunk 100] [--precision fp32] [--step-scale 1.0]
+    python -m paper_2108_07605_gb300.serve --plan-study [--precision fp64]
+        (batch-plan placements timed on groups of the mix; plan_study)
 
 Requests (reactor, flame or channel solves of different grid sizes) arrive
 over time.  The loop admits a request as soon as it has arrived and its
@@ -260,6 +262,71 @@ def summarize(done, elapsed, node_updates):
     }
 
 
+# placements of a batch plan timed by plan_study: name -> lbm_batch_set_launch
+# arguments (p0: one launch per kernel; p1: the same on persistent grids;
+# p2: the whole step as one launch, nN = nodes per thread, f = fused
+# collision)
+PLAN_PLACEMENTS = {
+    "p0": dict(persistent=0), "p0 fused": dict(persistent=0, collide_split=0, chem_lanes=1),
+    "p1": dict(persistent=1),
+    "p2 n1": dict(persistent=2, collide_split=1, nodes_per_thread=1),
+    "p2 n2": dict(persistent=2, collide_split=1, nodes_per_thread=2),
+    "p2 n4": dict(persistent=2, collide_split=1, nodes_per_thread=4),
+    "p2 f n1": dict(persistent=2, collide_split=0, nodes_per_thread=1),
+    "p2 f n2": dict(persistent=2, collide_split=0, nodes_per_thread=2),
+}
+
+
+def plan_study(mech, precision, device=0, steps=20, warmup=4, reps=3):
+    """Batch-plan placements on groups of the serving mix (seed 0): small8,
+    its first eight D3Q27 requests of at most 40 000 nodes; mixed, its
+    first twelve D3Q27 requests; tube, the 600x40x40 microtube alone (also
+    timed with lbm_step).  Per group: ms per step of every placement (best of
+    `reps` runs of `steps` steps after `warmup`, host clock around
+    lbm_batch_run and a device synchronize) and the autotuner's pick.
+    Yields one dict per group."""
+    import torch
+    from lbm_workloads.fields import microtube, serving_mix
+    stream = serving_mix(seed=0, n_requests=64, mech=mech)
+    d3 = [w for _, w in stream if w["lattice"] == "D3Q27"]
+    groups = {"small8": [w for w in d3 if int(np.prod(w["shape"])) <= 40000][:8],
+              "mixed": d3[:12], "tube": [microtube(mech=mech)]}
+
+    def solver(w):
+        s = lbm.Solver(mech, lattice=w["lattice"], shape=w["shape"], dx=w["dx"],
+                       precision=precision, substeps=w["substeps"], T_max=w["T_max"],
+                       device=device, **_bc_kwargs(w))
+        s.init_fields_pressure(w["P"], w["u"], w["T"], w["Y"])
+        return s
+
+    def timed(run):
+        run(warmup)
+        torch.cuda.synchronize(device)
+        best = float("inf")
+        for _ in range(reps):
+            t0 = time.perf_counter()
+            run(steps)
+            torch.cuda.synchronize(device)
+            best = min(best, (time.perf_counter() - t0) / steps)
+        return best * 1e3
+
+    for name, ws in groups.items():
+        ss = [solver(w) for w in ws]
+        out = {"group": name, "precision": precision, "domains": len(ss),
+               "nodes": int(sum(s.N for s in ss)), "ms_per_step": {}}
+        if len(ss) == 1:
+            out["ms_per_step"]["lbm_step"] = timed(ss[0].step)
+        plan = lbm.lbm_batch_create([s.h for s in ss])
+        for pname, kw in PLAN_PLACEMENTS.items():
+            lbm.lbm_batch_set_launch(plan, **kw)
+            out["ms_per_step"][pname] = timed(lambda n: lbm.lbm_batch_run(plan, n))
+        out["autotune"] = lbm.lbm_batch_autotune(plan, 3)
+        lbm.lbm_batch_destroy(plan)
+        for s in ss:
+            s.close()
+        yield out
+
+
 def main():
     p = argparse.ArgumentParser()
     p.add_argument("--requests", type=int, default=64)
@@ -274,6 +341,8 @@ def main():
     p.add_argument("--max-nodes", type=int, default=0,
                    help="fifo: cap on the resident requests' nodes (0: admit by memory only)")
     p.add_argument("--policy", default="srpt", choices=["srpt", "fifo"])
+    p.add_argument("--plan-study", action="store_true",
+                   help="time the batch-plan placements on groups of the mix instead")
     p.add_argument("--active-nodes", type=int, default=600_000,
                    help="srpt: nodes advanced per tick (least remaining work first)")
     args = p.parse_args()
@@ -282,6 +351,10 @@ def main():
     from lbm_workloads.fields import serving_mix
     from lbm_workloads.mechanism import h2_air_synthetic
     mech = h2_air_synthetic()
+    if args.plan_study:
+        for out in plan_study(mech, args.precision):
+            print(json.dumps(out), flush=True)
+        return
     stream = serving_mix(seed=args.seed, n_requests=args.requests, mech=mech)
     for _, w in stream:
         w["steps"] = max(1, int(round(w["steps"] * args.step_scale)))
