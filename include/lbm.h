@@ -235,15 +235,19 @@ lbm_status lbm_init_fields_pressure(lbm_t h, const double* P, const double* u,
  * Asynchronous on the handle's stream. */
 lbm_status lbm_step(lbm_t h, int nsteps);
 
-/* Advance several handles by nsteps steps together: each step is one launch
- * per kernel over the concatenated tiles of all handles (128-node tiles; the
- * boundary kernel over 4-interface-node tiles), so many small domains fill
- * the GPU.  The handles must share lattice, species count, precision and
- * device; each keeps its own mechanism, units and boundaries.  The work runs
- * on hs[0]'s stream after the earlier work of every handle's stream, and
- * every handle's stream waits for it.  Results equal n separate lbm_step
- * calls to rounding (the same per-node arithmetic in separately compiled
- * kernels). */
+/* Advance several handles by nsteps steps together, in the placement a
+ * batch plan of the same handles starts with (see lbm_batch_set_launch):
+ * FP64 storage under 311,296 nodes in all, each step is ONE persistent
+ * launch over a work-list of the handles' tiles (persistent = 2); else one
+ * launch per kernel over the concatenated tiles (128-node tiles, 64
+ * interface nodes per boundary block), so many small domains fill the GPU.
+ * The handles must share lattice, species count, precision and device; each
+ * keeps its own mechanism, units and boundaries.  The work runs on hs[0]'s
+ * stream after the earlier work of every handle's stream, and every
+ * handle's stream waits for it; with the single launch the call returns
+ * after the work (its work-list is freed).  Results equal n separate
+ * lbm_step calls to rounding (the same per-node arithmetic, summed in
+ * another order where the placements differ). */
 lbm_status lbm_batch_step(lbm_t* hs, int n, int nsteps);
 
 /* A batch plan: the batched step of lbm_batch_step for a fixed set of

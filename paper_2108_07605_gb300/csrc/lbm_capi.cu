@@ -685,6 +685,54 @@ void fill_units(const lbm_config& cfg, Units& un) {
 }
 }  // namespace lbm
 
+namespace {
+
+// The work-list of the single-launch step (PItem): stage 1 (the boundary
+// items of every domain, then the moments items), stage 2 (parameter items),
+// stage 3 (collision items), each stage domain by domain.  nsync: the sync
+// words the launch needs.
+void build_worklist(const long long* nodes, const long long* nif, int n, int npt, bool split,
+                    std::vector<PItem>& items, int& nsync) {
+  items.clear();
+  const long long tile = (long long)kPersistThreads * npt;
+  std::vector<int> n1(n, 0), pbase(n, 0);
+  for (int k = 0; k < n; ++k)
+    for (long long f = 0; f < nif[k]; f += kPersistBndNodes, ++n1[k])
+      items.push_back(PItem{PI_BND, k, f, 0, 0});
+  for (int k = 0; k < n; ++k)
+    for (long long f = 0; f < nodes[k]; f += tile, ++n1[k])
+      items.push_back(PItem{PI_MOM, k, f, 0, 0});
+  int nflag = 0;
+  if (!split) {
+    for (int k = 0; k < n; ++k)
+      for (long long f = 0; f < nodes[k]; f += tile)
+        items.push_back(PItem{PI_COLLIDE, k, f, n1[k], 0});
+    nsync = kSyncHead + n;
+    return;
+  }
+  for (int k = 0; k < n; ++k) {
+    pbase[k] = nflag;
+    for (long long f = 0; f < nodes[k]; f += tile)
+      items.push_back(PItem{PI_PREP, k, f, n1[k], nflag++});
+  }
+  for (int k = 0; k < n; ++k)
+    for (long long f = 0; f < nodes[k]; f += kCollNodesPerBlock)
+      items.push_back(PItem{PI_COLL, k, f, pbase[k] + (int)(f / tile), 0});
+  nsync = kSyncHead + n + nflag;
+}
+
+void build_worklist(lbm_ctx* const* hs, int n, int npt, bool split, std::vector<PItem>& items,
+                    int& nsync) {
+  std::vector<long long> nodes(n), nif(n);
+  for (int k = 0; k < n; ++k) {
+    nodes[k] = hs[k]->g.N;
+    nif[k] = hs[k]->bc.n_if;
+  }
+  build_worklist(nodes.data(), nif.data(), n, npt, split, items, nsync);
+}
+
+}  // namespace
+
 extern "C" {
 
 void lbm_config_defaults(lbm_config* cfg) {
@@ -1064,7 +1112,10 @@ lbm_status lbm_batch_step(lbm_t* hs, int n, int nsteps) {
   DeviceGuard dg(h0->cfg.device);
   std::vector<DomainDev> doms;
   BatchGrids gr;
-  const Launch lc = resolve_launch(lbm_launch{-1, -1, -1, -1}, total_nodes(hs, n), hs[0]->cfg.precision);
+  // the placement a new plan of these handles starts with (for FP64 under
+  // kPlanSingleLaunch nodes: the whole step as one launch over a work-list)
+  const Launch lc = resolve_launch(lbm_launch{-1, -1, -1, -1}, total_nodes(hs, n),
+                                   hs[0]->cfg.precision, true);
   fill_domains(hs, n, lc, doms, gr);
   // every handle's earlier work precedes the batch; the batch runs on the
   // first handle's stream and each handle's stream waits for it afterwards
@@ -1080,14 +1131,35 @@ lbm_status lbm_batch_step(lbm_t* hs, int n, int nsteps) {
   if (!ddev) e = cudaErrorMemoryAllocation;
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(ddev, doms.data(), n * sizeof(DomainDev), cudaMemcpyHostToDevice, s0);
+  std::vector<PItem> items;
+  PItem* items_dev = nullptr;
+  int* sync_dev = nullptr;
+  if (e == cudaSuccess && lc.persistent == 2) {
+    int nsync = 0;
+    build_worklist(hs, n, lc.npt, lc.coll_split != 0, items, nsync);
+    items_dev = static_cast<PItem*>(dalloc(h0->cfg, items.size() * sizeof(PItem)));
+    sync_dev = static_cast<int*>(dalloc(h0->cfg, (size_t)nsync * sizeof(int)));
+    if (!items_dev || !sync_dev) e = cudaErrorMemoryAllocation;
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(items_dev, items.data(), items.size() * sizeof(PItem),
+                          cudaMemcpyHostToDevice, s0);
+    gr.items = items_dev;
+    gr.nitems = (int)items.size();
+    gr.sync = sync_dev;
+    gr.nsync = nsync;
+  }
   for (int step = 0; step < nsteps && e == cudaSuccess; ++step)
     e = launch_batch_step(h0->D, h0->M, kernel_precision(h0->cfg), ddev, n, gr, lc, step & 1, s0);
   if (e == cudaSuccess) e = cudaEventRecord(ev, s0);
   for (int k = 1; k < n && e == cudaSuccess; ++k)
     if (hs[k]->stream != s0) e = cudaStreamWaitEvent(hs[k]->stream, ev, 0);
-  if (ddev) {
-    if (!h0->cfg.dev_free) cudaStreamSynchronize(s0);  // plain cudaFree is not stream-ordered
+  if (ddev || items_dev || sync_dev) {
+    // plain cudaFree is not stream-ordered; the host copy of the items must
+    // outlive its asynchronous upload
+    if (!h0->cfg.dev_free || items_dev) cudaStreamSynchronize(s0);
     dfree(h0->cfg, ddev);
+    dfree(h0->cfg, items_dev);
+    dfree(h0->cfg, sync_dev);
   }
   if (ev) cudaEventDestroy(ev);
   if (e != cudaSuccess) return cuda_fail(h0, e, "batched step");
@@ -1118,50 +1190,6 @@ struct lbm_batch_ctx {
 };
 
 namespace {
-
-// The work-list of the single-launch step (PItem): stage 1 (the boundary
-// items of every domain, then the moments items), stage 2 (parameter items),
-// stage 3 (collision items), each stage domain by domain.  nsync: the sync
-// words the launch needs.
-void build_worklist(const long long* nodes, const long long* nif, int n, int npt, bool split,
-                    std::vector<PItem>& items, int& nsync) {
-  items.clear();
-  const long long tile = (long long)kPersistThreads * npt;
-  std::vector<int> n1(n, 0), pbase(n, 0);
-  for (int k = 0; k < n; ++k)
-    for (long long f = 0; f < nif[k]; f += kPersistBndNodes, ++n1[k])
-      items.push_back(PItem{PI_BND, k, f, 0, 0});
-  for (int k = 0; k < n; ++k)
-    for (long long f = 0; f < nodes[k]; f += tile, ++n1[k])
-      items.push_back(PItem{PI_MOM, k, f, 0, 0});
-  int nflag = 0;
-  if (!split) {
-    for (int k = 0; k < n; ++k)
-      for (long long f = 0; f < nodes[k]; f += tile)
-        items.push_back(PItem{PI_COLLIDE, k, f, n1[k], 0});
-    nsync = kSyncHead + n;
-    return;
-  }
-  for (int k = 0; k < n; ++k) {
-    pbase[k] = nflag;
-    for (long long f = 0; f < nodes[k]; f += tile)
-      items.push_back(PItem{PI_PREP, k, f, n1[k], nflag++});
-  }
-  for (int k = 0; k < n; ++k)
-    for (long long f = 0; f < nodes[k]; f += kCollNodesPerBlock)
-      items.push_back(PItem{PI_COLL, k, f, pbase[k] + (int)(f / tile), 0});
-  nsync = kSyncHead + n + nflag;
-}
-
-void build_worklist(lbm_ctx* const* hs, int n, int npt, bool split, std::vector<PItem>& items,
-                    int& nsync) {
-  std::vector<long long> nodes(n), nif(n);
-  for (int k = 0; k < n; ++k) {
-    nodes[k] = hs[k]->g.N;
-    nif[k] = hs[k]->bc.n_if;
-  }
-  build_worklist(nodes.data(), nif.data(), n, npt, split, items, nsync);
-}
 
 cudaError_t batch_upload(lbm_batch_ctx* b) {
   std::vector<DomainDev> doms;
