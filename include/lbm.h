@@ -393,6 +393,13 @@ typedef struct {
   double u_max;          /* largest |u| (m/s) */
 } lbm_diag;
 lbm_status lbm_diagnostics(lbm_t h, lbm_diag* out);
+/* The same over the nodes with x in [x0, x0 + nplanes) only (the own planes
+ * of a slab, whose partial results combine over the slabs: sums add,
+ * maxima take the largest, flame_x that of the largest hrr_max); flame_x is
+ * the x coordinate in this handle's grid, NaN (and hrr_max, T_max, u_max
+ * -inf) when the planes hold no fluid node.  LBM_ERR_RANGE for planes
+ * outside 0..nx-1. */
+lbm_status lbm_diagnostics_planes(lbm_t h, int x0, int nplanes, lbm_diag* out);
 
 /* All stored populations converted to FP64, layout [lattice][i][N]
  * (lattice-unit values: species and f in kg/m^3, g in kg/m^3 * J/kg / c_ref^2). */

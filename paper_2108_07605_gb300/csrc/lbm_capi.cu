@@ -1,6 +1,7 @@
 // Host side of the C ABI declared in include/lbm.h: configuration checks,
 // mechanism preprocessing, device buffers, launches and error reporting.
 #include <algorithm>
+#include <climits>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -1524,9 +1525,11 @@ lbm_status lbm_moments(lbm_t h, double* rho, double* u, double* T, double* Y, do
   return check_status(h);
 }
 
-lbm_status lbm_diagnostics(lbm_t h, lbm_diag* out) {
+lbm_status lbm_diagnostics_planes(lbm_t h, int x0, int nplanes, lbm_diag* out) {
   if (!h || !out) return fail(h, LBM_ERR_INVALID, "handle or out is NULL");
   if (!h->initialized) return fail(h, LBM_ERR_STATE, "lbm_diagnostics before lbm_init_fields");
+  if (x0 < 0 || nplanes < 0 || x0 + (long long)nplanes > h->g.nx)
+    return fail(h, LBM_ERR_RANGE, "planes outside 0..nx-1");
   DeviceGuard dg(h->cfg.device);
   const long long nb = (h->g.N + 127) / 128;
   const size_t need = (size_t)(nb + 1) * sizeof(DiagPart);
@@ -1536,7 +1539,7 @@ lbm_status lbm_diagnostics(lbm_t h, lbm_diag* out) {
   DiagPart* dout = part + nb;
   cudaError_t e = launch_diagnostics(h->D, h->M, kernel_precision(h->cfg), h->mech, h->g, h->un,
                                      h->pops[h->cur], h->Tf, h->bc.tag, part, dout, h->status,
-                                     h->stream);
+                                     x0, x0 + nplanes, h->stream);
   DiagPart r;
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(&r, dout, sizeof(DiagPart), cudaMemcpyDeviceToHost, h->stream);
@@ -1545,10 +1548,16 @@ lbm_status lbm_diagnostics(lbm_t h, lbm_diag* out) {
   const double cell = h->D == 3 ? h->un.dx * h->un.dx * h->un.dx : h->un.dx * h->un.dx;
   out->hrr_integral = r.q_sum * cell;
   out->hrr_max = r.q_max;
-  out->flame_x = (double)(r.n_max % h->g.nx) * h->un.dx;
+  // no fluid node in the planes: no maximum, no position
+  out->flame_x = r.n_max == LLONG_MAX ? NAN : (double)(r.n_max % h->g.nx) * h->un.dx;
   out->T_max = r.T_max;
   out->u_max = r.u_max;
   return check_status(h);
+}
+
+lbm_status lbm_diagnostics(lbm_t h, lbm_diag* out) {
+  if (!h) return fail(h, LBM_ERR_INVALID, "handle or out is NULL");
+  return lbm_diagnostics_planes(h, 0, h->g.nx, out);
 }
 
 lbm_status lbm_get_populations(lbm_t h, double* out, int on_device) {

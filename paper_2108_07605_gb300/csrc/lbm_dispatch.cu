@@ -109,10 +109,10 @@ __global__ void k_diag_final(const DiagPart* __restrict__ part, int nb, DiagPart
 cudaError_t launch_diagnostics(int D, int M, lbm_precision prec, const DevMech& mech,
                                const Geom& g, const Units& un, const void* pops,
                                const double* Tfield, const int* tag, DiagPart* part,
-                               DiagPart* out, int* status, cudaStream_t s) {
+                               DiagPart* out, int* status, int x0, int x1, cudaStream_t s) {
   const KernelSet* k = kernel_set(D, M, prec);
   if (!k) return cudaErrorInvalidValue;
-  cudaError_t e = k->diag(mech, g, un, pops, Tfield, tag, part, status, s);
+  cudaError_t e = k->diag(mech, g, un, pops, Tfield, tag, part, status, x0, x1, s);
   if (e != cudaSuccess) return e;
   const int nb = (int)((g.N + 127) / 128);
   k_diag_final<<<1, 256, 0, s>>>(part, nb, out);

@@ -267,7 +267,7 @@ struct KernelSet {
                      double* E, int* status, cudaStream_t s);
   cudaError_t (*diag)(const DevMech& mech, const Geom& g, const Units& un, const void* pops,
                       const double* Tfield, const int* tag, DiagPart* part, int* status,
-                      cudaStream_t s);
+                      int x0, int x1, cudaStream_t s);
   int record_fields;   // moment-record fields
   int param_fields;    // collision-parameter fields
 };
@@ -298,12 +298,12 @@ cudaError_t launch_moments_out(int D, int M, lbm_precision prec, const DevMech& 
 cudaError_t launch_to_fp64(lbm_precision prec, const void* pops, double* out,
                            long long count, cudaStream_t s, long long N = 1,
                            const float4* codec = nullptr);
-// Flame diagnostics: per-block partials, then their deterministic reduction
-// into out (one DiagPart).
+// Flame diagnostics over the nodes with x in [x0, x1): per-block partials,
+// then their deterministic reduction into out (one DiagPart).
 cudaError_t launch_diagnostics(int D, int M, lbm_precision prec, const DevMech& mech,
                                const Geom& g, const Units& un, const void* pops,
                                const double* Tfield, const int* tag, DiagPart* part,
-                               DiagPart* out, int* status, cudaStream_t s);
+                               DiagPart* out, int* status, int x0, int x1, cudaStream_t s);
 // FP16 storage codec (lbm_dispatch.cu)
 cudaError_t launch_codec_extent(const float* eq, const float* off, int L, int Q, long long N,
                                 unsigned* dev_max, unsigned* abs_max, cudaStream_t s);

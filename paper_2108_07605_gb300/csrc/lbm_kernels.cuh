@@ -2081,7 +2081,7 @@ template <int D, int M, typename S>
 __global__ void __launch_bounds__(128)
 k_diag(const S* __restrict__ pops, const double* __restrict__ Tf, const int* __restrict__ tag,
        DiagPart* __restrict__ part, int* __restrict__ status, Geom g, Units un,
-       const __grid_constant__ DevMech mech) {
+       const __grid_constant__ DevMech mech, int x0, int x1) {
   constexpr int Q = Lat<D>::Q;
   __shared__ double s_sum[128], s_qmax[128], s_T[128], s_u[128];
   __shared__ long long s_n[128];
@@ -2089,7 +2089,8 @@ k_diag(const S* __restrict__ pops, const double* __restrict__ Tf, const int* __r
   const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   double q = 0.0, qmax = -INFINITY, Tmax = -INFINITY, umax = -INFINITY;
   long long nmax = LLONG_MAX;
-  if (n < N && !(tag && tag[n] == TAG_SOLID)) {
+  const int xn = (int)(n % g.nx);   // the nodes with x in [x0, x1) only
+  if (n < N && xn >= x0 && xn < x1 && !(tag && tag[n] == TAG_SOLID)) {
     double rho = 0.0, rhoE = 0.0, j[D], rs[M];
     for (int d = 0; d < D; ++d) j[d] = 0.0;
     for (int a = 0; a < M; ++a) rs[a] = 0.0;
@@ -2353,9 +2354,9 @@ static cudaError_t init_impl(const DevMech& mech, const Geom& g, const Units& un
 template <int D, int M, typename S>
 static cudaError_t diag_impl(const DevMech& mech, const Geom& g, const Units& un,
                              const void* pops, const double* Tfield, const int* tag,
-                             DiagPart* part, int* status, cudaStream_t s) {
+                             DiagPart* part, int* status, int x0, int x1, cudaStream_t s) {
   k_diag<D, M, S><<<blocks_for(g.N, 128), 128, 0, s>>>(static_cast<const S*>(pops), Tfield, tag,
-                                                        part, status, g, un, mech);
+                                                        part, status, g, un, mech, x0, x1);
   return cudaGetLastError();
 }
 

@@ -120,6 +120,7 @@ EXPORTS = {
     "lbm_moments": (C.c_int, [C.c_void_p] + [C.c_void_p] * 5 + [C.c_int]),
     "lbm_get_populations": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int]),
     "lbm_diagnostics": (C.c_int, [C.c_void_p, C.POINTER(lbm_diag)]),
+    "lbm_diagnostics_planes": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.POINTER(lbm_diag)]),
     "lbm_synchronize": (C.c_int, [C.c_void_p]),
     "lbm_get_state": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_size_t)]),
     "lbm_set_state": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t]),
@@ -381,6 +382,13 @@ def lbm_moments(h, rho=None, u=None, T=None, Y=None, E=None):
 def lbm_diagnostics(h):
     out = lbm_diag()
     _check(load_library().lbm_diagnostics(h, C.byref(out)), h)
+    return {k: getattr(out, k) for k, _ in lbm_diag._fields_}
+
+
+def lbm_diagnostics_planes(h, x0, nplanes):
+    """lbm_diagnostics over the planes x0 .. x0 + nplanes - 1 only."""
+    out = lbm_diag()
+    _check(load_library().lbm_diagnostics_planes(h, int(x0), int(nplanes), C.byref(out)), h)
     return {k: getattr(out, k) for k, _ in lbm_diag._fields_}
 
 

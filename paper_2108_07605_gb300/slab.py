@@ -25,6 +25,11 @@ to the neighbouring slabs' ghost planes (point-to-point, torch.distributed
 P2P over gloo or NCCL, or direct copies between handles in one process).
 Nothing here computes a step of the method: the engine (the CUDA library's
 handle, or any object with get_planes / set_planes / step) does.
+
+Diagnostics: each slab evaluates the flame diagnostics of its own planes
+(engine.diagnostics), and one all-gather of five scalars per slab combines
+them into those of the whole domain (heat release integrals add, maxima
+take the largest, the flame position follows the largest heat release).
 """
 import numpy as np
 
@@ -144,6 +149,55 @@ class Exchange:
             engine.step(1)
 
 
+def combine_diagnostics(parts):
+    """Flame diagnostics of the whole domain from those of the slabs' own
+    planes (each a dict of lbm_diagnostics_planes with flame_x already in
+    global x): heat release integrals add, maxima take the largest, the flame
+    position is that of the largest heat release (among equal maxima the
+    smallest x, as on one domain: the slabs are in x order)."""
+    out = {"hrr_integral": float(sum(p["hrr_integral"] for p in parts))}
+    best = None
+    for p in parts:
+        if best is None or p["hrr_max"] > best["hrr_max"]:
+            best = p
+    out["hrr_max"] = best["hrr_max"]
+    out["flame_x"] = best["flame_x"]
+    out["T_max"] = max(p["T_max"] for p in parts)
+    out["u_max"] = max(p["u_max"] for p in parts)
+    return out
+
+
+def own_diagnostics(layout, rank, engine, dx):
+    """The flame diagnostics of the slab's own planes (engine.diagnostics(x0,
+    n), x in the slab's local grid), the flame position shifted to global x
+    (the local plane i is the global plane g_lo + i)."""
+    x_lo, x_hi, g_lo, g_hi = layout.local(rank)
+    own = engine.diagnostics(x_lo - g_lo, x_hi - x_lo)
+    fx = own["flame_x"]
+    if fx == fx:   # not NaN: the plane index times dx, as on one domain
+        fx = (int(round(fx / dx)) + g_lo) * dx
+    return dict(own, flame_x=fx)
+
+
+def diagnostics(layout, rank, engine, dx, pg=None):
+    """The whole domain's flame diagnostics from every rank's slab: each rank
+    evaluates its own planes (own_diagnostics), and one all-gather of five
+    scalars per rank (torch.distributed, or none for one slab) combines them
+    identically on every rank."""
+    own = own_diagnostics(layout, rank, engine, dx)
+    if pg is None or layout.world == 1:
+        return combine_diagnostics([own])
+    import torch
+    keys = ("hrr_integral", "hrr_max", "flame_x", "T_max", "u_max")
+    mine = torch.tensor([float(own[k]) for k in keys], dtype=torch.float64)
+    if pg.get_backend() == "nccl":
+        mine = mine.cuda()
+    gathered = [torch.empty_like(mine) for _ in range(layout.world)]
+    pg.all_gather(gathered, mine)
+    parts = [dict(zip(keys, g.cpu().tolist())) for g in gathered]
+    return combine_diagnostics(parts)
+
+
 def exchange_in_process(layout, engines):
     """The same exchange between slabs held by one process (engines[rank]):
     direct copies, no collective."""
@@ -189,3 +243,6 @@ class SolverEngine:
 
     def step(self, n=1):
         self.s.step(n)
+
+    def diagnostics(self, x0, n):
+        return self.lbm.lbm_diagnostics_planes(self.s.h, x0, n)

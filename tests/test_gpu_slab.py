@@ -4,7 +4,8 @@ halo planes), and before every step the halos are copied between them
 (lbm_get_planes / lbm_set_planes, device to device; the copies run between
 the handles' steps, never while a kernel of the other handle waits).  The
 slabs' own planes equal the undivided domain's, bit for bit, in FP64 and
-FP32 storage.  On several GPUs the same exchange runs as NCCL point-to-point
+FP32 storage, and the flame diagnostics of the slabs' own planes combine
+into the undivided domain's (the integral to summation order).  On several GPUs the same exchange runs as NCCL point-to-point
 transfers (slab.Exchange); this run has one GPU."""
 import numpy as np
 import pytest
@@ -32,6 +33,7 @@ def test_two_slabs_equal_one_domain(case, precision):
     whole = make_gpu(mech, w, precision=precision)
     whole.step(nsteps)
     ref = whole.populations()
+    dref = whole.diagnostics()
     whole.close()
     layout = slab.SlabLayout(w["shape"][0], 2, w["faces"][0] == "periodic")
     parts = [make_gpu(mech, slab.slab_workload(w, layout, r), precision=precision)
@@ -41,6 +43,13 @@ def test_two_slabs_equal_one_domain(case, precision):
         slab.exchange_in_process(layout, engines)
         for e in engines:
             e.step(1)
+    # the whole domain's diagnostics from the slabs' own planes (the
+    # combination the ranks' all-gather performs)
+    dg = slab.combine_diagnostics([slab.own_diagnostics(layout, r, engines[r], w["dx"])
+                                   for r in range(2)])
+    assert dg["hrr_integral"] == pytest.approx(dref["hrr_integral"], rel=1e-12)
+    for k in ("hrr_max", "flame_x", "T_max", "u_max"):
+        assert dg[k] == dref[k], k
     nx, ny, nz = w["shape"]
     L, Q = ref.shape[:2]
     ref = ref.reshape(L, Q, nz, ny, nx)

@@ -5,7 +5,9 @@ temperature guesses) with its neighbour before every step, reproduce the
 undivided oracle run exactly on the slabs' own planes: a periodic box (a
 neighbour on both sides, the same rank), the flame layout (inlet and LODI
 outlet at the global faces) and the staircase tube with off-grid TMS
-targets.  The layout arithmetic is checked without ranks."""
+targets.  The ranks' flame diagnostics, each of its own planes and combined
+by one all-gather, equal the undivided domain's.  The layout arithmetic is
+checked without ranks."""
 import os
 import socket
 
@@ -38,11 +40,13 @@ def _case(name):
 
 
 class OracleEngine:
-    """The oracle as a slab engine: halo planes as float64 tensors."""
+    """The oracle as a slab engine: halo planes as float64 tensors; flame
+    diagnostics of a range of planes from the oracle's moments."""
 
-    def __init__(self, o):
+    def __init__(self, o, mech=None, w=None):
         import torch
         self.o, self.torch = o, torch
+        self.mech, self.w = mech, w
         L, Q, nz, ny, _ = o.pops.shape
         self.per_plane = L * Q * nz * ny + nz * ny
 
@@ -64,6 +68,17 @@ class OracleEngine:
     def step(self, n=1):
         self.o.step(n)
 
+    def diagnostics(self, x0, n):
+        from oracle import diagnostics
+        mo = self.o.moments()
+        sl = (Ellipsis, slice(x0, x0 + n))
+        solid = self.w.get("solid")
+        fluid = None if solid is None else ~np.asarray(solid)[sl]
+        d = diagnostics.diagnostics(self.mech, mo["rho"][sl], mo["u"][sl], mo["T"][sl],
+                                    mo["Y"][sl], self.w["dx"], 3, n, fluid)
+        d["flame_x"] += x0 * self.w["dx"]          # x in this engine's grid
+        return d
+
 
 def _rank_main(rank, world, port, name, nsteps, out):
     import torch
@@ -74,11 +89,12 @@ def _rank_main(rank, world, port, name, nsteps, out):
     mech, w = _case(name)
     layout = slab.SlabLayout(w["shape"][0], world, w["faces"][0] == "periodic")
     wl = slab_workload = slab.slab_workload(w, layout, rank)
-    eng = OracleEngine(make_oracle(mech, wl))
+    eng = OracleEngine(make_oracle(mech, wl), mech, wl)
     ex = slab.Exchange(layout, rank, dist)
     ex.step(eng, nsteps)
     a, b = ex.own
-    out[rank] = (wl["slab"]["x_lo"], eng.o.pops[..., a:b].copy(), eng.o.T[..., a:b].copy())
+    diag = slab.diagnostics(layout, rank, eng, w["dx"], dist)
+    out[rank] = (wl["slab"]["x_lo"], eng.o.pops[..., a:b].copy(), eng.o.T[..., a:b].copy(), diag)
     del slab_workload
     dist.barrier()
     dist.destroy_process_group()
@@ -95,8 +111,15 @@ def test_two_gloo_slabs_equal_the_undivided_domain(name, nsteps):
     mech, w = _case(name)
     o = make_oracle(mech, w)
     o.step(nsteps)
+    # the whole domain's flame diagnostics, combined by the ranks' all-gather
+    dref = OracleEngine(o, mech, w).diagnostics(0, w["shape"][0])
     for rank in (0, 1):
-        x_lo, pops, T = res[rank]
+        d = res[rank][3]
+        assert d["hrr_integral"] == pytest.approx(dref["hrr_integral"], rel=1e-12)
+        for k in ("hrr_max", "flame_x", "T_max", "u_max"):
+            assert d[k] == dref[k], (rank, k)
+    for rank in (0, 1):
+        x_lo, pops, T, _ = res[rank]
         n = pops.shape[-1]
         ref = o.pops[..., x_lo:x_lo + n]
         fluid = slice(None)
