@@ -186,6 +186,5 @@ __host__ inline ff ff_host(double d) {
   const float h = (float)d;
   return ff(h, (float)(d - (double)h));
 }
-__device__ __forceinline__ float ff_abs_hi(ff a) { return fabsf(a.hi); }
 
 }  // namespace lbm

@@ -32,16 +32,6 @@ __host__ __device__ constexpr int csq(int i, int D) {
   return cvel(i, 0) * cvel(i, 0) + cvel(i, 1) * cvel(i, 1) +
          (D == 3 ? cvel(i, 2) * cvel(i, 2) : 0);
 }
-// Isotropic stencil weights of the standard lattice: product of 2/3, 1/6,
-// evaluated in the caller's type R (a constant once the direction loop is
-// unrolled).
-template <typename R = double>
-__host__ __device__ constexpr R wstd(int i, int D) {
-  return (cvel(i, 0) == 0 ? R(2.0 / 3.0) : R(1.0 / 6.0)) *
-         (cvel(i, 1) == 0 ? R(2.0 / 3.0) : R(1.0 / 6.0)) *
-         (D == 3 ? (cvel(i, 2) == 0 ? R(2.0 / 3.0) : R(1.0 / 6.0)) : R(1));
-}
-
 // Per-axis product-form factor Psi_c(xi, P), Eqs. phi0, phiPlus, phis.
 template <typename R>
 __device__ __forceinline__ R psi1(int c, R xi, R P) {
@@ -245,37 +235,10 @@ __device__ void production_rates_ff(const DevMech& m, ff T, const ff* r, ff* rdo
 }
 
 // ------------------------------------------------------------------------
-// Gaussian elimination without pivoting for A V = B with 3 right-hand sides.
+// Gaussian elimination without pivoting for A V = B with 3 right-hand sides,
+// the matrix stored with entry (r, c) at A[(r M + c) st].
 // A is strictly row diagonally dominant (diagonal 1 + sum of |off-diagonal|),
 // so every pivot is at least 1.
-template <int M, int D, typename R>
-__device__ __forceinline__ void solve_dd(R (&A)[M][M], R (&B)[M][D]) {
-#pragma unroll
-  for (int k = 0; k < M; ++k) {
-    const R inv = R(1) / A[k][k];
-#pragma unroll
-    for (int r = k + 1; r < M; ++r) {
-      const R f = A[r][k] * inv;
-#pragma unroll
-      for (int c = k + 1; c < M; ++c) A[r][c] -= f * A[k][c];
-#pragma unroll
-      for (int d = 0; d < D; ++d) B[r][d] -= f * B[k][d];
-    }
-  }
-#pragma unroll
-  for (int k = M - 1; k >= 0; --k) {
-    const R inv = R(1) / A[k][k];
-#pragma unroll
-    for (int d = 0; d < D; ++d) {
-      R s = B[k][d];
-#pragma unroll
-      for (int c = k + 1; c < M; ++c) s -= A[k][c] * B[c][d];
-      B[k][d] = s * inv;
-    }
-  }
-}
-
-// The same elimination on a matrix stored with entry (r, c) at A[(r M + c) st].
 template <int M, int D, typename R>
 __device__ __forceinline__ void solve_dd_strided(R* A, int st, R (&B)[M][D]) {
 #pragma unroll
